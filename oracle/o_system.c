@@ -1,0 +1,639 @@
+/*
+ * Oracle: assembly of Eq. (MPMweak) (static part), penalty contact (Sec. 2.3),
+ * the ghost term (Sec. 4), strong Dirichlet conditions and the Newton-Raphson
+ * load step with line search (Sec. 2.4).  TEST INFRASTRUCTURE ONLY.
+ *
+ * Readings:
+ *  - quasi-static load steps: the inertia term of Eq. (MPMweak) is dropped;
+ *  - updated Lagrangian: S and grad S are fixed at the step start; gradients
+ *    in the current configuration are grad_x S = grad S . dF^{-1};
+ *    V_p sigma_p = V0_p tau_p;
+ *  - ghost: K_G added to the tangent and K_G du to the residual;
+ *  - contact: the 8 corners of each GIMP domain are the contact nodes,
+ *    eps_N = pf E_p (V0_p)^(2/3), frictionless, force spread to the grid by the
+ *    background basis at the corner;
+ *  - line search: eta = 1, else the best of {0.5, 0.25, 0.1};
+ *  - convergence: ||R_free|| <= tol * max(||f_int||, ||f_ext + f_c||).
+ */
+#include "o_internal.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+o_model* o_create(const o_params* prm) {
+  o_model* m = (o_model*)calloc(1, sizeof(o_model));
+  m->p = *prm;
+  m->D = prm->depth_max;
+  m->unit = prm->L / ldexp(1.0, m->D);
+  m->scale = ldexp(1.0, m->D) / prm->L;
+  return m;
+}
+
+void o_nodes_release(o_nodes* nd);
+
+void o_free(o_model* m) {
+  if (!m) return;
+  free(m->x); free(m->lp); free(m->l0); free(m->F); free(m->be);
+  free(m->V0); free(m->mass); free(m->E); free(m->ys);
+  o_tree_free(&m->t);
+  o_nodes_release(&m->nd);
+  free(m->nsup); free(m->sidx); free(m->S); free(m->dS);
+  free(m->populated); free(m->betaK); free(m->bcmask);
+  free(m->row_ptr); free(m->col); free(m->kg); free(m->gface);
+  free(m);
+}
+
+int o_set_points(o_model* m, int n, const double* x, const double* lp, const double* l0,
+                 const double* F, const double* be, const double* V0, const double* mass,
+                 const double* E, const double* ys) {
+  m->np = n;
+  m->cap = n;
+  m->x = (double*)realloc(m->x, sizeof(double) * 3 * (size_t)n);
+  m->lp = (double*)realloc(m->lp, sizeof(double) * 3 * (size_t)n);
+  m->l0 = (double*)realloc(m->l0, sizeof(double) * 3 * (size_t)n);
+  m->F = (double*)realloc(m->F, sizeof(double) * 9 * (size_t)n);
+  m->be = (double*)realloc(m->be, sizeof(double) * 6 * (size_t)n);
+  m->V0 = (double*)realloc(m->V0, sizeof(double) * (size_t)n);
+  m->mass = (double*)realloc(m->mass, sizeof(double) * (size_t)n);
+  m->E = (double*)realloc(m->E, sizeof(double) * (size_t)n);
+  m->ys = (double*)realloc(m->ys, sizeof(double) * (size_t)n);
+  memcpy(m->x, x, sizeof(double) * 3 * (size_t)n);
+  memcpy(m->lp, lp, sizeof(double) * 3 * (size_t)n);
+  memcpy(m->l0, l0, sizeof(double) * 3 * (size_t)n);
+  memcpy(m->F, F, sizeof(double) * 9 * (size_t)n);
+  memcpy(m->be, be, sizeof(double) * 6 * (size_t)n);
+  memcpy(m->V0, V0, sizeof(double) * (size_t)n);
+  memcpy(m->mass, mass, sizeof(double) * (size_t)n);
+  memcpy(m->E, E, sizeof(double) * (size_t)n);
+  memcpy(m->ys, ys, sizeof(double) * (size_t)n);
+  m->built = 0;
+  return O_OK;
+}
+
+int o_get_points(const o_model* m, double* x, double* lp, double* l0, double* F, double* be,
+                 double* V0, double* mass, double* E, double* ys) {
+  int n = m->np;
+  if (x) memcpy(x, m->x, sizeof(double) * 3 * (size_t)n);
+  if (lp) memcpy(lp, m->lp, sizeof(double) * 3 * (size_t)n);
+  if (l0) memcpy(l0, m->l0, sizeof(double) * 3 * (size_t)n);
+  if (F) memcpy(F, m->F, sizeof(double) * 9 * (size_t)n);
+  if (be) memcpy(be, m->be, sizeof(double) * 6 * (size_t)n);
+  if (V0) memcpy(V0, m->V0, sizeof(double) * (size_t)n);
+  if (mass) memcpy(mass, m->mass, sizeof(double) * (size_t)n);
+  if (E) memcpy(E, m->E, sizeof(double) * (size_t)n);
+  if (ys) memcpy(ys, m->ys, sizeof(double) * (size_t)n);
+  return O_OK;
+}
+
+void o_set_body_z(o_model* m, double z) { m->p.body_z = z; }
+
+int o_build(o_model* m, int nosplit) {
+  int st = o_build_tree(m);
+  if (st) return st;
+  if (!nosplit) {
+    st = o_split_points(m);
+    if (st) return st;
+  }
+  st = o_build_nodes(m);
+  if (st) return st;
+  st = o_build_basis(m);
+  if (st) return st;
+  st = o_build_pattern_and_ghost(m);
+  if (st) return st;
+  m->built = 1;
+  return O_OK;
+}
+
+void o_counts_get(const o_model* m, o_counts* c) {
+  memset(c, 0, sizeof(*c));
+  c->nleaf = m->t.n;
+  c->nnode = m->nd.n;
+  for (int n = 0; n < m->nd.n; ++n) c->nhang += m->nd.hang ? m->nd.hang[n] : 0;
+  c->ndof = m->nd.ndof;
+  c->nnzb = m->nnzb;
+  c->nghost = m->nghost;
+  c->npts = m->np;
+  for (int p = 0; p < m->np && m->nsup; ++p)
+    if (m->nsup[p] > c->maxs) c->maxs = m->nsup[p];
+}
+
+void o_export_tree(const o_model* m, int* lev, int* anchor) {
+  memcpy(lev, m->t.lev, sizeof(int) * (size_t)m->t.n);
+  memcpy(anchor, m->t.a, sizeof(int) * 3 * (size_t)m->t.n);
+}
+
+void o_export_nodes(const o_model* m, int* coord, int* hang, int* dof, int* cptr, int* cidx,
+                    double* cw) {
+  const o_nodes* nd = &m->nd;
+  memcpy(coord, nd->c, sizeof(int) * 3 * (size_t)nd->n);
+  memcpy(hang, nd->hang, sizeof(int) * (size_t)nd->n);
+  memcpy(dof, nd->dof, sizeof(int) * (size_t)nd->n);
+  memcpy(cptr, nd->cptr, sizeof(int) * (size_t)(nd->n + 1));
+  memcpy(cidx, nd->cidx, sizeof(int) * (size_t)nd->cptr[nd->n]);
+  memcpy(cw, nd->cw, sizeof(double) * (size_t)nd->cptr[nd->n]);
+}
+
+void o_export_support(const o_model* m, int* nsup, int* sidx, double* S, double* dS) {
+  memcpy(nsup, m->nsup, sizeof(int) * (size_t)m->np);
+  memcpy(sidx, m->sidx, sizeof(int) * O_MAXS * (size_t)m->np);
+  memcpy(S, m->S, sizeof(double) * O_MAXS * (size_t)m->np);
+  memcpy(dS, m->dS, sizeof(double) * 3 * O_MAXS * (size_t)m->np);
+}
+
+void o_export_pattern(const o_model* m, int* row_ptr, int* col) {
+  memcpy(row_ptr, m->row_ptr, sizeof(int) * (size_t)(m->nd.ndof + 1));
+  memcpy(col, m->col, sizeof(int) * (size_t)m->nnzb);
+}
+
+void o_export_ghost(const o_model* m, double* kg) {
+  memcpy(kg, m->kg, sizeof(double) * (size_t)m->nnzb);
+}
+
+void o_export_ghost_faces(const o_model* m, int* faces, int* populated) {
+  memcpy(faces, m->gface, sizeof(int) * 4 * (size_t)m->nghost);
+  memcpy(populated, m->populated, sizeof(int) * (size_t)m->t.n);
+}
+
+void o_export_bcmask(const o_model* m, int* mask) {
+  memcpy(mask, m->bcmask, sizeof(int) * (size_t)m->nd.ndof);
+}
+
+/* leaf holding the box corner, taken on the inside of the box */
+static int corner_leaf(const o_model* m, const double* X, const int* side, double* xi) {
+  int N = 1 << m->D, q[3];
+  for (int d = 0; d < 3; ++d) {
+    q[d] = side[d] > 0 ? (int)ceil(X[d]) - 1 : (int)floor(X[d]);
+    if (q[d] < 0) q[d] = 0;
+    if (q[d] > N - 1) q[d] = N - 1;
+  }
+  int K = o_locate(&m->t, q[0], q[1], q[2]);
+  int s = 1 << (m->D - m->t.lev[K]);
+  for (int d = 0; d < 3; ++d) xi[d] = (X[d] - (double)m->t.a[3 * K + d]) / (double)s;
+  return K;
+}
+
+int o_eval_background(const o_model* m, const double* x, int* nent, int* idx, double* phi,
+                      double* dphi) {
+  double X[3], xi[3];
+  int side[3] = {-1, -1, -1};
+  for (int d = 0; d < 3; ++d) X[d] = x[d] * m->scale;
+  int K = corner_leaf(m, X, side, xi);
+  int st = o_leaf_basis(m, K, xi, nent, idx, phi, dphi);
+  for (int i = 0; i < *nent; ++i) {
+    idx[i] = m->nd.dof[idx[i]];
+    for (int d = 0; d < 3; ++d) dphi[3 * i + d] *= m->scale;
+  }
+  return st;
+}
+
+/* point kinematics: dF = I + sum_v du_v (x) grad S_vp */
+static void point_dF(const o_model* m, int p, const double* du, double* dF) {
+  for (int i = 0; i < 9; ++i) dF[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  const int* si = m->sidx + O_MAXS * (size_t)p;
+  const double* dS = m->dS + 3 * O_MAXS * (size_t)p;
+  for (int k = 0; k < m->nsup[p]; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) dF[3 * i + j] += du[3 * si[k] + i] * dS[3 * k + j];
+}
+
+int o_point_stress(o_model* m, const double* du, double* sigma) {
+  for (int p = 0; p < m->np; ++p) {
+    double dF[9], tau[9], ben[6], Ft[9];
+    int pl;
+    point_dF(m, p, du, dF);
+    int st = o_constitutive(&m->p, m->E[p], m->ys[p], m->be + 6 * (size_t)p, dF, tau, ben, NULL, &pl);
+    if (st) return st;
+    o_mat33_mul(dF, m->F + 9 * (size_t)p, Ft);
+    double J = o_det33(Ft);
+    for (int i = 0; i < 9; ++i) sigma[9 * (size_t)p + i] = tau[i] / J;
+  }
+  return O_OK;
+}
+
+int o_assemble(o_model* m, const double* du, double load, double* R, double* Kv, double* fint_all,
+               double* reaction) {
+  int ndof = m->nd.ndof;
+  for (int i = 0; i < 3 * ndof; ++i) R[i] = 0.0;
+  if (fint_all)
+    for (int i = 0; i < 3 * ndof; ++i) fint_all[i] = 0.0;
+  if (Kv)
+    for (size_t i = 0; i < 9 * (size_t)m->nnzb; ++i) Kv[i] = 0.0;
+  if (reaction) reaction[0] = reaction[1] = reaction[2] = 0.0;
+  double* fext_c = (double*)calloc(3 * (size_t)ndof, sizeof(double));
+  double A[81];
+  for (int p = 0; p < m->np; ++p) {
+    const int* si = m->sidx + O_MAXS * (size_t)p;
+    const double* S = m->S + O_MAXS * (size_t)p;
+    const double* dS = m->dS + 3 * O_MAXS * (size_t)p;
+    int ns = m->nsup[p];
+    double dF[9], dFi[9], tau[9], ben[6];
+    int pl;
+    point_dF(m, p, du, dF);
+    if (!(o_det33(dF) > 0.0)) {
+      free(fext_c);
+      return O_ERR_NAN;
+    }
+    int st = o_constitutive(&m->p, m->E[p], m->ys[p], m->be + 6 * (size_t)p, dF, tau, ben,
+                            Kv ? A : NULL, &pl);
+    if (st) {
+      free(fext_c);
+      return st;
+    }
+    o_inv33(dF, dFi);
+    double V0 = m->V0[p];
+    double gx[O_MAXS][3];
+    for (int k = 0; k < ns; ++k)
+      for (int mm = 0; mm < 3; ++mm) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l) s += dS[3 * k + l] * dFi[3 * l + mm];
+        gx[k][mm] = s;
+      }
+    /* f_int,v = V_p sigma grad_x S_v = V0 tau grad_x S_v; f_ext,v = S_v m g */
+    for (int k = 0; k < ns; ++k)
+      for (int i = 0; i < 3; ++i) {
+        double f = 0.0;
+        for (int j = 0; j < 3; ++j) f += tau[3 * i + j] * gx[k][j];
+        f *= V0;
+        R[3 * si[k] + i] += f;
+        if (fint_all) fint_all[3 * si[k] + i] += f;
+        double fe = load * m->mass[p] * S[k] * m->p.g[i];
+        R[3 * si[k] + i] -= fe;
+        fext_c[3 * si[k] + i] += fe;
+      }
+    if (Kv) {
+      /* K_{vi,wk} = V0 sum_{j,m} gx_vj (A_ijkm - tau_im delta_jk) gx_wm */
+      for (int a = 0; a < ns; ++a)
+        for (int b = 0; b < ns; ++b) {
+          int sl = o_find_slot(m, si[a], si[b]);
+          double* blk = Kv + 9 * (size_t)sl;
+          for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) {
+              double s = 0.0;
+              for (int j = 0; j < 3; ++j)
+                for (int mm = 0; mm < 3; ++mm) {
+                  double a4 = A[((i * 3 + j) * 3 + k) * 3 + mm] - (j == k ? tau[3 * i + mm] : 0.0);
+                  s += gx[a][j] * a4 * gx[b][mm];
+                }
+              blk[3 * i + k] += V0 * s;
+            }
+        }
+    }
+  }
+  /* ghost penalty on the step increment (Sec. 4, reading: K_G and K_G du) */
+  for (int i = 0; i < ndof; ++i)
+    for (int s = m->row_ptr[i]; s < m->row_ptr[i + 1]; ++s) {
+      double kg = m->kg[s];
+      if (kg == 0.0) continue;
+      int j = m->col[s];
+      for (int c = 0; c < 3; ++c) R[3 * i + c] += kg * du[3 * j + c];
+      if (Kv)
+        for (int c = 0; c < 3; ++c) Kv[9 * (size_t)s + 4 * c] += kg;
+    }
+  /* node-to-surface penalty contact at the GIMP domain corners (Sec. 2.3) */
+  if (m->p.contact_on && m->p.body_kind != 0) {
+    int idx[O_MAXS], nent;
+    double ph[O_MAXS], dph[3 * O_MAXS];
+    for (int p = 0; p < m->np; ++p) {
+      double Lo[3], Hi[3];
+      double N = (double)(1 << m->D);
+      for (int d = 0; d < 3; ++d) {
+        double lo = (m->x[3 * p + d] - m->lp[3 * p + d]) * m->scale;
+        double hi = (m->x[3 * p + d] + m->lp[3 * p + d]) * m->scale;
+        double rl = floor(lo + 0.5), rh = floor(hi + 0.5);
+        lo = fabs(lo - rl) < 1e-9 ? rl : lo;
+        hi = fabs(hi - rh) < 1e-9 ? rh : hi;
+        Lo[d] = lo < 0.0 ? 0.0 : lo;
+        Hi[d] = hi > N ? N : hi;
+      }
+      double epsN = m->p.pf * m->E[p] * pow(m->V0[p], 2.0 / 3.0);
+      for (int c = 0; c < 8; ++c) {
+        int side[3];
+        double X[3], y[3], xi[3];
+        for (int d = 0; d < 3; ++d) {
+          side[d] = ((c >> d) & 1) ? 1 : -1;
+          X[d] = side[d] > 0 ? Hi[d] : Lo[d];
+          y[d] = m->x[3 * p + d] + side[d] * m->lp[3 * p + d];
+        }
+        int K = corner_leaf(m, X, side, xi);
+        o_leaf_basis(m, K, xi, &nent, idx, ph, dph);
+        for (int i = 0; i < nent; ++i) {
+          idx[i] = m->nd.dof[idx[i]];
+          for (int d = 0; d < 3; ++d) y[d] += ph[i] * du[3 * idx[i] + d];
+        }
+        double phi, n[3], H[9];
+        o_body_sdf(&m->p, y, &phi, n, H);
+        if (!(phi < 0.0)) continue;
+        double f[3];
+        for (int d = 0; d < 3; ++d) f[d] = -epsN * phi * n[d];
+        if (reaction)
+          for (int d = 0; d < 3; ++d) reaction[d] -= f[d];
+        for (int i = 0; i < nent; ++i)
+          for (int d = 0; d < 3; ++d) {
+            R[3 * idx[i] + d] -= ph[i] * f[d];
+            fext_c[3 * idx[i] + d] += ph[i] * f[d];
+          }
+        if (Kv) {
+          double kc[9];
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) kc[3 * a + b] = epsN * (n[a] * n[b] + phi * H[3 * a + b]);
+          for (int a = 0; a < nent; ++a)
+            for (int b = 0; b < nent; ++b) {
+              int sl = o_find_slot(m, idx[a], idx[b]);
+              for (int q = 0; q < 9; ++q) Kv[9 * (size_t)sl + q] += ph[a] * ph[b] * kc[q];
+            }
+        }
+      }
+    }
+  }
+  if (fint_all) {
+    /* second half of the reference force: ||f_ext + f_c|| stored after f_int */
+    double s = 0.0;
+    for (int i = 0; i < 3 * ndof; ++i) s += fext_c[i] * fext_c[i];
+    fint_all[3 * ndof] = sqrt(s);
+  }
+  free(fext_c);
+  for (int i = 0; i < 3 * ndof; ++i)
+    if (!isfinite(R[i])) return O_ERR_NAN;
+  return O_OK;
+}
+
+/* ---------------- linear solves on the free components ---------------- */
+
+static int lu_solve(int n, double* A, double* b) {
+  int* piv = (int*)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  for (int k = 0; k < n; ++k) {
+    int pm = k;
+    for (int i = k + 1; i < n; ++i)
+      if (fabs(A[(size_t)i * n + k]) > fabs(A[(size_t)pm * n + k])) pm = i;
+    if (A[(size_t)pm * n + k] == 0.0) {
+      free(piv);
+      return O_ERR_KRYLOV;
+    }
+    piv[k] = pm;
+    if (pm != k) {
+      for (int j = 0; j < n; ++j) {
+        double t = A[(size_t)k * n + j];
+        A[(size_t)k * n + j] = A[(size_t)pm * n + j];
+        A[(size_t)pm * n + j] = t;
+      }
+      double t = b[k];
+      b[k] = b[pm];
+      b[pm] = t;
+    }
+    for (int i = k + 1; i < n; ++i) {
+      double f = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+      if (f == 0.0) continue;
+      for (int j = k; j < n; ++j) A[(size_t)i * n + j] -= f * A[(size_t)k * n + j];
+      b[i] -= f * b[k];
+    }
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int j = i + 1; j < n; ++j) s -= A[(size_t)i * n + j] * b[j];
+    b[i] = s / A[(size_t)i * n + i];
+  }
+  free(piv);
+  return O_OK;
+}
+
+/* y = K x restricted to free components (fixed components of y are zero) */
+static void free_matvec(const o_model* m, const double* Kv, const double* x, double* y) {
+  int ndof = m->nd.ndof;
+  for (int i = 0; i < ndof; ++i)
+    for (int c = 0; c < 3; ++c) {
+      if (m->bcmask[i] & (1 << c)) {
+        y[3 * i + c] = 0.0;
+        continue;
+      }
+      double s = 0.0;
+      for (int q = m->row_ptr[i]; q < m->row_ptr[i + 1]; ++q) {
+        int j = m->col[q];
+        for (int e = 0; e < 3; ++e)
+          if (!(m->bcmask[j] & (1 << e))) s += Kv[9 * (size_t)q + 3 * c + e] * x[3 * j + e];
+      }
+      y[3 * i + c] = s;
+    }
+}
+
+static double dot(int n, const double* a, const double* b) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+int o_solve(o_model* m, const double* Kv, const double* b, double* x, double tol, int maxit,
+            int* its) {
+  int ndof = m->nd.ndof, n3 = 3 * ndof;
+  int* fid = (int*)malloc(sizeof(int) * (size_t)n3);
+  int nf = 0;
+  for (int i = 0; i < n3; ++i) {
+    fid[i] = (m->bcmask[i / 3] & (1 << (i % 3))) ? -1 : nf++;
+    x[i] = 0.0;
+  }
+  *its = 0;
+  int st = O_OK;
+  if (nf <= 1500) {
+    double* A = (double*)calloc((size_t)nf * (size_t)nf, sizeof(double));
+    double* r = (double*)malloc(sizeof(double) * (size_t)(nf > 0 ? nf : 1));
+    for (int i = 0; i < ndof; ++i)
+      for (int q = m->row_ptr[i]; q < m->row_ptr[i + 1]; ++q) {
+        int j = m->col[q];
+        for (int c = 0; c < 3; ++c)
+          for (int e = 0; e < 3; ++e) {
+            int fi = fid[3 * i + c], fj = fid[3 * j + e];
+            if (fi >= 0 && fj >= 0) A[(size_t)fi * nf + fj] += Kv[9 * (size_t)q + 3 * c + e];
+          }
+      }
+    for (int i = 0; i < n3; ++i)
+      if (fid[i] >= 0) r[fid[i]] = b[i];
+    st = lu_solve(nf, A, r);
+    for (int i = 0; i < n3; ++i)
+      if (fid[i] >= 0) x[i] = r[fid[i]];
+    free(A);
+    free(r);
+    *its = 1;
+    free(fid);
+    return st;
+  }
+  free(fid);
+  /* point-Jacobi preconditioned CG (symmetric) or BiCGStab (Drucker-Prager
+   * with psi != phi gives a non-symmetric tangent) */
+  double* diag = (double*)malloc(sizeof(double) * (size_t)n3);
+  for (int i = 0; i < ndof; ++i) {
+    int q = o_find_slot(m, i, i);
+    for (int c = 0; c < 3; ++c) {
+      double dv = q >= 0 ? Kv[9 * (size_t)q + 4 * c] : 0.0;
+      diag[3 * i + c] = (m->bcmask[i] & (1 << c)) || dv == 0.0 ? 0.0 : 1.0 / dv;
+    }
+  }
+  double* r = (double*)malloc(sizeof(double) * (size_t)n3);
+  double* z = (double*)malloc(sizeof(double) * (size_t)n3);
+  double* pv = (double*)malloc(sizeof(double) * (size_t)n3);
+  double* q = (double*)malloc(sizeof(double) * (size_t)n3);
+  for (int i = 0; i < n3; ++i) r[i] = (m->bcmask[i / 3] & (1 << (i % 3))) ? 0.0 : b[i];
+  double bn = sqrt(dot(n3, r, r));
+  int nonsym = m->p.model == 2 && m->p.psi != m->p.phi;
+  st = O_ERR_KRYLOV;
+  if (bn == 0.0) {
+    st = O_OK;
+  } else if (!nonsym) {
+    for (int i = 0; i < n3; ++i) {
+      z[i] = diag[i] * r[i];
+      pv[i] = z[i];
+    }
+    double rz = dot(n3, r, z);
+    for (int k = 1; k <= maxit; ++k) {
+      free_matvec(m, Kv, pv, q);
+      double alpha = rz / dot(n3, pv, q);
+      for (int i = 0; i < n3; ++i) {
+        x[i] += alpha * pv[i];
+        r[i] -= alpha * q[i];
+      }
+      *its = k;
+      if (sqrt(dot(n3, r, r)) <= tol * bn) {
+        st = O_OK;
+        break;
+      }
+      for (int i = 0; i < n3; ++i) z[i] = diag[i] * r[i];
+      double rz2 = dot(n3, r, z);
+      double beta = rz2 / rz;
+      rz = rz2;
+      for (int i = 0; i < n3; ++i) pv[i] = z[i] + beta * pv[i];
+    }
+  } else {
+    double* r0 = (double*)malloc(sizeof(double) * (size_t)n3);
+    double* v = (double*)calloc((size_t)n3, sizeof(double));
+    double* s = (double*)malloc(sizeof(double) * (size_t)n3);
+    double* t = (double*)malloc(sizeof(double) * (size_t)n3);
+    double* ph = (double*)malloc(sizeof(double) * (size_t)n3);
+    double* sh = (double*)malloc(sizeof(double) * (size_t)n3);
+    memcpy(r0, r, sizeof(double) * (size_t)n3);
+    for (int i = 0; i < n3; ++i) pv[i] = 0.0;
+    double rho = 1.0, alpha = 1.0, omega = 1.0;
+    for (int k = 1; k <= maxit; ++k) {
+      double rho1 = dot(n3, r0, r);
+      if (rho1 == 0.0) break;
+      double beta = (rho1 / rho) * (alpha / omega);
+      rho = rho1;
+      for (int i = 0; i < n3; ++i) pv[i] = r[i] + beta * (pv[i] - omega * v[i]);
+      for (int i = 0; i < n3; ++i) ph[i] = diag[i] * pv[i];
+      free_matvec(m, Kv, ph, v);
+      alpha = rho / dot(n3, r0, v);
+      for (int i = 0; i < n3; ++i) s[i] = r[i] - alpha * v[i];
+      *its = k;
+      if (sqrt(dot(n3, s, s)) <= tol * bn) {
+        for (int i = 0; i < n3; ++i) x[i] += alpha * ph[i];
+        st = O_OK;
+        break;
+      }
+      for (int i = 0; i < n3; ++i) sh[i] = diag[i] * s[i];
+      free_matvec(m, Kv, sh, t);
+      double tt = dot(n3, t, t);
+      omega = tt > 0.0 ? dot(n3, t, s) / tt : 0.0;
+      for (int i = 0; i < n3; ++i) {
+        x[i] += alpha * ph[i] + omega * sh[i];
+        r[i] = s[i] - omega * t[i];
+      }
+      if (sqrt(dot(n3, r, r)) <= tol * bn) {
+        st = O_OK;
+        break;
+      }
+      if (omega == 0.0) break;
+    }
+    free(r0); free(v); free(s); free(t); free(ph); free(sh);
+  }
+  free(diag); free(r); free(z); free(pv); free(q);
+  return st;
+}
+
+/* ---------------- Newton load step (Sec. 2.4) and point update ---------------- */
+
+static double norm_free(const o_model* m, const double* R) {
+  double s = 0.0;
+  for (int i = 0; i < 3 * m->nd.ndof; ++i)
+    if (!(m->bcmask[i / 3] & (1 << (i % 3)))) s += R[i] * R[i];
+  return sqrt(s);
+}
+
+static double norm2(int n, const double* a) { return sqrt(dot(n, a, a)); }
+
+int o_step(o_model* m, const o_step_params* sp, o_step_stats* stt) {
+  memset(stt, 0, sizeof(*stt));
+  int st = o_build(m, 0);
+  if (st) return stt->status = st;
+  int n3 = 3 * m->nd.ndof;
+  double* du = (double*)calloc((size_t)n3, sizeof(double));
+  double* R = (double*)malloc(sizeof(double) * (size_t)n3);
+  double* R1 = (double*)malloc(sizeof(double) * (size_t)n3);
+  double* fi = (double*)malloc(sizeof(double) * (size_t)(n3 + 1));
+  double* Kv = (double*)malloc(sizeof(double) * 9 * (size_t)(m->nnzb > 0 ? m->nnzb : 1));
+  double* dx = (double*)malloc(sizeof(double) * (size_t)n3);
+  double* trial = (double*)malloc(sizeof(double) * (size_t)n3);
+  double reac[3];
+  st = o_assemble(m, du, sp->load, R, Kv, fi, reac);
+  int conv = 0;
+  for (int it = 0; st == O_OK && it <= sp->maxit; ++it) {
+    double rn = norm_free(m, R);
+    double fref = fmax(norm2(n3, fi), fi[n3]);
+    if (it < 64) stt->res_hist[it] = fref > 0 ? rn / fref : rn;
+    if (rn <= sp->tol * fref || fref == 0.0) {
+      conv = 1;
+      stt->newton_its = it;
+      break;
+    }
+    if (it == sp->maxit) break;
+    for (int i = 0; i < n3; ++i) trial[i] = -R[i];
+    int lits = 0;
+    st = o_solve(m, Kv, trial, dx, sp->lin_tol, sp->lin_maxit, &lits);
+    stt->lin_its_total += lits;
+    if (st) break;
+    /* line search (Sec. 2.4): eta = 1, else the lowest residual of {0.5,0.25,0.1} */
+    const double etas[4] = {1.0, 0.5, 0.25, 0.1};
+    double best = -1.0, besteta = 1.0;
+    for (int e = 0; e < 4; ++e) {
+      for (int i = 0; i < n3; ++i) trial[i] = du[i] + etas[e] * dx[i];
+      int s2 = o_assemble(m, trial, sp->load, R1, NULL, NULL, NULL);
+      double r1 = s2 ? INFINITY : norm_free(m, R1);
+      if (best < 0.0 || r1 < best) {
+        best = r1;
+        besteta = etas[e];
+      }
+      if (e == 0 && r1 < rn) break;
+    }
+    if (it < 64) stt->eta_hist[it] = besteta;
+    for (int i = 0; i < n3; ++i) du[i] += besteta * dx[i];
+    st = o_assemble(m, du, sp->load, R, Kv, fi, reac);
+  }
+  if (st == O_OK && !conv) st = O_ERR_NEWTON;
+  if (st == O_OK) {
+    for (int d = 0; d < 3; ++d) stt->reaction[d] = reac[d];
+    /* point update: x += sum_v S_vp du_v; F, b_e from the converged state;
+     * domain half-lengths l = l0 diag(U), U = sqrt(F^T F) (reading) */
+    for (int p = 0; p < m->np; ++p) {
+      double dF[9], tau[9], ben[6], Fn[9];
+      int pl;
+      point_dF(m, p, du, dF);
+      o_constitutive(&m->p, m->E[p], m->ys[p], m->be + 6 * (size_t)p, dF, tau, ben, NULL, &pl);
+      o_mat33_mul(dF, m->F + 9 * (size_t)p, Fn);
+      const int* si = m->sidx + O_MAXS * (size_t)p;
+      const double* S = m->S + O_MAXS * (size_t)p;
+      for (int k = 0; k < m->nsup[p]; ++k)
+        for (int d = 0; d < 3; ++d) m->x[3 * p + d] += S[k] * du[3 * si[k] + d];
+      memcpy(m->F + 9 * (size_t)p, Fn, sizeof(Fn));
+      memcpy(m->be + 6 * (size_t)p, ben, sizeof(ben));
+      double C[9], Ft[9], lam[3], Q[9];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Ft[3 * i + j] = Fn[3 * j + i];
+      o_mat33_mul(Ft, Fn, C);
+      o_eig_sym3(C, lam, Q);
+      for (int d = 0; d < 3; ++d) {
+        double u = 0.0;
+        for (int a = 0; a < 3; ++a) u += sqrt(lam[a]) * Q[3 * d + a] * Q[3 * d + a];
+        m->lp[3 * p + d] = m->l0[3 * p + d] * u;
+      }
+    }
+  }
+  free(du); free(R); free(R1); free(fi); free(Kv); free(dx); free(trial);
+  stt->status = st;
+  return st;
+}

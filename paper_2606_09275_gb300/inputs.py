@@ -1,0 +1,143 @@
+"""Seeded synthetic inputs shared by the GPU path, the oracle and the benchmark.
+
+This module holds none of the method's arithmetic.  It only
+  * places material points on a regular lattice inside a block (optionally
+    jittered with a seeded uniform offset) and gives them their material
+    constants (optionally a seeded lognormal Young's modulus), and
+  * states the parameter sets of the workloads: domain cube, refinement depths,
+    Dirichlet planes, rigid body and its motion, material, load schedule.
+
+Point arrays (all float64, C order):
+  x (P,3) centre, lp (P,3) current half-lengths, l0 (P,3) reference
+  half-lengths, F (P,9) row-major deformation gradient, be (P,6) elastic left
+  Cauchy-Green tensor as (xx, yy, zz, xy, yz, xz), V0 (P,) reference volume,
+  mass (P,), E (P,) Young's modulus, ys (P,) yield stress (von Mises) or
+  cohesion (Drucker-Prager).
+"""
+import copy
+import math
+
+import numpy as np
+
+# roller planes: (axis, position, fixed-component mask); mask bit d = component d
+ROLLER_X, ROLLER_Y, ROLLER_Z, FIXED = 1, 2, 4, 7
+
+
+def lattice_points(lo, hi, spacing, rho, E, ys, jitter=0.0, seed=0, E_sigma=0.0):
+    """Material points on a lattice of the given spacing filling [lo, hi].
+
+    Each point's domain is the lattice cell (half-length spacing/2).  With
+    jitter > 0 every centre is moved by U(-jitter, jitter) per axis (seeded).
+    With E_sigma > 0 the modulus is lognormal around E (seeded, seed + 1).
+    """
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    n = [int(round((hi[d] - lo[d]) / spacing)) for d in range(3)]
+    iz, iy, ix = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    idx = np.stack([ix.ravel(), iy.ravel(), iz.ravel()], axis=1).astype(np.float64)
+    x = lo[None, :] + (idx + 0.5) * spacing
+    P = x.shape[0]
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        x = x + rng.uniform(-jitter, jitter, size=(P, 3))
+    half = 0.5 * spacing
+    pts = {
+        "x": np.ascontiguousarray(x),
+        "lp": np.full((P, 3), half),
+        "l0": np.full((P, 3), half),
+        "F": np.tile(np.eye(3).ravel(), (P, 1)),
+        "be": np.tile(np.array([1.0, 1.0, 1.0, 0.0, 0.0, 0.0]), (P, 1)),
+        "V0": np.full(P, spacing ** 3),
+        "mass": np.full(P, rho * spacing ** 3),
+        "E": np.full(P, float(E)),
+        "ys": np.full(P, float(ys)),
+    }
+    if E_sigma > 0.0:
+        rng = np.random.default_rng(seed + 1)
+        pts["E"] = np.exp(rng.normal(math.log(E), E_sigma, size=P))
+    return pts
+
+
+def make_points(cfg):
+    pc = cfg["points"]
+    return lattice_points(pc["lo"], pc["hi"], pc["spacing"], pc["rho"], pc["E"], pc["ys"],
+                          jitter=pc.get("jitter", 0.0), seed=pc.get("seed", 0),
+                          E_sigma=pc.get("E_sigma", 0.0))
+
+
+def body_z(cfg, step):
+    """Vertical position of the rigid body at the end of load step `step` (1-based)."""
+    b = cfg["body"]
+    return b["z0"] + step * b["dz"]
+
+
+def load_factor(cfg, step):
+    return step / cfg["nsteps"] if cfg.get("ramp_load", False) else 1.0
+
+
+def _block_rollers(x1, y1, fixed_base=True):
+    return [(0, 0.0, ROLLER_X), (0, x1, ROLLER_X), (1, 0.0, ROLLER_Y), (1, y1, ROLLER_Y),
+            (2, 0.0, FIXED if fixed_base else ROLLER_Z)]
+
+
+_BASE = dict(beta=2.0, nu=0.3, phi=0.0, psi=0.0, g=(0.0, 0.0, 0.0), kappa=10.0, pf=50.0,
+             ghost=1, contact=1, body=None, dx_region=0.0, ramp_load=False,
+             newton_tol=1e-8, newton_maxit=30, lin_tol=1e-8, lin_maxit=20000)
+
+
+def workload(name, **over):
+    """Parameter set of a named workload (a fresh dict; keyword overrides win)."""
+    c = copy.deepcopy(_BASE)
+    if name == "column":
+        # elastic column under self-weight, unit cube, uniform depth 3, 2x2x2 points
+        # per cell, gravity ramped over 10 load steps, roller sides, fixed base
+        c.update(L=1.0, depth_min=3, depth_max=3, bc=_block_rollers(1.0, 1.0), model=0,
+                 g=(0.0, 0.0, -9.81), nsteps=10, ramp_load=True, contact=0,
+                 points=dict(lo=(0, 0, 0), hi=(1, 1, 1), spacing=1.0 / 16, rho=1000.0,
+                             E=1e6, ys=0.0))
+    elif name == "punch":
+        # flat-ended cylindrical punch (r = 0.1 m) into a 1 x 1 x 0.5 m von Mises
+        # block, depth 3 far field refined to depth 6 within 2 finest cells of the
+        # punch, 50 load steps to 0.1 m
+        c.update(L=1.0, depth_min=3, depth_max=6, bc=_block_rollers(1.0, 1.0), model=1,
+                 body=dict(kind=1, cx=0.5, cy=0.5, z0=0.5, r=0.1, alpha=0.0, dz=-0.1 / 50),
+                 dx_region=2.0 / 64, nsteps=50,
+                 points=dict(lo=(0, 0, 0), hi=(1, 1, 0.5), spacing=1.0 / 16, rho=1000.0,
+                             E=1e7, ys=1e5))
+    elif name == "cone":
+        # 60-degree cone (base diameter 0.036 m) pushed 0.3 m into a 1 x 1 x 1.2 m
+        # Drucker-Prager layer; the cube [0,1.6]^3 at depth 4 (0.1 m cells) keeps
+        # the layer faces on cell faces; refined to depth 8 at the cone
+        c.update(L=1.6, depth_min=4, depth_max=8, bc=_block_rollers(1.0, 1.0), model=2,
+                 phi=math.radians(30.0), psi=0.0,
+                 body=dict(kind=2, cx=0.5, cy=0.5, z0=1.2, r=0.018, alpha=math.radians(30.0),
+                           dz=-0.3 / 200),
+                 dx_region=2.0 * 1.6 / 256, nsteps=200,
+                 points=dict(lo=(0, 0, 0), hi=(1, 1, 1.2), spacing=0.05, rho=1000.0,
+                             E=2e7, ys=5e3))
+    elif name == "adjoint":
+        # the punch at depth 3 to 5, 20 load steps, lognormal E (sigma 0.2)
+        c.update(L=1.0, depth_min=3, depth_max=5, bc=_block_rollers(1.0, 1.0), model=1,
+                 body=dict(kind=1, cx=0.5, cy=0.5, z0=0.5, r=0.1, alpha=0.0, dz=-0.1 / 50),
+                 dx_region=2.0 / 32, nsteps=20,
+                 points=dict(lo=(0, 0, 0), hi=(1, 1, 0.5), spacing=1.0 / 16, rho=1000.0,
+                             E=1e7, ys=1e5, E_sigma=0.2, seed=0))
+    elif name == "indent":
+        # indentation at the ~1M-DOF scale: the punch physics of "punch" on a depth 6
+        # far field (2x2x2 jittered points per cell, U(-h/8, h/8)) refined to depth
+        # 7 at the punch; block 1 x 1 x 0.875 m under the cube top
+        c.update(L=1.0, depth_min=6, depth_max=7, bc=_block_rollers(1.0, 1.0), model=1,
+                 body=dict(kind=1, cx=0.5, cy=0.5, z0=0.875, r=0.1, alpha=0.0, dz=-0.1 / 50),
+                 dx_region=2.0 / 128, nsteps=50,
+                 points=dict(lo=(0, 0, 0), hi=(1, 1, 0.875), spacing=1.0 / 128, rho=1000.0,
+                             E=1e7, ys=1e5, jitter=1.0 / 512, seed=0))
+    else:
+        raise KeyError(name)
+    for k, v in over.items():
+        if k == "points":
+            c["points"].update(v)
+        elif k == "body" and v is not None and c["body"] is not None:
+            c["body"].update(v)
+        else:
+            c[k] = v
+    return c
