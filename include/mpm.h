@@ -1,0 +1,211 @@
+/*
+ * mpm.h -- C ABI of libmpm_gb300.so: the data-parallel hot path of one load step
+ * of the implicit octree-based GIMP Material Point Method (Bird, Coombs,
+ * Augarde, Pretti, O'Hare, "An implicit octree-based adaptive Material Point
+ * Method").  Every computation behind these calls runs in hand-written CUDA
+ * kernels for sm_103a on the stream given to mpm_create.
+ *
+ * Conventions
+ *  - "device" pointers are CUDA global memory of the current device, owned by
+ *    the caller unless stated otherwise; "host" pointers are ordinary memory.
+ *  - Point arrays are structure-of-arrays in the caller's (canonical) order:
+ *      x[3P] centre, lp[3P] current half-lengths, l0[3P] reference
+ *      half-lengths, F[9P] row-major deformation gradient, be[6P] elastic left
+ *      Cauchy-Green tensor (xx, yy, zz, xy, yz, xz), V0[P] reference volume,
+ *      mass[P], E[P] Young's modulus, ys[P] yield stress (von Mises) or
+ *      cohesion (Drucker-Prager).  All double precision.
+ *  - Nodal vectors are [3*ndof] doubles, component-fastest, dofs numbered in
+ *    Morton order of the active independent nodes of the mesh.
+ *  - Stiffness values use a row-sliced 3x3 block layout: block row r owns the
+ *    blocks s = row_ptr[r] .. row_ptr[r+1]-1 (nb = their count); entry (i,j) of
+ *    its k-th block lives at values[9*row_ptr[r] + (3*i + j)*nb + k].  The block
+ *    columns col[s] are sorted ascending in each row.
+ *  - Every call returns an mpm_status; on failure mpm_last_error(ctx) gives a
+ *    message.  No call aborts, traps or spins without bound: device-side
+ *    failures (support overflow, NaN, Krylov breakdown) come back as status
+ *    codes and leave the context usable.
+ *  - Calls are asynchronous on the context stream except where they return host
+ *    values (counts, statistics, reaction), which synchronise that stream.
+ */
+#ifndef MPM_GB300_H
+#define MPM_GB300_H
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPM_MAXS 64 /* support entries per material point */
+
+typedef enum {
+  MPM_OK = 0,
+  MPM_ERR_ARG = 1,       /* invalid argument                                  */
+  MPM_ERR_CUDA = 2,      /* a CUDA runtime call failed                        */
+  MPM_ERR_NEWTON = 3,    /* Newton iterations exhausted                       */
+  MPM_ERR_KRYLOV = 4,    /* Krylov iteration cap reached or breakdown         */
+  MPM_ERR_NAN = 5,       /* non-finite value or det F <= 0                    */
+  MPM_ERR_SUPPORT = 6,   /* support / overlap / constraint list overflow      */
+  MPM_ERR_CAPACITY = 7,  /* point capacity too small for the GIMP split       */
+  MPM_ERR_BALANCE = 8,   /* octree balance or hanging-node layout failure     */
+  MPM_ERR_DOMAIN = 9     /* a GIMP domain lies outside the cube               */
+} mpm_status;
+
+typedef enum { MPM_FP64 = 0, MPM_MIXED = 1 } mpm_precision;
+
+/* Problem domain: the closed cube [0,L]^3 of Sec. 3.1, octree depths, and the
+ * strong Dirichlet planes of Sec. 2.4 (nodes with coordinate bc_pos on axis
+ * bc_axis have the components in bc_mask -- bit d = component d -- fixed). */
+typedef struct {
+  double L;
+  int depth_min, depth_max;
+  int nbc;
+  int bc_axis[8];
+  double bc_pos[8];
+  int bc_mask[8];
+} mpm_domain;
+
+/* Rigid body of Sec. 2.3 as an analytic surface: kind 0 none, 1 flat-ended
+ * cylinder {z >= z, rho <= r}, 2 cone of half angle alpha with tip at z and a
+ * cylindrical shaft of radius r; axis through (cx, cy). */
+typedef struct {
+  int kind;
+  double cx, cy, z, r, alpha;
+} mpm_rigid;
+
+/* Adaptivity of Sec. 5: refine leaves meeting the body or with a node within
+ * dx_region of it (down to depth_max); split GIMPs with l_K < beta l_p. */
+typedef struct {
+  double dx_region, beta;
+} mpm_adapt;
+
+/* Material of Sec. 2.2 (model 0 Hencky elastic, 1 von Mises, 2 Drucker-Prager
+ * with friction phi and dilation psi in radians), gravity g (Eq. MPMweak body
+ * force), ghost constant kappa (Sec. 4), contact penalty factor pf (Sec. 2.3). */
+typedef struct {
+  int model;
+  double nu, phi, psi;
+  double g[3];
+  double kappa, pf;
+  int ghost_on, contact_on;
+} mpm_material;
+
+/* Caller-owned device point arrays (layout above).  mpm_octree_build may grow
+ * `count` up to `capacity` when it splits GIMPs (Sec. 5). */
+typedef struct {
+  int count, capacity;
+  double *x, *lp, *l0, *F, *be, *V0, *mass, *E, *ys;
+} mpm_points;
+
+typedef struct {
+  int nleaf, nnode, nhang, ndof, nnzb, nghost, npts, maxs, ncontact, maxrow;
+} mpm_mesh_info;
+
+typedef struct {
+  int method;      /* 0 auto (PCG if symmetric else BiCGStab), 1 PCG, 2 BiCGStab */
+  int precision;   /* mpm_precision of the stored matrix and the inner solve     */
+  double tol;      /* relative residual target ||b - K x|| <= tol ||b||           */
+  int maxit;       /* cap on Krylov iterations (all refinement rounds together)  */
+  double inner_tol;/* MPM_MIXED: relative target of each FP32 inner solve        */
+} mpm_solve_params;
+
+typedef struct {
+  int iterations, refinements, status;
+  double relres;
+} mpm_solve_stats;
+
+typedef struct {
+  double load;     /* load factor multiplying gravity                          */
+  double tol;      /* Newton: ||R_free|| <= tol * max(||f_int||, ||f_ext+f_c||)  */
+  int maxit;
+  mpm_solve_params lin;
+} mpm_step_params;
+
+typedef struct {
+  int newton_its, lin_its, status, npts, ndof, nnzb;
+  double res_hist[64];
+  double eta_hist[64];
+  double reaction[3];
+  double ms_build, ms_assemble, ms_solve, ms_update;
+} mpm_step_stats;
+
+typedef struct mpm_ctx mpm_ctx;
+typedef struct mpm_mesh mpm_mesh;
+
+/* Create a context bound to the current CUDA device and to `stream` (a
+ * cudaStream_t; NULL = legacy default stream).  The context owns scratch
+ * memory and a device error word; release it with mpm_destroy. */
+int mpm_create(mpm_ctx** ctx, void* stream);
+int mpm_destroy(mpm_ctx* ctx);
+const char* mpm_last_error(const mpm_ctx* ctx);
+
+/* Sec. 5 (Steps 1-3, GIMP refinement) and Sec. 3 (octree, hanging nodes, Eq.
+ * GIMP numerical) and Sec. 4 (ghost faces, Eq. ghost): rebuild the octree for
+ * the body pose, split GIMPs (pts->count may grow; MPM_ERR_CAPACITY if it would
+ * exceed pts->capacity), build nodes, hanging constraints, the discrete GIMP
+ * basis, the 3x3 block pattern and the ghost matrix.  `flags` bit 0 disables
+ * the GIMP split.  *mesh is created on first use and reused (its buffers grow)
+ * when passed back non-NULL.  The mesh keeps a cell-sorted copy of the point
+ * state: the points must not change until the mesh is rebuilt. */
+int mpm_octree_build(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body,
+                     const mpm_adapt* ad, const mpm_material* mat, mpm_points* pts, int flags,
+                     mpm_mesh** mesh);
+int mpm_mesh_free(mpm_mesh* mesh);
+/* counts of the mesh (host) */
+int mpm_mesh_counts(const mpm_mesh* mesh, mpm_mesh_info* info);
+
+/* Copies one mesh array to host memory for inspection (`what` selects it; see
+ * MPM_EXPORT_*), `bytes` is the size of `dst` and must be large enough. */
+enum {
+  MPM_EXPORT_LEAF_LEVEL = 0,   /* int[nleaf]                                    */
+  MPM_EXPORT_LEAF_ANCHOR = 1,  /* int[3*nleaf], finest-grid units               */
+  MPM_EXPORT_NODE_COORD = 2,   /* int[3*nnode]                                  */
+  MPM_EXPORT_NODE_HANG = 3,    /* int[nnode]                                    */
+  MPM_EXPORT_NODE_DOF = 4,     /* int[nnode], -1 for inactive or hanging        */
+  MPM_EXPORT_CPTR = 5,         /* int[nnode+1] resolved constraint lists         */
+  MPM_EXPORT_CIDX = 6,         /* int[cptr[nnode]] independent node ids          */
+  MPM_EXPORT_CW = 7,           /* double[cptr[nnode]] weights                    */
+  MPM_EXPORT_NSUP = 8,         /* int[P] support size per point (caller order)   */
+  MPM_EXPORT_SIDX = 9,         /* int[P*MPM_MAXS] support dofs, sorted          */
+  MPM_EXPORT_S = 10,           /* double[P*MPM_MAXS] S_vp                        */
+  MPM_EXPORT_DS = 11,          /* double[P*MPM_MAXS*3] grad S_vp                 */
+  MPM_EXPORT_ROW_PTR = 12,     /* int[ndof+1]                                   */
+  MPM_EXPORT_COL = 13,         /* int[nnzb]                                     */
+  MPM_EXPORT_GHOST = 14,       /* double[nnzb] ghost coefficient per block      */
+  MPM_EXPORT_BCMASK = 15,      /* int[ndof] fixed components                    */
+  MPM_EXPORT_POPULATED = 16,   /* int[nleaf]                                    */
+  MPM_EXPORT_GHOST_FACES = 17  /* int[4*nghost]: K, N, axis, sign              */
+};
+int mpm_mesh_export(const mpm_mesh* mesh, int what, void* dst, size_t bytes);
+
+/* Eq. (MPMweak), static part, with the ghost term of Sec. 4 and the penalty
+ * contact of Sec. 2.3: for the nodal increment du (device [3*ndof]) of the
+ * current load step, R (device [3*ndof]) = f_int - load*f_ext - f_c + K_G du and,
+ * if K_values (device [9*nnzb], double for MPM_FP64, float for MPM_MIXED) is
+ * non-NULL, the consistent tangent with the Dirichlet rows and columns
+ * replaced by identity.  reaction (host [3], may be NULL) receives the force of
+ * the material on the rigid body.  fint_norms (host [2], may be NULL) receives
+ * ||f_int|| and ||f_ext + f_c||. */
+int mpm_assemble(mpm_ctx* ctx, const mpm_mesh* mesh, const mpm_material* mat,
+                 const mpm_rigid* body, const double* du, double load, int precision, double* R,
+                 void* K_values, double* reaction, double* fint_norms);
+
+/* Preconditioned Krylov solve of K x = rhs on the free components (Sec. 1 names
+ * Krylov solvers with a Jacobi-type preconditioner as the scalable option), 3x3
+ * block-Jacobi preconditioner; MPM_MIXED runs FP32 inner solves inside FP64
+ * iterative refinement.  K_values as produced by mpm_assemble with the same
+ * precision; rhs, x device [3*ndof] doubles (x is overwritten). */
+int mpm_solve(mpm_ctx* ctx, const mpm_mesh* mesh, const mpm_material* mat, const void* K_values,
+              const double* rhs, double* x, const mpm_solve_params* prm, mpm_solve_stats* stats);
+
+/* One quasi-static load step (Sec. 2.4 Newton-Raphson with line search, Sec. 5
+ * re-adaptation): rebuild the mesh for the body pose, iterate assemble/solve
+ * until converged, then update the points (positions, F, b_e, domain sizes).
+ * stats (host) receives the history.  The mesh is kept in the context. */
+int mpm_step(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body, const mpm_adapt* ad,
+             const mpm_material* mat, mpm_points* pts, const mpm_step_params* prm,
+             mpm_step_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

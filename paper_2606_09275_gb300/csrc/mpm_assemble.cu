@@ -1,0 +1,709 @@
+// Per-Newton-iteration assembly of Eq. (MPMweak) (static part): point
+// kinematics, the Hencky / return-map constitutive update with its consistent
+// spatial tangent (Sec. 2.2), the internal force, the tangent gathered row by
+// row into the 3x3 block matrix, the ghost term (Sec. 4), the penalty contact
+// (Sec. 2.3) and the strong Dirichlet rows (Sec. 2.4).
+#include "mpm_internal.cuh"
+
+namespace mpm {
+namespace {
+
+// ------------------------------------------------------------------ kinematics
+
+// dF = I + sum_v du_v (x) grad S_vp, one warp per point
+__global__ void k_kinematics(int P, const int* __restrict__ nsup, const int* __restrict__ sidx,
+                             const double* __restrict__ dS, const double* __restrict__ du,
+                             double* dF) {
+  int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= P) return;
+  double a[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) a[i] = 0.0;
+  int n = nsup[w];
+  for (int k = lane; k < n; k += 32) {
+    size_t o = (size_t)w * MAXS + k;
+    int j = sidx[o];
+    double u0 = du[3 * (size_t)j], u1 = du[3 * (size_t)j + 1], u2 = du[3 * (size_t)j + 2];
+    double g0 = dS[3 * o], g1 = dS[3 * o + 1], g2 = dS[3 * o + 2];
+    a[0] += u0 * g0; a[1] += u0 * g1; a[2] += u0 * g2;
+    a[3] += u1 * g0; a[4] += u1 * g1; a[5] += u1 * g2;
+    a[6] += u2 * g0; a[7] += u2 * g1; a[8] += u2 * g2;
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) a[i] = warp_sum(a[i]);
+  if (lane < 9) dF[9 * (size_t)w + lane] = a[lane] + ((lane % 4 == 0) ? 1.0 : 0.0);
+}
+
+// ------------------------------------------------------------------ constitutive
+
+struct Law {
+  int model;
+  double nu, eta, xi, etab;
+};
+
+// symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations; columns of Q
+// are the eigenvectors (Q[3*i + a] = component i of vector a)
+__device__ void jacobi3(double* A, double* lam, double* Q) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Q[i] = (i == 0 || i == 4 || i == 8) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+    double on = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+    if (off == 0.0 || off <= 1e-36 * on) break;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int p = (r == 2) ? 1 : 0, q = (r == 0) ? 1 : 2;
+      double apq = A[3 * p + q];
+      if (apq == 0.0) continue;
+      double h = A[3 * q + q] - A[3 * p + p];
+      // tan of the rotation angle, smaller root of t^2 + (h/apq) t - 1 = 0
+      double th = 0.5 * h / apq;
+      double t = fabs(th) > 1e150 ? 0.5 / th : copysign(1.0, th) / (fabs(th) + sqrt(th * th + 1.0));
+      double cs = rsqrt(t * t + 1.0);
+      double sn = t * cs;
+      // rows/columns p and q of A, and columns of Q
+      double app = A[3 * p + p], aqq = A[3 * q + q];
+      A[3 * p + p] = app - t * apq;
+      A[3 * q + q] = aqq + t * apq;
+      A[3 * p + q] = A[3 * q + p] = 0.0;
+      const int o = 3 - p - q;
+      double aop = A[3 * o + p], aoq = A[3 * o + q];
+      A[3 * o + p] = A[3 * p + o] = cs * aop - sn * aoq;
+      A[3 * o + q] = A[3 * q + o] = sn * aop + cs * aoq;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        double qp = Q[3 * k + p], qq = Q[3 * k + q];
+        Q[3 * k + p] = cs * qp - sn * qq;
+        Q[3 * k + q] = sn * qp + cs * qq;
+      }
+    }
+  }
+  lam[0] = A[0];
+  lam[1] = A[4];
+  lam[2] = A[8];
+}
+
+// divided difference of the logarithm: (ln a - ln b)/(a - b), 1/b in the limit
+__device__ inline double ln_divdiff(double a, double b) {
+  double x = (a - b) / b;
+  if (fabs(x) < 1e-6) return (1.0 + x * (-0.5 + x * (1.0 / 3.0 - 0.25 * x))) / b;
+  return log1p(x) / (a - b);
+}
+
+// principal-space return: trial strains e -> tau_a, tangent d_ab = dtau_a/deps_b,
+// shear ratio g = (tau_a - tau_b)/(eps_a - eps_b); Hencky moduli from E, nu
+__device__ void principal_return(const Law& L, double E, double ys, const double* e, double* ta,
+                                 double* dd, double* gr) {
+  double mu = E / (2.0 * (1.0 + L.nu));
+  double lm = E * L.nu / ((1.0 + L.nu) * (1.0 - 2.0 * L.nu));
+  double kb = lm + 2.0 * mu / 3.0;
+  double tr = e[0] + e[1] + e[2];
+  double dev[3] = {e[0] - tr / 3.0, e[1] - tr / 3.0, e[2] - tr / 3.0};
+  double dn = sqrt(dev[0] * dev[0] + dev[1] * dev[1] + dev[2] * dev[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ta[a] = kb * tr + 2.0 * mu * dev[a];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) dd[3 * a + b] = lm + (a == b ? 2.0 * mu : 0.0);
+  }
+  *gr = 2.0 * mu;
+  if (L.model == 1) {
+    // von Mises: q = sqrt(3/2)|s|, radial return onto q = ys
+    double q = 1.224744871391589 * 2.0 * mu * dn;
+    if (q <= ys) return;
+    double fac = ys / q, g = 2.0 * mu * fac;
+    double n0 = dev[0] / dn, n1 = dev[1] / dn, n2 = dev[2] / dn;
+    double nn[3] = {n0, n1, n2};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      ta[a] = kb * tr + g * dev[a];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) dd[3 * a + b] = kb + g * ((a == b ? 1.0 : 0.0) - 1.0 / 3.0 - nn[a] * nn[b]);
+    }
+    *gr = g;
+  } else if (L.model == 2) {
+    // Drucker-Prager: f = sqrt(J2) + eta p - xi c, potential with etab
+    double G = mu, pm = kb * tr;
+    double sj = 1.4142135623730951 * G * dn;
+    double f = sj + L.eta * pm - L.xi * ys;
+    if (f <= 0.0) return;
+    double den = G + kb * L.eta * L.etab;
+    double dg = f / den;
+    if (sj - G * dg >= 0.0 && dn > 0.0) {
+      double ratio = 1.0 - G * dg / sj;
+      double pn = pm - kb * L.etab * dg;
+      double nn[3] = {dev[0] / dn, dev[1] / dn, dev[2] / dn};
+      double ddg[3];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) ddg[b] = (1.4142135623730951 * G * nn[b] + L.eta * kb) / den;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        ta[a] = pn + 2.0 * G * ratio * dev[a];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          double pd = (a == b ? 1.0 : 0.0) - 1.0 / 3.0;
+          dd[3 * a + b] = 2.0 * G * pd -
+                          1.4142135623730951 * G * (nn[a] * ddg[b] + dg * (pd - nn[a] * nn[b]) / dn) +
+                          kb * (1.0 - L.etab * ddg[b]);
+        }
+      }
+      *gr = 2.0 * G * ratio;
+    } else {
+      double pa = L.xi * ys / L.eta;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        ta[a] = pa;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) dd[3 * a + b] = 0.0;
+      }
+      *gr = 0.0;
+    }
+  }
+}
+
+// Full per-point update.  in: dF, b_e,n (6); out: tau (6: xx yy zz xy yz xz),
+// b_e (6), A' (81, layout [(i*9 + k*3 + m)*3 + j] = A_ijkm - tau_im delta_jk)
+template <bool TANGENT, class TA>
+__device__ bool point_update_law(const Law& L, double E, double ys, const double* be, const double* dF,
+                                 double* tau6, double* be_new, TA* Aout) {
+  double b[9] = {be[0], be[3], be[5], be[3], be[1], be[4], be[5], be[4], be[2]};
+  double t[9], bt[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      t[3 * i + j] = dF[3 * i] * b[j] + dF[3 * i + 1] * b[3 + j] + dF[3 * i + 2] * b[6 + j];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      bt[3 * i + j] = t[3 * i] * dF[3 * j] + t[3 * i + 1] * dF[3 * j + 1] + t[3 * i + 2] * dF[3 * j + 2];
+  // symmetrise before the rotations
+  bt[1] = bt[3] = 0.5 * (bt[1] + bt[3]);
+  bt[2] = bt[6] = 0.5 * (bt[2] + bt[6]);
+  bt[5] = bt[7] = 0.5 * (bt[5] + bt[7]);
+  double lam[3], Q[9];
+  jacobi3(bt, lam, Q);
+  if (!(lam[0] > 0.0 && lam[1] > 0.0 && lam[2] > 0.0) || !isfinite(lam[0] + lam[1] + lam[2]))
+    return false;
+  double eps[3] = {0.5 * log(lam[0]), 0.5 * log(lam[1]), 0.5 * log(lam[2])};
+  double ta[3], dd[9], gr;
+  principal_return(L, E, ys, eps, ta, dd, &gr);
+  double mu = E / (2.0 * (1.0 + L.nu));
+  double lm = E * L.nu / ((1.0 + L.nu) * (1.0 - 2.0 * L.nu));
+  double tt = ta[0] + ta[1] + ta[2];
+  double bw[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) bw[a] = exp(2.0 * (ta[a] - lm * tt / (3.0 * lm + 2.0 * mu)) / (2.0 * mu));
+  // tau = Q diag(ta) Q^T, b_e = Q diag(bw) Q^T
+  const int ii[6] = {0, 1, 2, 0, 1, 0}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    int i = ii[s], j = jj[s];
+    tau6[s] = Q[3 * i] * ta[0] * Q[3 * j] + Q[3 * i + 1] * ta[1] * Q[3 * j + 1] + Q[3 * i + 2] * ta[2] * Q[3 * j + 2];
+    be_new[s] = Q[3 * i] * bw[0] * Q[3 * j] + Q[3 * i + 1] * bw[1] * Q[3 * j + 1] + Q[3 * i + 2] * bw[2] * Q[3 * j + 2];
+  }
+  if (TANGENT) {
+    // theta_ab = (tau_a - tau_b)/(lam_a - lam_b) = g/2 * divided difference of ln
+    double th01 = 0.5 * gr * ln_divdiff(lam[0], lam[1]);
+    double th02 = 0.5 * gr * ln_divdiff(lam[0], lam[2]);
+    double th12 = 0.5 * gr * ln_divdiff(lam[1], lam[2]);
+    double th[9] = {0.0, th01, th02, th01, 0.0, th12, th02, th12, 0.0};
+    double taum[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        int s = (i == j) ? i : (i + j == 1 ? 3 : (i + j == 3 ? 4 : 5));
+        taum[3 * i + j] = tau6[s];
+      }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k)
+          for (int m = 0; m < 3; ++m) {
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              double qia = Q[3 * i + a];
+#pragma unroll
+              for (int c = 0; c < 3; ++c) {
+                s += dd[3 * a + c] * qia * Q[3 * j + a] * Q[3 * k + c] * Q[3 * m + c];
+                if (a != c)
+                  s += th[3 * a + c] * qia * Q[3 * j + c] *
+                       (lam[c] * Q[3 * k + a] * Q[3 * m + c] + lam[a] * Q[3 * k + c] * Q[3 * m + a]);
+              }
+            }
+            if (j == k) s -= taum[3 * i + m];
+            Aout[(i * 9 + k * 3 + m) * 3 + j] = (TA)s;
+          }
+  }
+  return true;
+}
+
+__device__ inline double det3(const double* a) {
+  return a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+         a[2] * (a[3] * a[7] - a[4] * a[6]);
+}
+
+template <bool TANGENT, class TA>
+__global__ void k_constitutive(int P, Law L, const double* __restrict__ E, const double* __restrict__ ys,
+                               const double* __restrict__ be, const double* __restrict__ dF,
+                               double* tau, double* dFinv, TA* Aalg, int* err) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= P) return;
+  double f[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) f[i] = dF[9 * (size_t)w + i];
+  double det = det3(f);
+  double t6[6], bn[6];
+  bool ok = det > 0.0 && isfinite(det) &&
+            point_update_law<TANGENT, TA>(L, E[w], ys[w], be + 6 * (size_t)w, f, t6, bn,
+                                          Aalg + 81 * (size_t)w);
+  if (!ok) {
+    atomicOr(err, EB_NAN);
+#pragma unroll
+    for (int s = 0; s < 6; ++s) t6[s] = 0.0;
+    det = 1.0;
+  }
+#pragma unroll
+  for (int s = 0; s < 6; ++s) tau[6 * (size_t)w + s] = t6[s];
+  double id = 1.0 / det;
+  double* o = dFinv + 9 * (size_t)w;
+  o[0] = (f[4] * f[8] - f[5] * f[7]) * id;
+  o[1] = (f[2] * f[7] - f[1] * f[8]) * id;
+  o[2] = (f[1] * f[5] - f[2] * f[4]) * id;
+  o[3] = (f[5] * f[6] - f[3] * f[8]) * id;
+  o[4] = (f[0] * f[8] - f[2] * f[6]) * id;
+  o[5] = (f[2] * f[3] - f[0] * f[5]) * id;
+  o[6] = (f[3] * f[7] - f[4] * f[6]) * id;
+  o[7] = (f[1] * f[6] - f[0] * f[7]) * id;
+  o[8] = (f[0] * f[4] - f[1] * f[3]) * id;
+}
+
+// ------------------------------------------------------------------ internal force
+
+// f_int,v = V0 tau grad_x S_v with grad_x S = grad S . dF^{-1}; optionally store
+// grad_x S for the tangent gather
+template <class TG, bool STORE>
+__global__ void k_force(int P, const int* __restrict__ nsup, const int* __restrict__ sidx,
+                        const double* __restrict__ dS, const double* __restrict__ dFinv,
+                        const double* __restrict__ tau, const double* __restrict__ V0, double* fint,
+                        TG* gx) {
+  int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= P) return;
+  const double* fi = dFinv + 9 * (size_t)w;
+  double t0 = tau[6 * (size_t)w], t1 = tau[6 * (size_t)w + 1], t2 = tau[6 * (size_t)w + 2];
+  double t3 = tau[6 * (size_t)w + 3], t4 = tau[6 * (size_t)w + 4], t5 = tau[6 * (size_t)w + 5];
+  double v0 = V0[w];
+  int n = nsup[w];
+  for (int k = lane; k < n; k += 32) {
+    size_t o = (size_t)w * MAXS + k;
+    double a0 = dS[3 * o], a1 = dS[3 * o + 1], a2 = dS[3 * o + 2];
+    double g0 = a0 * fi[0] + a1 * fi[3] + a2 * fi[6];
+    double g1 = a0 * fi[1] + a1 * fi[4] + a2 * fi[7];
+    double g2 = a0 * fi[2] + a1 * fi[5] + a2 * fi[8];
+    int j = sidx[o];
+    atomicAdd(fint + 3 * (size_t)j, v0 * (t0 * g0 + t3 * g1 + t5 * g2));
+    atomicAdd(fint + 3 * (size_t)j + 1, v0 * (t3 * g0 + t1 * g1 + t4 * g2));
+    atomicAdd(fint + 3 * (size_t)j + 2, v0 * (t5 * g0 + t4 * g1 + t2 * g2));
+    if (STORE) {
+      gx[3 * o] = (TG)g0;
+      gx[3 * o + 1] = (TG)g1;
+      gx[3 * o + 2] = (TG)g2;
+    }
+  }
+}
+
+// R = f_int - load f_ext + K_G du   (one warp per row)
+__global__ void k_residual_rows(int nd, double load, const int* __restrict__ rp,
+                                const int* __restrict__ col, const double* __restrict__ kg,
+                                const double* __restrict__ du, const double* __restrict__ fint,
+                                const double* __restrict__ fext, double* R) {
+  int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= nd) return;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int s = rp[r] + lane; s < rp[r + 1]; s += 32) {
+    double k = kg[s];
+    if (k != 0.0) {
+      int c = col[s];
+      a0 += k * du[3 * (size_t)c];
+      a1 += k * du[3 * (size_t)c + 1];
+      a2 += k * du[3 * (size_t)c + 2];
+    }
+  }
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  a2 = warp_sum(a2);
+  if (lane < 3) {
+    double g = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+    size_t i = 3 * (size_t)r + lane;
+    R[i] = fint[i] - load * fext[i] + g;
+  }
+}
+
+// ------------------------------------------------------------------ tangent (row gather)
+
+constexpr int TW = 4;  // warps per block of the tangent gather
+
+__device__ inline int find_in(const int* a, int n, int v) {
+  int lo = 0, hi = n - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int x = a[mid];
+    if (x == v) return mid;
+    if (x < v)
+      lo = mid + 1;
+    else
+      hi = mid - 1;
+  }
+  return -1;
+}
+
+// One warp owns block row r: for every point p with r in its support (local
+// index k), K_{r,w} += V0_p (grad_x S_k)^T A'_p (grad_x S_w) for all w in the
+// support of p.  The row is written by this warp only, in source order, so the
+// sum is free of atomics and deterministic.  Ghost coefficients and the
+// Dirichlet identity rows/columns are applied at the end.
+template <class T>
+__global__ void __launch_bounds__(32 * TW)
+    k_tangent_rows(int nd, int P, const int* __restrict__ rp, const int* __restrict__ col,
+                   const long long* __restrict__ sptr, const uint64_t* __restrict__ skeys,
+                   const int* __restrict__ nsup, const int* __restrict__ sidx,
+                   const T* __restrict__ gx, const T* __restrict__ Aalg,
+                   const double* __restrict__ V0, const double* __restrict__ kg,
+                   const int* __restrict__ mask, T* K, int* err) {
+  __shared__ int cols[TW][MAXROW];
+  __shared__ T Tt[TW][32];
+  int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int r = blockIdx.x * TW + wi;
+  if (r >= nd) return;
+  int s0 = rp[r], nb = rp[r + 1] - s0;
+  if (nb > MAXROW) {
+    if (lane == 0) atomicOr(err, EB_ROW);
+    return;
+  }
+  for (int i = lane; i < nb; i += 32) cols[wi][i] = col[s0 + i];
+  T* Kr = K + 9 * (size_t)s0;
+  for (int i = lane; i < 9 * nb; i += 32) Kr[i] = (T)0;
+  __syncwarp();
+  for (long long q = sptr[r]; q < sptr[r + 1]; ++q) {
+    uint32_t sid = (uint32_t)skeys[q];
+    int w = (int)(sid >> 6), k = (int)(sid & 63);
+    if (w >= P) continue;  // ghost-face source: no point tangent
+    size_t ok = ((size_t)w * MAXS + k) * 3;
+    T gk0 = gx[ok], gk1 = gx[ok + 1], gk2 = gx[ok + 2];
+    T v0 = (T)V0[w];
+    if (lane < 27) {
+      const T* A = Aalg + 81 * (size_t)w + 3 * lane;
+      Tt[wi][lane] = v0 * (gk0 * A[0] + gk1 * A[1] + gk2 * A[2]);
+    }
+    __syncwarp();
+    int n = nsup[w];
+    for (int l = lane; l < n; l += 32) {
+      size_t o = (size_t)w * MAXS + l;
+      int c = sidx[o];
+      T g0 = gx[3 * o], g1 = gx[3 * o + 1], g2 = gx[3 * o + 2];
+      int idx = find_in(cols[wi], nb, c);
+      if (idx < 0) continue;
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        const T* tt = &Tt[wi][3 * e];
+        Kr[(size_t)e * nb + idx] += tt[0] * g0 + tt[1] * g1 + tt[2] * g2;
+      }
+    }
+    __syncwarp();
+  }
+  // ghost, then the Dirichlet identity
+  int mr = mask[r];
+  for (int i = lane; i < nb; i += 32) {
+    double kv = kg[s0 + i];
+    int c = cols[wi][i];
+    int mc = mask[c];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        size_t at = (size_t)(3 * a + b) * nb + i;
+        T v = Kr[at];
+        if (a == b) v += (T)kv;
+        if (((mr >> a) & 1) || ((mc >> b) & 1)) v = (c == r && a == b) ? (T)1 : (T)0;
+        Kr[at] = v;
+      }
+  }
+}
+
+// ------------------------------------------------------------------ contact (Sec. 2.3)
+
+__device__ inline int find_slot(const int* __restrict__ rp, const int* __restrict__ col, int r, int c) {
+  int lo = rp[r], hi = rp[r + 1] - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int v = col[mid];
+    if (v == c) return mid;
+    if (v < c)
+      lo = mid + 1;
+    else
+      hi = mid - 1;
+  }
+  return -1;
+}
+
+// one thread per candidate domain corner: gap against the body at the moved
+// corner, force -eps_N phi n spread by the background basis, stiffness
+// eps_N (n n^T + phi H) phi_a phi_b (Dirichlet entries skipped)
+template <class T, bool TANGENT>
+__global__ void k_contact(int nc8, const int* __restrict__ cand, const int* __restrict__ cb_n,
+                          const int* __restrict__ cb_idx, const double* __restrict__ cb_phi,
+                          const double* __restrict__ cb_y0, const double* __restrict__ pE,
+                          const double* __restrict__ pV0, mpm_rigid body, double L, double pf,
+                          const double* __restrict__ du, double* R, double* fc, double* reac,
+                          const int* __restrict__ rp, const int* __restrict__ col,
+                          const int* __restrict__ mask, T* K) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nc8) return;
+  int w = cand[i >> 3], n = cb_n[i];
+  const int* ids = cb_idx + (size_t)i * MAXCB;
+  const double* ph = cb_phi + (size_t)i * MAXCB;
+  double y[3] = {cb_y0[3 * (size_t)i], cb_y0[3 * (size_t)i + 1], cb_y0[3 * (size_t)i + 2]};
+  for (int e = 0; e < n; ++e)
+    for (int d = 0; d < 3; ++d) y[d] += ph[e] * du[3 * (size_t)ids[e] + d];
+  double phi, nv[3], H[9];
+  if (!body_sdf(body, L, y, &phi, nv, H) || !(phi < 0.0)) return;
+  double epsN = pf * pE[w] * pow(pV0[w], 2.0 / 3.0);
+  double f[3] = {-epsN * phi * nv[0], -epsN * phi * nv[1], -epsN * phi * nv[2]};
+  for (int d = 0; d < 3; ++d) atomicAdd(reac + d, -f[d]);
+  for (int e = 0; e < n; ++e)
+    for (int d = 0; d < 3; ++d) {
+      atomicAdd(R + 3 * (size_t)ids[e] + d, -ph[e] * f[d]);
+      atomicAdd(fc + 3 * (size_t)ids[e] + d, ph[e] * f[d]);
+    }
+  if (!TANGENT) return;
+  double kc[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) kc[3 * a + b] = epsN * (nv[a] * nv[b] + phi * H[3 * a + b]);
+  for (int ea = 0; ea < n; ++ea) {
+    int ra = ids[ea];
+    int s0 = rp[ra], nb = rp[ra + 1] - s0, ma = mask[ra];
+    for (int eb = 0; eb < n; ++eb) {
+      int cb = ids[eb];
+      int sl = find_slot(rp, col, ra, cb);
+      if (sl < 0) continue;
+      int mb = mask[cb];
+      double pp = ph[ea] * ph[eb];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          if (((ma >> a) & 1) || ((mb >> b) & 1)) continue;
+          atomicAdd(K + 9 * (size_t)s0 + (size_t)(3 * a + b) * nb + (sl - s0), (T)(pp * kc[3 * a + b]));
+        }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ norms
+
+// slots: 0 ||R_free||^2, 1 ||f_int||^2, 2 ||load f_ext + f_c||^2
+__global__ void k_norms(int n3, const double* __restrict__ R, const double* __restrict__ fint,
+                        const double* __restrict__ fext, const double* __restrict__ fc, double load,
+                        const int* __restrict__ mask, double* out) {
+  __shared__ double sh[32];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
+    if (!((mask[i / 3] >> (i % 3)) & 1)) a += R[i] * R[i];
+    if (fint) b += fint[i] * fint[i];
+    if (fext) {
+      double e = load * fext[i] + (fc ? fc[i] : 0.0);
+      c += e * e;
+    }
+  }
+  a = block_sum(a, sh);
+  b = block_sum(b, sh);
+  c = block_sum(c, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(out, a);
+    atomicAdd(out + 1, b);
+    atomicAdd(out + 2, c);
+  }
+}
+
+}  // namespace
+
+Law make_law(const mpm_material& mat) {
+  Law L{};
+  L.model = mat.model;
+  L.nu = mat.nu;
+  double sp = sin(mat.phi), ss = sin(mat.psi);
+  L.eta = 6.0 * sp / (sqrt(3.0) * (3.0 - sp));
+  L.xi = 6.0 * cos(mat.phi) / (sqrt(3.0) * (3.0 - sp));
+  L.etab = 6.0 * ss / (sqrt(3.0) * (3.0 - ss));
+  return L;
+}
+
+double norm_free(mpm_ctx* c, const mpm_mesh* m, const double* R) {
+  double* slot = c->d_red + 16;
+  MPM_CUDA(cudaMemsetAsync(slot, 0, 3 * sizeof(double), c->stream));
+  k_norms<<<4 * 152, 256, 0, c->stream>>>(3 * m->ndof, R, nullptr, nullptr, nullptr, 0.0,
+                                          ptr<int>(m->dof_mask), slot);
+  MPM_CUDA(cudaMemcpyAsync(c->h_red + 16, slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  MPM_CUDA(cudaStreamSynchronize(c->stream));
+  return sqrt(c->h_red[16]);
+}
+
+void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm_rigid& body,
+              const double* du, double load, int precision, double* R, void* K, AsmOut* out,
+              bool want_norms) {
+  mpm_mesh* m = const_cast<mpm_mesh*>(mc);
+  cudaStream_t st = c->stream;
+  int P = m->np, nd = m->ndof;
+  Law L = make_law(mat);
+  double* dF = grow<double>(c, m->dF, 9 * (size_t)P);
+  double* dFinv = grow<double>(c, m->dFinv, 9 * (size_t)P);
+  double* tau = grow<double>(c, m->tau, 6 * (size_t)P);
+  const int* nsup = ptr<int>(m->nsup);
+  const int* sidx = ptr<int>(m->sidx);
+  const double* dS = ptr<double>(m->dS);
+  k_kinematics<<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, du, dF);
+  bool mixed = precision == MPM_MIXED;
+  size_t asz = mixed ? sizeof(float) : sizeof(double);
+  void* Aalg = K ? grow_bytes(c, m->Aalg, 81 * (size_t)P * asz) : nullptr;
+  void* gx = K ? grow_bytes(c, m->gx, 3 * (size_t)P * MAXS * asz) : nullptr;
+  if (!K)
+    k_constitutive<false, double><<<grid_for(P, 128), 128, 0, st>>>(
+        P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv, nullptr,
+        c->d_err);
+  else if (mixed)
+    k_constitutive<true, float><<<grid_for(P, 128), 128, 0, st>>>(
+        P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv,
+        (float*)Aalg, c->d_err);
+  else
+    k_constitutive<true, double><<<grid_for(P, 128), 128, 0, st>>>(
+        P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv,
+        (double*)Aalg, c->d_err);
+  double* fint = grow<double>(c, c->v[0], 3 * (size_t)nd);
+  double* fc = grow<double>(c, c->v[1], 3 * (size_t)nd);
+  MPM_CUDA(cudaMemsetAsync(fint, 0, sizeof(double) * 3 * nd, st));
+  MPM_CUDA(cudaMemsetAsync(fc, 0, sizeof(double) * 3 * nd, st));
+  const double* V0 = ptr<double>(m->pV0);
+  if (!K)
+    k_force<double, false><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
+                                                           nullptr);
+  else if (mixed)
+    k_force<float, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
+                                                         (float*)gx);
+  else
+    k_force<double, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
+                                                          (double*)gx);
+  const int* rp = ptr<int>(m->row_ptr);
+  const int* col = ptr<int>(m->col);
+  k_residual_rows<<<grid_for(nd, 8), 256, 0, st>>>(nd, load, rp, col, ptr<double>(m->kg), du, fint,
+                                                   ptr<double>(m->fext), R);
+  if (K) {
+    if (mixed)
+      k_tangent_rows<float><<<grid_for(nd, TW), 32 * TW, 0, st>>>(
+          nd, P, rp, col, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
+          (const float*)gx, (const float*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
+          (float*)K, c->d_err);
+    else
+      k_tangent_rows<double><<<grid_for(nd, TW), 32 * TW, 0, st>>>(
+          nd, P, rp, col, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
+          (const double*)gx, (const double*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
+          (double*)K, c->d_err);
+  }
+  double* reac = c->d_red + 20;
+  MPM_CUDA(cudaMemsetAsync(reac, 0, 3 * sizeof(double), st));
+  if (m->ncand && mat.contact_on && body.kind != 0) {
+    int n8 = 8 * m->ncand;
+    if (!K)
+      k_contact<double, false><<<grid_for(n8, 128), 128, 0, st>>>(
+          n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
+          ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
+          col, ptr<int>(m->dof_mask), (double*)nullptr);
+    else if (mixed)
+      k_contact<float, true><<<grid_for(n8, 128), 128, 0, st>>>(
+          n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
+          ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
+          col, ptr<int>(m->dof_mask), (float*)K);
+    else
+      k_contact<double, true><<<grid_for(n8, 128), 128, 0, st>>>(
+          n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
+          ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
+          col, ptr<int>(m->dof_mask), (double*)K);
+  }
+  if (want_norms) {
+    double* slot = c->d_red + 16;
+    MPM_CUDA(cudaMemsetAsync(slot, 0, 3 * sizeof(double), st));
+    k_norms<<<4 * 152, 256, 0, st>>>(3 * nd, R, fint, ptr<double>(m->fext), fc, load,
+                                     ptr<int>(m->dof_mask), slot);
+    MPM_CUDA(cudaMemcpyAsync(c->h_red + 16, slot, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(cudaStreamSynchronize(st));
+    out->fint_norm = sqrt(c->h_red[17]);
+    out->fextc_norm = sqrt(c->h_red[18]);
+    for (int d = 0; d < 3; ++d) out->reaction[d] = c->h_red[20 + d];
+  }
+}
+
+// ------------------------------------------------------------------ point update helpers (used by mpm_step.cu)
+
+namespace {
+
+// end-of-step update, one thread per (sorted) point: x += sum S du, F <- dF F,
+// b_e from the converged return, l = l0 diag(U), U = sqrt(F^T F)
+__global__ void k_point_update(int P, Law L, const int* __restrict__ perm,
+                               const int* __restrict__ nsup, const int* __restrict__ sidx,
+                               const double* __restrict__ S, const double* __restrict__ dS,
+                               const double* __restrict__ du, const double* __restrict__ pE,
+                               const double* __restrict__ pys, const double* __restrict__ pbe,
+                               const double* __restrict__ pF, const double* __restrict__ px,
+                               const double* __restrict__ pl0, mpm_points pts, int* err) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= P) return;
+  double dF[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, dx[3] = {0, 0, 0};
+  int n = nsup[w];
+  for (int k = 0; k < n; ++k) {
+    size_t o = (size_t)w * MAXS + k;
+    int j = sidx[o];
+    double u[3] = {du[3 * (size_t)j], du[3 * (size_t)j + 1], du[3 * (size_t)j + 2]};
+    for (int i = 0; i < 3; ++i) {
+      dx[i] += S[o] * u[i];
+      for (int jj = 0; jj < 3; ++jj) dF[3 * i + jj] += u[i] * dS[3 * o + jj];
+    }
+  }
+  double t6[6], bn[6];
+  if (!point_update_law<false, double>(L, pE[w], pys[w], pbe + 6 * (size_t)w, dF, t6, bn, nullptr)) {
+    atomicOr(err, EB_NAN);
+    return;
+  }
+  const double* Fo = pF + 9 * (size_t)w;
+  double Fn[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      Fn[3 * i + j] = dF[3 * i] * Fo[j] + dF[3 * i + 1] * Fo[3 + j] + dF[3 * i + 2] * Fo[6 + j];
+  double C[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      C[3 * i + j] = Fn[i] * Fn[j] + Fn[3 + i] * Fn[3 + j] + Fn[6 + i] * Fn[6 + j];
+  double lam[3], Q[9];
+  jacobi3(C, lam, Q);
+  size_t p = perm[w];
+  for (int d = 0; d < 3; ++d) {
+    double u = 0.0;
+    for (int a = 0; a < 3; ++a) u += sqrt(lam[a]) * Q[3 * d + a] * Q[3 * d + a];
+    pts.x[3 * p + d] = px[3 * (size_t)w + d] + dx[d];
+    pts.lp[3 * p + d] = pl0[3 * (size_t)w + d] * u;
+  }
+  for (int i = 0; i < 9; ++i) pts.F[9 * p + i] = Fn[i];
+  for (int s = 0; s < 6; ++s) pts.be[6 * p + s] = bn[s];
+}
+
+}  // namespace
+
+void point_update(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const double* du,
+                  mpm_points* pts) {
+  mpm_mesh* m = const_cast<mpm_mesh*>(mc);
+  int P = m->np;
+  k_point_update<<<grid_for(P, 128), 128, 0, c->stream>>>(
+      P, make_law(mat), ptr<int>(m->perm), ptr<int>(m->nsup), ptr<int>(m->sidx), ptr<double>(m->S),
+      ptr<double>(m->dS), du, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe),
+      ptr<double>(m->pF), ptr<double>(m->px), ptr<double>(m->pl0), *pts, c->d_err);
+}
+
+}  // namespace mpm

@@ -1,0 +1,377 @@
+// Internal declarations of libmpm_gb300: context, mesh, device helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+
+#include "mpm.h"
+
+namespace mpm {
+
+constexpr int MAXS = MPM_MAXS;   // support entries per point
+constexpr int MAXC = 16;         // resolved constraint entries per node
+constexpr int MAXK = 27;         // leaves overlapped by one GIMP domain (basis)
+constexpr int SPLIT_STACK = 64;  // work list of the split test (overflow => split)
+constexpr int MAXE = 512;        // (leaf corner, constraint) entries of one domain
+constexpr int MAXCB = 32;        // background-basis entries at a contact corner
+constexpr int MAXG = 64;         // dofs of one ghost face, I(K+) u I(K-)
+constexpr int HASH = 2048;       // per-warp hash set of the pattern builder
+constexpr int MAXROW = 1024;     // blocks in one row of the stiffness
+
+// device error word bits
+enum : int {
+  EB_SUPPORT = 1,
+  EB_NAN = 2,
+  EB_BALANCE = 4,
+  EB_DOMAIN = 8,
+  EB_ROW = 16,
+  EB_KRYLOV = 32
+};
+
+struct Geo {
+  int D;        // finest level
+  int N;        // 2^D finest cells per axis
+  double L;     // cube side
+  double unit;  // L / 2^D
+  double scale; // 2^D / L
+};
+
+struct CudaError : std::runtime_error {
+  int code;
+  CudaError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define MPM_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      throw ::mpm::CudaError(MPM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace mpm
+
+struct mpm_ctx {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int* d_err = nullptr;        // device error word
+  double* d_red = nullptr;     // device reduction slots (64 doubles)
+  double* h_red = nullptr;     // pinned host mirror
+  int* h_int = nullptr;        // pinned host ints (counts)
+  mpm::Buf cub_tmp;            // CUB temporary storage
+  mpm::Buf tmp[8];             // general scratch
+  std::string err;
+  mpm_mesh* step_mesh = nullptr;
+  // Newton / Krylov work vectors (grown on demand)
+  mpm::Buf v[24];
+};
+
+struct mpm_mesh {
+  mpm_ctx* ctx = nullptr;
+  mpm::Geo g{};
+  mpm_domain dom{};
+  mpm_rigid body{};
+  mpm_adapt ad{};
+  mpm_material mat{};
+  // octree leaves, Morton order of the anchor
+  int nleaf = 0;
+  mpm::Buf leaf_key, leaf_lev, leaf_tmp_key, leaf_tmp_lev, flag, scan;
+  // nodes
+  int nnode = 0, nhang = 0, ncon = 0;
+  mpm::Buf node_key, corner, hang, owner, cptr, cidx, cw, node_dof;
+  // dofs
+  int ndof = 0;
+  mpm::Buf dof_node, dof_mask;
+  // points, in cell-sorted order (perm: sorted index -> caller index)
+  int np = 0, maxs = 0;
+  mpm::Buf perm, pcell, px, plp, pl0, pF, pbe, pV0, pmass, pE, pys;
+  mpm::Buf nsup, sidx, S, dS, S32, dS32;
+  mpm::Buf populated, betaK, isB;
+  // ghost faces
+  int nghost = 0;
+  mpm::Buf gface, gdof, gn;
+  // pattern
+  int nnzb = 0, maxrow = 0;
+  mpm::Buf row_ptr, col, kg, rowcnt;
+  // sources of each row: (sorted point or ghost face) << 6 | local index
+  long long nsrc = 0;
+  mpm::Buf src_key, src_ptr;
+  // gravity force at load 1
+  mpm::Buf fext;
+  // contact candidates (sorted point ids) and the basis at their 8 corners
+  int ncand = 0;
+  mpm::Buf cand, cb_n, cb_idx, cb_phi, cb_y0;
+  // per-iteration point data
+  mpm::Buf dF, dFinv, tau, Aalg, gx;
+  int built = 0;
+};
+
+namespace mpm {
+
+// ------------------------------------------------------------------ growable buffers
+
+inline void* grow_bytes(mpm_ctx* c, Buf& b, size_t need) {
+  if (need == 0) need = 16;
+  if (need > b.bytes) {
+    if (b.p) MPM_CUDA(cudaFreeAsync(b.p, c->stream));
+    b.p = nullptr;
+    size_t nb = need + need / 4 + 256;
+    MPM_CUDA(cudaMallocAsync(&b.p, nb, c->stream));
+    b.bytes = nb;
+  }
+  return b.p;
+}
+
+template <class T>
+inline T* grow(mpm_ctx* c, Buf& b, size_t n) {
+  return (T*)grow_bytes(c, b, n * sizeof(T));
+}
+
+template <class T>
+inline T* ptr(const Buf& b) {
+  return (T*)b.p;
+}
+
+inline void free_buf(mpm_ctx* c, Buf& b) {
+  if (b.p) cudaFreeAsync(b.p, c->stream);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+inline int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }
+
+// ------------------------------------------------------------------ Morton codes
+
+__host__ __device__ inline uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffULL;
+  v = (v | (v << 32)) & 0x1f00000000ffffULL;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+  v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+  v = (v | (v << 2)) & 0x1249249249249249ULL;
+  return v;
+}
+
+__host__ __device__ inline uint32_t compact3(uint64_t v) {
+  v &= 0x1249249249249249ULL;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ULL;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00fULL;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffULL;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffULL;
+  v = (v ^ (v >> 32)) & 0x1fffffULL;
+  return (uint32_t)v;
+}
+
+__host__ __device__ inline uint64_t morton(int x, int y, int z) {
+  return spread3((uint64_t)x) | (spread3((uint64_t)y) << 1) | (spread3((uint64_t)z) << 2);
+}
+
+__host__ __device__ inline void demorton(uint64_t k, int* a) {
+  a[0] = (int)compact3(k);
+  a[1] = (int)compact3(k >> 1);
+  a[2] = (int)compact3(k >> 2);
+}
+
+// leaf holding finest cell (x,y,z): last anchor key <= key(cell)
+__device__ inline int locate(const uint64_t* __restrict__ key, int n, int x, int y, int z) {
+  uint64_t k = morton(x, y, z);
+  int lo = 0, hi = n;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(key + mid) <= k)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// box bound in finest-grid units, moved onto a grid plane when within 1e-9
+__device__ inline double snap_grid(double v) {
+  double r = floor(v + 0.5);
+  return fabs(v - r) < 1e-9 ? r : v;
+}
+
+// ------------------------------------------------------------------ rigid body geometry
+
+__device__ inline double body_rxy(const mpm_rigid& b, const double* lo, const double* hi) {
+  double dx = fmax(fmax(lo[0] - b.cx, 0.0), b.cx - hi[0]);
+  double dy = fmax(fmax(lo[1] - b.cy, 0.0), b.cy - hi[1]);
+  return sqrt(dx * dx + dy * dy);
+}
+
+// does the closed box meet the solid body?
+__device__ inline bool body_meets_box(const mpm_rigid& b, const double* lo, const double* hi) {
+  if (b.kind == 1) return hi[2] >= b.z && body_rxy(b, lo, hi) <= b.r;
+  if (b.kind == 2) {
+    if (hi[2] < b.z) return false;
+    double rmax = fmin((hi[2] - b.z) * tan(b.alpha), b.r);
+    return body_rxy(b, lo, hi) <= rmax;
+  }
+  return false;
+}
+
+__device__ inline double dist_to_segment(double px, double pz, double ax, double az, double bx,
+                                         double bz) {
+  double vx = bx - ax, vz = bz - az;
+  double t = ((px - ax) * vx + (pz - az) * vz) / (vx * vx + vz * vz);
+  t = fmin(fmax(t, 0.0), 1.0);
+  double qx = ax + t * vx - px, qz = az + t * vz - pz;
+  return sqrt(qx * qx + qz * qz);
+}
+
+// Euclidean distance from a point to the solid (0 inside)
+__device__ inline double body_distance(const mpm_rigid& b, const double* x) {
+  double rx = x[0] - b.cx, ry = x[1] - b.cy;
+  double rho = sqrt(rx * rx + ry * ry), z = x[2];
+  if (b.kind == 1) {
+    if (z >= b.z) return fmax(rho - b.r, 0.0);
+    if (rho <= b.r) return b.z - z;
+    return hypot(rho - b.r, b.z - z);
+  }
+  if (b.kind == 2) {
+    double ta = tan(b.alpha), hc = b.r / ta;
+    if (z >= b.z && rho <= fmin((z - b.z) * ta, b.r)) return 0.0;
+    double d1 = dist_to_segment(rho, z, 0.0, b.z, b.r, b.z + hc);
+    double d2 = (z >= b.z + hc) ? fabs(rho - b.r) : hypot(rho - b.r, b.z + hc - z);
+    return fmin(d1, d2);
+  }
+  return 1e300;
+}
+
+// Signed distance (negative inside), outward normal n and Hessian H (row-major)
+// of the body surface, for the penalty contact.  Returns true inside.
+__device__ inline bool body_sdf(const mpm_rigid& b, double L, const double* x, double* phi,
+                                double* n, double* H) {
+  double rx = x[0] - b.cx, ry = x[1] - b.cy;
+  double rho = sqrt(rx * rx + ry * ry), z = x[2];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) H[i] = 0.0;
+  n[0] = n[1] = n[2] = 0.0;
+  bool axis = rho < 1e-12 * L;
+  double ux = axis ? 1.0 : rx / rho, uy = axis ? 0.0 : ry / rho;
+  double curv = 0.0;  // curvature factor of the lateral surface
+  if (b.kind == 1) {
+    if (!(z > b.z && rho < b.r)) {
+      *phi = body_distance(b, x);
+      return false;
+    }
+    double fb = b.z - z, fs = rho - b.r;
+    if (fb >= fs) {
+      *phi = fb;
+      n[2] = -1.0;
+      return true;
+    }
+    *phi = fs;
+    n[0] = ux;
+    n[1] = uy;
+    curv = 1.0;
+  } else if (b.kind == 2) {
+    double ta = tan(b.alpha), hc = b.r / ta;
+    if (!(z > b.z && rho < fmin((z - b.z) * ta, b.r))) {
+      *phi = body_distance(b, x);
+      return false;
+    }
+    if (z <= b.z + hc) {
+      double ca = cos(b.alpha), sa = sin(b.alpha);
+      *phi = rho * ca - (z - b.z) * sa;
+      n[0] = ca * ux;
+      n[1] = ca * uy;
+      n[2] = -sa;
+      curv = ca;
+    } else {
+      *phi = rho - b.r;
+      n[0] = ux;
+      n[1] = uy;
+      curv = 1.0;
+    }
+  } else {
+    *phi = 1e300;
+    return false;
+  }
+  if (!axis) {
+    H[0] = curv * (1.0 - ux * ux) / rho;
+    H[1] = -curv * ux * uy / rho;
+    H[3] = H[1];
+    H[4] = curv * (1.0 - uy * uy) / rho;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ warp helpers
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ inline int warp_sum_int(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum, result valid in thread 0; blockDim.x a multiple of 32, <= 1024
+__device__ inline double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------ host entry helpers
+
+void set_error(mpm_ctx* c, const std::string& m);
+int check_device_error(mpm_ctx* c, const char* where);
+void sync(mpm_ctx* c);
+
+// build phase (mpm_build.cu)
+void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid& body,
+                const mpm_adapt& ad, const mpm_material& mat, mpm_points* pts, int flags);
+
+// assembly (mpm_assemble.cu)
+struct AsmOut {
+  double reaction[3];
+  double fint_norm, fextc_norm;
+};
+void assemble(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const mpm_rigid& body,
+              const double* du, double load, int precision, double* R, void* K, AsmOut* out,
+              bool want_norms);
+double norm_free(mpm_ctx* c, const mpm_mesh* m, const double* R);
+
+// solve (mpm_solve.cu)
+void solve(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const void* K, const double* b,
+           double* x, const mpm_solve_params& prm, mpm_solve_stats* st);
+
+// point update (mpm_step.cu)
+void point_update(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const double* du,
+                  mpm_points* pts);
+
+// CUB wrappers (mpm_cub.cu)
+void cub_exclusive_sum_int(mpm_ctx* c, const int* in, int* out, int n);
+void cub_sort_u64(mpm_ctx* c, uint64_t* keys, uint64_t* tmp, int n, int end_bit);
+void cub_sort_pairs_int(mpm_ctx* c, const int* kin, int* kout, const int* vin, int* vout, int n,
+                        int end_bit);
+int cub_unique_u64(mpm_ctx* c, const uint64_t* in, uint64_t* out, int n);
+
+}  // namespace mpm

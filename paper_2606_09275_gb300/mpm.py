@@ -1,0 +1,345 @@
+"""ctypes binding of libmpm_gb300.so (include/mpm.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Device memory is held in torch tensors (passed as raw pointers) and
+work is issued on the current torch CUDA stream.  There is no fallback: if the
+shared library is missing or fails to load, the import raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+MAXS = 64
+OK = 0
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_NEWTON", 4: "ERR_KRYLOV", 5: "ERR_NAN",
+          6: "ERR_SUPPORT", 7: "ERR_CAPACITY", 8: "ERR_BALANCE", 9: "ERR_DOMAIN"}
+FP64, MIXED = 0, 1
+
+EXPORT = dict(leaf_level=0, leaf_anchor=1, node_coord=2, node_hang=3, node_dof=4, cptr=5, cidx=6,
+              cw=7, nsup=8, sidx=9, S=10, dS=11, row_ptr=12, col=13, ghost=14, bcmask=15,
+              populated=16, ghost_faces=17)
+
+SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_octree_build", "mpm_mesh_free",
+           "mpm_mesh_counts", "mpm_mesh_export", "mpm_assemble", "mpm_solve", "mpm_step"]
+
+
+class Domain(C.Structure):
+    _fields_ = [("L", C.c_double), ("depth_min", C.c_int), ("depth_max", C.c_int),
+                ("nbc", C.c_int), ("bc_axis", C.c_int * 8), ("bc_pos", C.c_double * 8),
+                ("bc_mask", C.c_int * 8)]
+
+
+class Rigid(C.Structure):
+    _fields_ = [("kind", C.c_int), ("cx", C.c_double), ("cy", C.c_double), ("z", C.c_double),
+                ("r", C.c_double), ("alpha", C.c_double)]
+
+
+class Adapt(C.Structure):
+    _fields_ = [("dx_region", C.c_double), ("beta", C.c_double)]
+
+
+class Material(C.Structure):
+    _fields_ = [("model", C.c_int), ("nu", C.c_double), ("phi", C.c_double), ("psi", C.c_double),
+                ("g", C.c_double * 3), ("kappa", C.c_double), ("pf", C.c_double),
+                ("ghost_on", C.c_int), ("contact_on", C.c_int)]
+
+
+class PointsT(C.Structure):
+    _fields_ = [("count", C.c_int), ("capacity", C.c_int)] + [
+        (n, C.c_void_p) for n in ("x", "lp", "l0", "F", "be", "V0", "mass", "E", "ys")]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("nleaf", "nnode", "nhang", "ndof", "nnzb", "nghost", "npts",
+                                       "maxs", "ncontact", "maxrow")]
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("method", C.c_int), ("precision", C.c_int), ("tol", C.c_double),
+                ("maxit", C.c_int), ("inner_tol", C.c_double)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int), ("status", C.c_int),
+                ("relres", C.c_double)]
+
+
+class StepParams(C.Structure):
+    _fields_ = [("load", C.c_double), ("tol", C.c_double), ("maxit", C.c_int),
+                ("lin", SolveParams)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("newton_its", "lin_its", "status", "npts", "ndof", "nnzb")] + [
+        ("res_hist", C.c_double * 64), ("eta_hist", C.c_double * 64), ("reaction", C.c_double * 3),
+        ("ms_build", C.c_double), ("ms_assemble", C.c_double), ("ms_solve", C.c_double),
+        ("ms_update", C.c_double)]
+
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libmpm_gb300.so (building it first if it is out of date)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, i, d = C.c_void_p, C.c_int, C.c_double
+        L.mpm_create.argtypes = [C.POINTER(vp), vp]
+        L.mpm_destroy.argtypes = [vp]
+        L.mpm_last_error.argtypes = [vp]
+        L.mpm_last_error.restype = C.c_char_p
+        L.mpm_octree_build.argtypes = [vp, C.POINTER(Domain), C.POINTER(Rigid), C.POINTER(Adapt),
+                                       C.POINTER(Material), C.POINTER(PointsT), i, C.POINTER(vp)]
+        L.mpm_mesh_free.argtypes = [vp]
+        L.mpm_mesh_counts.argtypes = [vp, C.POINTER(MeshInfo)]
+        L.mpm_mesh_export.argtypes = [vp, i, vp, C.c_size_t]
+        L.mpm_assemble.argtypes = [vp, vp, C.POINTER(Material), C.POINTER(Rigid), vp, d, i, vp, vp,
+                                   vp, vp]
+        L.mpm_solve.argtypes = [vp, vp, C.POINTER(Material), vp, vp, vp, C.POINTER(SolveParams),
+                                C.POINTER(SolveStats)]
+        L.mpm_step.argtypes = [vp, C.POINTER(Domain), C.POINTER(Rigid), C.POINTER(Adapt),
+                               C.POINTER(Material), C.POINTER(PointsT), C.POINTER(StepParams),
+                               C.POINTER(StepStats)]
+        _lib = L
+    return _lib
+
+
+class MPMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+# ----------------------------------------------------------------- parameter structs
+
+def domain(cfg):
+    d = Domain()
+    d.L = cfg["L"]
+    d.depth_min, d.depth_max = cfg["depth_min"], cfg["depth_max"]
+    d.nbc = len(cfg["bc"])
+    for k, (ax, pos, mask) in enumerate(cfg["bc"]):
+        d.bc_axis[k], d.bc_pos[k], d.bc_mask[k] = ax, pos, mask
+    return d
+
+
+def rigid(cfg, z=None):
+    r = Rigid()
+    b = cfg.get("body")
+    if b:
+        r.kind, r.cx, r.cy = b["kind"], b["cx"], b["cy"]
+        r.z = b["z0"] if z is None else z
+        r.r, r.alpha = b["r"], b.get("alpha", 0.0)
+    return r
+
+
+def adapt(cfg):
+    return Adapt(cfg.get("dx_region", 0.0), cfg.get("beta", 2.0))
+
+
+def material(cfg):
+    m = Material()
+    m.model, m.nu, m.phi, m.psi = cfg["model"], cfg["nu"], cfg.get("phi", 0.0), cfg.get("psi", 0.0)
+    for k in range(3):
+        m.g[k] = cfg["g"][k]
+    m.kappa, m.pf = cfg.get("kappa", 10.0), cfg.get("pf", 50.0)
+    m.ghost_on, m.contact_on = int(cfg.get("ghost", 1)), int(cfg.get("contact", 1))
+    return m
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ----------------------------------------------------------------- objects
+
+class Context:
+    """Library context bound to the current torch CUDA stream."""
+
+    def __init__(self, stream=None):
+        h = C.c_void_p()
+        s = C.c_void_p(stream.cuda_stream) if stream is not None else _stream()
+        st = lib().mpm_create(C.byref(h), s)
+        if st:
+            raise MPMError(st, "mpm_create failed")
+        self.h = h
+
+    def error(self):
+        return lib().mpm_last_error(self.h).decode()
+
+    def check(self, st):
+        if st:
+            raise MPMError(st, self.error())
+
+    def close(self):
+        if self.h:
+            lib().mpm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_PT = (("x", 3), ("lp", 3), ("l0", 3), ("F", 9), ("be", 6), ("V0", 1), ("mass", 1), ("E", 1),
+       ("ys", 1))
+
+
+class Points:
+    """Caller-owned device point arrays (torch float64 tensors of `capacity` rows)."""
+
+    def __init__(self, pts, capacity=None, device="cuda"):
+        n = len(pts["x"])
+        cap = max(n, capacity or n)
+        self.count, self.capacity = n, cap
+        self.t = {}
+        for k, w in _PT:
+            t = torch.zeros((cap, w) if w > 1 else (cap,), dtype=torch.float64, device=device)
+            t[:n] = torch.as_tensor(np.asarray(pts[k], dtype=np.float64)).reshape(t[:n].shape)
+            self.t[k] = t
+
+    def struct(self):
+        s = PointsT()
+        s.count, s.capacity = self.count, self.capacity
+        for k, _ in _PT:
+            setattr(s, k, self.t[k].data_ptr())
+        return s
+
+    def numpy(self):
+        n = self.count
+        return {k: self.t[k][:n].cpu().numpy().copy() for k, _ in _PT}
+
+
+class Mesh:
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+
+    def info(self):
+        i = MeshInfo()
+        self.ctx.check(lib().mpm_mesh_counts(self.h, C.byref(i)))
+        return {n: getattr(i, n) for n, _ in MeshInfo._fields_}
+
+    def export(self, what):
+        info = self.info()
+        nl, nn, nd, nz, P = info["nleaf"], info["nnode"], info["ndof"], info["nnzb"], info["npts"]
+        sizes = dict(leaf_level=(nl, np.int32), leaf_anchor=((nl, 3), np.int32),
+                     node_coord=((nn, 3), np.int32), node_hang=(nn, np.int32),
+                     node_dof=(nn, np.int32), cptr=(nn + 1, np.int32), nsup=(P, np.int32),
+                     sidx=((P, MAXS), np.int32), S=((P, MAXS), np.float64),
+                     dS=((P, MAXS, 3), np.float64), row_ptr=(nd + 1, np.int32),
+                     col=(nz, np.int32), ghost=(nz, np.float64), bcmask=(nd, np.int32),
+                     populated=(nl, np.int32), ghost_faces=((info["nghost"], 4), np.int32))
+        if what in ("cidx", "cw"):
+            ncon = int(self.export("cptr")[-1])
+            shape, dt = ncon, (np.int32 if what == "cidx" else np.float64)
+        else:
+            shape, dt = sizes[what]
+        out = np.zeros(shape, dtype=dt)
+        if out.size:
+            self.ctx.check(lib().mpm_mesh_export(self.h, EXPORT[what],
+                                                 out.ctypes.data_as(C.c_void_p), out.nbytes))
+        return out
+
+    def free(self):
+        if self.h:
+            lib().mpm_mesh_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def octree_build(ctx, cfg, points, body_z=None, nosplit=False, mesh=None):
+    """mpm_octree_build: adapt, split, nodes, basis, pattern, ghost for the body pose."""
+    s = points.struct()
+    h = C.c_void_p(mesh.h.value if isinstance(mesh.h, C.c_void_p) else mesh.h) if mesh else C.c_void_p()
+    st = lib().mpm_octree_build(ctx.h, C.byref(domain(cfg)), C.byref(rigid(cfg, body_z)),
+                                C.byref(adapt(cfg)), C.byref(material(cfg)), C.byref(s),
+                                1 if nosplit else 0, C.byref(h))
+    points.count = s.count
+    if mesh is None and h.value:
+        mesh = Mesh(ctx, h)
+    ctx.check(st)
+    return mesh
+
+
+def assemble(ctx, mesh, cfg, du, load=1.0, precision=FP64, tangent=True, body_z=None):
+    """mpm_assemble: residual R (and the tangent values) at the increment du."""
+    info = mesh.info()
+    nd, nz = info["ndof"], info["nnzb"]
+    R = torch.empty(3 * nd, dtype=torch.float64, device=du.device)
+    K = None
+    if tangent:
+        K = torch.empty(9 * max(nz, 1), dtype=torch.float32 if precision == MIXED else torch.float64,
+                        device=du.device)
+    reac = (C.c_double * 3)()
+    norms = (C.c_double * 2)()
+    st = lib().mpm_assemble(ctx.h, mesh.h, C.byref(material(cfg)), C.byref(rigid(cfg, body_z)),
+                            _p(du), load, precision, _p(R), _p(K), reac, norms)
+    ctx.check(st)
+    return dict(R=R, K=K, reaction=np.array(reac[:]), fint_norm=norms[0], fextc_norm=norms[1])
+
+
+def solve(ctx, mesh, cfg, K, rhs, precision=FP64, tol=1e-10, maxit=20000, method=0,
+          inner_tol=1e-4):
+    """mpm_solve: block-Jacobi PCG / BiCGStab (FP32 inner + FP64 refinement when mixed)."""
+    x = torch.empty_like(rhs)
+    sp = SolveParams(method, precision, tol, maxit, inner_tol)
+    ss = SolveStats()
+    st = lib().mpm_solve(ctx.h, mesh.h, C.byref(material(cfg)), _p(K), _p(rhs), _p(x), C.byref(sp),
+                         C.byref(ss))
+    stats = dict(iterations=ss.iterations, refinements=ss.refinements, status=ss.status,
+                 relres=ss.relres)
+    ctx.check(st)
+    return x, stats
+
+
+def step(ctx, cfg, points, body_z=None, load=1.0, tol=1e-8, maxit=30, lin_tol=1e-8,
+         lin_maxit=20000, precision=FP64, method=0, inner_tol=1e-4, check=True):
+    """mpm_step: one quasi-static load step; returns the statistics."""
+    s = points.struct()
+    sp = StepParams(load, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol))
+    ss = StepStats()
+    st = lib().mpm_step(ctx.h, C.byref(domain(cfg)), C.byref(rigid(cfg, body_z)), C.byref(adapt(cfg)),
+                        C.byref(material(cfg)), C.byref(s), C.byref(sp), C.byref(ss))
+    points.count = s.count
+    out = dict(status=st, newton_its=ss.newton_its, lin_its=ss.lin_its, npts=ss.npts, ndof=ss.ndof,
+               nnzb=ss.nnzb, res_hist=np.array(ss.res_hist[: ss.newton_its + 1]),
+               eta_hist=np.array(ss.eta_hist[: ss.newton_its]), reaction=np.array(ss.reaction[:]),
+               ms_build=ss.ms_build, ms_assemble=ss.ms_assemble, ms_solve=ss.ms_solve,
+               ms_update=ss.ms_update)
+    if check:
+        ctx.check(st)
+    return out
+
+
+def blocks_from_sliced(values, row_ptr):
+    """Row-sliced block values (layout of include/mpm.h) -> array [nnzb, 3, 3] (host)."""
+    v = np.asarray(values, dtype=np.float64)
+    rp = np.asarray(row_ptr, dtype=np.int64)
+    nz = int(rp[-1])
+    nb = np.diff(rp)
+    row = np.repeat(np.arange(len(nb)), nb)
+    k = np.arange(nz) - rp[row]
+    out = np.empty((nz, 9))
+    for e in range(9):
+        out[:, e] = v[9 * rp[row] + e * nb[row] + k]
+    return out.reshape(nz, 3, 3)
