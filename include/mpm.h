@@ -149,6 +149,8 @@ const char* mpm_last_error(const mpm_ctx* ctx);
 int mpm_octree_build(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body,
                      const mpm_adapt* ad, const mpm_material* mat, mpm_points* pts, int flags,
                      mpm_mesh** mesh);
+/* Frees a mesh early.  Meshes still alive when their context is destroyed are
+ * freed by mpm_destroy; a mesh must not be used or freed after that. */
 int mpm_mesh_free(mpm_mesh* mesh);
 /* counts of the mesh (host) */
 int mpm_mesh_counts(const mpm_mesh* mesh, mpm_mesh_info* info);

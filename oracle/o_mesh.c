@@ -255,6 +255,12 @@ int o_body_sdf(const o_params* p, const double* x, double* phi, double* n, doubl
     double ca = cos(p->body_alpha), sa = sin(p->body_alpha), f;
     if (z <= p->body_z + hc) {
       *phi = rho * ca - (z - p->body_z) * sa;
+      if (axis) {
+        /* on the axis the closest points form a circle: take the mean of their
+         * normals, (0, 0, -sin alpha), and no curvature term (reading) */
+        n[2] = -sa;
+        return 1;
+      }
       n[0] = ca * ux;
       n[1] = ca * uy;
       n[2] = -sa;

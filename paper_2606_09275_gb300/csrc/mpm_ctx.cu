@@ -97,6 +97,11 @@ extern "C" int mpm_destroy(mpm_ctx* c) {
     mesh_release(c->step_mesh);
     delete c->step_mesh;
   }
+  for (mpm_mesh* m : c->meshes) {
+    mesh_release(m);
+    delete m;
+  }
+  c->meshes.clear();
   free_buf(c, c->cub_tmp);
   for (auto& b : c->tmp) free_buf(c, b);
   for (auto& b : c->v) free_buf(c, b);
@@ -141,6 +146,7 @@ extern "C" int mpm_octree_build(mpm_ctx* c, const mpm_domain* dom, const mpm_rig
     if (!*mesh) {
       *mesh = new mpm_mesh();
       (*mesh)->ctx = c;
+      c->meshes.push_back(*mesh);
     }
     build_mesh(c, *mesh, *dom, body ? *body : nob, *ad, *mat, pts, flags);
     int st = check_device_error(c, "mpm_octree_build");
@@ -152,6 +158,11 @@ extern "C" int mpm_octree_build(mpm_ctx* c, const mpm_domain* dom, const mpm_rig
 extern "C" int mpm_mesh_free(mpm_mesh* m) {
   if (!m) return MPM_ERR_ARG;
   mpm_ctx* c = m->ctx;
+  for (size_t i = 0; i < c->meshes.size(); ++i)
+    if (c->meshes[i] == m) {
+      c->meshes.erase(c->meshes.begin() + i);
+      break;
+    }
   try {
     mesh_release(m);
     cudaStreamSynchronize(c->stream);

@@ -5,6 +5,7 @@
 
 #include <stdexcept>
 #include <string>
+#include <vector>
 
 #include "mpm.h"
 
@@ -68,6 +69,7 @@ struct mpm_ctx {
   mpm::Buf tmp[8];             // general scratch
   std::string err;
   mpm_mesh* step_mesh = nullptr;
+  std::vector<mpm_mesh*> meshes;  // meshes made by mpm_octree_build, freed with the context
   // Newton / Krylov work vectors (grown on demand)
   mpm::Buf v[24];
 };
@@ -144,7 +146,12 @@ inline void free_buf(mpm_ctx* c, Buf& b) {
   b.bytes = 0;
 }
 
-inline int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }
+// at least one block: an empty grid is a launch error, and every kernel
+// bounds-checks its index
+inline int grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  return (int)(g < 1 ? 1 : g);
+}
 
 // ------------------------------------------------------------------ Morton codes
 
@@ -281,6 +288,11 @@ __device__ inline bool body_sdf(const mpm_rigid& b, double L, const double* x, d
     if (z <= b.z + hc) {
       double ca = cos(b.alpha), sa = sin(b.alpha);
       *phi = rho * ca - (z - b.z) * sa;
+      if (axis) {
+        // on the axis: mean normal of the circle of closest points, no curvature
+        n[2] = -sa;
+        return true;
+      }
       n[0] = ca * ux;
       n[1] = ca * uy;
       n[2] = -sa;

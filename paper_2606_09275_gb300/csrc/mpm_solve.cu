@@ -9,6 +9,7 @@
 //    refinement, the refinement residual accumulated in FP64.
 #include <algorithm>
 #include <cmath>
+#include <string>
 
 #include "mpm_internal.cuh"
 
@@ -222,13 +223,13 @@ __global__ void k_pcg_b(int nd, int k, const int* __restrict__ rp, const int* __
 
 // ---------------------------------------------------------------- BiCGStab
 
-// generic y = K x (+ optional dots a.y into slot, b2.y into slot2).  Skipped once
-// the solve is done, or (check_s) once the half-step residual s has converged.
+// generic y = K x (+ optional dots a.y into slot and y.y into slot2).  Skipped
+// once the solve is done, or (check_s) once the half-step residual s has converged.
 template <class T>
 __global__ void k_spmv_dot(int nd, const int* __restrict__ rp, const int* __restrict__ col,
                            const T* __restrict__ K, const double* __restrict__ x, double* y,
                            const double* __restrict__ a, double* slot, double* slot2,
-                           const double* __restrict__ b2, const Scal* sc, int check_s) {
+                           const Scal* sc, int check_s) {
   __shared__ double sh[32];
   if (sc->done || (check_s && sc->a[5] <= sc->thr)) return;
   int r = blockIdx.x * SW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
@@ -241,7 +242,7 @@ __global__ void k_spmv_dot(int nd, const int* __restrict__ rp, const int* __rest
       size_t j = 3 * (size_t)r + lane;
       y[j] = v;
       if (a) p1 = a[j] * v;
-      if (b2) p2 = b2[j] * v;
+      p2 = v * v;
     }
   }
   if (slot) {
@@ -500,11 +501,11 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
       MPM_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
       k_bicg_p<<<vb, 256, 0, st>>>(nd, p, r, v, ph, Dinv, sc_d);
       k_spmv_dot<T><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, ph, v, r0, &sc_d->a[4],
-                                                          nullptr, nullptr, sc_d, 0);
+                                                          nullptr, sc_d, 0);
       k_bicg_s<<<vb, 256, 0, st>>>(nd, r, v, s, shv, Dinv, sc_d);
       k_bicg_check_s<<<vb, 256, 0, st>>>(nd, x, ph, sc_d);
       k_spmv_dot<T><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, shv, t, s, &sc_d->a[6],
-                                                          &sc_d->a[7], t, sc_d, 1);
+                                                          &sc_d->a[7], sc_d, 1);
       k_bicg_x<<<vb, 256, 0, st>>>(nd, x, r, ph, shv, s, t, r0, sc_d, red, red + 1);
       k_bicg_rotate<<<1, 1, 0, st>>>(sc_d, red, red + 1, it + 1);
     }
@@ -546,7 +547,10 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     out->iterations = its;
     out->relres = rel;
     out->status = s;
-    if (s) set_error(c, "Krylov solve did not reach the tolerance");
+    if (s)
+      set_error(c, std::string(method == 1 ? "PCG" : "BiCGStab") + " did not reach the tolerance (" +
+                       std::to_string(its) + " iterations, relative residual " +
+                       std::to_string(rel) + (sc_h->breakdown ? ", breakdown)" : ")"));
     return;
   }
   // mixed: FP32 inner solves inside FP64 iterative refinement
@@ -602,7 +606,10 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   out->iterations = its;
   out->relres = rel;
   out->status = s;
-  if (s) set_error(c, "Krylov solve did not reach the tolerance");
+  if (s)
+    set_error(c, "BiCGStab (FP32 matrix) did not reach the tolerance (" + std::to_string(its) +
+                     " iterations, relative residual " + std::to_string(rel) +
+                     (sc_h->breakdown ? ", breakdown)" : ")"));
 }
 
 }  // namespace mpm

@@ -8,8 +8,8 @@
 namespace mpm {
 namespace {
 
-__global__ void k_axpy_out(int n, double* y, const double* __restrict__ a, double eta,
-                           const double* __restrict__ b) {
+// y = a + eta b (y may alias a)
+__global__ void k_axpy_out(int n, double* y, const double* a, double eta, const double* b) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = a[i] + eta * b[i];
 }

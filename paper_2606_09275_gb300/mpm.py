@@ -5,8 +5,10 @@ kernels.  Device memory is held in torch tensors (passed as raw pointers) and
 work is issued on the current torch CUDA stream.  There is no fallback: if the
 shared library is missing or fails to load, the import raises.
 """
+import atexit
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 import torch
@@ -166,8 +168,18 @@ def _stream():
 
 # ----------------------------------------------------------------- objects
 
+_contexts = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all():
+    for c in list(_contexts):
+        c.close()
+
+
 class Context:
-    """Library context bound to the current torch CUDA stream."""
+    """Library context bound to the current torch CUDA stream.  Meshes made with
+    it are freed before it (explicitly, by close(), or at interpreter exit)."""
 
     def __init__(self, stream=None):
         h = C.c_void_p()
@@ -176,6 +188,8 @@ class Context:
         if st:
             raise MPMError(st, "mpm_create failed")
         self.h = h
+        self.meshes = weakref.WeakSet()
+        _contexts.add(self)
 
     def error(self):
         return lib().mpm_last_error(self.h).decode()
@@ -186,6 +200,8 @@ class Context:
 
     def close(self):
         if self.h:
+            for m in list(self.meshes):
+                m.h = None  # the library frees them with the context
             lib().mpm_destroy(self.h)
             self.h = None
 
@@ -228,6 +244,7 @@ class Points:
 class Mesh:
     def __init__(self, ctx, h):
         self.ctx, self.h = ctx, h
+        ctx.meshes.add(self)
 
     def info(self):
         i = MeshInfo()
@@ -256,9 +273,9 @@ class Mesh:
         return out
 
     def free(self):
-        if self.h:
+        if self.h and self.ctx.h:
             lib().mpm_mesh_free(self.h)
-            self.h = None
+        self.h = None
 
     def __del__(self):
         try:
