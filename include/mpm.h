@@ -207,6 +207,32 @@ int mpm_step(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body, const m
              const mpm_material* mat, mpm_points* pts, const mpm_step_params* prm,
              mpm_step_stats* stats);
 
+/* Measurement hooks (no counterpart in the paper; they serve the benchmark):
+ * CUDA events recorded on the context stream around every launch of the
+ * tracked kernel classes below, and a count of all kernel launches made by
+ * the library.  mpm_profile(ctx, 1) clears the totals and starts recording,
+ * mpm_profile(ctx, 0) stops; mpm_profile_read synchronises the stream and
+ * returns, per class, the launches and the summed milliseconds (host arrays
+ * of MPM_PROF_NCLASS entries). */
+enum {
+  MPM_PROF_PCG_UPDATE = 0,   /* PCG vector update + preconditioner + dots       */
+  MPM_PROF_PCG_SPMV = 1,     /* PCG SpMV fused with the direction update        */
+  MPM_PROF_TANGENT = 2,      /* row-gather tangent assembly                     */
+  MPM_PROF_CONSTITUTIVE = 3, /* per-point return map (+ spatial tangent)        */
+  MPM_PROF_KINEMATICS = 4,   /* per-point dF                                     */
+  MPM_PROF_FORCE = 5,        /* internal force scatter                           */
+  MPM_PROF_BASIS = 6,        /* discrete GIMP basis                              */
+  MPM_PROF_RESIDUAL = 7,     /* residual rows (ghost term, gravity)              */
+  MPM_PROF_CONTACT = 8,      /* penalty contact                                  */
+  MPM_PROF_BICG_SPMV = 9,    /* BiCGStab SpMV                                    */
+  MPM_PROF_REFINE = 10,      /* FP64 refinement residual                         */
+  MPM_PROF_PATTERN = 11,     /* block pattern rows                               */
+  MPM_PROF_NCLASS = 12
+};
+int mpm_profile(mpm_ctx* ctx, int enable);
+int mpm_profile_read(mpm_ctx* ctx, long long* launches, double* ms);
+int mpm_launch_count(const mpm_ctx* ctx, long long* launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -541,8 +541,8 @@ Law make_law(const mpm_material& mat) {
 double norm_free(mpm_ctx* c, const mpm_mesh* m, const double* R) {
   double* slot = c->d_red + 16;
   MPM_CUDA(cudaMemsetAsync(slot, 0, 3 * sizeof(double), c->stream));
-  k_norms<<<4 * 152, 256, 0, c->stream>>>(3 * m->ndof, R, nullptr, nullptr, nullptr, 0.0,
-                                          ptr<int>(m->dof_mask), slot);
+  MPM_LAUNCH(k_norms<<<4 * 152, 256, 0, c->stream>>>(3 * m->ndof, R, nullptr, nullptr, nullptr, 0.0,
+                                          ptr<int>(m->dof_mask), slot));
   MPM_CUDA(cudaMemcpyAsync(c->h_red + 16, slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   MPM_CUDA(cudaStreamSynchronize(c->stream));
   return sqrt(c->h_red[16]);
@@ -561,78 +561,78 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
   const int* nsup = ptr<int>(m->nsup);
   const int* sidx = ptr<int>(m->sidx);
   const double* dS = ptr<double>(m->dS);
-  k_kinematics<<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, du, dF);
+  MPM_LAUNCH_P(MPM_PROF_KINEMATICS, k_kinematics<<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, du, dF));
   bool mixed = precision == MPM_MIXED;
   size_t asz = mixed ? sizeof(float) : sizeof(double);
   void* Aalg = K ? grow_bytes(c, m->Aalg, 81 * (size_t)P * asz) : nullptr;
   void* gx = K ? grow_bytes(c, m->gx, 3 * (size_t)P * MAXS * asz) : nullptr;
   if (!K)
-    k_constitutive<false, double><<<grid_for(P, 128), 128, 0, st>>>(
+    MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<false, double><<<grid_for(P, 128), 128, 0, st>>>(
         P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv, nullptr,
-        c->d_err);
+        c->d_err));
   else if (mixed)
-    k_constitutive<true, float><<<grid_for(P, 128), 128, 0, st>>>(
+    MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<true, float><<<grid_for(P, 128), 128, 0, st>>>(
         P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv,
-        (float*)Aalg, c->d_err);
+        (float*)Aalg, c->d_err));
   else
-    k_constitutive<true, double><<<grid_for(P, 128), 128, 0, st>>>(
+    MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<true, double><<<grid_for(P, 128), 128, 0, st>>>(
         P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv,
-        (double*)Aalg, c->d_err);
+        (double*)Aalg, c->d_err));
   double* fint = grow<double>(c, c->v[0], 3 * (size_t)nd);
   double* fc = grow<double>(c, c->v[1], 3 * (size_t)nd);
   MPM_CUDA(cudaMemsetAsync(fint, 0, sizeof(double) * 3 * nd, st));
   MPM_CUDA(cudaMemsetAsync(fc, 0, sizeof(double) * 3 * nd, st));
   const double* V0 = ptr<double>(m->pV0);
   if (!K)
-    k_force<double, false><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
-                                                           nullptr);
+    MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<double, false><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
+                                                           nullptr));
   else if (mixed)
-    k_force<float, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
-                                                         (float*)gx);
+    MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<float, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
+                                                         (float*)gx));
   else
-    k_force<double, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
-                                                          (double*)gx);
+    MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<double, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
+                                                          (double*)gx));
   const int* rp = ptr<int>(m->row_ptr);
   const int* col = ptr<int>(m->col);
-  k_residual_rows<<<grid_for(nd, 8), 256, 0, st>>>(nd, load, rp, col, ptr<double>(m->kg), du, fint,
-                                                   ptr<double>(m->fext), R);
+  MPM_LAUNCH_P(MPM_PROF_RESIDUAL, k_residual_rows<<<grid_for(nd, 8), 256, 0, st>>>(nd, load, rp, col, ptr<double>(m->kg), du, fint,
+                                                   ptr<double>(m->fext), R));
   if (K) {
     if (mixed)
-      k_tangent_rows<float><<<grid_for(nd, TW), 32 * TW, 0, st>>>(
+      MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<float><<<grid_for(nd, TW), 32 * TW, 0, st>>>(
           nd, P, rp, col, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
           (const float*)gx, (const float*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
-          (float*)K, c->d_err);
+          (float*)K, c->d_err));
     else
-      k_tangent_rows<double><<<grid_for(nd, TW), 32 * TW, 0, st>>>(
+      MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<double><<<grid_for(nd, TW), 32 * TW, 0, st>>>(
           nd, P, rp, col, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
           (const double*)gx, (const double*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
-          (double*)K, c->d_err);
+          (double*)K, c->d_err));
   }
   double* reac = c->d_red + 20;
   MPM_CUDA(cudaMemsetAsync(reac, 0, 3 * sizeof(double), st));
   if (m->ncand && mat.contact_on && body.kind != 0) {
     int n8 = 8 * m->ncand;
     if (!K)
-      k_contact<double, false><<<grid_for(n8, 128), 128, 0, st>>>(
+      MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<double, false><<<grid_for(n8, 128), 128, 0, st>>>(
           n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
           ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
-          col, ptr<int>(m->dof_mask), (double*)nullptr);
+          col, ptr<int>(m->dof_mask), (double*)nullptr));
     else if (mixed)
-      k_contact<float, true><<<grid_for(n8, 128), 128, 0, st>>>(
+      MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<float, true><<<grid_for(n8, 128), 128, 0, st>>>(
           n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
           ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
-          col, ptr<int>(m->dof_mask), (float*)K);
+          col, ptr<int>(m->dof_mask), (float*)K));
     else
-      k_contact<double, true><<<grid_for(n8, 128), 128, 0, st>>>(
+      MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<double, true><<<grid_for(n8, 128), 128, 0, st>>>(
           n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
           ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
-          col, ptr<int>(m->dof_mask), (double*)K);
+          col, ptr<int>(m->dof_mask), (double*)K));
   }
   if (want_norms) {
     double* slot = c->d_red + 16;
     MPM_CUDA(cudaMemsetAsync(slot, 0, 3 * sizeof(double), st));
-    k_norms<<<4 * 152, 256, 0, st>>>(3 * nd, R, fint, ptr<double>(m->fext), fc, load,
-                                     ptr<int>(m->dof_mask), slot);
+    MPM_LAUNCH(k_norms<<<4 * 152, 256, 0, st>>>(3 * nd, R, fint, ptr<double>(m->fext), fc, load,
+                                     ptr<int>(m->dof_mask), slot));
     MPM_CUDA(cudaMemcpyAsync(c->h_red + 16, slot, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
     out->fint_norm = sqrt(c->h_red[17]);
@@ -700,10 +700,10 @@ void point_update(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const
                   mpm_points* pts) {
   mpm_mesh* m = const_cast<mpm_mesh*>(mc);
   int P = m->np;
-  k_point_update<<<grid_for(P, 128), 128, 0, c->stream>>>(
+  MPM_LAUNCH(k_point_update<<<grid_for(P, 128), 128, 0, c->stream>>>(
       P, make_law(mat), ptr<int>(m->perm), ptr<int>(m->nsup), ptr<int>(m->sidx), ptr<double>(m->S),
       ptr<double>(m->dS), du, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe),
-      ptr<double>(m->pF), ptr<double>(m->px), ptr<double>(m->pl0), *pts, c->d_err);
+      ptr<double>(m->pF), ptr<double>(m->px), ptr<double>(m->pl0), *pts, c->d_err));
 }
 
 }  // namespace mpm

@@ -1088,14 +1088,14 @@ void tree_refine(mpm_ctx* c, mpm_mesh* m, const int* flag) {
   int n = m->nleaf;
   int* cnt = grow<int>(c, c->tmp[0], n);
   int* pos = grow<int>(c, m->scan, n);
-  k_child_count<<<grid_for(n, 256), 256, 0, c->stream>>>(n, flag, cnt);
+  MPM_LAUNCH(k_child_count<<<grid_for(n, 256), 256, 0, c->stream>>>(n, flag, cnt));
   cub_exclusive_sum_int(c, cnt, pos, n);
   int total = read_total(c, pos, cnt, n);
   uint64_t* okey = grow<uint64_t>(c, m->leaf_tmp_key, total);
   int* olev = grow<int>(c, m->leaf_tmp_lev, total);
-  k_refine_write<<<grid_for(n, 256), 256, 0, c->stream>>>(n, ptr<uint64_t>(m->leaf_key),
+  MPM_LAUNCH(k_refine_write<<<grid_for(n, 256), 256, 0, c->stream>>>(n, ptr<uint64_t>(m->leaf_key),
                                                           ptr<int>(m->leaf_lev), flag, pos, m->g.D,
-                                                          okey, olev);
+                                                          okey, olev));
   std::swap(m->leaf_key, m->leaf_tmp_key);
   std::swap(m->leaf_lev, m->leaf_tmp_lev);
   m->nleaf = total;
@@ -1108,8 +1108,8 @@ void tree_balance(mpm_ctx* c, mpm_mesh* m) {
     int* flag = grow<int>(c, m->flag, n);
     MPM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int) * n, c->stream));
     MPM_CUDA(cudaMemsetAsync(any, 0, sizeof(int), c->stream));
-    k_balance_mark<<<grid_for(n, 256), 256, 0, c->stream>>>(n, ptr<uint64_t>(m->leaf_key),
-                                                            ptr<int>(m->leaf_lev), m->g, flag, any);
+    MPM_LAUNCH(k_balance_mark<<<grid_for(n, 256), 256, 0, c->stream>>>(n, ptr<uint64_t>(m->leaf_key),
+                                                            ptr<int>(m->leaf_lev), m->g, flag, any));
     if (!read_flag(c, any)) return;
     tree_refine(c, m, flag);
   }
@@ -1147,8 +1147,8 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     int n = 1 << (3 * dom.depth_min);
     grow<uint64_t>(c, m->leaf_key, n);
     grow<int>(c, m->leaf_lev, n);
-    k_tree_uniform<<<grid_for(n, 256), 256, 0, st>>>(n, 3 * (g.D - dom.depth_min), dom.depth_min,
-                                                     ptr<uint64_t>(m->leaf_key), ptr<int>(m->leaf_lev));
+    MPM_LAUNCH(k_tree_uniform<<<grid_for(n, 256), 256, 0, st>>>(n, 3 * (g.D - dom.depth_min), dom.depth_min,
+                                                     ptr<uint64_t>(m->leaf_key), ptr<int>(m->leaf_lev)));
     m->nleaf = n;
     if (body.kind != 0 && dom.depth_max > dom.depth_min) {
       int* any = (int*)(c->d_red + 8);
@@ -1157,9 +1157,9 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
         int nl = m->nleaf;
         int* flag = grow<int>(c, m->flag, nl);
         MPM_CUDA(cudaMemsetAsync(any, 0, sizeof(int), st));
-        k_mark_refine<<<grid_for(nl, 256), 256, 0, st>>>(nl, ptr<uint64_t>(m->leaf_key),
+        MPM_LAUNCH(k_mark_refine<<<grid_for(nl, 256), 256, 0, st>>>(nl, ptr<uint64_t>(m->leaf_key),
                                                          ptr<int>(m->leaf_lev), g, body, ad.dx_region,
-                                                         dom.depth_max, flag, any);
+                                                         dom.depth_max, flag, any));
         if (!read_flag(c, any)) {
           settled = true;
           break;
@@ -1180,8 +1180,8 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
       int P = pts->count;
       int* flag = grow<int>(c, c->tmp[1], P);
       int* rank = grow<int>(c, c->tmp[2], P);
-      k_split_flag<<<grid_for(P, 128), 128, 0, st>>>(P, pts->x, pts->lp, pts->l0, lkey, llev, nl, g,
-                                                     ad.beta, flag, d_err);
+      MPM_LAUNCH(k_split_flag<<<grid_for(P, 128), 128, 0, st>>>(P, pts->x, pts->lp, pts->l0, lkey, llev, nl, g,
+                                                     ad.beta, flag, d_err));
       cub_exclusive_sum_int(c, flag, rank, P);
       int cnt = read_total(c, rank, flag, P);
       if (cnt == 0) break;
@@ -1189,7 +1189,7 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
       if (np > pts->capacity)
         throw CudaError(MPM_ERR_CAPACITY, "GIMP split needs " + std::to_string(np) +
                                               " points, capacity is " + std::to_string(pts->capacity));
-      k_split_write<<<grid_for(P, 128), 128, 0, st>>>(P, flag, rank, *pts);
+      MPM_LAUNCH(k_split_write<<<grid_for(P, 128), 128, 0, st>>>(P, flag, rank, *pts));
       pts->count = (int)np;
       if (round == 31) throw CudaError(MPM_ERR_SUPPORT, "GIMP split did not settle");
     }
@@ -1201,27 +1201,27 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
   {
     uint64_t* ck = grow<uint64_t>(c, c->tmp[3], 8 * (size_t)nl);
     uint64_t* alt = grow<uint64_t>(c, c->tmp[4], 8 * (size_t)nl);
-    k_corner_keys<<<grid_for(nl, 256), 256, 0, st>>>(nl, lkey, llev, g.D, ck);
+    MPM_LAUNCH(k_corner_keys<<<grid_for(nl, 256), 256, 0, st>>>(nl, lkey, llev, g.D, ck));
     cub_sort_u64(c, ck, alt, 8 * nl, 3 * (g.D + 1));
     uint64_t* nkey = grow<uint64_t>(c, m->node_key, 8 * (size_t)nl);
     int nn = cub_unique_u64(c, ck, nkey, 8 * nl);
     m->nnode = nn;
     int* corner = grow<int>(c, m->corner, 8 * (size_t)nl);
-    k_corner_ids<<<grid_for(nl, 256), 256, 0, st>>>(nl, lkey, llev, g.D, nkey, nn, corner);
+    MPM_LAUNCH(k_corner_ids<<<grid_for(nl, 256), 256, 0, st>>>(nl, lkey, llev, g.D, nkey, nn, corner));
     int* hang = grow<int>(c, m->hang, nn);
     int* owner = grow<int>(c, m->owner, nn);
-    k_hang<<<grid_for(nn, 256), 256, 0, st>>>(nn, nkey, lkey, llev, nl, g, hang, owner);
+    MPM_LAUNCH(k_hang<<<grid_for(nn, 256), 256, 0, st>>>(nn, nkey, lkey, llev, nl, g, hang, owner));
     NodeView v{nkey, lkey, llev, corner, hang, owner, g.D};
     int* cnt = grow<int>(c, c->tmp[0], nn + 1);
     int* cptr = grow<int>(c, m->cptr, nn + 1);
-    k_con_count<<<grid_for(nn, 128), 128, 0, st>>>(nn, v, cnt, d_err);
+    MPM_LAUNCH(k_con_count<<<grid_for(nn, 128), 128, 0, st>>>(nn, v, cnt, d_err));
     MPM_CUDA(cudaMemsetAsync(cnt + nn, 0, sizeof(int), st));
     cub_exclusive_sum_int(c, cnt, cptr, nn + 1);
     int ncon = read_total(c, cptr, cnt, nn + 1);
     m->ncon = ncon;
     int* cidx = grow<int>(c, m->cidx, ncon);
     double* cw = grow<double>(c, m->cw, ncon);
-    k_con_fill<<<grid_for(nn, 128), 128, 0, st>>>(nn, v, cptr, cidx, cw);
+    MPM_LAUNCH(k_con_fill<<<grid_for(nn, 128), 128, 0, st>>>(nn, v, cptr, cidx, cw));
     int st2 = check_device_error(c, "node constraints");
     if (st2) throw CudaError(st2, c->err);
   }
@@ -1237,13 +1237,13 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     int* idx = grow<int>(c, c->tmp[2], P);
     int* perm = grow<int>(c, m->perm, P);
     int* pcell = grow<int>(c, m->pcell, P);
-    k_point_cell<<<grid_for(P, 256), 256, 0, st>>>(P, pts->x, g, lkey, nl, cell, idx);
+    MPM_LAUNCH(k_point_cell<<<grid_for(P, 256), 256, 0, st>>>(P, pts->x, g, lkey, nl, cell, idx));
     cub_sort_pairs_int(c, cell, pcell, idx, perm, P, bits_for(nl));
-    k_gather_points<<<grid_for(P, 256), 256, 0, st>>>(
+    MPM_LAUNCH(k_gather_points<<<grid_for(P, 256), 256, 0, st>>>(
         P, perm, *pts, grow<double>(c, m->px, 3 * (size_t)P), grow<double>(c, m->plp, 3 * (size_t)P),
         grow<double>(c, m->pl0, 3 * (size_t)P), grow<double>(c, m->pF, 9 * (size_t)P),
         grow<double>(c, m->pbe, 6 * (size_t)P), grow<double>(c, m->pV0, P),
-        grow<double>(c, m->pmass, P), grow<double>(c, m->pE, P), grow<double>(c, m->pys, P));
+        grow<double>(c, m->pmass, P), grow<double>(c, m->pE, P), grow<double>(c, m->pys, P)));
   }
 
   // ---- a4: discrete GIMP basis
@@ -1255,10 +1255,10 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
   double* betaK = grow<double>(c, m->betaK, nl);
   MPM_CUDA(cudaMemsetAsync(pop, 0, sizeof(int) * nl, st));
   MPM_CUDA(cudaMemsetAsync(betaK, 0, sizeof(double) * nl, st));
-  k_basis<<<grid_for(P, BW), 32 * BW, 0, st>>>(P, g, ptr<double>(m->px), ptr<double>(m->plp),
+  MPM_LAUNCH_P(MPM_PROF_BASIS, k_basis<<<grid_for(P, BW), 32 * BW, 0, st>>>(P, g, ptr<double>(m->px), ptr<double>(m->plp),
                                                ptr<double>(m->pE), lkey, llev, nl, corner, cptr, cidx,
                                                cw, nsup, sidx, S, dS, pop,
-                                               (unsigned long long*)betaK, d_err);
+                                               (unsigned long long*)betaK, d_err));
   {
     int e = check_device_error(c, "GIMP basis");
     if (e) throw CudaError(e, c->err);
@@ -1268,14 +1268,14 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     int* active = grow<int>(c, c->tmp[0], nn);
     int* pos = grow<int>(c, c->tmp[1], nn);
     MPM_CUDA(cudaMemsetAsync(active, 0, sizeof(int) * nn, st));
-    k_mark_active<<<grid_for((long long)P * MAXS, 256), 256, 0, st>>>(P, nsup, sidx, active);
+    MPM_LAUNCH(k_mark_active<<<grid_for((long long)P * MAXS, 256), 256, 0, st>>>(P, nsup, sidx, active));
     cub_exclusive_sum_int(c, active, pos, nn);
     int nd = read_total(c, pos, active, nn);
     m->ndof = nd;
     int* node_dof = grow<int>(c, m->node_dof, nn);
     int* dof_node = grow<int>(c, m->dof_node, nd);
-    k_number_dofs<<<grid_for(nn, 256), 256, 0, st>>>(nn, active, pos, node_dof, dof_node);
-    k_sidx_to_dof<<<grid_for((long long)P * MAXS, 256), 256, 0, st>>>(P, nsup, node_dof, sidx);
+    MPM_LAUNCH(k_number_dofs<<<grid_for(nn, 256), 256, 0, st>>>(nn, active, pos, node_dof, dof_node));
+    MPM_LAUNCH(k_sidx_to_dof<<<grid_for((long long)P * MAXS, 256), 256, 0, st>>>(P, nsup, node_dof, sidx));
     Planes pl{};
     pl.n = dom.nbc;
     for (int b = 0; b < dom.nbc; ++b) {
@@ -1283,8 +1283,8 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
       pl.pos[b] = (int)floor(dom.bc_pos[b] * g.scale + 0.5);
       pl.mask[b] = dom.bc_mask[b];
     }
-    k_dof_mask<<<grid_for(nd, 256), 256, 0, st>>>(nd, dof_node, ptr<uint64_t>(m->node_key), pl,
-                                                  grow<int>(c, m->dof_mask, nd));
+    MPM_LAUNCH(k_dof_mask<<<grid_for(nd, 256), 256, 0, st>>>(nd, dof_node, ptr<uint64_t>(m->node_key), pl,
+                                                  grow<int>(c, m->dof_mask, nd)));
   }
   int nd = m->ndof;
   const int* node_dof = ptr<int>(m->node_dof);
@@ -1293,18 +1293,18 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
   int nf = 0;
   {
     int* isB = grow<int>(c, m->isB, nl);
-    k_boundary_elements<<<grid_for(nl, 256), 256, 0, st>>>(nl, lkey, llev, g, pop, isB);
+    MPM_LAUNCH(k_boundary_elements<<<grid_for(nl, 256), 256, 0, st>>>(nl, lkey, llev, g, pop, isB));
     if (mat.ghost_on) {
       int* flag = grow<int>(c, c->tmp[0], 6 * (size_t)nl);
       int* pos = grow<int>(c, c->tmp[1], 6 * (size_t)nl);
-      k_ghost_face_flag<<<grid_for(6LL * nl, 256), 256, 0, st>>>(nl, lkey, llev, g, pop, isB, flag);
+      MPM_LAUNCH(k_ghost_face_flag<<<grid_for(6LL * nl, 256), 256, 0, st>>>(nl, lkey, llev, g, pop, isB, flag));
       cub_exclusive_sum_int(c, flag, pos, 6 * nl);
       nf = read_total(c, pos, flag, 6 * nl);
       int* face = grow<int>(c, m->gface, 4 * (size_t)nf);
-      k_ghost_face_write<<<grid_for(6LL * nl, 256), 256, 0, st>>>(nl, lkey, llev, g, flag, pos, face);
-      k_ghost_face_dofs<<<grid_for(nf, 128), 128, 0, st>>>(nf, face, corner, cptr, cidx, node_dof,
+      MPM_LAUNCH(k_ghost_face_write<<<grid_for(6LL * nl, 256), 256, 0, st>>>(nl, lkey, llev, g, flag, pos, face));
+      MPM_LAUNCH(k_ghost_face_dofs<<<grid_for(nf, 128), 128, 0, st>>>(nf, face, corner, cptr, cidx, node_dof,
                                                           grow<int>(c, m->gdof, (size_t)nf * MAXG),
-                                                          grow<int>(c, m->gn, nf), d_err);
+                                                          grow<int>(c, m->gn, nf), d_err));
     }
     m->nghost = nf;
   }
@@ -1319,24 +1319,24 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     long long total = npt + (long long)nf * MAXG;
     uint64_t* keys = grow<uint64_t>(c, m->src_key, total);
     uint64_t* alt = grow<uint64_t>(c, c->tmp[3], total);
-    k_src_keys_points<<<grid_for((long long)P * MAXS, 256), 256, 0, st>>>(P, nsup, sidx, off, keys);
+    MPM_LAUNCH(k_src_keys_points<<<grid_for((long long)P * MAXS, 256), 256, 0, st>>>(P, nsup, sidx, off, keys));
     if (nf) {
       // unused face slots keep an out-of-range row so that they sort last
       MPM_CUDA(cudaMemsetAsync(keys + npt, 0xff, sizeof(uint64_t) * (size_t)nf * MAXG, st));
-      k_src_keys_faces<<<grid_for((long long)nf * MAXG, 256), 256, 0, st>>>(
-          nf, P, ptr<int>(m->gn), ptr<int>(m->gdof), npt, keys);
+      MPM_LAUNCH(k_src_keys_faces<<<grid_for((long long)nf * MAXG, 256), 256, 0, st>>>(
+          nf, P, ptr<int>(m->gn), ptr<int>(m->gdof), npt, keys));
     }
     cub_sort_u64(c, keys, alt, (int)total, 64);
     long long* sptr = grow<long long>(c, m->src_ptr, nd + 1);
     MPM_CUDA(cudaMemsetAsync(sptr, 0, sizeof(long long) * (nd + 1), st));
-    k_src_ptr<<<grid_for(total, 256), 256, 0, st>>>(total, keys, nd, sptr);
+    MPM_LAUNCH(k_src_ptr<<<grid_for(total, 256), 256, 0, st>>>(total, keys, nd, sptr));
     m->nsrc = total;
     int* rowcnt = grow<int>(c, m->rowcnt, nd + 1);
     int* rp = grow<int>(c, m->row_ptr, nd + 1);
     MPM_CUDA(cudaMemsetAsync(rowcnt + nd, 0, sizeof(int), st));
-    k_pattern_rows<<<grid_for(nd, PW), 32 * PW, 0, st>>>(nd, P, 0, sptr, keys, nsup, sidx,
+    MPM_LAUNCH_P(MPM_PROF_PATTERN, k_pattern_rows<<<grid_for(nd, PW), 32 * PW, 0, st>>>(nd, P, 0, sptr, keys, nsup, sidx,
                                                          ptr<int>(m->gn), ptr<int>(m->gdof), rowcnt,
-                                                         nullptr, nullptr, d_err);
+                                                         nullptr, nullptr, d_err));
     cub_exclusive_sum_int(c, rowcnt, rp, nd + 1);
     int nnzb = read_total(c, rp, rowcnt, nd + 1);
     {
@@ -1345,9 +1345,9 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     }
     m->nnzb = nnzb;
     int* col = grow<int>(c, m->col, nnzb);
-    k_pattern_rows<<<grid_for(nd, PW), 32 * PW, 0, st>>>(nd, P, 1, sptr, keys, nsup, sidx,
+    MPM_LAUNCH_P(MPM_PROF_PATTERN, k_pattern_rows<<<grid_for(nd, PW), 32 * PW, 0, st>>>(nd, P, 1, sptr, keys, nsup, sidx,
                                                          ptr<int>(m->gn), ptr<int>(m->gdof), rowcnt,
-                                                         rp, col, d_err);
+                                                         rp, col, d_err));
     // longest row (for the solver's launch shapes)
     std::vector<int> h(nd + 1);
     MPM_CUDA(cudaMemcpyAsync(h.data(), rp, sizeof(int) * (nd + 1), cudaMemcpyDeviceToHost, st));
@@ -1364,9 +1364,9 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     double* kg = grow<double>(c, m->kg, m->nnzb);
     MPM_CUDA(cudaMemsetAsync(kg, 0, sizeof(double) * m->nnzb, st));
     if (nf)
-      k_ghost_matrix<<<grid_for(nf, 4), 128, 0, st>>>(nf, g, mat.kappa, ptr<int>(m->gface), lkey, llev,
+      MPM_LAUNCH(k_ghost_matrix<<<grid_for(nf, 4), 128, 0, st>>>(nf, g, mat.kappa, ptr<int>(m->gface), lkey, llev,
                                                       betaK, ptr<int>(m->gdof), ptr<int>(m->gn),
-                                                      corner, cptr, cidx, cw, node_dof, rp, col, kg);
+                                                      corner, cptr, cidx, cw, node_dof, rp, col, kg));
   }
 
   // ---- gravity force at load 1: f_ext,v = sum_p S_vp m_p g
@@ -1374,8 +1374,8 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     double* fext = grow<double>(c, m->fext, 3 * (size_t)nd);
     MPM_CUDA(cudaMemsetAsync(fext, 0, sizeof(double) * 3 * nd, st));
     if (mat.g[0] != 0.0 || mat.g[1] != 0.0 || mat.g[2] != 0.0)
-      k_fext<<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, S, ptr<double>(m->pmass), mat.g[0],
-                                             mat.g[1], mat.g[2], fext);
+      MPM_LAUNCH(k_fext<<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, S, ptr<double>(m->pmass), mat.g[0],
+                                             mat.g[1], mat.g[2], fext));
   }
 
   // ---- contact candidates: domains with a corner within 4 finest cells of the body
@@ -1383,20 +1383,20 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
   if (mat.contact_on && body.kind != 0) {
     int* flag = grow<int>(c, c->tmp[0], P);
     int* pos = grow<int>(c, c->tmp[1], P);
-    k_cand_flag<<<grid_for(P, 256), 256, 0, st>>>(P, ptr<double>(m->px), ptr<double>(m->plp), body,
-                                                  4.0 * g.unit, flag);
+    MPM_LAUNCH(k_cand_flag<<<grid_for(P, 256), 256, 0, st>>>(P, ptr<double>(m->px), ptr<double>(m->plp), body,
+                                                  4.0 * g.unit, flag));
     cub_exclusive_sum_int(c, flag, pos, P);
     int nc = read_total(c, pos, flag, P);
     m->ncand = nc;
     if (nc) {
       int* cand = grow<int>(c, m->cand, nc);
-      k_cand_write<<<grid_for(P, 256), 256, 0, st>>>(P, flag, pos, cand);
-      k_cand_basis<<<grid_for(8LL * nc, 128), 128, 0, st>>>(
+      MPM_LAUNCH(k_cand_write<<<grid_for(P, 256), 256, 0, st>>>(P, flag, pos, cand));
+      MPM_LAUNCH(k_cand_basis<<<grid_for(8LL * nc, 128), 128, 0, st>>>(
           nc, cand, g, ptr<double>(m->px), ptr<double>(m->plp), lkey, llev, nl, corner, cptr, cidx,
           cw, node_dof, grow<int>(c, m->cb_n, 8 * (size_t)nc),
           grow<int>(c, m->cb_idx, 8 * (size_t)nc * MAXCB),
           grow<double>(c, m->cb_phi, 8 * (size_t)nc * MAXCB),
-          grow<double>(c, m->cb_y0, 24 * (size_t)nc), d_err);
+          grow<double>(c, m->cb_y0, 24 * (size_t)nc), d_err));
     }
   }
 

@@ -41,9 +41,63 @@ int check_device_error(mpm_ctx* c, const char* where) {
   return st;
 }
 
+void prof_flush(mpm_ctx* c) {
+  if (c->prof.empty()) return;
+  MPM_CUDA(cudaStreamSynchronize(c->stream));
+  for (ProfEv& e : c->prof) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      c->prof_ms[e.cls] += ms;
+      c->prof_n[e.cls] += 1;
+    }
+    c->evpool.push_back(e.a);
+    c->evpool.push_back(e.b);
+  }
+  c->prof.clear();
+}
+
 }  // namespace mpm
 
 using namespace mpm;
+
+extern "C" int mpm_profile(mpm_ctx* c, int enable) {
+  if (!c) return MPM_ERR_ARG;
+  try {
+    prof_flush(c);
+  } catch (const CudaError& e) {
+    set_error(c, e.what());
+    return e.code;
+  }
+  if (enable) {
+    for (int i = 0; i < MPM_PROF_NCLASS; ++i) {
+      c->prof_ms[i] = 0.0;
+      c->prof_n[i] = 0;
+    }
+  }
+  c->prof_on = enable != 0;
+  return MPM_OK;
+}
+
+extern "C" int mpm_profile_read(mpm_ctx* c, long long* launches, double* ms) {
+  if (!c || !launches || !ms) return MPM_ERR_ARG;
+  try {
+    prof_flush(c);
+  } catch (const CudaError& e) {
+    set_error(c, e.what());
+    return e.code;
+  }
+  for (int i = 0; i < MPM_PROF_NCLASS; ++i) {
+    launches[i] = c->prof_n[i];
+    ms[i] = c->prof_ms[i];
+  }
+  return MPM_OK;
+}
+
+extern "C" int mpm_launch_count(const mpm_ctx* c, long long* n) {
+  if (!c || !n) return MPM_ERR_ARG;
+  *n = c->nlaunch;
+  return MPM_OK;
+}
 
 #define MPM_GUARD(ctx, ...)                                  \
   try {                                                      \
@@ -105,6 +159,11 @@ extern "C" int mpm_destroy(mpm_ctx* c) {
   free_buf(c, c->cub_tmp);
   for (auto& b : c->tmp) free_buf(c, b);
   for (auto& b : c->v) free_buf(c, b);
+  try {
+    prof_flush(c);
+  } catch (...) {
+  }
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->d_err) cudaFreeAsync(c->d_err, c->stream);
   if (c->d_red) cudaFreeAsync(c->d_red, c->stream);
   cudaStreamSynchronize(c->stream);
@@ -240,16 +299,16 @@ extern "C" int mpm_mesh_export(const mpm_mesh* mc, int what, void* dst, size_t b
       case MPM_EXPORT_LEAF_ANCHOR: {
         need = sizeof(int) * 3 * m->nleaf;
         int* o = grow<int>(c, t, 3 * (size_t)m->nleaf);
-        k_export_leaves<<<grid_for(m->nleaf, 256), 256, 0, c->stream>>>(
-            m->nleaf, ptr<uint64_t>(m->leaf_key), ptr<int>(m->leaf_lev), nullptr, o);
+        MPM_LAUNCH(k_export_leaves<<<grid_for(m->nleaf, 256), 256, 0, c->stream>>>(
+            m->nleaf, ptr<uint64_t>(m->leaf_key), ptr<int>(m->leaf_lev), nullptr, o));
         src = o;
         break;
       }
       case MPM_EXPORT_NODE_COORD: {
         need = sizeof(int) * 3 * m->nnode;
         int* o = grow<int>(c, t, 3 * (size_t)m->nnode);
-        k_export_node_coord<<<grid_for(m->nnode, 256), 256, 0, c->stream>>>(
-            m->nnode, ptr<uint64_t>(m->node_key), o);
+        MPM_LAUNCH(k_export_node_coord<<<grid_for(m->nnode, 256), 256, 0, c->stream>>>(
+            m->nnode, ptr<uint64_t>(m->node_key), o));
         src = o;
         break;
       }
@@ -276,32 +335,32 @@ extern "C" int mpm_mesh_export(const mpm_mesh* mc, int what, void* dst, size_t b
       case MPM_EXPORT_NSUP: {
         need = sizeof(int) * m->np;
         int* o = grow<int>(c, t, m->np);
-        k_unpermute<int><<<grid_for(m->np, 256), 256, 0, c->stream>>>(
-            m->np, 1, ptr<int>(m->perm), ptr<int>(m->nsup), o);
+        MPM_LAUNCH(k_unpermute<int><<<grid_for(m->np, 256), 256, 0, c->stream>>>(
+            m->np, 1, ptr<int>(m->perm), ptr<int>(m->nsup), o));
         src = o;
         break;
       }
       case MPM_EXPORT_SIDX: {
         need = sizeof(int) * (size_t)m->np * MAXS;
         int* o = grow<int>(c, t, (size_t)m->np * MAXS);
-        k_unpermute<int><<<grid_for((long long)m->np * MAXS, 256), 256, 0, c->stream>>>(
-            m->np, MAXS, ptr<int>(m->perm), ptr<int>(m->sidx), o);
+        MPM_LAUNCH(k_unpermute<int><<<grid_for((long long)m->np * MAXS, 256), 256, 0, c->stream>>>(
+            m->np, MAXS, ptr<int>(m->perm), ptr<int>(m->sidx), o));
         src = o;
         break;
       }
       case MPM_EXPORT_S: {
         need = sizeof(double) * (size_t)m->np * MAXS;
         double* o = grow<double>(c, t, (size_t)m->np * MAXS);
-        k_unpermute<double><<<grid_for((long long)m->np * MAXS, 256), 256, 0, c->stream>>>(
-            m->np, MAXS, ptr<int>(m->perm), ptr<double>(m->S), o);
+        MPM_LAUNCH(k_unpermute<double><<<grid_for((long long)m->np * MAXS, 256), 256, 0, c->stream>>>(
+            m->np, MAXS, ptr<int>(m->perm), ptr<double>(m->S), o));
         src = o;
         break;
       }
       case MPM_EXPORT_DS: {
         need = sizeof(double) * (size_t)m->np * MAXS * 3;
         double* o = grow<double>(c, t, (size_t)m->np * MAXS * 3);
-        k_unpermute<double><<<grid_for((long long)m->np * MAXS * 3, 256), 256, 0, c->stream>>>(
-            m->np, MAXS * 3, ptr<int>(m->perm), ptr<double>(m->dS), o);
+        MPM_LAUNCH(k_unpermute<double><<<grid_for((long long)m->np * MAXS * 3, 256), 256, 0, c->stream>>>(
+            m->np, MAXS * 3, ptr<int>(m->perm), ptr<double>(m->dS), o));
         src = o;
         break;
       }

@@ -56,7 +56,28 @@ struct Buf {
   size_t bytes = 0;
 };
 
+struct ProfEv {
+  int cls;
+  cudaEvent_t a, b;
+};
+
 }  // namespace mpm
+
+// every kernel launch of the library goes through these: the launch count is
+// reported by mpm_launch_count; MPM_LAUNCH_P also brackets it with events
+#define MPM_COUNT(ctx) (++(ctx)->nlaunch)
+#define MPM_LAUNCH(...) \
+  do {                  \
+    __VA_ARGS__;        \
+    MPM_COUNT(c);       \
+  } while (0)
+#define MPM_LAUNCH_P(cls, ...) \
+  do {                         \
+    ::mpm::prof_begin(c, cls); \
+    __VA_ARGS__;               \
+    MPM_COUNT(c);              \
+    ::mpm::prof_end(c);        \
+  } while (0)
 
 struct mpm_ctx {
   cudaStream_t stream = nullptr;
@@ -72,6 +93,13 @@ struct mpm_ctx {
   std::vector<mpm_mesh*> meshes;  // meshes made by mpm_octree_build, freed with the context
   // Newton / Krylov work vectors (grown on demand)
   mpm::Buf v[24];
+  // measurement: launch count and optional per-class CUDA-event timing
+  long long nlaunch = 0;
+  bool prof_on = false;
+  std::vector<mpm::ProfEv> prof;
+  std::vector<cudaEvent_t> evpool;
+  double prof_ms[MPM_PROF_NCLASS] = {};
+  long long prof_n[MPM_PROF_NCLASS] = {};
 };
 
 struct mpm_mesh {
@@ -349,6 +377,35 @@ __device__ inline double block_sum(double v, double* sh) {
   }
   __syncthreads();
   return r;
+}
+
+// ------------------------------------------------------------------ event timing
+
+void prof_flush(mpm_ctx* c);
+
+inline cudaEvent_t prof_event(mpm_ctx* c) {
+  if (c->evpool.empty()) {
+    cudaEvent_t e;
+    MPM_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+  cudaEvent_t e = c->evpool.back();
+  c->evpool.pop_back();
+  return e;
+}
+
+// bracket one launch of class `cls` with events on the context stream
+inline void prof_begin(mpm_ctx* c, int cls) {
+  if (!c->prof_on) return;
+  if (c->prof.size() >= 2048) prof_flush(c);
+  ProfEv e{cls, prof_event(c), prof_event(c)};
+  MPM_CUDA(cudaEventRecord(e.a, c->stream));
+  c->prof.push_back(e);
+}
+
+inline void prof_end(mpm_ctx* c) {
+  if (!c->prof_on || c->prof.empty()) return;
+  MPM_CUDA(cudaEventRecord(c->prof.back().b, c->stream));
 }
 
 // ------------------------------------------------------------------ host entry helpers

@@ -418,8 +418,8 @@ int run_pcg(mpm_ctx* c, const mpm_mesh* m, const T* K, const V* Dinv, const doub
   const int* col = ptr<int>(m->col);
   MPM_CUDA(cudaMemsetAsync(sc_d, 0, sizeof(Scal), st));
   int vb = 4 * 152;
-  k_pcg_init<V><<<vb, 256, 0, st>>>(nd, b, ptr<int>(m->dof_mask), Dinv, x, r, z, p, sc_d);
-  k_pcg_q0<T, V><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, p, q, sc_d);
+  MPM_LAUNCH(k_pcg_init<V><<<vb, 256, 0, st>>>(nd, b, ptr<int>(m->dof_mask), Dinv, x, r, z, p, sc_d));
+  MPM_LAUNCH(k_pcg_q0<T, V><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, p, q, sc_d));
   MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
   MPM_CUDA(cudaStreamSynchronize(st));
   double bb = sc_h->bb;
@@ -436,8 +436,8 @@ int run_pcg(mpm_ctx* c, const mpm_mesh* m, const T* K, const V* Dinv, const doub
   while (k < maxit) {
     int kend = std::min(maxit, k + batch);
     for (; k < kend; ++k) {
-      k_pcg_a<V><<<vb, 256, 0, st>>>(nd, k, Dinv, x, r, z, p, q, sc_d);
-      k_pcg_b<T, V><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, k, rp, col, K, z, p, q, sc_d);
+      MPM_LAUNCH_P(MPM_PROF_PCG_UPDATE, k_pcg_a<V><<<vb, 256, 0, st>>>(nd, k, Dinv, x, r, z, p, q, sc_d));
+      MPM_LAUNCH_P(MPM_PROF_PCG_SPMV, k_pcg_b<T, V><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, k, rp, col, K, z, p, q, sc_d));
     }
     MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
@@ -477,8 +477,8 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
   double* red = c->d_red + 40;  // rho1 / rr accumulators of the next iteration
   MPM_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
   // r = r0 = b (free), ||b||^2 via r = b - K*0
-  k_residual64<T><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, x, b, mask, r, &sc_d->bb);
-  k_copy_d<<<grid_for(n3, 256), 256, 0, st>>>(n3, r0, r);
+  MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<T><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, x, b, mask, r, &sc_d->bb));
+  MPM_LAUNCH(k_copy_d<<<grid_for(n3, 256), 256, 0, st>>>(n3, r0, r));
   MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
   MPM_CUDA(cudaStreamSynchronize(st));
   double bb = sc_h->bb;
@@ -499,15 +499,15 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
     int iend = std::min(maxit, it + batch);
     for (; it < iend; ++it) {
       MPM_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
-      k_bicg_p<<<vb, 256, 0, st>>>(nd, p, r, v, ph, Dinv, sc_d);
-      k_spmv_dot<T><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, ph, v, r0, &sc_d->a[4],
-                                                          nullptr, sc_d, 0);
-      k_bicg_s<<<vb, 256, 0, st>>>(nd, r, v, s, shv, Dinv, sc_d);
-      k_bicg_check_s<<<vb, 256, 0, st>>>(nd, x, ph, sc_d);
-      k_spmv_dot<T><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, shv, t, s, &sc_d->a[6],
-                                                          &sc_d->a[7], sc_d, 1);
-      k_bicg_x<<<vb, 256, 0, st>>>(nd, x, r, ph, shv, s, t, r0, sc_d, red, red + 1);
-      k_bicg_rotate<<<1, 1, 0, st>>>(sc_d, red, red + 1, it + 1);
+      MPM_LAUNCH(k_bicg_p<<<vb, 256, 0, st>>>(nd, p, r, v, ph, Dinv, sc_d));
+      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, ph, v, r0, &sc_d->a[4],
+                                                          nullptr, sc_d, 0));
+      MPM_LAUNCH(k_bicg_s<<<vb, 256, 0, st>>>(nd, r, v, s, shv, Dinv, sc_d));
+      MPM_LAUNCH(k_bicg_check_s<<<vb, 256, 0, st>>>(nd, x, ph, sc_d));
+      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, shv, t, s, &sc_d->a[6],
+                                                          &sc_d->a[7], sc_d, 1));
+      MPM_LAUNCH(k_bicg_x<<<vb, 256, 0, st>>>(nd, x, r, ph, shv, s, t, r0, sc_d, red, red + 1));
+      MPM_LAUNCH(k_bicg_rotate<<<1, 1, 0, st>>>(sc_d, red, red + 1, it + 1));
     }
     MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
@@ -539,7 +539,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   if (prm.precision == MPM_FP64) {
     const double* Kd = (const double*)K;
     double* Dinv = grow<double>(c, c->v[3], 9 * (size_t)nd);
-    k_block_jacobi<double, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, Kd, Dinv, c->d_err);
+    MPM_LAUNCH(k_block_jacobi<double, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, Kd, Dinv, c->d_err));
     int its = 0;
     double rel = 0.0;
     int s = method == 1 ? run_pcg<double, double>(c, m, Kd, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its)
@@ -561,10 +561,10 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   double* slot = c->d_red + 44;
   if (method == 1) {
     float* Dinv = grow<float>(c, c->v[3], 9 * (size_t)nd);
-    k_block_jacobi<float, float><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, Kf, Dinv, c->d_err);
+    MPM_LAUNCH(k_block_jacobi<float, float><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, Kf, Dinv, c->d_err));
     MPM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n3, st));
     MPM_CUDA(cudaMemsetAsync(slot, 0, sizeof(double), st));
-    k_residual64<float><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, Kf, x, b, ptr<int>(m->dof_mask), r64, slot);
+    MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, Kf, x, b, ptr<int>(m->dof_mask), r64, slot));
     MPM_CUDA(cudaMemcpyAsync(c->h_red + 60, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
     double bb = c->h_red[60], rr = bb;
@@ -583,9 +583,9 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
         status = MPM_ERR_KRYLOV;
         break;
       }
-      k_axpy_f2d<<<grid_for(n3, 256), 256, 0, st>>>(n3, x, d32);
+      MPM_LAUNCH(k_axpy_f2d<<<grid_for(n3, 256), 256, 0, st>>>(n3, x, d32));
       MPM_CUDA(cudaMemsetAsync(slot, 0, sizeof(double), st));
-      k_residual64<float><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, Kf, x, b, ptr<int>(m->dof_mask), r64, slot);
+      MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, Kf, x, b, ptr<int>(m->dof_mask), r64, slot));
       MPM_CUDA(cudaMemcpyAsync(c->h_red + 60, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
       MPM_CUDA(cudaStreamSynchronize(st));
       rr = c->h_red[60];
@@ -599,7 +599,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   }
   // non-symmetric mixed: BiCGStab on the FP32 matrix with FP64 vectors
   double* Dinv = grow<double>(c, c->v[3], 9 * (size_t)nd);
-  k_block_jacobi<float, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, Kf, Dinv, c->d_err);
+  MPM_LAUNCH(k_block_jacobi<float, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, Kf, Dinv, c->d_err));
   int its = 0;
   double rel = 0.0;
   int s = run_bicgstab<float>(c, m, Kf, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);

@@ -85,7 +85,7 @@ extern "C" int mpm_step(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* body
     MPM_CUDA(cudaMemsetAsync(du, 0, sizeof(double) * n3, s));
     AsmOut o{};
     tm.start();
-    assemble(c, m, *mat, bd, du, prm->load, prec, R, K, &o, true);
+    assemble(c, m, *mat, bd, du, prm->load, prec, R, nullptr, &o, true);
     st.ms_assemble += tm.stop();
     status = check_device_error(c, "assembly");
     if (status) throw CudaError(status, c->err);
@@ -101,7 +101,14 @@ extern "C" int mpm_step(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* body
         break;
       }
       if (it == prm->maxit) break;
-      k_neg<<<grid_for(n3, 256), 256, 0, s>>>(n3, rhs, R);
+      // consistent tangent at the current increment (the residual is recomputed
+      // with it and is unchanged)
+      tm.start();
+      assemble(c, m, *mat, bd, du, prm->load, prec, R, K, &o, false);
+      st.ms_assemble += tm.stop();
+      status = check_device_error(c, "tangent assembly");
+      if (status) throw CudaError(status, c->err);
+      MPM_LAUNCH(k_neg<<<grid_for(n3, 256), 256, 0, s>>>(n3, rhs, R));
       mpm_solve_stats ss{};
       tm.start();
       solve(c, m, *mat, K, rhs, dx, prm->lin, &ss);
@@ -113,27 +120,38 @@ extern "C" int mpm_step(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* body
       // line search (Sec. 2.4): eta = 1, else the lowest residual of {0.5, 0.25, 0.1}
       const double etas[4] = {1.0, 0.5, 0.25, 0.1};
       double best = -1.0, beta_ = 1.0;
+      int ibest = 0, ilast = 0;
+      AsmOut obest{};
       tm.start();
       for (int e = 0; e < 4; ++e) {
-        k_axpy_out<<<grid_for(n3, 256), 256, 0, s>>>(n3, trial, du, etas[e], dx);
+        MPM_LAUNCH(k_axpy_out<<<grid_for(n3, 256), 256, 0, s>>>(n3, trial, du, etas[e], dx));
         AsmOut ot{};
         assemble(c, m, *mat, bd, trial, prm->load, prec, Rt, nullptr, &ot, true);
         double r1 = sqrt(c->h_red[16]);
         int es = check_device_error(c, "line search");
         if (es) r1 = INFINITY;
+        ilast = e;
         if (best < 0.0 || r1 < best) {
           best = r1;
           beta_ = etas[e];
+          ibest = e;
+          obest = ot;
         }
         if (e == 0 && r1 < rn) break;
       }
       st.eta_hist[it] = beta_;
-      k_axpy_out<<<grid_for(n3, 256), 256, 0, s>>>(n3, du, du, beta_, dx);
-      assemble(c, m, *mat, bd, du, prm->load, prec, R, K, &o, true);
+      MPM_LAUNCH(k_axpy_out<<<grid_for(n3, 256), 256, 0, s>>>(n3, du, du, beta_, dx));
+      if (ibest == ilast && std::isfinite(best)) {
+        std::swap(R, Rt);  // the accepted trial's residual is the last one computed
+        o = obest;
+        rn = best;
+      } else {
+        assemble(c, m, *mat, bd, du, prm->load, prec, R, nullptr, &o, true);
+        status = check_device_error(c, "assembly");
+        if (status) throw CudaError(status, c->err);
+        rn = sqrt(c->h_red[16]);
+      }
       st.ms_assemble += tm.stop();
-      status = check_device_error(c, "assembly");
-      if (status) throw CudaError(status, c->err);
-      rn = sqrt(c->h_red[16]);
     }
     if (!conv) {
       st.newton_its = prm->maxit;

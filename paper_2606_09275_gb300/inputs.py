@@ -132,6 +132,14 @@ def workload(name, **over):
                  dx_region=2.0 / 128, nsteps=50,
                  points=dict(lo=(0, 0, 0), hi=(1, 1, 0.875), spacing=1.0 / 128, rho=1000.0,
                              E=1e7, ys=1e5, jitter=1.0 / 512, seed=0))
+    elif name == "indent_small":
+        # the indentation recipe one level coarser (depth 5 -> 6): stiffness larger
+        # than L2 but a few GB on the device, for detailed profiles
+        c.update(L=1.0, depth_min=5, depth_max=6, bc=_block_rollers(1.0, 1.0), model=1,
+                 body=dict(kind=1, cx=0.5, cy=0.5, z0=0.875, r=0.1, alpha=0.0, dz=-0.1 / 50),
+                 dx_region=2.0 / 64, nsteps=50,
+                 points=dict(lo=(0, 0, 0), hi=(1, 1, 0.875), spacing=1.0 / 64, rho=1000.0,
+                             E=1e7, ys=1e5, jitter=1.0 / 256, seed=0))
     else:
         raise KeyError(name)
     for k, v in over.items():

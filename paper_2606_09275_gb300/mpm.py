@@ -26,7 +26,8 @@ EXPORT = dict(leaf_level=0, leaf_anchor=1, node_coord=2, node_hang=3, node_dof=4
               populated=16, ghost_faces=17)
 
 SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_octree_build", "mpm_mesh_free",
-           "mpm_mesh_counts", "mpm_mesh_export", "mpm_assemble", "mpm_solve", "mpm_step"]
+           "mpm_mesh_counts", "mpm_mesh_export", "mpm_assemble", "mpm_solve", "mpm_step",
+           "mpm_profile", "mpm_profile_read", "mpm_launch_count"]
 
 
 class Domain(C.Structure):
@@ -112,6 +113,9 @@ def lib():
         L.mpm_step.argtypes = [vp, C.POINTER(Domain), C.POINTER(Rigid), C.POINTER(Adapt),
                                C.POINTER(Material), C.POINTER(PointsT), C.POINTER(StepParams),
                                C.POINTER(StepStats)]
+        L.mpm_profile.argtypes = [vp, i]
+        L.mpm_profile_read.argtypes = [vp, vp, vp]
+        L.mpm_launch_count.argtypes = [vp, vp]
         _lib = L
     return _lib
 
