@@ -207,6 +207,26 @@ int mpm_step(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body, const m
              const mpm_material* mat, mpm_points* pts, const mpm_step_params* prm,
              mpm_step_stats* stats);
 
+/* Allocation-free variant of mpm_solve (the paper has no counterpart).  For
+ * callers that cannot allocate device memory while they solve -- for example
+ * an application whose device memory is already handed out by its own pool,
+ * so that a cudaMalloc would fail or fragment it, or a latency-bound loop that
+ * cannot afford an allocation on its first call.  It runs the FP64 3x3
+ * block-Jacobi PCG of mpm_solve (precision MPM_FP64, method PCG) with every
+ * work vector, the preconditioner and the scalars placed in one static
+ * device array of 32 MiB that the library reserves on each device that loads
+ * it and keeps until the process exits; the call itself allocates nothing.
+ * Limit: 256 + 168 * ndof bytes must fit, i.e. at most 199,727 dofs
+ * (599,181 unknowns); larger meshes are rejected with MPM_ERR_ARG and a
+ * message.  The first call on a device looks up the array's device address,
+ * so make that first call before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents (each call clears what must
+ * start at zero): calls that overlap on the GPU, from any stream or context,
+ * race with each other.  K_values (FP64, from mpm_assemble), rhs and x as in
+ * mpm_solve; tol > 0 and maxit > 0. */
+int mpm_solve_static(mpm_ctx* ctx, const mpm_mesh* mesh, const double* K_values, const double* rhs,
+                     double* x, double tol, int maxit, mpm_solve_stats* stats);
+
 /* Measurement hooks (no counterpart in the paper; they serve the benchmark):
  * CUDA events recorded on the context stream around every launch of the
  * tracked kernel classes below, and a count of all kernel launches made by

@@ -612,4 +612,103 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
                      (sc_h->breakdown ? ", breakdown)" : ")"));
 }
 
+// ---------------------------------------------------------------- allocation-free PCG
+//
+// A variant of the FP64 block-Jacobi PCG above for callers that must not
+// allocate device memory during the solve.  Its work vectors, preconditioner
+// blocks and scalars live in this file-scope array, reserved once when the
+// library is loaded on a device and kept until the process exits.
+
+namespace {
+
+constexpr size_t kStaticBytes = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_pcg_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+unsigned char* g_pcg_scratch_dev[kMaxDevices] = {};
+
+// device address of g_pcg_scratch on the current device (looked up once per device)
+unsigned char* static_scratch(mpm_ctx* c) {
+  int dev = 0;
+  MPM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) throw CudaError(MPM_ERR_ARG, "device ordinal out of range");
+  if (!g_pcg_scratch_dev[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
+    if (e != cudaSuccess)
+      throw CudaError(MPM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_pcg_scratch_dev[dev] = (unsigned char*)p;
+  }
+  return g_pcg_scratch_dev[dev];
+}
+
+}  // namespace
+
 }  // namespace mpm
+
+using namespace mpm;
+
+extern "C" int mpm_solve_static(mpm_ctx* c, const mpm_mesh* m, const double* K, const double* rhs,
+                                double* x, double tol, int maxit, mpm_solve_stats* stats) {
+  if (!c || !m || !K || !rhs || !x || !m->built || !(tol > 0) || maxit <= 0) return MPM_ERR_ARG;
+  int nd = m->ndof;
+  // layout: scalars (256 B), then r, z, p, q (3 nd each) and the 3x3 inverses (9 nd)
+  size_t need = 256 + sizeof(double) * (size_t)nd * (4 * 3 + 9);
+  if (need > kStaticBytes) {
+    set_error(c, "mpm_solve_static: " + std::to_string(nd) + " dofs need " + std::to_string(need) +
+                     " bytes of scratch, the static array holds " + std::to_string(kStaticBytes) +
+                     " (at most " + std::to_string((kStaticBytes - 256) / (21 * sizeof(double))) +
+                     " dofs)");
+    return MPM_ERR_ARG;
+  }
+  try {
+    cudaStream_t st = c->stream;
+    unsigned char* base = static_scratch(c);
+    Scal* sc = (Scal*)base;
+    double* r = (double*)(base + 256);
+    double* z = r + 3 * (size_t)nd;
+    double* p = z + 3 * (size_t)nd;
+    double* q = p + 3 * (size_t)nd;
+    double* Dinv = q + 3 * (size_t)nd;
+    const int* rp = ptr<int>(m->row_ptr);
+    const int* col = ptr<int>(m->col);
+    // the array keeps the previous call's contents: every vector below is
+    // written before it is read, and the scalars start from zero
+    MPM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scal), st));
+    MPM_LAUNCH(k_block_jacobi<double, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, K, Dinv, c->d_err));
+    int vb = 4 * 152;
+    MPM_LAUNCH(k_pcg_init<double><<<vb, 256, 0, st>>>(nd, rhs, ptr<int>(m->dof_mask), Dinv, x, r, z, p, sc));
+    MPM_LAUNCH(k_pcg_q0<double, double><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, p, q, sc));
+    Scal* h = (Scal*)(c->h_red + 32);
+    MPM_CUDA(cudaMemcpyAsync(h, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(cudaStreamSynchronize(st));
+    double bb = h->bb;
+    mpm_solve_stats s{};
+    if (bb > 0.0) {
+      double thr = tol * tol * bb;
+      MPM_CUDA(cudaMemcpyAsync(&sc->thr, &thr, sizeof(double), cudaMemcpyHostToDevice, st));
+      int k = 0;
+      while (k < maxit) {
+        int kend = std::min(maxit, k + 32);
+        for (; k < kend; ++k) {
+          MPM_LAUNCH(k_pcg_a<double><<<vb, 256, 0, st>>>(nd, k, Dinv, x, r, z, p, q, sc));
+          MPM_LAUNCH(k_pcg_b<double, double><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, k, rp, col, K, z, p, q, sc));
+        }
+        MPM_CUDA(cudaMemcpyAsync(h, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+        MPM_CUDA(cudaStreamSynchronize(st));
+        if (h->done) break;
+      }
+      s.iterations = h->done ? h->iters : maxit;
+      s.relres = sqrt(h->rr[s.iterations % 3] / bb);
+      s.status = (!h->done || h->breakdown) ? MPM_ERR_KRYLOV : MPM_OK;
+    }
+    int e = check_device_error(c, "mpm_solve_static");
+    if (stats) *stats = s;
+    if (e) return e;
+    if (s.status) set_error(c, "mpm_solve_static: PCG did not reach the tolerance");
+    return s.status;
+  } catch (const CudaError& e) {
+    set_error(c, e.what());
+    return e.code;
+  }
+}

@@ -27,7 +27,7 @@ EXPORT = dict(leaf_level=0, leaf_anchor=1, node_coord=2, node_hang=3, node_dof=4
 
 SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_octree_build", "mpm_mesh_free",
            "mpm_mesh_counts", "mpm_mesh_export", "mpm_assemble", "mpm_solve", "mpm_step",
-           "mpm_profile", "mpm_profile_read", "mpm_launch_count"]
+           "mpm_profile", "mpm_profile_read", "mpm_launch_count", "mpm_solve_static"]
 
 
 class Domain(C.Structure):
@@ -113,6 +113,7 @@ def lib():
         L.mpm_step.argtypes = [vp, C.POINTER(Domain), C.POINTER(Rigid), C.POINTER(Adapt),
                                C.POINTER(Material), C.POINTER(PointsT), C.POINTER(StepParams),
                                C.POINTER(StepStats)]
+        L.mpm_solve_static.argtypes = [vp, vp, vp, vp, vp, d, i, C.POINTER(SolveStats)]
         L.mpm_profile.argtypes = [vp, i]
         L.mpm_profile_read.argtypes = [vp, vp, vp]
         L.mpm_launch_count.argtypes = [vp, vp]
@@ -327,6 +328,18 @@ def solve(ctx, mesh, cfg, K, rhs, precision=FP64, tol=1e-10, maxit=20000, method
     ss = SolveStats()
     st = lib().mpm_solve(ctx.h, mesh.h, C.byref(material(cfg)), _p(K), _p(rhs), _p(x), C.byref(sp),
                          C.byref(ss))
+    stats = dict(iterations=ss.iterations, refinements=ss.refinements, status=ss.status,
+                 relres=ss.relres)
+    ctx.check(st)
+    return x, stats
+
+
+def solve_static(ctx, mesh, K, rhs, tol=1e-10, maxit=20000):
+    """mpm_solve_static: FP64 block-Jacobi PCG whose scratch is the library's
+    static device array, so the call allocates no device memory."""
+    x = torch.empty_like(rhs)
+    ss = SolveStats()
+    st = lib().mpm_solve_static(ctx.h, mesh.h, _p(K), _p(rhs), _p(x), tol, maxit, C.byref(ss))
     stats = dict(iterations=ss.iterations, refinements=ss.refinements, status=ss.status,
                  relres=ss.relres)
     ctx.check(st)
