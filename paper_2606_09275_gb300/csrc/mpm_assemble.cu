@@ -3,6 +3,8 @@
 // spatial tangent (Sec. 2.2), the internal force, the tangent gathered row by
 // row into the 3x3 block matrix, the ghost term (Sec. 4), the penalty contact
 // (Sec. 2.3) and the strong Dirichlet rows (Sec. 2.4).
+#include <algorithm>
+
 #include "mpm_internal.cuh"
 
 namespace mpm {
@@ -10,28 +12,40 @@ namespace {
 
 // ------------------------------------------------------------------ kinematics
 
-// dF = I + sum_v du_v (x) grad S_vp, one warp per point
+// dF = I + sum_v du_v (x) grad S_vp; eight lanes per point, four points per warp
 __global__ void k_kinematics(int P, const int* __restrict__ nsup, const int* __restrict__ sidx,
                              const double* __restrict__ dS, const double* __restrict__ du,
                              double* dF) {
-  int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w >= P) return;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int w = (int)(t >> 3), sub = (int)(t & 7);
   double a[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) a[i] = 0.0;
-  int n = nsup[w];
-  for (int k = lane; k < n; k += 32) {
-    size_t o = (size_t)w * MAXS + k;
-    int j = sidx[o];
-    double u0 = du[3 * (size_t)j], u1 = du[3 * (size_t)j + 1], u2 = du[3 * (size_t)j + 2];
-    double g0 = dS[3 * o], g1 = dS[3 * o + 1], g2 = dS[3 * o + 2];
-    a[0] += u0 * g0; a[1] += u0 * g1; a[2] += u0 * g2;
-    a[3] += u1 * g0; a[4] += u1 * g1; a[5] += u1 * g2;
-    a[6] += u2 * g0; a[7] += u2 * g1; a[8] += u2 * g2;
+  if (w < P) {
+    int n = nsup[w];
+    for (int k = sub; k < n; k += 8) {
+      size_t o = (size_t)w * MAXS + k;
+      int j = sidx[o];
+      double u0 = du[3 * (size_t)j], u1 = du[3 * (size_t)j + 1], u2 = du[3 * (size_t)j + 2];
+      double g0 = dS[3 * o], g1 = dS[3 * o + 1], g2 = dS[3 * o + 2];
+      a[0] += u0 * g0; a[1] += u0 * g1; a[2] += u0 * g2;
+      a[3] += u1 * g0; a[4] += u1 * g1; a[5] += u1 * g2;
+      a[6] += u2 * g0; a[7] += u2 * g1; a[8] += u2 * g2;
+    }
   }
 #pragma unroll
-  for (int i = 0; i < 9; ++i) a[i] = warp_sum(a[i]);
-  if (lane < 9) dF[9 * (size_t)w + lane] = a[lane] + ((lane % 4 == 0) ? 1.0 : 0.0);
+  for (int i = 0; i < 9; ++i) {
+    a[i] += __shfl_xor_sync(0xffffffffu, a[i], 4);
+    a[i] += __shfl_xor_sync(0xffffffffu, a[i], 2);
+    a[i] += __shfl_xor_sync(0xffffffffu, a[i], 1);
+  }
+  if (w < P) {
+    double v = a[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) v = (sub == i) ? a[i] : v;
+    dF[9 * (size_t)w + sub] = v + ((sub % 4 == 0) ? 1.0 : 0.0);
+    if (sub == 0) dF[9 * (size_t)w + 8] = a[8] + 1.0;
+  }
 }
 
 // ------------------------------------------------------------------ constitutive
@@ -204,7 +218,9 @@ __device__ bool point_update_law(const Law& L, double E, double ys, const double
     be_new[s] = Q[3 * i] * bw[0] * Q[3 * j] + Q[3 * i + 1] * bw[1] * Q[3 * j + 1] + Q[3 * i + 2] * bw[2] * Q[3 * j + 2];
   }
   if (TANGENT) {
-    // theta_ab = (tau_a - tau_b)/(lam_a - lam_b) = g/2 * divided difference of ln
+    // theta_ab = (tau_a - tau_b)/(lam_a - lam_b) = g/2 * divided difference of ln.
+    // Built in FP64 and rounded once at the store: an FP32 rotation slows the
+    // last Newton iterations enough to move the converged state by ~1e-4.
     double th01 = 0.5 * gr * ln_divdiff(lam[0], lam[1]);
     double th02 = 0.5 * gr * ln_divdiff(lam[0], lam[2]);
     double th12 = 0.5 * gr * ln_divdiff(lam[1], lam[2]);
@@ -343,7 +359,7 @@ __global__ void k_residual_rows(int nd, double load, const int* __restrict__ rp,
 
 // ------------------------------------------------------------------ tangent (row gather)
 
-constexpr int TW = 4;  // warps per block of the tangent gather
+constexpr int TW = 4;  // warps per block of the tangent gather (at most)
 
 __device__ inline int find_in(const int* a, int n, int v) {
   int lo = 0, hi = n - 1;
@@ -359,32 +375,39 @@ __device__ inline int find_in(const int* a, int n, int v) {
   return -1;
 }
 
+template <class T>
+__host__ __device__ inline size_t tangent_warp_bytes(int mr) {
+  return (size_t)mr * (9 * sizeof(T) + sizeof(int)) + 32 * sizeof(T);
+}
+
 // One warp owns block row r: for every point p with r in its support (local
 // index k), K_{r,w} += V0_p (grad_x S_k)^T A'_p (grad_x S_w) for all w in the
-// support of p.  The row is written by this warp only, in source order, so the
-// sum is free of atomics and deterministic.  Ghost coefficients and the
-// Dirichlet identity rows/columns are applied at the end.
+// support of p.  The row accumulates in shared memory (mr = longest row, a
+// multiple of 4), in source order, free of atomics and deterministic; ghost
+// coefficients and the Dirichlet identity rows/columns are applied when the
+// row is written out, coalesced, in the row-sliced layout.
 template <class T>
 __global__ void __launch_bounds__(32 * TW)
-    k_tangent_rows(int nd, int P, const int* __restrict__ rp, const int* __restrict__ col,
+    k_tangent_rows(int nd, int P, int mr, const int* __restrict__ rp, const int* __restrict__ col,
                    const long long* __restrict__ sptr, const uint64_t* __restrict__ skeys,
                    const int* __restrict__ nsup, const int* __restrict__ sidx,
                    const T* __restrict__ gx, const T* __restrict__ Aalg,
                    const double* __restrict__ V0, const double* __restrict__ kg,
                    const int* __restrict__ mask, T* K, int* err) {
-  __shared__ int cols[TW][MAXROW];
-  __shared__ T Tt[TW][32];
+  extern __shared__ __align__(16) unsigned char smraw[];
   int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int r = blockIdx.x * TW + wi;
+  T* acc = (T*)(smraw + wi * tangent_warp_bytes<T>(mr));
+  T* Tt = acc + 9 * (size_t)mr;
+  int* cols = (int*)(Tt + 32);
+  int r = blockIdx.x * (blockDim.x >> 5) + wi;
   if (r >= nd) return;
   int s0 = rp[r], nb = rp[r + 1] - s0;
-  if (nb > MAXROW) {
+  if (nb > mr) {
     if (lane == 0) atomicOr(err, EB_ROW);
     return;
   }
-  for (int i = lane; i < nb; i += 32) cols[wi][i] = col[s0 + i];
-  T* Kr = K + 9 * (size_t)s0;
-  for (int i = lane; i < 9 * nb; i += 32) Kr[i] = (T)0;
+  for (int i = lane; i < nb; i += 32) cols[i] = col[s0 + i];
+  for (int i = lane; i < 9 * nb; i += 32) acc[i] = (T)0;
   __syncwarp();
   for (long long q = sptr[r]; q < sptr[r + 1]; ++q) {
     uint32_t sid = (uint32_t)skeys[q];
@@ -395,7 +418,7 @@ __global__ void __launch_bounds__(32 * TW)
     T v0 = (T)V0[w];
     if (lane < 27) {
       const T* A = Aalg + 81 * (size_t)w + 3 * lane;
-      Tt[wi][lane] = v0 * (gk0 * A[0] + gk1 * A[1] + gk2 * A[2]);
+      Tt[lane] = v0 * (gk0 * A[0] + gk1 * A[1] + gk2 * A[2]);
     }
     __syncwarp();
     int n = nsup[w];
@@ -403,31 +426,29 @@ __global__ void __launch_bounds__(32 * TW)
       size_t o = (size_t)w * MAXS + l;
       int c = sidx[o];
       T g0 = gx[3 * o], g1 = gx[3 * o + 1], g2 = gx[3 * o + 2];
-      int idx = find_in(cols[wi], nb, c);
+      int idx = find_in(cols, nb, c);
       if (idx < 0) continue;
 #pragma unroll
-      for (int e = 0; e < 9; ++e) {
-        const T* tt = &Tt[wi][3 * e];
-        Kr[(size_t)e * nb + idx] += tt[0] * g0 + tt[1] * g1 + tt[2] * g2;
-      }
+      for (int e = 0; e < 9; ++e) acc[e * nb + idx] += Tt[3 * e] * g0 + Tt[3 * e + 1] * g1 + Tt[3 * e + 2] * g2;
     }
     __syncwarp();
   }
-  // ghost, then the Dirichlet identity
-  int mr = mask[r];
+  // ghost, then the Dirichlet identity, then one coalesced write of the row
+  int mr_ = mask[r];
+  T* Kr = K + 9 * (size_t)s0;
   for (int i = lane; i < nb; i += 32) {
-    double kv = kg[s0 + i];
-    int c = cols[wi][i];
+    T kv = (T)kg[s0 + i];
+    int c = cols[i];
     int mc = mask[c];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        size_t at = (size_t)(3 * a + b) * nb + i;
-        T v = Kr[at];
-        if (a == b) v += (T)kv;
-        if (((mr >> a) & 1) || ((mc >> b) & 1)) v = (c == r && a == b) ? (T)1 : (T)0;
-        Kr[at] = v;
+        int e = 3 * a + b;
+        T v = acc[e * nb + i];
+        if (a == b) v += kv;
+        if (((mr_ >> a) & 1) || ((mc >> b) & 1)) v = (c == r && a == b) ? (T)1 : (T)0;
+        Kr[(size_t)e * nb + i] = v;
       }
   }
 }
@@ -561,7 +582,7 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
   const int* nsup = ptr<int>(m->nsup);
   const int* sidx = ptr<int>(m->sidx);
   const double* dS = ptr<double>(m->dS);
-  MPM_LAUNCH_P(MPM_PROF_KINEMATICS, k_kinematics<<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, du, dF));
+  MPM_LAUNCH_P(MPM_PROF_KINEMATICS, k_kinematics<<<grid_for(8LL * P, 256), 256, 0, st>>>(P, nsup, sidx, dS, du, dF));
   bool mixed = precision == MPM_MIXED;
   size_t asz = mixed ? sizeof(float) : sizeof(double);
   void* Aalg = K ? grow_bytes(c, m->Aalg, 81 * (size_t)P * asz) : nullptr;
@@ -597,16 +618,24 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
   MPM_LAUNCH_P(MPM_PROF_RESIDUAL, k_residual_rows<<<grid_for(nd, 8), 256, 0, st>>>(nd, load, rp, col, ptr<double>(m->kg), du, fint,
                                                    ptr<double>(m->fext), R));
   if (K) {
-    if (mixed)
-      MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<float><<<grid_for(nd, TW), 32 * TW, 0, st>>>(
-          nd, P, rp, col, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
+    int mr = (m->maxrow + 3) & ~3;
+    size_t wb = mixed ? tangent_warp_bytes<float>(mr) : tangent_warp_bytes<double>(mr);
+    int tw = (int)std::min<size_t>(TW, (size_t)(220 * 1024) / wb);
+    if (tw < 1) throw CudaError(MPM_ERR_SUPPORT, "stiffness row too long for the tangent gather");
+    size_t smem = wb * tw;
+    if (mixed) {
+      MPM_CUDA(cudaFuncSetAttribute(k_tangent_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<float><<<grid_for(nd, tw), 32 * tw, smem, st>>>(
+          nd, P, mr, rp, col, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
           (const float*)gx, (const float*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
           (float*)K, c->d_err));
-    else
-      MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<double><<<grid_for(nd, TW), 32 * TW, 0, st>>>(
-          nd, P, rp, col, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
+    } else {
+      MPM_CUDA(cudaFuncSetAttribute(k_tangent_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<double><<<grid_for(nd, tw), 32 * tw, smem, st>>>(
+          nd, P, mr, rp, col, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
           (const double*)gx, (const double*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
           (double*)K, c->d_err));
+    }
   }
   double* reac = c->d_red + 20;
   MPM_CUDA(cudaMemsetAsync(reac, 0, 3 * sizeof(double), st));

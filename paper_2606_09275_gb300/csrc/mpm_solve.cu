@@ -555,7 +555,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   }
   // mixed: FP32 inner solves inside FP64 iterative refinement
   const float* Kf = (const float*)K;
-  double inner = prm.inner_tol > 0 ? prm.inner_tol : 1e-4;
+  double inner = prm.inner_tol > 0 ? prm.inner_tol : 1e-3;
   double* r64 = grow<double>(c, c->v[12], n3);
   float* d32 = grow<float>(c, c->v[13], n3);
   double* slot = c->d_red + 44;

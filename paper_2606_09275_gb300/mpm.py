@@ -321,7 +321,7 @@ def assemble(ctx, mesh, cfg, du, load=1.0, precision=FP64, tangent=True, body_z=
 
 
 def solve(ctx, mesh, cfg, K, rhs, precision=FP64, tol=1e-10, maxit=20000, method=0,
-          inner_tol=1e-4):
+          inner_tol=1e-3):
     """mpm_solve: block-Jacobi PCG / BiCGStab (FP32 inner + FP64 refinement when mixed)."""
     x = torch.empty_like(rhs)
     sp = SolveParams(method, precision, tol, maxit, inner_tol)
@@ -347,7 +347,7 @@ def solve_static(ctx, mesh, K, rhs, tol=1e-10, maxit=20000):
 
 
 def step(ctx, cfg, points, body_z=None, load=1.0, tol=1e-8, maxit=30, lin_tol=1e-8,
-         lin_maxit=20000, precision=FP64, method=0, inner_tol=1e-4, check=True):
+         lin_maxit=20000, precision=FP64, method=0, inner_tol=1e-3, check=True):
     """mpm_step: one quasi-static load step; returns the statistics."""
     s = points.struct()
     sp = StepParams(load, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol))
