@@ -16,10 +16,11 @@
  *      cohesion (Drucker-Prager).  All double precision.
  *  - Nodal vectors are [3*ndof] doubles, component-fastest, dofs numbered in
  *    Morton order of the active independent nodes of the mesh.
- *  - Stiffness values use a row-sliced 3x3 block layout: block row r owns the
- *    blocks s = row_ptr[r] .. row_ptr[r+1]-1 (nb = their count); entry (i,j) of
- *    its k-th block lives at values[9*row_ptr[r] + (3*i + j)*nb + k].  The block
- *    columns col[s] are sorted ascending in each row.
+ *  - The stiffness is a 3x3 block matrix whose pattern is the sorted CSR
+ *    (row_ptr, col) of mpm_mesh_export.  Its values are held in a sliced layout
+ *    (slices of 32 block rows, each padded to a width that is a multiple of 4
+ *    blocks) sized 9 * nslot entries (mpm_mesh_info.nslot); mpm_blocks_export
+ *    reads them back as plain [nnzb][3][3] row-major blocks in CSR order.
  *  - Every call returns an mpm_status; on failure mpm_last_error(ctx) gives a
  *    message.  No call aborts, traps or spins without bound: device-side
  *    failures (support overflow, NaN, Krylov breakdown) come back as status
@@ -97,7 +98,7 @@ typedef struct {
 } mpm_points;
 
 typedef struct {
-  int nleaf, nnode, nhang, ndof, nnzb, nghost, npts, maxs, ncontact, maxrow;
+  int nleaf, nnode, nhang, ndof, nnzb, nghost, npts, maxs, ncontact, maxrow, nslot;
 } mpm_mesh_info;
 
 typedef struct {
@@ -182,7 +183,7 @@ int mpm_mesh_export(const mpm_mesh* mesh, int what, void* dst, size_t bytes);
 /* Eq. (MPMweak), static part, with the ghost term of Sec. 4 and the penalty
  * contact of Sec. 2.3: for the nodal increment du (device [3*ndof]) of the
  * current load step, R (device [3*ndof]) = f_int - load*f_ext - f_c + K_G du and,
- * if K_values (device [9*nnzb], double for MPM_FP64, float for MPM_MIXED) is
+ * if K_values (device [9*nslot], double for MPM_FP64, float for MPM_MIXED) is
  * non-NULL, the consistent tangent with the Dirichlet rows and columns
  * replaced by identity.  reaction (host [3], may be NULL) receives the force of
  * the material on the rigid body.  fint_norms (host [2], may be NULL) receives
@@ -190,6 +191,12 @@ int mpm_mesh_export(const mpm_mesh* mesh, int what, void* dst, size_t bytes);
 int mpm_assemble(mpm_ctx* ctx, const mpm_mesh* mesh, const mpm_material* mat,
                  const mpm_rigid* body, const double* du, double load, int precision, double* R,
                  void* K_values, double* reaction, double* fint_norms);
+
+/* Copies stiffness values (as written by mpm_assemble with `precision`) to host
+ * memory as [nnzb][3][3] row-major blocks in the CSR order of the pattern;
+ * blocks_host must hold 9*nnzb doubles.  Synchronises the stream. */
+int mpm_blocks_export(mpm_ctx* ctx, const mpm_mesh* mesh, const void* K_values, int precision,
+                      double* blocks_host);
 
 /* Preconditioned Krylov solve of K x = rhs on the free components (Sec. 1 names
  * Krylov solvers with a Jacobi-type preconditioner as the scalable option), 3x3
@@ -216,8 +223,9 @@ int mpm_step(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body, const m
  * work vector, the preconditioner and the scalars placed in one static
  * device array of 32 MiB that the library reserves on each device that loads
  * it and keeps until the process exits; the call itself allocates nothing.
- * Limit: 256 + 168 * ndof bytes must fit, i.e. at most 199,727 dofs
- * (599,181 unknowns); larger meshes are rejected with MPM_ERR_ARG and a
+ * Limit: 256 + 224 * 32 * ceil(ndof / 32) bytes must fit (vectors padded
+ * to 4 components and to whole slices of 32 rows), i.e. at most 149,792 dofs
+ * (449,376 unknowns); larger meshes are rejected with MPM_ERR_ARG and a
  * message.  The first call on a device looks up the array's device address,
  * so make that first call before any stream capture.  All calls share the one
  * array and it keeps the last call's contents (each call clears what must

@@ -389,7 +389,7 @@ __host__ __device__ inline size_t tangent_warp_bytes(int mr) {
 template <class T>
 __global__ void __launch_bounds__(32 * TW)
     k_tangent_rows(int nd, int P, int mr, const int* __restrict__ rp, const int* __restrict__ col,
-                   const long long* __restrict__ sptr, const uint64_t* __restrict__ skeys,
+                   Sliced S, const long long* __restrict__ sptr, const uint64_t* __restrict__ skeys,
                    const int* __restrict__ nsup, const int* __restrict__ sidx,
                    const T* __restrict__ gx, const T* __restrict__ Aalg,
                    const double* __restrict__ V0, const double* __restrict__ kg,
@@ -433,10 +433,18 @@ __global__ void __launch_bounds__(32 * TW)
     }
     __syncwarp();
   }
-  // ghost, then the Dirichlet identity, then one coalesced write of the row
+  // ghost, then the Dirichlet identity, then the row (and its padding slots,
+  // zero) into the sliced storage
   int mr_ = mask[r];
-  T* Kr = K + 9 * (size_t)s0;
-  for (int i = lane; i < nb; i += 32) {
+  int sl = r >> 5, W = S.w[sl];
+  long long b0 = S.base[sl];
+  for (int i = lane; i < W; i += 32) {
+    long long slot = sliced_slot(b0, r, i);
+    if (i >= nb) {
+#pragma unroll
+      for (int e = 0; e < 9; ++e) K[sliced_entry(b0, W, slot, e)] = (T)0;
+      continue;
+    }
     T kv = (T)kg[s0 + i];
     int c = cols[i];
     int mc = mask[c];
@@ -448,8 +456,37 @@ __global__ void __launch_bounds__(32 * TW)
         T v = acc[e * nb + i];
         if (a == b) v += kv;
         if (((mr_ >> a) & 1) || ((mc >> b) & 1)) v = (c == r && a == b) ? (T)1 : (T)0;
-        Kr[(size_t)e * nb + i] = v;
+        K[sliced_entry(b0, W, slot, e)] = v;
       }
+  }
+}
+
+// rows beyond ndof in the last slice: zero padding slots
+template <class T>
+__global__ void k_zero_pad_rows(int nd, int npad, Sliced S, T* K) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int r = nd + (int)(t >> 5), lane = (int)(t & 31);
+  if (r >= npad) return;
+  int sl = r >> 5, W = S.w[sl];
+  long long b0 = S.base[sl];
+  for (int i = lane; i < W; i += 32) {
+    long long slot = sliced_slot(b0, r, i);
+    for (int e = 0; e < 9; ++e) K[sliced_entry(b0, W, slot, e)] = (T)0;
+  }
+}
+
+// sliced values -> plain [nnzb][3][3] blocks (FP64)
+template <class T>
+__global__ void k_blocks_export(int nd, const int* __restrict__ rp, Sliced S, const T* __restrict__ K,
+                                double* out) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int r = (int)(t >> 5), lane = (int)(t & 31);
+  if (r >= nd) return;
+  int sl = r >> 5, W = S.w[sl];
+  long long b0 = S.base[sl];
+  for (int i = lane; i < rp[r + 1] - rp[r]; i += 32) {
+    long long slot = sliced_slot(b0, r, i);
+    for (int e = 0; e < 9; ++e) out[9 * (size_t)(rp[r] + i) + e] = (double)K[sliced_entry(b0, W, slot, e)];
   }
 }
 
@@ -478,7 +515,7 @@ __global__ void k_contact(int nc8, const int* __restrict__ cand, const int* __re
                           const double* __restrict__ cb_y0, const double* __restrict__ pE,
                           const double* __restrict__ pV0, mpm_rigid body, double L, double pf,
                           const double* __restrict__ du, double* R, double* fc, double* reac,
-                          const int* __restrict__ rp, const int* __restrict__ col,
+                          const int* __restrict__ rp, const int* __restrict__ col, Sliced S,
                           const int* __restrict__ mask, T* K) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nc8) return;
@@ -504,17 +541,20 @@ __global__ void k_contact(int nc8, const int* __restrict__ cand, const int* __re
     for (int b = 0; b < 3; ++b) kc[3 * a + b] = epsN * (nv[a] * nv[b] + phi * H[3 * a + b]);
   for (int ea = 0; ea < n; ++ea) {
     int ra = ids[ea];
-    int s0 = rp[ra], nb = rp[ra + 1] - s0, ma = mask[ra];
+    int s0 = rp[ra], ma = mask[ra];
+    int slc = ra >> 5, W = S.w[slc];
+    long long b0 = S.base[slc];
     for (int eb = 0; eb < n; ++eb) {
       int cb = ids[eb];
       int sl = find_slot(rp, col, ra, cb);
       if (sl < 0) continue;
+      long long slot = sliced_slot(b0, ra, sl - s0);
       int mb = mask[cb];
       double pp = ph[ea] * ph[eb];
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
           if (((ma >> a) & 1) || ((mb >> b) & 1)) continue;
-          atomicAdd(K + 9 * (size_t)s0 + (size_t)(3 * a + b) * nb + (sl - s0), (T)(pp * kc[3 * a + b]));
+          atomicAdd(K + sliced_entry(b0, W, slot, 3 * a + b), (T)(pp * kc[3 * a + b]));
         }
     }
   }
@@ -615,6 +655,7 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
                                                           (double*)gx));
   const int* rp = ptr<int>(m->row_ptr);
   const int* col = ptr<int>(m->col);
+  Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
   MPM_LAUNCH_P(MPM_PROF_RESIDUAL, k_residual_rows<<<grid_for(nd, 8), 256, 0, st>>>(nd, load, rp, col, ptr<double>(m->kg), du, fint,
                                                    ptr<double>(m->fext), R));
   if (K) {
@@ -626,15 +667,22 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
     if (mixed) {
       MPM_CUDA(cudaFuncSetAttribute(k_tangent_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<float><<<grid_for(nd, tw), 32 * tw, smem, st>>>(
-          nd, P, mr, rp, col, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
+          nd, P, mr, rp, col, S, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
           (const float*)gx, (const float*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
           (float*)K, c->d_err));
     } else {
       MPM_CUDA(cudaFuncSetAttribute(k_tangent_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<double><<<grid_for(nd, tw), 32 * tw, smem, st>>>(
-          nd, P, mr, rp, col, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
+          nd, P, mr, rp, col, S, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
           (const double*)gx, (const double*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
           (double*)K, c->d_err));
+    }
+    int npad = 32 * m->nslice;
+    if (npad > nd) {
+      if (mixed)
+        MPM_LAUNCH(k_zero_pad_rows<float><<<grid_for(32LL * (npad - nd), 256), 256, 0, st>>>(nd, npad, S, (float*)K));
+      else
+        MPM_LAUNCH(k_zero_pad_rows<double><<<grid_for(32LL * (npad - nd), 256), 256, 0, st>>>(nd, npad, S, (double*)K));
     }
   }
   double* reac = c->d_red + 20;
@@ -645,17 +693,17 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
       MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<double, false><<<grid_for(n8, 128), 128, 0, st>>>(
           n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
           ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
-          col, ptr<int>(m->dof_mask), (double*)nullptr));
+          col, S, ptr<int>(m->dof_mask), (double*)nullptr));
     else if (mixed)
       MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<float, true><<<grid_for(n8, 128), 128, 0, st>>>(
           n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
           ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
-          col, ptr<int>(m->dof_mask), (float*)K));
+          col, S, ptr<int>(m->dof_mask), (float*)K));
     else
       MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<double, true><<<grid_for(n8, 128), 128, 0, st>>>(
           n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
           ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
-          col, ptr<int>(m->dof_mask), (double*)K));
+          col, S, ptr<int>(m->dof_mask), (double*)K));
   }
   if (want_norms) {
     double* slot = c->d_red + 16;
@@ -668,6 +716,15 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
     out->fextc_norm = sqrt(c->h_red[18]);
     for (int d = 0; d < 3; ++d) out->reaction[d] = c->h_red[20 + d];
   }
+}
+
+void blocks_export(mpm_ctx* c, const mpm_mesh* m, const void* K, int precision, double* out) {
+  Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+  int nd = m->ndof;
+  if (precision == MPM_MIXED)
+    MPM_LAUNCH(k_blocks_export<float><<<grid_for(32LL * nd, 256), 256, 0, c->stream>>>(nd, ptr<int>(m->row_ptr), S, (const float*)K, out));
+  else
+    MPM_LAUNCH(k_blocks_export<double><<<grid_for(32LL * nd, 256), 256, 0, c->stream>>>(nd, ptr<int>(m->row_ptr), S, (const double*)K, out));
 }
 
 // ------------------------------------------------------------------ point update helpers (used by mpm_step.cu)

@@ -1068,6 +1068,40 @@ __global__ void k_cand_basis(int nc, const int* __restrict__ cand, Geo g,
   cb_n[i] = n;
 }
 
+// ------------------------------------------------------------------ sliced storage
+
+// width of each slice of 32 rows: longest row, rounded up to 4 blocks
+__global__ void k_slice_width(int nd, int ns, const int* __restrict__ rp, int* w) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  int m = 0;
+  for (int r = 32 * s; r < min(nd, 32 * s + 32); ++r) m = max(m, rp[r + 1] - rp[r]);
+  w[s] = (m + 3) & ~3;
+}
+
+__global__ void k_slice_slots(int ns, const int* __restrict__ w, int* slots) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < ns) slots[s] = 32 * w[s];
+}
+
+__global__ void k_slice_base64(int ns, const int* __restrict__ pos, long long* base) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < ns) base[s] = pos[s];
+}
+
+// slot columns: the row's sorted columns, then padding slots pointing at the row
+__global__ void k_slice_cols(int nd, int ns, const int* __restrict__ rp, const int* __restrict__ col,
+                             const int* __restrict__ w, const long long* __restrict__ base,
+                             int* scol) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int r = (int)(t >> 5), lane = (int)(t & 31);
+  if (r >= 32 * ns) return;
+  int s = r >> 5;
+  int nb = r < nd ? rp[r + 1] - rp[r] : 0;
+  for (int idx = lane; idx < w[s]; idx += 32)
+    scol[sliced_slot(base[s], r, idx)] = idx < nb ? col[rp[r] + idx] : (r < nd ? r : 0);
+}
+
 // ------------------------------------------------------------------ host helpers
 
 int read_total(mpm_ctx* c, const int* scan_out, const int* cnt, int n) {
@@ -1355,6 +1389,21 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     int mr = 0;
     for (int r = 0; r < nd; ++r) mr = std::max(mr, h[r + 1] - h[r]);
     m->maxrow = mr;
+    // sliced storage of the stiffness
+    int ns = (nd + 31) / 32;
+    m->nslice = ns;
+    int* sw = grow<int>(c, m->slice_w, ns + 1);
+    int* slots = grow<int>(c, c->tmp[1], ns + 1);
+    int* spos = grow<int>(c, c->tmp[2], ns + 1);
+    MPM_LAUNCH(k_slice_width<<<grid_for(ns, 256), 256, 0, st>>>(nd, ns, rp, sw));
+    MPM_LAUNCH(k_slice_slots<<<grid_for(ns, 256), 256, 0, st>>>(ns, sw, slots));
+    MPM_CUDA(cudaMemsetAsync(slots + ns, 0, sizeof(int), st));
+    cub_exclusive_sum_int(c, slots, spos, ns + 1);
+    m->nslot = read_total(c, spos, slots, ns + 1);
+    long long* sb = grow<long long>(c, m->slice_base, ns + 1);
+    MPM_LAUNCH(k_slice_base64<<<grid_for(ns + 1, 256), 256, 0, st>>>(ns + 1, spos, sb));
+    int* scol = grow<int>(c, m->scol, m->nslot);
+    MPM_LAUNCH(k_slice_cols<<<grid_for(32LL * 32 * ns, 256), 256, 0, st>>>(nd, ns, rp, col, sw, sb, scol));
   }
   const int* rp = ptr<int>(m->row_ptr);
   const int* col = ptr<int>(m->col);

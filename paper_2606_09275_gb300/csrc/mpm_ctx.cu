@@ -141,7 +141,7 @@ static void mesh_release(mpm_mesh* m) {
                  &m->nsup, &m->sidx, &m->S, &m->dS, &m->S32, &m->dS32, &m->populated, &m->betaK,
                  &m->isB, &m->gface, &m->gdof, &m->gn, &m->row_ptr, &m->col, &m->kg, &m->rowcnt,
                  &m->src_key, &m->src_ptr, &m->fext, &m->cand, &m->cb_n, &m->cb_idx, &m->cb_phi,
-                 &m->cb_y0, &m->dF, &m->dFinv, &m->tau, &m->Aalg, &m->gx};
+                 &m->cb_y0, &m->dF, &m->dFinv, &m->tau, &m->Aalg, &m->gx, &m->slice_w, &m->slice_base, &m->scol};
   for (Buf* b : bufs) free_buf(c, *b);
 }
 
@@ -243,7 +243,20 @@ extern "C" int mpm_mesh_counts(const mpm_mesh* m, mpm_mesh_info* info) {
   info->maxs = m->maxs;
   info->ncontact = m->ncand;
   info->maxrow = m->maxrow;
+  info->nslot = (int)m->nslot;
   return MPM_OK;
+}
+
+extern "C" int mpm_blocks_export(mpm_ctx* c, const mpm_mesh* m, const void* K, int precision,
+                                 double* host) {
+  if (!c || !m || !K || !host || !m->built) return MPM_ERR_ARG;
+  MPM_GUARD(c, {
+    double* d = grow<double>(c, c->tmp[6], 9 * (size_t)m->nnzb);
+    blocks_export(c, m, K, precision, d);
+    MPM_CUDA(cudaMemcpyAsync(host, d, sizeof(double) * 9 * (size_t)m->nnzb, cudaMemcpyDeviceToHost, c->stream));
+    MPM_CUDA(cudaStreamSynchronize(c->stream));
+    return (int)MPM_OK;
+  })
 }
 
 namespace {

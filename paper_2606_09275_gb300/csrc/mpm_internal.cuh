@@ -126,9 +126,13 @@ struct mpm_mesh {
   // ghost faces
   int nghost = 0;
   mpm::Buf gface, gdof, gn;
-  // pattern
+  // pattern (sorted CSR over dofs) and its sliced storage: slices of 32 block
+  // rows, each padded to a width that is a multiple of 4 blocks
   int nnzb = 0, maxrow = 0;
   mpm::Buf row_ptr, col, kg, rowcnt;
+  int nslice = 0;
+  long long nslot = 0;                  // padded block slots of the sliced storage
+  mpm::Buf slice_w, slice_base, scol;   // width, first slot of each slice, slot columns
   // sources of each row: (sorted point or ghost face) << 6 | local index
   long long nsrc = 0;
   mpm::Buf src_key, src_ptr;
@@ -141,6 +145,23 @@ struct mpm_mesh {
   mpm::Buf dF, dFinv, tau, Aalg, gx;
   int built = 0;
 };
+
+namespace mpm {
+// position of block idx of row r in the sliced storage (block slot index);
+// entry e of that block lives at values[9*base + e*32*w + slot - base] where
+// base/w are the slice's first slot and width
+struct Sliced {
+  const int* w;          // width (blocks) of each slice
+  const long long* base; // first slot of each slice
+  const int* scol;       // column of each slot (padding slots: the row itself)
+};
+__host__ __device__ inline long long sliced_slot(long long base, int r, int idx) {
+  return base + ((long long)(idx >> 2) * 32 + (r & 31)) * 4 + (idx & 3);
+}
+__host__ __device__ inline long long sliced_entry(long long base, int w, long long slot, int e) {
+  return 9 * base + (long long)e * 32 * w + (slot - base);
+}
+}  // namespace mpm
 
 namespace mpm {
 
@@ -427,6 +448,7 @@ void assemble(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const mpm_
               const double* du, double load, int precision, double* R, void* K, AsmOut* out,
               bool want_norms);
 double norm_free(mpm_ctx* c, const mpm_mesh* m, const double* R);
+void blocks_export(mpm_ctx* c, const mpm_mesh* m, const void* K, int precision, double* out);
 
 // solve (mpm_solve.cu)
 void solve(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const void* K, const double* b,

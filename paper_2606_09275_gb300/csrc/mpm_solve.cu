@@ -16,7 +16,7 @@
 namespace mpm {
 namespace {
 
-constexpr int SW = 8;  // warps (rows) per block of the row kernels
+constexpr int SW = 8;  // warps (slices of 32 rows) per block of the row kernels
 
 struct Scal {
   double rz[3], pq[3], rr[3];
@@ -25,28 +25,63 @@ struct Scal {
   int done, iters, breakdown, pad;
 };
 
-template <class T, class V, class A>
-__device__ inline void row_dot(int r, int lane, const int* __restrict__ rp, const int* __restrict__ col,
-                               const T* __restrict__ K, const V* __restrict__ x, A& y0, A& y1, A& y2) {
-  int s0 = rp[r], nb = rp[r + 1] - s0;
-  const T* b = K + 9 * (size_t)s0;
-  y0 = y1 = y2 = (A)0;
-  for (int k = lane; k < nb; k += 32) {
-    int c = col[s0 + k];
-    A x0 = (A)x[3 * (size_t)c], x1 = (A)x[3 * (size_t)c + 1], x2 = (A)x[3 * (size_t)c + 2];
-    y0 += (A)b[k] * x0 + (A)b[nb + k] * x1 + (A)b[2 * (size_t)nb + k] * x2;
-    y1 += (A)b[3 * (size_t)nb + k] * x0 + (A)b[4 * (size_t)nb + k] * x1 + (A)b[5 * (size_t)nb + k] * x2;
-    y2 += (A)b[6 * (size_t)nb + k] * x0 + (A)b[7 * (size_t)nb + k] * x1 + (A)b[8 * (size_t)nb + k] * x2;
-  }
-  y0 = warp_sum(y0);
-  y1 = warp_sum(y1);
-  y2 = warp_sum(y2);
+// 4-wide loads and stores (16-byte aligned; two 16-byte halves for double)
+__device__ inline void ld4(const float* p, float* v) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ inline void ld4(const double* p, double* v) {
+  double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ inline void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ inline void st4(double* p, const double* v) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
 }
 
-// block-Jacobi: inverse of each 3x3 diagonal block (row-major, 9 per dof)
+// y = row r of K times x, sliced storage (one thread per row; a warp is one
+// slice).  XS = 4: x padded to 4 components per dof; XS = 3: plain 3-vectors.
+template <class T, class V, class A, int XS>
+__device__ inline void sliced_row(int r, Sliced S, const T* __restrict__ K,
+                                  const V* __restrict__ x, A* y) {
+  int s = r >> 5, ln = r & 31;
+  int W = S.w[s];
+  long long b0 = S.base[s];
+  const T* Kb = K + 9 * b0;
+  const int* cb = S.scol + b0;
+  size_t plane = (size_t)32 * W;
+  y[0] = y[1] = y[2] = (A)0;
+  for (int k4 = 0; k4 < (W >> 2); ++k4) {
+    size_t off = ((size_t)k4 * 32 + ln) * 4;
+    int4 c = *reinterpret_cast<const int4*>(cb + off);
+    int cc[4] = {c.x, c.y, c.z, c.w};
+    T v[9][4];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) ld4(Kb + e * plane + off, v[e]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      A x0, x1, x2;
+      if (XS == 4) {
+        V xv[4];
+        ld4(x + 4 * (size_t)cc[j], xv);
+        x0 = (A)xv[0]; x1 = (A)xv[1]; x2 = (A)xv[2];
+      } else {
+        x0 = (A)x[3 * (size_t)cc[j]]; x1 = (A)x[3 * (size_t)cc[j] + 1]; x2 = (A)x[3 * (size_t)cc[j] + 2];
+      }
+      y[0] += (A)v[0][j] * x0 + (A)v[1][j] * x1 + (A)v[2][j] * x2;
+      y[1] += (A)v[3][j] * x0 + (A)v[4][j] * x1 + (A)v[5][j] * x2;
+      y[2] += (A)v[6][j] * x0 + (A)v[7][j] * x1 + (A)v[8][j] * x2;
+    }
+  }
+}
+
+// block-Jacobi: inverse of each 3x3 diagonal block, rows padded to 4 (12 per dof)
 template <class T, class V>
 __global__ void k_block_jacobi(int nd, const int* __restrict__ rp, const int* __restrict__ col,
-                               const T* __restrict__ K, V* Dinv, int* err) {
+                               Sliced S, const T* __restrict__ K, V* Dinv, int* err) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nd) return;
   int s0 = rp[r], nb = rp[r + 1] - s0, k = -1;
@@ -63,8 +98,11 @@ __global__ void k_block_jacobi(int nd, const int* __restrict__ rp, const int* __
     else
       hi = mid - 1;
   }
+  int sl = r >> 5;
+  long long b0 = S.base[sl], slot = k >= 0 ? sliced_slot(b0, r, k) : 0;
   double a[9];
-  for (int e = 0; e < 9; ++e) a[e] = k >= 0 ? (double)K[9 * (size_t)s0 + (size_t)e * nb + k] : (e % 4 == 0);
+  for (int e = 0; e < 9; ++e)
+    a[e] = k >= 0 ? (double)K[sliced_entry(b0, S.w[sl], slot, e)] : (double)(e % 4 == 0);
   double c0 = a[4] * a[8] - a[5] * a[7], c1 = a[5] * a[6] - a[3] * a[8], c2 = a[3] * a[7] - a[4] * a[6];
   double det = a[0] * c0 + a[1] * c1 + a[2] * c2;
   if (!(fabs(det) > 0.0) || !isfinite(det)) {
@@ -72,42 +110,58 @@ __global__ void k_block_jacobi(int nd, const int* __restrict__ rp, const int* __
     det = 1.0;
   }
   double id = 1.0 / det;
-  V* o = Dinv + 9 * (size_t)r;
+  V* o = Dinv + 12 * (size_t)r;
   o[0] = (V)(c0 * id);
   o[1] = (V)((a[2] * a[7] - a[1] * a[8]) * id);
   o[2] = (V)((a[1] * a[5] - a[2] * a[4]) * id);
-  o[3] = (V)(c1 * id);
-  o[4] = (V)((a[0] * a[8] - a[2] * a[6]) * id);
-  o[5] = (V)((a[2] * a[3] - a[0] * a[5]) * id);
-  o[6] = (V)(c2 * id);
-  o[7] = (V)((a[1] * a[6] - a[0] * a[7]) * id);
-  o[8] = (V)((a[0] * a[4] - a[1] * a[3]) * id);
+  o[3] = (V)0;
+  o[4] = (V)(c1 * id);
+  o[5] = (V)((a[0] * a[8] - a[2] * a[6]) * id);
+  o[6] = (V)((a[2] * a[3] - a[0] * a[5]) * id);
+  o[7] = (V)0;
+  o[8] = (V)(c2 * id);
+  o[9] = (V)((a[1] * a[6] - a[0] * a[7]) * id);
+  o[10] = (V)((a[0] * a[4] - a[1] * a[3]) * id);
+  o[11] = (V)0;
+}
+
+template <class V>
+__device__ inline void apply_dinv(const V* __restrict__ Dinv, size_t i, const V* rv, V* zv) {
+  V d0[4], d1[4], d2[4];
+  ld4(Dinv + 12 * i, d0);
+  ld4(Dinv + 12 * i + 4, d1);
+  ld4(Dinv + 12 * i + 8, d2);
+  zv[0] = d0[0] * rv[0] + d0[1] * rv[1] + d0[2] * rv[2];
+  zv[1] = d1[0] * rv[0] + d1[1] * rv[1] + d1[2] * rv[2];
+  zv[2] = d2[0] * rv[0] + d2[1] * rv[1] + d2[2] * rv[2];
+  zv[3] = (V)0;
 }
 
 // ---------------------------------------------------------------- PCG
+// vectors r, z, p, q are padded to 4 components over 32*nslice rows; x keeps
+// the 3-component layout of the caller.
 
 // setup: r = b (free components), x = 0, z = M r, p = z, rz_0, ||b||^2
 template <class V>
-__global__ void k_pcg_init(int nd, const double* __restrict__ b, const int* __restrict__ mask,
+__global__ void k_pcg_init(int nd, int npad, const double* __restrict__ b, const int* __restrict__ mask,
                            const V* __restrict__ Dinv, V* x, V* r, V* z, V* p, Scal* sc) {
   __shared__ double sh[32];
   double rz = 0.0, bb = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x) {
-    int mk = mask[i];
-    V rv[3];
-    for (int c = 0; c < 3; ++c) {
-      rv[c] = ((mk >> c) & 1) ? (V)0 : (V)b[3 * (size_t)i + c];
-      r[3 * (size_t)i + c] = rv[c];
-      x[3 * (size_t)i + c] = (V)0;
-      bb += (double)rv[c] * (double)rv[c];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
+    V rv[4] = {(V)0, (V)0, (V)0, (V)0}, zv[4] = {(V)0, (V)0, (V)0, (V)0};
+    if (i < nd) {
+      int mk = mask[i];
+      for (int c = 0; c < 3; ++c) {
+        rv[c] = ((mk >> c) & 1) ? (V)0 : (V)b[3 * (size_t)i + c];
+        x[3 * (size_t)i + c] = (V)0;
+        bb += (double)rv[c] * (double)rv[c];
+      }
+      apply_dinv(Dinv, i, rv, zv);
+      for (int c = 0; c < 3; ++c) rz += (double)rv[c] * (double)zv[c];
     }
-    const V* D = Dinv + 9 * (size_t)i;
-    for (int c = 0; c < 3; ++c) {
-      V zc = D[3 * c] * rv[0] + D[3 * c + 1] * rv[1] + D[3 * c + 2] * rv[2];
-      z[3 * (size_t)i + c] = zc;
-      p[3 * (size_t)i + c] = zc;
-      rz += (double)rv[c] * (double)zc;
-    }
+    st4(r + 4 * (size_t)i, rv);
+    st4(z + 4 * (size_t)i, zv);
+    st4(p + 4 * (size_t)i, zv);
   }
   rz = block_sum(rz, sh);
   bb = block_sum(bb, sh);
@@ -117,21 +171,22 @@ __global__ void k_pcg_init(int nd, const double* __restrict__ b, const int* __re
   }
 }
 
-// q = K p, pq_0
+// q = K p, pq_0 (one thread per row)
 template <class T, class V>
-__global__ void k_pcg_q0(int nd, const int* __restrict__ rp, const int* __restrict__ col,
-                         const T* __restrict__ K, const V* __restrict__ p, V* q, Scal* sc) {
+__global__ void k_pcg_q0(int nd, int npad, Sliced S, const T* __restrict__ K, const V* __restrict__ p,
+                         V* q, Scal* sc) {
   __shared__ double sh[32];
-  int r = blockIdx.x * SW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
   double part = 0.0;
-  if (r < nd) {
-    V y0, y1, y2;
-    row_dot<T, V, V>(r, lane, rp, col, K, p, y0, y1, y2);
-    if (lane < 3) {
-      V y = lane == 0 ? y0 : (lane == 1 ? y1 : y2);
-      q[3 * (size_t)r + lane] = y;
-      part = (double)y * (double)p[3 * (size_t)r + lane];
-    }
+  if (r < npad) {
+    V y[3];
+    sliced_row<T, V, V, 4>(r, S, K, p, y);
+    V yv[4] = {y[0], y[1], y[2], (V)0};
+    if (r >= nd) yv[0] = yv[1] = yv[2] = (V)0;
+    st4(q + 4 * (size_t)r, yv);
+    V pv[4];
+    ld4(p + 4 * (size_t)r, pv);
+    part = (double)yv[0] * pv[0] + (double)yv[1] * pv[1] + (double)yv[2] * pv[2];
   }
   part = block_sum(part, sh);
   if (threadIdx.x == 0) atomicAdd(&sc->pq[0], part);
@@ -157,20 +212,19 @@ __global__ void k_pcg_a(int nd, int k, const V* __restrict__ Dinv, V* x, V* r, V
   V alpha = (V)(sc->rz[i0] / pq);
   double rz = 0.0, rr = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x) {
-    V rv[3];
+    V pv[4], qv[4], rv[4], zv[4];
+    ld4(p + 4 * (size_t)i, pv);
+    ld4(q + 4 * (size_t)i, qv);
+    ld4(r + 4 * (size_t)i, rv);
     for (int c = 0; c < 3; ++c) {
-      size_t j = 3 * (size_t)i + c;
-      x[j] += alpha * p[j];
-      rv[c] = r[j] - alpha * q[j];
-      r[j] = rv[c];
+      x[3 * (size_t)i + c] += alpha * pv[c];
+      rv[c] -= alpha * qv[c];
       rr += (double)rv[c] * (double)rv[c];
     }
-    const V* D = Dinv + 9 * (size_t)i;
-    for (int c = 0; c < 3; ++c) {
-      V zc = D[3 * c] * rv[0] + D[3 * c + 1] * rv[1] + D[3 * c + 2] * rv[2];
-      z[3 * (size_t)i + c] = zc;
-      rz += (double)rv[c] * (double)zc;
-    }
+    st4(r + 4 * (size_t)i, rv);
+    apply_dinv(Dinv, i, rv, zv);
+    st4(z + 4 * (size_t)i, zv);
+    for (int c = 0; c < 3; ++c) rz += (double)rv[c] * (double)zv[c];
   }
   rz = block_sum(rz, sh);
   rr = block_sum(rr, sh);
@@ -181,10 +235,10 @@ __global__ void k_pcg_a(int nd, int k, const V* __restrict__ Dinv, V* x, V* r, V
 }
 
 // B_k: converged? else beta = rz_{k+1}/rz_k; w = K z; p = z + beta p;
-// q = w + beta q; pq_{k+1}
+// q = w + beta q; pq_{k+1}  (one thread per row)
 template <class T, class V>
-__global__ void k_pcg_b(int nd, int k, const int* __restrict__ rp, const int* __restrict__ col,
-                        const T* __restrict__ K, const V* __restrict__ z, V* p, V* q, Scal* sc) {
+__global__ void k_pcg_b(int nd, int npad, int k, Sliced S, const T* __restrict__ K,
+                        const V* __restrict__ z, V* p, V* q, Scal* sc) {
   __shared__ double sh[32];
   if (sc->done) return;
   int i0 = k % 3, i1 = (k + 1) % 3, i2 = (k + 2) % 3;
@@ -202,19 +256,23 @@ __global__ void k_pcg_b(int nd, int k, const int* __restrict__ rp, const int* __
     sc->rz[i2] = 0.0;
     sc->rr[i2] = 0.0;
   }
-  int r = blockIdx.x * SW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
   double part = 0.0;
-  if (r < nd) {
-    V y0, y1, y2;
-    row_dot<T, V, V>(r, lane, rp, col, K, z, y0, y1, y2);
-    if (lane < 3) {
-      V y = lane == 0 ? y0 : (lane == 1 ? y1 : y2);
-      size_t j = 3 * (size_t)r + lane;
-      V pn = z[j] + beta * p[j];
-      V qn = y + beta * q[j];
-      p[j] = pn;
-      q[j] = qn;
-      part = (double)pn * (double)qn;
+  if (r < npad) {
+    V y[3];
+    sliced_row<T, V, V, 4>(r, S, K, z, y);
+    if (r < nd) {
+      V zv[4], pv[4], qv[4];
+      ld4(z + 4 * (size_t)r, zv);
+      ld4(p + 4 * (size_t)r, pv);
+      ld4(q + 4 * (size_t)r, qv);
+      for (int c = 0; c < 3; ++c) {
+        pv[c] = zv[c] + beta * pv[c];
+        qv[c] = y[c] + beta * qv[c];
+        part += (double)pv[c] * (double)qv[c];
+      }
+      st4(p + 4 * (size_t)r, pv);
+      st4(q + 4 * (size_t)r, qv);
     }
   }
   part = block_sum(part, sh);
@@ -222,28 +280,31 @@ __global__ void k_pcg_b(int nd, int k, const int* __restrict__ rp, const int* __
 }
 
 // ---------------------------------------------------------------- BiCGStab
+// FP64 vectors padded to 4 components over 32*nslice rows; x keeps the
+// caller's 3-component layout.
 
-// generic y = K x (+ optional dots a.y into slot and y.y into slot2).  Skipped
-// once the solve is done, or (check_s) once the half-step residual s has converged.
+// y = K x (+ optional dots a.y into slot and y.y into slot2).  Skipped once
+// the solve is done, or (check_s) once the half-step residual s has converged.
 template <class T>
-__global__ void k_spmv_dot(int nd, const int* __restrict__ rp, const int* __restrict__ col,
-                           const T* __restrict__ K, const double* __restrict__ x, double* y,
-                           const double* __restrict__ a, double* slot, double* slot2,
-                           const Scal* sc, int check_s) {
+__global__ void k_spmv_dot(int nd, int npad, Sliced S, const T* __restrict__ K,
+                           const double* __restrict__ x, double* y, const double* __restrict__ a,
+                           double* slot, double* slot2, const Scal* sc, int check_s) {
   __shared__ double sh[32];
   if (sc->done || (check_s && sc->a[5] <= sc->thr)) return;
-  int r = blockIdx.x * SW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
   double p1 = 0.0, p2 = 0.0;
-  if (r < nd) {
-    double y0, y1, y2;
-    row_dot<T, double, double>(r, lane, rp, col, K, x, y0, y1, y2);
-    if (lane < 3) {
-      double v = lane == 0 ? y0 : (lane == 1 ? y1 : y2);
-      size_t j = 3 * (size_t)r + lane;
-      y[j] = v;
-      if (a) p1 = a[j] * v;
-      p2 = v * v;
+  if (r < npad) {
+    double v[3];
+    sliced_row<T, double, double, 4>(r, S, K, x, v);
+    if (r >= nd) v[0] = v[1] = v[2] = 0.0;
+    double yv[4] = {v[0], v[1], v[2], 0.0};
+    st4(y + 4 * (size_t)r, yv);
+    if (a) {
+      double av[4];
+      ld4(a + 4 * (size_t)r, av);
+      p1 = av[0] * v[0] + av[1] * v[1] + av[2] * v[2];
     }
+    p2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
   }
   if (slot) {
     p1 = block_sum(p1, sh);
@@ -258,41 +319,42 @@ __global__ void k_spmv_dot(int nd, const int* __restrict__ rp, const int* __rest
 // BiCGStab scalar slots in Scal::a: 0 rho, 1 alpha, 2 omega, 3 rho1 (r0.r),
 // 4 r0.v, 5 s.s, 6 t.s, 7 t.t; rr[0] = r.r.  Only k_bicg_rotate (one thread)
 // writes `done`, so no block ever sees it change within a launch.
-__global__ void k_bicg_p(int nd, double* p, const double* __restrict__ r, const double* __restrict__ v,
+__global__ void k_bicg_p(int npad, double* p, const double* __restrict__ r, const double* __restrict__ v,
                          double* ph, const double* __restrict__ Dinv, const Scal* sc) {
   if (sc->done) return;
   double beta = (sc->a[3] / sc->a[0]) * (sc->a[1] / sc->a[2]);
   double om = sc->a[2];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x) {
-    double pv[3];
-    for (int c = 0; c < 3; ++c) {
-      size_t j = 3 * (size_t)i + c;
-      pv[c] = r[j] + beta * (p[j] - om * v[j]);
-      p[j] = pv[c];
-    }
-    const double* D = Dinv + 9 * (size_t)i;
-    for (int c = 0; c < 3; ++c) ph[3 * (size_t)i + c] = D[3 * c] * pv[0] + D[3 * c + 1] * pv[1] + D[3 * c + 2] * pv[2];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
+    double pv[4], rv[4], vv[4], zv[4];
+    ld4(p + 4 * (size_t)i, pv);
+    ld4(r + 4 * (size_t)i, rv);
+    ld4(v + 4 * (size_t)i, vv);
+    for (int c = 0; c < 4; ++c) pv[c] = rv[c] + beta * (pv[c] - om * vv[c]);
+    st4(p + 4 * (size_t)i, pv);
+    apply_dinv(Dinv, i, pv, zv);
+    st4(ph + 4 * (size_t)i, zv);
   }
 }
 
-__global__ void k_bicg_s(int nd, const double* __restrict__ r, const double* __restrict__ v, double* s,
+__global__ void k_bicg_s(int npad, const double* __restrict__ r, const double* __restrict__ v, double* s,
                          double* sh_, const double* __restrict__ Dinv, Scal* sc) {
   __shared__ double sh[32];
   if (sc->done) return;
-  double rv = sc->a[4];
-  if (!(fabs(rv) > 0.0) || !isfinite(rv)) return;  // breakdown, recorded by k_bicg_rotate
-  double alpha = sc->a[3] / rv;
+  double rv0 = sc->a[4];
+  if (!(fabs(rv0) > 0.0) || !isfinite(rv0)) return;  // breakdown, recorded by k_bicg_rotate
+  double alpha = sc->a[3] / rv0;
   double ss = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nd; i += gridDim.x * blockDim.x) {
-    double sv[3];
-    for (int c = 0; c < 3; ++c) {
-      size_t j = 3 * (size_t)i + c;
-      sv[c] = r[j] - alpha * v[j];
-      s[j] = sv[c];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
+    double rv[4], vv[4], sv[4], zv[4];
+    ld4(r + 4 * (size_t)i, rv);
+    ld4(v + 4 * (size_t)i, vv);
+    for (int c = 0; c < 4; ++c) {
+      sv[c] = rv[c] - alpha * vv[c];
       ss += sv[c] * sv[c];
     }
-    const double* D = Dinv + 9 * (size_t)i;
-    for (int c = 0; c < 3; ++c) sh_[3 * (size_t)i + c] = D[3 * c] * sv[0] + D[3 * c + 1] * sv[1] + D[3 * c + 2] * sv[2];
+    st4(s + 4 * (size_t)i, sv);
+    apply_dinv(Dinv, i, sv, zv);
+    st4(sh_ + 4 * (size_t)i, zv);
   }
   ss = block_sum(ss, sh);
   if (threadIdx.x == 0) atomicAdd(&sc->a[5], ss);
@@ -305,27 +367,36 @@ __global__ void k_bicg_check_s(int nd, double* x, const double* __restrict__ ph,
   if (!(fabs(rv) > 0.0) || !isfinite(rv)) return;
   double alpha = sc->a[3] / rv;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * nd; i += gridDim.x * blockDim.x)
-    x[i] += alpha * ph[i];
+    x[i] += alpha * ph[4 * (size_t)(i / 3) + i % 3];
 }
 
-__global__ void k_bicg_x(int nd, double* x, double* r, const double* __restrict__ ph,
+__global__ void k_bicg_x(int nd, int npad, double* x, double* r, const double* __restrict__ ph,
                          const double* __restrict__ shv, const double* __restrict__ s,
                          const double* __restrict__ t, const double* __restrict__ r0, const Scal* sc,
                          double* next_rho1, double* next_rr) {
   __shared__ double sh[32];
   if (sc->done || sc->a[5] <= sc->thr) return;
-  double rv = sc->a[4];
-  if (!(fabs(rv) > 0.0) || !isfinite(rv)) return;
+  double rv0 = sc->a[4];
+  if (!(fabs(rv0) > 0.0) || !isfinite(rv0)) return;
   double tt = sc->a[7];
   double om = tt > 0.0 ? sc->a[6] / tt : 0.0;
-  double alpha = sc->a[3] / rv;
+  double alpha = sc->a[3] / rv0;
   double rr = 0.0, rho1 = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * nd; i += gridDim.x * blockDim.x) {
-    x[i] += alpha * ph[i] + om * shv[i];
-    double rvv = s[i] - om * t[i];
-    r[i] = rvv;
-    rr += rvv * rvv;
-    rho1 += r0[i] * rvv;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
+    double pv[4], zv[4], sv[4], tv[4], r0v[4], rv[4];
+    ld4(ph + 4 * (size_t)i, pv);
+    ld4(shv + 4 * (size_t)i, zv);
+    ld4(s + 4 * (size_t)i, sv);
+    ld4(t + 4 * (size_t)i, tv);
+    ld4(r0 + 4 * (size_t)i, r0v);
+    for (int c = 0; c < 4; ++c) {
+      rv[c] = sv[c] - om * tv[c];
+      rr += rv[c] * rv[c];
+      rho1 += r0v[c] * rv[c];
+    }
+    st4(r + 4 * (size_t)i, rv);
+    if (i < nd)
+      for (int c = 0; c < 3; ++c) x[3 * (size_t)i + c] += alpha * pv[c] + om * zv[c];
   }
   rr = block_sum(rr, sh);
   rho1 = block_sum(rho1, sh);
@@ -371,25 +442,30 @@ __global__ void k_bicg_rotate(Scal* sc, const double* next_rho1, const double* n
 
 // ---------------------------------------------------------------- refinement helpers
 
-// r = b - K x  (FP64 x, FP64 accumulation, any matrix precision), masked; slot += r.r
-template <class T>
-__global__ void k_residual64(int nd, const int* __restrict__ rp, const int* __restrict__ col,
-                             const T* __restrict__ K, const double* __restrict__ x,
-                             const double* __restrict__ b, const int* __restrict__ mask, double* r,
-                             double* slot) {
+// r = b - K x (FP64 x in 3 components, FP64 accumulation, any matrix
+// precision), masked, written in 3 (R3) or 4 components; slot += r.r
+template <class T, int RS>
+__global__ void k_residual64(int nd, int npad, Sliced S, const T* __restrict__ K,
+                             const double* __restrict__ x, const double* __restrict__ b,
+                             const int* __restrict__ mask, double* r, double* slot) {
   __shared__ double sh[32];
-  int rr = blockIdx.x * SW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  int rr = blockIdx.x * blockDim.x + threadIdx.x;
   double part = 0.0;
-  if (rr < nd) {
-    double y0, y1, y2;
-    row_dot<T, double, double>(rr, lane, rp, col, K, x, y0, y1, y2);
-    if (lane < 3) {
-      double y = lane == 0 ? y0 : (lane == 1 ? y1 : y2);
-      size_t j = 3 * (size_t)rr + lane;
-      double v = ((mask[rr] >> lane) & 1) ? 0.0 : b[j] - y;
-      r[j] = v;
-      part = v * v;
+  if (rr < npad) {
+    double y[3];
+    sliced_row<T, double, double, 3>(rr, S, K, x, y);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (rr < nd) {
+      int mk = mask[rr];
+      for (int c = 0; c < 3; ++c) {
+        v[c] = ((mk >> c) & 1) ? 0.0 : b[3 * (size_t)rr + c] - y[c];
+        part += v[c] * v[c];
+      }
     }
+    if (RS == 4)
+      st4(r + 4 * (size_t)rr, v);
+    else if (rr < nd)
+      for (int c = 0; c < 3; ++c) r[3 * (size_t)rr + c] = v[c];
   }
   part = block_sum(part, sh);
   if (threadIdx.x == 0) atomicAdd(slot, part);
@@ -405,21 +481,21 @@ __global__ void k_copy_d(int n, double* y, const double* __restrict__ x) {
   if (i < n) y[i] = x[i];
 }
 
+Sliced sliced_of(const mpm_mesh* m) {
+  return Sliced{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+}
+
 template <class T, class V>
 int run_pcg(mpm_ctx* c, const mpm_mesh* m, const T* K, const V* Dinv, const double* b, V* x,
-            double tol, int maxit, Scal* sc_d, Scal* sc_h, double* relres, int* iters) {
+            double tol, int maxit, Scal* sc_d, Scal* sc_h, double* relres, int* iters, V* r, V* z,
+            V* p, V* q) {
   cudaStream_t st = c->stream;
-  int nd = m->ndof;
-  V* r = grow<V>(c, c->v[4], 3 * (size_t)nd);
-  V* z = grow<V>(c, c->v[5], 3 * (size_t)nd);
-  V* p = grow<V>(c, c->v[6], 3 * (size_t)nd);
-  V* q = grow<V>(c, c->v[7], 3 * (size_t)nd);
-  const int* rp = ptr<int>(m->row_ptr);
-  const int* col = ptr<int>(m->col);
+  int nd = m->ndof, npad = 32 * m->nslice;
+  Sliced S = sliced_of(m);
   MPM_CUDA(cudaMemsetAsync(sc_d, 0, sizeof(Scal), st));
   int vb = 4 * 152;
-  MPM_LAUNCH(k_pcg_init<V><<<vb, 256, 0, st>>>(nd, b, ptr<int>(m->dof_mask), Dinv, x, r, z, p, sc_d));
-  MPM_LAUNCH(k_pcg_q0<T, V><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, p, q, sc_d));
+  MPM_LAUNCH(k_pcg_init<V><<<vb, 256, 0, st>>>(nd, npad, b, ptr<int>(m->dof_mask), Dinv, x, r, z, p, sc_d));
+  MPM_LAUNCH(k_pcg_q0<T, V><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, p, q, sc_d));
   MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
   MPM_CUDA(cudaStreamSynchronize(st));
   double bb = sc_h->bb;
@@ -437,7 +513,7 @@ int run_pcg(mpm_ctx* c, const mpm_mesh* m, const T* K, const V* Dinv, const doub
     int kend = std::min(maxit, k + batch);
     for (; k < kend; ++k) {
       MPM_LAUNCH_P(MPM_PROF_PCG_UPDATE, k_pcg_a<V><<<vb, 256, 0, st>>>(nd, k, Dinv, x, r, z, p, q, sc_d));
-      MPM_LAUNCH_P(MPM_PROF_PCG_SPMV, k_pcg_b<T, V><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, k, rp, col, K, z, p, q, sc_d));
+      MPM_LAUNCH_P(MPM_PROF_PCG_SPMV, k_pcg_b<T, V><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, k, S, K, z, p, q, sc_d));
     }
     MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
@@ -458,27 +534,27 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
                  double* x, double tol, int maxit, Scal* sc_d, Scal* sc_h, double* relres,
                  int* iters) {
   cudaStream_t st = c->stream;
-  int nd = m->ndof, n3 = 3 * nd;
-  double* r = grow<double>(c, c->v[4], n3);
-  double* r0 = grow<double>(c, c->v[5], n3);
-  double* p = grow<double>(c, c->v[6], n3);
-  double* v = grow<double>(c, c->v[7], n3);
-  double* s = grow<double>(c, c->v[8], n3);
-  double* t = grow<double>(c, c->v[9], n3);
-  double* ph = grow<double>(c, c->v[10], n3);
-  double* shv = grow<double>(c, c->v[11], n3);
-  const int* rp = ptr<int>(m->row_ptr);
-  const int* col = ptr<int>(m->col);
+  int nd = m->ndof, npad = 32 * m->nslice;
+  size_t n4 = 4 * (size_t)npad;
+  double* r = grow<double>(c, c->v[4], n4);
+  double* r0 = grow<double>(c, c->v[5], n4);
+  double* p = grow<double>(c, c->v[6], n4);
+  double* v = grow<double>(c, c->v[7], n4);
+  double* s = grow<double>(c, c->v[8], n4);
+  double* t = grow<double>(c, c->v[9], n4);
+  double* ph = grow<double>(c, c->v[10], n4);
+  double* shv = grow<double>(c, c->v[11], n4);
+  Sliced S = sliced_of(m);
   const int* mask = ptr<int>(m->dof_mask);
   MPM_CUDA(cudaMemsetAsync(sc_d, 0, sizeof(Scal), st));
-  MPM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n3, st));
-  MPM_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * n3, st));
-  MPM_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * n3, st));
+  MPM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * 3 * nd, st));
+  MPM_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * n4, st));
+  MPM_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * n4, st));
   double* red = c->d_red + 40;  // rho1 / rr accumulators of the next iteration
   MPM_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
-  // r = r0 = b (free), ||b||^2 via r = b - K*0
-  MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<T><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, x, b, mask, r, &sc_d->bb));
-  MPM_LAUNCH(k_copy_d<<<grid_for(n3, 256), 256, 0, st>>>(n3, r0, r));
+  // r = r0 = b (free components), ||b||^2 via r = b - K*0
+  MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<T, 4><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, x, b, mask, r, &sc_d->bb));
+  MPM_LAUNCH(k_copy_d<<<grid_for((long long)n4, 256), 256, 0, st>>>((int)n4, r0, r));
   MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
   MPM_CUDA(cudaStreamSynchronize(st));
   double bb = sc_h->bb;
@@ -499,14 +575,12 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
     int iend = std::min(maxit, it + batch);
     for (; it < iend; ++it) {
       MPM_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
-      MPM_LAUNCH(k_bicg_p<<<vb, 256, 0, st>>>(nd, p, r, v, ph, Dinv, sc_d));
-      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, ph, v, r0, &sc_d->a[4],
-                                                          nullptr, sc_d, 0));
-      MPM_LAUNCH(k_bicg_s<<<vb, 256, 0, st>>>(nd, r, v, s, shv, Dinv, sc_d));
+      MPM_LAUNCH(k_bicg_p<<<vb, 256, 0, st>>>(npad, p, r, v, ph, Dinv, sc_d));
+      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, ph, v, r0, &sc_d->a[4], nullptr, sc_d, 0));
+      MPM_LAUNCH(k_bicg_s<<<vb, 256, 0, st>>>(npad, r, v, s, shv, Dinv, sc_d));
       MPM_LAUNCH(k_bicg_check_s<<<vb, 256, 0, st>>>(nd, x, ph, sc_d));
-      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, shv, t, s, &sc_d->a[6],
-                                                          &sc_d->a[7], sc_d, 1));
-      MPM_LAUNCH(k_bicg_x<<<vb, 256, 0, st>>>(nd, x, r, ph, shv, s, t, r0, sc_d, red, red + 1));
+      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, shv, t, s, &sc_d->a[6], &sc_d->a[7], sc_d, 1));
+      MPM_LAUNCH(k_bicg_x<<<vb, 256, 0, st>>>(nd, npad, x, r, ph, shv, s, t, r0, sc_d, red, red + 1));
       MPM_LAUNCH(k_bicg_rotate<<<1, 1, 0, st>>>(sc_d, red, red + 1, it + 1));
     }
     MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
@@ -525,9 +599,11 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
            const double* b, double* x, const mpm_solve_params& prm, mpm_solve_stats* out) {
   mpm_mesh* m = const_cast<mpm_mesh*>(mc);
   cudaStream_t st = c->stream;
-  int nd = m->ndof, n3 = 3 * nd;
+  int nd = m->ndof, n3 = 3 * nd, npad = 32 * m->nslice;
+  size_t n4 = 4 * (size_t)npad;
   const int* rp = ptr<int>(m->row_ptr);
   const int* col = ptr<int>(m->col);
+  Sliced S = sliced_of(m);
   int method = prm.method;
   if (method == 0) method = (mat.model == 2 && mat.psi != mat.phi) ? 2 : 1;
   Scal* sc_d = grow<Scal>(c, c->v[20], 1);
@@ -538,16 +614,21 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   out->status = MPM_OK;
   if (prm.precision == MPM_FP64) {
     const double* Kd = (const double*)K;
-    double* Dinv = grow<double>(c, c->v[3], 9 * (size_t)nd);
-    MPM_LAUNCH(k_block_jacobi<double, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, Kd, Dinv, c->d_err));
+    double* Dinv = grow<double>(c, c->v[3], 12 * (size_t)npad);
+    MPM_LAUNCH(k_block_jacobi<double, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, Kd, Dinv, c->d_err));
     int its = 0;
     double rel = 0.0;
-    int s = method == 1 ? run_pcg<double, double>(c, m, Kd, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its)
-                        : run_bicgstab<double>(c, m, Kd, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
+    int sst;
+    if (method == 1)
+      sst = run_pcg<double, double>(c, m, Kd, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its,
+                                    grow<double>(c, c->v[4], n4), grow<double>(c, c->v[5], n4),
+                                    grow<double>(c, c->v[6], n4), grow<double>(c, c->v[7], n4));
+    else
+      sst = run_bicgstab<double>(c, m, Kd, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
     out->iterations = its;
     out->relres = rel;
-    out->status = s;
-    if (s)
+    out->status = sst;
+    if (sst)
       set_error(c, std::string(method == 1 ? "PCG" : "BiCGStab") + " did not reach the tolerance (" +
                        std::to_string(its) + " iterations, relative residual " +
                        std::to_string(rel) + (sc_h->breakdown ? ", breakdown)" : ")"));
@@ -560,11 +641,15 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   float* d32 = grow<float>(c, c->v[13], n3);
   double* slot = c->d_red + 44;
   if (method == 1) {
-    float* Dinv = grow<float>(c, c->v[3], 9 * (size_t)nd);
-    MPM_LAUNCH(k_block_jacobi<float, float><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, Kf, Dinv, c->d_err));
+    float* Dinv = grow<float>(c, c->v[3], 12 * (size_t)npad);
+    MPM_LAUNCH(k_block_jacobi<float, float><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, Kf, Dinv, c->d_err));
+    float* r = grow<float>(c, c->v[4], n4);
+    float* z = grow<float>(c, c->v[5], n4);
+    float* pp = grow<float>(c, c->v[6], n4);
+    float* q = grow<float>(c, c->v[7], n4);
     MPM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n3, st));
     MPM_CUDA(cudaMemsetAsync(slot, 0, sizeof(double), st));
-    MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, Kf, x, b, ptr<int>(m->dof_mask), r64, slot));
+    MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, b, ptr<int>(m->dof_mask), r64, slot));
     MPM_CUDA(cudaMemcpyAsync(c->h_red + 60, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
     double bb = c->h_red[60], rr = bb;
@@ -576,16 +661,17 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
       }
       int its = 0;
       double rel = 0.0;
-      int s = run_pcg<float, float>(c, m, Kf, Dinv, r64, d32, inner, prm.maxit - total, sc_d, sc_h, &rel, &its);
+      int sst = run_pcg<float, float>(c, m, Kf, Dinv, r64, d32, inner, prm.maxit - total, sc_d, sc_h,
+                                      &rel, &its, r, z, pp, q);
       total += its;
       ++rounds;
-      if (s && its == 0) {
+      if (sst && its == 0) {
         status = MPM_ERR_KRYLOV;
         break;
       }
       MPM_LAUNCH(k_axpy_f2d<<<grid_for(n3, 256), 256, 0, st>>>(n3, x, d32));
       MPM_CUDA(cudaMemsetAsync(slot, 0, sizeof(double), st));
-      MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, Kf, x, b, ptr<int>(m->dof_mask), r64, slot));
+      MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, b, ptr<int>(m->dof_mask), r64, slot));
       MPM_CUDA(cudaMemcpyAsync(c->h_red + 60, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
       MPM_CUDA(cudaStreamSynchronize(st));
       rr = c->h_red[60];
@@ -598,15 +684,15 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     return;
   }
   // non-symmetric mixed: BiCGStab on the FP32 matrix with FP64 vectors
-  double* Dinv = grow<double>(c, c->v[3], 9 * (size_t)nd);
-  MPM_LAUNCH(k_block_jacobi<float, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, Kf, Dinv, c->d_err));
+  double* Dinv = grow<double>(c, c->v[3], 12 * (size_t)npad);
+  MPM_LAUNCH(k_block_jacobi<float, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, Kf, Dinv, c->d_err));
   int its = 0;
   double rel = 0.0;
-  int s = run_bicgstab<float>(c, m, Kf, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
+  int sst = run_bicgstab<float>(c, m, Kf, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
   out->iterations = its;
   out->relres = rel;
-  out->status = s;
-  if (s)
+  out->status = sst;
+  if (sst)
     set_error(c, "BiCGStab (FP32 matrix) did not reach the tolerance (" + std::to_string(its) +
                      " iterations, relative residual " + std::to_string(rel) +
                      (sc_h->breakdown ? ", breakdown)" : ")"));
@@ -651,14 +737,15 @@ using namespace mpm;
 extern "C" int mpm_solve_static(mpm_ctx* c, const mpm_mesh* m, const double* K, const double* rhs,
                                 double* x, double tol, int maxit, mpm_solve_stats* stats) {
   if (!c || !m || !K || !rhs || !x || !m->built || !(tol > 0) || maxit <= 0) return MPM_ERR_ARG;
-  int nd = m->ndof;
-  // layout: scalars (256 B), then r, z, p, q (3 nd each) and the 3x3 inverses (9 nd)
-  size_t need = 256 + sizeof(double) * (size_t)nd * (4 * 3 + 9);
+  int nd = m->ndof, npad = 32 * m->nslice;
+  // layout: scalars (256 B), then r, z, p, q (4 per row over the padded rows)
+  // and the 3x3 inverses (12 per row)
+  size_t need = 256 + sizeof(double) * (size_t)npad * (4 * 4 + 12);
+  const size_t max_rows = (kStaticBytes - 256) / (28 * sizeof(double));
   if (need > kStaticBytes) {
     set_error(c, "mpm_solve_static: " + std::to_string(nd) + " dofs need " + std::to_string(need) +
                      " bytes of scratch, the static array holds " + std::to_string(kStaticBytes) +
-                     " (at most " + std::to_string((kStaticBytes - 256) / (21 * sizeof(double))) +
-                     " dofs)");
+                     " (at most " + std::to_string(max_rows / 32 * 32) + " dofs)");
     return MPM_ERR_ARG;
   }
   try {
@@ -666,19 +753,20 @@ extern "C" int mpm_solve_static(mpm_ctx* c, const mpm_mesh* m, const double* K, 
     unsigned char* base = static_scratch(c);
     Scal* sc = (Scal*)base;
     double* r = (double*)(base + 256);
-    double* z = r + 3 * (size_t)nd;
-    double* p = z + 3 * (size_t)nd;
-    double* q = p + 3 * (size_t)nd;
-    double* Dinv = q + 3 * (size_t)nd;
+    double* z = r + 4 * (size_t)npad;
+    double* p = z + 4 * (size_t)npad;
+    double* q = p + 4 * (size_t)npad;
+    double* Dinv = q + 4 * (size_t)npad;
     const int* rp = ptr<int>(m->row_ptr);
     const int* col = ptr<int>(m->col);
+    Sliced S = sliced_of(m);
     // the array keeps the previous call's contents: every vector below is
     // written before it is read, and the scalars start from zero
     MPM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scal), st));
-    MPM_LAUNCH(k_block_jacobi<double, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, K, Dinv, c->d_err));
+    MPM_LAUNCH(k_block_jacobi<double, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, K, Dinv, c->d_err));
     int vb = 4 * 152;
-    MPM_LAUNCH(k_pcg_init<double><<<vb, 256, 0, st>>>(nd, rhs, ptr<int>(m->dof_mask), Dinv, x, r, z, p, sc));
-    MPM_LAUNCH(k_pcg_q0<double, double><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, rp, col, K, p, q, sc));
+    MPM_LAUNCH(k_pcg_init<double><<<vb, 256, 0, st>>>(nd, npad, rhs, ptr<int>(m->dof_mask), Dinv, x, r, z, p, sc));
+    MPM_LAUNCH(k_pcg_q0<double, double><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, p, q, sc));
     Scal* h = (Scal*)(c->h_red + 32);
     MPM_CUDA(cudaMemcpyAsync(h, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
@@ -692,7 +780,7 @@ extern "C" int mpm_solve_static(mpm_ctx* c, const mpm_mesh* m, const double* K, 
         int kend = std::min(maxit, k + 32);
         for (; k < kend; ++k) {
           MPM_LAUNCH(k_pcg_a<double><<<vb, 256, 0, st>>>(nd, k, Dinv, x, r, z, p, q, sc));
-          MPM_LAUNCH(k_pcg_b<double, double><<<grid_for(nd, SW), 32 * SW, 0, st>>>(nd, k, rp, col, K, z, p, q, sc));
+          MPM_LAUNCH(k_pcg_b<double, double><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, k, S, K, z, p, q, sc));
         }
         MPM_CUDA(cudaMemcpyAsync(h, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
         MPM_CUDA(cudaStreamSynchronize(st));

@@ -81,7 +81,7 @@ extern "C" int mpm_step(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* body
     double* dx = grow<double>(c, c->v[17], n3);
     double* trial = grow<double>(c, c->v[18], n3);
     double* rhs = grow<double>(c, c->v[19], n3);
-    void* K = grow_bytes(c, c->v[21], (size_t)m->nnzb * 9 * (prec == MPM_MIXED ? 4 : 8));
+    void* K = grow_bytes(c, c->v[21], (size_t)m->nslot * 9 * (prec == MPM_MIXED ? 4 : 8));
     MPM_CUDA(cudaMemsetAsync(du, 0, sizeof(double) * n3, s));
     AsmOut o{};
     tm.start();

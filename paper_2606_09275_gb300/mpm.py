@@ -27,7 +27,8 @@ EXPORT = dict(leaf_level=0, leaf_anchor=1, node_coord=2, node_hang=3, node_dof=4
 
 SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_octree_build", "mpm_mesh_free",
            "mpm_mesh_counts", "mpm_mesh_export", "mpm_assemble", "mpm_solve", "mpm_step",
-           "mpm_profile", "mpm_profile_read", "mpm_launch_count", "mpm_solve_static"]
+           "mpm_profile", "mpm_profile_read", "mpm_launch_count", "mpm_solve_static",
+           "mpm_blocks_export"]
 
 
 class Domain(C.Structure):
@@ -58,7 +59,7 @@ class PointsT(C.Structure):
 
 class MeshInfo(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("nleaf", "nnode", "nhang", "ndof", "nnzb", "nghost", "npts",
-                                       "maxs", "ncontact", "maxrow")]
+                                       "maxs", "ncontact", "maxrow", "nslot")]
 
 
 class SolveParams(C.Structure):
@@ -113,6 +114,7 @@ def lib():
         L.mpm_step.argtypes = [vp, C.POINTER(Domain), C.POINTER(Rigid), C.POINTER(Adapt),
                                C.POINTER(Material), C.POINTER(PointsT), C.POINTER(StepParams),
                                C.POINTER(StepStats)]
+        L.mpm_blocks_export.argtypes = [vp, vp, vp, i, vp]
         L.mpm_solve_static.argtypes = [vp, vp, vp, vp, vp, d, i, C.POINTER(SolveStats)]
         L.mpm_profile.argtypes = [vp, i]
         L.mpm_profile_read.argtypes = [vp, vp, vp]
@@ -306,11 +308,11 @@ def octree_build(ctx, cfg, points, body_z=None, nosplit=False, mesh=None):
 def assemble(ctx, mesh, cfg, du, load=1.0, precision=FP64, tangent=True, body_z=None):
     """mpm_assemble: residual R (and the tangent values) at the increment du."""
     info = mesh.info()
-    nd, nz = info["ndof"], info["nnzb"]
+    nd, ns = info["ndof"], info["nslot"]
     R = torch.empty(3 * nd, dtype=torch.float64, device=du.device)
     K = None
     if tangent:
-        K = torch.empty(9 * max(nz, 1), dtype=torch.float32 if precision == MIXED else torch.float64,
+        K = torch.empty(9 * max(ns, 1), dtype=torch.float32 if precision == MIXED else torch.float64,
                         device=du.device)
     reac = (C.c_double * 3)()
     norms = (C.c_double * 2)()
@@ -365,15 +367,10 @@ def step(ctx, cfg, points, body_z=None, load=1.0, tol=1e-8, maxit=30, lin_tol=1e
     return out
 
 
-def blocks_from_sliced(values, row_ptr):
-    """Row-sliced block values (layout of include/mpm.h) -> array [nnzb, 3, 3] (host)."""
-    v = np.asarray(values, dtype=np.float64)
-    rp = np.asarray(row_ptr, dtype=np.int64)
-    nz = int(rp[-1])
-    nb = np.diff(rp)
-    row = np.repeat(np.arange(len(nb)), nb)
-    k = np.arange(nz) - rp[row]
-    out = np.empty((nz, 9))
-    for e in range(9):
-        out[:, e] = v[9 * rp[row] + e * nb[row] + k]
-    return out.reshape(nz, 3, 3)
+def blocks(ctx, mesh, K, precision=FP64):
+    """mpm_blocks_export: stiffness values -> host array [nnzb, 3, 3] in CSR order."""
+    nz = mesh.info()["nnzb"]
+    out = np.zeros((max(nz, 1), 3, 3))
+    ctx.check(lib().mpm_blocks_export(ctx.h, mesh.h, _p(K), precision,
+                                      out.ctypes.data_as(C.c_void_p)))
+    return out[:nz]

@@ -124,7 +124,7 @@ def test_assembly_matches_oracle(gpu, case, precision):
     fi = np.linalg.norm(o["fint"])
     assert abs(g["fint_norm"] - fi) <= 1e-10 * fi
     rp, col = om.pattern()
-    Kg = mpm.blocks_from_sliced(g["K"].cpu().numpy().astype(np.float64), rp)
+    Kg = mpm.blocks(ctx, mesh, g["K"], precision)
     Ko = o["K"]
     row = np.repeat(np.arange(nd), np.diff(rp))
     fm = fr.reshape(-1, 3)
