@@ -214,6 +214,46 @@ int mpm_step(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body, const m
              const mpm_material* mat, mpm_points* pts, const mpm_step_params* prm,
              mpm_step_stats* stats);
 
+/* Discrete adjoint of a sequence of load steps (the paper differentiates
+ * nothing; this is the reverse mode of the Sec. 2.4 load step with the Sec. 5
+ * re-adaptation, for inverse problems on the per-point material constants).
+ *
+ * ckpts[n] (n = 0..nsteps-1) is the point state at the START of load step n
+ * (device SoA, before that step's GIMP splits; count and capacity as the
+ * forward saw them) with the body position `body_z` and the load factor
+ * `load` that the step used; ckpts[nsteps-1].pts.capacity must hold every
+ * split of the last step.  The functional is J = w . reaction, the reaction
+ * force on the body at the converged end of the last step, with w =
+ * dJ_dreaction (host [3]).  Every discrete event (octree, splits, supports,
+ * plastic/elastic branch of each point, contact candidates, ghost faces and
+ * their beta) is frozen at its forward value, so J is differentiated where it
+ * is smooth.  Per step, in reverse: rebuild the mesh from the checkpoint,
+ * re-solve Newton (prm: tolerance and Krylov settings of the forward), solve
+ * K mu = dJ/du with the FP64 consistent tangent by block-Jacobi PCG (K is
+ * symmetric for material models 0 and 1; model 2 is rejected with
+ * MPM_ERR_ARG), and run the backward kernels of the residual, the point
+ * update, the contact, the ghost term and the GIMP basis.
+ * Outputs dJ_dE, dJ_dys: device [ckpts[0].pts.count] doubles (overwritten).
+ * The checkpoint arrays are only read.  stats (host, optional) receives the
+ * reaction of the last step, the adjoint Krylov iterations and the time of
+ * the forward re-solves and of the backward work. */
+typedef struct {
+  mpm_points pts;
+  double body_z;
+  double load;
+} mpm_checkpoint;
+
+typedef struct {
+  int status, lin_its;
+  double reaction[3];
+  double ms_forward, ms_backward;
+} mpm_adjoint_stats;
+
+int mpm_adjoint(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body, const mpm_adapt* ad,
+                const mpm_material* mat, const mpm_checkpoint* ckpts, int nsteps,
+                const mpm_step_params* prm, const double* dJ_dreaction, double* dJ_dE,
+                double* dJ_dys, mpm_adjoint_stats* stats);
+
 /* Allocation-free variant of mpm_solve (the paper has no counterpart).  For
  * callers that cannot allocate device memory while they solve -- for example
  * an application whose device memory is already handed out by its own pool,

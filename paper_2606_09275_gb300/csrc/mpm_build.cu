@@ -1209,6 +1209,11 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
   const int* llev = ptr<int>(m->leaf_lev);
 
   // ---- a3: GIMP refinement, in the caller's arrays
+  for (SplitRound& r : m->split_log) {
+    free_buf(c, r.flag);
+    free_buf(c, r.rank);
+  }
+  m->split_log.clear();
   if (!(flags & 1)) {
     for (int round = 0; round < 32; ++round) {
       int P = pts->count;
@@ -1224,6 +1229,14 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
         throw CudaError(MPM_ERR_CAPACITY, "GIMP split needs " + std::to_string(np) +
                                               " points, capacity is " + std::to_string(pts->capacity));
       MPM_LAUNCH(k_split_write<<<grid_for(P, 128), 128, 0, st>>>(P, flag, rank, *pts));
+      if (m->record_splits) {
+        m->split_log.emplace_back();
+        SplitRound& r = m->split_log.back();
+        r.P = P;
+        r.cnt = cnt;
+        MPM_CUDA(cudaMemcpyAsync(grow<int>(c, r.flag, P), flag, sizeof(int) * P, cudaMemcpyDeviceToDevice, st));
+        MPM_CUDA(cudaMemcpyAsync(grow<int>(c, r.rank, P), rank, sizeof(int) * P, cudaMemcpyDeviceToDevice, st));
+      }
       pts->count = (int)np;
       if (round == 31) throw CudaError(MPM_ERR_SUPPORT, "GIMP split did not settle");
     }

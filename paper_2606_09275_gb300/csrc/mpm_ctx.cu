@@ -132,8 +132,14 @@ extern "C" int mpm_create(mpm_ctx** out, void* stream) {
   return MPM_OK;
 }
 
-static void mesh_release(mpm_mesh* m) {
+namespace mpm {
+void mesh_release(mpm_mesh* m) {
   mpm_ctx* c = m->ctx;
+  for (SplitRound& r : m->split_log) {
+    free_buf(c, r.flag);
+    free_buf(c, r.rank);
+  }
+  m->split_log.clear();
   Buf* bufs[] = {&m->leaf_key, &m->leaf_lev, &m->leaf_tmp_key, &m->leaf_tmp_lev, &m->flag,
                  &m->scan, &m->node_key, &m->corner, &m->hang, &m->owner, &m->cptr, &m->cidx,
                  &m->cw, &m->node_dof, &m->dof_node, &m->dof_mask, &m->perm, &m->pcell, &m->px,
@@ -144,6 +150,7 @@ static void mesh_release(mpm_mesh* m) {
                  &m->cb_y0, &m->dF, &m->dFinv, &m->tau, &m->Aalg, &m->gx, &m->slice_w, &m->slice_base, &m->scol};
   for (Buf* b : bufs) free_buf(c, *b);
 }
+}  // namespace mpm
 
 extern "C" int mpm_destroy(mpm_ctx* c) {
   if (!c) return MPM_ERR_ARG;

@@ -61,6 +61,12 @@ struct ProfEv {
   cudaEvent_t a, b;
 };
 
+// one round of GIMP splitting (kept when the mesh records its splits)
+struct SplitRound {
+  int P = 0, cnt = 0;
+  Buf flag, rank;
+};
+
 }  // namespace mpm
 
 // every kernel launch of the library goes through these: the launch count is
@@ -144,6 +150,8 @@ struct mpm_mesh {
   // per-iteration point data
   mpm::Buf dF, dFinv, tau, Aalg, gx;
   int built = 0;
+  bool record_splits = false;
+  std::vector<mpm::SplitRound> split_log;
 };
 
 namespace mpm {
@@ -453,6 +461,14 @@ void blocks_export(mpm_ctx* c, const mpm_mesh* m, const void* K, int precision, 
 // solve (mpm_solve.cu)
 void solve(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const void* K, const double* b,
            double* x, const mpm_solve_params& prm, mpm_solve_stats* st);
+
+// release every buffer of a mesh (mpm_ctx.cu)
+void mesh_release(mpm_mesh* m);
+
+// Newton-Raphson of one load step on a built mesh (mpm_step.cu); *du_out is
+// the converged increment (context scratch)
+void newton(mpm_ctx* c, mpm_mesh* m, const mpm_material* mat, const mpm_rigid& bd,
+            const mpm_step_params* prm, mpm_step_stats& st, double** du_out);
 
 // point update (mpm_step.cu)
 void point_update(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const double* du,

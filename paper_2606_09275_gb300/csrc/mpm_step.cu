@@ -43,36 +43,15 @@ struct Timer {
 }  // namespace
 }  // namespace mpm
 
-using namespace mpm;
+namespace mpm {
 
-extern "C" int mpm_step(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* body,
-                        const mpm_adapt* ad, const mpm_material* mat, mpm_points* pts,
-                        const mpm_step_params* prm, mpm_step_stats* stats) {
-  if (!c || !dom || !ad || !mat || !pts || !prm) return MPM_ERR_ARG;
-  if (!(prm->tol > 0) || prm->maxit < 0 || prm->maxit > 63) {
-    set_error(c, "step: need tol > 0 and 0 <= maxit <= 63");
-    return MPM_ERR_ARG;
-  }
-  mpm_step_stats st{};
-  mpm_rigid nob{};
-  const mpm_rigid& bd = body ? *body : nob;
+// Newton-Raphson with the line search of Sec. 2.4 on a built mesh; leaves the
+// converged increment in du (device [3*ndof], grown in c->v[14]).
+void newton(mpm_ctx* c, mpm_mesh* m, const mpm_material* mat, const mpm_rigid& bd,
+            const mpm_step_params* prm, mpm_step_stats& st, double** du_out) {
+  cudaStream_t s = c->stream;
+  Timer tm(s);
   int status = MPM_OK;
-  try {
-    cudaStream_t s = c->stream;
-    Timer tm(s);
-    if (!c->step_mesh) {
-      c->step_mesh = new mpm_mesh();
-      c->step_mesh->ctx = c;
-    }
-    mpm_mesh* m = c->step_mesh;
-    tm.start();
-    build_mesh(c, m, *dom, bd, *ad, *mat, pts, 0);
-    status = check_device_error(c, "mesh build");
-    st.ms_build = tm.stop();
-    st.npts = m->np;
-    st.ndof = m->ndof;
-    st.nnzb = m->nnzb;
-    if (status) throw CudaError(status, c->err);
     int n3 = 3 * m->ndof;
     int prec = prm->lin.precision;
     double* du = grow<double>(c, c->v[14], n3);
@@ -157,6 +136,43 @@ extern "C" int mpm_step(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* body
       st.newton_its = prm->maxit;
       throw CudaError(MPM_ERR_NEWTON, "Newton iterations exhausted");
     }
+  *du_out = du;
+}
+
+}  // namespace mpm
+
+using namespace mpm;
+
+extern "C" int mpm_step(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* body,
+                        const mpm_adapt* ad, const mpm_material* mat, mpm_points* pts,
+                        const mpm_step_params* prm, mpm_step_stats* stats) {
+  if (!c || !dom || !ad || !mat || !pts || !prm) return MPM_ERR_ARG;
+  if (!(prm->tol > 0) || prm->maxit < 0 || prm->maxit > 63) {
+    set_error(c, "step: need tol > 0 and 0 <= maxit <= 63");
+    return MPM_ERR_ARG;
+  }
+  mpm_step_stats st{};
+  mpm_rigid nob{};
+  const mpm_rigid& bd = body ? *body : nob;
+  int status = MPM_OK;
+  try {
+    cudaStream_t s = c->stream;
+    Timer tm(s);
+    if (!c->step_mesh) {
+      c->step_mesh = new mpm_mesh();
+      c->step_mesh->ctx = c;
+    }
+    mpm_mesh* m = c->step_mesh;
+    tm.start();
+    build_mesh(c, m, *dom, bd, *ad, *mat, pts, 0);
+    status = check_device_error(c, "mesh build");
+    st.ms_build = tm.stop();
+    st.npts = m->np;
+    st.ndof = m->ndof;
+    st.nnzb = m->nnzb;
+    if (status) throw CudaError(status, c->err);
+    double* du = nullptr;
+    newton(c, m, mat, bd, prm, st, &du);
     tm.start();
     point_update(c, m, *mat, du, pts);
     status = check_device_error(c, "point update");

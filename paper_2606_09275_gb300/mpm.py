@@ -28,7 +28,7 @@ EXPORT = dict(leaf_level=0, leaf_anchor=1, node_coord=2, node_hang=3, node_dof=4
 SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_octree_build", "mpm_mesh_free",
            "mpm_mesh_counts", "mpm_mesh_export", "mpm_assemble", "mpm_solve", "mpm_step",
            "mpm_profile", "mpm_profile_read", "mpm_launch_count", "mpm_solve_static",
-           "mpm_blocks_export"]
+           "mpm_blocks_export", "mpm_adjoint"]
 
 
 class Domain(C.Structure):
@@ -84,6 +84,15 @@ class StepStats(C.Structure):
         ("ms_update", C.c_double)]
 
 
+class Checkpoint(C.Structure):
+    _fields_ = [("pts", PointsT), ("body_z", C.c_double), ("load", C.c_double)]
+
+
+class AdjointStats(C.Structure):
+    _fields_ = [("status", C.c_int), ("lin_its", C.c_int), ("reaction", C.c_double * 3),
+                ("ms_forward", C.c_double), ("ms_backward", C.c_double)]
+
+
 _lib = None
 
 
@@ -119,6 +128,9 @@ def lib():
         L.mpm_profile.argtypes = [vp, i]
         L.mpm_profile_read.argtypes = [vp, vp, vp]
         L.mpm_launch_count.argtypes = [vp, vp]
+        L.mpm_adjoint.argtypes = [vp, C.POINTER(Domain), C.POINTER(Rigid), C.POINTER(Adapt),
+                                  C.POINTER(Material), C.POINTER(Checkpoint), i,
+                                  C.POINTER(StepParams), vp, vp, vp, C.POINTER(AdjointStats)]
         _lib = L
     return _lib
 
@@ -235,6 +247,13 @@ class Points:
             t = torch.zeros((cap, w) if w > 1 else (cap,), dtype=torch.float64, device=device)
             t[:n] = torch.as_tensor(np.asarray(pts[k], dtype=np.float64)).reshape(t[:n].shape)
             self.t[k] = t
+
+    def clone(self):
+        """A device copy of the first `count` rows with the same capacity."""
+        c = Points.__new__(Points)
+        c.count, c.capacity = self.count, self.capacity
+        c.t = {k: v.clone() for k, v in self.t.items()}
+        return c
 
     def struct(self):
         s = PointsT()
@@ -374,3 +393,32 @@ def blocks(ctx, mesh, K, precision=FP64):
     ctx.check(lib().mpm_blocks_export(ctx.h, mesh.h, _p(K), precision,
                                       out.ctypes.data_as(C.c_void_p)))
     return out[:nz]
+
+
+def adjoint(ctx, cfg, checkpoints, w, tol=1e-8, maxit=30, lin_tol=1e-10, lin_maxit=20000,
+            method=0, precision=FP64, inner_tol=1e-3):
+    """mpm_adjoint: gradient of w . reaction (end of the last step) with respect
+    to the per-point E and yield stress of the first checkpoint.
+
+    checkpoints: list of (Points, body_z, load), the state at the start of each
+    step; the Newton settings should be those of the forward run.  Returns
+    (dJ_dE, dJ_dys) as device float64 tensors and the statistics."""
+    n = len(checkpoints)
+    arr = (Checkpoint * n)()
+    for k, (pts, bz, ld) in enumerate(checkpoints):
+        arr[k].pts = pts.struct()
+        arr[k].body_z = bz
+        arr[k].load = ld
+    p0 = checkpoints[0][0]
+    dE = torch.zeros(p0.count, dtype=torch.float64, device=p0.t["E"].device)
+    dys = torch.zeros_like(dE)
+    wv = (C.c_double * 3)(*[float(v) for v in w])
+    sp = StepParams(1.0, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol))
+    st_ = AdjointStats()
+    st = lib().mpm_adjoint(ctx.h, C.byref(domain(cfg)), C.byref(rigid(cfg)), C.byref(adapt(cfg)),
+                           C.byref(material(cfg)), arr, n, C.byref(sp),
+                           C.cast(wv, C.c_void_p), _p(dE), _p(dys), C.byref(st_))
+    ctx.check(st)
+    stats = dict(lin_its=st_.lin_its, reaction=np.array(st_.reaction[:]),
+                 ms_forward=st_.ms_forward, ms_backward=st_.ms_backward)
+    return dE, dys, stats
