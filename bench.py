@@ -43,6 +43,7 @@ def args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -174,6 +175,47 @@ def traffic_record(kernel):
     if hashlib.sha256(txt.encode()).hexdigest()[:16] != r["source_sha"]:
         return None  # the kernel changed since the counters were taken
     return r
+
+
+def adjoint_leg(dev):
+    """Cost of the discrete adjoint against the forward run it differentiates:
+    the punch at depth 3 -> 5 with lognormal E, 20 load steps, FP64, gradient
+    of the final vertical punch reaction in every point's E and yield stress."""
+    import torch
+
+    from paper_2606_09275_gb300 import autodiff, inputs, mpm
+    cfg = inputs.workload("adjoint")
+    pts = inputs.make_points(cfg)
+    ctx = mpm.Context()
+    path = autodiff.LoadPath(ctx, cfg, pts, cfg["nsteps"], tol=cfg["newton_tol"],
+                             lin_tol=cfg["lin_tol"], lin_maxit=cfg["lin_maxit"])
+    E = torch.tensor(pts["E"], device=dev)
+    ys = torch.tensor(pts["ys"], device=dev)
+    path.run(E, ys, keep=False)  # warm-up (allocations, module load)
+    stream = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    _, _, st_plain = path.run(E, ys, keep=False)
+    e[1].record(stream)
+    _, ckpts, _ = path.run(E, ys, keep=True)
+    e[2].record(stream)
+    dE, dys, ast = path.gradient(ckpts, (0.0, 0.0, 1.0))
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    n = cfg["nsteps"]
+    fwd, fwd_ck, adj = (e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3]))
+    ctx.close()
+    return {"workload": "adjoint: flat punch into a von Mises block 1x1x0.5 m, depth 3 -> 5, "
+                        "lognormal E (sigma 0.2), %d load steps, FP64, d(reaction_z)/d(E, ys)" % n,
+            "points_last_step": st_plain[-1]["npts"], "dof_last_step": st_plain[-1]["ndof"],
+            "forward_ms_per_step": round(fwd / n, 3),
+            "forward_with_checkpoints_ms_per_step": round(fwd_ck / n, 3),
+            "adjoint_ms_per_step": round(adj / n, 3),
+            "adjoint_over_forward": round(adj / fwd, 3),
+            "adjoint_resolve_ms_per_step": round(ast["ms_forward"] / n, 3),
+            "adjoint_backward_ms_per_step": round(ast["ms_backward"] / n, 3),
+            "adjoint_krylov_its": ast["lin_its"],
+            "forward_krylov_its": int(sum(s["lin_its"] for s in st_plain))}
 
 
 def gpu_main(a):
@@ -336,6 +378,8 @@ def gpu_main(a):
         line["roofline"] = roof
     if mixed["clocks"]:
         line["clocks"] = mixed["clocks"]
+    if not a.no_adjoint:
+        line["adjoint"] = adjoint_leg(dev)
     if not a.no_cpu and world >= 1:
         v, dt, sample, its = run_oracle_sample(a.workload, 1)
         line["cpu_baseline"] = {"value": round(v, 5), "unit": "Newton it/s", "cores": 1,

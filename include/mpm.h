@@ -219,19 +219,23 @@ int mpm_step(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body, const m
  * re-adaptation, for inverse problems on the per-point material constants).
  *
  * ckpts[n] (n = 0..nsteps-1) is the point state at the START of load step n
- * (device SoA, before that step's GIMP splits; count and capacity as the
- * forward saw them) with the body position `body_z` and the load factor
- * `load` that the step used; ckpts[nsteps-1].pts.capacity must hold every
- * split of the last step.  The functional is J = w . reaction, the reaction
+ * (device SoA, before that step's GIMP splits) with the body position
+ * `body_z` and the load factor `load` that the step used.  Only the first
+ * `count` rows of each array are read; the largest `capacity` over the
+ * checkpoints sizes the library's working copy and must hold every split of
+ * every step (MPM_ERR_CAPACITY otherwise).  A rebuilt step whose point count
+ * differs from the next checkpoint's is rejected with MPM_ERR_ARG.  The functional is J = w . reaction, the reaction
  * force on the body at the converged end of the last step, with w =
  * dJ_dreaction (host [3]).  Every discrete event (octree, splits, supports,
  * plastic/elastic branch of each point, contact candidates, ghost faces and
  * their beta) is frozen at its forward value, so J is differentiated where it
  * is smooth.  Per step, in reverse: rebuild the mesh from the checkpoint,
- * re-solve Newton (prm: tolerance and Krylov settings of the forward), solve
- * K mu = dJ/du with the FP64 consistent tangent by block-Jacobi PCG (K is
- * symmetric for material models 0 and 1; model 2 is rejected with
- * MPM_ERR_ARG), and run the backward kernels of the residual, the point
+ * re-solve Newton (prm: the forward's Newton and Krylov settings; prm->load
+ * is ignored, each checkpoint carries its own), solve K mu = dJ/du with the
+ * FP64 consistent tangent by block-Jacobi PCG to prm->lin.tol within
+ * prm->lin.maxit iterations (K is symmetric for material models 0 and 1;
+ * model 2 is rejected with MPM_ERR_ARG), and run the backward kernels of the
+ * residual, the point
  * update, the contact, the ghost term and the GIMP basis.
  * Outputs dJ_dE, dJ_dys: device [ckpts[0].pts.count] doubles (overwritten).
  * The checkpoint arrays are only read.  stats (host, optional) receives the
