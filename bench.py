@@ -28,8 +28,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "indent"
+SOLVER = 3
 CPU_SAMPLE = dict(depth_min=4, depth_max=5, dx_region=2.0 / 32,
                   points=dict(spacing=1.0 / 32, jitter=1.0 / 128))
+PROF_NAMES = ["pcg_update", "pcg_spmv", "tangent_rows", "constitutive", "kinematics", "force",
+              "basis", "residual_rows", "contact", "bicgstab_spmv", "refine_residual", "pattern",
+              "multigrid_vcycle", "multigrid_setup"]
+NPROF = len(PROF_NAMES)
 METRIC = "Newton iters/s at ~1M DOF: FP32+refine vs FP64 (1e-8 residual); HBM roofline %"
 
 
@@ -44,6 +49,10 @@ def args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--method", type=int, default=SOLVER,
+                    help="Krylov method of mpm_solve_params (1 block-Jacobi PCG, 3 multigrid PCG)")
+    ap.add_argument("--mg-reuse", type=int, default=1,
+                    help="method 3: keep the coarse operators across the Newton iterations of a step")
     return ap.parse_args()
 
 
@@ -260,7 +269,8 @@ def gpu_main(a):
             for k in host:
                 host[k].copy_(P.t[k])
         step_kw = dict(load=1.0, tol=cfg["newton_tol"], maxit=cfg["newton_maxit"],
-                       lin_tol=cfg["lin_tol"], lin_maxit=cfg["lin_maxit"], precision=precision)
+                       lin_tol=cfg["lin_tol"], lin_maxit=cfg["lin_maxit"], precision=precision,
+                       method=a.method, mg_reuse=a.mg_reuse)
         for n in range(1, W + 1):
             mpm.step(ctx, cfg, P, body_z=inputs.body_z(cfg, n), **step_kw)
         if e2e:
@@ -296,8 +306,8 @@ def gpu_main(a):
         mpm.lib().mpm_launch_count(ctx.h, mpm.C.byref(nl1))
         prof = None
         if profile:
-            L = (mpm.C.c_longlong * 12)()
-            T = (mpm.C.c_double * 12)()
+            L = (mpm.C.c_longlong * NPROF)()
+            T = (mpm.C.c_double * NPROF)()
             mpm.lib().mpm_profile_read(ctx.h, L, T)
             mpm.lib().mpm_profile(ctx.h, 0)
             prof = {"launches": list(L), "ms": list(T)}
@@ -322,8 +332,7 @@ def gpu_main(a):
     last = mixed["stats"][-1]
     nnzb = np.mean([s["nnzb"] for s in mixed["stats"]])
     nd = np.mean([s["ndof"] for s in mixed["stats"]]) / 3.0
-    names = ["pcg_update", "pcg_spmv", "tangent_rows", "constitutive", "kinematics", "force",
-             "basis", "residual_rows", "contact", "bicgstab_spmv", "refine_residual", "pattern"]
+    names = PROF_NAMES
     prof = mixed["prof"]
     kern = {n: {"launches": prof["launches"][i], "ms": round(prof["ms"][i], 3)}
             for i, n in enumerate(names) if prof["launches"][i]}
@@ -354,10 +363,17 @@ def gpu_main(a):
                                "per cell" % a.workload,
                    "points": last["npts"], "dof": last["ndof"], "nnzb": last["nnzb"],
                    "newton_tol": cfg["newton_tol"], "krylov_tol": cfg["lin_tol"],
+                   "krylov": {1: "block-Jacobi PCG", 3: "multigrid-preconditioned PCG"}.get(
+                       a.method, "method %d" % a.method),
                    "step": "one load step: mesh rebuild + Newton to 1e-8 + point update",
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (stiffness %.2f GB FP32)" % (nnzb * 40 / 1e9)},
         "newton_its": mixed["its"], "krylov_its": sum(s["lin_its"] for s in mixed["stats"]),
+        "solver_only": {
+            "value": round(mixed["its"] * world / (1e-3 * sum(
+                s["ms_assemble"] + s["ms_solve"] for s in mixed["stats"])), 4),
+            "unit": "Newton it/s", "what": "assembly + Krylov solve + line search, rebuild and "
+                                          "point update excluded"},
         "kernels": kern,
         "gpu_launches": mixed["launches"],
     }
@@ -367,6 +383,9 @@ def gpu_main(a):
                         "ms_per_step": round(fp64["ms"] / K, 2), "newton_its": fp64["its"],
                         "krylov_its": sum(s["lin_its"] for s in fp64["stats"])}
         line["mixed_speedup_vs_fp64"] = round(value / v64, 3)
+        line["mixed_time_per_step_speedup_vs_fp64"] = round(fp64["ms"] / mixed["ms"], 3)
+        ev = lambda arm: [(s["npts"], s["ndof"], s["nnzb"]) for s in arm["stats"]]
+        line["events_match_fp64"] = ev(mixed) == ev(fp64)
         line["reaction_mixed_vs_fp64_rel"] = float(
             abs(mixed["stats"][-1]["reaction"][2] - fp64["stats"][-1]["reaction"][2]) /
             abs(fp64["stats"][-1]["reaction"][2]))

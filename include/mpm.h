@@ -102,11 +102,18 @@ typedef struct {
 } mpm_mesh_info;
 
 typedef struct {
-  int method;      /* 0 auto (PCG if symmetric else BiCGStab), 1 PCG, 2 BiCGStab */
+  int method;      /* 0 auto (PCG if symmetric else BiCGStab), 1 PCG, 2 BiCGStab,
+                      3 PCG preconditioned by a geometric multigrid V-cycle
+                      (symmetric tangents only; MPM_ERR_ARG otherwise)       */
   int precision;   /* mpm_precision of the stored matrix and the inner solve     */
   double tol;      /* relative residual target ||b - K x|| <= tol ||b||           */
   int maxit;       /* cap on Krylov iterations (all refinement rounds together)  */
   double inner_tol;/* MPM_MIXED: relative target of each FP32 inner solve        */
+  int mg_reuse;    /* method 3: 0 builds the coarse Galerkin operators from this
+                      K; 1 keeps those of the first method-3 solve since the
+                      mesh was last built (the fine-level smoother is always
+                      rebuilt from K), e.g. across the Newton iterations of one
+                      load step: the V-cycle stays symmetric positive definite */
 } mpm_solve_params;
 
 typedef struct {
@@ -299,7 +306,9 @@ enum {
   MPM_PROF_BICG_SPMV = 9,    /* BiCGStab SpMV                                    */
   MPM_PROF_REFINE = 10,      /* FP64 refinement residual                         */
   MPM_PROF_PATTERN = 11,     /* block pattern rows                               */
-  MPM_PROF_NCLASS = 12
+  MPM_PROF_MG = 12,          /* one multigrid V-cycle (all of its launches)      */
+  MPM_PROF_MG_SETUP = 13,    /* multigrid Galerkin operators and inverses        */
+  MPM_PROF_NCLASS = 14
 };
 int mpm_profile(mpm_ctx* ctx, int enable);
 int mpm_profile_read(mpm_ctx* ctx, long long* launches, double* ms);

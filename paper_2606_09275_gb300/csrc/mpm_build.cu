@@ -1164,6 +1164,7 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
                 const mpm_adapt& ad, const mpm_material& mat, mpm_points* pts, int flags) {
   cudaStream_t st = c->stream;
   m->built = 0;
+  ++m->gen;
   m->dom = dom;
   m->body = body;
   m->ad = ad;

@@ -135,6 +135,7 @@ extern "C" int mpm_create(mpm_ctx** out, void* stream) {
 namespace mpm {
 void mesh_release(mpm_mesh* m) {
   mpm_ctx* c = m->ctx;
+  mg_release(c, m);
   for (SplitRound& r : m->split_log) {
     free_buf(c, r.flag);
     free_buf(c, r.rank);

@@ -67,6 +67,39 @@ struct SplitRound {
   Buf flag, rank;
 };
 
+// device scalars of one Krylov solve: rotating slots k % 3 of r.z, p.q, r.r,
+// ||b||^2 and the stopping threshold; the solve is over once `done` is set
+struct Scal {
+  double rz[3], pq[3], rr[3];
+  double bb, thr;    // ||b||^2 and tol^2 ||b||^2
+  double a[8];       // BiCGStab scalars
+  int done, iters, breakdown, pad;
+};
+
+// one coarse level of the geometric multigrid: the active nodes of the uniform
+// grid of depth d, a Galerkin operator stored per stencil offset (a cube of
+// side 2R+1 around each node), the smoother's 3x3 inverses and level vectors
+struct MGLevel {
+  int d = 0, n1 = 0;           // depth, nodes per axis (2^d + 1)
+  int nrow = 0, npad = 0;      // active nodes, padded to 32
+  int R = 2, S = 125;          // stencil radius and size (2R+1)^3
+  Buf gid, xyz, mask;          // grid node -> row (-1), row -> packed coords, fixed bits
+  Buf A, Dinv, b, x, r;        // operator [S*9][npad], inverses [npad][12], vectors [npad][4]
+};
+
+struct MGData {
+  long long gen = -1;          // mesh build the structure belongs to
+  long long num_gen = -1;      // mesh build of the last coarse operators
+  int prec = -1;               // value precision of the coarse operators
+  int nlev = 0;                // coarse levels (the last one is solved densely)
+  MGLevel lev[8];
+  Buf p_idx, p_w;              // fine dof -> up to 8 level-1 rows and weights
+  Buf pt_ptr, pt_idx, pt_w;    // level-1 row -> fine dofs and weights
+  Buf fDinv, fx, fr, fb;       // fine smoother inverses, fine V-cycle vectors
+  Buf cinv;                    // dense inverse of the coarsest operator
+  int n3c = 0;
+};
+
 }  // namespace mpm
 
 // every kernel launch of the library goes through these: the launch count is
@@ -150,6 +183,8 @@ struct mpm_mesh {
   // per-iteration point data
   mpm::Buf dF, dFinv, tau, Aalg, gx;
   int built = 0;
+  long long gen = 0;                    // incremented by every build
+  mpm::MGData* mg = nullptr;            // multigrid structure (built on first use)
   bool record_splits = false;
   std::vector<mpm::SplitRound> split_log;
 };
@@ -461,6 +496,18 @@ void blocks_export(mpm_ctx* c, const mpm_mesh* m, const void* K, int precision, 
 // solve (mpm_solve.cu)
 void solve(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const void* K, const double* b,
            double* x, const mpm_solve_params& prm, mpm_solve_stats* st);
+
+// geometric multigrid preconditioner (mpm_mg.cu): structure for the current
+// mesh build and Galerkin operators for the stiffness K (T = float or double);
+// mg_apply computes z = B r (one V-cycle).  `sk`/`k` let a PCG loop skip the
+// work once its residual has converged (slot (k+1) % 3 of rr).  rz (device,
+// may be null) receives += r.z.
+template <class T>
+void mg_setup(mpm_ctx* c, mpm_mesh* m, const T* K, bool reuse);
+template <class T>
+void mg_apply(mpm_ctx* c, const mpm_mesh* m, const T* K, const T* r, T* z, const Scal* sk, int k,
+              double* rz);
+void mg_release(mpm_ctx* c, mpm_mesh* m);
 
 // release every buffer of a mesh (mpm_ctx.cu)
 void mesh_release(mpm_mesh* m);

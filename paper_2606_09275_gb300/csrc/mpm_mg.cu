@@ -1,0 +1,899 @@
+// Geometric multigrid preconditioner for the symmetric stiffness: a V-cycle
+// used inside PCG, the multilevel counterpart of the Jacobi-type
+// preconditioning that Sec. 1 names for Krylov solvers.
+//
+// Levels: the octree dofs (fine), then the active nodes of uniform grids of
+// depth d1 > d2 > ... > 1.  d1 is at most the coarsest leaf depth, so every
+// coarse trilinear field lies in the fine octree space and the prolongation P
+// is plain trilinear interpolation at the fine node positions (components
+// fixed by a Dirichlet plane are dropped from P).  Coarse operators are
+// Galerkin products A_c = P^T A P, gathered row by row in shared memory (no
+// global atomics) and stored per stencil offset on the uniform grid.  The
+// smoother is l1 block Jacobi, M = D + diag(sum over the row's off-diagonal
+// |entries|), which is convergent without eigenvalue estimates; one sweep
+// before and one after the coarse correction, so the V-cycle is symmetric
+// positive definite.  The depth-1 level is solved with a dense inverse.
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "mpm_internal.cuh"
+#include "mpm_sliced.cuh"
+
+namespace mpm {
+namespace {
+
+constexpr int MGW = 4;  // warps per block of the warp-per-row level kernels
+
+// packed grid coordinates (coarse grids have at most 2^7 + 1 nodes per axis)
+__host__ __device__ inline int pack3(int x, int y, int z) { return x | (y << 10) | (z << 20); }
+__host__ __device__ inline void unpack3(int v, int* c) {
+  c[0] = v & 1023;
+  c[1] = (v >> 10) & 1023;
+  c[2] = v >> 20;
+}
+
+__device__ inline bool skip(const Scal* sk, int k) {
+  return sk && (sk->done || sk->rr[(k + 1) % 3] <= sk->thr);
+}
+
+// ---------------------------------------------------------------- structure
+
+// level-1 interpolation weights of every fine dof; marks the coarse nodes used
+__global__ void k_mg_p1(int nd, int D, int d1, const int* __restrict__ dof_node,
+                        const uint64_t* __restrict__ nkey, const int* __restrict__ mask, int* pidx,
+                        float* pw, int* active, int* freeb) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  int X[3];
+  demorton(nkey[dof_node[i]], X);
+  int sh = D - d1, n = 1 << d1, n1 = n + 1;
+  int cc[3];
+  float t[3];
+  for (int d = 0; d < 3; ++d) {
+    cc[d] = min(X[d] >> sh, n - 1);
+    t[d] = (float)(X[d] - (cc[d] << sh)) / (float)(1 << sh);
+  }
+  int fr = 7 & ~mask[i];
+  int q = 0;
+  for (int c = 0; c < 8; ++c) {
+    float w = 1.0f;
+    for (int d = 0; d < 3; ++d) w *= ((c >> d) & 1) ? t[d] : 1.0f - t[d];
+    if (w == 0.0f) continue;
+    int lin = (cc[0] + (c & 1)) + n1 * ((cc[1] + ((c >> 1) & 1)) + n1 * (cc[2] + ((c >> 2) & 1)));
+    pidx[8 * (size_t)i + q] = lin;
+    pw[8 * (size_t)i + q] = w;
+    ++q;
+    active[lin] = 1;
+    if (fr) atomicOr(freeb + lin, fr);
+  }
+  for (; q < 8; ++q) pidx[8 * (size_t)i + q] = -1;
+}
+
+// coarse nodes used by the interpolation from the active rows of a uniform level
+__global__ void k_mg_mark_u(int nrow, const int* __restrict__ xyz, const int* __restrict__ mask,
+                            int n1c, int* active, int* freeb) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrow) return;
+  int c[3];
+  unpack3(xyz[i], c);
+  int fr = 7 & ~mask[i];
+  int lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = c[d] >> 1;
+    hi[d] = (c[d] + 1) >> 1;
+  }
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x) {
+        int lin = x + n1c * (y + n1c * z);
+        active[lin] = 1;
+        if (fr) atomicOr(freeb + lin, fr);
+      }
+}
+
+// compact numbering of the active grid nodes
+__global__ void k_mg_compact(int ng, int n1, const int* __restrict__ active,
+                             const int* __restrict__ scan, const int* __restrict__ freeb, int* gid,
+                             int* xyz, int* mask) {
+  int lin = blockIdx.x * blockDim.x + threadIdx.x;
+  if (lin >= ng) return;
+  if (!active[lin]) {
+    gid[lin] = -1;
+    return;
+  }
+  int r = scan[lin];
+  gid[lin] = r;
+  int x = lin % n1, y = (lin / n1) % n1, z = lin / (n1 * n1);
+  xyz[r] = pack3(x, y, z);
+  mask[r] = 7 & ~freeb[lin];
+}
+
+// fine -> level-1 entries: grid ids to rows; keys (row << 32 | entry) of P^T
+__global__ void k_mg_p1_rows(int nd, const int* __restrict__ gid, int* pidx, uint64_t* keys) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 8LL * nd) return;
+  int lin = pidx[e];
+  if (lin < 0) {
+    keys[e] = ~0ULL;
+    return;
+  }
+  int r = gid[lin];
+  pidx[e] = r;
+  keys[e] = ((uint64_t)(uint32_t)r << 32) | (uint64_t)e;
+}
+
+__global__ void k_mg_pt(long long n, const uint64_t* __restrict__ keys, int nrow, int* ptr,
+                        int* idx) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t r = (uint32_t)(keys[i] >> 32);
+  if (r >= (uint32_t)nrow) return;
+  idx[i] = (int)(uint32_t)keys[i];
+  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != r) ptr[r] = (int)i;
+  if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != r) ptr[r + 1] = (int)(i + 1);
+}
+
+// largest level-1 cell distance between the two dofs of any stored block
+__global__ void k_mg_reach(int nd, int D, int d1, const int* __restrict__ rp,
+                           const int* __restrict__ col, const int* __restrict__ dof_node,
+                           const uint64_t* __restrict__ nkey, int* reach) {
+  int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= nd) return;
+  int sh = D - d1, n = 1 << d1;
+  int X[3], ci[3];
+  demorton(nkey[dof_node[r]], X);
+  for (int d = 0; d < 3; ++d) ci[d] = min(X[d] >> sh, n - 1);
+  int m = 0;
+  for (int s = rp[r] + lane; s < rp[r + 1]; s += 32) {
+    int Y[3];
+    demorton(nkey[dof_node[col[s]]], Y);
+    for (int d = 0; d < 3; ++d) m = max(m, abs(min(Y[d] >> sh, n - 1) - ci[d]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0 && m > 0) atomicMax(reach, m);
+}
+
+// ---------------------------------------------------------------- Galerkin products
+
+__device__ inline int stencil_index(const int* cb, const int* ca, int R) {
+  int S1 = 2 * R + 1;
+  int dx = cb[0] - ca[0] + R, dy = cb[1] - ca[1] + R, dz = cb[2] - ca[2] + R;
+  if ((unsigned)dx >= (unsigned)S1 || (unsigned)dy >= (unsigned)S1 || (unsigned)dz >= (unsigned)S1)
+    return -1;
+  return dx + S1 * (dy + S1 * dz);
+}
+
+// write one accumulated row (Dirichlet components: identity on the diagonal)
+template <class T>
+__device__ inline void write_row(int a, int S, int R, int cm, const T* acc, T* A, int lane) {
+  int S1 = 2 * R + 1, center = R + S1 * (R + S1 * R);
+  T* row = A + (size_t)a * S * 9;
+  for (int u = lane; u < 9 * S; u += 32) {
+    int o = u / 9, e = u - 9 * o, ci = e / 3, ck = e - 3 * ci;
+    T v = acc[u];
+    if (((cm >> ci) & 1) || ((cm >> ck) & 1)) v = (o == center && ci == ck) ? (T)1 : (T)0;
+    row[u] = v;
+  }
+}
+
+// level 1: one warp per coarse row a; sum over fine dofs i with P_ia != 0 of
+// their block rows, each block spread to the coarse columns of its dof j.
+// Lanes take different fine rows i (consecutive columns of one row share
+// their coarse targets, which would serialise the shared-memory atomics).
+template <class T>
+__global__ void k_mg_rap1(int nrow, int R, int S, const int* __restrict__ pt_ptr,
+                          const int* __restrict__ pt_idx, const float* __restrict__ pw,
+                          const int* __restrict__ pidx, const int* __restrict__ fmask,
+                          const int* __restrict__ rp, const int* __restrict__ col, Sliced SK,
+                          const T* __restrict__ K, const int* __restrict__ xyz,
+                          const int* __restrict__ cmask, T* A, int* err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* acc = (T*)smraw + (size_t)wi * 9 * S;
+  int a = blockIdx.x * (blockDim.x >> 5) + wi;
+  if (a >= nrow) return;
+  for (int u = lane; u < 9 * S; u += 32) acc[u] = (T)0;
+  __syncwarp();
+  int ca[3];
+  unpack3(xyz[a], ca);
+  for (int t = pt_ptr[a] + lane; t < pt_ptr[a + 1]; t += 32) {
+    int e8 = pt_idx[t];
+    int i = e8 >> 3;
+    T wi_ = (T)pw[e8];
+    int mi = fmask[i];
+    int s0 = rp[i], nb = rp[i + 1] - s0;
+    int sl = i >> 5, W = SK.w[sl];
+    long long b0 = SK.base[sl];
+    for (int idx = 0; idx < nb; ++idx) {
+      int j = col[s0 + idx];
+      int mj = fmask[j];
+      long long slot = sliced_slot(b0, i, idx);
+      T v[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        int ci = e / 3, ck = e - 3 * (e / 3);
+        v[e] = (((mi >> ci) & 1) || ((mj >> ck) & 1)) ? (T)0 : K[sliced_entry(b0, W, slot, e)];
+      }
+      for (int q = 0; q < 8; ++q) {
+        int b = pidx[8 * (size_t)j + q];
+        if (b < 0) break;
+        T f = wi_ * (T)pw[8 * (size_t)j + q];
+        int cb[3];
+        unpack3(xyz[b], cb);
+        int o = stencil_index(cb, ca, R);
+        if (o < 0) {
+          atomicOr(err, EB_ROW);
+          continue;
+        }
+#pragma unroll
+        for (int e = 0; e < 9; ++e) atomicAdd(acc + 9 * o + e, f * v[e]);
+      }
+    }
+  }
+  __syncwarp();
+  write_row<T>(a, S, R, cmask[a], acc, A, lane);
+}
+
+// uniform level -> next coarser: fine rows 2C + delta (weights
+// prod(1 - |delta|/2)); lanes take different fine rows
+template <class T>
+__global__ void k_mg_rapu(int nrow, int Rc, int Sc, const int* __restrict__ xyz_c,
+                          const int* __restrict__ cmask, int Rf, int Sf, int n1f,
+                          const int* __restrict__ gid_f, const int* __restrict__ xyz_f,
+                          const int* __restrict__ fmask, const T* __restrict__ Af, T* A, int* err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* acc = (T*)smraw + (size_t)wi * 9 * Sc;
+  int a = blockIdx.x * (blockDim.x >> 5) + wi;
+  if (a >= nrow) return;
+  for (int u = lane; u < 9 * Sc; u += 32) acc[u] = (T)0;
+  __syncwarp();
+  int ca[3];
+  unpack3(xyz_c[a], ca);
+  int S1f = 2 * Rf + 1;
+  for (int dl = lane; dl < 27; dl += 32) {
+    int del[3] = {dl % 3 - 1, (dl / 3) % 3 - 1, dl / 9 - 1};
+    int fi[3];
+    bool in = true;
+    for (int d = 0; d < 3; ++d) {
+      fi[d] = 2 * ca[d] + del[d];
+      in = in && fi[d] >= 0 && fi[d] < n1f;
+    }
+    if (!in) continue;
+    int i = gid_f[fi[0] + n1f * (fi[1] + n1f * fi[2])];
+    if (i < 0) continue;
+    T wi_ = (T)1;
+    for (int d = 0; d < 3; ++d) wi_ *= del[d] ? (T)0.5 : (T)1;
+    int mi = fmask[i];
+    const T* row = Af + (size_t)i * Sf * 9;
+    for (int of = 0; of < Sf; ++of) {
+      int fj[3] = {fi[0] + of % S1f - Rf, fi[1] + (of / S1f) % S1f - Rf, fi[2] + of / (S1f * S1f) - Rf};
+      if (fj[0] < 0 || fj[1] < 0 || fj[2] < 0 || fj[0] >= n1f || fj[1] >= n1f || fj[2] >= n1f) continue;
+      int j = gid_f[fj[0] + n1f * (fj[1] + n1f * fj[2])];
+      if (j < 0) continue;
+      int mj = fmask[j];
+      T v[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        int ci = e / 3, ck = e - 3 * (e / 3);
+        v[e] = (((mi >> ci) & 1) || ((mj >> ck) & 1)) ? (T)0 : row[9 * of + e];
+      }
+      int lo[3], hi[3];
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = fj[d] >> 1;
+        hi[d] = (fj[d] + 1) >> 1;
+      }
+      for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+          for (int x = lo[0]; x <= hi[0]; ++x) {
+            T f = wi_;
+            if (lo[0] != hi[0]) f *= (T)0.5;
+            if (lo[1] != hi[1]) f *= (T)0.5;
+            if (lo[2] != hi[2]) f *= (T)0.5;
+            int cb[3] = {x, y, z};
+            int o = stencil_index(cb, ca, Rc);
+            if (o < 0) {
+              atomicOr(err, EB_ROW);
+              continue;
+            }
+#pragma unroll
+            for (int e = 0; e < 9; ++e) atomicAdd(acc + 9 * o + e, f * v[e]);
+          }
+    }
+  }
+  __syncwarp();
+  write_row<T>(a, Sc, Rc, cmask[a], acc, A, lane);
+}
+
+// ---------------------------------------------------------------- smoother inverses
+
+// inverse of D + diag(l1 sums of the off-diagonal blocks), 12 per row
+template <class T>
+__device__ inline void store_inv(const double* a, T* o, int* err) {
+  double c0 = a[4] * a[8] - a[5] * a[7], c1 = a[5] * a[6] - a[3] * a[8], c2 = a[3] * a[7] - a[4] * a[6];
+  double det = a[0] * c0 + a[1] * c1 + a[2] * c2;
+  if (!(fabs(det) > 0.0) || !isfinite(det)) {
+    atomicOr(err, EB_KRYLOV);
+    det = 1.0;
+  }
+  double id = 1.0 / det;
+  o[0] = (T)(c0 * id);
+  o[1] = (T)((a[2] * a[7] - a[1] * a[8]) * id);
+  o[2] = (T)((a[1] * a[5] - a[2] * a[4]) * id);
+  o[3] = (T)0;
+  o[4] = (T)(c1 * id);
+  o[5] = (T)((a[0] * a[8] - a[2] * a[6]) * id);
+  o[6] = (T)((a[2] * a[3] - a[0] * a[5]) * id);
+  o[7] = (T)0;
+  o[8] = (T)(c2 * id);
+  o[9] = (T)((a[1] * a[6] - a[0] * a[7]) * id);
+  o[10] = (T)((a[0] * a[4] - a[1] * a[3]) * id);
+  o[11] = (T)0;
+}
+
+template <class T>
+__global__ void k_mg_dinv_fine(int nd, int npad, Sliced SK, const T* __restrict__ K, T* Dinv, int* err) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= npad) return;
+  T* o = Dinv + 12 * (size_t)r;
+  if (r >= nd) {
+    for (int e = 0; e < 12; ++e) o[e] = (T)0;
+    return;
+  }
+  int sl = r >> 5, W = SK.w[sl];
+  long long b0 = SK.base[sl];
+  double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, s[3] = {0, 0, 0};
+  for (int idx = 0; idx < W; ++idx) {
+    long long slot = sliced_slot(b0, r, idx);
+    int c = SK.scol[slot];
+    double v[9];
+    for (int e = 0; e < 9; ++e) v[e] = (double)K[sliced_entry(b0, W, slot, e)];
+    if (c == r) {
+      for (int e = 0; e < 9; ++e) a[e] += v[e];
+    } else {
+      for (int e = 0; e < 9; ++e) s[e / 3] += fabs(v[e]);
+    }
+  }
+  for (int d = 0; d < 3; ++d) a[4 * d] += s[d];
+  store_inv<T>(a, o, err);
+}
+
+template <class T>
+__global__ void k_mg_dinv(int nrow, int npad, int S, int R, const T* __restrict__ A, T* Dinv, int* err) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= npad) return;
+  T* o = Dinv + 12 * (size_t)r;
+  if (r >= nrow) {
+    for (int e = 0; e < 12; ++e) o[e] = (T)0;
+    return;
+  }
+  int S1 = 2 * R + 1, center = R + S1 * (R + S1 * R);
+  const T* row = A + (size_t)r * S * 9;
+  double a[9], s[3] = {0, 0, 0};
+  for (int e = 0; e < 9; ++e) a[e] = (double)row[9 * center + e];
+  for (int oo = 0; oo < S; ++oo) {
+    if (oo == center) continue;
+    for (int e = 0; e < 9; ++e) s[e / 3] += fabs((double)row[9 * oo + e]);
+  }
+  for (int d = 0; d < 3; ++d) a[4 * d] += s[d];
+  store_inv<T>(a, o, err);
+}
+
+// dense inverse of the coarsest operator (one block; n3 = 3 nrow <= 81),
+// Gauss-Jordan without pivoting on the symmetric positive semi-definite
+// matrix, in FP64.  A pivot below 1e-12 of the largest diagonal entry marks a
+// direction the coarse space does not resolve (interpolation columns that
+// coincide on a thin active region): its row and column are dropped, which
+// leaves the pseudo-inverse on the rest and keeps the V-cycle positive
+// definite (the smoother part alone is).
+template <class T>
+__global__ void k_mg_dense(int nrow, int S, int R, const int* __restrict__ xyz, int n1,
+                           const int* __restrict__ gid, const T* __restrict__ A, T* Cinv) {
+  extern __shared__ double M[];  // [n3][2 n3]
+  __shared__ double dmax;
+  int n3 = 3 * nrow, w2 = 2 * n3;
+  for (int u = threadIdx.x; u < n3 * w2; u += blockDim.x) M[u] = 0.0;
+  __syncthreads();
+  int S1 = 2 * R + 1;
+  for (int u = threadIdx.x; u < nrow * S; u += blockDim.x) {
+    int a = u / S, o = u - S * a;
+    int ca[3];
+    unpack3(xyz[a], ca);
+    int cb[3] = {ca[0] + o % S1 - R, ca[1] + (o / S1) % S1 - R, ca[2] + o / (S1 * S1) - R};
+    if (cb[0] < 0 || cb[1] < 0 || cb[2] < 0 || cb[0] >= n1 || cb[1] >= n1 || cb[2] >= n1) continue;
+    int b = gid[cb[0] + n1 * (cb[1] + n1 * cb[2])];
+    if (b < 0) continue;
+    const T* blk = A + ((size_t)a * S + o) * 9;
+    for (int e = 0; e < 9; ++e) M[(3 * a + e / 3) * w2 + 3 * b + e % 3] = (double)blk[e];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double d = 0.0;
+    for (int i = 0; i < n3; ++i) d = fmax(d, M[i * w2 + i]);
+    dmax = d;
+  }
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) M[i * w2 + n3 + i] = 1.0;
+  __syncthreads();
+  double tiny = 1e-12 * dmax;
+  for (int k = 0; k < n3; ++k) {
+    double piv = M[k * w2 + k];
+    __syncthreads();
+    if (!(piv > tiny) || !isfinite(piv)) {
+      // drop direction k: zero its row and column in both halves
+      for (int j = threadIdx.x; j < w2; j += blockDim.x) M[k * w2 + j] = 0.0;
+      for (int i = threadIdx.x; i < n3; i += blockDim.x) {
+        M[i * w2 + k] = 0.0;
+        M[i * w2 + n3 + k] = 0.0;
+      }
+      __syncthreads();
+      continue;
+    }
+    for (int j = threadIdx.x; j < w2; j += blockDim.x) M[k * w2 + j] /= piv;
+    __syncthreads();
+    for (int u = threadIdx.x; u < n3 * w2; u += blockDim.x) {
+      int i = u / w2, j = u - w2 * i;
+      if (i == k || j == k) continue;
+      M[u] -= M[i * w2 + k] * M[k * w2 + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n3; i += blockDim.x)
+      if (i != k) M[i * w2 + k] = 0.0;
+    __syncthreads();
+  }
+  for (int u = threadIdx.x; u < n3 * n3; u += blockDim.x) {
+    int i = u / n3, j = u - n3 * i;
+    Cinv[u] = (T)M[i * w2 + n3 + j];
+  }
+}
+
+// ---------------------------------------------------------------- V-cycle kernels
+
+// x = Dinv b (rows padded to 4 components)
+template <class T>
+__global__ void k_mg_jac0(int n, const T* __restrict__ Dinv, const T* __restrict__ b, T* x,
+                          const Scal* sk, int k) {
+  if (skip(sk, k)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T bv[4], xv[4];
+  ld4(b + 4 * (size_t)i, bv);
+  apply_dinv(Dinv, i, bv, xv);
+  st4(x + 4 * (size_t)i, xv);
+}
+
+// fine level: r = b - K x (MODE 0), or xo = x + Dinv (b - K x) with r.z += b.xo (MODE 1)
+template <class T, int MODE>
+__global__ void k_mg_fine(int nd, int npad, Sliced SK, const T* __restrict__ K, const T* __restrict__ b,
+                          const T* __restrict__ x, const T* __restrict__ Dinv, T* out, double* rz,
+                          const Scal* sk, int k) {
+  __shared__ double sh[32];
+  if (skip(sk, k)) return;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  double part = 0.0;
+  if (r < npad) {
+    T y[3];
+    sliced_row<T, T, T, 4>(r, SK, K, x, y);
+    T bv[4], res[4];
+    ld4(b + 4 * (size_t)r, bv);
+    for (int c = 0; c < 3; ++c) res[c] = r < nd ? bv[c] - y[c] : (T)0;
+    res[3] = (T)0;
+    if (MODE == 0) {
+      st4(out + 4 * (size_t)r, res);
+    } else {
+      T xv[4], d[4];
+      ld4(x + 4 * (size_t)r, xv);
+      apply_dinv(Dinv, r, res, d);
+      for (int c = 0; c < 3; ++c) xv[c] = r < nd ? xv[c] + d[c] : (T)0;
+      xv[3] = (T)0;
+      st4(out + 4 * (size_t)r, xv);
+      for (int c = 0; c < 3; ++c) part += (double)bv[c] * (double)xv[c];
+    }
+  }
+  if (MODE == 1 && rz) {
+    part = block_sum(part, sh);
+    if (threadIdx.x == 0) atomicAdd(rz, part);
+  }
+}
+
+// uniform level (warp per row): r = b - A x (MODE 0) or xo = x + Dinv (b - A x) (MODE 1)
+template <class T, int MODE>
+__global__ void k_mg_lvl(int nrow, int S, int R, int n1, const int* __restrict__ xyz,
+                         const int* __restrict__ gid, const T* __restrict__ A, const T* __restrict__ b,
+                         const T* __restrict__ x, const T* __restrict__ Dinv, T* out, const Scal* sk,
+                         int k) {
+  if (skip(sk, k)) return;
+  int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (a >= nrow) return;
+  int ca[3];
+  unpack3(xyz[a], ca);
+  int S1 = 2 * R + 1;
+  const T* row = A + (size_t)a * S * 9;
+  T y0 = 0, y1 = 0, y2 = 0;
+  for (int o = lane; o < S; o += 32) {
+    int cb[3] = {ca[0] + o % S1 - R, ca[1] + (o / S1) % S1 - R, ca[2] + o / (S1 * S1) - R};
+    if (cb[0] < 0 || cb[1] < 0 || cb[2] < 0 || cb[0] >= n1 || cb[1] >= n1 || cb[2] >= n1) continue;
+    int j = gid[cb[0] + n1 * (cb[1] + n1 * cb[2])];
+    if (j < 0) continue;
+    T xv[4];
+    ld4(x + 4 * (size_t)j, xv);
+    const T* v = row + 9 * o;
+    y0 += v[0] * xv[0] + v[1] * xv[1] + v[2] * xv[2];
+    y1 += v[3] * xv[0] + v[4] * xv[1] + v[5] * xv[2];
+    y2 += v[6] * xv[0] + v[7] * xv[1] + v[8] * xv[2];
+  }
+  y0 = warp_sum(y0);
+  y1 = warp_sum(y1);
+  y2 = warp_sum(y2);
+  if (lane == 0) {
+    T bv[4], res[4];
+    ld4(b + 4 * (size_t)a, bv);
+    res[0] = bv[0] - y0;
+    res[1] = bv[1] - y1;
+    res[2] = bv[2] - y2;
+    res[3] = (T)0;
+    if (MODE == 0) {
+      st4(out + 4 * (size_t)a, res);
+    } else {
+      T xv[4], d[4];
+      ld4(x + 4 * (size_t)a, xv);
+      apply_dinv(Dinv, a, res, d);
+      for (int c = 0; c < 3; ++c) xv[c] += d[c];
+      xv[3] = (T)0;
+      st4(out + 4 * (size_t)a, xv);
+    }
+  }
+}
+
+// b1 = P^T r (fine -> level 1)
+template <class T>
+__global__ void k_mg_restrict1(int nrow, const int* __restrict__ pt_ptr, const int* __restrict__ pt_idx,
+                               const float* __restrict__ pw, const int* __restrict__ fmask,
+                               const T* __restrict__ rf, T* b, const Scal* sk, int k) {
+  if (skip(sk, k)) return;
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nrow) return;
+  T s[4] = {0, 0, 0, 0};
+  for (int t = pt_ptr[a]; t < pt_ptr[a + 1]; ++t) {
+    int e8 = pt_idx[t], i = e8 >> 3;
+    T w = (T)pw[e8];
+    int mi = fmask[i];
+    T rv[4];
+    ld4(rf + 4 * (size_t)i, rv);
+    for (int c = 0; c < 3; ++c)
+      if (!((mi >> c) & 1)) s[c] += w * rv[c];
+  }
+  st4(b + 4 * (size_t)a, s);
+}
+
+// xf += P x1 (level 1 -> fine)
+template <class T>
+__global__ void k_mg_prolong1(int nd, const int* __restrict__ pidx, const float* __restrict__ pw,
+                              const int* __restrict__ fmask, const T* __restrict__ x1, T* xf,
+                              const Scal* sk, int k) {
+  if (skip(sk, k)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  T s[3] = {0, 0, 0};
+  for (int q = 0; q < 8; ++q) {
+    int a = pidx[8 * (size_t)i + q];
+    if (a < 0) break;
+    T w = (T)pw[8 * (size_t)i + q];
+    T xv[4];
+    ld4(x1 + 4 * (size_t)a, xv);
+    for (int c = 0; c < 3; ++c) s[c] += w * xv[c];
+  }
+  int mi = fmask[i];
+  T xv[4];
+  ld4(xf + 4 * (size_t)i, xv);
+  for (int c = 0; c < 3; ++c)
+    if (!((mi >> c) & 1)) xv[c] += s[c];
+  st4(xf + 4 * (size_t)i, xv);
+}
+
+// bc = P^T rf between uniform levels
+template <class T>
+__global__ void k_mg_restrict_u(int nrow, const int* __restrict__ xyz_c, int n1f,
+                                const int* __restrict__ gid_f, const int* __restrict__ fmask,
+                                const T* __restrict__ rf, T* bc, const Scal* sk, int k) {
+  if (skip(sk, k)) return;
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nrow) return;
+  int ca[3];
+  unpack3(xyz_c[a], ca);
+  T s[4] = {0, 0, 0, 0};
+  for (int dl = 0; dl < 27; ++dl) {
+    int del[3] = {dl % 3 - 1, (dl / 3) % 3 - 1, dl / 9 - 1};
+    int fi[3];
+    bool in = true;
+    T w = (T)1;
+    for (int d = 0; d < 3; ++d) {
+      fi[d] = 2 * ca[d] + del[d];
+      in = in && fi[d] >= 0 && fi[d] < n1f;
+      if (del[d]) w *= (T)0.5;
+    }
+    if (!in) continue;
+    int i = gid_f[fi[0] + n1f * (fi[1] + n1f * fi[2])];
+    if (i < 0) continue;
+    int mi = fmask[i];
+    T rv[4];
+    ld4(rf + 4 * (size_t)i, rv);
+    for (int c = 0; c < 3; ++c)
+      if (!((mi >> c) & 1)) s[c] += w * rv[c];
+  }
+  st4(bc + 4 * (size_t)a, s);
+}
+
+// xf += P xc between uniform levels
+template <class T>
+__global__ void k_mg_prolong_u(int nrow, const int* __restrict__ xyz_f, const int* __restrict__ fmask,
+                               int n1c, const int* __restrict__ gid_c, const T* __restrict__ xc, T* xf,
+                               const Scal* sk, int k) {
+  if (skip(sk, k)) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrow) return;
+  int c[3];
+  unpack3(xyz_f[i], c);
+  int lo[3], hi[3];
+  T f = (T)1;
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = c[d] >> 1;
+    hi[d] = (c[d] + 1) >> 1;
+    if (lo[d] != hi[d]) f *= (T)0.5;
+  }
+  T s[3] = {0, 0, 0};
+  for (int z = lo[2]; z <= hi[2]; ++z)
+    for (int y = lo[1]; y <= hi[1]; ++y)
+      for (int x = lo[0]; x <= hi[0]; ++x) {
+        int b = gid_c[x + n1c * (y + n1c * z)];
+        if (b < 0) continue;
+        T xv[4];
+        ld4(xc + 4 * (size_t)b, xv);
+        for (int cc = 0; cc < 3; ++cc) s[cc] += f * xv[cc];
+      }
+  int mi = fmask[i];
+  T xv[4];
+  ld4(xf + 4 * (size_t)i, xv);
+  for (int cc = 0; cc < 3; ++cc)
+    if (!((mi >> cc) & 1)) xv[cc] += s[cc];
+  st4(xf + 4 * (size_t)i, xv);
+}
+
+// coarsest: x = Cinv b (one block)
+template <class T>
+__global__ void k_mg_coarse(int nrow, const T* __restrict__ Cinv, const T* __restrict__ b, T* x,
+                            const Scal* sk, int k) {
+  if (skip(sk, k)) return;
+  int n3 = 3 * nrow;
+  for (int i = threadIdx.x; i < 4 * nrow; i += blockDim.x) {
+    int a = i >> 2, c = i & 3;
+    T s = (T)0;
+    if (c < 3) {
+      const T* row = Cinv + (size_t)(3 * a + c) * n3;
+      for (int j = 0; j < nrow; ++j)
+        s += row[3 * j] * b[4 * j] + row[3 * j + 1] * b[4 * j + 1] + row[3 * j + 2] * b[4 * j + 2];
+    }
+    x[i] = s;
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+int pad32(int n) { return (n + 31) & ~31; }
+
+size_t rap_smem(int S, size_t tsz) { return (size_t)MGW * 9 * S * tsz; }
+
+// structure for the current mesh build (once per build)
+void mg_structure(mpm_ctx* c, mpm_mesh* m) {
+  cudaStream_t st = c->stream;
+  if (!m->mg) m->mg = new MGData();
+  MGData& G = *m->mg;
+  const Geo& g = m->g;
+  int nd = m->ndof;
+  int d1 = std::min(std::min(m->dom.depth_min, g.D - 1), 7);
+  // the first coarse grid should hold at most a quarter of the fine unknowns
+  while (d1 > 1 && (double)(1 << d1) * (1 << d1) * (1 << d1) > 0.25 * nd) --d1;
+  if (d1 < 1) throw CudaError(MPM_ERR_ARG, "multigrid needs an octree of depth 2 or more");
+  G.nlev = d1;  // depths d1, d1-1, ..., 1
+  // level 1 from the fine dofs
+  for (int l = 0; l < G.nlev; ++l) {
+    MGLevel& L = G.lev[l];
+    L.d = d1 - l;
+    L.n1 = (1 << L.d) + 1;
+    int ng = L.n1 * L.n1 * L.n1;
+    int* active = grow<int>(c, c->tmp[1], ng);
+    int* freeb = grow<int>(c, c->tmp[2], ng);
+    int* scan = grow<int>(c, c->tmp[3], ng);
+    MPM_CUDA(cudaMemsetAsync(active, 0, sizeof(int) * ng, st));
+    MPM_CUDA(cudaMemsetAsync(freeb, 0, sizeof(int) * ng, st));
+    if (l == 0) {
+      int* pidx = grow<int>(c, G.p_idx, 8 * (size_t)nd);
+      float* pw = grow<float>(c, G.p_w, 8 * (size_t)nd);
+      MPM_LAUNCH(k_mg_p1<<<grid_for(nd, 256), 256, 0, st>>>(nd, g.D, L.d, ptr<int>(m->dof_node),
+                                                            ptr<uint64_t>(m->node_key), ptr<int>(m->dof_mask),
+                                                            pidx, pw, active, freeb));
+    } else {
+      MGLevel& F = G.lev[l - 1];
+      MPM_LAUNCH(k_mg_mark_u<<<grid_for(F.nrow, 256), 256, 0, st>>>(F.nrow, ptr<int>(F.xyz), ptr<int>(F.mask),
+                                                                    L.n1, active, freeb));
+    }
+    cub_exclusive_sum_int(c, active, scan, ng);
+    int last[2];
+    MPM_CUDA(cudaMemcpyAsync(&c->h_int[2], scan + ng - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(cudaMemcpyAsync(&c->h_int[3], active + ng - 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(cudaStreamSynchronize(st));
+    last[0] = c->h_int[2];
+    last[1] = c->h_int[3];
+    L.nrow = last[0] + last[1];
+    L.npad = pad32(std::max(L.nrow, 1));
+    int* gid = grow<int>(c, L.gid, ng);
+    grow<int>(c, L.xyz, L.npad);
+    grow<int>(c, L.mask, L.npad);
+    MPM_LAUNCH(k_mg_compact<<<grid_for(ng, 256), 256, 0, st>>>(ng, L.n1, active, scan, freeb, gid,
+                                                              ptr<int>(L.xyz), ptr<int>(L.mask)));
+    if (l == 0) {
+      // P^T of level 1
+      long long ne = 8LL * nd;
+      uint64_t* keys = grow<uint64_t>(c, c->tmp[6], ne);
+      uint64_t* alt = grow<uint64_t>(c, c->tmp[7], ne);
+      MPM_LAUNCH(k_mg_p1_rows<<<grid_for(ne, 256), 256, 0, st>>>(nd, gid, ptr<int>(G.p_idx), keys));
+      cub_sort_u64(c, keys, alt, (int)ne, 64);
+      int* ptr_ = grow<int>(c, G.pt_ptr, L.nrow + 1);
+      MPM_CUDA(cudaMemsetAsync(ptr_, 0, sizeof(int) * (L.nrow + 1), st));
+      MPM_LAUNCH(k_mg_pt<<<grid_for(ne, 256), 256, 0, st>>>(ne, keys, L.nrow, ptr_, grow<int>(c, G.pt_idx, ne)));
+      // stencil radius of level 1 from the reach of the fine blocks
+      int* reach = (int*)(c->d_red + 8);
+      MPM_CUDA(cudaMemsetAsync(reach, 0, sizeof(int), st));
+      MPM_LAUNCH(k_mg_reach<<<grid_for(nd, 8), 256, 0, st>>>(nd, g.D, L.d, ptr<int>(m->row_ptr), ptr<int>(m->col),
+                                                             ptr<int>(m->dof_node), ptr<uint64_t>(m->node_key), reach));
+      MPM_CUDA(cudaMemcpyAsync(&c->h_int[2], reach, sizeof(int), cudaMemcpyDeviceToHost, st));
+      MPM_CUDA(cudaStreamSynchronize(st));
+      L.R = std::max(2, c->h_int[2] + 1);
+    } else {
+      L.R = std::max(2, (G.lev[l - 1].R + 2) / 2);
+    }
+    int S1 = 2 * L.R + 1;
+    L.S = S1 * S1 * S1;
+  }
+  MGLevel& C = G.lev[G.nlev - 1];
+  G.n3c = 3 * C.nrow;
+  if (G.n3c > 81) throw CudaError(MPM_ERR_ARG, "multigrid: coarsest level too large");
+  int e = check_device_error(c, "multigrid structure");
+  if (e) throw CudaError(e, c->err);
+  G.gen = m->gen;
+  G.prec = -1;
+  G.num_gen = -1;
+}
+
+template <class T>
+void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
+  cudaStream_t st = c->stream;
+  MGData& G = *m->mg;
+  int nd = m->ndof, npad = 32 * m->nslice;
+  Sliced SK{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+  // fine smoother and V-cycle vectors
+  T* fD = grow<T>(c, G.fDinv, 12 * (size_t)npad);
+  MPM_LAUNCH(k_mg_dinv_fine<T><<<grid_for(npad, 256), 256, 0, st>>>(nd, npad, SK, K, fD, c->d_err));
+  grow<T>(c, G.fx, 4 * (size_t)npad);
+  grow<T>(c, G.fr, 4 * (size_t)npad);
+  if (!coarse) return;
+  for (int l = 0; l < G.nlev; ++l) {
+    MGLevel& L = G.lev[l];
+    T* A = grow<T>(c, L.A, (size_t)L.nrow * L.S * 9);
+    size_t smem = rap_smem(L.S, sizeof(T));
+    if (smem > 200 * 1024) throw CudaError(MPM_ERR_SUPPORT, "multigrid: coarse stencil too wide");
+    if (l == 0) {
+      MPM_CUDA(cudaFuncSetAttribute(k_mg_rap1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MPM_LAUNCH(k_mg_rap1<T><<<grid_for(L.nrow, MGW), 32 * MGW, smem, st>>>(
+          L.nrow, L.R, L.S, ptr<int>(G.pt_ptr), ptr<int>(G.pt_idx), ptr<float>(G.p_w), ptr<int>(G.p_idx),
+          ptr<int>(m->dof_mask), ptr<int>(m->row_ptr), ptr<int>(m->col), SK, K, ptr<int>(L.xyz),
+          ptr<int>(L.mask), A, c->d_err));
+    } else {
+      MGLevel& F = G.lev[l - 1];
+      MPM_CUDA(cudaFuncSetAttribute(k_mg_rapu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      MPM_LAUNCH(k_mg_rapu<T><<<grid_for(L.nrow, MGW), 32 * MGW, smem, st>>>(
+          L.nrow, L.R, L.S, ptr<int>(L.xyz), ptr<int>(L.mask), F.R, F.S, F.n1, ptr<int>(F.gid),
+          ptr<int>(F.xyz), ptr<int>(F.mask), ptr<T>(F.A), A, c->d_err));
+    }
+    MPM_LAUNCH(k_mg_dinv<T><<<grid_for(L.npad, 128), 128, 0, st>>>(L.nrow, L.npad, L.S, L.R, A,
+                                                                   grow<T>(c, L.Dinv, 12 * (size_t)L.npad), c->d_err));
+    // level vectors: padding rows stay zero
+    MPM_CUDA(cudaMemsetAsync(grow<T>(c, L.b, 4 * (size_t)L.npad), 0, sizeof(T) * 4 * L.npad, st));
+    MPM_CUDA(cudaMemsetAsync(grow<T>(c, L.x, 4 * (size_t)L.npad), 0, sizeof(T) * 4 * L.npad, st));
+    MPM_CUDA(cudaMemsetAsync(grow<T>(c, L.r, 4 * (size_t)L.npad), 0, sizeof(T) * 4 * L.npad, st));
+  }
+  MGLevel& C = G.lev[G.nlev - 1];
+  int n3 = G.n3c;
+  T* Ci = grow<T>(c, G.cinv, (size_t)std::max(n3 * n3, 1));
+  size_t dsm = sizeof(double) * (size_t)n3 * 2 * n3;
+  MPM_CUDA(cudaFuncSetAttribute(k_mg_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+  MPM_LAUNCH(k_mg_dense<T><<<1, 256, dsm, st>>>(C.nrow, C.S, C.R, ptr<int>(C.xyz), C.n1, ptr<int>(C.gid),
+                                                ptr<T>(C.A), Ci));
+  G.prec = sizeof(T) == 4 ? MPM_MIXED : MPM_FP64;
+  G.num_gen = m->gen;
+}
+
+}  // namespace
+
+template <class T>
+void mg_setup(mpm_ctx* c, mpm_mesh* m, const T* K, bool reuse) {
+  prof_begin(c, MPM_PROF_MG_SETUP);
+  if (!m->mg || m->mg->gen != m->gen) mg_structure(c, m);
+  MGData& G = *m->mg;
+  int prec = sizeof(T) == 4 ? MPM_MIXED : MPM_FP64;
+  bool keep = reuse && G.num_gen == m->gen && G.prec == prec;
+  mg_numeric<T>(c, m, K, !keep);
+  prof_end(c);
+}
+
+template <class T>
+void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, const Scal* sk, int k,
+              double* rz) {
+  mpm_mesh* m = const_cast<mpm_mesh*>(mc);
+  cudaStream_t st = c->stream;
+  MGData& G = *m->mg;
+  int nd = m->ndof, npad = 32 * m->nslice;
+  Sliced SK{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+  const int* fmask = ptr<int>(m->dof_mask);
+  T* fx = ptr<T>(G.fx);
+  T* fr = ptr<T>(G.fr);
+  const T* fD = ptr<T>(G.fDinv);
+  const int FB = 8 * 32;  // rows per block of the fine row kernels
+  // fine pre-smoothing from zero, residual, restriction
+  MPM_LAUNCH(k_mg_jac0<T><<<grid_for(npad, 256), 256, 0, st>>>(npad, fD, r, fx, sk, k));
+  MPM_LAUNCH(k_mg_fine<T, 0><<<grid_for(npad, FB), FB, 0, st>>>(nd, npad, SK, K, r, fx, fD, fr, nullptr, sk, k));
+  MGLevel& L0 = G.lev[0];
+  MPM_LAUNCH(k_mg_restrict1<T><<<grid_for(L0.nrow, 128), 128, 0, st>>>(
+      L0.nrow, ptr<int>(G.pt_ptr), ptr<int>(G.pt_idx), ptr<float>(G.p_w), fmask, fr, ptr<T>(L0.b), sk, k));
+  // down the uniform levels
+  T* xcur[8];
+  for (int l = 0; l + 1 < G.nlev; ++l) {
+    MGLevel& L = G.lev[l];
+    MGLevel& N = G.lev[l + 1];
+    MPM_LAUNCH(k_mg_jac0<T><<<grid_for(L.npad, 256), 256, 0, st>>>(L.npad, ptr<T>(L.Dinv), ptr<T>(L.b), ptr<T>(L.x), sk, k));
+    MPM_LAUNCH(k_mg_lvl<T, 0><<<grid_for(L.nrow, MGW), 32 * MGW, 0, st>>>(
+        L.nrow, L.S, L.R, L.n1, ptr<int>(L.xyz), ptr<int>(L.gid), ptr<T>(L.A), ptr<T>(L.b), ptr<T>(L.x),
+        ptr<T>(L.Dinv), ptr<T>(L.r), sk, k));
+    MPM_LAUNCH(k_mg_restrict_u<T><<<grid_for(N.nrow, 128), 128, 0, st>>>(
+        N.nrow, ptr<int>(N.xyz), L.n1, ptr<int>(L.gid), ptr<int>(L.mask), ptr<T>(L.r), ptr<T>(N.b), sk, k));
+  }
+  MGLevel& C = G.lev[G.nlev - 1];
+  MPM_LAUNCH(k_mg_coarse<T><<<1, 256, 0, st>>>(C.nrow, ptr<T>(G.cinv), ptr<T>(C.b), ptr<T>(C.x), sk, k));
+  xcur[G.nlev - 1] = ptr<T>(C.x);
+  // up: prolongate, post-smooth (into the r buffer, which becomes the iterate)
+  for (int l = G.nlev - 2; l >= 0; --l) {
+    MGLevel& L = G.lev[l];
+    MGLevel& N = G.lev[l + 1];
+    MPM_LAUNCH(k_mg_prolong_u<T><<<grid_for(L.nrow, 128), 128, 0, st>>>(
+        L.nrow, ptr<int>(L.xyz), ptr<int>(L.mask), N.n1, ptr<int>(N.gid), xcur[l + 1], ptr<T>(L.x), sk, k));
+    MPM_LAUNCH(k_mg_lvl<T, 1><<<grid_for(L.nrow, MGW), 32 * MGW, 0, st>>>(
+        L.nrow, L.S, L.R, L.n1, ptr<int>(L.xyz), ptr<int>(L.gid), ptr<T>(L.A), ptr<T>(L.b), ptr<T>(L.x),
+        ptr<T>(L.Dinv), ptr<T>(L.r), sk, k));
+    xcur[l] = ptr<T>(L.r);
+  }
+  MPM_LAUNCH(k_mg_prolong1<T><<<grid_for(nd, 128), 128, 0, st>>>(nd, ptr<int>(G.p_idx), ptr<float>(G.p_w), fmask,
+                                                                  xcur[0], fx, sk, k));
+  MPM_LAUNCH(k_mg_fine<T, 1><<<grid_for(npad, FB), FB, 0, st>>>(nd, npad, SK, K, r, fx, fD, z, rz, sk, k));
+}
+
+void mg_release(mpm_ctx* c, mpm_mesh* m) {
+  if (!m->mg) return;
+  MGData& G = *m->mg;
+  for (auto& L : G.lev) {
+    Buf* b[] = {&L.gid, &L.xyz, &L.mask, &L.A, &L.Dinv, &L.b, &L.x, &L.r};
+    for (Buf* x : b) free_buf(c, *x);
+  }
+  Buf* b[] = {&G.p_idx, &G.p_w, &G.pt_ptr, &G.pt_idx, &G.pt_w, &G.fDinv, &G.fx, &G.fr, &G.fb, &G.cinv};
+  for (Buf* x : b) free_buf(c, *x);
+  delete m->mg;
+  m->mg = nullptr;
+}
+
+template void mg_setup<float>(mpm_ctx*, mpm_mesh*, const float*, bool);
+template void mg_setup<double>(mpm_ctx*, mpm_mesh*, const double*, bool);
+template void mg_apply<float>(mpm_ctx*, const mpm_mesh*, const float*, const float*, float*, const Scal*,
+                              int, double*);
+template void mg_apply<double>(mpm_ctx*, const mpm_mesh*, const double*, const double*, double*,
+                               const Scal*, int, double*);
+
+}  // namespace mpm

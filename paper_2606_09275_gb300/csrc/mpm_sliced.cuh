@@ -1,0 +1,74 @@
+// Device helpers of the sliced block storage shared by the Krylov solves and
+// the multigrid preconditioner: 16-byte vector loads and stores, one row of
+// K times x, and the 3x3 inverse-block product.
+#pragma once
+#include "mpm_internal.cuh"
+
+namespace mpm {
+
+// 4-wide loads and stores (16-byte aligned; two 16-byte halves for double)
+__device__ inline void ld4(const float* p, float* v) {
+  float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ inline void ld4(const double* p, double* v) {
+  double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ inline void st4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ inline void st4(double* p, const double* v) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+
+// y = row r of K times x, sliced storage (one thread per row; a warp is one
+// slice).  XS = 4: x padded to 4 components per dof; XS = 3: plain 3-vectors.
+template <class T, class V, class A, int XS>
+__device__ inline void sliced_row(int r, Sliced S, const T* __restrict__ K,
+                                  const V* __restrict__ x, A* y) {
+  int s = r >> 5, ln = r & 31;
+  int W = S.w[s];
+  long long b0 = S.base[s];
+  const T* Kb = K + 9 * b0;
+  const int* cb = S.scol + b0;
+  size_t plane = (size_t)32 * W;
+  y[0] = y[1] = y[2] = (A)0;
+  for (int k4 = 0; k4 < (W >> 2); ++k4) {
+    size_t off = ((size_t)k4 * 32 + ln) * 4;
+    int4 c = *reinterpret_cast<const int4*>(cb + off);
+    int cc[4] = {c.x, c.y, c.z, c.w};
+    T v[9][4];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) ld4(Kb + e * plane + off, v[e]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      A x0, x1, x2;
+      if (XS == 4) {
+        V xv[4];
+        ld4(x + 4 * (size_t)cc[j], xv);
+        x0 = (A)xv[0]; x1 = (A)xv[1]; x2 = (A)xv[2];
+      } else {
+        x0 = (A)x[3 * (size_t)cc[j]]; x1 = (A)x[3 * (size_t)cc[j] + 1]; x2 = (A)x[3 * (size_t)cc[j] + 2];
+      }
+      y[0] += (A)v[0][j] * x0 + (A)v[1][j] * x1 + (A)v[2][j] * x2;
+      y[1] += (A)v[3][j] * x0 + (A)v[4][j] * x1 + (A)v[5][j] * x2;
+      y[2] += (A)v[6][j] * x0 + (A)v[7][j] * x1 + (A)v[8][j] * x2;
+    }
+  }
+}
+
+template <class V>
+__device__ inline void apply_dinv(const V* __restrict__ Dinv, size_t i, const V* rv, V* zv) {
+  V d0[4], d1[4], d2[4];
+  ld4(Dinv + 12 * i, d0);
+  ld4(Dinv + 12 * i + 4, d1);
+  ld4(Dinv + 12 * i + 8, d2);
+  zv[0] = d0[0] * rv[0] + d0[1] * rv[1] + d0[2] * rv[2];
+  zv[1] = d1[0] * rv[0] + d1[1] * rv[1] + d1[2] * rv[2];
+  zv[2] = d2[0] * rv[0] + d2[1] * rv[1] + d2[2] * rv[2];
+  zv[3] = (V)0;
+}
+
+}  // namespace mpm

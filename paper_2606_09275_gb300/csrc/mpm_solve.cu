@@ -12,71 +12,13 @@
 #include <string>
 
 #include "mpm_internal.cuh"
+#include "mpm_sliced.cuh"
 
 namespace mpm {
 namespace {
 
 constexpr int SW = 8;  // warps (slices of 32 rows) per block of the row kernels
 
-struct Scal {
-  double rz[3], pq[3], rr[3];
-  double bb, thr;    // ||b||^2 and tol^2 ||b||^2
-  double a[8];       // BiCGStab scalars
-  int done, iters, breakdown, pad;
-};
-
-// 4-wide loads and stores (16-byte aligned; two 16-byte halves for double)
-__device__ inline void ld4(const float* p, float* v) {
-  float4 t = *reinterpret_cast<const float4*>(p);
-  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
-}
-__device__ inline void ld4(const double* p, double* v) {
-  double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-__device__ inline void st4(float* p, const float* v) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-__device__ inline void st4(double* p, const double* v) {
-  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-  *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
-}
-
-// y = row r of K times x, sliced storage (one thread per row; a warp is one
-// slice).  XS = 4: x padded to 4 components per dof; XS = 3: plain 3-vectors.
-template <class T, class V, class A, int XS>
-__device__ inline void sliced_row(int r, Sliced S, const T* __restrict__ K,
-                                  const V* __restrict__ x, A* y) {
-  int s = r >> 5, ln = r & 31;
-  int W = S.w[s];
-  long long b0 = S.base[s];
-  const T* Kb = K + 9 * b0;
-  const int* cb = S.scol + b0;
-  size_t plane = (size_t)32 * W;
-  y[0] = y[1] = y[2] = (A)0;
-  for (int k4 = 0; k4 < (W >> 2); ++k4) {
-    size_t off = ((size_t)k4 * 32 + ln) * 4;
-    int4 c = *reinterpret_cast<const int4*>(cb + off);
-    int cc[4] = {c.x, c.y, c.z, c.w};
-    T v[9][4];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) ld4(Kb + e * plane + off, v[e]);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      A x0, x1, x2;
-      if (XS == 4) {
-        V xv[4];
-        ld4(x + 4 * (size_t)cc[j], xv);
-        x0 = (A)xv[0]; x1 = (A)xv[1]; x2 = (A)xv[2];
-      } else {
-        x0 = (A)x[3 * (size_t)cc[j]]; x1 = (A)x[3 * (size_t)cc[j] + 1]; x2 = (A)x[3 * (size_t)cc[j] + 2];
-      }
-      y[0] += (A)v[0][j] * x0 + (A)v[1][j] * x1 + (A)v[2][j] * x2;
-      y[1] += (A)v[3][j] * x0 + (A)v[4][j] * x1 + (A)v[5][j] * x2;
-      y[2] += (A)v[6][j] * x0 + (A)v[7][j] * x1 + (A)v[8][j] * x2;
-    }
-  }
-}
 
 // block-Jacobi: inverse of each 3x3 diagonal block, rows padded to 4 (12 per dof)
 template <class T, class V>
@@ -125,17 +67,6 @@ __global__ void k_block_jacobi(int nd, const int* __restrict__ rp, const int* __
   o[11] = (V)0;
 }
 
-template <class V>
-__device__ inline void apply_dinv(const V* __restrict__ Dinv, size_t i, const V* rv, V* zv) {
-  V d0[4], d1[4], d2[4];
-  ld4(Dinv + 12 * i, d0);
-  ld4(Dinv + 12 * i + 4, d1);
-  ld4(Dinv + 12 * i + 8, d2);
-  zv[0] = d0[0] * rv[0] + d0[1] * rv[1] + d0[2] * rv[2];
-  zv[1] = d1[0] * rv[0] + d1[1] * rv[1] + d1[2] * rv[2];
-  zv[2] = d2[0] * rv[0] + d2[1] * rv[1] + d2[2] * rv[2];
-  zv[3] = (V)0;
-}
 
 // ---------------------------------------------------------------- PCG
 // vectors r, z, p, q are padded to 4 components over 32*nslice rows; x keeps
@@ -193,7 +124,7 @@ __global__ void k_pcg_q0(int nd, int npad, Sliced S, const T* __restrict__ K, co
 }
 
 // A_k: alpha = rz_k/pq_k; x += alpha p; r -= alpha q; z = M r; rz_{k+1}, rr_{k+1}
-template <class V>
+template <class V, bool PRE = true>
 __global__ void k_pcg_a(int nd, int k, const V* __restrict__ Dinv, V* x, V* r, V* z,
                         const V* __restrict__ p, const V* __restrict__ q, Scal* sc) {
   __shared__ double sh[32];
@@ -222,15 +153,49 @@ __global__ void k_pcg_a(int nd, int k, const V* __restrict__ Dinv, V* x, V* r, V
       rr += (double)rv[c] * (double)rv[c];
     }
     st4(r + 4 * (size_t)i, rv);
-    apply_dinv(Dinv, i, rv, zv);
-    st4(z + 4 * (size_t)i, zv);
-    for (int c = 0; c < 3; ++c) rz += (double)rv[c] * (double)zv[c];
+    if (PRE) {
+      apply_dinv(Dinv, i, rv, zv);
+      st4(z + 4 * (size_t)i, zv);
+      for (int c = 0; c < 3; ++c) rz += (double)rv[c] * (double)zv[c];
+    }
   }
-  rz = block_sum(rz, sh);
+  if (PRE) rz = block_sum(rz, sh);
   rr = block_sum(rr, sh);
   if (threadIdx.x == 0) {
-    atomicAdd(&sc->rz[i1], rz);
+    if (PRE) atomicAdd(&sc->rz[i1], rz);
     atomicAdd(&sc->rr[i1], rr);
+  }
+}
+
+// multigrid-preconditioned start: r = b (free components), x = 0, ||b||^2
+template <class V>
+__global__ void k_pcg_init_mg(int nd, int npad, const double* __restrict__ b, const int* __restrict__ mask,
+                              V* x, V* r, Scal* sc) {
+  __shared__ double sh[32];
+  double bb = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
+    V rv[4] = {(V)0, (V)0, (V)0, (V)0};
+    if (i < nd) {
+      int mk = mask[i];
+      for (int c = 0; c < 3; ++c) {
+        rv[c] = ((mk >> c) & 1) ? (V)0 : (V)b[3 * (size_t)i + c];
+        x[3 * (size_t)i + c] = (V)0;
+        bb += (double)rv[c] * (double)rv[c];
+      }
+    }
+    st4(r + 4 * (size_t)i, rv);
+  }
+  bb = block_sum(bb, sh);
+  if (threadIdx.x == 0) atomicAdd(&sc->bb, bb);
+}
+
+template <class V>
+__global__ void k_copy4(int npad, const V* __restrict__ a, V* b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < npad) {
+    V v[4];
+    ld4(a + 4 * (size_t)i, v);
+    st4(b + 4 * (size_t)i, v);
   }
 }
 
@@ -529,6 +494,56 @@ int run_pcg(mpm_ctx* c, const mpm_mesh* m, const T* K, const V* Dinv, const doub
   return sc_h->breakdown ? MPM_ERR_KRYLOV : MPM_OK;
 }
 
+// PCG preconditioned by one multigrid V-cycle per iteration (mpm_mg.cu);
+// the V-cycle kernels skip their work once the residual of the iteration has
+// converged, so batches of launches cost nothing after convergence
+template <class T>
+int run_pcg_mg(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* b, T* x, double tol,
+               int maxit, Scal* sc_d, Scal* sc_h, double* relres, int* iters, T* r, T* z, T* p, T* q) {
+  cudaStream_t st = c->stream;
+  int nd = m->ndof, npad = 32 * m->nslice;
+  Sliced S = sliced_of(m);
+  MPM_CUDA(cudaMemsetAsync(sc_d, 0, sizeof(Scal), st));
+  int vb = 4 * 152;
+  MPM_LAUNCH(k_pcg_init_mg<T><<<vb, 256, 0, st>>>(nd, npad, b, ptr<int>(m->dof_mask), x, r, sc_d));
+  mg_apply<T>(c, m, K, r, z, nullptr, 0, &sc_d->rz[0]);
+  MPM_LAUNCH(k_copy4<T><<<grid_for(npad, 256), 256, 0, st>>>(npad, z, p));
+  MPM_LAUNCH(k_pcg_q0<T, T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, p, q, sc_d));
+  MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+  MPM_CUDA(cudaStreamSynchronize(st));
+  double bb = sc_h->bb;
+  if (bb == 0.0) {
+    *relres = 0.0;
+    *iters = 0;
+    return MPM_OK;
+  }
+  double thr = tol * tol * bb;
+  MPM_CUDA(cudaMemcpyAsync(&sc_d->thr, &thr, sizeof(double), cudaMemcpyHostToDevice, st));
+  int k = 0;
+  const int batch = 4;
+  while (k < maxit) {
+    int kend = std::min(maxit, k + batch);
+    for (; k < kend; ++k) {
+      MPM_LAUNCH_P(MPM_PROF_PCG_UPDATE, k_pcg_a<T, false><<<vb, 256, 0, st>>>(nd, k, nullptr, x, r, z, p, q, sc_d));
+      prof_begin(c, MPM_PROF_MG);
+      mg_apply<T>(c, m, K, r, z, sc_d, k, &sc_d->rz[(k + 1) % 3]);
+      prof_end(c);
+      MPM_LAUNCH_P(MPM_PROF_PCG_SPMV, k_pcg_b<T, T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, k, S, K, z, p, q, sc_d));
+    }
+    MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(cudaStreamSynchronize(st));
+    if (sc_h->done) break;
+  }
+  if (!sc_h->done) {
+    *iters = maxit;
+    *relres = sqrt(sc_h->rr[maxit % 3] / bb);
+    return MPM_ERR_KRYLOV;
+  }
+  *iters = sc_h->iters;
+  *relres = sqrt(sc_h->rr[sc_h->iters % 3] / bb);
+  return sc_h->breakdown ? MPM_ERR_KRYLOV : MPM_OK;
+}
+
 template <class T>
 int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, const double* b,
                  double* x, double tol, int maxit, Scal* sc_d, Scal* sc_h, double* relres,
@@ -605,7 +620,15 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   const int* col = ptr<int>(m->col);
   Sliced S = sliced_of(m);
   int method = prm.method;
-  if (method == 0) method = (mat.model == 2 && mat.psi != mat.phi) ? 2 : 1;
+  bool sym = !(mat.model == 2 && mat.psi != mat.phi);
+  if (method == 0) method = sym ? 1 : 2;
+  if (method == 3 && !sym) {
+    out->iterations = 0;
+    out->refinements = 0;
+    out->status = MPM_ERR_ARG;
+    set_error(c, "multigrid PCG needs a symmetric tangent (non-associated Drucker-Prager is not)");
+    return;
+  }
   Scal* sc_d = grow<Scal>(c, c->v[20], 1);
   Scal* sc_h = (Scal*)(c->h_red + 32);  // pinned, 32 doubles fit Scal
   static_assert(sizeof(Scal) <= 32 * sizeof(double), "scalar block too large");
@@ -619,7 +642,12 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     int its = 0;
     double rel = 0.0;
     int sst;
-    if (method == 1)
+    if (method == 3) {
+      mg_setup<double>(c, m, Kd, prm.mg_reuse != 0);
+      sst = run_pcg_mg<double>(c, m, Kd, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its,
+                               grow<double>(c, c->v[4], n4), grow<double>(c, c->v[5], n4),
+                               grow<double>(c, c->v[6], n4), grow<double>(c, c->v[7], n4));
+    } else if (method == 1)
       sst = run_pcg<double, double>(c, m, Kd, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its,
                                     grow<double>(c, c->v[4], n4), grow<double>(c, c->v[5], n4),
                                     grow<double>(c, c->v[6], n4), grow<double>(c, c->v[7], n4));
@@ -629,7 +657,8 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     out->relres = rel;
     out->status = sst;
     if (sst)
-      set_error(c, std::string(method == 1 ? "PCG" : "BiCGStab") + " did not reach the tolerance (" +
+      set_error(c, std::string(method == 1 ? "PCG" : (method == 3 ? "multigrid PCG" : "BiCGStab")) +
+                       " did not reach the tolerance (" +
                        std::to_string(its) + " iterations, relative residual " +
                        std::to_string(rel) + (sc_h->breakdown ? ", breakdown)" : ")"));
     return;
@@ -640,9 +669,12 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   double* r64 = grow<double>(c, c->v[12], n3);
   float* d32 = grow<float>(c, c->v[13], n3);
   double* slot = c->d_red + 44;
-  if (method == 1) {
+  if (method == 1 || method == 3) {
     float* Dinv = grow<float>(c, c->v[3], 12 * (size_t)npad);
-    MPM_LAUNCH(k_block_jacobi<float, float><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, Kf, Dinv, c->d_err));
+    if (method == 3)
+      mg_setup<float>(c, m, Kf, prm.mg_reuse != 0);
+    else
+      MPM_LAUNCH(k_block_jacobi<float, float><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, Kf, Dinv, c->d_err));
     float* r = grow<float>(c, c->v[4], n4);
     float* z = grow<float>(c, c->v[5], n4);
     float* pp = grow<float>(c, c->v[6], n4);
@@ -661,8 +693,11 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
       }
       int its = 0;
       double rel = 0.0;
-      int sst = run_pcg<float, float>(c, m, Kf, Dinv, r64, d32, inner, prm.maxit - total, sc_d, sc_h,
-                                      &rel, &its, r, z, pp, q);
+      int sst = method == 3
+                    ? run_pcg_mg<float>(c, m, Kf, r64, d32, inner, prm.maxit - total, sc_d, sc_h, &rel,
+                                        &its, r, z, pp, q)
+                    : run_pcg<float, float>(c, m, Kf, Dinv, r64, d32, inner, prm.maxit - total, sc_d,
+                                            sc_h, &rel, &its, r, z, pp, q);
       total += its;
       ++rounds;
       if (sst && its == 0) {

@@ -64,7 +64,7 @@ class MeshInfo(C.Structure):
 
 class SolveParams(C.Structure):
     _fields_ = [("method", C.c_int), ("precision", C.c_int), ("tol", C.c_double),
-                ("maxit", C.c_int), ("inner_tol", C.c_double)]
+                ("maxit", C.c_int), ("inner_tol", C.c_double), ("mg_reuse", C.c_int)]
 
 
 class SolveStats(C.Structure):
@@ -342,10 +342,11 @@ def assemble(ctx, mesh, cfg, du, load=1.0, precision=FP64, tangent=True, body_z=
 
 
 def solve(ctx, mesh, cfg, K, rhs, precision=FP64, tol=1e-10, maxit=20000, method=0,
-          inner_tol=1e-3):
-    """mpm_solve: block-Jacobi PCG / BiCGStab (FP32 inner + FP64 refinement when mixed)."""
+          inner_tol=1e-3, mg_reuse=0):
+    """mpm_solve: block-Jacobi PCG, BiCGStab or multigrid PCG (method 3); FP32
+    inner solves inside FP64 refinement when mixed."""
     x = torch.empty_like(rhs)
-    sp = SolveParams(method, precision, tol, maxit, inner_tol)
+    sp = SolveParams(method, precision, tol, maxit, inner_tol, mg_reuse)
     ss = SolveStats()
     st = lib().mpm_solve(ctx.h, mesh.h, C.byref(material(cfg)), _p(K), _p(rhs), _p(x), C.byref(sp),
                          C.byref(ss))
@@ -368,10 +369,11 @@ def solve_static(ctx, mesh, K, rhs, tol=1e-10, maxit=20000):
 
 
 def step(ctx, cfg, points, body_z=None, load=1.0, tol=1e-8, maxit=30, lin_tol=1e-8,
-         lin_maxit=20000, precision=FP64, method=0, inner_tol=1e-3, check=True):
+         lin_maxit=20000, precision=FP64, method=0, inner_tol=1e-3, check=True, mg_reuse=0):
     """mpm_step: one quasi-static load step; returns the statistics."""
     s = points.struct()
-    sp = StepParams(load, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol))
+    sp = StepParams(load, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol,
+                                                  mg_reuse))
     ss = StepStats()
     st = lib().mpm_step(ctx.h, C.byref(domain(cfg)), C.byref(rigid(cfg, body_z)), C.byref(adapt(cfg)),
                         C.byref(material(cfg)), C.byref(s), C.byref(sp), C.byref(ss))

@@ -1,0 +1,116 @@
+"""PCG preconditioned by the geometric multigrid V-cycle (solve method 3),
+through the C ABI, against the oracle's dense LU and against the load steps
+of the oracle.  The preconditioner changes how the Krylov solve gets to the
+tolerance, not the solution: the same FP64 and mixed-precision bars apply as
+for block-Jacobi PCG."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2606_09275_gb300 import inputs
+
+from test_gpu_parity import CASES, both
+
+pytestmark = pytest.mark.gpu
+
+MG = 3
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    from paper_2606_09275_gb300 import mpm
+    assert torch.cuda.is_available()
+    ctx = mpm.Context()
+    return mpm, ctx, torch
+
+
+# (the jittered hanging-node case is left out: its contact tangent has a
+# negative eigenvalue at this pose, where no conjugate-gradient method applies)
+@pytest.mark.parametrize("case", ["tiny_punch", "punch_d3_6", "column_d3"])
+def test_multigrid_pcg_matches_oracle_lu(gpu, case):
+    mpm, ctx, torch = gpu
+    cfg, bz = CASES[case]()
+    om, mesh, P = both(gpu, cfg, bz)
+    nd = om.counts()["ndof"]
+    # the tangent at the start of the step (symmetric positive definite)
+    du = np.zeros(3 * nd)
+    o = om.assemble(du)
+    xo, _ = om.solve(o["K"], -o["R"], tol=1e-14)
+    g = mpm.assemble(ctx, mesh, cfg, torch.tensor(du, device="cuda"), body_z=bz)
+    x, st = mpm.solve(ctx, mesh, cfg, g["K"], -g["R"], tol=1e-13, maxit=5000, method=MG)
+    assert st["status"] == 0 and st["relres"] <= 1e-13
+    assert np.max(np.abs(x.cpu().numpy() - xo)) <= 1e-9 * np.abs(xo).max()
+    xb, sb = mpm.solve(ctx, mesh, cfg, g["K"], -g["R"], tol=1e-13, maxit=50000, method=1)
+    print("%s: %d dofs, multigrid PCG %d iterations, block-Jacobi PCG %d" % (
+        case, nd, st["iterations"], sb["iterations"]))
+    # mixed: FP32 V-cycle and inner PCG inside FP64 refinement
+    gm = mpm.assemble(ctx, mesh, cfg, torch.tensor(du, device="cuda"), precision=1, body_z=bz)
+    xm, sm = mpm.solve(ctx, mesh, cfg, gm["K"], -gm["R"], precision=1, tol=1e-10, maxit=5000,
+                       method=MG)
+    assert sm["status"] == 0 and sm["refinements"] >= 1
+    assert np.max(np.abs(xm.cpu().numpy() - xo)) <= 1e-5 * np.abs(xo).max()
+
+
+def test_multigrid_needs_far_fewer_iterations_at_scale(gpu):
+    # indentation one level below the benchmark (33,600 dofs): the block-Jacobi
+    # count grows with the mesh, the multigrid count does not
+    mpm, ctx, torch = gpu
+    cfg = inputs.workload("indent_small")
+    pts = inputs.make_points(cfg)
+    P = mpm.Points(pts, capacity=2 * len(pts["x"]))
+    bz = inputs.body_z(cfg, 1)
+    mesh = mpm.octree_build(ctx, cfg, P, body_z=bz)
+    nd = mesh.info()["ndof"]
+    zero = torch.zeros(3 * nd, dtype=torch.float64, device="cuda")
+    for prec in (0, 1):
+        g = mpm.assemble(ctx, mesh, cfg, zero, body_z=bz, precision=prec)
+        xb, sb = mpm.solve(ctx, mesh, cfg, g["K"], -g["R"], tol=1e-8, maxit=50000, method=1,
+                           precision=prec)
+        xm, sm = mpm.solve(ctx, mesh, cfg, g["K"], -g["R"], tol=1e-8, maxit=5000, method=MG,
+                           precision=prec)
+        assert sm["status"] == 0 and sb["status"] == 0
+        assert sm["iterations"] * 4 <= sb["iterations"], (prec, sm, sb)
+        xb, xm = xb.cpu().numpy(), xm.cpu().numpy()
+        assert np.max(np.abs(xm - xb)) <= 1e-6 * np.abs(xb).max()
+        # reusing the coarse operators of the same K gives the same solve (up to
+        # the summation order of the dot products)
+        xr, sr = mpm.solve(ctx, mesh, cfg, g["K"], -g["R"], tol=1e-8, maxit=5000, method=MG,
+                           precision=prec, mg_reuse=1)
+        assert abs(sr["iterations"] - sm["iterations"]) <= 1
+        assert np.max(np.abs(xr.cpu().numpy() - xm)) <= 1e-7 * np.abs(xm).max()
+
+
+@pytest.mark.parametrize("reuse", [0, 1])
+def test_multigrid_punch_steps_match_oracle(gpu, reuse):
+    mpm, ctx, torch = gpu
+    cfg = inputs.workload("punch")
+    pts = inputs.make_points(cfg)
+    om = oracle.Model(cfg, pts)
+    P = mpm.Points(pts, capacity=64 * len(pts["x"]))
+    Pm = mpm.Points(pts, capacity=64 * len(pts["x"]))
+    for n in range(1, 4):
+        bz = inputs.body_z(cfg, n)
+        om.set_body_z(bz)
+        so = om.step(load=1.0, tol=1e-12, lin_tol=1e-13)
+        sg = mpm.step(ctx, cfg, P, body_z=bz, tol=1e-12, lin_tol=1e-13, lin_maxit=20000, method=MG,
+                      mg_reuse=reuse)
+        sm = mpm.step(ctx, cfg, Pm, body_z=bz, tol=1e-8, lin_tol=1e-8, lin_maxit=20000, method=MG,
+                      precision=1, mg_reuse=reuse)
+        assert so["status"] == 0 and sg["status"] == 0 and sm["status"] == 0
+        assert abs(sg["reaction"][2] - so["reaction"][2]) <= 1e-9 * abs(so["reaction"][2])
+        assert abs(sm["reaction"][2] - so["reaction"][2]) <= 1e-6 * abs(so["reaction"][2])
+    po, pg = om.points(), P.numpy()
+    assert np.max(np.abs(pg["x"] - po["x"])) <= 1e-9 * 0.1 * 3 / 50
+
+
+def test_multigrid_rejects_a_non_symmetric_tangent(gpu):
+    mpm, ctx, torch = gpu
+    cfg, bz = CASES["cone_d4_8"]()
+    om, mesh, P = both(gpu, cfg, bz)
+    nd = mesh.info()["ndof"]
+    g = mpm.assemble(ctx, mesh, cfg, torch.zeros(3 * nd, dtype=torch.float64, device="cuda"),
+                     body_z=bz)
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.solve(ctx, mesh, cfg, g["K"], -g["R"], tol=1e-8, method=MG)
+    assert e.value.code == 1
