@@ -51,6 +51,8 @@ def args():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--method", type=int, default=SOLVER,
                     help="Krylov method of mpm_solve_params (1 block-Jacobi PCG, 3 multigrid PCG)")
+    ap.add_argument("--inner-tol", type=float, default=1e-4,
+                    help="mixed precision: relative target of each FP32 inner solve")
     ap.add_argument("--mg-reuse", type=int, default=1,
                     help="method 3: keep the coarse operators across the Newton iterations of a step")
     return ap.parse_args()
@@ -270,7 +272,7 @@ def gpu_main(a):
                 host[k].copy_(P.t[k])
         step_kw = dict(load=1.0, tol=cfg["newton_tol"], maxit=cfg["newton_maxit"],
                        lin_tol=cfg["lin_tol"], lin_maxit=cfg["lin_maxit"], precision=precision,
-                       method=a.method, mg_reuse=a.mg_reuse)
+                       method=a.method, mg_reuse=a.mg_reuse, inner_tol=a.inner_tol)
         for n in range(1, W + 1):
             mpm.step(ctx, cfg, P, body_z=inputs.body_z(cfg, n), **step_kw)
         if e2e:
@@ -365,6 +367,7 @@ def gpu_main(a):
                    "newton_tol": cfg["newton_tol"], "krylov_tol": cfg["lin_tol"],
                    "krylov": {1: "block-Jacobi PCG", 3: "multigrid-preconditioned PCG"}.get(
                        a.method, "method %d" % a.method),
+                   "mixed_inner_tol": a.inner_tol, "mg_reuse": a.mg_reuse,
                    "step": "one load step: mesh rebuild + Newton to 1e-8 + point update",
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "inputs larger than L2 (stiffness %.2f GB FP32)" % (nnzb * 40 / 1e9)},

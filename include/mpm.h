@@ -183,7 +183,10 @@ enum {
   MPM_EXPORT_GHOST = 14,       /* double[nnzb] ghost coefficient per block      */
   MPM_EXPORT_BCMASK = 15,      /* int[ndof] fixed components                    */
   MPM_EXPORT_POPULATED = 16,   /* int[nleaf]                                    */
-  MPM_EXPORT_GHOST_FACES = 17  /* int[4*nghost]: K, N, axis, sign              */
+  MPM_EXPORT_GHOST_FACES = 17, /* int[4*nghost]: K, N, axis, sign              */
+  MPM_EXPORT_MG_LEVELS = 18    /* int[32]: per multigrid coarse level (up to 8):
+                                  depth, rows, stencil radius, stencil size;
+                                  zeros until a method-3 solve on this build */
 };
 int mpm_mesh_export(const mpm_mesh* mesh, int what, void* dst, size_t bytes);
 

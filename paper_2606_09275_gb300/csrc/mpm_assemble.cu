@@ -94,39 +94,49 @@ __device__ bool point_update_law(const Law& L, double E, double ys, const double
     be_new[s] = Q[3 * i] * bw[0] * Q[3 * j] + Q[3 * i + 1] * bw[1] * Q[3 * j + 1] + Q[3 * i + 2] * bw[2] * Q[3 * j + 2];
   }
   if (TANGENT) {
-    // theta_ab = (tau_a - tau_b)/(lam_a - lam_b) = g/2 * divided difference of ln.
-    // Built in FP64 and rounded once at the store: an FP32 rotation slows the
-    // last Newton iterations enough to move the converged state by ~1e-4.
+    // theta_ab = (tau_a - tau_b)/(lam_a - lam_b) = g/2 * divided difference of ln
+    // (in FP64), then the eigenbasis rotation of the 81 entries in the
+    // precision the tangent is stored in: FP32 for the mixed path, where it
+    // runs on the FP32 pipe
+    typedef TA R;
     double th01 = 0.5 * gr * ln_divdiff(lam[0], lam[1]);
     double th02 = 0.5 * gr * ln_divdiff(lam[0], lam[2]);
     double th12 = 0.5 * gr * ln_divdiff(lam[1], lam[2]);
-    double th[9] = {0.0, th01, th02, th01, 0.0, th12, th02, th12, 0.0};
-    double taum[9];
+    R th[9] = {(R)0, (R)th01, (R)th02, (R)th01, (R)0, (R)th12, (R)th02, (R)th12, (R)0};
+    R q[9], d[9], lr[3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      q[i] = (R)Q[i];
+      d[i] = (R)dd[i];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) lr[a] = (R)lam[a];
+    R taum[9];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         int s = (i == j) ? i : (i + j == 1 ? 3 : (i + j == 3 ? 4 : 5));
-        taum[3 * i + j] = tau6[s];
+        taum[3 * i + j] = (R)tau6[s];
       }
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j)
         for (int k = 0; k < 3; ++k)
           for (int m = 0; m < 3; ++m) {
-            double s = 0.0;
+            R s = (R)0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-              double qia = Q[3 * i + a];
+              R qia = q[3 * i + a];
 #pragma unroll
               for (int c = 0; c < 3; ++c) {
-                s += dd[3 * a + c] * qia * Q[3 * j + a] * Q[3 * k + c] * Q[3 * m + c];
+                s += d[3 * a + c] * qia * q[3 * j + a] * q[3 * k + c] * q[3 * m + c];
                 if (a != c)
-                  s += th[3 * a + c] * qia * Q[3 * j + c] *
-                       (lam[c] * Q[3 * k + a] * Q[3 * m + c] + lam[a] * Q[3 * k + c] * Q[3 * m + a]);
+                  s += th[3 * a + c] * qia * q[3 * j + c] *
+                       (lr[c] * q[3 * k + a] * q[3 * m + c] + lr[a] * q[3 * k + c] * q[3 * m + a]);
               }
             }
             if (j == k) s -= taum[3 * i + m];
-            Aout[(i * 9 + k * 3 + m) * 3 + j] = (TA)s;
+            Aout[(i * 9 + k * 3 + m) * 3 + j] = s;
           }
   }
   return true;

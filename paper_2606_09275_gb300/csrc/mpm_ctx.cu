@@ -409,6 +409,24 @@ extern "C" int mpm_mesh_export(const mpm_mesh* mc, int what, void* dst, size_t b
         need = sizeof(int) * 4 * m->nghost;
         src = m->gface.p;
         break;
+      case MPM_EXPORT_MG_LEVELS: {
+        // host data: depth, rows, stencil radius, stencil size per coarse level
+        int info[32] = {0};
+        const MGData* G = (m->mg && m->mg->gen == m->gen) ? m->mg : nullptr;
+        if (G)
+          for (int l = 0; l < G->nlev; ++l) {
+            info[4 * l] = G->lev[l].d;
+            info[4 * l + 1] = G->lev[l].nrow;
+            info[4 * l + 2] = G->lev[l].R;
+            info[4 * l + 3] = G->lev[l].S;
+          }
+        if (bytes < sizeof(info)) {
+          set_error(c, "export buffer too small");
+          return (int)MPM_ERR_ARG;
+        }
+        memcpy(dst, info, sizeof(info));
+        return (int)MPM_OK;
+      }
       default:
         set_error(c, "unknown export selector");
         return (int)MPM_ERR_ARG;

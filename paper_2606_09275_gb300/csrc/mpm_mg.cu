@@ -449,12 +449,17 @@ __global__ void k_mg_dense(int nrow, int S, int R, const int* __restrict__ xyz, 
 
 // ---------------------------------------------------------------- V-cycle kernels
 
-// x = Dinv b (rows padded to 4 components)
+// x = Dinv b (rows padded to 4 components); also clears the first nz rows of
+// zb (the next level's right-hand side, accumulated by atomics)
 template <class T>
 __global__ void k_mg_jac0(int n, const T* __restrict__ Dinv, const T* __restrict__ b, T* x,
-                          const Scal* sk, int k) {
+                          T* zb, int nz, const Scal* sk, int k) {
   if (skip(sk, k)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nz) {
+    T z4[4] = {0, 0, 0, 0};
+    st4(zb + 4 * (size_t)i, z4);
+  }
   if (i >= n) return;
   T bv[4], xv[4];
   ld4(b + 4 * (size_t)i, bv);
@@ -462,11 +467,13 @@ __global__ void k_mg_jac0(int n, const T* __restrict__ Dinv, const T* __restrict
   st4(x + 4 * (size_t)i, xv);
 }
 
-// fine level: r = b - K x (MODE 0), or xo = x + Dinv (b - K x) with r.z += b.xo (MODE 1)
+// fine level: MODE 0, b1 += P^T (b - K x) (the residual restricted to level 1
+// by atomics); MODE 1, xo = x + Dinv (b - K x) with r.z += b.xo
 template <class T, int MODE>
 __global__ void k_mg_fine(int nd, int npad, Sliced SK, const T* __restrict__ K, const T* __restrict__ b,
-                          const T* __restrict__ x, const T* __restrict__ Dinv, T* out, double* rz,
-                          const Scal* sk, int k) {
+                          const T* __restrict__ x, const T* __restrict__ Dinv, T* out,
+                          const int* __restrict__ pidx, const float* __restrict__ pw,
+                          const int* __restrict__ fmask, double* rz, const Scal* sk, int k) {
   __shared__ double sh[32];
   if (skip(sk, k)) return;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -479,7 +486,16 @@ __global__ void k_mg_fine(int nd, int npad, Sliced SK, const T* __restrict__ K, 
     for (int c = 0; c < 3; ++c) res[c] = r < nd ? bv[c] - y[c] : (T)0;
     res[3] = (T)0;
     if (MODE == 0) {
-      st4(out + 4 * (size_t)r, res);
+      if (r < nd) {
+        int mi = fmask[r];
+        for (int q = 0; q < 8; ++q) {
+          int a = pidx[8 * (size_t)r + q];
+          if (a < 0) break;
+          T w = (T)pw[8 * (size_t)r + q];
+          for (int c = 0; c < 3; ++c)
+            if (!((mi >> c) & 1)) atomicAdd(out + 4 * (size_t)a + c, w * res[c]);
+        }
+      }
     } else {
       T xv[4], d[4];
       ld4(x + 4 * (size_t)r, xv);
@@ -543,27 +559,6 @@ __global__ void k_mg_lvl(int nrow, int S, int R, int n1, const int* __restrict__
       st4(out + 4 * (size_t)a, xv);
     }
   }
-}
-
-// b1 = P^T r (fine -> level 1)
-template <class T>
-__global__ void k_mg_restrict1(int nrow, const int* __restrict__ pt_ptr, const int* __restrict__ pt_idx,
-                               const float* __restrict__ pw, const int* __restrict__ fmask,
-                               const T* __restrict__ rf, T* b, const Scal* sk, int k) {
-  if (skip(sk, k)) return;
-  int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= nrow) return;
-  T s[4] = {0, 0, 0, 0};
-  for (int t = pt_ptr[a]; t < pt_ptr[a + 1]; ++t) {
-    int e8 = pt_idx[t], i = e8 >> 3;
-    T w = (T)pw[e8];
-    int mi = fmask[i];
-    T rv[4];
-    ld4(rf + 4 * (size_t)i, rv);
-    for (int c = 0; c < 3; ++c)
-      if (!((mi >> c) & 1)) s[c] += w * rv[c];
-  }
-  st4(b + 4 * (size_t)a, s);
 }
 
 // xf += P x1 (level 1 -> fine)
@@ -836,21 +831,22 @@ void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, cons
   Sliced SK{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
   const int* fmask = ptr<int>(m->dof_mask);
   T* fx = ptr<T>(G.fx);
-  T* fr = ptr<T>(G.fr);
   const T* fD = ptr<T>(G.fDinv);
   const int FB = 8 * 32;  // rows per block of the fine row kernels
   // fine pre-smoothing from zero, residual, restriction
-  MPM_LAUNCH(k_mg_jac0<T><<<grid_for(npad, 256), 256, 0, st>>>(npad, fD, r, fx, sk, k));
-  MPM_LAUNCH(k_mg_fine<T, 0><<<grid_for(npad, FB), FB, 0, st>>>(nd, npad, SK, K, r, fx, fD, fr, nullptr, sk, k));
   MGLevel& L0 = G.lev[0];
-  MPM_LAUNCH(k_mg_restrict1<T><<<grid_for(L0.nrow, 128), 128, 0, st>>>(
-      L0.nrow, ptr<int>(G.pt_ptr), ptr<int>(G.pt_idx), ptr<float>(G.p_w), fmask, fr, ptr<T>(L0.b), sk, k));
+  MPM_LAUNCH(k_mg_jac0<T><<<grid_for(std::max(npad, L0.npad), 256), 256, 0, st>>>(npad, fD, r, fx, ptr<T>(L0.b),
+                                                                                 L0.npad, sk, k));
+  MPM_LAUNCH(k_mg_fine<T, 0><<<grid_for(npad, FB), FB, 0, st>>>(nd, npad, SK, K, r, fx, fD, ptr<T>(L0.b),
+                                                               ptr<int>(G.p_idx), ptr<float>(G.p_w), fmask,
+                                                               nullptr, sk, k));
   // down the uniform levels
   T* xcur[8];
   for (int l = 0; l + 1 < G.nlev; ++l) {
     MGLevel& L = G.lev[l];
     MGLevel& N = G.lev[l + 1];
-    MPM_LAUNCH(k_mg_jac0<T><<<grid_for(L.npad, 256), 256, 0, st>>>(L.npad, ptr<T>(L.Dinv), ptr<T>(L.b), ptr<T>(L.x), sk, k));
+    MPM_LAUNCH(k_mg_jac0<T><<<grid_for(L.npad, 256), 256, 0, st>>>(L.npad, ptr<T>(L.Dinv), ptr<T>(L.b), ptr<T>(L.x),
+                                                                   nullptr, 0, sk, k));
     MPM_LAUNCH(k_mg_lvl<T, 0><<<grid_for(L.nrow, MGW), 32 * MGW, 0, st>>>(
         L.nrow, L.S, L.R, L.n1, ptr<int>(L.xyz), ptr<int>(L.gid), ptr<T>(L.A), ptr<T>(L.b), ptr<T>(L.x),
         ptr<T>(L.Dinv), ptr<T>(L.r), sk, k));
@@ -873,7 +869,8 @@ void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, cons
   }
   MPM_LAUNCH(k_mg_prolong1<T><<<grid_for(nd, 128), 128, 0, st>>>(nd, ptr<int>(G.p_idx), ptr<float>(G.p_w), fmask,
                                                                   xcur[0], fx, sk, k));
-  MPM_LAUNCH(k_mg_fine<T, 1><<<grid_for(npad, FB), FB, 0, st>>>(nd, npad, SK, K, r, fx, fD, z, rz, sk, k));
+  MPM_LAUNCH(k_mg_fine<T, 1><<<grid_for(npad, FB), FB, 0, st>>>(nd, npad, SK, K, r, fx, fD, z, nullptr,
+                                                               nullptr, nullptr, rz, sk, k));
 }
 
 void mg_release(mpm_ctx* c, mpm_mesh* m) {

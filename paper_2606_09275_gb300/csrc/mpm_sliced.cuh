@@ -71,4 +71,56 @@ __device__ inline void apply_dinv(const V* __restrict__ Dinv, size_t i, const V*
   zv[3] = (V)0;
 }
 
+// y = row r of K times x with FP32 values and FP64 x, accumulated in
+// double-float arithmetic: each product k * x is split exactly as
+// k * x_hi = p + e (Dekker's two-product through one fused multiply-add),
+// k * x_lo is added to the error term, and p enters a (hi, lo) pair of floats
+// by Knuth's two-sum.  The sum carries about 48 significant bits, enough for
+// the FP64 refinement residual, while every operation runs on the FP32 pipe
+// (GB300 issues FP64 at 1/64 of the FP32 rate).
+__device__ inline void df_acc(float& hi, float& lo, float k, float xh, float xl) {
+  float p = k * xh;
+  float e = fmaf(k, xh, -p);
+  e = fmaf(k, xl, e);
+  float s = hi + p;
+  float bv = s - hi;
+  float err = (hi - (s - bv)) + (p - bv);
+  hi = s;
+  lo += err + e;
+}
+
+__device__ inline void sliced_row_df(int r, Sliced S, const float* __restrict__ K,
+                                     const double* __restrict__ x, double* y) {
+  int s = r >> 5, ln = r & 31;
+  int W = S.w[s];
+  long long b0 = S.base[s];
+  const float* Kb = K + 9 * b0;
+  const int* cb = S.scol + b0;
+  size_t plane = (size_t)32 * W;
+  float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+  for (int k4 = 0; k4 < (W >> 2); ++k4) {
+    size_t off = ((size_t)k4 * 32 + ln) * 4;
+    int4 c = *reinterpret_cast<const int4*>(cb + off);
+    int cc[4] = {c.x, c.y, c.z, c.w};
+    float v[9][4];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) ld4(Kb + e * plane + off, v[e]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float xh[3], xl[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double xv = x[3 * (size_t)cc[j] + d];
+        xh[d] = (float)xv;
+        xl[d] = (float)(xv - (double)xh[d]);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) df_acc(h[a], l[a], v[3 * a + d][j], xh[d], xl[d]);
+    }
+  }
+  for (int a = 0; a < 3; ++a) y[a] = (double)h[a] + (double)l[a];
+}
+
 }  // namespace mpm

@@ -418,7 +418,10 @@ __global__ void k_residual64(int nd, int npad, Sliced S, const T* __restrict__ K
   double part = 0.0;
   if (rr < npad) {
     double y[3];
-    sliced_row<T, double, double, 3>(rr, S, K, x, y);
+    if constexpr (sizeof(T) == 4)
+      sliced_row_df(rr, S, (const float*)K, x, y);
+    else
+      sliced_row<T, double, double, 3>(rr, S, K, x, y);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (rr < nd) {
       int mk = mask[rr];

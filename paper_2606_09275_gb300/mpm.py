@@ -23,7 +23,7 @@ FP64, MIXED = 0, 1
 
 EXPORT = dict(leaf_level=0, leaf_anchor=1, node_coord=2, node_hang=3, node_dof=4, cptr=5, cidx=6,
               cw=7, nsup=8, sidx=9, S=10, dS=11, row_ptr=12, col=13, ghost=14, bcmask=15,
-              populated=16, ghost_faces=17)
+              populated=16, ghost_faces=17, mg_levels=18)
 
 SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_octree_build", "mpm_mesh_free",
            "mpm_mesh_counts", "mpm_mesh_export", "mpm_assemble", "mpm_solve", "mpm_step",
@@ -286,7 +286,8 @@ class Mesh:
                      sidx=((P, MAXS), np.int32), S=((P, MAXS), np.float64),
                      dS=((P, MAXS, 3), np.float64), row_ptr=(nd + 1, np.int32),
                      col=(nz, np.int32), ghost=(nz, np.float64), bcmask=(nd, np.int32),
-                     populated=(nl, np.int32), ghost_faces=((info["nghost"], 4), np.int32))
+                     populated=(nl, np.int32), ghost_faces=((info["nghost"], 4), np.int32),
+                     mg_levels=((8, 4), np.int32))
         if what in ("cidx", "cw"):
             ncon = int(self.export("cptr")[-1])
             shape, dt = ncon, (np.int32 if what == "cidx" else np.float64)

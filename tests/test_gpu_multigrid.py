@@ -79,6 +79,12 @@ def test_multigrid_needs_far_fewer_iterations_at_scale(gpu):
                            precision=prec, mg_reuse=1)
         assert abs(sr["iterations"] - sm["iterations"]) <= 1
         assert np.max(np.abs(xr.cpu().numpy() - xm)) <= 1e-7 * np.abs(xm).max()
+    # levels: depths down to 1, each coarser grid with fewer rows
+    lv = mesh.export("mg_levels")
+    lv = lv[lv[:, 0] > 0]
+    print("multigrid levels (depth, rows, radius, stencil):", lv.tolist())
+    assert list(lv[:, 0]) == list(range(lv[0, 0], 0, -1))
+    assert np.all(np.diff(lv[:, 1]) < 0) and lv[0, 1] * 4 <= nd
 
 
 @pytest.mark.parametrize("reuse", [0, 1])
