@@ -438,6 +438,7 @@ __global__ void k_gather_points(int P, const int* __restrict__ perm, mpm_points 
 struct SubBox {
   double xi[3];  // centroid in the leaf's local coordinates
   double w;      // V_Kp / V_p
+  double is;     // 1 / leaf size (a power of two, exact)
   int K, s;
 };
 
@@ -515,7 +516,11 @@ __global__ void __launch_bounds__(32 * BW)
           break;
         }
         SubBox& o = sb[wi][n++];
-        for (int d = 0; d < 3; ++d) o.xi[d] = (0.5 * (a[d] + e[d]) - (double)ka[d]) / (double)s;
+        // the leaf size is a power of two: multiplying by its exact reciprocal
+        // equals the division and keeps the FP64 pipe (slow on this part) free
+        double is = ldexp(1.0, llev[K] - g.D);
+        o.is = is;
+        for (int d = 0; d < 3; ++d) o.xi[d] = (0.5 * (a[d] + e[d]) - (double)ka[d]) * is;
         o.w = vol / Vp;
         o.K = K;
         o.s = s;
@@ -617,7 +622,7 @@ __global__ void __launch_bounds__(32 * BW)
       double f0 = (c & 1) ? o.xi[0] : 1.0 - o.xi[0];
       double f1 = (c & 2) ? o.xi[1] : 1.0 - o.xi[1];
       double f2 = (c & 4) ? o.xi[2] : 1.0 - o.xi[2];
-      double inv = 1.0 / (double)o.s;
+      double inv = o.is;
       double d0 = (c & 1) ? inv : -inv, d1 = (c & 2) ? inv : -inv, d2 = (c & 4) ? inv : -inv;
       double ww = e_w[wi][e] * o.w;
       s0 += ww * (f0 * f1 * f2);
