@@ -188,7 +188,7 @@ def traffic_record(kernel):
     return r
 
 
-def adjoint_leg(dev):
+def adjoint_leg(dev, method):
     """Cost of the discrete adjoint against the forward run it differentiates:
     the punch at depth 3 -> 5 with lognormal E, 20 load steps, FP64, gradient
     of the final vertical punch reaction in every point's E and yield stress."""
@@ -199,7 +199,8 @@ def adjoint_leg(dev):
     pts = inputs.make_points(cfg)
     ctx = mpm.Context()
     path = autodiff.LoadPath(ctx, cfg, pts, cfg["nsteps"], tol=cfg["newton_tol"],
-                             lin_tol=cfg["lin_tol"], lin_maxit=cfg["lin_maxit"])
+                             lin_tol=cfg["lin_tol"], lin_maxit=cfg["lin_maxit"], method=method,
+                             mg_reuse=1)
     E = torch.tensor(pts["E"], device=dev)
     ys = torch.tensor(pts["ys"], device=dev)
     path.run(E, ys, keep=False)  # warm-up (allocations, module load)
@@ -225,7 +226,7 @@ def adjoint_leg(dev):
             "adjoint_over_forward": round(adj / fwd, 3),
             "adjoint_resolve_ms_per_step": round(ast["ms_forward"] / n, 3),
             "adjoint_backward_ms_per_step": round(ast["ms_backward"] / n, 3),
-            "adjoint_krylov_its": ast["lin_its"],
+            "adjoint_krylov_its": ast["lin_its"], "krylov_method": method,
             "forward_krylov_its": int(sum(s["lin_its"] for s in st_plain))}
 
 
@@ -401,7 +402,8 @@ def gpu_main(a):
     if mixed["clocks"]:
         line["clocks"] = mixed["clocks"]
     if not a.no_adjoint:
-        line["adjoint"] = adjoint_leg(dev)
+        # the adjoint workload is small (about a thousand dofs): block-Jacobi PCG
+        line["adjoint"] = adjoint_leg(dev, 1)
     if not a.no_cpu and world >= 1:
         v, dt, sample, its = run_oracle_sample(a.workload, 1)
         line["cpu_baseline"] = {"value": round(v, 5), "unit": "Newton it/s", "cores": 1,

@@ -242,8 +242,9 @@ int mpm_step(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body, const m
  * is smooth.  Per step, in reverse: rebuild the mesh from the checkpoint,
  * re-solve Newton (prm: the forward's Newton and Krylov settings; prm->load
  * is ignored, each checkpoint carries its own), solve K mu = dJ/du with the
- * FP64 consistent tangent by block-Jacobi PCG to prm->lin.tol within
- * prm->lin.maxit iterations (K is symmetric for material models 0 and 1;
+ * FP64 consistent tangent by PCG to prm->lin.tol within prm->lin.maxit
+ * iterations (multigrid-preconditioned if prm->lin.method is 3, else block
+ * Jacobi) (K is symmetric for material models 0 and 1;
  * model 2 is rejected with MPM_ERR_ARG), and run the backward kernels of the
  * residual, the point
  * update, the contact, the ghost term and the GIMP basis.

@@ -18,11 +18,11 @@ class LoadPath:
     and Krylov settings used by both the forward run and the adjoint."""
 
     def __init__(self, ctx, cfg, points, nsteps, capacity=None, tol=1e-12, maxit=30, lin_tol=1e-12,
-                 lin_maxit=200000, precision=mpm.FP64, method=0):
+                 lin_maxit=200000, precision=mpm.FP64, method=0, mg_reuse=0):
         self.ctx, self.cfg, self.points, self.nsteps = ctx, cfg, points, nsteps
         self.capacity = capacity or 64 * len(points["x"])
         self.kw = dict(tol=tol, maxit=maxit, lin_tol=lin_tol, lin_maxit=lin_maxit,
-                       precision=precision, method=method)
+                       precision=precision, method=method, mg_reuse=mg_reuse)
 
     def schedule(self, n):
         """(body position, load factor) of load step n (0-based)."""

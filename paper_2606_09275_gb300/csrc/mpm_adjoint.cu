@@ -965,7 +965,9 @@ extern "C" int mpm_adjoint(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* b
             dJ_dreaction[2], ub, Mid, A));
       MPM_LAUNCH(k_mask_vec<<<grid_for(nd, 256), 256, 0, st>>>(nd, ptr<int>(m->dof_mask), ub));
       // 3. K mu = seed (K symmetric)
-      mpm_solve_params lp{1, MPM_FP64, prm->lin.tol, prm->lin.maxit, 0.0};
+      // FP64 PCG, multigrid-preconditioned when the forward used method 3
+      mpm_solve_params lp{prm->lin.method == 3 ? 3 : 1, MPM_FP64, prm->lin.tol, prm->lin.maxit, 0.0,
+                          prm->lin.mg_reuse};
       mpm_solve_stats ls{};
       solve(c, m, *mat, K, ub, mu, lp, &ls);
       stt.lin_its += ls.iterations;

@@ -94,8 +94,7 @@ struct MGData {
   int nlev = 0;                // coarse levels (the last one is solved densely)
   MGLevel lev[8];
   Buf p_idx, p_w;              // fine dof -> up to 8 level-1 rows and weights
-  Buf pt_ptr, pt_idx, pt_w;    // level-1 row -> fine dofs and weights
-  Buf fDinv, fx, fr, fb;       // fine smoother inverses, fine V-cycle vectors
+  Buf fDinv, fx, fr;           // fine smoother inverses, fine V-cycle vectors
   Buf cinv;                    // dense inverse of the coarsest operator
   int n3c = 0;
 };

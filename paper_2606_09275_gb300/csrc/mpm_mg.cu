@@ -109,29 +109,12 @@ __global__ void k_mg_compact(int ng, int n1, const int* __restrict__ active,
   mask[r] = 7 & ~freeb[lin];
 }
 
-// fine -> level-1 entries: grid ids to rows; keys (row << 32 | entry) of P^T
-__global__ void k_mg_p1_rows(int nd, const int* __restrict__ gid, int* pidx, uint64_t* keys) {
+// fine -> level-1 entries: grid ids to rows
+__global__ void k_mg_p1_rows(int nd, const int* __restrict__ gid, int* pidx) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= 8LL * nd) return;
   int lin = pidx[e];
-  if (lin < 0) {
-    keys[e] = ~0ULL;
-    return;
-  }
-  int r = gid[lin];
-  pidx[e] = r;
-  keys[e] = ((uint64_t)(uint32_t)r << 32) | (uint64_t)e;
-}
-
-__global__ void k_mg_pt(long long n, const uint64_t* __restrict__ keys, int nrow, int* ptr,
-                        int* idx) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint32_t r = (uint32_t)(keys[i] >> 32);
-  if (r >= (uint32_t)nrow) return;
-  idx[i] = (int)(uint32_t)keys[i];
-  if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != r) ptr[r] = (int)i;
-  if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != r) ptr[r + 1] = (int)(i + 1);
+  if (lin >= 0) pidx[e] = gid[lin];
 }
 
 // largest level-1 cell distance between the two dofs of any stored block
@@ -164,61 +147,56 @@ __device__ inline int stencil_index(const int* cb, const int* ca, int R) {
   return dx + S1 * (dy + S1 * dz);
 }
 
-// write one accumulated row (Dirichlet components: identity on the diagonal)
+// Dirichlet components of a coarse row: identity on the diagonal (their rows
+// and columns receive no contribution from the Galerkin products)
 template <class T>
-__device__ inline void write_row(int a, int S, int R, int cm, const T* acc, T* A, int lane) {
+__global__ void k_mg_fix_masked(int nrow, int S, int R, const int* __restrict__ cmask, T* A) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nrow) return;
+  int cm = cmask[a];
+  if (!cm) return;
   int S1 = 2 * R + 1, center = R + S1 * (R + S1 * R);
-  T* row = A + (size_t)a * S * 9;
-  for (int u = lane; u < 9 * S; u += 32) {
-    int o = u / 9, e = u - 9 * o, ci = e / 3, ck = e - 3 * ci;
-    T v = acc[u];
-    if (((cm >> ci) & 1) || ((cm >> ck) & 1)) v = (o == center && ci == ck) ? (T)1 : (T)0;
-    row[u] = v;
-  }
+  for (int c = 0; c < 3; ++c)
+    if ((cm >> c) & 1) A[((size_t)a * S + center) * 9 + 4 * c] = (T)1;
 }
 
-// level 1: one warp per coarse row a; sum over fine dofs i with P_ia != 0 of
-// their block rows, each block spread to the coarse columns of its dof j.
-// Lanes take different fine rows i (consecutive columns of one row share
-// their coarse targets, which would serialise the shared-memory atomics).
+// level 1: one warp per fine dof i; its block row, weighted by P_ia for every
+// coarse row a it interpolates from, spread to the coarse columns of each
+// column dof j.  The sums go to the zeroed coarse operator by global atomics
+// (resolved in L2); a warp per fine row keeps the work balanced when the
+// coarse grid is much coarser than the finest leaves.
 template <class T>
-__global__ void k_mg_rap1(int nrow, int R, int S, const int* __restrict__ pt_ptr,
-                          const int* __restrict__ pt_idx, const float* __restrict__ pw,
+__global__ void k_mg_rap1(int nd, int R, int S, const float* __restrict__ pw,
                           const int* __restrict__ pidx, const int* __restrict__ fmask,
                           const int* __restrict__ rp, const int* __restrict__ col, Sliced SK,
-                          const T* __restrict__ K, const int* __restrict__ xyz,
-                          const int* __restrict__ cmask, T* A, int* err) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* acc = (T*)smraw + (size_t)wi * 9 * S;
-  int a = blockIdx.x * (blockDim.x >> 5) + wi;
-  if (a >= nrow) return;
-  for (int u = lane; u < 9 * S; u += 32) acc[u] = (T)0;
-  __syncwarp();
-  int ca[3];
-  unpack3(xyz[a], ca);
-  for (int t = pt_ptr[a] + lane; t < pt_ptr[a + 1]; t += 32) {
-    int e8 = pt_idx[t];
-    int i = e8 >> 3;
-    T wi_ = (T)pw[e8];
-    int mi = fmask[i];
-    int s0 = rp[i], nb = rp[i + 1] - s0;
-    int sl = i >> 5, W = SK.w[sl];
-    long long b0 = SK.base[sl];
-    for (int idx = 0; idx < nb; ++idx) {
-      int j = col[s0 + idx];
-      int mj = fmask[j];
-      long long slot = sliced_slot(b0, i, idx);
-      T v[9];
+                          const T* __restrict__ K, const int* __restrict__ xyz, T* A, int* err) {
+  int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= nd) return;
+  int mi = fmask[i];
+  int s0 = rp[i], nb = rp[i + 1] - s0;
+  int sl = i >> 5, W = SK.w[sl];
+  long long b0 = SK.base[sl];
+  for (int idx = lane; idx < nb; idx += 32) {
+    int j = col[s0 + idx];
+    int mj = fmask[j];
+    long long slot = sliced_slot(b0, i, idx);
+    T v[9];
 #pragma unroll
-      for (int e = 0; e < 9; ++e) {
-        int ci = e / 3, ck = e - 3 * (e / 3);
-        v[e] = (((mi >> ci) & 1) || ((mj >> ck) & 1)) ? (T)0 : K[sliced_entry(b0, W, slot, e)];
-      }
+    for (int e = 0; e < 9; ++e) {
+      int ci = e / 3, ck = e - 3 * (e / 3);
+      v[e] = (((mi >> ci) & 1) || ((mj >> ck) & 1)) ? (T)0 : K[sliced_entry(b0, W, slot, e)];
+    }
+    for (int qa = 0; qa < 8; ++qa) {
+      int a = pidx[8 * (size_t)i + qa];
+      if (a < 0) break;
+      T wa = (T)pw[8 * (size_t)i + qa];
+      int ca[3];
+      unpack3(xyz[a], ca);
+      T* row = A + (size_t)a * S * 9;
       for (int q = 0; q < 8; ++q) {
         int b = pidx[8 * (size_t)j + q];
         if (b < 0) break;
-        T f = wi_ * (T)pw[8 * (size_t)j + q];
+        T f = wa * (T)pw[8 * (size_t)j + q];
         int cb[3];
         unpack3(xyz[b], cb);
         int o = stencil_index(cb, ca, R);
@@ -227,83 +205,81 @@ __global__ void k_mg_rap1(int nrow, int R, int S, const int* __restrict__ pt_ptr
           continue;
         }
 #pragma unroll
-        for (int e = 0; e < 9; ++e) atomicAdd(acc + 9 * o + e, f * v[e]);
+        for (int e = 0; e < 9; ++e) atomicAdd(row + 9 * o + e, f * v[e]);
       }
     }
   }
-  __syncwarp();
-  write_row<T>(a, S, R, cmask[a], acc, A, lane);
 }
 
-// uniform level -> next coarser: fine rows 2C + delta (weights
-// prod(1 - |delta|/2)); lanes take different fine rows
+// uniform level -> next coarser: one warp per row i of the finer level; its
+// operator row, weighted by the trilinear weights prod(1 - |delta|/2) of the
+// coarse rows a around it, spread to the coarse columns of each column j
 template <class T>
-__global__ void k_mg_rapu(int nrow, int Rc, int Sc, const int* __restrict__ xyz_c,
-                          const int* __restrict__ cmask, int Rf, int Sf, int n1f,
-                          const int* __restrict__ gid_f, const int* __restrict__ xyz_f,
-                          const int* __restrict__ fmask, const T* __restrict__ Af, T* A, int* err) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* acc = (T*)smraw + (size_t)wi * 9 * Sc;
-  int a = blockIdx.x * (blockDim.x >> 5) + wi;
-  if (a >= nrow) return;
-  for (int u = lane; u < 9 * Sc; u += 32) acc[u] = (T)0;
-  __syncwarp();
-  int ca[3];
-  unpack3(xyz_c[a], ca);
+__global__ void k_mg_rapu(int nrow_f, int Rc, int Sc, int n1c, const int* __restrict__ gid_c,
+                          int Rf, int Sf, int n1f, const int* __restrict__ gid_f,
+                          const int* __restrict__ xyz_f, const int* __restrict__ fmask,
+                          const T* __restrict__ Af, T* A, int* err) {
+  int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= nrow_f) return;
+  int fi[3];
+  unpack3(xyz_f[i], fi);
+  int mi = fmask[i];
   int S1f = 2 * Rf + 1;
-  for (int dl = lane; dl < 27; dl += 32) {
-    int del[3] = {dl % 3 - 1, (dl / 3) % 3 - 1, dl / 9 - 1};
-    int fi[3];
-    bool in = true;
-    for (int d = 0; d < 3; ++d) {
-      fi[d] = 2 * ca[d] + del[d];
-      in = in && fi[d] >= 0 && fi[d] < n1f;
-    }
-    if (!in) continue;
-    int i = gid_f[fi[0] + n1f * (fi[1] + n1f * fi[2])];
-    if (i < 0) continue;
-    T wi_ = (T)1;
-    for (int d = 0; d < 3; ++d) wi_ *= del[d] ? (T)0.5 : (T)1;
-    int mi = fmask[i];
-    const T* row = Af + (size_t)i * Sf * 9;
-    for (int of = 0; of < Sf; ++of) {
-      int fj[3] = {fi[0] + of % S1f - Rf, fi[1] + (of / S1f) % S1f - Rf, fi[2] + of / (S1f * S1f) - Rf};
-      if (fj[0] < 0 || fj[1] < 0 || fj[2] < 0 || fj[0] >= n1f || fj[1] >= n1f || fj[2] >= n1f) continue;
-      int j = gid_f[fj[0] + n1f * (fj[1] + n1f * fj[2])];
-      if (j < 0) continue;
-      int mj = fmask[j];
-      T v[9];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) {
-        int ci = e / 3, ck = e - 3 * (e / 3);
-        v[e] = (((mi >> ci) & 1) || ((mj >> ck) & 1)) ? (T)0 : row[9 * of + e];
-      }
-      int lo[3], hi[3];
-      for (int d = 0; d < 3; ++d) {
-        lo[d] = fj[d] >> 1;
-        hi[d] = (fj[d] + 1) >> 1;
-      }
-      for (int z = lo[2]; z <= hi[2]; ++z)
-        for (int y = lo[1]; y <= hi[1]; ++y)
-          for (int x = lo[0]; x <= hi[0]; ++x) {
-            T f = wi_;
-            if (lo[0] != hi[0]) f *= (T)0.5;
-            if (lo[1] != hi[1]) f *= (T)0.5;
-            if (lo[2] != hi[2]) f *= (T)0.5;
-            int cb[3] = {x, y, z};
-            int o = stencil_index(cb, ca, Rc);
-            if (o < 0) {
-              atomicOr(err, EB_ROW);
-              continue;
-            }
-#pragma unroll
-            for (int e = 0; e < 9; ++e) atomicAdd(acc + 9 * o + e, f * v[e]);
-          }
-    }
+  int alo[3], ahi[3];
+  for (int d = 0; d < 3; ++d) {
+    alo[d] = fi[d] >> 1;
+    ahi[d] = (fi[d] + 1) >> 1;
   }
-  __syncwarp();
-  write_row<T>(a, Sc, Rc, cmask[a], acc, A, lane);
+  const T* frow = Af + (size_t)i * Sf * 9;
+  for (int of = lane; of < Sf; of += 32) {
+    int fj[3] = {fi[0] + of % S1f - Rf, fi[1] + (of / S1f) % S1f - Rf, fi[2] + of / (S1f * S1f) - Rf};
+    if (fj[0] < 0 || fj[1] < 0 || fj[2] < 0 || fj[0] >= n1f || fj[1] >= n1f || fj[2] >= n1f) continue;
+    int j = gid_f[fj[0] + n1f * (fj[1] + n1f * fj[2])];
+    if (j < 0) continue;
+    int mj = fmask[j];
+    T v[9];
+    bool any = false;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      int ci = e / 3, ck = e - 3 * (e / 3);
+      v[e] = (((mi >> ci) & 1) || ((mj >> ck) & 1)) ? (T)0 : frow[9 * of + e];
+      any = any || v[e] != (T)0;
+    }
+    if (!any) continue;
+    int blo[3], bhi[3];
+    for (int d = 0; d < 3; ++d) {
+      blo[d] = fj[d] >> 1;
+      bhi[d] = (fj[d] + 1) >> 1;
+    }
+    for (int az = alo[2]; az <= ahi[2]; ++az)
+      for (int ay = alo[1]; ay <= ahi[1]; ++ay)
+        for (int ax = alo[0]; ax <= ahi[0]; ++ax) {
+          int a = gid_c[ax + n1c * (ay + n1c * az)];
+          if (a < 0) continue;
+          T wa = (T)1;
+          if (alo[0] != ahi[0]) wa *= (T)0.5;
+          if (alo[1] != ahi[1]) wa *= (T)0.5;
+          if (alo[2] != ahi[2]) wa *= (T)0.5;
+          T* row = A + (size_t)a * Sc * 9;
+          int ca[3] = {ax, ay, az};
+          for (int z = blo[2]; z <= bhi[2]; ++z)
+            for (int y = blo[1]; y <= bhi[1]; ++y)
+              for (int x = blo[0]; x <= bhi[0]; ++x) {
+                T f = wa;
+                if (blo[0] != bhi[0]) f *= (T)0.5;
+                if (blo[1] != bhi[1]) f *= (T)0.5;
+                if (blo[2] != bhi[2]) f *= (T)0.5;
+                int cb[3] = {x, y, z};
+                int o = stencil_index(cb, ca, Rc);
+                if (o < 0) {
+                  atomicOr(err, EB_ROW);
+                  continue;
+                }
+#pragma unroll
+                for (int e = 0; e < 9; ++e) atomicAdd(row + 9 * o + e, f * v[e]);
+              }
+        }
+  }
 }
 
 // ---------------------------------------------------------------- smoother inverses
@@ -676,8 +652,6 @@ __global__ void k_mg_coarse(int nrow, const T* __restrict__ Cinv, const T* __res
 
 int pad32(int n) { return (n + 31) & ~31; }
 
-size_t rap_smem(int S, size_t tsz) { return (size_t)MGW * 9 * S * tsz; }
-
 // structure for the current mesh build (once per build)
 void mg_structure(mpm_ctx* c, mpm_mesh* m) {
   cudaStream_t st = c->stream;
@@ -727,15 +701,7 @@ void mg_structure(mpm_ctx* c, mpm_mesh* m) {
     MPM_LAUNCH(k_mg_compact<<<grid_for(ng, 256), 256, 0, st>>>(ng, L.n1, active, scan, freeb, gid,
                                                               ptr<int>(L.xyz), ptr<int>(L.mask)));
     if (l == 0) {
-      // P^T of level 1
-      long long ne = 8LL * nd;
-      uint64_t* keys = grow<uint64_t>(c, c->tmp[6], ne);
-      uint64_t* alt = grow<uint64_t>(c, c->tmp[7], ne);
-      MPM_LAUNCH(k_mg_p1_rows<<<grid_for(ne, 256), 256, 0, st>>>(nd, gid, ptr<int>(G.p_idx), keys));
-      cub_sort_u64(c, keys, alt, (int)ne, 64);
-      int* ptr_ = grow<int>(c, G.pt_ptr, L.nrow + 1);
-      MPM_CUDA(cudaMemsetAsync(ptr_, 0, sizeof(int) * (L.nrow + 1), st));
-      MPM_LAUNCH(k_mg_pt<<<grid_for(ne, 256), 256, 0, st>>>(ne, keys, L.nrow, ptr_, grow<int>(c, G.pt_idx, ne)));
+      MPM_LAUNCH(k_mg_p1_rows<<<grid_for(8LL * nd, 256), 256, 0, st>>>(nd, gid, ptr<int>(G.p_idx)));
       // stencil radius of level 1 from the reach of the fine blocks
       int* reach = (int*)(c->d_red + 8);
       MPM_CUDA(cudaMemsetAsync(reach, 0, sizeof(int), st));
@@ -770,26 +736,22 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
   T* fD = grow<T>(c, G.fDinv, 12 * (size_t)npad);
   MPM_LAUNCH(k_mg_dinv_fine<T><<<grid_for(npad, 256), 256, 0, st>>>(nd, npad, SK, K, fD, c->d_err));
   grow<T>(c, G.fx, 4 * (size_t)npad);
-  grow<T>(c, G.fr, 4 * (size_t)npad);
   if (!coarse) return;
   for (int l = 0; l < G.nlev; ++l) {
     MGLevel& L = G.lev[l];
     T* A = grow<T>(c, L.A, (size_t)L.nrow * L.S * 9);
-    size_t smem = rap_smem(L.S, sizeof(T));
-    if (smem > 200 * 1024) throw CudaError(MPM_ERR_SUPPORT, "multigrid: coarse stencil too wide");
+    MPM_CUDA(cudaMemsetAsync(A, 0, sizeof(T) * (size_t)L.nrow * L.S * 9, st));
     if (l == 0) {
-      MPM_CUDA(cudaFuncSetAttribute(k_mg_rap1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      MPM_LAUNCH(k_mg_rap1<T><<<grid_for(L.nrow, MGW), 32 * MGW, smem, st>>>(
-          L.nrow, L.R, L.S, ptr<int>(G.pt_ptr), ptr<int>(G.pt_idx), ptr<float>(G.p_w), ptr<int>(G.p_idx),
-          ptr<int>(m->dof_mask), ptr<int>(m->row_ptr), ptr<int>(m->col), SK, K, ptr<int>(L.xyz),
-          ptr<int>(L.mask), A, c->d_err));
+      MPM_LAUNCH(k_mg_rap1<T><<<grid_for(nd, 8), 256, 0, st>>>(
+          nd, L.R, L.S, ptr<float>(G.p_w), ptr<int>(G.p_idx), ptr<int>(m->dof_mask), ptr<int>(m->row_ptr),
+          ptr<int>(m->col), SK, K, ptr<int>(L.xyz), A, c->d_err));
     } else {
       MGLevel& F = G.lev[l - 1];
-      MPM_CUDA(cudaFuncSetAttribute(k_mg_rapu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      MPM_LAUNCH(k_mg_rapu<T><<<grid_for(L.nrow, MGW), 32 * MGW, smem, st>>>(
-          L.nrow, L.R, L.S, ptr<int>(L.xyz), ptr<int>(L.mask), F.R, F.S, F.n1, ptr<int>(F.gid),
-          ptr<int>(F.xyz), ptr<int>(F.mask), ptr<T>(F.A), A, c->d_err));
+      MPM_LAUNCH(k_mg_rapu<T><<<grid_for(F.nrow, 8), 256, 0, st>>>(
+          F.nrow, L.R, L.S, L.n1, ptr<int>(L.gid), F.R, F.S, F.n1, ptr<int>(F.gid), ptr<int>(F.xyz),
+          ptr<int>(F.mask), ptr<T>(F.A), A, c->d_err));
     }
+    MPM_LAUNCH(k_mg_fix_masked<T><<<grid_for(L.nrow, 128), 128, 0, st>>>(L.nrow, L.S, L.R, ptr<int>(L.mask), A));
     MPM_LAUNCH(k_mg_dinv<T><<<grid_for(L.npad, 128), 128, 0, st>>>(L.nrow, L.npad, L.S, L.R, A,
                                                                    grow<T>(c, L.Dinv, 12 * (size_t)L.npad), c->d_err));
     // level vectors: padding rows stay zero
@@ -880,7 +842,7 @@ void mg_release(mpm_ctx* c, mpm_mesh* m) {
     Buf* b[] = {&L.gid, &L.xyz, &L.mask, &L.A, &L.Dinv, &L.b, &L.x, &L.r};
     for (Buf* x : b) free_buf(c, *x);
   }
-  Buf* b[] = {&G.p_idx, &G.p_w, &G.pt_ptr, &G.pt_idx, &G.pt_w, &G.fDinv, &G.fx, &G.fr, &G.fb, &G.cinv};
+  Buf* b[] = {&G.p_idx, &G.p_w, &G.fDinv, &G.fx, &G.fr, &G.cinv};
   for (Buf* x : b) free_buf(c, *x);
   delete m->mg;
   m->mg = nullptr;

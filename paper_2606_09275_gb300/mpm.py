@@ -399,7 +399,7 @@ def blocks(ctx, mesh, K, precision=FP64):
 
 
 def adjoint(ctx, cfg, checkpoints, w, tol=1e-8, maxit=30, lin_tol=1e-10, lin_maxit=20000,
-            method=0, precision=FP64, inner_tol=1e-3):
+            method=0, precision=FP64, inner_tol=1e-3, mg_reuse=0):
     """mpm_adjoint: gradient of w . reaction (end of the last step) with respect
     to the per-point E and yield stress of the first checkpoint.
 
@@ -416,7 +416,8 @@ def adjoint(ctx, cfg, checkpoints, w, tol=1e-8, maxit=30, lin_tol=1e-10, lin_max
     dE = torch.zeros(p0.count, dtype=torch.float64, device=p0.t["E"].device)
     dys = torch.zeros_like(dE)
     wv = (C.c_double * 3)(*[float(v) for v in w])
-    sp = StepParams(1.0, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol))
+    sp = StepParams(1.0, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol,
+                                                 mg_reuse))
     st_ = AdjointStats()
     st = lib().mpm_adjoint(ctx.h, C.byref(domain(cfg)), C.byref(rigid(cfg)), C.byref(adapt(cfg)),
                            C.byref(material(cfg)), arr, n, C.byref(sp),

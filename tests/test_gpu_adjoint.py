@@ -173,3 +173,15 @@ def test_adjoint_rejects_the_non_symmetric_model(gpu):
     with pytest.raises(mpm.MPMError) as e:
         mpm.adjoint(ctx, cfg, [(P, inputs.body_z(cfg, 1), 1.0)], W)
     assert e.value.code == 1
+
+
+def test_adjoint_with_multigrid_pcg_matches(gpu, problem):
+    # the same gradient when forward and adjoint solves use the multigrid PCG
+    mpm, autodiff, ctx, torch = gpu
+    path = autodiff.LoadPath(ctx, problem["cfg"], problem["pts"], NSTEPS, method=3, mg_reuse=1)
+    r, ck, _ = path.run(problem["E"], problem["ys"])
+    dE, dys, _ = path.gradient(ck, W)
+    dE, dys = dE.cpu().numpy(), dys.cpu().numpy()
+    assert np.allclose(r.numpy(), problem["reaction"], rtol=1e-9)
+    assert np.max(np.abs(dE - problem["dE"])) <= 1e-7 * np.abs(problem["dE"]).max()
+    assert np.max(np.abs(dys - problem["dys"])) <= 1e-7 * np.abs(problem["dys"]).max()
