@@ -247,31 +247,32 @@ __global__ void k_residual_rows(int nd, double load, const int* __restrict__ rp,
 
 constexpr int TW = 4;  // warps per block of the tangent gather (at most)
 
-__device__ inline int find_in(const int* a, int n, int v) {
-  int lo = 0, hi = n - 1;
-  while (lo <= hi) {
-    int mid = (lo + hi) >> 1;
-    int x = a[mid];
-    if (x == v) return mid;
-    if (x < v)
-      lo = mid + 1;
-    else
-      hi = mid - 1;
-  }
-  return -1;
+
+// open-addressing table of a row's columns (dof -> position in the row), in
+// shared memory: a power of two at least twice the longest row
+__host__ __device__ inline int tangent_hash_size(int mr) {
+  int h = 64;
+  while (h < 2 * mr) h <<= 1;
+  return h;
 }
 
 template <class T>
 __host__ __device__ inline size_t tangent_warp_bytes(int mr) {
-  return (size_t)mr * (9 * sizeof(T) + sizeof(int)) + 32 * sizeof(T);
+  return (size_t)mr * 9 * sizeof(T) + 32 * sizeof(T) + (size_t)tangent_hash_size(mr) * 2 * sizeof(int);
+}
+
+__device__ inline unsigned tangent_hash(int c, int hmask) {
+  return ((unsigned)c * 2654435761u >> 7) & (unsigned)hmask;
 }
 
 // One warp owns block row r: for every point p with r in its support (local
 // index k), K_{r,w} += V0_p (grad_x S_k)^T A'_p (grad_x S_w) for all w in the
 // support of p.  The row accumulates in shared memory (mr = longest row, a
-// multiple of 4), in source order, free of atomics and deterministic; ghost
-// coefficients and the Dirichlet identity rows/columns are applied when the
-// row is written out, coalesced, in the row-sliced layout.
+// multiple of 4), in source order, free of atomics and deterministic; the
+// position of a column in the row comes from a per-row hash table, and the 27
+// entries of (grad_x S_k)^T A'_p sit in registers while the point's support
+// is swept.  Ghost coefficients and the Dirichlet identity rows/columns are
+// applied when the row is written out, coalesced, in the sliced layout.
 template <class T>
 __global__ void __launch_bounds__(32 * TW)
     k_tangent_rows(int nd, int P, int mr, const int* __restrict__ rp, const int* __restrict__ col,
@@ -284,7 +285,9 @@ __global__ void __launch_bounds__(32 * TW)
   int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* acc = (T*)(smraw + wi * tangent_warp_bytes<T>(mr));
   T* Tt = acc + 9 * (size_t)mr;
-  int* cols = (int*)(Tt + 32);
+  int* hkey = (int*)(Tt + 32);
+  int hs = tangent_hash_size(mr), hmask = hs - 1;
+  int* hval = hkey + hs;
   int r = blockIdx.x * (blockDim.x >> 5) + wi;
   if (r >= nd) return;
   int s0 = rp[r], nb = rp[r + 1] - s0;
@@ -292,8 +295,15 @@ __global__ void __launch_bounds__(32 * TW)
     if (lane == 0) atomicOr(err, EB_ROW);
     return;
   }
-  for (int i = lane; i < nb; i += 32) cols[i] = col[s0 + i];
+  for (int i = lane; i < hs; i += 32) hkey[i] = -1;
   for (int i = lane; i < 9 * nb; i += 32) acc[i] = (T)0;
+  __syncwarp();
+  for (int i = lane; i < nb; i += 32) {
+    int c = col[s0 + i];
+    unsigned h = tangent_hash(c, hmask);
+    while (atomicCAS(hkey + h, -1, c) != -1) h = (h + 1) & hmask;
+    hval[h] = i;
+  }
   __syncwarp();
   for (long long q = sptr[r]; q < sptr[r + 1]; ++q) {
     uint32_t sid = (uint32_t)skeys[q];
@@ -307,15 +317,21 @@ __global__ void __launch_bounds__(32 * TW)
       Tt[lane] = v0 * (gk0 * A[0] + gk1 * A[1] + gk2 * A[2]);
     }
     __syncwarp();
+    T t[27];
+#pragma unroll
+    for (int e = 0; e < 27; ++e) t[e] = Tt[e];
     int n = nsup[w];
     for (int l = lane; l < n; l += 32) {
       size_t o = (size_t)w * MAXS + l;
       int c = sidx[o];
       T g0 = gx[3 * o], g1 = gx[3 * o + 1], g2 = gx[3 * o + 2];
-      int idx = find_in(cols, nb, c);
-      if (idx < 0) continue;
+      unsigned h = tangent_hash(c, hmask);
+      int key;
+      while ((key = hkey[h]) != c && key != -1) h = (h + 1) & hmask;
+      if (key != c) continue;
+      int idx = hval[h];
 #pragma unroll
-      for (int e = 0; e < 9; ++e) acc[e * nb + idx] += Tt[3 * e] * g0 + Tt[3 * e + 1] * g1 + Tt[3 * e + 2] * g2;
+      for (int e = 0; e < 9; ++e) acc[e * nb + idx] += t[3 * e] * g0 + t[3 * e + 1] * g1 + t[3 * e + 2] * g2;
     }
     __syncwarp();
   }
@@ -332,7 +348,7 @@ __global__ void __launch_bounds__(32 * TW)
       continue;
     }
     T kv = (T)kg[s0 + i];
-    int c = cols[i];
+    int c = col[s0 + i];
     int mc = mask[c];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
