@@ -453,10 +453,16 @@ __device__ inline int warp_excl_scan(int v, int lane) {
 
 constexpr int BW = 4;  // warps per block of the basis kernel
 
+constexpr int BH = 512;  // per-warp hash set of the basis kernel's node ids (at most MAXS distinct)
+
+__device__ inline unsigned basis_hash(int j) { return ((unsigned)j * 2654435761u) >> 23; }
+
 // Eq. (GIMP numerical), one warp per point (cell-sorted order):
 //  1. lane 0 cuts the domain into its leaf intersections (centre, volume);
 //  2. the (leaf corner, constraint entry) pairs are listed in a fixed order;
-//  3. the distinct independent nodes are ranked (support sorted by node id);
+//  3. the distinct independent nodes are found by a shared-memory hash set and
+//     ranked by id (support sorted by node id); the entries are grouped by
+//     node, each group keeping list order;
 //  4. lane k sums the contributions of support node k in list order, so the
 //     result does not depend on scheduling.
 __global__ void __launch_bounds__(32 * BW)
@@ -469,10 +475,16 @@ __global__ void __launch_bounds__(32 * BW)
   __shared__ SubBox sb[BW][MAXK];
   __shared__ int e_node[BW][MAXE];
   __shared__ short e_q[BW][MAXE];
-  __shared__ unsigned char e_first[BW][MAXE];
-  __shared__ double e_w[BW][MAXE];
+  __shared__ short e_ord[BW][MAXE];
+  __shared__ float e_w[BW][MAXE];  // constraint weights are products of 1/2 and 1/4: exact
+  __shared__ unsigned char e_rk[BW][MAXE];
   __shared__ int sup[BW][MAXS];
-  __shared__ int nsub_s[BW];
+  __shared__ int hkey[BW][BH];
+  __shared__ unsigned char hslot[BW][BH];
+  __shared__ int uid[BW][MAXS];
+  __shared__ unsigned char urank[BW][MAXS];
+  __shared__ int ucnt[BW][MAXS], ubase[BW][MAXS], ustart[BW][MAXS];
+  __shared__ int nsub_s[BW], nu_s[BW];
   int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int w = blockIdx.x * BW + wi;
   if (w >= P) return;
@@ -575,33 +587,32 @@ __global__ void __launch_bounds__(32 * BW)
     for (int t = cptr[node]; t < cptr[node + 1]; ++t) {
       e_node[wi][pos] = cidx[t];
       e_q[wi][pos] = (short)q;
-      e_w[wi][pos] = cw[t];
+      e_w[wi][pos] = (float)cw[t];
       ++pos;
     }
   }
   __syncwarp();
-  // 3. distinct nodes, ranked by id
+  // 3. distinct nodes (hash set), ranked by id, entries grouped by node
+  for (int i = lane; i < BH; i += 32) hkey[wi][i] = -1;
+  if (lane == 0) nu_s[wi] = 0;
+  __syncwarp();
   for (int e = lane; e < total; e += 32) {
     int j = e_node[wi][e];
-    unsigned char f = 1;
-    for (int e2 = 0; e2 < e; ++e2)
-      if (e_node[wi][e2] == j) {
-        f = 0;
+    unsigned h = basis_hash(j);
+    for (int probe = 0; probe < BH; ++probe) {
+      int prev = atomicCAS(&hkey[wi][h], -1, j);
+      if (prev == -1) {
+        int slot = atomicAdd(&nu_s[wi], 1);
+        if (slot < MAXS) uid[wi][slot] = j;
+        hslot[wi][h] = (unsigned char)min(slot, 255);
         break;
       }
-    e_first[wi][e] = f;
+      if (prev == j) break;
+      h = (h + 1) & (BH - 1);
+    }
   }
   __syncwarp();
-  int cnt = 0;
-  for (int e = lane; e < total; e += 32) {
-    if (!e_first[wi][e]) continue;
-    int j = e_node[wi][e];
-    int r = 0;
-    for (int e2 = 0; e2 < total; ++e2) r += (e_first[wi][e2] && e_node[wi][e2] < j) ? 1 : 0;
-    if (r < MAXS) sup[wi][r] = j;
-    ++cnt;
-  }
-  int ns = warp_sum_int(cnt);
+  int ns = nu_s[wi];
   if (ns > MAXS) {
     if (lane == 0) {
       atomicOr(err, EB_SUPPORT);
@@ -609,13 +620,54 @@ __global__ void __launch_bounds__(32 * BW)
     }
     return;
   }
+  for (int u = lane; u < ns; u += 32) {
+    int j = uid[wi][u], r = 0;
+    for (int u2 = 0; u2 < ns; ++u2) r += uid[wi][u2] < j ? 1 : 0;
+    urank[wi][u] = (unsigned char)r;
+    sup[wi][r] = j;
+  }
+  for (int u = lane; u < MAXS; u += 32) ucnt[wi][u] = 0;
   __syncwarp();
+  // rank of every entry (hash lookup) and the count per rank
+  for (int e = lane; e < total; e += 32) {
+    int j = e_node[wi][e];
+    unsigned h = basis_hash(j);
+    while (hkey[wi][h] != j) h = (h + 1) & (BH - 1);
+    int r = urank[wi][hslot[wi][h]];
+    e_rk[wi][e] = (unsigned char)r;
+    atomicAdd(&ucnt[wi][r], 1);
+  }
+  __syncwarp();
+  {
+    int c0 = lane < ns ? ucnt[wi][lane] : 0, c1 = lane + 32 < ns ? ucnt[wi][lane + 32] : 0;
+    int x0 = warp_excl_scan(c0, lane), x1 = warp_excl_scan(c1, lane);
+    int t0 = __shfl_sync(0xffffffffu, x0 + c0, 31);
+    if (lane < ns) ubase[wi][lane] = ustart[wi][lane] = x0;
+    if (lane + 32 < ns) ubase[wi][lane + 32] = ustart[wi][lane + 32] = t0 + x1;
+  }
+  __syncwarp();
+  // stable grouping: chunks of 32 entries in list order, positions inside a
+  // chunk by lane order among the lanes of the same rank
+  for (int c0 = 0; c0 < total; c0 += 32) {
+    int e = c0 + lane;
+    bool valid = e < total;
+    int r = valid ? (int)e_rk[wi][e] : -1 - lane;
+    unsigned grp = __match_any_sync(0xffffffffu, r);
+    int before = __popc(grp & ((1u << lane) - 1u));
+    int pos = valid ? ubase[wi][r] + before : 0;
+    __syncwarp();
+    if (valid) {
+      e_ord[wi][pos] = (short)e;
+      if (before == 0) ubase[wi][r] += __popc(grp);
+    }
+    __syncwarp();
+  }
   // 4. values and gradients of S_vp
   for (int k = lane; k < ns; k += 32) {
     int j = sup[wi][k];
     double s0 = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
-    for (int e = 0; e < total; ++e) {
-      if (e_node[wi][e] != j) continue;
+    for (int t = ustart[wi][k]; t < ustart[wi][k] + ucnt[wi][k]; ++t) {
+      int e = e_ord[wi][t];
       int q = e_q[wi][e];
       const SubBox& o = sb[wi][q >> 3];
       int c = q & 7;
