@@ -95,6 +95,7 @@ struct MGData {
   MGLevel lev[8];
   Buf p_idx, p_w;              // fine dof -> up to 8 level-1 rows and weights
   Buf fDinv, fx, fr;           // fine smoother inverses, fine V-cycle vectors
+  Buf fKh;                     // FP16 copy of the fine matrix (mixed path)
   Buf cinv;                    // dense inverse of the coarsest operator
   int n3c = 0;
 };

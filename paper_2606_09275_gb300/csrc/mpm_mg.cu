@@ -423,6 +423,30 @@ __global__ void k_mg_dense(int nrow, int S, int R, const int* __restrict__ xyz, 
   }
 }
 
+// ---------------------------------------------------------------- FP16 smoothing copy
+
+// largest |K| (as ordered bits of a non-negative float)
+__global__ void k_absmax(long long n, const float* __restrict__ K, unsigned* out) {
+  float m = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(K[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// FP16 copy of K scaled by 2^e (the largest |entry| maps below 2^14, clear of
+// the FP16 limit 65504); scaling by a power of two keeps the copy exactly as
+// symmetric as K.  kscale receives 2^-e.
+__global__ void k_to_half(long long n, const float* __restrict__ K, const unsigned* amax, __half* Kh,
+                          float* kscale) {
+  float m = __uint_as_float(*amax);
+  int e = 14 - (m > 0.f ? (int)ceilf(log2f(m)) : 0);
+  float sc = ldexpf(1.f, e);
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *kscale = ldexpf(1.f, -e);
+  for (; i < n; i += (long long)gridDim.x * blockDim.x) Kh[i] = __float2half_rn(K[i] * sc);
+}
+
 // ---------------------------------------------------------------- V-cycle kernels
 
 // x = Dinv b (rows padded to 4 components); also clears the first nz rows of
@@ -445,10 +469,10 @@ __global__ void k_mg_jac0(int n, const T* __restrict__ Dinv, const T* __restrict
 
 // fine level: MODE 0, b1 += P^T (b - K x) (the residual restricted to level 1
 // by atomics); MODE 1, xo = x + Dinv (b - K x) with r.z += b.xo
-template <class T, int MODE>
-__global__ void k_mg_fine(int nd, int npad, Sliced SK, const T* __restrict__ K, const T* __restrict__ b,
-                          const T* __restrict__ x, const T* __restrict__ Dinv, T* out,
-                          const int* __restrict__ pidx, const float* __restrict__ pw,
+template <class T, int MODE, class TK>
+__global__ void k_mg_fine(int nd, int npad, Sliced SK, const TK* __restrict__ K, const float* kscale,
+                          const T* __restrict__ b, const T* __restrict__ x, const T* __restrict__ Dinv,
+                          T* out, const int* __restrict__ pidx, const float* __restrict__ pw,
                           const int* __restrict__ fmask, double* rz, const Scal* sk, int k) {
   __shared__ double sh[32];
   if (skip(sk, k)) return;
@@ -456,7 +480,14 @@ __global__ void k_mg_fine(int nd, int npad, Sliced SK, const T* __restrict__ K, 
   double part = 0.0;
   if (r < npad) {
     T y[3];
-    sliced_row<T, T, T, 4>(r, SK, K, x, y);
+    if constexpr (sizeof(TK) == 2) {
+      float yf[3];
+      sliced_row_h(r, SK, (const __half*)K, (const float*)x, yf);
+      float ks = *kscale;
+      for (int c = 0; c < 3; ++c) y[c] = (T)(yf[c] * ks);
+    } else {
+      sliced_row<T, T, T, 4>(r, SK, (const T*)K, x, y);
+    }
     T bv[4], res[4];
     ld4(b + 4 * (size_t)r, bv);
     for (int c = 0; c < 3; ++c) res[c] = r < nd ? bv[c] - y[c] : (T)0;
@@ -736,6 +767,15 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
   T* fD = grow<T>(c, G.fDinv, 12 * (size_t)npad);
   MPM_LAUNCH(k_mg_dinv_fine<T><<<grid_for(npad, 256), 256, 0, st>>>(nd, npad, SK, K, fD, c->d_err));
   grow<T>(c, G.fx, 4 * (size_t)npad);
+  if constexpr (sizeof(T) == 4) {
+    // FP16 copy of the fine matrix for the V-cycle's two fine-level products
+    long long n9 = 9LL * m->nslot;
+    unsigned* amax = (unsigned*)(c->d_red + 10);
+    float* ksc = (float*)(c->d_red + 11);
+    MPM_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned), st));
+    MPM_LAUNCH(k_absmax<<<4 * 152, 256, 0, st>>>(n9, K, amax));
+    MPM_LAUNCH(k_to_half<<<8 * 152, 256, 0, st>>>(n9, K, amax, grow<__half>(c, G.fKh, n9), ksc));
+  }
   if (!coarse) return;
   for (int l = 0; l < G.nlev; ++l) {
     MGLevel& L = G.lev[l];
@@ -799,9 +839,15 @@ void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, cons
   MGLevel& L0 = G.lev[0];
   MPM_LAUNCH(k_mg_jac0<T><<<grid_for(std::max(npad, L0.npad), 256), 256, 0, st>>>(npad, fD, r, fx, ptr<T>(L0.b),
                                                                                  L0.npad, sk, k));
-  MPM_LAUNCH(k_mg_fine<T, 0><<<grid_for(npad, FB), FB, 0, st>>>(nd, npad, SK, K, r, fx, fD, ptr<T>(L0.b),
-                                                               ptr<int>(G.p_idx), ptr<float>(G.p_w), fmask,
-                                                               nullptr, sk, k));
+  const float* ksc = (const float*)(c->d_red + 11);
+  if constexpr (sizeof(T) == 4)
+    MPM_LAUNCH(k_mg_fine<T, 0, __half><<<grid_for(npad, FB), FB, 0, st>>>(
+        nd, npad, SK, ptr<__half>(G.fKh), ksc, r, fx, fD, ptr<T>(L0.b), ptr<int>(G.p_idx),
+        ptr<float>(G.p_w), fmask, nullptr, sk, k));
+  else
+    MPM_LAUNCH(k_mg_fine<T, 0, T><<<grid_for(npad, FB), FB, 0, st>>>(
+        nd, npad, SK, K, ksc, r, fx, fD, ptr<T>(L0.b), ptr<int>(G.p_idx), ptr<float>(G.p_w), fmask,
+        nullptr, sk, k));
   // down the uniform levels
   T* xcur[8];
   for (int l = 0; l + 1 < G.nlev; ++l) {
@@ -831,8 +877,12 @@ void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, cons
   }
   MPM_LAUNCH(k_mg_prolong1<T><<<grid_for(nd, 128), 128, 0, st>>>(nd, ptr<int>(G.p_idx), ptr<float>(G.p_w), fmask,
                                                                   xcur[0], fx, sk, k));
-  MPM_LAUNCH(k_mg_fine<T, 1><<<grid_for(npad, FB), FB, 0, st>>>(nd, npad, SK, K, r, fx, fD, z, nullptr,
-                                                               nullptr, nullptr, rz, sk, k));
+  if constexpr (sizeof(T) == 4)
+    MPM_LAUNCH(k_mg_fine<T, 1, __half><<<grid_for(npad, FB), FB, 0, st>>>(
+        nd, npad, SK, ptr<__half>(G.fKh), ksc, r, fx, fD, z, nullptr, nullptr, nullptr, rz, sk, k));
+  else
+    MPM_LAUNCH(k_mg_fine<T, 1, T><<<grid_for(npad, FB), FB, 0, st>>>(
+        nd, npad, SK, K, ksc, r, fx, fD, z, nullptr, nullptr, nullptr, rz, sk, k));
 }
 
 void mg_release(mpm_ctx* c, mpm_mesh* m) {
@@ -842,7 +892,7 @@ void mg_release(mpm_ctx* c, mpm_mesh* m) {
     Buf* b[] = {&L.gid, &L.xyz, &L.mask, &L.A, &L.Dinv, &L.b, &L.x, &L.r};
     for (Buf* x : b) free_buf(c, *x);
   }
-  Buf* b[] = {&G.p_idx, &G.p_w, &G.fDinv, &G.fx, &G.fr, &G.cinv};
+  Buf* b[] = {&G.p_idx, &G.p_w, &G.fDinv, &G.fx, &G.fr, &G.fKh, &G.cinv};
   for (Buf* x : b) free_buf(c, *x);
   delete m->mg;
   m->mg = nullptr;

@@ -2,6 +2,8 @@
 // the multigrid preconditioner: 16-byte vector loads and stores, one row of
 // K times x, and the 3x3 inverse-block product.
 #pragma once
+#include <cuda_fp16.h>
+
 #include "mpm_internal.cuh"
 
 namespace mpm {
@@ -121,6 +123,46 @@ __device__ inline void sliced_row_df(int r, Sliced S, const float* __restrict__ 
     }
   }
   for (int a = 0; a < 3; ++a) y[a] = (double)h[a] + (double)l[a];
+}
+
+// four FP16 values (8-byte aligned) to floats
+__device__ inline void ld4h(const __half* p, float* v) {
+  uint2 u = *reinterpret_cast<const uint2*>(p);
+  __half2 a = *reinterpret_cast<const __half2*>(&u.x), b = *reinterpret_cast<const __half2*>(&u.y);
+  float2 fa = __half22float2(a), fb = __half22float2(b);
+  v[0] = fa.x;
+  v[1] = fa.y;
+  v[2] = fb.x;
+  v[3] = fb.y;
+}
+
+// y = row r of an FP16 copy of K (same sliced layout, values scaled by a power
+// of two) times x; FP32 arithmetic, the caller undoes the scale
+__device__ inline void sliced_row_h(int r, Sliced S, const __half* __restrict__ K,
+                                    const float* __restrict__ x, float* y) {
+  int s = r >> 5, ln = r & 31;
+  int W = S.w[s];
+  long long b0 = S.base[s];
+  const __half* Kb = K + 9 * b0;
+  const int* cb = S.scol + b0;
+  size_t plane = (size_t)32 * W;
+  y[0] = y[1] = y[2] = 0.f;
+  for (int k4 = 0; k4 < (W >> 2); ++k4) {
+    size_t off = ((size_t)k4 * 32 + ln) * 4;
+    int4 c = *reinterpret_cast<const int4*>(cb + off);
+    int cc[4] = {c.x, c.y, c.z, c.w};
+    float v[9][4];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) ld4h(Kb + e * plane + off, v[e]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float xv[4];
+      ld4(x + 4 * (size_t)cc[j], xv);
+      y[0] += v[0][j] * xv[0] + v[1][j] * xv[1] + v[2][j] * xv[2];
+      y[1] += v[3][j] * xv[0] + v[4][j] * xv[1] + v[5][j] * xv[2];
+      y[2] += v[6][j] * xv[0] + v[7][j] * xv[1] + v[8][j] * xv[2];
+    }
+  }
 }
 
 }  // namespace mpm
