@@ -317,21 +317,34 @@ __global__ void k_mg_dinv_fine(int nd, int npad, Sliced SK, const T* __restrict_
     for (int e = 0; e < 12; ++e) o[e] = (T)0;
     return;
   }
-  int sl = r >> 5, W = SK.w[sl];
+  // the row in the access pattern of the SpMV: four slots per 16-byte load
+  int sl = r >> 5, ln = r & 31, W = SK.w[sl];
   long long b0 = SK.base[sl];
-  double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, s[3] = {0, 0, 0};
-  for (int idx = 0; idx < W; ++idx) {
-    long long slot = sliced_slot(b0, r, idx);
-    int c = SK.scol[slot];
-    double v[9];
-    for (int e = 0; e < 9; ++e) v[e] = (double)K[sliced_entry(b0, W, slot, e)];
-    if (c == r) {
-      for (int e = 0; e < 9; ++e) a[e] += v[e];
-    } else {
-      for (int e = 0; e < 9; ++e) s[e / 3] += fabs(v[e]);
+  const T* Kb = K + 9 * b0;
+  const int* cb = SK.scol + b0;
+  size_t plane = (size_t)32 * W;
+  // (the l1 sums, a smoother parameter, accumulate in the matrix precision)
+  double a[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  T s[3] = {0, 0, 0};
+  for (int k4 = 0; k4 < (W >> 2); ++k4) {
+    size_t off = ((size_t)k4 * 32 + ln) * 4;
+    int4 c = *reinterpret_cast<const int4*>(cb + off);
+    int cc[4] = {c.x, c.y, c.z, c.w};
+    T v[9][4];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) ld4(Kb + e * plane + off, v[e]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (cc[j] == r) {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) a[e] += (double)v[e][j];
+      } else {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) s[e / 3] += v[e][j] < (T)0 ? -v[e][j] : v[e][j];
+      }
     }
   }
-  for (int d = 0; d < 3; ++d) a[4 * d] += s[d];
+  for (int d = 0; d < 3; ++d) a[4 * d] += (double)s[d];
   store_inv<T>(a, o, err);
 }
 

@@ -92,7 +92,7 @@ __device__ inline void df_acc(float& hi, float& lo, float k, float xh, float xl)
 }
 
 __device__ inline void sliced_row_df(int r, Sliced S, const float* __restrict__ K,
-                                     const double* __restrict__ x, double* y) {
+                                     const float4* __restrict__ xs, double* y) {
   int s = r >> 5, ln = r & 31;
   int W = S.w[s];
   long long b0 = S.base[s];
@@ -109,13 +109,9 @@ __device__ inline void sliced_row_df(int r, Sliced S, const float* __restrict__ 
     for (int e = 0; e < 9; ++e) ld4(Kb + e * plane + off, v[e]);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      float xh[3], xl[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        double xv = x[3 * (size_t)cc[j] + d];
-        xh[d] = (float)xv;
-        xl[d] = (float)(xv - (double)xh[d]);
-      }
+      // x split into hi and lo floats, two 16-byte loads per column
+      float4 p0 = xs[2 * (size_t)cc[j]], p1 = xs[2 * (size_t)cc[j] + 1];
+      float xh[3] = {p0.x, p0.z, p1.x}, xl[3] = {p0.y, p0.w, p1.y};
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -123,6 +119,22 @@ __device__ inline void sliced_row_df(int r, Sliced S, const float* __restrict__ 
     }
   }
   for (int a = 0; a < 3; ++a) y[a] = (double)h[a] + (double)l[a];
+}
+
+// x (FP64, 3 per dof) -> (hi, lo) float pairs, 8 floats per dof (padding zero)
+__global__ inline void k_split_df(int npad, int nd, const double* __restrict__ x, float4* xs) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  float hl[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (i < nd)
+    for (int d = 0; d < 3; ++d) {
+      double v = x[3 * (size_t)i + d];
+      float hi = (float)v;
+      hl[2 * d] = hi;
+      hl[2 * d + 1] = (float)(v - (double)hi);
+    }
+  xs[2 * (size_t)i] = make_float4(hl[0], hl[1], hl[2], hl[3]);
+  xs[2 * (size_t)i + 1] = make_float4(hl[4], hl[5], 0.f, 0.f);
 }
 
 // four FP16 values (8-byte aligned) to floats

@@ -411,15 +411,16 @@ __global__ void k_bicg_rotate(Scal* sc, const double* next_rho1, const double* n
 // precision), masked, written in 3 (R3) or 4 components; slot += r.r
 template <class T, int RS>
 __global__ void k_residual64(int nd, int npad, Sliced S, const T* __restrict__ K,
-                             const double* __restrict__ x, const double* __restrict__ b,
-                             const int* __restrict__ mask, double* r, double* slot) {
+                             const double* __restrict__ x, const float4* __restrict__ xs,
+                             const double* __restrict__ b, const int* __restrict__ mask, double* r,
+                             double* slot) {
   __shared__ double sh[32];
   int rr = blockIdx.x * blockDim.x + threadIdx.x;
   double part = 0.0;
   if (rr < npad) {
     double y[3];
     if constexpr (sizeof(T) == 4)
-      sliced_row_df(rr, S, (const float*)K, x, y);
+      sliced_row_df(rr, S, (const float*)K, xs, y);
     else
       sliced_row<T, double, double, 3>(rr, S, K, x, y);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -447,6 +448,21 @@ __global__ void k_axpy_f2d(int n, double* x, const float* __restrict__ d) {
 __global__ void k_copy_d(int n, double* y, const double* __restrict__ x) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = x[i];
+}
+
+// for an FP32 matrix, the (hi, lo) float split of x used by the double-float
+// residual (nullptr otherwise)
+template <class T>
+const float4* residual_split(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* x) {
+  (void)K;
+  if constexpr (sizeof(T) != 4) {
+    return nullptr;
+  } else {
+    int npad = 32 * m->nslice;
+    float4* xs = grow<float4>(c, c->v[22], 2 * (size_t)npad);
+    MPM_LAUNCH(k_split_df<<<grid_for(npad, 256), 256, 0, c->stream>>>(npad, m->ndof, x, xs));
+    return xs;
+  }
 }
 
 Sliced sliced_of(const mpm_mesh* m) {
@@ -571,7 +587,7 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
   double* red = c->d_red + 40;  // rho1 / rr accumulators of the next iteration
   MPM_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
   // r = r0 = b (free components), ||b||^2 via r = b - K*0
-  MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<T, 4><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, x, b, mask, r, &sc_d->bb));
+  MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<T, 4><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, x, residual_split(c, m, K, x), b, mask, r, &sc_d->bb));
   MPM_LAUNCH(k_copy_d<<<grid_for((long long)n4, 256), 256, 0, st>>>((int)n4, r0, r));
   MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
   MPM_CUDA(cudaStreamSynchronize(st));
@@ -684,7 +700,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     float* q = grow<float>(c, c->v[7], n4);
     MPM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n3, st));
     MPM_CUDA(cudaMemsetAsync(slot, 0, sizeof(double), st));
-    MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, b, ptr<int>(m->dof_mask), r64, slot));
+    MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, residual_split(c, m, Kf, x), b, ptr<int>(m->dof_mask), r64, slot));
     MPM_CUDA(cudaMemcpyAsync(c->h_red + 60, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
     double bb = c->h_red[60], rr = bb;
@@ -709,7 +725,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
       }
       MPM_LAUNCH(k_axpy_f2d<<<grid_for(n3, 256), 256, 0, st>>>(n3, x, d32));
       MPM_CUDA(cudaMemsetAsync(slot, 0, sizeof(double), st));
-      MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, b, ptr<int>(m->dof_mask), r64, slot));
+      MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, residual_split(c, m, Kf, x), b, ptr<int>(m->dof_mask), r64, slot));
       MPM_CUDA(cudaMemcpyAsync(c->h_red + 60, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
       MPM_CUDA(cudaStreamSynchronize(st));
       rr = c->h_red[60];
