@@ -275,7 +275,8 @@ __device__ inline unsigned tangent_hash(int c, int hmask) {
 // applied when the row is written out, coalesced, in the sliced layout.
 template <class T>
 __global__ void __launch_bounds__(32 * TW)
-    k_tangent_rows(int nd, int P, int mr, const int* __restrict__ rp, const int* __restrict__ col,
+    k_tangent_rows(int nd, int P, int minlen, int mr, int last, const int* __restrict__ rp,
+                   const int* __restrict__ col,
                    Sliced S, const long long* __restrict__ sptr, const uint64_t* __restrict__ skeys,
                    const int* __restrict__ nsup, const int* __restrict__ sidx,
                    const T* __restrict__ gx, const T* __restrict__ Aalg,
@@ -291,8 +292,10 @@ __global__ void __launch_bounds__(32 * TW)
   int r = blockIdx.x * (blockDim.x >> 5) + wi;
   if (r >= nd) return;
   int s0 = rp[r], nb = rp[r + 1] - s0;
+  if (nb <= minlen) return;  // done by the pass for shorter rows
   if (nb > mr) {
-    if (lane == 0) atomicOr(err, EB_ROW);
+    // left to the pass for longer rows; an error only in the last pass
+    if (lane == 0 && last) atomicOr(err, EB_ROW);
     return;
   }
   for (int i = lane; i < hs; i += 32) hkey[i] = -1;
@@ -551,23 +554,32 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
   MPM_LAUNCH_P(MPM_PROF_RESIDUAL, k_residual_rows<<<grid_for(nd, 8), 256, 0, st>>>(nd, load, rp, col, ptr<double>(m->kg), du, fint,
                                                    ptr<double>(m->fext), R));
   if (K) {
+    // two passes: rows up to 128 blocks (the 5^3 interior stencil and below)
+    // with a small shared-memory footprint per warp, for occupancy, then the
+    // longer rows near hanging nodes
     int mr = (m->maxrow + 3) & ~3;
-    size_t wb = mixed ? tangent_warp_bytes<float>(mr) : tangent_warp_bytes<double>(mr);
-    int tw = (int)std::min<size_t>(TW, (size_t)(220 * 1024) / wb);
-    if (tw < 1) throw CudaError(MPM_ERR_SUPPORT, "stiffness row too long for the tangent gather");
-    size_t smem = wb * tw;
-    if (mixed) {
-      MPM_CUDA(cudaFuncSetAttribute(k_tangent_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<float><<<grid_for(nd, tw), 32 * tw, smem, st>>>(
-          nd, P, mr, rp, col, S, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
-          (const float*)gx, (const float*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
-          (float*)K, c->d_err));
-    } else {
-      MPM_CUDA(cudaFuncSetAttribute(k_tangent_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<double><<<grid_for(nd, tw), 32 * tw, smem, st>>>(
-          nd, P, mr, rp, col, S, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx,
-          (const double*)gx, (const double*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
-          (double*)K, c->d_err));
+    const int SHORT = 128;
+    int passes[2][2] = {{-1, std::min(mr, SHORT)}, {SHORT, mr}};
+    int np_ = mr > SHORT ? 2 : 1;
+    for (int ps = 0; ps < np_; ++ps) {
+      int lo = passes[ps][0], hi = passes[ps][1], last = ps == np_ - 1;
+      size_t wb = mixed ? tangent_warp_bytes<float>(hi) : tangent_warp_bytes<double>(hi);
+      int tw = (int)std::min<size_t>(TW, (size_t)(220 * 1024) / wb);
+      if (tw < 1) throw CudaError(MPM_ERR_SUPPORT, "stiffness row too long for the tangent gather");
+      size_t smem = wb * tw;
+      if (mixed) {
+        MPM_CUDA(cudaFuncSetAttribute(k_tangent_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<float><<<grid_for(nd, tw), 32 * tw, smem, st>>>(
+            nd, P, lo, hi, last, rp, col, S, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup,
+            sidx, (const float*)gx, (const float*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
+            (float*)K, c->d_err));
+      } else {
+        MPM_CUDA(cudaFuncSetAttribute(k_tangent_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<double><<<grid_for(nd, tw), 32 * tw, smem, st>>>(
+            nd, P, lo, hi, last, rp, col, S, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup,
+            sidx, (const double*)gx, (const double*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
+            (double*)K, c->d_err));
+      }
     }
     int npad = 32 * m->nslice;
     if (npad > nd) {
