@@ -7,8 +7,10 @@
 // coarse trilinear field lies in the fine octree space and the prolongation P
 // is plain trilinear interpolation at the fine node positions (components
 // fixed by a Dirichlet plane are dropped from P).  Coarse operators are
-// Galerkin products A_c = P^T A P, gathered row by row in shared memory (no
-// global atomics) and stored per stencil offset on the uniform grid.  The
+// Galerkin products A_c = P^T A P, accumulated by one warp per finer-level row
+// into the coarse rows (atomics resolved in L2) and stored per stencil offset
+// on the uniform grid.  Restrictions are scattered the same way by the
+// residual kernels; prolongations gather.  The
 // smoother is l1 block Jacobi, M = D + diag(sum over the row's off-diagonal
 // |entries|), which is convergent without eigenvalue estimates; one sweep
 // before and one after the coarse correction, so the V-cycle is symmetric
@@ -532,12 +534,15 @@ __global__ void k_mg_fine(int nd, int npad, Sliced SK, const TK* __restrict__ K,
   }
 }
 
-// uniform level (warp per row): r = b - A x (MODE 0) or xo = x + Dinv (b - A x) (MODE 1)
+// uniform level (warp per row): MODE 0, the residual b - A x restricted to the
+// next coarser level by atomics into its (zeroed) right-hand side `out`;
+// MODE 1, xo = x + Dinv (b - A x)
 template <class T, int MODE>
 __global__ void k_mg_lvl(int nrow, int S, int R, int n1, const int* __restrict__ xyz,
                          const int* __restrict__ gid, const T* __restrict__ A, const T* __restrict__ b,
-                         const T* __restrict__ x, const T* __restrict__ Dinv, T* out, const Scal* sk,
-                         int k) {
+                         const T* __restrict__ x, const T* __restrict__ Dinv, T* out,
+                         const int* __restrict__ mask, int n1c, const int* __restrict__ gid_c,
+                         const Scal* sk, int k) {
   if (skip(sk, k)) return;
   int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (a >= nrow) return;
@@ -569,7 +574,21 @@ __global__ void k_mg_lvl(int nrow, int S, int R, int n1, const int* __restrict__
     res[2] = bv[2] - y2;
     res[3] = (T)0;
     if (MODE == 0) {
-      st4(out + 4 * (size_t)a, res);
+      int mi = mask[a], lo[3], hi[3];
+      T f = (T)1;
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = ca[d] >> 1;
+        hi[d] = (ca[d] + 1) >> 1;
+        if (lo[d] != hi[d]) f *= (T)0.5;
+      }
+      for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+          for (int xx = lo[0]; xx <= hi[0]; ++xx) {
+            int bc = gid_c[xx + n1c * (y + n1c * z)];
+            if (bc < 0) continue;
+            for (int c = 0; c < 3; ++c)
+              if (!((mi >> c) & 1)) atomicAdd(out + 4 * (size_t)bc + c, f * res[c]);
+          }
     } else {
       T xv[4], d[4];
       ld4(x + 4 * (size_t)a, xv);
@@ -604,39 +623,6 @@ __global__ void k_mg_prolong1(int nd, const int* __restrict__ pidx, const float*
   for (int c = 0; c < 3; ++c)
     if (!((mi >> c) & 1)) xv[c] += s[c];
   st4(xf + 4 * (size_t)i, xv);
-}
-
-// bc = P^T rf between uniform levels
-template <class T>
-__global__ void k_mg_restrict_u(int nrow, const int* __restrict__ xyz_c, int n1f,
-                                const int* __restrict__ gid_f, const int* __restrict__ fmask,
-                                const T* __restrict__ rf, T* bc, const Scal* sk, int k) {
-  if (skip(sk, k)) return;
-  int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= nrow) return;
-  int ca[3];
-  unpack3(xyz_c[a], ca);
-  T s[4] = {0, 0, 0, 0};
-  for (int dl = 0; dl < 27; ++dl) {
-    int del[3] = {dl % 3 - 1, (dl / 3) % 3 - 1, dl / 9 - 1};
-    int fi[3];
-    bool in = true;
-    T w = (T)1;
-    for (int d = 0; d < 3; ++d) {
-      fi[d] = 2 * ca[d] + del[d];
-      in = in && fi[d] >= 0 && fi[d] < n1f;
-      if (del[d]) w *= (T)0.5;
-    }
-    if (!in) continue;
-    int i = gid_f[fi[0] + n1f * (fi[1] + n1f * fi[2])];
-    if (i < 0) continue;
-    int mi = fmask[i];
-    T rv[4];
-    ld4(rf + 4 * (size_t)i, rv);
-    for (int c = 0; c < 3; ++c)
-      if (!((mi >> c) & 1)) s[c] += w * rv[c];
-  }
-  st4(bc + 4 * (size_t)a, s);
 }
 
 // xf += P xc between uniform levels
@@ -866,13 +852,11 @@ void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, cons
   for (int l = 0; l + 1 < G.nlev; ++l) {
     MGLevel& L = G.lev[l];
     MGLevel& N = G.lev[l + 1];
-    MPM_LAUNCH(k_mg_jac0<T><<<grid_for(L.npad, 256), 256, 0, st>>>(L.npad, ptr<T>(L.Dinv), ptr<T>(L.b), ptr<T>(L.x),
-                                                                   nullptr, 0, sk, k));
+    MPM_LAUNCH(k_mg_jac0<T><<<grid_for(std::max(L.npad, N.npad), 256), 256, 0, st>>>(
+        L.npad, ptr<T>(L.Dinv), ptr<T>(L.b), ptr<T>(L.x), ptr<T>(N.b), N.npad, sk, k));
     MPM_LAUNCH(k_mg_lvl<T, 0><<<grid_for(L.nrow, MGW), 32 * MGW, 0, st>>>(
         L.nrow, L.S, L.R, L.n1, ptr<int>(L.xyz), ptr<int>(L.gid), ptr<T>(L.A), ptr<T>(L.b), ptr<T>(L.x),
-        ptr<T>(L.Dinv), ptr<T>(L.r), sk, k));
-    MPM_LAUNCH(k_mg_restrict_u<T><<<grid_for(N.nrow, 128), 128, 0, st>>>(
-        N.nrow, ptr<int>(N.xyz), L.n1, ptr<int>(L.gid), ptr<int>(L.mask), ptr<T>(L.r), ptr<T>(N.b), sk, k));
+        ptr<T>(L.Dinv), ptr<T>(N.b), ptr<int>(L.mask), N.n1, ptr<int>(N.gid), sk, k));
   }
   MGLevel& C = G.lev[G.nlev - 1];
   MPM_LAUNCH(k_mg_coarse<T><<<1, 256, 0, st>>>(C.nrow, ptr<T>(G.cinv), ptr<T>(C.b), ptr<T>(C.x), sk, k));
@@ -885,7 +869,7 @@ void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, cons
         L.nrow, ptr<int>(L.xyz), ptr<int>(L.mask), N.n1, ptr<int>(N.gid), xcur[l + 1], ptr<T>(L.x), sk, k));
     MPM_LAUNCH(k_mg_lvl<T, 1><<<grid_for(L.nrow, MGW), 32 * MGW, 0, st>>>(
         L.nrow, L.S, L.R, L.n1, ptr<int>(L.xyz), ptr<int>(L.gid), ptr<T>(L.A), ptr<T>(L.b), ptr<T>(L.x),
-        ptr<T>(L.Dinv), ptr<T>(L.r), sk, k));
+        ptr<T>(L.Dinv), ptr<T>(L.r), nullptr, 0, nullptr, sk, k));
     xcur[l] = ptr<T>(L.r);
   }
   MPM_LAUNCH(k_mg_prolong1<T><<<grid_for(nd, 128), 128, 0, st>>>(nd, ptr<int>(G.p_idx), ptr<float>(G.p_w), fmask,
