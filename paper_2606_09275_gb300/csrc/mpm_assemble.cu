@@ -53,9 +53,63 @@ __global__ void k_kinematics(int P, const int* __restrict__ nsup, const int* __r
 
 // Full per-point update.  in: dF, b_e,n (6); out: tau (6: xx yy zz xy yz xz),
 // b_e (6), A' (81, layout [(i*9 + k*3 + m)*3 + j] = A_ijkm - tau_im delta_jk)
+// The consistent spatial tangent from the spectral state: theta_ab =
+// (tau_a - tau_b)/(lam_a - lam_b) = g/2 * divided difference of ln (in FP64),
+// then the eigenbasis rotation of the 81 entries in the precision the tangent
+// is stored in (FP32 for the mixed path, where it runs on the FP32 pipe).
+// Layout [(i*9 + k*3 + m)*3 + j] = A_ijkm - tau_im delta_jk.
+template <class TA>
+__device__ void tangent_rotate(const double* Q, const double* lam, const double* dd, double gr,
+                               const double* tau6, TA* Aout) {
+  // theta_ab = (tau_a - tau_b)/(lam_a - lam_b) = g/2 * divided difference of ln
+  // (in FP64), then the eigenbasis rotation of the 81 entries in the
+  // precision the tangent is stored in: FP32 for the mixed path, where it
+  // runs on the FP32 pipe
+  typedef TA R;
+  double th01 = 0.5 * gr * ln_divdiff(lam[0], lam[1]);
+  double th02 = 0.5 * gr * ln_divdiff(lam[0], lam[2]);
+  double th12 = 0.5 * gr * ln_divdiff(lam[1], lam[2]);
+  R th[9] = {(R)0, (R)th01, (R)th02, (R)th01, (R)0, (R)th12, (R)th02, (R)th12, (R)0};
+  R q[9], d[9], lr[3];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    q[i] = (R)Q[i];
+    d[i] = (R)dd[i];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) lr[a] = (R)lam[a];
+  R taum[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      int s = (i == j) ? i : (i + j == 1 ? 3 : (i + j == 3 ? 4 : 5));
+      taum[3 * i + j] = (R)tau6[s];
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k)
+        for (int m = 0; m < 3; ++m) {
+          R s = (R)0;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            R qia = q[3 * i + a];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              s += d[3 * a + c] * qia * q[3 * j + a] * q[3 * k + c] * q[3 * m + c];
+              if (a != c)
+                s += th[3 * a + c] * qia * q[3 * j + c] *
+                     (lr[c] * q[3 * k + a] * q[3 * m + c] + lr[a] * q[3 * k + c] * q[3 * m + a]);
+            }
+          }
+          if (j == k) s -= taum[3 * i + m];
+          Aout[(i * 9 + k * 3 + m) * 3 + j] = s;
+        }
+}
+
 template <bool TANGENT, class TA>
 __device__ bool point_update_law(const Law& L, double E, double ys, const double* be, const double* dF,
-                                 double* tau6, double* be_new, TA* Aout) {
+                                 double* tau6, double* be_new, TA* Aout, double* save = nullptr) {
   double b[9] = {be[0], be[3], be[5], be[3], be[1], be[4], be[5], be[4], be[2]};
   double t[9], bt[9];
 #pragma unroll
@@ -93,51 +147,16 @@ __device__ bool point_update_law(const Law& L, double E, double ys, const double
     tau6[s] = Q[3 * i] * ta[0] * Q[3 * j] + Q[3 * i + 1] * ta[1] * Q[3 * j + 1] + Q[3 * i + 2] * ta[2] * Q[3 * j + 2];
     be_new[s] = Q[3 * i] * bw[0] * Q[3 * j] + Q[3 * i + 1] * bw[1] * Q[3 * j + 1] + Q[3 * i + 2] * bw[2] * Q[3 * j + 2];
   }
-  if (TANGENT) {
-    // theta_ab = (tau_a - tau_b)/(lam_a - lam_b) = g/2 * divided difference of ln
-    // (in FP64), then the eigenbasis rotation of the 81 entries in the
-    // precision the tangent is stored in: FP32 for the mixed path, where it
-    // runs on the FP32 pipe
-    typedef TA R;
-    double th01 = 0.5 * gr * ln_divdiff(lam[0], lam[1]);
-    double th02 = 0.5 * gr * ln_divdiff(lam[0], lam[2]);
-    double th12 = 0.5 * gr * ln_divdiff(lam[1], lam[2]);
-    R th[9] = {(R)0, (R)th01, (R)th02, (R)th01, (R)0, (R)th12, (R)th02, (R)th12, (R)0};
-    R q[9], d[9], lr[3];
+  if (TANGENT) tangent_rotate<TA>(Q, lam, dd, gr, tau6, Aout);
+  if (save) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      q[i] = (R)Q[i];
-      d[i] = (R)dd[i];
+      save[i] = Q[i];
+      save[12 + i] = dd[i];
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) lr[a] = (R)lam[a];
-    R taum[9];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        int s = (i == j) ? i : (i + j == 1 ? 3 : (i + j == 3 ? 4 : 5));
-        taum[3 * i + j] = (R)tau6[s];
-      }
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j)
-        for (int k = 0; k < 3; ++k)
-          for (int m = 0; m < 3; ++m) {
-            R s = (R)0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              R qia = q[3 * i + a];
-#pragma unroll
-              for (int c = 0; c < 3; ++c) {
-                s += d[3 * a + c] * qia * q[3 * j + a] * q[3 * k + c] * q[3 * m + c];
-                if (a != c)
-                  s += th[3 * a + c] * qia * q[3 * j + c] *
-                       (lr[c] * q[3 * k + a] * q[3 * m + c] + lr[a] * q[3 * k + c] * q[3 * m + a]);
-              }
-            }
-            if (j == k) s -= taum[3 * i + m];
-            Aout[(i * 9 + k * 3 + m) * 3 + j] = s;
-          }
+    for (int a = 0; a < 3; ++a) save[9 + a] = lam[a];
+    save[21] = gr;
   }
   return true;
 }
@@ -150,7 +169,7 @@ __device__ inline double det3(const double* a) {
 template <bool TANGENT, class TA>
 __global__ void k_constitutive(int P, Law L, const double* __restrict__ E, const double* __restrict__ ys,
                                const double* __restrict__ be, const double* __restrict__ dF,
-                               double* tau, double* dFinv, TA* Aalg, int* err) {
+                               double* tau, double* dFinv, TA* Aalg, double* lawst, int* err) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= P) return;
   double f[9];
@@ -160,7 +179,8 @@ __global__ void k_constitutive(int P, Law L, const double* __restrict__ E, const
   double t6[6], bn[6];
   bool ok = det > 0.0 && isfinite(det) &&
             point_update_law<TANGENT, TA>(L, E[w], ys[w], be + 6 * (size_t)w, f, t6, bn,
-                                          Aalg + 81 * (size_t)w);
+                                          Aalg + 81 * (size_t)w,
+                                          lawst ? lawst + 22 * (size_t)w : nullptr);
   if (!ok) {
     atomicOr(err, EB_NAN);
 #pragma unroll
@@ -180,6 +200,47 @@ __global__ void k_constitutive(int P, Law L, const double* __restrict__ E, const
   o[6] = (f[3] * f[7] - f[4] * f[6]) * id;
   o[7] = (f[1] * f[6] - f[0] * f[7]) * id;
   o[8] = (f[0] * f[4] - f[1] * f[3]) * id;
+}
+
+// the tangent of the state the last residual evaluation left (same increment):
+// no second eigen-decomposition or return map
+template <class TA>
+__global__ void k_tangent_state(int P, const double* __restrict__ lawst, const double* __restrict__ tau,
+                                TA* Aalg) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= P) return;
+  const double* st = lawst + 22 * (size_t)w;
+  double Q[9], lam[3], dd[9], t6[6];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    Q[i] = st[i];
+    dd[i] = st[12 + i];
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) lam[a] = st[9 + a];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) t6[i] = tau[6 * (size_t)w + i];
+  tangent_rotate<TA>(Q, lam, dd, st[21], t6, Aalg + 81 * (size_t)w);
+}
+
+// grad_x S = grad S . dF^{-1} for the tangent gather (in its precision), without
+// the internal force
+template <class TG>
+__global__ void k_gx(int P, const int* __restrict__ nsup, const double* __restrict__ dS,
+                     const double* __restrict__ dFinv, TG* gx) {
+  int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= P) return;
+  TG fi[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fi[i] = (TG)dFinv[9 * (size_t)w + i];
+  int n = nsup[w];
+  for (int k = lane; k < n; k += 32) {
+    size_t o = (size_t)w * MAXS + k;
+    TG a0 = (TG)dS[3 * o], a1 = (TG)dS[3 * o + 1], a2 = (TG)dS[3 * o + 2];
+    gx[3 * o] = a0 * fi[0] + a1 * fi[3] + a2 * fi[6];
+    gx[3 * o + 1] = a0 * fi[1] + a1 * fi[4] + a2 * fi[7];
+    gx[3 * o + 2] = a0 * fi[2] + a1 * fi[5] + a2 * fi[8];
+  }
 }
 
 // ------------------------------------------------------------------ internal force
@@ -414,7 +475,7 @@ __device__ inline int find_slot(const int* __restrict__ rp, const int* __restric
 // one thread per candidate domain corner: gap against the body at the moved
 // corner, force -eps_N phi n spread by the background basis, stiffness
 // eps_N (n n^T + phi H) phi_a phi_b (Dirichlet entries skipped)
-template <class T, bool TANGENT>
+template <class T, bool TANGENT, bool RES = true>
 __global__ void k_contact(int nc8, const int* __restrict__ cand, const int* __restrict__ cb_n,
                           const int* __restrict__ cb_idx, const double* __restrict__ cb_phi,
                           const double* __restrict__ cb_y0, const double* __restrict__ pE,
@@ -434,12 +495,14 @@ __global__ void k_contact(int nc8, const int* __restrict__ cand, const int* __re
   if (!body_sdf(body, L, y, &phi, nv, H) || !(phi < 0.0)) return;
   double epsN = pf * pE[w] * pow(pV0[w], 2.0 / 3.0);
   double f[3] = {-epsN * phi * nv[0], -epsN * phi * nv[1], -epsN * phi * nv[2]};
-  for (int d = 0; d < 3; ++d) atomicAdd(reac + d, -f[d]);
-  for (int e = 0; e < n; ++e)
-    for (int d = 0; d < 3; ++d) {
-      atomicAdd(R + 3 * (size_t)ids[e] + d, -ph[e] * f[d]);
-      atomicAdd(fc + 3 * (size_t)ids[e] + d, ph[e] * f[d]);
-    }
+  if (RES) {
+    for (int d = 0; d < 3; ++d) atomicAdd(reac + d, -f[d]);
+    for (int e = 0; e < n; ++e)
+      for (int d = 0; d < 3; ++d) {
+        atomicAdd(R + 3 * (size_t)ids[e] + d, -ph[e] * f[d]);
+        atomicAdd(fc + 3 * (size_t)ids[e] + d, ph[e] * f[d]);
+      }
+  }
   if (!TANGENT) return;
   double kc[9];
   for (int a = 0; a < 3; ++a)
@@ -506,7 +569,7 @@ double norm_free(mpm_ctx* c, const mpm_mesh* m, const double* R) {
 
 void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm_rigid& body,
               const double* du, double load, int precision, double* R, void* K, AsmOut* out,
-              bool want_norms) {
+              bool want_norms, bool reuse) {
   mpm_mesh* m = const_cast<mpm_mesh*>(mc);
   cudaStream_t st = c->stream;
   int P = m->np, nd = m->ndof;
@@ -514,45 +577,60 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
   double* dF = grow<double>(c, m->dF, 9 * (size_t)P);
   double* dFinv = grow<double>(c, m->dFinv, 9 * (size_t)P);
   double* tau = grow<double>(c, m->tau, 6 * (size_t)P);
+  double* lawst = grow<double>(c, m->lawst, 22 * (size_t)P);
   const int* nsup = ptr<int>(m->nsup);
   const int* sidx = ptr<int>(m->sidx);
   const double* dS = ptr<double>(m->dS);
-  MPM_LAUNCH_P(MPM_PROF_KINEMATICS, k_kinematics<<<grid_for(8LL * P, 256), 256, 0, st>>>(P, nsup, sidx, dS, du, dF));
+  const double* V0 = ptr<double>(m->pV0);
+  const int* rp = ptr<int>(m->row_ptr);
+  const int* col = ptr<int>(m->col);
+  Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
   bool mixed = precision == MPM_MIXED;
   size_t asz = mixed ? sizeof(float) : sizeof(double);
   void* Aalg = K ? grow_bytes(c, m->Aalg, 81 * (size_t)P * asz) : nullptr;
   void* gx = K ? grow_bytes(c, m->gx, 3 * (size_t)P * MAXS * asz) : nullptr;
-  if (!K)
-    MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<false, double><<<grid_for(P, 128), 128, 0, st>>>(
-        P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv, nullptr,
-        c->d_err));
-  else if (mixed)
-    MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<true, float><<<grid_for(P, 128), 128, 0, st>>>(
-        P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv,
-        (float*)Aalg, c->d_err));
-  else
-    MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<true, double><<<grid_for(P, 128), 128, 0, st>>>(
-        P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv,
-        (double*)Aalg, c->d_err));
   double* fint = grow<double>(c, c->v[0], 3 * (size_t)nd);
   double* fc = grow<double>(c, c->v[1], 3 * (size_t)nd);
-  MPM_CUDA(cudaMemsetAsync(fint, 0, sizeof(double) * 3 * nd, st));
-  MPM_CUDA(cudaMemsetAsync(fc, 0, sizeof(double) * 3 * nd, st));
-  const double* V0 = ptr<double>(m->pV0);
-  if (!K)
-    MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<double, false><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
-                                                           nullptr));
-  else if (mixed)
-    MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<float, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
-                                                         (float*)gx));
-  else
-    MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<double, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
-                                                          (double*)gx));
-  const int* rp = ptr<int>(m->row_ptr);
-  const int* col = ptr<int>(m->col);
-  Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
-  MPM_LAUNCH_P(MPM_PROF_RESIDUAL, k_residual_rows<<<grid_for(nd, 8), 256, 0, st>>>(nd, load, rp, col, ptr<double>(m->kg), du, fint,
-                                                   ptr<double>(m->fext), R));
+  bool contact = m->ncand && mat.contact_on && body.kind != 0;
+  int n8 = 8 * m->ncand;
+  if (K && reuse) {
+    // Newton's tangent at the increment of the last residual evaluation: its
+    // dF, dF^-1, tau and spectral state are still in place, R is complete
+    if (mixed) {
+      MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_tangent_state<float><<<grid_for(P, 128), 128, 0, st>>>(P, lawst, tau, (float*)Aalg));
+      MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<float><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, (float*)gx));
+    } else {
+      MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_tangent_state<double><<<grid_for(P, 128), 128, 0, st>>>(P, lawst, tau, (double*)Aalg));
+      MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<double><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, (double*)gx));
+    }
+  } else {
+    MPM_LAUNCH_P(MPM_PROF_KINEMATICS, k_kinematics<<<grid_for(8LL * P, 256), 256, 0, st>>>(P, nsup, sidx, dS, du, dF));
+    if (!K)
+      MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<false, double><<<grid_for(P, 128), 128, 0, st>>>(
+          P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv, nullptr,
+          lawst, c->d_err));
+    else if (mixed)
+      MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<true, float><<<grid_for(P, 128), 128, 0, st>>>(
+          P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv,
+          (float*)Aalg, nullptr, c->d_err));
+    else
+      MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<true, double><<<grid_for(P, 128), 128, 0, st>>>(
+          P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv,
+          (double*)Aalg, nullptr, c->d_err));
+    MPM_CUDA(cudaMemsetAsync(fint, 0, sizeof(double) * 3 * nd, st));
+    MPM_CUDA(cudaMemsetAsync(fc, 0, sizeof(double) * 3 * nd, st));
+    if (!K)
+      MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<double, false><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
+                                                             nullptr));
+    else if (mixed)
+      MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<float, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
+                                                           (float*)gx));
+    else
+      MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<double, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
+                                                            (double*)gx));
+    MPM_LAUNCH_P(MPM_PROF_RESIDUAL, k_residual_rows<<<grid_for(nd, 8), 256, 0, st>>>(nd, load, rp, col, ptr<double>(m->kg), du, fint,
+                                                     ptr<double>(m->fext), R));
+  }
   if (K) {
     // two passes: rows up to 128 blocks (the 5^3 interior stencil and below)
     // with a small shared-memory footprint per warp, for occupancy, then the
@@ -590,9 +668,24 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
     }
   }
   double* reac = c->d_red + 20;
+  if (K && reuse) {
+    // contact stiffness only: its forces are already in R
+    if (contact) {
+      if (mixed)
+        MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<float, true, false><<<grid_for(n8, 128), 128, 0, st>>>(
+            n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
+            ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
+            col, S, ptr<int>(m->dof_mask), (float*)K));
+      else
+        MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<double, true, false><<<grid_for(n8, 128), 128, 0, st>>>(
+            n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
+            ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
+            col, S, ptr<int>(m->dof_mask), (double*)K));
+    }
+    return;
+  }
   MPM_CUDA(cudaMemsetAsync(reac, 0, 3 * sizeof(double), st));
-  if (m->ncand && mat.contact_on && body.kind != 0) {
-    int n8 = 8 * m->ncand;
+  if (contact) {
     if (!K)
       MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<double, false><<<grid_for(n8, 128), 128, 0, st>>>(
           n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),

@@ -148,7 +148,8 @@ void mesh_release(mpm_mesh* m) {
                  &m->nsup, &m->sidx, &m->S, &m->dS, &m->S32, &m->dS32, &m->populated, &m->betaK,
                  &m->isB, &m->gface, &m->gdof, &m->gn, &m->row_ptr, &m->col, &m->kg, &m->rowcnt,
                  &m->src_key, &m->src_ptr, &m->fext, &m->cand, &m->cb_n, &m->cb_idx, &m->cb_phi,
-                 &m->cb_y0, &m->dF, &m->dFinv, &m->tau, &m->Aalg, &m->gx, &m->slice_w, &m->slice_base, &m->scol};
+                 &m->cb_y0, &m->dF, &m->dFinv, &m->tau, &m->Aalg, &m->gx, &m->slice_w, &m->slice_base, &m->scol,
+                 &m->lawst};
   for (Buf* b : bufs) free_buf(c, *b);
 }
 }  // namespace mpm

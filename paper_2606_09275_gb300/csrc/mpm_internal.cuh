@@ -182,6 +182,7 @@ struct mpm_mesh {
   mpm::Buf cand, cb_n, cb_idx, cb_phi, cb_y0;
   // per-iteration point data
   mpm::Buf dF, dFinv, tau, Aalg, gx;
+  mpm::Buf lawst;  // spectral state of the last residual-only evaluation (22 per point)
   int built = 0;
   long long gen = 0;                    // incremented by every build
   mpm::MGData* mg = nullptr;            // multigrid structure (built on first use)
@@ -487,9 +488,11 @@ struct AsmOut {
   double reaction[3];
   double fint_norm, fextc_norm;
 };
+// reuse: with K, only the tangent, from the state the last residual-only call
+// left at the same increment (dF, tau and the spectral state); R untouched
 void assemble(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const mpm_rigid& body,
               const double* du, double load, int precision, double* R, void* K, AsmOut* out,
-              bool want_norms);
+              bool want_norms, bool reuse = false);
 double norm_free(mpm_ctx* c, const mpm_mesh* m, const double* R);
 void blocks_export(mpm_ctx* c, const mpm_mesh* m, const void* K, int precision, double* out);
 

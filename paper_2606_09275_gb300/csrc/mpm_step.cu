@@ -80,10 +80,10 @@ void newton(mpm_ctx* c, mpm_mesh* m, const mpm_material* mat, const mpm_rigid& b
         break;
       }
       if (it == prm->maxit) break;
-      // consistent tangent at the current increment (the residual is recomputed
-      // with it and is unchanged)
+      // consistent tangent at the current increment, built from the state that
+      // the last residual evaluation (at this increment) left; R stays as it is
       tm.start();
-      assemble(c, m, *mat, bd, du, prm->load, prec, R, K, &o, false);
+      assemble(c, m, *mat, bd, du, prm->load, prec, R, K, &o, false, true);
       st.ms_assemble += tm.stop();
       status = check_device_error(c, "tangent assembly");
       if (status) throw CudaError(status, c->err);
