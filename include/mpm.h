@@ -126,6 +126,10 @@ typedef struct {
   double tol;      /* Newton: ||R_free|| <= tol * max(||f_int||, ||f_ext+f_c||)  */
   int maxit;
   mpm_solve_params lin;
+  double* du_out;  /* mpm_step, optional (device): receives the converged nodal
+                      increment, 3*ndof doubles in the step's dof numbering, so
+                      that mpm_adjoint need not solve the step again           */
+  long long du_capacity; /* doubles du_out holds (MPM_ERR_CAPACITY if short) */
 } mpm_step_params;
 
 typedef struct {
@@ -240,8 +244,10 @@ int mpm_step(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body, const m
  * plastic/elastic branch of each point, contact candidates, ghost faces and
  * their beta) is frozen at its forward value, so J is differentiated where it
  * is smooth.  Per step, in reverse: rebuild the mesh from the checkpoint,
- * re-solve Newton (prm: the forward's Newton and Krylov settings; prm->load
- * is ignored, each checkpoint carries its own), solve K mu = dJ/du with the
+ * take the converged increment the forward stored in the checkpoint (`du`,
+ * from mpm_step_params.du_out; the rebuild reproduces its dof numbering) or,
+ * without one, re-solve Newton (prm: the forward's Newton and Krylov settings;
+ * prm->load is ignored, each checkpoint carries its own), solve K mu = dJ/du with the
  * FP64 consistent tangent by PCG to prm->lin.tol within prm->lin.maxit
  * iterations (multigrid-preconditioned if prm->lin.method is 3, else block
  * Jacobi) (K is symmetric for material models 0 and 1;
@@ -256,6 +262,8 @@ typedef struct {
   mpm_points pts;
   double body_z;
   double load;
+  const double* du;  /* optional (device): the step's converged increment   */
+  long long du_len;  /* its length, 3*ndof (MPM_ERR_ARG if it does not match) */
 } mpm_checkpoint;
 
 typedef struct {

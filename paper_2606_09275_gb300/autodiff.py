@@ -18,9 +18,12 @@ class LoadPath:
     and Krylov settings used by both the forward run and the adjoint."""
 
     def __init__(self, ctx, cfg, points, nsteps, capacity=None, tol=1e-12, maxit=30, lin_tol=1e-12,
-                 lin_maxit=200000, precision=mpm.FP64, method=0, mg_reuse=0):
+                 lin_maxit=200000, precision=mpm.FP64, method=0, mg_reuse=0, store_increments=True):
         self.ctx, self.cfg, self.points, self.nsteps = ctx, cfg, points, nsteps
         self.capacity = capacity or 64 * len(points["x"])
+        # keep each step's converged increment with its checkpoint, so that the
+        # adjoint does not solve the step again (one nodal vector per step)
+        self.store_increments = store_increments
         self.kw = dict(tol=tol, maxit=maxit, lin_tol=lin_tol, lin_maxit=lin_maxit,
                        precision=precision, method=method, mg_reuse=mg_reuse)
 
@@ -37,11 +40,19 @@ class LoadPath:
         pts.t["E"][:n0] = E.detach().to(pts.t["E"].device, torch.float64)
         pts.t["ys"][:n0] = ys.detach().to(pts.t["ys"].device, torch.float64)
         ckpts, stats = [], []
+        # nodal increments: at most 3 per node, and a mesh has fewer active
+        # nodes than 8 per point
+        du = (torch.empty(24 * self.capacity, dtype=torch.float64, device=pts.t["x"].device)
+              if keep and self.store_increments else None)
         for n in range(self.nsteps):
             bz, ld = self.schedule(n)
             if keep:
-                ckpts.append((pts.clone(), bz, ld))
-            stats.append(mpm.step(self.ctx, self.cfg, pts, body_z=bz, load=ld, **self.kw))
+                start = pts.clone()
+            st = mpm.step(self.ctx, self.cfg, pts, body_z=bz, load=ld, du_out=du, **self.kw)
+            stats.append(st)
+            if keep:
+                ckpts.append((start, bz, ld, du[:3 * st["ndof"]].clone()) if du is not None
+                             else (start, bz, ld))
         reaction = torch.tensor(stats[-1]["reaction"], dtype=torch.float64)
         return reaction, ckpts, stats
 

@@ -927,14 +927,24 @@ extern "C" int mpm_adjoint(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* b
       if (n + 1 < nsteps && m->np != ck[n + 1].pts.count)
         throw CudaError(MPM_ERR_ARG, "adjoint: step " + std::to_string(n) + " rebuilt " + std::to_string(m->np) +
                                          " points, the next checkpoint holds " + std::to_string(ck[n + 1].pts.count));
-      mpm_step_params sp = *prm;
-      sp.load = k.load;
-      mpm_step_stats ss{};
-      double* u = nullptr;
-      newton(c, m, mat, bd, &sp, ss, &u);
+      const double* u = nullptr;
+      if (k.du) {
+        // the increment the forward stored: no second Newton solve
+        if (k.du_len != 3LL * m->ndof)
+          throw CudaError(MPM_ERR_ARG, "adjoint: checkpoint " + std::to_string(n) + " stores " +
+                                           std::to_string(k.du_len) + " increments, the rebuilt step has " +
+                                           std::to_string(3LL * m->ndof));
+        u = k.du;
+      } else {
+        mpm_step_params sp = *prm;
+        sp.load = k.load;
+        sp.du_out = nullptr;
+        mpm_step_stats ss{};
+        double* un = nullptr;
+        newton(c, m, mat, bd, &sp, ss, &un);
+        u = un;
+      }
       stt.ms_forward += X.lap();
-      if (n == nsteps - 1)
-        for (int d = 0; d < 3; ++d) stt.reaction[d] = ss.reaction[d];
       MPM_CUDA(cudaEventRecord(X.e0, st));
       // consistent FP64 tangent at the converged increment
       int P = m->np, nd = m->ndof, n3 = 3 * nd;
@@ -943,7 +953,9 @@ extern "C" int mpm_adjoint(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* b
       double* mu = grow<double>(c, X.vec[2], n3);
       double* K = grow<double>(c, X.vec[3], 9 * (size_t)m->nslot);
       AsmOut o{};
-      assemble(c, m, *mat, bd, u, k.load, MPM_FP64, R, K, &o, false);
+      assemble(c, m, *mat, bd, u, k.load, MPM_FP64, R, K, &o, true);
+      if (n == nsteps - 1)
+        for (int d = 0; d < 3; ++d) stt.reaction[d] = o.reaction[d];
       double* Sb = grow<double>(c, X.sg[0], (size_t)P * MAXS);
       double* Gb = grow<double>(c, X.sg[1], (size_t)P * MAXS * 3);
       MPM_CUDA(cudaMemsetAsync(ub, 0, sizeof(double) * n3, st));

@@ -2,6 +2,7 @@
 // (Sec. 5), Newton-Raphson with the line search, then the point update.
 #include <algorithm>
 #include <cmath>
+#include <string>
 
 #include "mpm_internal.cuh"
 
@@ -173,6 +174,13 @@ extern "C" int mpm_step(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* body
     if (status) throw CudaError(status, c->err);
     double* du = nullptr;
     newton(c, m, mat, bd, prm, st, &du);
+    if (prm->du_out) {
+      long long n3 = 3LL * m->ndof;
+      if (n3 > prm->du_capacity)
+        throw CudaError(MPM_ERR_CAPACITY, "step: du_out holds " + std::to_string(prm->du_capacity) +
+                                              " doubles, the increment has " + std::to_string(n3));
+      MPM_CUDA(cudaMemcpyAsync(prm->du_out, du, sizeof(double) * n3, cudaMemcpyDeviceToDevice, s));
+    }
     tm.start();
     point_update(c, m, *mat, du, pts);
     status = check_device_error(c, "point update");

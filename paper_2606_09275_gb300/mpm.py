@@ -74,7 +74,7 @@ class SolveStats(C.Structure):
 
 class StepParams(C.Structure):
     _fields_ = [("load", C.c_double), ("tol", C.c_double), ("maxit", C.c_int),
-                ("lin", SolveParams)]
+                ("lin", SolveParams), ("du_out", C.c_void_p), ("du_capacity", C.c_longlong)]
 
 
 class StepStats(C.Structure):
@@ -85,7 +85,8 @@ class StepStats(C.Structure):
 
 
 class Checkpoint(C.Structure):
-    _fields_ = [("pts", PointsT), ("body_z", C.c_double), ("load", C.c_double)]
+    _fields_ = [("pts", PointsT), ("body_z", C.c_double), ("load", C.c_double),
+                ("du", C.c_void_p), ("du_len", C.c_longlong)]
 
 
 class AdjointStats(C.Structure):
@@ -370,11 +371,15 @@ def solve_static(ctx, mesh, K, rhs, tol=1e-10, maxit=20000):
 
 
 def step(ctx, cfg, points, body_z=None, load=1.0, tol=1e-8, maxit=30, lin_tol=1e-8,
-         lin_maxit=20000, precision=FP64, method=0, inner_tol=1e-3, check=True, mg_reuse=0):
-    """mpm_step: one quasi-static load step; returns the statistics."""
+         lin_maxit=20000, precision=FP64, method=0, inner_tol=1e-3, check=True, mg_reuse=0,
+         du_out=None):
+    """mpm_step: one quasi-static load step; returns the statistics.  du_out
+    (optional float64 device tensor) receives the converged increment."""
     s = points.struct()
     sp = StepParams(load, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol,
-                                                  mg_reuse))
+                                                  mg_reuse),
+                    _p(du_out) if du_out is not None else None,
+                    du_out.numel() if du_out is not None else 0)
     ss = StepStats()
     st = lib().mpm_step(ctx.h, C.byref(domain(cfg)), C.byref(rigid(cfg, body_z)), C.byref(adapt(cfg)),
                         C.byref(material(cfg)), C.byref(s), C.byref(sp), C.byref(ss))
@@ -403,21 +408,27 @@ def adjoint(ctx, cfg, checkpoints, w, tol=1e-8, maxit=30, lin_tol=1e-10, lin_max
     """mpm_adjoint: gradient of w . reaction (end of the last step) with respect
     to the per-point E and yield stress of the first checkpoint.
 
-    checkpoints: list of (Points, body_z, load), the state at the start of each
-    step; the Newton settings should be those of the forward run.  Returns
-    (dJ_dE, dJ_dys) as device float64 tensors and the statistics."""
+    checkpoints: list of (Points, body_z, load) or (Points, body_z, load, du),
+    the state at the start of each step and, optionally, the step's converged
+    increment (then the step is not solved again); the Newton settings should
+    be those of the forward run.  Returns (dJ_dE, dJ_dys) as device float64
+    tensors and the statistics."""
     n = len(checkpoints)
     arr = (Checkpoint * n)()
-    for k, (pts, bz, ld) in enumerate(checkpoints):
+    for k, ck in enumerate(checkpoints):
+        pts, bz, ld = ck[:3]
+        du = ck[3] if len(ck) > 3 else None
         arr[k].pts = pts.struct()
         arr[k].body_z = bz
         arr[k].load = ld
+        arr[k].du = _p(du) if du is not None else None
+        arr[k].du_len = du.numel() if du is not None else 0
     p0 = checkpoints[0][0]
     dE = torch.zeros(p0.count, dtype=torch.float64, device=p0.t["E"].device)
     dys = torch.zeros_like(dE)
     wv = (C.c_double * 3)(*[float(v) for v in w])
     sp = StepParams(1.0, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol,
-                                                 mg_reuse))
+                                                 mg_reuse), None, 0)
     st_ = AdjointStats()
     st = lib().mpm_adjoint(ctx.h, C.byref(domain(cfg)), C.byref(rigid(cfg)), C.byref(adapt(cfg)),
                            C.byref(material(cfg)), arr, n, C.byref(sp),

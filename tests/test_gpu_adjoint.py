@@ -185,3 +185,17 @@ def test_adjoint_with_multigrid_pcg_matches(gpu, problem):
     assert np.allclose(r.numpy(), problem["reaction"], rtol=1e-9)
     assert np.max(np.abs(dE - problem["dE"])) <= 1e-7 * np.abs(problem["dE"]).max()
     assert np.max(np.abs(dys - problem["dys"])) <= 1e-7 * np.abs(problem["dys"]).max()
+
+
+def test_adjoint_from_stored_increments_equals_resolve(gpu, problem):
+    # checkpoints with the forward's converged increments (no Newton re-solve in
+    # the reverse pass) give the gradient of the re-solving adjoint
+    mpm, autodiff, ctx, torch = gpu
+    path = autodiff.LoadPath(ctx, problem["cfg"], problem["pts"], NSTEPS, store_increments=False)
+    _, ck, _ = path.run(problem["E"], problem["ys"])
+    assert all(len(c) == 3 for c in ck)
+    dE, dys, st = path.gradient(ck, W)
+    dE, dys = dE.cpu().numpy(), dys.cpu().numpy()
+    assert np.max(np.abs(dE - problem["dE"])) <= 1e-8 * np.abs(problem["dE"]).max()
+    assert np.max(np.abs(dys - problem["dys"])) <= 1e-8 * np.abs(problem["dys"]).max()
+    assert st["ms_forward"] > problem["adj_stats"]["ms_forward"]
