@@ -103,8 +103,9 @@ typedef struct {
 
 typedef struct {
   int method;      /* 0 auto (PCG if symmetric else BiCGStab), 1 PCG, 2 BiCGStab,
-                      3 PCG preconditioned by a geometric multigrid V-cycle
-                      (symmetric tangents only; MPM_ERR_ARG otherwise)       */
+                      3 preconditioned by a geometric multigrid V-cycle:
+                      PCG for symmetric tangents, BiCGStab (one V-cycle per
+                      half-step) for the non-associated Drucker-Prager one */
   int precision;   /* mpm_precision of the stored matrix and the inner solve     */
   double tol;      /* relative residual target ||b - K x|| <= tol ||b||           */
   int maxit;       /* cap on Krylov iterations (all refinement rounds together)  */

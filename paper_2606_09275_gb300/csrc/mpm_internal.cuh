@@ -503,8 +503,8 @@ void solve(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const void* K
 // geometric multigrid preconditioner (mpm_mg.cu): structure for the current
 // mesh build and Galerkin operators for the stiffness K (T = float or double);
 // mg_apply computes z = B r (one V-cycle).  `sk`/`k` let a PCG loop skip the
-// work once its residual has converged (slot (k+1) % 3 of rr).  rz (device,
-// may be null) receives += r.z.
+// work once its residual has converged (slot (k+1) % 3 of rr); with k < 0
+// only sk->done is looked at.  rz (device, may be null) receives += r.z.
 template <class T>
 void mg_setup(mpm_ctx* c, mpm_mesh* m, const T* K, bool reuse);
 template <class T>

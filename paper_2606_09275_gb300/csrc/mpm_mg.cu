@@ -35,8 +35,9 @@ __host__ __device__ inline void unpack3(int v, int* c) {
   c[2] = v >> 20;
 }
 
+// k < 0 (BiCGStab): only the solve's `done` flag stops the work
 __device__ inline bool skip(const Scal* sk, int k) {
-  return sk && (sk->done || sk->rr[(k + 1) % 3] <= sk->thr);
+  return sk && (sk->done || (k >= 0 && sk->rr[(k + 1) % 3] <= sk->thr));
 }
 
 // ---------------------------------------------------------------- structure

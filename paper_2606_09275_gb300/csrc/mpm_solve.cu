@@ -296,8 +296,10 @@ __global__ void k_bicg_p(int npad, double* p, const double* __restrict__ r, cons
     ld4(v + 4 * (size_t)i, vv);
     for (int c = 0; c < 4; ++c) pv[c] = rv[c] + beta * (pv[c] - om * vv[c]);
     st4(p + 4 * (size_t)i, pv);
-    apply_dinv(Dinv, i, pv, zv);
-    st4(ph + 4 * (size_t)i, zv);
+    if (Dinv) {  // else the multigrid V-cycle writes ph
+      apply_dinv(Dinv, i, pv, zv);
+      st4(ph + 4 * (size_t)i, zv);
+    }
   }
 }
 
@@ -318,8 +320,10 @@ __global__ void k_bicg_s(int npad, const double* __restrict__ r, const double* _
       ss += sv[c] * sv[c];
     }
     st4(s + 4 * (size_t)i, sv);
-    apply_dinv(Dinv, i, sv, zv);
-    st4(sh_ + 4 * (size_t)i, zv);
+    if (Dinv) {
+      apply_dinv(Dinv, i, sv, zv);
+      st4(sh_ + 4 * (size_t)i, zv);
+    }
   }
   ss = block_sum(ss, sh);
   if (threadIdx.x == 0) atomicAdd(&sc->a[5], ss);
@@ -563,6 +567,40 @@ int run_pcg_mg(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* b, T* x,
   return sc_h->breakdown ? MPM_ERR_KRYLOV : MPM_OK;
 }
 
+__global__ void k_d2f(long long n, const double* __restrict__ a, float* b, const Scal* sc) {
+  if (sc && sc->done) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+__global__ void k_f2d(long long n, const float* __restrict__ a, double* b, const Scal* sc) {
+  if (sc && sc->done) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+// z = B y by one V-cycle on FP64 vectors (4 components over 32*nslice rows).
+// The FP32 V-cycle of the mixed path works on FP32 copies of y and z.
+template <class T>
+void mg_precondition(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* y, double* z,
+                     const Scal* sc) {
+  if constexpr (sizeof(T) == 8) {
+    mg_apply<double>(c, m, K, y, z, sc, -1, nullptr);
+  } else {
+    cudaStream_t st = c->stream;
+    long long n4 = 4LL * 32 * m->nslice;
+    float* y32 = grow<float>(c, c->v[23], 2 * (size_t)n4);
+    float* z32 = y32 + n4;
+    MPM_LAUNCH(k_d2f<<<4 * 152, 256, 0, st>>>(n4, y, y32, sc));
+    mg_apply<float>(c, m, K, y32, z32, sc, -1, nullptr);
+    MPM_LAUNCH(k_f2d<<<4 * 152, 256, 0, st>>>(n4, z32, z, sc));
+  }
+}
+
+// BiCGStab, right preconditioned by block Jacobi (Dinv) or, with Dinv null,
+// by one multigrid V-cycle per half-step (mg_setup already run for K)
 template <class T>
 int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, const double* b,
                  double* x, double tol, int maxit, Scal* sc_d, Scal* sc_h, double* relres,
@@ -604,15 +642,25 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
   init.a[3] = bb;  // r0 . r at the start
   MPM_CUDA(cudaMemcpyAsync(sc_d, &init, sizeof(Scal), cudaMemcpyHostToDevice, st));
   int vb = 4 * 152, it = 0;
-  const int batch = 16;
+  const int batch = Dinv ? 16 : 4;
   while (it < maxit) {
     int iend = std::min(maxit, it + batch);
     for (; it < iend; ++it) {
       MPM_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
       MPM_LAUNCH(k_bicg_p<<<vb, 256, 0, st>>>(npad, p, r, v, ph, Dinv, sc_d));
+      if (!Dinv) {
+        prof_begin(c, MPM_PROF_MG);
+        mg_precondition<T>(c, m, K, p, ph, sc_d);
+        prof_end(c);
+      }
       MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, ph, v, r0, &sc_d->a[4], nullptr, sc_d, 0));
       MPM_LAUNCH(k_bicg_s<<<vb, 256, 0, st>>>(npad, r, v, s, shv, Dinv, sc_d));
       MPM_LAUNCH(k_bicg_check_s<<<vb, 256, 0, st>>>(nd, x, ph, sc_d));
+      if (!Dinv) {
+        prof_begin(c, MPM_PROF_MG);
+        mg_precondition<T>(c, m, K, s, shv, sc_d);
+        prof_end(c);
+      }
       MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, shv, t, s, &sc_d->a[6], &sc_d->a[7], sc_d, 1));
       MPM_LAUNCH(k_bicg_x<<<vb, 256, 0, st>>>(nd, npad, x, r, ph, shv, s, t, r0, sc_d, red, red + 1));
       MPM_LAUNCH(k_bicg_rotate<<<1, 1, 0, st>>>(sc_d, red, red + 1, it + 1));
@@ -641,13 +689,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   int method = prm.method;
   bool sym = !(mat.model == 2 && mat.psi != mat.phi);
   if (method == 0) method = sym ? 1 : 2;
-  if (method == 3 && !sym) {
-    out->iterations = 0;
-    out->refinements = 0;
-    out->status = MPM_ERR_ARG;
-    set_error(c, "multigrid PCG needs a symmetric tangent (non-associated Drucker-Prager is not)");
-    return;
-  }
+  bool mgb = method == 3 && !sym;  // multigrid-preconditioned BiCGStab
   Scal* sc_d = grow<Scal>(c, c->v[20], 1);
   Scal* sc_h = (Scal*)(c->h_red + 32);  // pinned, 32 doubles fit Scal
   static_assert(sizeof(Scal) <= 32 * sizeof(double), "scalar block too large");
@@ -661,7 +703,10 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     int its = 0;
     double rel = 0.0;
     int sst;
-    if (method == 3) {
+    if (mgb) {
+      mg_setup<double>(c, m, Kd, prm.mg_reuse != 0);
+      sst = run_bicgstab<double>(c, m, Kd, nullptr, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
+    } else if (method == 3) {
       mg_setup<double>(c, m, Kd, prm.mg_reuse != 0);
       sst = run_pcg_mg<double>(c, m, Kd, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its,
                                grow<double>(c, c->v[4], n4), grow<double>(c, c->v[5], n4),
@@ -676,7 +721,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     out->relres = rel;
     out->status = sst;
     if (sst)
-      set_error(c, std::string(method == 1 ? "PCG" : (method == 3 ? "multigrid PCG" : "BiCGStab")) +
+      set_error(c, std::string(method == 1 ? "PCG" : (mgb ? "multigrid BiCGStab" : (method == 3 ? "multigrid PCG" : "BiCGStab"))) +
                        " did not reach the tolerance (" +
                        std::to_string(its) + " iterations, relative residual " +
                        std::to_string(rel) + (sc_h->breakdown ? ", breakdown)" : ")"));
@@ -688,7 +733,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   double* r64 = grow<double>(c, c->v[12], n3);
   float* d32 = grow<float>(c, c->v[13], n3);
   double* slot = c->d_red + 44;
-  if (method == 1 || method == 3) {
+  if ((method == 1 || method == 3) && !mgb) {
     float* Dinv = grow<float>(c, c->v[3], 12 * (size_t)npad);
     if (method == 3)
       mg_setup<float>(c, m, Kf, prm.mg_reuse != 0);
@@ -737,9 +782,15 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     if (status) set_error(c, "mixed-precision refinement did not reach the tolerance");
     return;
   }
-  // non-symmetric mixed: BiCGStab on the FP32 matrix with FP64 vectors
-  double* Dinv = grow<double>(c, c->v[3], 12 * (size_t)npad);
-  MPM_LAUNCH(k_block_jacobi<float, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, Kf, Dinv, c->d_err));
+  // non-symmetric mixed: BiCGStab on the FP32 matrix with FP64 vectors,
+  // preconditioned by block Jacobi or by the FP32 multigrid V-cycle
+  double* Dinv = nullptr;
+  if (mgb) {
+    mg_setup<float>(c, m, Kf, prm.mg_reuse != 0);
+  } else {
+    Dinv = grow<double>(c, c->v[3], 12 * (size_t)npad);
+    MPM_LAUNCH(k_block_jacobi<float, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, Kf, Dinv, c->d_err));
+  }
   int its = 0;
   double rel = 0.0;
   int sst = run_bicgstab<float>(c, m, Kf, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
@@ -747,7 +798,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   out->relres = rel;
   out->status = sst;
   if (sst)
-    set_error(c, "BiCGStab (FP32 matrix) did not reach the tolerance (" + std::to_string(its) +
+    set_error(c, std::string(mgb ? "multigrid BiCGStab" : "BiCGStab") + " (FP32 matrix) did not reach the tolerance (" + std::to_string(its) +
                      " iterations, relative residual " + std::to_string(rel) +
                      (sc_h->breakdown ? ", breakdown)" : ")"));
 }

@@ -345,7 +345,7 @@ def assemble(ctx, mesh, cfg, du, load=1.0, precision=FP64, tangent=True, body_z=
 
 def solve(ctx, mesh, cfg, K, rhs, precision=FP64, tol=1e-10, maxit=20000, method=0,
           inner_tol=1e-3, mg_reuse=0):
-    """mpm_solve: block-Jacobi PCG, BiCGStab or multigrid PCG (method 3); FP32
+    """mpm_solve: block-Jacobi PCG, BiCGStab or multigrid PCG / BiCGStab (method 3); FP32
     inner solves inside FP64 refinement when mixed."""
     x = torch.empty_like(rhs)
     sp = SolveParams(method, precision, tol, maxit, inner_tol, mg_reuse)

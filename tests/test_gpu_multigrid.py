@@ -1,8 +1,9 @@
-"""PCG preconditioned by the geometric multigrid V-cycle (solve method 3),
-through the C ABI, against the oracle's dense LU and against the load steps
-of the oracle.  The preconditioner changes how the Krylov solve gets to the
-tolerance, not the solution: the same FP64 and mixed-precision bars apply as
-for block-Jacobi PCG."""
+"""Krylov solves preconditioned by the geometric multigrid V-cycle (solve
+method 3: PCG for symmetric tangents, BiCGStab for the non-associated
+Drucker-Prager one), through the C ABI, against the oracle's dense LU and
+against the load steps of the oracle.  The preconditioner changes how the
+Krylov solve gets to the tolerance, not the solution: the same FP64 and
+mixed-precision bars apply as for block Jacobi."""
 import numpy as np
 import pytest
 
@@ -110,13 +111,54 @@ def test_multigrid_punch_steps_match_oracle(gpu, reuse):
     assert np.max(np.abs(pg["x"] - po["x"])) <= 1e-9 * 0.1 * 3 / 50
 
 
-def test_multigrid_rejects_a_non_symmetric_tangent(gpu):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multigrid_bicgstab_on_the_drucker_prager_tangent(gpu, precision):
+    # non-associated Drucker-Prager (psi != phi), plastic increment: the
+    # tangent is not symmetric, so method 3 runs BiCGStab with the V-cycle
     mpm, ctx, torch = gpu
     cfg, bz = CASES["cone_d4_8"]()
     om, mesh, P = both(gpu, cfg, bz)
-    nd = mesh.info()["ndof"]
-    g = mpm.assemble(ctx, mesh, cfg, torch.zeros(3 * nd, dtype=torch.float64, device="cuda"),
-                     body_z=bz)
-    with pytest.raises(mpm.MPMError) as e:
-        mpm.solve(ctx, mesh, cfg, g["K"], -g["R"], tol=1e-8, method=MG)
-    assert e.value.code == 1
+    nd = om.counts()["ndof"]
+    rng = np.random.default_rng(8)
+    du = 1e-4 * rng.standard_normal(3 * nd)
+    bcm = om.bcmask()
+    du[[bool((bcm[i // 3] >> (i % 3)) & 1) for i in range(3 * nd)]] = 0.0
+    o = om.assemble(du)
+    xo, _ = om.solve(o["K"], -o["R"], tol=1e-14)
+    g = mpm.assemble(ctx, mesh, cfg, torch.tensor(du, device="cuda"), body_z=bz, precision=precision)
+    tol = 1e-11 if precision == 0 else 1e-9
+    x, st = mpm.solve(ctx, mesh, cfg, g["K"], -g["R"], tol=tol, maxit=5000, method=MG,
+                      precision=precision)
+    assert st["status"] == 0 and st["relres"] <= tol
+    bar = 1e-8 if precision == 0 else 1e-5
+    assert np.max(np.abs(x.cpu().numpy() - xo)) <= bar * np.abs(xo).max()
+    xb, sb = mpm.solve(ctx, mesh, cfg, g["K"], -g["R"], tol=tol, maxit=50000, method=2,
+                       precision=precision)
+    assert sb["status"] == 0
+    print("cone (precision %d): %d dofs, multigrid BiCGStab %d iterations, block-Jacobi %d" % (
+        precision, nd, st["iterations"], sb["iterations"]))
+    assert st["iterations"] < sb["iterations"]
+
+
+def test_multigrid_bicgstab_cone_steps_match_oracle(gpu):
+    # two load steps of the cone into the Drucker-Prager layer, Newton on the
+    # non-symmetric tangent with multigrid BiCGStab, FP64 and mixed
+    mpm, ctx, torch = gpu
+    cfg = inputs.workload("cone")
+    pts = inputs.make_points(cfg)
+    om = oracle.Model(cfg, pts)
+    P = mpm.Points(pts, capacity=64 * len(pts["x"]))
+    Pm = mpm.Points(pts, capacity=64 * len(pts["x"]))
+    for n in range(1, 3):
+        bz = inputs.body_z(cfg, n)
+        om.set_body_z(bz)
+        load = inputs.load_factor(cfg, n)
+        so = om.step(load=load, tol=1e-10, lin_tol=1e-11)
+        sg = mpm.step(ctx, cfg, P, body_z=bz, load=load, tol=1e-10, lin_tol=1e-11,
+                      lin_maxit=20000, method=MG, mg_reuse=1)
+        sm = mpm.step(ctx, cfg, Pm, body_z=bz, load=load, tol=1e-8, lin_tol=1e-8,
+                      lin_maxit=20000, method=MG, mg_reuse=1, precision=1)
+        assert so["status"] == 0 and sg["status"] == 0 and sm["status"] == 0
+        ra = so["reaction"][2]
+        assert abs(sg["reaction"][2] - ra) <= 1e-8 * abs(ra)
+        assert abs(sm["reaction"][2] - ra) <= 1e-6 * abs(ra)
