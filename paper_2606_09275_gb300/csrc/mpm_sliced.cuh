@@ -137,19 +137,34 @@ __global__ inline void k_split_df(int npad, int nd, const double* __restrict__ x
   xs[2 * (size_t)i + 1] = make_float4(hl[4], hl[5], 0.f, 0.f);
 }
 
-// four FP16 values (8-byte aligned) to floats
-__device__ inline void ld4h(const __half* p, float* v) {
-  uint2 u = *reinterpret_cast<const uint2*>(p);
-  __half2 a = *reinterpret_cast<const __half2*>(&u.x), b = *reinterpret_cast<const __half2*>(&u.y);
-  float2 fa = __half22float2(a), fb = __half22float2(b);
-  v[0] = fa.x;
-  v[1] = fa.y;
-  v[2] = fb.x;
-  v[3] = fb.y;
+// one group of four FP16 blocks (raw 8-byte words of the 9 planes) times x
+__device__ inline void acc_h4(const uint2* u, int4 c, const float* __restrict__ x, float* y) {
+  int cc[4] = {c.x, c.y, c.z, c.w};
+  float v[9][4];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    float2 fa = __half22float2(*reinterpret_cast<const __half2*>(&u[e].x));
+    float2 fb = __half22float2(*reinterpret_cast<const __half2*>(&u[e].y));
+    v[e][0] = fa.x;
+    v[e][1] = fa.y;
+    v[e][2] = fb.x;
+    v[e][3] = fb.y;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float xv[4];
+    ld4(x + 4 * (size_t)cc[j], xv);
+    y[0] += v[0][j] * xv[0] + v[1][j] * xv[1] + v[2][j] * xv[2];
+    y[1] += v[3][j] * xv[0] + v[4][j] * xv[1] + v[5][j] * xv[2];
+    y[2] += v[6][j] * xv[0] + v[7][j] * xv[1] + v[8][j] * xv[2];
+  }
 }
 
 // y = row r of an FP16 copy of K (same sliced layout, values scaled by a power
-// of two) times x; FP32 arithmetic, the caller undoes the scale
+// of two) times x; FP32 arithmetic, the caller undoes the scale.  Two groups
+// of four blocks per trip, all of their loads issued before the arithmetic:
+// FP16 blocks are half the bytes of FP32 ones, so a trip over one group would
+// keep half as many bytes in flight as the FP32 row product.
 __device__ inline void sliced_row_h(int r, Sliced S, const __half* __restrict__ K,
                                     const float* __restrict__ x, float* y) {
   int s = r >> 5, ln = r & 31;
@@ -159,21 +174,27 @@ __device__ inline void sliced_row_h(int r, Sliced S, const __half* __restrict__ 
   const int* cb = S.scol + b0;
   size_t plane = (size_t)32 * W;
   y[0] = y[1] = y[2] = 0.f;
-  for (int k4 = 0; k4 < (W >> 2); ++k4) {
-    size_t off = ((size_t)k4 * 32 + ln) * 4;
-    int4 c = *reinterpret_cast<const int4*>(cb + off);
-    int cc[4] = {c.x, c.y, c.z, c.w};
-    float v[9][4];
+  int n4 = W >> 2, k4 = 0;
+  for (; k4 + 2 <= n4; k4 += 2) {
+    size_t off0 = ((size_t)k4 * 32 + ln) * 4, off1 = off0 + 128;
+    int4 c0 = *reinterpret_cast<const int4*>(cb + off0);
+    int4 c1 = *reinterpret_cast<const int4*>(cb + off1);
+    uint2 u0[9], u1[9];
 #pragma unroll
-    for (int e = 0; e < 9; ++e) ld4h(Kb + e * plane + off, v[e]);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      float xv[4];
-      ld4(x + 4 * (size_t)cc[j], xv);
-      y[0] += v[0][j] * xv[0] + v[1][j] * xv[1] + v[2][j] * xv[2];
-      y[1] += v[3][j] * xv[0] + v[4][j] * xv[1] + v[5][j] * xv[2];
-      y[2] += v[6][j] * xv[0] + v[7][j] * xv[1] + v[8][j] * xv[2];
+    for (int e = 0; e < 9; ++e) {
+      u0[e] = *reinterpret_cast<const uint2*>(Kb + e * plane + off0);
+      u1[e] = *reinterpret_cast<const uint2*>(Kb + e * plane + off1);
     }
+    acc_h4(u0, c0, x, y);
+    acc_h4(u1, c1, x, y);
+  }
+  if (k4 < n4) {
+    size_t off = ((size_t)k4 * 32 + ln) * 4;
+    int4 c0 = *reinterpret_cast<const int4*>(cb + off);
+    uint2 u0[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) u0[e] = *reinterpret_cast<const uint2*>(Kb + e * plane + off);
+    acc_h4(u0, c0, x, y);
   }
 }
 
