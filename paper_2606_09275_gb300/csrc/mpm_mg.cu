@@ -554,17 +554,30 @@ __global__ void k_mg_lvl(int nrow, int S, int R, int n1, const int* __restrict__
   int S1 = 2 * R + 1;
   const T* row = A + (size_t)a * S * 9;
   T y0 = 0, y1 = 0, y2 = 0;
-  for (int o = lane; o < S; o += 32) {
-    int cb[3] = {ca[0] + o % S1 - R, ca[1] + (o / S1) % S1 - R, ca[2] + o / (S1 * S1) - R};
-    if (cb[0] < 0 || cb[1] < 0 || cb[2] < 0 || cb[0] >= n1 || cb[1] >= n1 || cb[2] >= n1) continue;
-    int j = gid[cb[0] + n1 * (cb[1] + n1 * cb[2])];
-    if (j < 0) continue;
-    T xv[4];
-    ld4(x + 4 * (size_t)j, xv);
-    const T* v = row + 9 * o;
-    y0 += v[0] * xv[0] + v[1] * xv[1] + v[2] * xv[2];
-    y1 += v[3] * xv[0] + v[4] * xv[1] + v[5] * xv[2];
-    y2 += v[6] * xv[0] + v[7] * xv[1] + v[8] * xv[2];
+  // four stencil trips of the warp per round: their grid lookups, then their
+  // x loads, go out together (two dependent round trips per round, not eight)
+  for (int o0 = 0; o0 < S; o0 += 128) {
+    int j[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int o = o0 + 32 * u + lane;
+      j[u] = -1;
+      if (o < S) {
+        int cb[3] = {ca[0] + o % S1 - R, ca[1] + (o / S1) % S1 - R, ca[2] + o / (S1 * S1) - R};
+        if (cb[0] >= 0 && cb[1] >= 0 && cb[2] >= 0 && cb[0] < n1 && cb[1] < n1 && cb[2] < n1)
+          j[u] = gid[cb[0] + n1 * (cb[1] + n1 * cb[2])];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (j[u] < 0) continue;
+      T xv[4];
+      ld4(x + 4 * (size_t)j[u], xv);
+      const T* v = row + 9 * (o0 + 32 * u + lane);
+      y0 += v[0] * xv[0] + v[1] * xv[1] + v[2] * xv[2];
+      y1 += v[3] * xv[0] + v[4] * xv[1] + v[5] * xv[2];
+      y2 += v[6] * xv[0] + v[7] * xv[1] + v[8] * xv[2];
+    }
   }
   y0 = warp_sum(y0);
   y1 = warp_sum(y1);
@@ -584,14 +597,18 @@ __global__ void k_mg_lvl(int nrow, int S, int R, int n1, const int* __restrict__
         hi[d] = (ca[d] + 1) >> 1;
         if (lo[d] != hi[d]) f *= (T)0.5;
       }
-      for (int z = lo[2]; z <= hi[2]; ++z)
-        for (int y = lo[1]; y <= hi[1]; ++y)
-          for (int xx = lo[0]; xx <= hi[0]; ++xx) {
-            int bc = gid_c[xx + n1c * (y + n1c * z)];
-            if (bc < 0) continue;
-            for (int c = 0; c < 3; ++c)
-              if (!((mi >> c) & 1)) atomicAdd(out + 4 * (size_t)bc + c, f * res[c]);
-          }
+      int bq[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int xx = lo[0] + (q & 1), y = lo[1] + ((q >> 1) & 1), z = lo[2] + (q >> 2);
+        bq[q] = (xx <= hi[0] && y <= hi[1] && z <= hi[2]) ? gid_c[xx + n1c * (y + n1c * z)] : -1;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (bq[q] < 0) continue;
+        for (int c = 0; c < 3; ++c)
+          if (!((mi >> c) & 1)) atomicAdd(out + 4 * (size_t)bq[q] + c, f * res[c]);
+      }
     } else {
       T xv[4], d[4];
       ld4(x + 4 * (size_t)a, xv);
@@ -612,13 +629,21 @@ __global__ void k_mg_prolong1(int nd, const int* __restrict__ pidx, const float*
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nd) return;
   T s[3] = {0, 0, 0};
+  // the row's 8 weights in two 16-byte loads each, then all coarse loads
+  int4 ia = *reinterpret_cast<const int4*>(pidx + 8 * (size_t)i);
+  int4 ib = *reinterpret_cast<const int4*>(pidx + 8 * (size_t)i + 4);
+  float4 wa = *reinterpret_cast<const float4*>(pw + 8 * (size_t)i);
+  float4 wb = *reinterpret_cast<const float4*>(pw + 8 * (size_t)i + 4);
+  int av[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
+  float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+  bool live = true;  // entries end at the first negative index
+#pragma unroll
   for (int q = 0; q < 8; ++q) {
-    int a = pidx[8 * (size_t)i + q];
-    if (a < 0) break;
-    T w = (T)pw[8 * (size_t)i + q];
+    live = live && av[q] >= 0;
+    if (!live) continue;
     T xv[4];
-    ld4(x1 + 4 * (size_t)a, xv);
-    for (int c = 0; c < 3; ++c) s[c] += w * xv[c];
+    ld4(x1 + 4 * (size_t)av[q], xv);
+    for (int c = 0; c < 3; ++c) s[c] += (T)wv[q] * xv[c];
   }
   int mi = fmask[i];
   T xv[4];
@@ -646,15 +671,20 @@ __global__ void k_mg_prolong_u(int nrow, const int* __restrict__ xyz_f, const in
     if (lo[d] != hi[d]) f *= (T)0.5;
   }
   T s[3] = {0, 0, 0};
-  for (int z = lo[2]; z <= hi[2]; ++z)
-    for (int y = lo[1]; y <= hi[1]; ++y)
-      for (int x = lo[0]; x <= hi[0]; ++x) {
-        int b = gid_c[x + n1c * (y + n1c * z)];
-        if (b < 0) continue;
-        T xv[4];
-        ld4(xc + 4 * (size_t)b, xv);
-        for (int cc = 0; cc < 3; ++cc) s[cc] += f * xv[cc];
-      }
+  // the (up to) 8 coarse corners in z, y, x order: lookups first, then loads
+  int bq[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    int x = lo[0] + (q & 1), y = lo[1] + ((q >> 1) & 1), z = lo[2] + (q >> 2);
+    bq[q] = (x <= hi[0] && y <= hi[1] && z <= hi[2]) ? gid_c[x + n1c * (y + n1c * z)] : -1;
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (bq[q] < 0) continue;
+    T xv[4];
+    ld4(xc + 4 * (size_t)bq[q], xv);
+    for (int cc = 0; cc < 3; ++cc) s[cc] += f * xv[cc];
+  }
   int mi = fmask[i];
   T xv[4];
   ld4(xf + 4 * (size_t)i, xv);
