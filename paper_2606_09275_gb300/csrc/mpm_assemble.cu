@@ -326,6 +326,29 @@ __device__ inline unsigned tangent_hash(int c, int hmask) {
   return ((unsigned)c * 2654435761u >> 7) & (unsigned)hmask;
 }
 
+// the 27 terms (grad_x S_k)^T A'_p of a source from shared memory (16-byte
+// aligned, 32 entries) in vector loads
+__device__ inline void tangent_terms(const float* Tt, float* t) {
+  const float4* v = reinterpret_cast<const float4*>(Tt);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    float4 a = v[i];
+    t[4 * i] = a.x;
+    if (4 * i + 1 < 27) t[4 * i + 1] = a.y;
+    if (4 * i + 2 < 27) t[4 * i + 2] = a.z;
+    if (4 * i + 3 < 27) t[4 * i + 3] = a.w;
+  }
+}
+__device__ inline void tangent_terms(const double* Tt, double* t) {
+  const double2* v = reinterpret_cast<const double2*>(Tt);
+#pragma unroll
+  for (int i = 0; i < 14; ++i) {
+    double2 a = v[i];
+    t[2 * i] = a.x;
+    if (2 * i + 1 < 27) t[2 * i + 1] = a.y;
+  }
+}
+
 // One warp owns block row r: for every point p with r in its support (local
 // index k), K_{r,w} += V0_p (grad_x S_k)^T A'_p (grad_x S_w) for all w in the
 // support of p.  The row accumulates in shared memory (mr = longest row, a
@@ -369,35 +392,41 @@ __global__ void __launch_bounds__(32 * TW)
     hval[h] = i;
   }
   __syncwarp();
-  for (long long q = sptr[r]; q < sptr[r + 1]; ++q) {
-    uint32_t sid = (uint32_t)skeys[q];
-    int w = (int)(sid >> 6), k = (int)(sid & 63);
-    if (w >= P) continue;  // ghost-face source: no point tangent
-    size_t ok = ((size_t)w * MAXS + k) * 3;
-    T gk0 = gx[ok], gk1 = gx[ok + 1], gk2 = gx[ok + 2];
-    T v0 = (T)V0[w];
-    if (lane < 27) {
-      const T* A = Aalg + 81 * (size_t)w + 3 * lane;
-      Tt[lane] = v0 * (gk0 * A[0] + gk1 * A[1] + gk2 * A[2]);
-    }
-    __syncwarp();
-    T t[27];
+  // the row's source keys 32 at a time (one coalesced load, then broadcast)
+  const unsigned FULL = 0xffffffffu;
+  long long q0 = sptr[r], q1 = sptr[r + 1];
+  for (long long qb = q0; qb < q1; qb += 32) {
+    int cnt = (int)min(32LL, q1 - qb);
+    uint32_t kb = lane < cnt ? (uint32_t)skeys[qb + lane] : 0u;
+    for (int u = 0; u < cnt; ++u) {
+      uint32_t sid = __shfl_sync(FULL, kb, u);
+      int w = (int)(sid >> 6), k = (int)(sid & 63);
+      if (w >= P) continue;  // ghost-face source: no point tangent
+      size_t ok = ((size_t)w * MAXS + k) * 3;
+      T gk0 = gx[ok], gk1 = gx[ok + 1], gk2 = gx[ok + 2];
+      T v0 = (T)V0[w];
+      if (lane < 27) {
+        const T* A = Aalg + 81 * (size_t)w + 3 * lane;
+        Tt[lane] = v0 * (gk0 * A[0] + gk1 * A[1] + gk2 * A[2]);
+      }
+      __syncwarp();
+      T t[27];
+      tangent_terms(Tt, t);
+      int n = nsup[w];
+      for (int l = lane; l < n; l += 32) {
+        size_t o = (size_t)w * MAXS + l;
+        int c = sidx[o];
+        T g0 = gx[3 * o], g1 = gx[3 * o + 1], g2 = gx[3 * o + 2];
+        unsigned h = tangent_hash(c, hmask);
+        int key;
+        while ((key = hkey[h]) != c && key != -1) h = (h + 1) & hmask;
+        if (key != c) continue;
+        int idx = hval[h];
 #pragma unroll
-    for (int e = 0; e < 27; ++e) t[e] = Tt[e];
-    int n = nsup[w];
-    for (int l = lane; l < n; l += 32) {
-      size_t o = (size_t)w * MAXS + l;
-      int c = sidx[o];
-      T g0 = gx[3 * o], g1 = gx[3 * o + 1], g2 = gx[3 * o + 2];
-      unsigned h = tangent_hash(c, hmask);
-      int key;
-      while ((key = hkey[h]) != c && key != -1) h = (h + 1) & hmask;
-      if (key != c) continue;
-      int idx = hval[h];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) acc[e * nb + idx] += t[3 * e] * g0 + t[3 * e + 1] * g1 + t[3 * e + 2] * g2;
+        for (int e = 0; e < 9; ++e) acc[e * nb + idx] += t[3 * e] * g0 + t[3 * e + 1] * g1 + t[3 * e + 2] * g2;
+      }
+      __syncwarp();
     }
-    __syncwarp();
   }
   // ghost, then the Dirichlet identity, then the row (and its padding slots,
   // zero) into the sliced storage

@@ -513,12 +513,19 @@ __global__ void k_mg_fine(int nd, int npad, Sliced SK, const TK* __restrict__ K,
     if (MODE == 0) {
       if (r < nd) {
         int mi = fmask[r];
+        int4 ia = *reinterpret_cast<const int4*>(pidx + 8 * (size_t)r);
+        int4 ib = *reinterpret_cast<const int4*>(pidx + 8 * (size_t)r + 4);
+        float4 wa = *reinterpret_cast<const float4*>(pw + 8 * (size_t)r);
+        float4 wb = *reinterpret_cast<const float4*>(pw + 8 * (size_t)r + 4);
+        int av[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
+        float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+        bool live = true;  // entries end at the first negative index
+#pragma unroll
         for (int q = 0; q < 8; ++q) {
-          int a = pidx[8 * (size_t)r + q];
-          if (a < 0) break;
-          T w = (T)pw[8 * (size_t)r + q];
+          live = live && av[q] >= 0;
+          if (!live) continue;
           for (int c = 0; c < 3; ++c)
-            if (!((mi >> c) & 1)) atomicAdd(out + 4 * (size_t)a + c, w * res[c]);
+            if (!((mi >> c) & 1)) atomicAdd(out + 4 * (size_t)av[q] + c, (T)wv[q] * res[c]);
         }
       }
     } else {
