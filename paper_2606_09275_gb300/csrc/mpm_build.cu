@@ -488,39 +488,56 @@ __global__ void __launch_bounds__(32 * BW)
   int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int w = blockIdx.x * BW + wi;
   if (w >= P) return;
+  // 1. the domain cut into its leaf intersections.  Every cut face is a leaf
+  // face, an integer in grid units, so lane 0 walks the leaves in integer
+  // arithmetic: a bound is either the domain's own (code -1) or a face.
+  // The walk's FP64 work (volumes, centroids) then runs one sub-box per
+  // lane: a warp's FP64 instruction costs the same pipe time whatever the
+  // number of active lanes.
+  double Lo[3], Hi[3];
+  double Vp = domain_box(px + 3 * (size_t)w, plp + 3 * (size_t)w, g, Lo, Hi);
   if (lane == 0) {
-    double Lo[3], Hi[3];
-    double Vp = domain_box(px + 3 * (size_t)w, plp + 3 * (size_t)w, g, Lo, Hi);
     int n = 0;
     if (!(Hi[0] > Lo[0]) || !(Hi[1] > Lo[1]) || !(Hi[2] > Lo[2])) {
       atomicOr(err, EB_DOMAIN);
       n = -1;
     } else {
-      double st[3 * MAXK + 8][6];
-      int ns = 1;
+      int fLo[3], fHi[3];
+      bool iHi[3];
       for (int d = 0; d < 3; ++d) {
-        st[0][d] = Lo[d];
-        st[0][3 + d] = Hi[d];
+        fLo[d] = (int)floor(Lo[d]);
+        fHi[d] = (int)floor(Hi[d]);
+        iHi[d] = Hi[d] == (double)fHi[d];
       }
+      int st[3 * MAXK + 8][6];
+      int ns = 1;
+      for (int d = 0; d < 6; ++d) st[0][d] = -1;
       while (ns > 0) {
         --ns;
-        double a[3], b[3], kh[3], e[3];
-        int q[3];
+        int a[3], b[3], kh[3], e[3], q[3];
         for (int d = 0; d < 3; ++d) {
           a[d] = st[ns][d];
           b[d] = st[ns][3 + d];
-          q[d] = (int)floor(a[d]);
+          q[d] = a[d] < 0 ? fLo[d] : a[d];
           q[d] = q[d] > g.N - 1 ? g.N - 1 : (q[d] < 0 ? 0 : q[d]);
         }
         int K = locate(lkey, nl, q[0], q[1], q[2]);
         int s = 1 << (g.D - llev[K]);
         int ka[3];
         demorton(lkey[K], ka);
-        double vol = 1.0;
+        bool gt[3];
         for (int d = 0; d < 3; ++d) {
-          kh[d] = (double)(ka[d] + s);
-          e[d] = b[d] < kh[d] ? b[d] : kh[d];
-          vol *= e[d] - a[d];
+          kh[d] = ka[d] + s;
+          if (b[d] < 0) {
+            // the domain's upper bound against the face kh: Hi < kh iff
+            // floor(Hi) < kh; Hi > kh iff floor(Hi) > kh, or equal and Hi
+            // is not an integer
+            e[d] = fHi[d] < kh[d] ? -1 : kh[d];
+            gt[d] = fHi[d] > kh[d] || (!iHi[d] && fHi[d] == kh[d]);
+          } else {
+            e[d] = b[d] < kh[d] ? b[d] : kh[d];
+            gt[d] = b[d] > kh[d];
+          }
         }
         if (n >= MAXK || ns + 3 > 3 * MAXK + 8) {
           atomicOr(err, EB_SUPPORT);
@@ -528,29 +545,54 @@ __global__ void __launch_bounds__(32 * BW)
           break;
         }
         SubBox& o = sb[wi][n++];
-        // the leaf size is a power of two: multiplying by its exact reciprocal
-        // equals the division and keeps the FP64 pipe (slow on this part) free
-        double is = ldexp(1.0, llev[K] - g.D);
-        o.is = is;
-        for (int d = 0; d < 3; ++d) o.xi[d] = (0.5 * (a[d] + e[d]) - (double)ka[d]) * is;
-        o.w = vol / Vp;
+        int* cd = reinterpret_cast<int*>(o.xi);  // bound codes until step 1b
+        for (int d = 0; d < 3; ++d) {
+          cd[d] = a[d];
+          cd[3 + d] = e[d];
+        }
         o.K = K;
         o.s = s;
-        if (b[0] > kh[0]) {
-          double* r = st[ns++];
+        if (gt[0]) {
+          int* r = st[ns++];
           r[0] = kh[0]; r[1] = a[1]; r[2] = a[2]; r[3] = b[0]; r[4] = b[1]; r[5] = b[2];
         }
-        if (b[1] > kh[1]) {
-          double* r = st[ns++];
+        if (gt[1]) {
+          int* r = st[ns++];
           r[0] = a[0]; r[1] = kh[1]; r[2] = a[2]; r[3] = e[0]; r[4] = b[1]; r[5] = b[2];
         }
-        if (b[2] > kh[2]) {
-          double* r = st[ns++];
+        if (gt[2]) {
+          int* r = st[ns++];
           r[0] = a[0]; r[1] = a[1]; r[2] = kh[2]; r[3] = e[0]; r[4] = e[1]; r[5] = b[2];
         }
       }
     }
     nsub_s[wi] = n;
+  }
+  __syncwarp();
+  // 1b. one lane per sub-box: volume fraction, centroid in leaf coordinates
+  if (lane < nsub_s[wi]) {
+    SubBox& o = sb[wi][lane];
+    const int* cd = reinterpret_cast<const int*>(o.xi);
+    int ca[3], ce[3];
+    for (int d = 0; d < 3; ++d) {
+      ca[d] = cd[d];
+      ce[d] = cd[3 + d];
+    }
+    int ka[3];
+    demorton(lkey[o.K], ka);
+    double vol = 1.0, xi[3];
+    // the leaf size is a power of two: multiplying by its exact reciprocal
+    // equals the division and keeps the FP64 pipe (slow on this part) free
+    double is = ldexp(1.0, llev[o.K] - g.D);
+    for (int d = 0; d < 3; ++d) {
+      double a = ca[d] < 0 ? Lo[d] : (double)ca[d];
+      double e = ce[d] < 0 ? Hi[d] : (double)ce[d];
+      vol *= e - a;
+      xi[d] = (0.5 * (a + e) - (double)ka[d]) * is;
+    }
+    for (int d = 0; d < 3; ++d) o.xi[d] = xi[d];
+    o.is = is;
+    o.w = vol / Vp;
   }
   __syncwarp();
   int nsub = nsub_s[wi];
