@@ -34,17 +34,34 @@ __global__ void k_kinematics(int P, const int* __restrict__ nsup, const int* __r
       a[6] += u2 * g0; a[7] += u2 * g1; a[8] += u2 * g2;
     }
   }
+  // reduce-scatter of a[0..7] over the 8 lanes of the point (lane sub ends
+  // with the sum of a[sub]: 7 FP64 additions instead of 24; the FP64 pipe
+  // bounds this kernel), a[8] by a butterfly
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    a[i] += __shfl_xor_sync(0xffffffffu, a[i], 4);
-    a[i] += __shfl_xor_sync(0xffffffffu, a[i], 2);
-    a[i] += __shfl_xor_sync(0xffffffffu, a[i], 1);
+  for (int i = 0; i < 4; ++i) {
+    bool up = sub & 4;
+    double send = up ? a[i] : a[i + 4];
+    double keep = up ? a[i + 4] : a[i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   }
-  if (w < P) {
-    double v = a[0];
 #pragma unroll
-    for (int i = 1; i < 8; ++i) v = (sub == i) ? a[i] : v;
-    dF[9 * (size_t)w + sub] = v + ((sub % 4 == 0) ? 1.0 : 0.0);
+  for (int i = 0; i < 2; ++i) {
+    bool up = sub & 2;
+    double send = up ? a[i] : a[i + 2];
+    double keep = up ? a[i + 2] : a[i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  {
+    bool up = sub & 1;
+    double send = up ? a[0] : a[1];
+    double keep = up ? a[1] : a[0];
+    a[0] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+  }
+  a[8] += __shfl_xor_sync(0xffffffffu, a[8], 4);
+  a[8] += __shfl_xor_sync(0xffffffffu, a[8], 2);
+  a[8] += __shfl_xor_sync(0xffffffffu, a[8], 1);
+  if (w < P) {
+    dF[9 * (size_t)w + sub] = a[0] + ((sub % 4 == 0) ? 1.0 : 0.0);
     if (sub == 0) dF[9 * (size_t)w + 8] = a[8] + 1.0;
   }
 }
@@ -259,6 +276,30 @@ __global__ void k_force(int P, const int* __restrict__ nsup, const int* __restri
   double t3 = tau[6 * (size_t)w + 3], t4 = tau[6 * (size_t)w + 4], t5 = tau[6 * (size_t)w + 5];
   double v0 = V0[w];
   int n = nsup[w];
+  if (!STORE) {
+    // residual only: f_k = M dS_k with M = V0 tau F^-T formed once per point,
+    // one entry per lane (9 FP64 multiply-adds per support instead of 21; the
+    // FP64 pipe bounds this kernel, and an FP64 warp instruction costs the
+    // same whatever the number of active lanes)
+    int lr = lane < 9 ? lane / 3 : 0, lc = lane < 9 ? lane % 3 : 0;
+    // row lr of tau (symmetric; stored xx yy zz xy yz xz)
+    double r0 = lr == 0 ? t0 : (lr == 1 ? t3 : t5);
+    double r1 = lr == 0 ? t3 : (lr == 1 ? t1 : t4);
+    double r2 = lr == 0 ? t5 : (lr == 1 ? t4 : t2);
+    double mv = v0 * (r0 * fi[3 * lc] + r1 * fi[3 * lc + 1] + r2 * fi[3 * lc + 2]);
+    double M[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) M[e] = __shfl_sync(0xffffffffu, mv, e);
+    for (int k = lane; k < n; k += 32) {
+      size_t o = (size_t)w * MAXS + k;
+      double a0 = dS[3 * o], a1 = dS[3 * o + 1], a2 = dS[3 * o + 2];
+      int j = sidx[o];
+      atomicAdd(fint + 3 * (size_t)j, M[0] * a0 + M[1] * a1 + M[2] * a2);
+      atomicAdd(fint + 3 * (size_t)j + 1, M[3] * a0 + M[4] * a1 + M[5] * a2);
+      atomicAdd(fint + 3 * (size_t)j + 2, M[6] * a0 + M[7] * a1 + M[8] * a2);
+    }
+    return;
+  }
   for (int k = lane; k < n; k += 32) {
     size_t o = (size_t)w * MAXS + k;
     double a0 = dS[3 * o], a1 = dS[3 * o + 1], a2 = dS[3 * o + 2];
