@@ -45,6 +45,7 @@ def lib():
                                      vp, vp]
         L.o_eig_sym3.argtypes = [vp, vp, vp]
         L.o_point_stress.argtypes = [vp, vp, vp]
+        L.o_body_sdf.argtypes = [C.POINTER(Params), vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -293,3 +294,20 @@ def eig_sym3(a):
     Q = np.zeros(9)
     lib().o_eig_sym3(_ptr(a), _ptr(lam), _ptr(Q))
     return lam, Q.reshape(3, 3)
+
+
+def body_sdf(cfg, x, body_z=None):
+    """Signed distance of the rigid body at points x (n, 3): (phi, n, H, inside)."""
+    p = params_from_cfg(cfg, body_z)
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    k = len(x)
+    phi, nv, H = np.zeros(k), np.zeros((k, 3)), np.zeros((k, 3, 3))
+    ins = np.zeros(k, dtype=bool)
+    f, nn, hh = C.c_double(), np.zeros(3), np.zeros(9)
+    for i in range(k):
+        xi = np.ascontiguousarray(x[i])
+        ins[i] = bool(lib().o_body_sdf(C.byref(p), _ptr(xi), C.cast(C.byref(f), C.c_void_p),
+                                       _ptr(nn), _ptr(hh)))
+        phi[i], nv[i], H[i] = f.value, nn, hh.reshape(3, 3)
+    return phi, nv, H, ins
+

@@ -122,6 +122,10 @@ int o_constitutive(const o_params* prm, double E, double ys, const double* be_n,
                    double* tau /*9*/, double* be_new /*6*/, double* A /*81*/, int* plastic);
 void o_eig_sym3(const double* a /*9*/, double* lam /*3*/, double* Q /*9 col-major eigvecs*/);
 
+/* signed distance of the rigid body (negative inside), outward normal n and
+ * Hessian H (row-major) at x; returns 1 inside (exposed for pins) */
+int o_body_sdf(const o_params* p, const double* x, double* phi, double* n /*3*/, double* H /*9*/);
+
 /* point-wise state at the current increment (for parity of stresses) */
 int o_point_stress(o_model* m, const double* du, double* sigma /*P*9*/);
 

@@ -234,14 +234,13 @@ int o_body_sdf(const o_params* p, const double* x, double* phi, double* n, doubl
       n[2] = -1.0;
     } else {
       *phi = fs;
+      if (axis) return 1; /* the mean normal of the circle of wall points is zero (reading) */
       n[0] = ux;
       n[1] = uy;
-      if (!axis) {
-        H[0] = (1.0 - ux * ux) / rho;
-        H[1] = -ux * uy / rho;
-        H[3] = -ux * uy / rho;
-        H[4] = (1.0 - uy * uy) / rho;
-      }
+      H[0] = (1.0 - ux * ux) / rho;
+      H[1] = -ux * uy / rho;
+      H[3] = -ux * uy / rho;
+      H[4] = (1.0 - uy * uy) / rho;
     }
     return 1;
   }
@@ -253,8 +252,15 @@ int o_body_sdf(const o_params* p, const double* x, double* phi, double* n, doubl
       return 0;
     }
     double ca = cos(p->body_alpha), sa = sin(p->body_alpha), f;
-    if (z <= p->body_z + hc) {
-      *phi = rho * ca - (z - p->body_z) * sa;
+    /* inside, the nearest boundary point is on the flank below the rim, or
+     * on the shaft wall above it; just above the rim near the axis the flank
+     * is the nearer of the two.  phi_f: signed distance to the flank's line,
+     * whose foot (moved along the flank normal) must lie below the rim. */
+    double phi_f = rho * ca - (z - p->body_z) * sa;
+    double zfoot = (z - p->body_z) + phi_f * sa;
+    int flank = z <= p->body_z + hc || (phi_f > rho - p->body_r && zfoot <= hc);
+    if (flank) {
+      *phi = phi_f;
       if (axis) {
         /* on the axis the closest points form a circle: take the mean of their
          * normals, (0, 0, -sin alpha), and no curvature term (reading) */
@@ -267,6 +273,7 @@ int o_body_sdf(const o_params* p, const double* x, double* phi, double* n, doubl
       f = ca;
     } else {
       *phi = rho - p->body_r;
+      if (axis) return 1; /* the mean normal of the circle of wall points is zero (reading) */
       n[0] = ux;
       n[1] = uy;
       f = 1.0;

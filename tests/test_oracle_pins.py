@@ -714,3 +714,226 @@ def test_contact_column_stress_within_one_percent_at_high_penalty():
     assert rel.max() < 0.01
     # uniform through the body
     assert np.std(sig[:, 2, 2]) < 0.01 * abs(ex)
+
+
+# ---------------------------------------------------------------- rigid body geometry (Sec. 2.3, Sec. 5)
+#
+# The rigid bodies are analytic solids: the flat-ended punch {z >= z0, rho <= r}
+# and the cone of half angle alpha with its tip at z0 and a shaft of radius r
+# above the rim (rho <= min((z - z0) tan alpha, r)), rho the distance to the
+# axis.  The pins below sample the solid's boundary densely and take distances
+# by brute force over the samples, so they share nothing with the oracle's
+# closed-form distance, normal and curvature.
+
+def surface_samples(cfg, z0, h, ztop):
+    """Points on the boundary of the solid, no surface point farther than h
+    from a sample (rings of arc step <= h at height / radius steps <= h)."""
+    b = cfg["body"]
+    cx, cy, r = b["cx"], b["cy"], b["r"]
+    pts = []
+
+    def ring(rho, z):
+        if rho <= 0:
+            pts.append(np.array([[cx, cy, z]]))
+            return
+        n = max(8, int(math.ceil(2 * math.pi * rho / h)))
+        t = np.arange(n) * (2 * math.pi / n)
+        pts.append(np.stack([cx + rho * np.cos(t), cy + rho * np.sin(t), np.full(n, z)], 1))
+
+    if b["kind"] == 1:
+        for rho in np.linspace(0, r, int(math.ceil(r / h)) + 1):
+            ring(rho, z0)  # bottom disk
+        zw = z0
+    else:
+        ta = math.tan(b["alpha"])
+        hc = r / ta
+        # lateral cone: slant step <= h
+        ns = int(math.ceil(hc / math.cos(b["alpha"]) / h)) + 1
+        for z in np.linspace(z0, z0 + hc, ns):
+            ring((z - z0) * ta, z)
+        zw = z0 + hc
+    for z in np.linspace(zw, ztop, int(math.ceil((ztop - zw) / h)) + 1):
+        ring(r, z)  # lateral wall / shaft
+    return np.concatenate(pts)
+
+
+def brute_dist(x, S, chunk=256):
+    """Distance from each point of x to the nearest sample of S."""
+    out = np.empty(len(x))
+    for i in range(0, len(x), chunk):
+        d = np.linalg.norm(x[i:i + chunk, None, :] - S[None, :, :], axis=2)
+        out[i:i + chunk] = d.min(1)
+    return out
+
+
+def in_solid(cfg, x, z0):
+    b = cfg["body"]
+    rho = np.hypot(x[:, 0] - b["cx"], x[:, 1] - b["cy"])
+    if b["kind"] == 1:
+        return (x[:, 2] >= z0) & (rho <= b["r"])
+    return (x[:, 2] >= z0) & (rho <= np.minimum((x[:, 2] - z0) * math.tan(b["alpha"]), b["r"]))
+
+
+def cone_cfg(**over):
+    """A cone large against the cells (1/16), so that its tip, flank, rim and
+    shaft all meet the refinement."""
+    c = inputs.workload("punch", depth_min=1, depth_max=4, dx_region=0.1,
+                        points=dict(spacing=0.125, jitter=0.01, seed=3))
+    c["body"] = dict(kind=2, cx=0.47, cy=0.52, z0=0.46, r=0.15, alpha=math.radians(35.0),
+                     dz=-0.002)
+    c.update(over)
+    return c
+
+
+@pytest.mark.parametrize("kind", ["punch", "cone"])
+def test_refinement_steps_1_and_2_brute_force(kind):
+    # Sec. 5: a leaf is refined while it meets the solid (Step 1) or one of its
+    # vertices lies within dx_region of it (Step 2), down to depth_max.  So
+    # (a) no leaf coarser than depth_max has a vertex within dx_region of the
+    # solid or a piece of the solid's boundary inside it, and (b) the parent of
+    # every depth_max leaf met one of the two criteria (the 2:1 balance never
+    # makes depth_max leaves).  Catches a wrong distance (e.g. the punch rim,
+    # the cone flank against its shaft) or a wrong box test.
+    cfg = tiny_cfg() if kind == "punch" else cone_cfg()
+    z0 = cfg["body"]["z0"]
+    m = built(cfg, body_z=z0)
+    lev, anc, s, D = leaf_boxes(m)
+    unit = cfg["L"] / (1 << D)
+    h = 0.1 * unit
+    S = surface_samples(cfg, z0, h, cfg["L"] + 2 * cfg["dx_region"])
+    corners = np.array([[i & 1, (i >> 1) & 1, (i >> 2) & 1] for i in range(8)])
+    dxr = cfg["dx_region"]
+    coarse = np.nonzero(lev < D)[0]
+    fine = np.nonzero(lev == D)[0]
+    assert len(coarse) and len(fine)
+    # (a)
+    V = ((anc[coarse, None, :] + corners[None] * s[coarse, None, None]) * unit).reshape(-1, 3)
+    dv = brute_dist(V, S).reshape(-1, 8)
+    assert np.all(dv > dxr), "a coarse leaf has a vertex within dx_region"
+    assert not np.any(in_solid(cfg, V, z0))
+    lo, hi = anc[coarse] * unit, (anc[coarse] + s[coarse, None]) * unit
+    for k in range(len(coarse)):
+        inside = np.all((S > lo[k]) & (S < hi[k]), axis=1)
+        assert not inside.any(), "the solid's boundary crosses a coarse leaf"
+    # (b)
+    ps = 2 * s[fine]
+    pa = (anc[fine] // ps[:, None]) * ps[:, None]
+    PV = ((pa[:, None, :] + corners[None] * ps[:, None, None]) * unit).reshape(-1, 3)
+    dp = brute_dist(PV, S).reshape(-1, 8).min(1)
+    plo, phi_ = pa * unit - h, (pa + ps[:, None]) * unit + h
+    for k in range(len(fine)):
+        if dp[k] <= dxr + h:
+            continue
+        assert np.any(np.all((S >= plo[k]) & (S <= phi_[k]), axis=1)), k
+
+
+def sdf_cases(cfg, z0, rng, n):
+    """Seeded points in a box around the body's lower part."""
+    b = cfg["body"]
+    span = 2.5 * b["r"]
+    x = np.stack([b["cx"] + rng.uniform(-span, span, n), b["cy"] + rng.uniform(-span, span, n),
+                  z0 + rng.uniform(-0.5 * span, 2.0 * span, n)], 1)
+    return x
+
+
+@pytest.mark.parametrize("kind", ["punch", "cone"])
+def test_body_signed_distance_brute_force(kind):
+    # |phi| is the distance to the solid's boundary, negative inside (Sec. 2.3
+    # gap function); the brute-force distance over the samples exceeds the
+    # true one by at most the sampling step h
+    cfg = tiny_cfg() if kind == "punch" else cone_cfg()
+    z0 = cfg["body"]["z0"]
+    rng = np.random.default_rng(11)
+    x = sdf_cases(cfg, z0, rng, 800)
+    h = 2e-3
+    S = surface_samples(cfg, z0, h, z0 + 1.0)
+    phi, n, H, ins = oracle.body_sdf(cfg, x, body_z=z0)
+    sol = in_solid(cfg, x, z0)
+    # strictly inside / outside points only (the boundary itself is measure zero)
+    assert np.array_equal(ins, sol)
+    assert sol.sum() > 40 and (~sol).sum() > 40
+    d = brute_dist(x, S)
+    assert np.all(np.abs(phi) <= d + 1e-12)
+    assert np.all(np.abs(phi) >= d - h)
+    assert np.all(phi[sol] <= 0) and np.all(phi[~sol] >= 0)
+
+
+def smooth_inside_points(cfg, z0, rng, n):
+    """Points inside the solid whose nearest boundary point is unique and on a
+    smooth piece (flank or shaft of the cone, wall or bottom of the punch),
+    away from the axis, the rim, the tip and the medial surfaces."""
+    b = cfg["body"]
+    r = b["r"]
+    out = []
+    while len(out) < n:
+        th = rng.uniform(0, 2 * math.pi)
+        if b["kind"] == 2:
+            ta = math.tan(b["alpha"])
+            hc = r / ta
+            if rng.uniform() < 0.6:  # near the flank, below the rim
+                z = z0 + rng.uniform(0.35, 0.8) * hc
+                rho = (z - z0) * ta - rng.uniform(0.02, 0.15) * (z - z0) * ta
+            else:  # near the shaft, above the rim
+                z = z0 + hc + rng.uniform(0.3, 1.0) * r
+                rho = r * rng.uniform(0.7, 0.95)
+        else:
+            if rng.uniform() < 0.5:  # near the bottom
+                z = z0 + rng.uniform(0.05, 0.3) * r
+                rho = r * rng.uniform(0.2, 0.6)
+            else:  # near the wall
+                z = z0 + rng.uniform(0.7, 2.0) * r
+                rho = r * rng.uniform(0.75, 0.95)
+        out.append([b["cx"] + rho * math.cos(th), b["cy"] + rho * math.sin(th), z])
+    return np.array(out)
+
+
+@pytest.mark.parametrize("kind", ["punch", "cone"])
+def test_body_normal_and_hessian_match_finite_differences(kind):
+    # n = grad phi and H = grad n (the contact stiffness eps_N (n n^T + phi H)
+    # of Sec. 2.3 needs both); central differences of the oracle's own phi and
+    # n at points with a unique, smooth nearest boundary point.  Catches a sign
+    # error in the normal or a wrong curvature factor (cos alpha on the flank).
+    cfg = tiny_cfg() if kind == "punch" else cone_cfg()
+    z0 = cfg["body"]["z0"]
+    rng = np.random.default_rng(5)
+    x = smooth_inside_points(cfg, z0, rng, 60)
+    phi, n, H, ins = oracle.body_sdf(cfg, x, body_z=z0)
+    assert ins.all() and np.all(phi < 0)
+    e = 1e-6
+    for d in range(3):
+        dx = np.zeros(3)
+        dx[d] = e
+        pp, npl, _, _ = oracle.body_sdf(cfg, x + dx, body_z=z0)
+        pm, nmi, _, _ = oracle.body_sdf(cfg, x - dx, body_z=z0)
+        assert np.allclose((pp - pm) / (2 * e), n[:, d], atol=1e-7)
+        assert np.allclose((npl - nmi) / (2 * e), H[:, :, d], atol=1e-5 * np.abs(H).max())
+    assert np.allclose(np.linalg.norm(n, axis=1), 1.0)
+    assert np.abs(H).max() > 0
+
+
+def test_global_tangent_matches_finite_difference_with_cone_contact():
+    # the FD pin of the global tangent with the cone in contact: corners on
+    # the flank and near the tip, so that eps_N (n n^T + phi H) enters
+    cfg = cone_cfg()
+    cfg["model"] = 0
+    z0 = cfg["body"]["z0"]
+    m = built(cfg, body_z=z0 - 0.06)
+    c = m.counts()
+    n3 = 3 * c["ndof"]
+    rng = np.random.default_rng(7)
+    du = 1e-3 * rng.normal(size=n3)
+    out = m.assemble(du)
+    assert np.linalg.norm(out["reaction"]) > 0  # contact active
+    rp, col = m.pattern()
+    K = out["K"]
+    h = 1e-7
+    for _ in range(3):
+        v = rng.normal(size=n3)
+        Rp = m.assemble(du + h * v, tangent=False)["R"]
+        Rm = m.assemble(du - h * v, tangent=False)["R"]
+        fd = (Rp - Rm) / (2 * h)
+        Kv = np.zeros(n3)
+        for i in range(c["ndof"]):
+            for s_ in range(rp[i], rp[i + 1]):
+                Kv[3 * i:3 * i + 3] += K[s_] @ v[3 * col[s_]:3 * col[s_] + 3]
+        assert np.linalg.norm(Kv - fd) <= 1e-6 * np.linalg.norm(fd)
