@@ -183,10 +183,13 @@ __device__ inline double det3(const double* a) {
          a[2] * (a[3] * a[7] - a[4] * a[6]);
 }
 
+// also M = V0 tau dF^-T (row-major, 12 per point, the last 3 unused), so that
+// the internal force of support k is M grad S_k (k_residual_rows)
 template <bool TANGENT, class TA>
 __global__ void k_constitutive(int P, Law L, const double* __restrict__ E, const double* __restrict__ ys,
                                const double* __restrict__ be, const double* __restrict__ dF,
-                               double* tau, double* dFinv, TA* Aalg, double* lawst, int* err) {
+                               const double* __restrict__ V0, double* tau, double* dFinv,
+                               double* Mf, TA* Aalg, double* lawst, int* err) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= P) return;
   double f[9];
@@ -217,6 +220,18 @@ __global__ void k_constitutive(int P, Law L, const double* __restrict__ E, const
   o[6] = (f[3] * f[7] - f[4] * f[6]) * id;
   o[7] = (f[1] * f[6] - f[0] * f[7]) * id;
   o[8] = (f[0] * f[4] - f[1] * f[3]) * id;
+  // M_il = V0 sum_j tau_ij (dF^-1)_lj
+  double fi[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) fi[e] = o[e];
+  double tm[9] = {t6[0], t6[3], t6[5], t6[3], t6[1], t6[4], t6[5], t6[4], t6[2]};
+  double v0 = V0[w];
+  double* M = Mf + 12 * (size_t)w;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      M[3 * i + l] = v0 * (tm[3 * i] * fi[3 * l] + tm[3 * i + 1] * fi[3 * l + 1] + tm[3 * i + 2] * fi[3 * l + 2]);
 }
 
 // the tangent of the state the last residual evaluation left (same increment):
@@ -260,88 +275,58 @@ __global__ void k_gx(int P, const int* __restrict__ nsup, const double* __restri
   }
 }
 
-// ------------------------------------------------------------------ internal force
+// ------------------------------------------------------------------ internal force and residual
 
-// f_int,v = V0 tau grad_x S_v with grad_x S = grad S . dF^{-1}; optionally store
-// grad_x S for the tangent gather
-template <class TG, bool STORE>
-__global__ void k_force(int P, const int* __restrict__ nsup, const int* __restrict__ sidx,
-                        const double* __restrict__ dS, const double* __restrict__ dFinv,
-                        const double* __restrict__ tau, const double* __restrict__ V0, double* fint,
-                        TG* gx) {
-  int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w >= P) return;
-  const double* fi = dFinv + 9 * (size_t)w;
-  double t0 = tau[6 * (size_t)w], t1 = tau[6 * (size_t)w + 1], t2 = tau[6 * (size_t)w + 2];
-  double t3 = tau[6 * (size_t)w + 3], t4 = tau[6 * (size_t)w + 4], t5 = tau[6 * (size_t)w + 5];
-  double v0 = V0[w];
-  int n = nsup[w];
-  if (!STORE) {
-    // residual only: f_k = M dS_k with M = V0 tau F^-T formed once per point,
-    // one entry per lane (9 FP64 multiply-adds per support instead of 21; the
-    // FP64 pipe bounds this kernel, and an FP64 warp instruction costs the
-    // same whatever the number of active lanes)
-    int lr = lane < 9 ? lane / 3 : 0, lc = lane < 9 ? lane % 3 : 0;
-    // row lr of tau (symmetric; stored xx yy zz xy yz xz)
-    double r0 = lr == 0 ? t0 : (lr == 1 ? t3 : t5);
-    double r1 = lr == 0 ? t3 : (lr == 1 ? t1 : t4);
-    double r2 = lr == 0 ? t5 : (lr == 1 ? t4 : t2);
-    double mv = v0 * (r0 * fi[3 * lc] + r1 * fi[3 * lc + 1] + r2 * fi[3 * lc + 2]);
-    double M[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) M[e] = __shfl_sync(0xffffffffu, mv, e);
-    for (int k = lane; k < n; k += 32) {
-      size_t o = (size_t)w * MAXS + k;
-      double a0 = dS[3 * o], a1 = dS[3 * o + 1], a2 = dS[3 * o + 2];
-      int j = sidx[o];
-      atomicAdd(fint + 3 * (size_t)j, M[0] * a0 + M[1] * a1 + M[2] * a2);
-      atomicAdd(fint + 3 * (size_t)j + 1, M[3] * a0 + M[4] * a1 + M[5] * a2);
-      atomicAdd(fint + 3 * (size_t)j + 2, M[6] * a0 + M[7] * a1 + M[8] * a2);
-    }
-    return;
-  }
-  for (int k = lane; k < n; k += 32) {
-    size_t o = (size_t)w * MAXS + k;
-    double a0 = dS[3 * o], a1 = dS[3 * o + 1], a2 = dS[3 * o + 2];
-    double g0 = a0 * fi[0] + a1 * fi[3] + a2 * fi[6];
-    double g1 = a0 * fi[1] + a1 * fi[4] + a2 * fi[7];
-    double g2 = a0 * fi[2] + a1 * fi[5] + a2 * fi[8];
-    int j = sidx[o];
-    atomicAdd(fint + 3 * (size_t)j, v0 * (t0 * g0 + t3 * g1 + t5 * g2));
-    atomicAdd(fint + 3 * (size_t)j + 1, v0 * (t3 * g0 + t1 * g1 + t4 * g2));
-    atomicAdd(fint + 3 * (size_t)j + 2, v0 * (t5 * g0 + t4 * g1 + t2 * g2));
-    if (STORE) {
-      gx[3 * o] = (TG)g0;
-      gx[3 * o + 1] = (TG)g1;
-      gx[3 * o + 2] = (TG)g2;
-    }
-  }
-}
-
-// R = f_int - load f_ext + K_G du   (one warp per row)
-__global__ void k_residual_rows(int nd, double load, const int* __restrict__ rp,
+// R = f_int - load f_ext + K_G du, one warp per row r, where f_int,r is the sum
+// over the point sources (p, k) of the row (the pattern's sorted source keys)
+// of M_p grad S_pk, M_p = V0 tau dF^-T from k_constitutive.  A fixed-order
+// gather: every lane sums a fixed set of sources in key order and the lanes
+// are combined by a fixed shuffle tree, so f_int and R are the same bit for
+// bit on every run (no floating-point atomics).
+__global__ void k_residual_rows(int nd, int P, double load, const long long* __restrict__ sptr,
+                                const uint64_t* __restrict__ skeys, const double* __restrict__ M,
+                                const double* __restrict__ dS, const int* __restrict__ rp,
                                 const int* __restrict__ col, const double* __restrict__ kg,
-                                const double* __restrict__ du, const double* __restrict__ fint,
-                                const double* __restrict__ fext, double* R) {
+                                const double* __restrict__ du, const double* __restrict__ fext,
+                                double* fint, double* R) {
   int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (r >= nd) return;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+  long long q1 = sptr[r + 1];
+  for (long long q = sptr[r] + lane; q < q1; q += 32) {
+    uint32_t sid = (uint32_t)skeys[q];
+    int w = (int)(sid >> 6), k = (int)(sid & 63);
+    if (w >= P) continue;  // ghost-face source
+    const double2* m = reinterpret_cast<const double2*>(M + 12 * (size_t)w);
+    double2 m01 = m[0], m23 = m[1], m45 = m[2], m67 = m[3], m8x = m[4];
+    const double* a = dS + 3 * ((size_t)w * MAXS + k);
+    double a0 = a[0], a1 = a[1], a2 = a[2];
+    f0 += m01.x * a0 + m01.y * a1 + m23.x * a2;
+    f1 += m23.y * a0 + m45.x * a1 + m45.y * a2;
+    f2 += m67.x * a0 + m67.y * a1 + m8x.x * a2;
+  }
+  double g0 = 0.0, g1 = 0.0, g2 = 0.0;
   for (int s = rp[r] + lane; s < rp[r + 1]; s += 32) {
     double k = kg[s];
     if (k != 0.0) {
       int c = col[s];
-      a0 += k * du[3 * (size_t)c];
-      a1 += k * du[3 * (size_t)c + 1];
-      a2 += k * du[3 * (size_t)c + 2];
+      g0 += k * du[3 * (size_t)c];
+      g1 += k * du[3 * (size_t)c + 1];
+      g2 += k * du[3 * (size_t)c + 2];
     }
   }
-  a0 = warp_sum(a0);
-  a1 = warp_sum(a1);
-  a2 = warp_sum(a2);
+  f0 = warp_sum(f0);
+  f1 = warp_sum(f1);
+  f2 = warp_sum(f2);
+  g0 = warp_sum(g0);
+  g1 = warp_sum(g1);
+  g2 = warp_sum(g2);
   if (lane < 3) {
-    double g = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+    double f = lane == 0 ? f0 : (lane == 1 ? f1 : f2);
+    double g = lane == 0 ? g0 : (lane == 1 ? g1 : g2);
     size_t i = 3 * (size_t)r + lane;
-    R[i] = fint[i] - load * fext[i] + g;
+    fint[i] = f;
+    R[i] = f - load * fext[i] + g;
   }
 }
 
@@ -542,69 +527,119 @@ __device__ inline int find_slot(const int* __restrict__ rp, const int* __restric
   return -1;
 }
 
-// one thread per candidate domain corner: gap against the body at the moved
-// corner, force -eps_N phi n spread by the background basis, stiffness
-// eps_N (n n^T + phi H) phi_a phi_b (Dirichlet entries skipped)
-template <class T, bool TANGENT, bool RES = true>
-__global__ void k_contact(int nc8, const int* __restrict__ cand, const int* __restrict__ cb_n,
-                          const int* __restrict__ cb_idx, const double* __restrict__ cb_phi,
-                          const double* __restrict__ cb_y0, const double* __restrict__ pE,
-                          const double* __restrict__ pV0, mpm_rigid body, double L, double pf,
-                          const double* __restrict__ du, double* R, double* fc, double* reac,
-                          const int* __restrict__ rp, const int* __restrict__ col, Sliced S,
-                          const int* __restrict__ mask, T* K) {
+// one thread per candidate domain corner: the gap against the body at the moved
+// corner; in contact the force on the material f = -eps_N phi n and the
+// stiffness k_c = eps_N (n n^T + phi H) are stored for the row gather below
+// (zeros and on = 0 otherwise), and with `reac` the force on the body, -sum f,
+// is summed in a fixed order (every thread of the grid takes part)
+__global__ void k_contact_corner(int nc8, const int* __restrict__ cand, const int* __restrict__ cb_n,
+                                 const int* __restrict__ cb_idx, const double* __restrict__ cb_phi,
+                                 const double* __restrict__ cb_y0, const double* __restrict__ pE,
+                                 const double* __restrict__ pV0, mpm_rigid body, double L, double pf,
+                                 const double* __restrict__ du, double* cf, double* ck, int* con,
+                                 double* reac, GridRed gr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nc8) return;
-  int w = cand[i >> 3], n = cb_n[i];
-  const int* ids = cb_idx + (size_t)i * MAXCB;
-  const double* ph = cb_phi + (size_t)i * MAXCB;
-  double y[3] = {cb_y0[3 * (size_t)i], cb_y0[3 * (size_t)i + 1], cb_y0[3 * (size_t)i + 2]};
-  for (int e = 0; e < n; ++e)
-    for (int d = 0; d < 3; ++d) y[d] += ph[e] * du[3 * (size_t)ids[e] + d];
-  double phi, nv[3], H[9];
-  if (!body_sdf(body, L, y, &phi, nv, H) || !(phi < 0.0)) return;
-  double epsN = pf * pE[w] * pow(pV0[w], 2.0 / 3.0);
-  double f[3] = {-epsN * phi * nv[0], -epsN * phi * nv[1], -epsN * phi * nv[2]};
-  if (RES) {
-    for (int d = 0; d < 3; ++d) atomicAdd(reac + d, -f[d]);
+  double f[3] = {0.0, 0.0, 0.0};
+  if (i < nc8) {
+    int w = cand[i >> 3], n = cb_n[i];
+    const int* ids = cb_idx + (size_t)i * MAXCB;
+    const double* ph = cb_phi + (size_t)i * MAXCB;
+    double y[3] = {cb_y0[3 * (size_t)i], cb_y0[3 * (size_t)i + 1], cb_y0[3 * (size_t)i + 2]};
     for (int e = 0; e < n; ++e)
-      for (int d = 0; d < 3; ++d) {
-        atomicAdd(R + 3 * (size_t)ids[e] + d, -ph[e] * f[d]);
-        atomicAdd(fc + 3 * (size_t)ids[e] + d, ph[e] * f[d]);
-      }
+      for (int d = 0; d < 3; ++d) y[d] += ph[e] * du[3 * (size_t)ids[e] + d];
+    double phi, nv[3], H[9];
+    bool on = body_sdf(body, L, y, &phi, nv, H) && phi < 0.0;
+    double kc[9];
+    for (int e = 0; e < 9; ++e) kc[e] = 0.0;
+    if (on) {
+      double epsN = pf * pE[w] * pow(pV0[w], 2.0 / 3.0);
+      for (int d = 0; d < 3; ++d) f[d] = -epsN * phi * nv[d];
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) kc[3 * a + b] = epsN * (nv[a] * nv[b] + phi * H[3 * a + b]);
+    }
+    for (int d = 0; d < 3; ++d) cf[3 * (size_t)i + d] = f[d];
+    for (int e = 0; e < 9; ++e) ck[9 * (size_t)i + e] = kc[e];
+    con[i] = on ? 1 : 0;
+  }
+  if (reac) {
+    double v[3] = {-f[0], -f[1], -f[2]};
+    double* o[3] = {reac, reac + 1, reac + 2};
+    grid_sum<3>(v, o, gr);
+  }
+}
+
+// One warp per row r of the contact list (the rows that the background basis
+// of some candidate corner touches; entries (corner, basis entry) in sorted
+// order).  RES: R_r -= sum of phi_e f and f_c,r += the same sum, lanes strided
+// over the entries and combined by the fixed shuffle tree.  TANGENT: K_{r,b}
+// += phi_e phi_b k_c over the basis entries b of each corner, one corner entry
+// at a time in list order (the lanes of one entry write distinct columns), the
+// Dirichlet components skipped.  No atomics: the same sums on every run.
+template <class T, bool RES, bool TANGENT>
+__global__ void k_contact_rows(int nrow, const int* __restrict__ crow, const int* __restrict__ cptr,
+                               const int* __restrict__ cent, const int* __restrict__ cb_n,
+                               const int* __restrict__ cb_idx, const double* __restrict__ cb_phi,
+                               const double* __restrict__ cf, const double* __restrict__ ck,
+                               const int* __restrict__ con, double* R, double* fc,
+                               const int* __restrict__ rp, const int* __restrict__ col, Sliced S,
+                               const int* __restrict__ mask, T* K) {
+  int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (t >= nrow) return;
+  int r = crow[t], e0 = cptr[t], e1 = cptr[t + 1];
+  if (RES) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int e = e0 + lane; e < e1; e += 32) {
+      int pk = cent[e], i = pk >> 5;
+      double ph = cb_phi[(size_t)i * MAXCB + (pk & 31)];
+      s0 += ph * cf[3 * (size_t)i];
+      s1 += ph * cf[3 * (size_t)i + 1];
+      s2 += ph * cf[3 * (size_t)i + 2];
+    }
+    s0 = warp_sum(s0);
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane < 3) {
+      double v = lane == 0 ? s0 : (lane == 1 ? s1 : s2);
+      R[3 * (size_t)r + lane] -= v;
+      fc[3 * (size_t)r + lane] += v;
+    }
   }
   if (!TANGENT) return;
-  double kc[9];
-  for (int a = 0; a < 3; ++a)
-    for (int b = 0; b < 3; ++b) kc[3 * a + b] = epsN * (nv[a] * nv[b] + phi * H[3 * a + b]);
-  for (int ea = 0; ea < n; ++ea) {
-    int ra = ids[ea];
-    int s0 = rp[ra], ma = mask[ra];
-    int slc = ra >> 5, W = S.w[slc];
-    long long b0 = S.base[slc];
-    for (int eb = 0; eb < n; ++eb) {
-      int cb = ids[eb];
-      int sl = find_slot(rp, col, ra, cb);
+  int s0r = rp[r], ma = mask[r];
+  int slc = r >> 5, W = S.w[slc];
+  long long b0 = S.base[slc];
+  for (int e = e0; e < e1; ++e) {
+    int pk = cent[e], i = pk >> 5;
+    if (!con[i]) continue;
+    const double* kc = ck + 9 * (size_t)i;
+    double pa = cb_phi[(size_t)i * MAXCB + (pk & 31)];
+    int n = cb_n[i];
+    for (int eb = lane; eb < n; eb += 32) {
+      int cb = cb_idx[(size_t)i * MAXCB + eb];
+      int sl = find_slot(rp, col, r, cb);
       if (sl < 0) continue;
-      long long slot = sliced_slot(b0, ra, sl - s0);
+      long long slot = sliced_slot(b0, r, sl - s0r);
       int mb = mask[cb];
-      double pp = ph[ea] * ph[eb];
+      double pp = pa * cb_phi[(size_t)i * MAXCB + eb];
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
           if (((ma >> a) & 1) || ((mb >> b) & 1)) continue;
-          atomicAdd(K + sliced_entry(b0, W, slot, 3 * a + b), (T)(pp * kc[3 * a + b]));
+          T* kv = K + sliced_entry(b0, W, slot, 3 * a + b);
+          *kv += (T)(pp * kc[3 * a + b]);
         }
     }
+    __syncwarp();
   }
 }
 
 // ------------------------------------------------------------------ norms
 
 // slots: 0 ||R_free||^2, 1 ||f_int||^2, 2 ||load f_ext + f_c||^2
+// (fixed-order grid sums: the norms, and so Newton's convergence test and
+// line search, are the same on every run)
 __global__ void k_norms(int n3, const double* __restrict__ R, const double* __restrict__ fint,
                         const double* __restrict__ fext, const double* __restrict__ fc, double load,
-                        const int* __restrict__ mask, double* out) {
-  __shared__ double sh[32];
+                        const int* __restrict__ mask, double* out, GridRed gr) {
   double a = 0.0, b = 0.0, c = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
     if (!((mask[i / 3] >> (i % 3)) & 1)) a += R[i] * R[i];
@@ -614,14 +649,9 @@ __global__ void k_norms(int n3, const double* __restrict__ R, const double* __re
       c += e * e;
     }
   }
-  a = block_sum(a, sh);
-  b = block_sum(b, sh);
-  c = block_sum(c, sh);
-  if (threadIdx.x == 0) {
-    atomicAdd(out, a);
-    atomicAdd(out + 1, b);
-    atomicAdd(out + 2, c);
-  }
+  double v[3] = {a, b, c};
+  double* o[3] = {out, out + 1, out + 2};
+  grid_sum<3>(v, o, gr);
 }
 
 }  // namespace
@@ -631,11 +661,37 @@ double norm_free(mpm_ctx* c, const mpm_mesh* m, const double* R) {
   double* slot = c->d_red + 16;
   MPM_CUDA(cudaMemsetAsync(slot, 0, 3 * sizeof(double), c->stream));
   MPM_LAUNCH(k_norms<<<4 * 152, 256, 0, c->stream>>>(3 * m->ndof, R, nullptr, nullptr, nullptr, 0.0,
-                                          ptr<int>(m->dof_mask), slot));
+                                          ptr<int>(m->dof_mask), slot, grid_red(c, 3, 4 * 152)));
   MPM_CUDA(cudaMemcpyAsync(c->h_red + 16, slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   MPM_CUDA(cudaStreamSynchronize(c->stream));
   return sqrt(c->h_red[16]);
 }
+
+namespace {
+
+// the penalty contact of one assembly: per-corner forces and stiffness (and
+// the reaction when `reac` is given), then the row gather
+template <class T, bool RES, bool TANGENT>
+void contact_terms(mpm_ctx* c, mpm_mesh* m, const mpm_material& mat, const mpm_rigid& body,
+                   const double* du, double* R, double* fc, double* reac, T* K) {
+  cudaStream_t st = c->stream;
+  int n8 = 8 * m->ncand;
+  double* cf = grow<double>(c, m->cc_f, 3 * (size_t)n8);
+  double* ck = grow<double>(c, m->cc_k, 9 * (size_t)n8);
+  int* con = grow<int>(c, m->cc_on, n8);
+  MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact_corner<<<grid_for(n8, 128), 128, 0, st>>>(
+      n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
+      ptr<double>(m->cb_y0), ptr<double>(m->pE), ptr<double>(m->pV0), body, m->g.L, mat.pf, du, cf, ck,
+      con, reac, grid_red(c, 3, grid_for(n8, 128))));
+  if (!m->nct) return;
+  Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+  MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact_rows<T, RES, TANGENT><<<grid_for(m->nct, 4), 128, 0, st>>>(
+      m->nct, ptr<int>(m->ct_row), ptr<int>(m->ct_ptr), ptr<int>(m->ct_ent), ptr<int>(m->cb_n),
+      ptr<int>(m->cb_idx), ptr<double>(m->cb_phi), cf, ck, con, R, fc, ptr<int>(m->row_ptr),
+      ptr<int>(m->col), S, ptr<int>(m->dof_mask), K));
+}
+
+}  // namespace
 
 void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm_rigid& body,
               const double* du, double load, int precision, double* R, void* K, AsmOut* out,
@@ -648,6 +704,7 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
   double* dFinv = grow<double>(c, m->dFinv, 9 * (size_t)P);
   double* tau = grow<double>(c, m->tau, 6 * (size_t)P);
   double* lawst = grow<double>(c, m->lawst, 22 * (size_t)P);
+  double* Mf = grow<double>(c, m->Mf, 12 * (size_t)P);
   const int* nsup = ptr<int>(m->nsup);
   const int* sidx = ptr<int>(m->sidx);
   const double* dS = ptr<double>(m->dS);
@@ -662,7 +719,9 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
   double* fint = grow<double>(c, c->v[0], 3 * (size_t)nd);
   double* fc = grow<double>(c, c->v[1], 3 * (size_t)nd);
   bool contact = m->ncand && mat.contact_on && body.kind != 0;
-  int n8 = 8 * m->ncand;
+  // grid-sum partials for every reduction below, sized once; a clean ticket
+  grid_red(c, 4, std::max(4096, grid_for(8LL * m->ncand, 128)));
+  MPM_CUDA(cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), st));
   if (K && reuse) {
     // Newton's tangent at the increment of the last residual evaluation: its
     // dF, dF^-1, tau and spectral state are still in place, R is complete
@@ -677,29 +736,26 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
     MPM_LAUNCH_P(MPM_PROF_KINEMATICS, k_kinematics<<<grid_for(8LL * P, 256), 256, 0, st>>>(P, nsup, sidx, dS, du, dF));
     if (!K)
       MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<false, double><<<grid_for(P, 128), 128, 0, st>>>(
-          P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv, nullptr,
-          lawst, c->d_err));
+          P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, V0, tau, dFinv, Mf,
+          nullptr, lawst, c->d_err));
     else if (mixed)
       MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<true, float><<<grid_for(P, 128), 128, 0, st>>>(
-          P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv,
+          P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, V0, tau, dFinv, Mf,
           (float*)Aalg, nullptr, c->d_err));
     else
       MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_constitutive<true, double><<<grid_for(P, 128), 128, 0, st>>>(
-          P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, tau, dFinv,
+          P, L, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe), dF, V0, tau, dFinv, Mf,
           (double*)Aalg, nullptr, c->d_err));
-    MPM_CUDA(cudaMemsetAsync(fint, 0, sizeof(double) * 3 * nd, st));
     MPM_CUDA(cudaMemsetAsync(fc, 0, sizeof(double) * 3 * nd, st));
-    if (!K)
-      MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<double, false><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
-                                                             nullptr));
-    else if (mixed)
-      MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<float, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
-                                                           (float*)gx));
-    else
-      MPM_LAUNCH_P(MPM_PROF_FORCE, k_force<double, true><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, dS, dFinv, tau, V0, fint,
-                                                            (double*)gx));
-    MPM_LAUNCH_P(MPM_PROF_RESIDUAL, k_residual_rows<<<grid_for(nd, 8), 256, 0, st>>>(nd, load, rp, col, ptr<double>(m->kg), du, fint,
-                                                     ptr<double>(m->fext), R));
+    MPM_LAUNCH_P(MPM_PROF_RESIDUAL, k_residual_rows<<<grid_for(nd, 8), 256, 0, st>>>(
+        nd, P, load, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), Mf, dS, rp, col,
+        ptr<double>(m->kg), du, ptr<double>(m->fext), fint, R));
+    if (K) {
+      if (mixed)
+        MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<float><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, (float*)gx));
+      else
+        MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<double><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, (double*)gx));
+    }
   }
   if (K) {
     // two passes: rows up to 128 blocks (the 5^3 interior stencil and below)
@@ -742,41 +798,26 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
     // contact stiffness only: its forces are already in R
     if (contact) {
       if (mixed)
-        MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<float, true, false><<<grid_for(n8, 128), 128, 0, st>>>(
-            n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
-            ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
-            col, S, ptr<int>(m->dof_mask), (float*)K));
+        contact_terms<float, false, true>(c, m, mat, body, du, R, fc, nullptr, (float*)K);
       else
-        MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<double, true, false><<<grid_for(n8, 128), 128, 0, st>>>(
-            n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
-            ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
-            col, S, ptr<int>(m->dof_mask), (double*)K));
+        contact_terms<double, false, true>(c, m, mat, body, du, R, fc, nullptr, (double*)K);
     }
     return;
   }
   MPM_CUDA(cudaMemsetAsync(reac, 0, 3 * sizeof(double), st));
   if (contact) {
     if (!K)
-      MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<double, false><<<grid_for(n8, 128), 128, 0, st>>>(
-          n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
-          ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
-          col, S, ptr<int>(m->dof_mask), (double*)nullptr));
+      contact_terms<double, true, false>(c, m, mat, body, du, R, fc, reac, (double*)nullptr);
     else if (mixed)
-      MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<float, true><<<grid_for(n8, 128), 128, 0, st>>>(
-          n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
-          ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
-          col, S, ptr<int>(m->dof_mask), (float*)K));
+      contact_terms<float, true, true>(c, m, mat, body, du, R, fc, reac, (float*)K);
     else
-      MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact<double, true><<<grid_for(n8, 128), 128, 0, st>>>(
-          n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
-          ptr<double>(m->cb_y0), ptr<double>(m->pE), V0, body, m->g.L, mat.pf, du, R, fc, reac, rp,
-          col, S, ptr<int>(m->dof_mask), (double*)K));
+      contact_terms<double, true, true>(c, m, mat, body, du, R, fc, reac, (double*)K);
   }
   if (want_norms) {
     double* slot = c->d_red + 16;
     MPM_CUDA(cudaMemsetAsync(slot, 0, 3 * sizeof(double), st));
     MPM_LAUNCH(k_norms<<<4 * 152, 256, 0, st>>>(3 * nd, R, fint, ptr<double>(m->fext), fc, load,
-                                     ptr<int>(m->dof_mask), slot));
+                                     ptr<int>(m->dof_mask), slot, grid_red(c, 3, 4 * 152)));
     MPM_CUDA(cudaMemcpyAsync(c->h_red + 16, slot, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
     out->fint_norm = sqrt(c->h_red[17]);

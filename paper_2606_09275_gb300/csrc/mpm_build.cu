@@ -915,17 +915,18 @@ __device__ double leaf_dphi(int K, int s, const double* xi, int axis, int j,
   return r;
 }
 
-// Eq. (ghost): 2x2 Gauss points on the smaller face, mapped into the larger leaf;
-// k_G(i,j) += w (h_F beta_F / kappa) J_i J_j with J the normal-derivative jump
-__global__ void k_ghost_matrix(int nf, Geo g, double kappa, const int* __restrict__ face,
-                               const uint64_t* __restrict__ lkey, const int* __restrict__ llev,
-                               const double* __restrict__ betaK, const int* __restrict__ gdof,
-                               const int* __restrict__ gn, const int* __restrict__ corner,
-                               const int* __restrict__ cptr, const int* __restrict__ cidx,
-                               const double* __restrict__ cw, const int* __restrict__ node_dof,
-                               const int* __restrict__ row_ptr, const int* __restrict__ col,
-                               double* kg) {
-  __shared__ double J[4][MAXG];
+// Eq. (ghost): 2x2 Gauss points on the smaller face, mapped into the larger
+// leaf; k_G(i,j) = sum over faces and Gauss points of w (h_F beta_F / kappa)
+// J_i J_j with J the normal-derivative jump.  One warp per face stores the
+// face's coefficient w h_F beta_F / kappa and its jumps J (4 x MAXG); the
+// rows are summed by k_ghost_rows.
+__global__ void k_ghost_jumps(int nf, Geo g, double kappa, const int* __restrict__ face,
+                              const uint64_t* __restrict__ lkey, const int* __restrict__ llev,
+                              const double* __restrict__ betaK, const int* __restrict__ gdof,
+                              const int* __restrict__ gn, const int* __restrict__ corner,
+                              const int* __restrict__ cptr, const int* __restrict__ cidx,
+                              const double* __restrict__ cw, const int* __restrict__ node_dof,
+                              double* gJ, double* gcoef) {
   int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int f = blockIdx.x * 4 + wi;
   if (f >= nf) return;
@@ -937,7 +938,7 @@ __global__ void k_ghost_matrix(int nf, Geo g, double kappa, const int* __restric
   double hF = (double)(sK > sN ? sK : sN) * g.unit;
   double bF = betaK[K] > betaK[Nb] ? betaK[K] : betaK[Nb];
   double area = ((double)sK * g.unit) * ((double)sK * g.unit);
-  double coef = hF * bF / kappa * area / 4.0;
+  if (lane == 0) gcoef[f] = hF * bF / kappa * area / 4.0;
   const double gq = 0.5 / sqrt(3.0);
   int t1 = (axis + 1) % 3, t2 = (axis + 2) % 3;
   int n = gn[f];
@@ -956,16 +957,38 @@ __global__ void k_ghost_matrix(int nf, Geo g, double kappa, const int* __restric
       int j = ids[e];
       double jk = leaf_dphi(K, sK, xiK, axis, j, corner, cptr, cidx, cw, node_dof);
       double jn = leaf_dphi(Nb, sN, xiN, axis, j, corner, cptr, cidx, cw, node_dof);
-      J[wi][e] = (double)sign * (jk - jn) * g.scale;
+      gJ[((size_t)f * 4 + gp) * MAXG + e] = (double)sign * (jk - jn) * g.scale;
     }
-    __syncwarp();
-    for (int a = lane; a < n; a += 32)
-      for (int b = 0; b < n; ++b) {
-        double v = coef * J[wi][a] * J[wi][b];
-        if (v == 0.0) continue;
-        int sl = find_slot(row_ptr, col, ids[a], ids[b]);
-        if (sl >= 0) atomicAdd(kg + sl, v);
-      }
+  }
+}
+
+// k_G row r: one warp; the row's ghost-face sources (face f, local index a of
+// r in the face's dofs) in key order, and for each the face's dofs b over the
+// lanes: k_G(r, b) += coef_f sum over Gauss points of J_a J_b.  The lanes of
+// one source write distinct columns and the sources follow one another, so
+// every entry is summed in a fixed order (no atomics).
+__global__ void k_ghost_rows(int nd, int P, const long long* __restrict__ sptr,
+                             const uint64_t* __restrict__ skeys, const int* __restrict__ gdof,
+                             const int* __restrict__ gn, const double* __restrict__ gJ,
+                             const double* __restrict__ gcoef, const int* __restrict__ row_ptr,
+                             const int* __restrict__ col, double* kg) {
+  int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= nd) return;
+  for (long long q = sptr[r]; q < sptr[r + 1]; ++q) {
+    uint32_t sid = (uint32_t)skeys[q];
+    int f = (int)(sid >> 6) - P, a = (int)(sid & 63);
+    if (f < 0) continue;  // a point source
+    double cf = gcoef[f];
+    const double* J = gJ + (size_t)f * 4 * MAXG;
+    double ja[4] = {J[a], J[MAXG + a], J[2 * MAXG + a], J[3 * MAXG + a]};
+    int n = gn[f];
+    for (int b = lane; b < n; b += 32) {
+      double v = cf * (ja[0] * J[b] + ja[1] * J[MAXG + b] + ja[2] * J[2 * MAXG + b] +
+                       ja[3] * J[3 * MAXG + b]);
+      if (v == 0.0) continue;
+      int sl = find_slot(row_ptr, col, r, gdof[(size_t)f * MAXG + b]);
+      if (sl >= 0) kg[sl] += v;
+    }
     __syncwarp();
   }
 }
@@ -1076,20 +1099,24 @@ __global__ void __launch_bounds__(32 * PW)
 
 // ------------------------------------------------------------------ gravity, contact candidates
 
-__global__ void k_fext(int P, const int* __restrict__ nsup, const int* __restrict__ sidx,
-                       const double* __restrict__ S, const double* __restrict__ mass, double g0,
-                       double g1, double g2, double* fext) {
-  int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w >= P) return;
-  double m = mass[w];
-  for (int k = lane; k < nsup[w]; k += 32) {
-    size_t o = (size_t)w * MAXS + k;
-    double s = S[o] * m;
-    int j = sidx[o];
-    if (g0 != 0.0) atomicAdd(fext + 3 * (size_t)j, s * g0);
-    if (g1 != 0.0) atomicAdd(fext + 3 * (size_t)j + 1, s * g1);
-    if (g2 != 0.0) atomicAdd(fext + 3 * (size_t)j + 2, s * g2);
+// f_ext,r = sum over the point sources (p, k) of row r of S_pk m_p g: one warp
+// per row, lanes strided over the sources in key order, then the fixed
+// shuffle tree (the same sums on every run)
+__global__ void k_fext_rows(int nd, int P, const long long* __restrict__ sptr,
+                            const uint64_t* __restrict__ skeys, const double* __restrict__ S,
+                            const double* __restrict__ mass, double g0, double g1, double g2,
+                            double* fext) {
+  int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= nd) return;
+  double a = 0.0;
+  for (long long q = sptr[r] + lane; q < sptr[r + 1]; q += 32) {
+    uint32_t sid = (uint32_t)skeys[q];
+    int w = (int)(sid >> 6), k = (int)(sid & 63);
+    if (w >= P) continue;
+    a += S[(size_t)w * MAXS + k] * mass[w];
   }
+  a = warp_sum(a);
+  if (lane < 3) fext[3 * (size_t)r + lane] = a * (lane == 0 ? g0 : (lane == 1 ? g1 : g2));
 }
 
 __global__ void k_cand_flag(int P, const double* __restrict__ px, const double* __restrict__ plp,
@@ -1165,6 +1192,39 @@ __global__ void k_cand_basis(int nc, const int* __restrict__ cand, Geo g,
     }
   }
   cb_n[i] = n;
+}
+
+// the transpose of the corner basis: keys (dof << 32 | corner << 5 | entry),
+// unused entries last
+__global__ void k_ct_keys(int nc8, const int* __restrict__ cb_n, const int* __restrict__ cb_idx,
+                          uint64_t* keys) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nc8 * MAXCB) return;
+  int i = (int)(t / MAXCB), e = (int)(t % MAXCB);
+  keys[t] = e < cb_n[i] ? ((uint64_t)(uint32_t)cb_idx[t] << 32) | ((uint64_t)i << 5) | (uint64_t)e
+                        : ~0ULL;
+}
+
+// first entry of each row in the sorted keys
+__global__ void k_ct_flag(long long n, const uint64_t* __restrict__ keys, int* flag) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  uint64_t k = keys[q];
+  flag[q] = k != ~0ULL && (q == 0 || (keys[q - 1] >> 32) != (k >> 32));
+}
+
+__global__ void k_ct_write(long long n, const uint64_t* __restrict__ keys, const int* __restrict__ flag,
+                           const int* __restrict__ pos, int nrow, int* crow, int* cptr, int* cent) {
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  uint64_t k = keys[q];
+  if (k == ~0ULL) return;
+  cent[q] = (int)(k & 0xffffffffULL);
+  if (flag[q]) {
+    crow[pos[q]] = (int)(k >> 32);
+    cptr[pos[q]] = (int)q;
+  }
+  if (q == n - 1 || keys[q + 1] == ~0ULL) cptr[nrow] = (int)(q + 1);
 }
 
 // ------------------------------------------------------------------ sliced storage
@@ -1525,10 +1585,16 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
   {
     double* kg = grow<double>(c, m->kg, m->nnzb);
     MPM_CUDA(cudaMemsetAsync(kg, 0, sizeof(double) * m->nnzb, st));
-    if (nf)
-      MPM_LAUNCH(k_ghost_matrix<<<grid_for(nf, 4), 128, 0, st>>>(nf, g, mat.kappa, ptr<int>(m->gface), lkey, llev,
-                                                      betaK, ptr<int>(m->gdof), ptr<int>(m->gn),
-                                                      corner, cptr, cidx, cw, node_dof, rp, col, kg));
+    if (nf) {
+      double* gJ = grow<double>(c, m->gJ, 4 * (size_t)nf * MAXG);
+      double* gco = grow<double>(c, m->gcoef, nf);
+      MPM_LAUNCH(k_ghost_jumps<<<grid_for(nf, 4), 128, 0, st>>>(nf, g, mat.kappa, ptr<int>(m->gface), lkey, llev,
+                                                               betaK, ptr<int>(m->gdof), ptr<int>(m->gn),
+                                                               corner, cptr, cidx, cw, node_dof, gJ, gco));
+      MPM_LAUNCH(k_ghost_rows<<<grid_for(nd, 8), 256, 0, st>>>(nd, P, ptr<long long>(m->src_ptr),
+                                                              ptr<uint64_t>(m->src_key), ptr<int>(m->gdof),
+                                                              ptr<int>(m->gn), gJ, gco, rp, col, kg));
+    }
   }
 
   // ---- gravity force at load 1: f_ext,v = sum_p S_vp m_p g
@@ -1536,12 +1602,15 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     double* fext = grow<double>(c, m->fext, 3 * (size_t)nd);
     MPM_CUDA(cudaMemsetAsync(fext, 0, sizeof(double) * 3 * nd, st));
     if (mat.g[0] != 0.0 || mat.g[1] != 0.0 || mat.g[2] != 0.0)
-      MPM_LAUNCH(k_fext<<<grid_for(P, 8), 256, 0, st>>>(P, nsup, sidx, S, ptr<double>(m->pmass), mat.g[0],
-                                             mat.g[1], mat.g[2], fext));
+      MPM_LAUNCH(k_fext_rows<<<grid_for(nd, 8), 256, 0, st>>>(nd, P, ptr<long long>(m->src_ptr),
+                                                             ptr<uint64_t>(m->src_key), S,
+                                                             ptr<double>(m->pmass), mat.g[0], mat.g[1],
+                                                             mat.g[2], fext));
   }
 
   // ---- contact candidates: domains with a corner within 4 finest cells of the body
   m->ncand = 0;
+  m->nct = 0;
   if (mat.contact_on && body.kind != 0) {
     int* flag = grow<int>(c, c->tmp[0], P);
     int* pos = grow<int>(c, c->tmp[1], P);
@@ -1559,6 +1628,22 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
           grow<int>(c, m->cb_idx, 8 * (size_t)nc * MAXCB),
           grow<double>(c, m->cb_phi, 8 * (size_t)nc * MAXCB),
           grow<double>(c, m->cb_y0, 24 * (size_t)nc), d_err));
+      // the transpose of the corner basis, rows with their (corner, entry)
+      // lists in sorted order, for the contact row gather
+      long long nk = 8LL * nc * MAXCB;
+      uint64_t* keys = grow<uint64_t>(c, c->tmp[4], nk);
+      uint64_t* alt = grow<uint64_t>(c, c->tmp[5], nk);
+      MPM_LAUNCH(k_ct_keys<<<grid_for(nk, 256), 256, 0, st>>>(8 * nc, ptr<int>(m->cb_n), ptr<int>(m->cb_idx), keys));
+      cub_sort_u64(c, keys, alt, (int)nk, 64);
+      int* cflag = grow<int>(c, c->tmp[6], nk + 1);
+      int* cpos = grow<int>(c, c->tmp[7], nk + 1);
+      MPM_LAUNCH(k_ct_flag<<<grid_for(nk, 256), 256, 0, st>>>(nk, keys, cflag));
+      cub_exclusive_sum_int(c, cflag, cpos, (int)nk);
+      int nrow = read_total(c, cpos, cflag, (int)nk);
+      m->nct = nrow;
+      MPM_LAUNCH(k_ct_write<<<grid_for(nk, 256), 256, 0, st>>>(
+          nk, keys, cflag, cpos, nrow, grow<int>(c, m->ct_row, nrow + 1), grow<int>(c, m->ct_ptr, nrow + 1),
+          grow<int>(c, m->ct_ent, nk)));
     }
   }
 

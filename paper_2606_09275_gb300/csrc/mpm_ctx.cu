@@ -119,6 +119,9 @@ extern "C" int mpm_create(mpm_ctx** out, void* stream) {
     MPM_CUDA(cudaMallocAsync((void**)&c->d_err, sizeof(int), c->stream));
     MPM_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     MPM_CUDA(cudaMallocAsync((void**)&c->d_red, 64 * sizeof(double), c->stream));
+    MPM_CUDA(cudaMallocAsync((void**)&c->d_ticket, 16, c->stream));
+    MPM_CUDA(cudaMemsetAsync(c->d_ticket, 0, 16, c->stream));
+    grid_red(c, 4, 4096);
     MPM_CUDA(cudaMallocHost((void**)&c->h_red, 64 * sizeof(double)));
     MPM_CUDA(cudaMallocHost((void**)&c->h_int, 64 * sizeof(int)));
     MPM_CUDA(cudaStreamSynchronize(c->stream));
@@ -149,7 +152,8 @@ void mesh_release(mpm_mesh* m) {
                  &m->isB, &m->gface, &m->gdof, &m->gn, &m->row_ptr, &m->col, &m->kg, &m->rowcnt,
                  &m->src_key, &m->src_ptr, &m->fext, &m->cand, &m->cb_n, &m->cb_idx, &m->cb_phi,
                  &m->cb_y0, &m->dF, &m->dFinv, &m->tau, &m->Aalg, &m->gx, &m->slice_w, &m->slice_base, &m->scol,
-                 &m->lawst};
+                 &m->lawst, &m->ct_row, &m->ct_ptr, &m->ct_ent, &m->cc_f, &m->cc_k, &m->cc_on,
+                 &m->gJ, &m->gcoef, &m->Mf};
   for (Buf* b : bufs) free_buf(c, *b);
 }
 }  // namespace mpm
@@ -166,6 +170,7 @@ extern "C" int mpm_destroy(mpm_ctx* c) {
   }
   c->meshes.clear();
   free_buf(c, c->cub_tmp);
+  free_buf(c, c->part);
   for (auto& b : c->tmp) free_buf(c, b);
   for (auto& b : c->v) free_buf(c, b);
   try {
@@ -175,6 +180,7 @@ extern "C" int mpm_destroy(mpm_ctx* c) {
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   if (c->d_err) cudaFreeAsync(c->d_err, c->stream);
   if (c->d_red) cudaFreeAsync(c->d_red, c->stream);
+  if (c->d_ticket) cudaFreeAsync(c->d_ticket, c->stream);
   cudaStreamSynchronize(c->stream);
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->h_int) cudaFreeHost(c->h_int);

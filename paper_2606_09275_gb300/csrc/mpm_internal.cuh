@@ -76,6 +76,12 @@ struct Scal {
   int done, iters, breakdown, pad;
 };
 
+// storage of a fixed-order grid sum (grid_sum below)
+struct GridRed {
+  double* part;      // [NV][gridDim.x] partials
+  unsigned* ticket;  // 0 before and after each launch
+};
+
 // one coarse level of the geometric multigrid: the active nodes of the uniform
 // grid of depth d, a Galerkin operator stored per stencil offset (a cube of
 // side 2R+1 around each node), the smoother's 3x3 inverses and level vectors
@@ -94,6 +100,10 @@ struct MGData {
   int nlev = 0;                // coarse levels (the last one is solved densely)
   MGLevel lev[8];
   Buf p_idx, p_w;              // fine dof -> up to 8 level-1 rows and weights
+  Buf t_ptr, t_idx, t_w;       // the transpose: level-1 row -> (fine dof, weight), by dof
+  int t_max = 0;               // longest row of the transpose
+  Buf acc;                     // 64-bit fixed-point accumulator of a Galerkin product
+  Buf bound;                   // per level: largest l1 norm of an operator row (double bits)
   Buf fDinv, fx, fr;           // fine smoother inverses, fine V-cycle vectors
   Buf fKh;                     // FP16 copy of the fine matrix (mixed path)
   Buf cinv;                    // dense inverse of the coarsest operator
@@ -123,6 +133,10 @@ struct mpm_ctx {
   int device = 0;
   int* d_err = nullptr;        // device error word
   double* d_red = nullptr;     // device reduction slots (64 doubles)
+  // fixed-order grid sums (mpm::GridRed): per-block partials and the ticket
+  // that elects the last block; the ticket is zero between launches
+  mpm::Buf part;
+  unsigned* d_ticket = nullptr;
   double* h_red = nullptr;     // pinned host mirror
   int* h_int = nullptr;        // pinned host ints (counts)
   mpm::Buf cub_tmp;            // CUB temporary storage
@@ -180,8 +194,14 @@ struct mpm_mesh {
   // contact candidates (sorted point ids) and the basis at their 8 corners
   int ncand = 0;
   mpm::Buf cand, cb_n, cb_idx, cb_phi, cb_y0;
-  // per-iteration point data
-  mpm::Buf dF, dFinv, tau, Aalg, gx;
+  // the transpose of the corner basis: nct rows, each with its (corner << 5 |
+  // entry) list sorted; per-assembly corner forces, stiffness and flags
+  int nct = 0;
+  mpm::Buf ct_row, ct_ptr, ct_ent, cc_f, cc_k, cc_on;
+  // ghost faces: jumps J at the 4 Gauss points (4 x MAXG) and the coefficient
+  mpm::Buf gJ, gcoef;
+  // per-iteration point data (Mf: V0 tau dF^-T, 12 per point)
+  mpm::Buf dF, dFinv, tau, Aalg, gx, Mf;
   mpm::Buf lawst;  // spectral state of the last residual-only evaluation (22 per point)
   int built = 0;
   long long gen = 0;                    // incremented by every build
@@ -237,6 +257,12 @@ inline void free_buf(mpm_ctx* c, Buf& b) {
   if (b.p) cudaFreeAsync(b.p, c->stream);
   b.p = nullptr;
   b.bytes = 0;
+}
+
+// partial-sum storage for a grid sum of nv values over `blocks` blocks
+inline GridRed grid_red(mpm_ctx* c, int nv, long long blocks) {
+  double* p = grow<double>(c, c->part, (size_t)nv * (size_t)(blocks < 1 ? 1 : blocks));
+  return GridRed{p, c->d_ticket};
 }
 
 // at least one block: an empty grid is a launch error, and every kernel
@@ -369,6 +395,7 @@ __device__ inline bool body_sdf(const mpm_rigid& b, double L, const double* x, d
       return true;
     }
     *phi = fs;
+    if (axis) return true;  // mean normal of the circle of wall points: zero
     n[0] = ux;
     n[1] = uy;
     curv = 1.0;
@@ -378,9 +405,14 @@ __device__ inline bool body_sdf(const mpm_rigid& b, double L, const double* x, d
       *phi = body_distance(b, x);
       return false;
     }
-    if (z <= b.z + hc) {
-      double ca = cos(b.alpha), sa = sin(b.alpha);
-      *phi = rho * ca - (z - b.z) * sa;
+    // nearest boundary point inside: the flank below the rim, the shaft wall
+    // above it, except near the axis just above the rim where the flank is
+    // nearer (its line's foot, moved along the flank normal, below the rim)
+    double ca = cos(b.alpha), sa = sin(b.alpha);
+    double pf = rho * ca - (z - b.z) * sa;
+    bool flank = z <= b.z + hc || (pf > rho - b.r && (z - b.z) + pf * sa <= hc);
+    if (flank) {
+      *phi = pf;
       if (axis) {
         // on the axis: mean normal of the circle of closest points, no curvature
         n[2] = -sa;
@@ -392,6 +424,7 @@ __device__ inline bool body_sdf(const mpm_rigid& b, double L, const double* x, d
       curv = ca;
     } else {
       *phi = rho - b.r;
+      if (axis) return true;  // mean normal of the circle of wall points: zero
       n[0] = ux;
       n[1] = uy;
       curv = 1.0;
@@ -442,6 +475,54 @@ __device__ inline double block_sum(double v, double* sh) {
   }
   __syncthreads();
   return r;
+}
+
+// ------------------------------------------------------------------ fixed-order grid sums
+//
+// Sums over a whole grid without floating-point atomics.  Each block reduces
+// its threads' values with the fixed shuffle tree of block_sum and stores the
+// result in its own slot; the block that finishes last (elected by an integer
+// ticket) adds the slots in block order.  For a given launch shape the result
+// is the same bit for bit on every run, whatever order the blocks run in, so
+// the Newton path (its residual norms, line search, Krylov scalars) is
+// reproducible.  Every block of the grid must reach grid_sum (or none: a
+// kernel may return early only where all of its blocks do).
+template <int NV>
+__device__ inline void grid_sum(const double* v, double* const* out, GridRed g) {
+  __shared__ double gsh[32];
+  __shared__ int glast;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = block_sum(v[i], gsh);
+    if (threadIdx.x == 0) g.part[(size_t)i * gridDim.x + blockIdx.x] = s;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    glast = atomicAdd(g.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!glast) return;
+  __threadfence();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      s += __ldcg(g.part + (size_t)i * gridDim.x + b);
+    s = block_sum(s, gsh);
+    if (threadIdx.x == 0 && out[i]) *out[i] += s;
+  }
+  if (threadIdx.x == 0) *g.ticket = 0u;
+}
+
+__device__ inline void grid_sum1(double v, double* out, GridRed g) {
+  double* o[1] = {out};
+  grid_sum<1>(&v, o, g);
+}
+
+__device__ inline void grid_sum2(double a, double b, double* oa, double* ob, GridRed g) {
+  double v[2] = {a, b};
+  double* o[2] = {oa, ob};
+  grid_sum<2>(v, o, g);
 }
 
 // ------------------------------------------------------------------ event timing

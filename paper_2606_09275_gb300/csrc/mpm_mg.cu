@@ -8,9 +8,12 @@
 // is plain trilinear interpolation at the fine node positions (components
 // fixed by a Dirichlet plane are dropped from P).  Coarse operators are
 // Galerkin products A_c = P^T A P, accumulated by one warp per finer-level row
-// into the coarse rows (atomics resolved in L2) and stored per stencil offset
-// on the uniform grid.  Restrictions are scattered the same way by the
-// residual kernels; prolongations gather.  The
+// into the coarse rows by 64-bit integer atomics on a fixed-point copy (exact
+// integer sums, so the operator is the same bit for bit whatever the order of
+// the atomics), and stored per stencil offset on the uniform grid.
+// Restrictions gather the stored residual of the finer level in a fixed
+// order (level 1 through the transpose of P, sorted by fine dof);
+// prolongations gather.  The
 // smoother is l1 block Jacobi, M = D + diag(sum over the row's off-diagonal
 // |entries|), damped by a fixed weight w < 2 (kSmoothW), which is convergent
 // without eigenvalue estimates; one sweep before and one after the coarse
@@ -121,6 +124,48 @@ __global__ void k_mg_p1_rows(int nd, const int* __restrict__ gid, int* pidx) {
   if (lin >= 0) pidx[e] = gid[lin];
 }
 
+// the transpose of the level-1 interpolation: keys (level-1 row << 35 | the
+// entry's position 8 i + q in pidx), unused entries last
+__global__ void k_mg_tkeys(int nd, const int* __restrict__ pidx, uint64_t* keys) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 8LL * nd) return;
+  int a = pidx[e];
+  keys[e] = a < 0 ? ~0ULL : ((uint64_t)a << 35) | (uint64_t)e;
+}
+
+// first entry of each level-1 row among the sorted keys (row nrow: the count)
+__global__ void k_mg_tptr(int nrow, long long n, const uint64_t* __restrict__ keys, int* tptr,
+                          int* tmax) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a > nrow) return;
+  auto first = [&](uint64_t k) {
+    long long lo = 0, hi = n;
+    while (lo < hi) {
+      long long mid = (lo + hi) >> 1;
+      if (keys[mid] < k)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    return lo;
+  };
+  long long b = first((uint64_t)a << 35);
+  tptr[a] = (int)b;
+  if (a < nrow) atomicMax(tmax, (int)(first((uint64_t)(a + 1) << 35) - b));
+}
+
+// (fine dof, weight) of each entry of the transpose
+__global__ void k_mg_tent(long long n, const uint64_t* __restrict__ keys, const float* __restrict__ pw,
+                          int* tidx, float* tw) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  uint64_t k = keys[e];
+  if (k == ~0ULL) return;
+  long long f = (long long)(k & ((1ULL << 35) - 1));
+  tidx[e] = (int)(f >> 3);
+  tw[e] = pw[f];
+}
+
 // largest level-1 cell distance between the two dofs of any stored block
 __global__ void k_mg_reach(int nd, int D, int d1, const int* __restrict__ rp,
                            const int* __restrict__ col, const int* __restrict__ dof_node,
@@ -142,6 +187,29 @@ __global__ void k_mg_reach(int nd, int D, int d1, const int* __restrict__ rp,
 }
 
 // ---------------------------------------------------------------- Galerkin products
+
+// Fixed-point scale of a Galerkin product whose entries are sums of terms
+// with sum |term| <= B: 2^(60 - floor(log2 B)), so that every partial sum
+// stays below 2^61 in magnitude and the 64-bit integer accumulation cannot
+// overflow; one unit is at most 2^-60 B (below FP64 rounding of the sum).
+__device__ inline double fixed_scale(double B) {
+  if (!(B > 0.0) || !isfinite(B)) return 1.0;
+  return ldexp(1.0, 60 - ilogb(B));
+}
+
+__device__ inline void fixed_add(unsigned long long* a, double v, double sc) {
+  atomicAdd(a, (unsigned long long)__double2ll_rn(v * sc));
+}
+
+// fixed point -> operator values
+template <class T>
+__global__ void k_mg_from_fixed(long long n, const unsigned long long* __restrict__ acc,
+                                const unsigned long long* __restrict__ bnd, double cnt, T* A) {
+  double inv = 1.0 / fixed_scale(__longlong_as_double((long long)*bnd) * cnt);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    A[i] = (T)((double)(long long)acc[i] * inv);
+}
 
 __device__ inline int stencil_index(const int* cb, const int* ca, int R) {
   int S1 = 2 * R + 1;
@@ -166,16 +234,22 @@ __global__ void k_mg_fix_masked(int nrow, int S, int R, const int* __restrict__ 
 
 // level 1: one warp per fine dof i; its block row, weighted by P_ia for every
 // coarse row a it interpolates from, spread to the coarse columns of each
-// column dof j.  The sums go to the zeroed coarse operator by global atomics
-// (resolved in L2); a warp per fine row keeps the work balanced when the
-// coarse grid is much coarser than the finest leaves.
+// column dof j.  The terms go to the zeroed fixed-point operator by 64-bit
+// integer atomics (resolved in L2); a warp per fine row keeps the work
+// balanced when the coarse grid is much coarser than the finest leaves.  The
+// bound: every entry sums terms P_ia |K_ij| P_jb with sum over j, b at most
+// the l1 norm of row i (bnd, from the fine smoother kernel) and at most cnt
+// fine rows i per coarse row a.
 template <class T>
 __global__ void k_mg_rap1(int nd, int R, int S, const float* __restrict__ pw,
                           const int* __restrict__ pidx, const int* __restrict__ fmask,
                           const int* __restrict__ rp, const int* __restrict__ col, Sliced SK,
-                          const T* __restrict__ K, const int* __restrict__ xyz, T* A, int* err) {
+                          const T* __restrict__ K, const int* __restrict__ xyz,
+                          unsigned long long* A, const unsigned long long* __restrict__ bnd,
+                          double cnt, int* err) {
   int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (i >= nd) return;
+  double sc = fixed_scale(__longlong_as_double((long long)*bnd) * cnt);
   int mi = fmask[i];
   int s0 = rp[i], nb = rp[i + 1] - s0;
   int sl = i >> 5, W = SK.w[sl];
@@ -193,14 +267,14 @@ __global__ void k_mg_rap1(int nd, int R, int S, const float* __restrict__ pw,
     for (int qa = 0; qa < 8; ++qa) {
       int a = pidx[8 * (size_t)i + qa];
       if (a < 0) break;
-      T wa = (T)pw[8 * (size_t)i + qa];
+      double wa = (double)pw[8 * (size_t)i + qa];
       int ca[3];
       unpack3(xyz[a], ca);
-      T* row = A + (size_t)a * S * 9;
+      unsigned long long* row = A + (size_t)a * S * 9;
       for (int q = 0; q < 8; ++q) {
         int b = pidx[8 * (size_t)j + q];
         if (b < 0) break;
-        T f = wa * (T)pw[8 * (size_t)j + q];
+        double f = wa * (double)pw[8 * (size_t)j + q];
         int cb[3];
         unpack3(xyz[b], cb);
         int o = stencil_index(cb, ca, R);
@@ -209,7 +283,7 @@ __global__ void k_mg_rap1(int nd, int R, int S, const float* __restrict__ pw,
           continue;
         }
 #pragma unroll
-        for (int e = 0; e < 9; ++e) atomicAdd(row + 9 * o + e, f * v[e]);
+        for (int e = 0; e < 9; ++e) fixed_add(row + 9 * o + e, f * (double)v[e], sc);
       }
     }
   }
@@ -217,14 +291,17 @@ __global__ void k_mg_rap1(int nd, int R, int S, const float* __restrict__ pw,
 
 // uniform level -> next coarser: one warp per row i of the finer level; its
 // operator row, weighted by the trilinear weights prod(1 - |delta|/2) of the
-// coarse rows a around it, spread to the coarse columns of each column j
+// coarse rows a around it, spread to the coarse columns of each column j, by
+// fixed-point integer atomics as above (at most 27 finer rows per coarse row)
 template <class T>
 __global__ void k_mg_rapu(int nrow_f, int Rc, int Sc, int n1c, const int* __restrict__ gid_c,
                           int Rf, int Sf, int n1f, const int* __restrict__ gid_f,
                           const int* __restrict__ xyz_f, const int* __restrict__ fmask,
-                          const T* __restrict__ Af, T* A, int* err) {
+                          const T* __restrict__ Af, unsigned long long* A,
+                          const unsigned long long* __restrict__ bnd, int* err) {
   int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (i >= nrow_f) return;
+  double sc = fixed_scale(__longlong_as_double((long long)*bnd) * 27.0);
   int fi[3];
   unpack3(xyz_f[i], fi);
   int mi = fmask[i];
@@ -260,19 +337,19 @@ __global__ void k_mg_rapu(int nrow_f, int Rc, int Sc, int n1c, const int* __rest
         for (int ax = alo[0]; ax <= ahi[0]; ++ax) {
           int a = gid_c[ax + n1c * (ay + n1c * az)];
           if (a < 0) continue;
-          T wa = (T)1;
-          if (alo[0] != ahi[0]) wa *= (T)0.5;
-          if (alo[1] != ahi[1]) wa *= (T)0.5;
-          if (alo[2] != ahi[2]) wa *= (T)0.5;
-          T* row = A + (size_t)a * Sc * 9;
+          double wa = 1.0;
+          if (alo[0] != ahi[0]) wa *= 0.5;
+          if (alo[1] != ahi[1]) wa *= 0.5;
+          if (alo[2] != ahi[2]) wa *= 0.5;
+          unsigned long long* row = A + (size_t)a * Sc * 9;
           int ca[3] = {ax, ay, az};
           for (int z = blo[2]; z <= bhi[2]; ++z)
             for (int y = blo[1]; y <= bhi[1]; ++y)
               for (int x = blo[0]; x <= bhi[0]; ++x) {
-                T f = wa;
-                if (blo[0] != bhi[0]) f *= (T)0.5;
-                if (blo[1] != bhi[1]) f *= (T)0.5;
-                if (blo[2] != bhi[2]) f *= (T)0.5;
+                double f = wa;
+                if (blo[0] != bhi[0]) f *= 0.5;
+                if (blo[1] != bhi[1]) f *= 0.5;
+                if (blo[2] != bhi[2]) f *= 0.5;
                 int cb[3] = {x, y, z};
                 int o = stencil_index(cb, ca, Rc);
                 if (o < 0) {
@@ -280,7 +357,7 @@ __global__ void k_mg_rapu(int nrow_f, int Rc, int Sc, int n1c, const int* __rest
                   continue;
                 }
 #pragma unroll
-                for (int e = 0; e < 9; ++e) atomicAdd(row + 9 * o + e, f * v[e]);
+                for (int e = 0; e < 9; ++e) fixed_add(row + 9 * o + e, f * (double)v[e], sc);
               }
         }
   }
@@ -312,9 +389,12 @@ __device__ inline void store_inv(const double* a, T* o, int* err, double w) {
   o[11] = (T)0;
 }
 
+// also the largest l1 norm of a row (all 9 entries of every block), the bound
+// of the level-1 Galerkin product (a maximum of non-negative doubles, by the
+// ordering of their bit patterns: the same whatever the order)
 template <class T>
 __global__ void k_mg_dinv_fine(int nd, int npad, Sliced SK, const T* __restrict__ K, T* Dinv, int* err,
-                               double w) {
+                               double w, unsigned long long* bnd) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= npad) return;
   T* o = Dinv + 12 * (size_t)r;
@@ -349,13 +429,16 @@ __global__ void k_mg_dinv_fine(int nd, int npad, Sliced SK, const T* __restrict_
       }
     }
   }
+  double l1 = (double)s[0] + (double)s[1] + (double)s[2];
+  for (int e = 0; e < 9; ++e) l1 += fabs(a[e]);
+  atomicMax(bnd, (unsigned long long)__double_as_longlong(l1));
   for (int d = 0; d < 3; ++d) a[4 * d] += (double)s[d];
   store_inv<T>(a, o, err, w);
 }
 
 template <class T>
 __global__ void k_mg_dinv(int nrow, int npad, int S, int R, const T* __restrict__ A, T* Dinv, int* err,
-                          double w) {
+                          double w, unsigned long long* bnd) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= npad) return;
   T* o = Dinv + 12 * (size_t)r;
@@ -371,6 +454,9 @@ __global__ void k_mg_dinv(int nrow, int npad, int S, int R, const T* __restrict_
     if (oo == center) continue;
     for (int e = 0; e < 9; ++e) s[e / 3] += fabs((double)row[9 * oo + e]);
   }
+  double l1 = s[0] + s[1] + s[2];
+  for (int e = 0; e < 9; ++e) l1 += fabs(a[e]);
+  atomicMax(bnd, (unsigned long long)__double_as_longlong(l1));
   for (int d = 0; d < 3; ++d) a[4 * d] += s[d];
   store_inv<T>(a, o, err, w);
 }
@@ -468,17 +554,12 @@ __global__ void k_to_half(long long n, const float* __restrict__ K, const unsign
 
 // ---------------------------------------------------------------- V-cycle kernels
 
-// x = Dinv b (rows padded to 4 components); also clears the first nz rows of
-// zb (the next level's right-hand side, accumulated by atomics)
+// x = Dinv b (rows padded to 4 components)
 template <class T>
 __global__ void k_mg_jac0(int n, const T* __restrict__ Dinv, const T* __restrict__ b, T* x,
-                          T* zb, int nz, const Scal* sk, int k) {
+                          const Scal* sk, int k) {
   if (skip(sk, k)) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nz) {
-    T z4[4] = {0, 0, 0, 0};
-    st4(zb + 4 * (size_t)i, z4);
-  }
   if (i >= n) return;
   T bv[4], xv[4];
   ld4(b + 4 * (size_t)i, bv);
@@ -486,14 +567,14 @@ __global__ void k_mg_jac0(int n, const T* __restrict__ Dinv, const T* __restrict
   st4(x + 4 * (size_t)i, xv);
 }
 
-// fine level: MODE 0, b1 += P^T (b - K x) (the residual restricted to level 1
-// by atomics); MODE 1, xo = x + Dinv (b - K x) with r.z += b.xo
+// fine level: MODE 0, out = b - K x with the Dirichlet components zeroed (the
+// residual that k_mg_restrict1 gathers to level 1); MODE 1, out = x + Dinv
+// (b - K x) with r.z += b.out by a fixed-order grid sum (rz non-null)
 template <class T, int MODE, class TK>
 __global__ void k_mg_fine(int nd, int npad, Sliced SK, const TK* __restrict__ K, const float* kscale,
                           const T* __restrict__ b, const T* __restrict__ x, const T* __restrict__ Dinv,
-                          T* out, const int* __restrict__ pidx, const float* __restrict__ pw,
-                          const int* __restrict__ fmask, double* rz, const Scal* sk, int k) {
-  __shared__ double sh[32];
+                          T* out, const int* __restrict__ fmask, double* rz, const Scal* sk, int k,
+                          GridRed gr) {
   if (skip(sk, k)) return;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   double part = 0.0;
@@ -512,23 +593,10 @@ __global__ void k_mg_fine(int nd, int npad, Sliced SK, const TK* __restrict__ K,
     for (int c = 0; c < 3; ++c) res[c] = r < nd ? bv[c] - y[c] : (T)0;
     res[3] = (T)0;
     if (MODE == 0) {
-      if (r < nd) {
-        int mi = fmask[r];
-        int4 ia = *reinterpret_cast<const int4*>(pidx + 8 * (size_t)r);
-        int4 ib = *reinterpret_cast<const int4*>(pidx + 8 * (size_t)r + 4);
-        float4 wa = *reinterpret_cast<const float4*>(pw + 8 * (size_t)r);
-        float4 wb = *reinterpret_cast<const float4*>(pw + 8 * (size_t)r + 4);
-        int av[8] = {ia.x, ia.y, ia.z, ia.w, ib.x, ib.y, ib.z, ib.w};
-        float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-        bool live = true;  // entries end at the first negative index
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          live = live && av[q] >= 0;
-          if (!live) continue;
-          for (int c = 0; c < 3; ++c)
-            if (!((mi >> c) & 1)) atomicAdd(out + 4 * (size_t)av[q] + c, (T)wv[q] * res[c]);
-        }
-      }
+      int mi = r < nd ? fmask[r] : 7;
+      for (int c = 0; c < 3; ++c)
+        if ((mi >> c) & 1) res[c] = (T)0;
+      st4(out + 4 * (size_t)r, res);
     } else {
       T xv[4], d[4];
       ld4(x + 4 * (size_t)r, xv);
@@ -539,21 +607,84 @@ __global__ void k_mg_fine(int nd, int npad, Sliced SK, const TK* __restrict__ K,
       for (int c = 0; c < 3; ++c) part += (double)bv[c] * (double)xv[c];
     }
   }
-  if (MODE == 1 && rz) {
-    part = block_sum(part, sh);
-    if (threadIdx.x == 0) atomicAdd(rz, part);
+  if (MODE == 1 && rz) grid_sum1(part, rz, gr);  // rz is the same for every block
+}
+
+// level-1 right-hand side b = P^T r (r: the fine residual of k_mg_fine MODE 0,
+// gathered through the transpose of P in the fixed order of its entries) and
+// the pre-smoothing x = Dinv b; one warp per level-1 row, padding rows zero
+template <class T>
+__global__ void k_mg_restrict1(int nrow, int npad, const int* __restrict__ tptr,
+                               const int* __restrict__ tidx, const float* __restrict__ tw,
+                               const T* __restrict__ r, const T* __restrict__ Dinv, T* b, T* x,
+                               const Scal* sk, int k) {
+  if (skip(sk, k)) return;
+  int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (a >= npad) return;
+  T s0 = (T)0, s1 = (T)0, s2 = (T)0;
+  if (a < nrow) {
+    int e1 = tptr[a + 1];
+    for (int e = tptr[a] + lane; e < e1; e += 32) {
+      T w = (T)tw[e];
+      T v[4];
+      ld4(r + 4 * (size_t)tidx[e], v);
+      s0 += w * v[0];
+      s1 += w * v[1];
+      s2 += w * v[2];
+    }
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  if (lane == 0) {
+    T bv[4] = {s0, s1, s2, (T)0}, xv[4];
+    st4(b + 4 * (size_t)a, bv);
+    apply_dinv(Dinv, a, bv, xv);  // padding rows of Dinv are zero
+    st4(x + 4 * (size_t)a, xv);
   }
 }
 
-// uniform level (warp per row): MODE 0, the residual b - A x restricted to the
-// next coarser level by atomics into its (zeroed) right-hand side `out`;
-// MODE 1, xo = x + Dinv (b - A x)
+// uniform level -> next coarser right-hand side: coarse node a gathers the
+// residual rf of the 27 finer nodes 2a + delta (delta in {-1, 0, 1}^3) with
+// the weights prod(1 - |delta|/2), then x = Dinv b; one thread per row
+template <class T>
+__global__ void k_mg_restrictu(int nrow, int npad, const int* __restrict__ xyz, int n1f,
+                               const int* __restrict__ gid_f, const T* __restrict__ rf,
+                               const T* __restrict__ Dinv, T* b, T* x, const Scal* sk, int k) {
+  if (skip(sk, k)) return;
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= npad) return;
+  T s[3] = {(T)0, (T)0, (T)0};
+  if (a < nrow) {
+    int ca[3];
+    unpack3(xyz[a], ca);
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int fx = 2 * ca[0] + dx, fy = 2 * ca[1] + dy, fz = 2 * ca[2] + dz;
+          if (fx < 0 || fy < 0 || fz < 0 || fx >= n1f || fy >= n1f || fz >= n1f) continue;
+          int j = gid_f[fx + n1f * (fy + n1f * fz)];
+          if (j < 0) continue;
+          T f = (T)((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+          T v[4];
+          ld4(rf + 4 * (size_t)j, v);
+          for (int c = 0; c < 3; ++c) s[c] += f * v[c];
+        }
+  }
+  T bv[4] = {s[0], s[1], s[2], (T)0}, xv[4];
+  st4(b + 4 * (size_t)a, bv);
+  apply_dinv(Dinv, a, bv, xv);
+  st4(x + 4 * (size_t)a, xv);
+}
+
+// uniform level (warp per row): MODE 0, out = b - A x with the Dirichlet
+// components zeroed (gathered by k_mg_restrictu of the next coarser level);
+// MODE 1, out = x + Dinv (b - A x)
 template <class T, int MODE>
 __global__ void k_mg_lvl(int nrow, int S, int R, int n1, const int* __restrict__ xyz,
                          const int* __restrict__ gid, const T* __restrict__ A, const T* __restrict__ b,
                          const T* __restrict__ x, const T* __restrict__ Dinv, T* out,
-                         const int* __restrict__ mask, int n1c, const int* __restrict__ gid_c,
-                         const Scal* sk, int k) {
+                         const int* __restrict__ mask, const Scal* sk, int k) {
   if (skip(sk, k)) return;
   int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (a >= nrow) return;
@@ -598,25 +729,10 @@ __global__ void k_mg_lvl(int nrow, int S, int R, int n1, const int* __restrict__
     res[2] = bv[2] - y2;
     res[3] = (T)0;
     if (MODE == 0) {
-      int mi = mask[a], lo[3], hi[3];
-      T f = (T)1;
-      for (int d = 0; d < 3; ++d) {
-        lo[d] = ca[d] >> 1;
-        hi[d] = (ca[d] + 1) >> 1;
-        if (lo[d] != hi[d]) f *= (T)0.5;
-      }
-      int bq[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        int xx = lo[0] + (q & 1), y = lo[1] + ((q >> 1) & 1), z = lo[2] + (q >> 2);
-        bq[q] = (xx <= hi[0] && y <= hi[1] && z <= hi[2]) ? gid_c[xx + n1c * (y + n1c * z)] : -1;
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (bq[q] < 0) continue;
-        for (int c = 0; c < 3; ++c)
-          if (!((mi >> c) & 1)) atomicAdd(out + 4 * (size_t)bq[q] + c, f * res[c]);
-      }
+      int mi = mask[a];
+      for (int c = 0; c < 3; ++c)
+        if ((mi >> c) & 1) res[c] = (T)0;
+      st4(out + 4 * (size_t)a, res);
     } else {
       T xv[4], d[4];
       ld4(x + 4 * (size_t)a, xv);
@@ -781,6 +897,23 @@ void mg_structure(mpm_ctx* c, mpm_mesh* m) {
       MPM_CUDA(cudaMemcpyAsync(&c->h_int[2], reach, sizeof(int), cudaMemcpyDeviceToHost, st));
       MPM_CUDA(cudaStreamSynchronize(st));
       L.R = std::max(2, c->h_int[2] + 1);
+      // the transpose of P, for the gathered restriction: keys sorted by
+      // (level-1 row, fine dof, entry)
+      long long n8 = 8LL * nd;
+      uint64_t* keys = grow<uint64_t>(c, c->tmp[4], n8);
+      uint64_t* alt = grow<uint64_t>(c, c->tmp[5], n8);
+      MPM_LAUNCH(k_mg_tkeys<<<grid_for(n8, 256), 256, 0, st>>>(nd, ptr<int>(G.p_idx), keys));
+      cub_sort_u64(c, keys, alt, (int)n8, 64);
+      int* tptr = grow<int>(c, G.t_ptr, L.nrow + 1);
+      int* tmax = (int*)(c->d_red + 8);
+      MPM_CUDA(cudaMemsetAsync(tmax, 0, sizeof(int), st));
+      MPM_LAUNCH(k_mg_tptr<<<grid_for(L.nrow + 1, 256), 256, 0, st>>>(L.nrow, n8, keys, tptr, tmax));
+      MPM_LAUNCH(k_mg_tent<<<grid_for(n8, 256), 256, 0, st>>>(n8, keys, ptr<float>(G.p_w),
+                                                             grow<int>(c, G.t_idx, n8),
+                                                             grow<float>(c, G.t_w, n8)));
+      MPM_CUDA(cudaMemcpyAsync(&c->h_int[2], tmax, sizeof(int), cudaMemcpyDeviceToHost, st));
+      MPM_CUDA(cudaStreamSynchronize(st));
+      G.t_max = c->h_int[2];
     } else {
       L.R = std::max(2, (G.lev[l - 1].R + 2) / 2);
     }
@@ -817,9 +950,13 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
   MGData& G = *m->mg;
   int nd = m->ndof, npad = 32 * m->nslice;
   Sliced SK{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
-  // fine smoother and V-cycle vectors
+  // fine smoother and V-cycle vectors; bnd[l]: largest row l1 norm of the
+  // level-l operator (l = 0 the fine matrix), the Galerkin products' bounds
+  unsigned long long* bnd = grow<unsigned long long>(c, G.bound, 16);
+  MPM_CUDA(cudaMemsetAsync(bnd, 0, 16 * sizeof(unsigned long long), st));
   T* fD = grow<T>(c, G.fDinv, 12 * (size_t)npad);
-  MPM_LAUNCH(k_mg_dinv_fine<T><<<grid_for(npad, 256), 256, 0, st>>>(nd, npad, SK, K, fD, c->d_err, kSmoothW));
+  MPM_LAUNCH(k_mg_dinv_fine<T><<<grid_for(npad, 256), 256, 0, st>>>(nd, npad, SK, K, fD, c->d_err, kSmoothW, bnd));
+  grow<T>(c, G.fr, 4 * (size_t)npad);
   grow<T>(c, G.fx, 4 * (size_t)npad);
   if constexpr (sizeof(T) == 4) {
     // FP16 copy of the fine matrix for the V-cycle's two fine-level products
@@ -833,21 +970,28 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
   if (!coarse) return;
   for (int l = 0; l < G.nlev; ++l) {
     MGLevel& L = G.lev[l];
-    T* A = grow<T>(c, L.A, (size_t)L.nrow * L.S * 9);
-    MPM_CUDA(cudaMemsetAsync(A, 0, sizeof(T) * (size_t)L.nrow * L.S * 9, st));
+    size_t nA = (size_t)L.nrow * L.S * 9;
+    T* A = grow<T>(c, L.A, nA);
+    unsigned long long* acc = grow<unsigned long long>(c, G.acc, nA);
+    MPM_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * nA, st));
+    double cnt;
     if (l == 0) {
+      cnt = (double)std::max(G.t_max, 1);
       MPM_LAUNCH(k_mg_rap1<T><<<grid_for(nd, 8), 256, 0, st>>>(
           nd, L.R, L.S, ptr<float>(G.p_w), ptr<int>(G.p_idx), ptr<int>(m->dof_mask), ptr<int>(m->row_ptr),
-          ptr<int>(m->col), SK, K, ptr<int>(L.xyz), A, c->d_err));
+          ptr<int>(m->col), SK, K, ptr<int>(L.xyz), acc, bnd, cnt, c->d_err));
     } else {
       MGLevel& F = G.lev[l - 1];
+      cnt = 27.0;
       MPM_LAUNCH(k_mg_rapu<T><<<grid_for(F.nrow, 8), 256, 0, st>>>(
           F.nrow, L.R, L.S, L.n1, ptr<int>(L.gid), F.R, F.S, F.n1, ptr<int>(F.gid), ptr<int>(F.xyz),
-          ptr<int>(F.mask), ptr<T>(F.A), A, c->d_err));
+          ptr<int>(F.mask), ptr<T>(F.A), acc, bnd + l, c->d_err));
     }
+    MPM_LAUNCH(k_mg_from_fixed<T><<<4 * 152, 256, 0, st>>>((long long)nA, acc, bnd + l, cnt, A));
     MPM_LAUNCH(k_mg_fix_masked<T><<<grid_for(L.nrow, 128), 128, 0, st>>>(L.nrow, L.S, L.R, ptr<int>(L.mask), A));
     MPM_LAUNCH(k_mg_dinv<T><<<grid_for(L.npad, 128), 128, 0, st>>>(L.nrow, L.npad, L.S, L.R, A,
-                                                                   grow<T>(c, L.Dinv, 12 * (size_t)L.npad), c->d_err, kSmoothW));
+                                                                   grow<T>(c, L.Dinv, 12 * (size_t)L.npad), c->d_err, kSmoothW,
+                                                                   bnd + l + 1));
     // level vectors: padding rows stay zero
     MPM_CUDA(cudaMemsetAsync(grow<T>(c, L.b, 4 * (size_t)L.npad), 0, sizeof(T) * 4 * L.npad, st));
     MPM_CUDA(cudaMemsetAsync(grow<T>(c, L.x, 4 * (size_t)L.npad), 0, sizeof(T) * 4 * L.npad, st));
@@ -889,29 +1033,33 @@ void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, cons
   T* fx = ptr<T>(G.fx);
   const T* fD = ptr<T>(G.fDinv);
   const int FB = 8 * 32;  // rows per block of the fine row kernels
-  // fine pre-smoothing from zero, residual, restriction
+  GridRed gr = grid_red(c, 1, grid_for(npad, FB));
+  // fine pre-smoothing from zero, residual, restriction (gathered)
   MGLevel& L0 = G.lev[0];
-  MPM_LAUNCH(k_mg_jac0<T><<<grid_for(std::max(npad, L0.npad), 256), 256, 0, st>>>(npad, fD, r, fx, ptr<T>(L0.b),
-                                                                                 L0.npad, sk, k));
+  T* fr = ptr<T>(G.fr);
+  MPM_LAUNCH(k_mg_jac0<T><<<grid_for(npad, 256), 256, 0, st>>>(npad, fD, r, fx, sk, k));
   const float* ksc = (const float*)(c->d_red + 11);
   if constexpr (sizeof(T) == 4)
     MPM_LAUNCH(k_mg_fine<T, 0, __half><<<grid_for(npad, FB), FB, 0, st>>>(
-        nd, npad, SK, ptr<__half>(G.fKh), ksc, r, fx, fD, ptr<T>(L0.b), ptr<int>(G.p_idx),
-        ptr<float>(G.p_w), fmask, nullptr, sk, k));
+        nd, npad, SK, ptr<__half>(G.fKh), ksc, r, fx, fD, fr, fmask, nullptr, sk, k, gr));
   else
     MPM_LAUNCH(k_mg_fine<T, 0, T><<<grid_for(npad, FB), FB, 0, st>>>(
-        nd, npad, SK, K, ksc, r, fx, fD, ptr<T>(L0.b), ptr<int>(G.p_idx), ptr<float>(G.p_w), fmask,
-        nullptr, sk, k));
-  // down the uniform levels
+        nd, npad, SK, K, ksc, r, fx, fD, fr, fmask, nullptr, sk, k, gr));
+  MPM_LAUNCH(k_mg_restrict1<T><<<grid_for(L0.npad, MGW), 32 * MGW, 0, st>>>(
+      L0.nrow, L0.npad, ptr<int>(G.t_ptr), ptr<int>(G.t_idx), ptr<float>(G.t_w), fr, ptr<T>(L0.Dinv),
+      ptr<T>(L0.b), ptr<T>(L0.x), sk, k));
+  // down the uniform levels: residual, then the next level's gathered
+  // right-hand side and pre-smoothing
   T* xcur[8];
   for (int l = 0; l + 1 < G.nlev; ++l) {
     MGLevel& L = G.lev[l];
     MGLevel& N = G.lev[l + 1];
-    MPM_LAUNCH(k_mg_jac0<T><<<grid_for(std::max(L.npad, N.npad), 256), 256, 0, st>>>(
-        L.npad, ptr<T>(L.Dinv), ptr<T>(L.b), ptr<T>(L.x), ptr<T>(N.b), N.npad, sk, k));
     MPM_LAUNCH(k_mg_lvl<T, 0><<<grid_for(L.nrow, MGW), 32 * MGW, 0, st>>>(
         L.nrow, L.S, L.R, L.n1, ptr<int>(L.xyz), ptr<int>(L.gid), ptr<T>(L.A), ptr<T>(L.b), ptr<T>(L.x),
-        ptr<T>(L.Dinv), ptr<T>(N.b), ptr<int>(L.mask), N.n1, ptr<int>(N.gid), sk, k));
+        ptr<T>(L.Dinv), ptr<T>(L.r), ptr<int>(L.mask), sk, k));
+    MPM_LAUNCH(k_mg_restrictu<T><<<grid_for(N.npad, 128), 128, 0, st>>>(
+        N.nrow, N.npad, ptr<int>(N.xyz), L.n1, ptr<int>(L.gid), ptr<T>(L.r), ptr<T>(N.Dinv), ptr<T>(N.b),
+        ptr<T>(N.x), sk, k));
   }
   MGLevel& C = G.lev[G.nlev - 1];
   MPM_LAUNCH(k_mg_coarse<T><<<1, 256, 0, st>>>(C.nrow, ptr<T>(G.cinv), ptr<T>(C.b), ptr<T>(C.x), sk, k));
@@ -924,17 +1072,17 @@ void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, cons
         L.nrow, ptr<int>(L.xyz), ptr<int>(L.mask), N.n1, ptr<int>(N.gid), xcur[l + 1], ptr<T>(L.x), sk, k));
     MPM_LAUNCH(k_mg_lvl<T, 1><<<grid_for(L.nrow, MGW), 32 * MGW, 0, st>>>(
         L.nrow, L.S, L.R, L.n1, ptr<int>(L.xyz), ptr<int>(L.gid), ptr<T>(L.A), ptr<T>(L.b), ptr<T>(L.x),
-        ptr<T>(L.Dinv), ptr<T>(L.r), nullptr, 0, nullptr, sk, k));
+        ptr<T>(L.Dinv), ptr<T>(L.r), nullptr, sk, k));
     xcur[l] = ptr<T>(L.r);
   }
   MPM_LAUNCH(k_mg_prolong1<T><<<grid_for(nd, 128), 128, 0, st>>>(nd, ptr<int>(G.p_idx), ptr<float>(G.p_w), fmask,
                                                                   xcur[0], fx, sk, k));
   if constexpr (sizeof(T) == 4)
     MPM_LAUNCH(k_mg_fine<T, 1, __half><<<grid_for(npad, FB), FB, 0, st>>>(
-        nd, npad, SK, ptr<__half>(G.fKh), ksc, r, fx, fD, z, nullptr, nullptr, nullptr, rz, sk, k));
+        nd, npad, SK, ptr<__half>(G.fKh), ksc, r, fx, fD, z, nullptr, rz, sk, k, gr));
   else
     MPM_LAUNCH(k_mg_fine<T, 1, T><<<grid_for(npad, FB), FB, 0, st>>>(
-        nd, npad, SK, K, ksc, r, fx, fD, z, nullptr, nullptr, nullptr, rz, sk, k));
+        nd, npad, SK, K, ksc, r, fx, fD, z, nullptr, rz, sk, k, gr));
 }
 
 void mg_release(mpm_ctx* c, mpm_mesh* m) {
@@ -944,7 +1092,8 @@ void mg_release(mpm_ctx* c, mpm_mesh* m) {
     Buf* b[] = {&L.gid, &L.xyz, &L.mask, &L.A, &L.Dinv, &L.b, &L.x, &L.r};
     for (Buf* x : b) free_buf(c, *x);
   }
-  Buf* b[] = {&G.p_idx, &G.p_w, &G.fDinv, &G.fx, &G.fr, &G.fKh, &G.cinv};
+  Buf* b[] = {&G.p_idx, &G.p_w, &G.t_ptr, &G.t_idx, &G.t_w, &G.acc, &G.bound, &G.fDinv, &G.fx,
+              &G.fr, &G.fKh, &G.cinv};
   for (Buf* x : b) free_buf(c, *x);
   delete m->mg;
   m->mg = nullptr;

@@ -8,6 +8,7 @@
 //  * MPM_MIXED: FP32 matrix and FP32 inner solves inside FP64 iterative
 //    refinement, the refinement residual accumulated in FP64.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <string>
 
@@ -75,8 +76,8 @@ __global__ void k_block_jacobi(int nd, const int* __restrict__ rp, const int* __
 // setup: r = b (free components), x = 0, z = M r, p = z, rz_0, ||b||^2
 template <class V>
 __global__ void k_pcg_init(int nd, int npad, const double* __restrict__ b, const int* __restrict__ mask,
-                           const V* __restrict__ Dinv, V* x, V* r, V* z, V* p, Scal* sc) {
-  __shared__ double sh[32];
+                           const V* __restrict__ Dinv, V* x, V* r, V* z, V* p, Scal* sc,
+                           GridRed gr) {
   double rz = 0.0, bb = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
     V rv[4] = {(V)0, (V)0, (V)0, (V)0}, zv[4] = {(V)0, (V)0, (V)0, (V)0};
@@ -94,19 +95,13 @@ __global__ void k_pcg_init(int nd, int npad, const double* __restrict__ b, const
     st4(z + 4 * (size_t)i, zv);
     st4(p + 4 * (size_t)i, zv);
   }
-  rz = block_sum(rz, sh);
-  bb = block_sum(bb, sh);
-  if (threadIdx.x == 0) {
-    atomicAdd(&sc->rz[0], rz);
-    atomicAdd(&sc->bb, bb);
-  }
+  grid_sum2(rz, bb, &sc->rz[0], &sc->bb, gr);
 }
 
 // q = K p, pq_0 (one thread per row)
 template <class T, class V>
 __global__ void k_pcg_q0(int nd, int npad, Sliced S, const T* __restrict__ K, const V* __restrict__ p,
-                         V* q, Scal* sc) {
-  __shared__ double sh[32];
+                         V* q, Scal* sc, GridRed gr) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   double part = 0.0;
   if (r < npad) {
@@ -119,15 +114,14 @@ __global__ void k_pcg_q0(int nd, int npad, Sliced S, const T* __restrict__ K, co
     ld4(p + 4 * (size_t)r, pv);
     part = (double)yv[0] * pv[0] + (double)yv[1] * pv[1] + (double)yv[2] * pv[2];
   }
-  part = block_sum(part, sh);
-  if (threadIdx.x == 0) atomicAdd(&sc->pq[0], part);
+  grid_sum1(part, &sc->pq[0], gr);
 }
 
 // A_k: alpha = rz_k/pq_k; x += alpha p; r -= alpha q; z = M r; rz_{k+1}, rr_{k+1}
 template <class V, bool PRE = true>
 __global__ void k_pcg_a(int nd, int k, const V* __restrict__ Dinv, V* x, V* r, V* z,
-                        const V* __restrict__ p, const V* __restrict__ q, Scal* sc) {
-  __shared__ double sh[32];
+                        const V* __restrict__ p, const V* __restrict__ q, Scal* sc, GridRed gr) {
+  // early returns are taken by every block alike (scalars of earlier launches)
   if (sc->done) return;
   int i0 = k % 3, i1 = (k + 1) % 3;
   if (blockIdx.x == 0 && threadIdx.x == 0) sc->pq[i1] = 0.0;
@@ -159,19 +153,13 @@ __global__ void k_pcg_a(int nd, int k, const V* __restrict__ Dinv, V* x, V* r, V
       for (int c = 0; c < 3; ++c) rz += (double)rv[c] * (double)zv[c];
     }
   }
-  if (PRE) rz = block_sum(rz, sh);
-  rr = block_sum(rr, sh);
-  if (threadIdx.x == 0) {
-    if (PRE) atomicAdd(&sc->rz[i1], rz);
-    atomicAdd(&sc->rr[i1], rr);
-  }
+  grid_sum2(rz, rr, PRE ? &sc->rz[i1] : nullptr, &sc->rr[i1], gr);
 }
 
 // multigrid-preconditioned start: r = b (free components), x = 0, ||b||^2
 template <class V>
 __global__ void k_pcg_init_mg(int nd, int npad, const double* __restrict__ b, const int* __restrict__ mask,
-                              V* x, V* r, Scal* sc) {
-  __shared__ double sh[32];
+                              V* x, V* r, Scal* sc, GridRed gr) {
   double bb = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
     V rv[4] = {(V)0, (V)0, (V)0, (V)0};
@@ -185,8 +173,7 @@ __global__ void k_pcg_init_mg(int nd, int npad, const double* __restrict__ b, co
     }
     st4(r + 4 * (size_t)i, rv);
   }
-  bb = block_sum(bb, sh);
-  if (threadIdx.x == 0) atomicAdd(&sc->bb, bb);
+  grid_sum1(bb, &sc->bb, gr);
 }
 
 template <class V>
@@ -203,8 +190,7 @@ __global__ void k_copy4(int npad, const V* __restrict__ a, V* b) {
 // q = w + beta q; pq_{k+1}  (one thread per row)
 template <class T, class V>
 __global__ void k_pcg_b(int nd, int npad, int k, Sliced S, const T* __restrict__ K,
-                        const V* __restrict__ z, V* p, V* q, Scal* sc) {
-  __shared__ double sh[32];
+                        const V* __restrict__ z, V* p, V* q, Scal* sc, GridRed gr) {
   if (sc->done) return;
   int i0 = k % 3, i1 = (k + 1) % 3, i2 = (k + 2) % 3;
   double rr = sc->rr[i1];
@@ -240,8 +226,7 @@ __global__ void k_pcg_b(int nd, int npad, int k, Sliced S, const T* __restrict__
       st4(q + 4 * (size_t)r, qv);
     }
   }
-  part = block_sum(part, sh);
-  if (threadIdx.x == 0) atomicAdd(&sc->pq[i1], part);
+  grid_sum1(part, &sc->pq[i1], gr);
 }
 
 // ---------------------------------------------------------------- BiCGStab
@@ -253,8 +238,7 @@ __global__ void k_pcg_b(int nd, int npad, int k, Sliced S, const T* __restrict__
 template <class T>
 __global__ void k_spmv_dot(int nd, int npad, Sliced S, const T* __restrict__ K,
                            const double* __restrict__ x, double* y, const double* __restrict__ a,
-                           double* slot, double* slot2, const Scal* sc, int check_s) {
-  __shared__ double sh[32];
+                           double* slot, double* slot2, const Scal* sc, int check_s, GridRed gr) {
   if (sc->done || (check_s && sc->a[5] <= sc->thr)) return;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   double p1 = 0.0, p2 = 0.0;
@@ -271,14 +255,7 @@ __global__ void k_spmv_dot(int nd, int npad, Sliced S, const T* __restrict__ K,
     }
     p2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
   }
-  if (slot) {
-    p1 = block_sum(p1, sh);
-    if (threadIdx.x == 0) atomicAdd(slot, p1);
-  }
-  if (slot2) {
-    p2 = block_sum(p2, sh);
-    if (threadIdx.x == 0) atomicAdd(slot2, p2);
-  }
+  grid_sum2(p1, p2, slot, slot2, gr);
 }
 
 // BiCGStab scalar slots in Scal::a: 0 rho, 1 alpha, 2 omega, 3 rho1 (r0.r),
@@ -304,8 +281,7 @@ __global__ void k_bicg_p(int npad, double* p, const double* __restrict__ r, cons
 }
 
 __global__ void k_bicg_s(int npad, const double* __restrict__ r, const double* __restrict__ v, double* s,
-                         double* sh_, const double* __restrict__ Dinv, Scal* sc) {
-  __shared__ double sh[32];
+                         double* sh_, const double* __restrict__ Dinv, Scal* sc, GridRed gr) {
   if (sc->done) return;
   double rv0 = sc->a[4];
   if (!(fabs(rv0) > 0.0) || !isfinite(rv0)) return;  // breakdown, recorded by k_bicg_rotate
@@ -325,8 +301,7 @@ __global__ void k_bicg_s(int npad, const double* __restrict__ r, const double* _
       st4(sh_ + 4 * (size_t)i, zv);
     }
   }
-  ss = block_sum(ss, sh);
-  if (threadIdx.x == 0) atomicAdd(&sc->a[5], ss);
+  grid_sum1(ss, &sc->a[5], gr);
 }
 
 // converged on s: x += alpha ph (the rest of the iteration is skipped)
@@ -342,8 +317,7 @@ __global__ void k_bicg_check_s(int nd, double* x, const double* __restrict__ ph,
 __global__ void k_bicg_x(int nd, int npad, double* x, double* r, const double* __restrict__ ph,
                          const double* __restrict__ shv, const double* __restrict__ s,
                          const double* __restrict__ t, const double* __restrict__ r0, const Scal* sc,
-                         double* next_rho1, double* next_rr) {
-  __shared__ double sh[32];
+                         double* next_rho1, double* next_rr, GridRed gr) {
   if (sc->done || sc->a[5] <= sc->thr) return;
   double rv0 = sc->a[4];
   if (!(fabs(rv0) > 0.0) || !isfinite(rv0)) return;
@@ -367,12 +341,7 @@ __global__ void k_bicg_x(int nd, int npad, double* x, double* r, const double* _
     if (i < nd)
       for (int c = 0; c < 3; ++c) x[3 * (size_t)i + c] += alpha * pv[c] + om * zv[c];
   }
-  rr = block_sum(rr, sh);
-  rho1 = block_sum(rho1, sh);
-  if (threadIdx.x == 0) {
-    atomicAdd(next_rr, rr);
-    atomicAdd(next_rho1, rho1);
-  }
+  grid_sum2(rr, rho1, next_rr, next_rho1, gr);
 }
 
 // end of an iteration (one thread): decide convergence or breakdown, rotate
@@ -417,8 +386,7 @@ template <class T, int RS>
 __global__ void k_residual64(int nd, int npad, Sliced S, const T* __restrict__ K,
                              const double* __restrict__ x, const float4* __restrict__ xs,
                              const double* __restrict__ b, const int* __restrict__ mask, double* r,
-                             double* slot) {
-  __shared__ double sh[32];
+                             double* slot, GridRed gr) {
   int rr = blockIdx.x * blockDim.x + threadIdx.x;
   double part = 0.0;
   if (rr < npad) {
@@ -440,8 +408,7 @@ __global__ void k_residual64(int nd, int npad, Sliced S, const T* __restrict__ K
     else if (rr < nd)
       for (int c = 0; c < 3; ++c) r[3 * (size_t)rr + c] = v[c];
   }
-  part = block_sum(part, sh);
-  if (threadIdx.x == 0) atomicAdd(slot, part);
+  grid_sum1(part, slot, gr);
 }
 
 __global__ void k_axpy_f2d(int n, double* x, const float* __restrict__ d) {
@@ -482,8 +449,9 @@ int run_pcg(mpm_ctx* c, const mpm_mesh* m, const T* K, const V* Dinv, const doub
   Sliced S = sliced_of(m);
   MPM_CUDA(cudaMemsetAsync(sc_d, 0, sizeof(Scal), st));
   int vb = 4 * 152;
-  MPM_LAUNCH(k_pcg_init<V><<<vb, 256, 0, st>>>(nd, npad, b, ptr<int>(m->dof_mask), Dinv, x, r, z, p, sc_d));
-  MPM_LAUNCH(k_pcg_q0<T, V><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, p, q, sc_d));
+  GridRed gr = grid_red(c, 2, std::max(vb, grid_for(npad, 32 * SW)));
+  MPM_LAUNCH(k_pcg_init<V><<<vb, 256, 0, st>>>(nd, npad, b, ptr<int>(m->dof_mask), Dinv, x, r, z, p, sc_d, gr));
+  MPM_LAUNCH(k_pcg_q0<T, V><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, p, q, sc_d, gr));
   MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
   MPM_CUDA(cudaStreamSynchronize(st));
   double bb = sc_h->bb;
@@ -500,8 +468,8 @@ int run_pcg(mpm_ctx* c, const mpm_mesh* m, const T* K, const V* Dinv, const doub
   while (k < maxit) {
     int kend = std::min(maxit, k + batch);
     for (; k < kend; ++k) {
-      MPM_LAUNCH_P(MPM_PROF_PCG_UPDATE, k_pcg_a<V><<<vb, 256, 0, st>>>(nd, k, Dinv, x, r, z, p, q, sc_d));
-      MPM_LAUNCH_P(MPM_PROF_PCG_SPMV, k_pcg_b<T, V><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, k, S, K, z, p, q, sc_d));
+      MPM_LAUNCH_P(MPM_PROF_PCG_UPDATE, k_pcg_a<V><<<vb, 256, 0, st>>>(nd, k, Dinv, x, r, z, p, q, sc_d, gr));
+      MPM_LAUNCH_P(MPM_PROF_PCG_SPMV, k_pcg_b<T, V><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, k, S, K, z, p, q, sc_d, gr));
     }
     MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
@@ -528,10 +496,11 @@ int run_pcg_mg(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* b, T* x,
   Sliced S = sliced_of(m);
   MPM_CUDA(cudaMemsetAsync(sc_d, 0, sizeof(Scal), st));
   int vb = 4 * 152;
-  MPM_LAUNCH(k_pcg_init_mg<T><<<vb, 256, 0, st>>>(nd, npad, b, ptr<int>(m->dof_mask), x, r, sc_d));
+  GridRed gr = grid_red(c, 2, std::max(vb, grid_for(npad, 32 * SW)));
+  MPM_LAUNCH(k_pcg_init_mg<T><<<vb, 256, 0, st>>>(nd, npad, b, ptr<int>(m->dof_mask), x, r, sc_d, gr));
   mg_apply<T>(c, m, K, r, z, nullptr, 0, &sc_d->rz[0]);
   MPM_LAUNCH(k_copy4<T><<<grid_for(npad, 256), 256, 0, st>>>(npad, z, p));
-  MPM_LAUNCH(k_pcg_q0<T, T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, p, q, sc_d));
+  MPM_LAUNCH(k_pcg_q0<T, T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, p, q, sc_d, gr));
   MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
   MPM_CUDA(cudaStreamSynchronize(st));
   double bb = sc_h->bb;
@@ -547,11 +516,11 @@ int run_pcg_mg(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* b, T* x,
   while (k < maxit) {
     int kend = std::min(maxit, k + batch);
     for (; k < kend; ++k) {
-      MPM_LAUNCH_P(MPM_PROF_PCG_UPDATE, k_pcg_a<T, false><<<vb, 256, 0, st>>>(nd, k, nullptr, x, r, z, p, q, sc_d));
+      MPM_LAUNCH_P(MPM_PROF_PCG_UPDATE, k_pcg_a<T, false><<<vb, 256, 0, st>>>(nd, k, nullptr, x, r, z, p, q, sc_d, gr));
       prof_begin(c, MPM_PROF_MG);
       mg_apply<T>(c, m, K, r, z, sc_d, k, &sc_d->rz[(k + 1) % 3]);
       prof_end(c);
-      MPM_LAUNCH_P(MPM_PROF_PCG_SPMV, k_pcg_b<T, T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, k, S, K, z, p, q, sc_d));
+      MPM_LAUNCH_P(MPM_PROF_PCG_SPMV, k_pcg_b<T, T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, k, S, K, z, p, q, sc_d, gr));
     }
     MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
@@ -624,8 +593,10 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
   MPM_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * n4, st));
   double* red = c->d_red + 40;  // rho1 / rr accumulators of the next iteration
   MPM_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
+  int vb = 4 * 152, it = 0;
+  GridRed gr = grid_red(c, 2, std::max(vb, grid_for(npad, 32 * SW)));
   // r = r0 = b (free components), ||b||^2 via r = b - K*0
-  MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<T, 4><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, x, residual_split(c, m, K, x), b, mask, r, &sc_d->bb));
+  MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<T, 4><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, x, residual_split(c, m, K, x), b, mask, r, &sc_d->bb, gr));
   MPM_LAUNCH(k_copy_d<<<grid_for((long long)n4, 256), 256, 0, st>>>((int)n4, r0, r));
   MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
   MPM_CUDA(cudaStreamSynchronize(st));
@@ -641,7 +612,6 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
   init.a[0] = init.a[1] = init.a[2] = 1.0;
   init.a[3] = bb;  // r0 . r at the start
   MPM_CUDA(cudaMemcpyAsync(sc_d, &init, sizeof(Scal), cudaMemcpyHostToDevice, st));
-  int vb = 4 * 152, it = 0;
   const int batch = Dinv ? 16 : 4;
   while (it < maxit) {
     int iend = std::min(maxit, it + batch);
@@ -653,16 +623,16 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
         mg_precondition<T>(c, m, K, p, ph, sc_d);
         prof_end(c);
       }
-      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, ph, v, r0, &sc_d->a[4], nullptr, sc_d, 0));
-      MPM_LAUNCH(k_bicg_s<<<vb, 256, 0, st>>>(npad, r, v, s, shv, Dinv, sc_d));
+      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, ph, v, r0, &sc_d->a[4], nullptr, sc_d, 0, gr));
+      MPM_LAUNCH(k_bicg_s<<<vb, 256, 0, st>>>(npad, r, v, s, shv, Dinv, sc_d, gr));
       MPM_LAUNCH(k_bicg_check_s<<<vb, 256, 0, st>>>(nd, x, ph, sc_d));
       if (!Dinv) {
         prof_begin(c, MPM_PROF_MG);
         mg_precondition<T>(c, m, K, s, shv, sc_d);
         prof_end(c);
       }
-      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, shv, t, s, &sc_d->a[6], &sc_d->a[7], sc_d, 1));
-      MPM_LAUNCH(k_bicg_x<<<vb, 256, 0, st>>>(nd, npad, x, r, ph, shv, s, t, r0, sc_d, red, red + 1));
+      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, shv, t, s, &sc_d->a[6], &sc_d->a[7], sc_d, 1, gr));
+      MPM_LAUNCH(k_bicg_x<<<vb, 256, 0, st>>>(nd, npad, x, r, ph, shv, s, t, r0, sc_d, red, red + 1, gr));
       MPM_LAUNCH(k_bicg_rotate<<<1, 1, 0, st>>>(sc_d, red, red + 1, it + 1));
     }
     MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
@@ -692,6 +662,10 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   bool mgb = method == 3 && !sym;  // multigrid-preconditioned BiCGStab
   Scal* sc_d = grow<Scal>(c, c->v[20], 1);
   Scal* sc_h = (Scal*)(c->h_red + 32);  // pinned, 32 doubles fit Scal
+  // partial sums of every grid sum of this solve in one buffer, sized once so
+  // that no later request moves it
+  grid_red(c, 4, std::max(4096, grid_for(npad, 32 * SW)));
+  MPM_CUDA(cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), st));
   static_assert(sizeof(Scal) <= 32 * sizeof(double), "scalar block too large");
   out->iterations = 0;
   out->refinements = 0;
@@ -733,6 +707,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   double* r64 = grow<double>(c, c->v[12], n3);
   float* d32 = grow<float>(c, c->v[13], n3);
   double* slot = c->d_red + 44;
+  GridRed gred = grid_red(c, 2, grid_for(npad, 32 * SW));
   if ((method == 1 || method == 3) && !mgb) {
     float* Dinv = grow<float>(c, c->v[3], 12 * (size_t)npad);
     if (method == 3)
@@ -745,7 +720,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     float* q = grow<float>(c, c->v[7], n4);
     MPM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n3, st));
     MPM_CUDA(cudaMemsetAsync(slot, 0, sizeof(double), st));
-    MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, residual_split(c, m, Kf, x), b, ptr<int>(m->dof_mask), r64, slot));
+    MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, residual_split(c, m, Kf, x), b, ptr<int>(m->dof_mask), r64, slot, gred));
     MPM_CUDA(cudaMemcpyAsync(c->h_red + 60, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
     double bb = c->h_red[60], rr = bb;
@@ -770,7 +745,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
       }
       MPM_LAUNCH(k_axpy_f2d<<<grid_for(n3, 256), 256, 0, st>>>(n3, x, d32));
       MPM_CUDA(cudaMemsetAsync(slot, 0, sizeof(double), st));
-      MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, residual_split(c, m, Kf, x), b, ptr<int>(m->dof_mask), r64, slot));
+      MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, residual_split(c, m, Kf, x), b, ptr<int>(m->dof_mask), r64, slot, gred));
       MPM_CUDA(cudaMemcpyAsync(c->h_red + 60, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
       MPM_CUDA(cudaStreamSynchronize(st));
       rr = c->h_red[60];
@@ -815,22 +790,35 @@ namespace {
 constexpr size_t kStaticBytes = size_t(32) << 20;  // 32 MiB
 static __device__ __align__(256) unsigned char g_pcg_scratch[kStaticBytes];
 
-constexpr int kMaxDevices = 64;
-unsigned char* g_pcg_scratch_dev[kMaxDevices] = {};
+// layout of the array: Krylov scalars, the grid-sum ticket, the per-block
+// partial sums (kStaticParts doubles), then the work vectors
+constexpr size_t kStaticScal = 256, kStaticTicket = 256, kStaticParts = 2048;
+constexpr size_t kStaticHead = kStaticScal + kStaticTicket + kStaticParts * sizeof(double);
 
-// device address of g_pcg_scratch on the current device (looked up once per device)
+constexpr int kMaxDevices = 64;
+std::atomic<unsigned char*> g_pcg_scratch_dev[kMaxDevices];
+
+// device address of g_pcg_scratch on the context's device, looked up once per
+// device; the context's device must be the current one (the address belongs
+// to the device current at the lookup)
 unsigned char* static_scratch(mpm_ctx* c) {
   int dev = 0;
   MPM_CUDA(cudaGetDevice(&dev));
+  if (dev != c->device)
+    throw CudaError(MPM_ERR_ARG, "mpm_solve_static: the context's device (" + std::to_string(c->device) +
+                                     ") is not the current device (" + std::to_string(dev) + ")");
   if (dev < 0 || dev >= kMaxDevices) throw CudaError(MPM_ERR_ARG, "device ordinal out of range");
-  if (!g_pcg_scratch_dev[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
+  unsigned char* p = g_pcg_scratch_dev[dev].load(std::memory_order_acquire);
+  if (!p) {
+    void* q = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&q, g_pcg_scratch);
     if (e != cudaSuccess)
       throw CudaError(MPM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_pcg_scratch_dev[dev] = (unsigned char*)p;
+    // two threads racing here look up the same address
+    g_pcg_scratch_dev[dev].store((unsigned char*)q, std::memory_order_release);
+    p = (unsigned char*)q;
   }
-  return g_pcg_scratch_dev[dev];
+  return p;
 }
 
 }  // namespace
@@ -843,10 +831,10 @@ extern "C" int mpm_solve_static(mpm_ctx* c, const mpm_mesh* m, const double* K, 
                                 double* x, double tol, int maxit, mpm_solve_stats* stats) {
   if (!c || !m || !K || !rhs || !x || !m->built || !(tol > 0) || maxit <= 0) return MPM_ERR_ARG;
   int nd = m->ndof, npad = 32 * m->nslice;
-  // layout: scalars (256 B), then r, z, p, q (4 per row over the padded rows)
-  // and the 3x3 inverses (12 per row)
-  size_t need = 256 + sizeof(double) * (size_t)npad * (4 * 4 + 12);
-  const size_t max_rows = (kStaticBytes - 256) / (28 * sizeof(double));
+  // layout: scalars, ticket and partial sums (kStaticHead bytes), then r, z,
+  // p, q (4 per row over the padded rows) and the 3x3 inverses (12 per row)
+  size_t need = kStaticHead + sizeof(double) * (size_t)npad * (4 * 4 + 12);
+  const size_t max_rows = (kStaticBytes - kStaticHead) / (28 * sizeof(double));
   if (need > kStaticBytes) {
     set_error(c, "mpm_solve_static: " + std::to_string(nd) + " dofs need " + std::to_string(need) +
                      " bytes of scratch, the static array holds " + std::to_string(kStaticBytes) +
@@ -857,7 +845,9 @@ extern "C" int mpm_solve_static(mpm_ctx* c, const mpm_mesh* m, const double* K, 
     cudaStream_t st = c->stream;
     unsigned char* base = static_scratch(c);
     Scal* sc = (Scal*)base;
-    double* r = (double*)(base + 256);
+    unsigned* ticket = (unsigned*)(base + kStaticScal);
+    GridRed gr{(double*)(base + kStaticScal + kStaticTicket), ticket};
+    double* r = (double*)(base + kStaticHead);
     double* z = r + 4 * (size_t)npad;
     double* p = z + 4 * (size_t)npad;
     double* q = p + 4 * (size_t)npad;
@@ -868,10 +858,15 @@ extern "C" int mpm_solve_static(mpm_ctx* c, const mpm_mesh* m, const double* K, 
     // the array keeps the previous call's contents: every vector below is
     // written before it is read, and the scalars start from zero
     MPM_CUDA(cudaMemsetAsync(sc, 0, sizeof(Scal), st));
+    MPM_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
     MPM_LAUNCH(k_block_jacobi<double, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, K, Dinv, c->d_err));
     int vb = 4 * 152;
-    MPM_LAUNCH(k_pcg_init<double><<<vb, 256, 0, st>>>(nd, npad, rhs, ptr<int>(m->dof_mask), Dinv, x, r, z, p, sc));
-    MPM_LAUNCH(k_pcg_q0<double, double><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, p, q, sc));
+    // every grid sum below has at most max(vb, npad / 256) blocks of 2 values
+    static_assert(2 * 4 * 152 <= kStaticParts, "partial sums of the vector kernels");
+    static_assert((kStaticBytes / (28 * sizeof(double)) / 256 + 1) <= kStaticParts,
+                  "partial sums of the row kernels");
+    MPM_LAUNCH(k_pcg_init<double><<<vb, 256, 0, st>>>(nd, npad, rhs, ptr<int>(m->dof_mask), Dinv, x, r, z, p, sc, gr));
+    MPM_LAUNCH(k_pcg_q0<double, double><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, p, q, sc, gr));
     Scal* h = (Scal*)(c->h_red + 32);
     MPM_CUDA(cudaMemcpyAsync(h, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
@@ -884,8 +879,8 @@ extern "C" int mpm_solve_static(mpm_ctx* c, const mpm_mesh* m, const double* K, 
       while (k < maxit) {
         int kend = std::min(maxit, k + 32);
         for (; k < kend; ++k) {
-          MPM_LAUNCH(k_pcg_a<double><<<vb, 256, 0, st>>>(nd, k, Dinv, x, r, z, p, q, sc));
-          MPM_LAUNCH(k_pcg_b<double, double><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, k, S, K, z, p, q, sc));
+          MPM_LAUNCH(k_pcg_a<double><<<vb, 256, 0, st>>>(nd, k, Dinv, x, r, z, p, q, sc, gr));
+          MPM_LAUNCH(k_pcg_b<double, double><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, k, S, K, z, p, q, sc, gr));
         }
         MPM_CUDA(cudaMemcpyAsync(h, sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
         MPM_CUDA(cudaStreamSynchronize(st));

@@ -360,7 +360,18 @@ def solve(ctx, mesh, cfg, K, rhs, precision=FP64, tol=1e-10, maxit=20000, method
 
 def solve_static(ctx, mesh, K, rhs, tol=1e-10, maxit=20000):
     """mpm_solve_static: FP64 block-Jacobi PCG whose scratch is the library's
-    static device array, so the call allocates no device memory."""
+    static device array, so the call allocates no device memory.  K must be the
+    FP64 values of mpm_assemble (9 * nslot doubles) and rhs 3 * ndof doubles,
+    both contiguous on the current CUDA device: the library cannot check the
+    size of a device buffer, so they are checked here."""
+    info = mesh.info()
+    dev = torch.cuda.current_device()
+    for name, t, n in (("K", K, 9 * max(info["nslot"], 1)), ("rhs", rhs, 3 * info["ndof"])):
+        ok = (isinstance(t, torch.Tensor) and t.dtype == torch.float64 and t.is_cuda and
+              t.device.index == dev and t.is_contiguous() and t.numel() == n)
+        if not ok:
+            raise MPMError(1, "solve_static: %s must be a contiguous float64 tensor of %d entries "
+                              "on cuda:%d" % (name, n, dev))
     x = torch.empty_like(rhs)
     ss = SolveStats()
     st = lib().mpm_solve_static(ctx.h, mesh.h, _p(K), _p(rhs), _p(x), tol, maxit, C.byref(ss))

@@ -53,11 +53,11 @@ def test_static_solve_rejects_meshes_beyond_its_limit():
     P = mpm.Points(pts, capacity=2 * len(pts["x"]))
     mesh = mpm.octree_build(ctx, cfg, P, body_z=inputs.body_z(cfg, 1))
     info = mesh.info()
-    if info["ndof"] <= 149792:
+    if info["ndof"] <= 149696:
         pytest.skip("mesh within the static limit")
     K = torch.zeros(9 * info["nslot"], dtype=torch.float64, device="cuda")
     rhs = torch.zeros(3 * info["ndof"], dtype=torch.float64, device="cuda")
     with pytest.raises(mpm.MPMError) as e:
         mpm.solve_static(ctx, mesh, K, rhs)
-    assert e.value.code == 1 and "149792" in str(e.value)
+    assert e.value.code == 1 and "149696" in str(e.value)
     ctx.close()
