@@ -59,7 +59,8 @@ class Params(C.Structure):
                 ("dx_region", C.c_double), ("beta", C.c_double),
                 ("model", C.c_int), ("nu", C.c_double), ("phi", C.c_double), ("psi", C.c_double),
                 ("g", C.c_double * 3), ("kappa", C.c_double), ("pf", C.c_double),
-                ("ghost_on", C.c_int), ("contact_on", C.c_int)]
+                ("ghost_on", C.c_int), ("contact_on", C.c_int),
+                ("mu", C.c_double), ("pt", C.c_double), ("body_d", C.c_double * 3)]
 
 
 class Counts(C.Structure):
@@ -102,6 +103,11 @@ def params_from_cfg(cfg, body_z=None):
         p.g[d] = cfg["g"][d]
     p.kappa, p.pf = cfg.get("kappa", 10.0), cfg.get("pf", 50.0)
     p.ghost_on, p.contact_on = int(cfg.get("ghost", 1)), int(cfg.get("contact", 1))
+    p.mu, p.pt = cfg.get("mu", 0.0), cfg.get("pt", 25.0)
+    if b:
+        d = b.get("step_d", (0.0, 0.0, b.get("dz", 0.0)))
+        for k in range(3):
+            p.body_d[k] = d[k]
     return p
 
 

@@ -54,6 +54,11 @@ typedef struct {
   /* ghost (Sec. 4) and contact (Sec. 2.3) constants */
   double kappa, pf;
   int ghost_on, contact_on;
+  /* Coulomb friction (Sec. 2.3): coefficient mu, tangential penalty factor pt
+   * (eps_T = pt E_p (V0_p)^(2/3)), and the body's translation over the current
+   * load step, against which the contact nodes' slip is measured */
+  double mu, pt;
+  double body_d[3];
 } o_params;
 
 typedef struct o_model o_model;

@@ -210,6 +210,43 @@ int o_point_stress(o_model* m, const double* du, double* sigma) {
   return O_OK;
 }
 
+/* Coulomb friction at a contact node (Sec. 2.3: stick-slip regularised by the
+ * tangential penalty eps_T = pt E_p (V0_p)^(2/3)).  Reading: the slip is the
+ * node's displacement relative to the body over the current load step,
+ * g = (y - y0) - d_body, projected on the tangent plane; no tangential force
+ * is carried from one load step to the next.  Trial force t = -eps_T (I - n n^T) g;
+ * stick if |t| <= mu f_N, else slip with mu f_N t / |t|.  Adds the force to f
+ * and its stiffness -d f / d y to kc (non-symmetric when slipping). */
+static void friction(const o_params* p, double E, double V0, const double* y, const double* y0,
+                     const double* n, const double* H, double fN, double epsN, double* f,
+                     double* kc) {
+  double epsT = p->pt * E * pow(V0, 2.0 / 3.0);
+  double g[3], t[3], Hg[3], D[9];
+  for (int d = 0; d < 3; ++d) g[d] = (y[d] - y0[d]) - p->body_d[d];
+  double ng = n[0] * g[0] + n[1] * g[1] + n[2] * g[2];
+  for (int a = 0; a < 3; ++a) Hg[a] = H[3 * a] * g[0] + H[3 * a + 1] * g[1] + H[3 * a + 2] * g[2];
+  for (int d = 0; d < 3; ++d) t[d] = -epsT * (g[d] - n[d] * ng);
+  /* D = d t / d y = -eps_T (I - n n^T - (n.g) H - n (H g)^T) */
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      D[3 * a + b] = -epsT * ((a == b ? 1.0 : 0.0) - n[a] * n[b] - ng * H[3 * a + b] - n[a] * Hg[b]);
+  double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+  if (tn <= p->mu * fN) {
+    for (int d = 0; d < 3; ++d) f[d] += t[d];
+    for (int q = 0; q < 9; ++q) kc[q] -= D[q];
+    return;
+  }
+  double u[3] = {t[0] / tn, t[1] / tn, t[2] / tn};
+  for (int d = 0; d < 3; ++d) f[d] += p->mu * fN * u[d];
+  /* d(mu f_N u)/dy = mu u (d f_N/dy)^T + mu f_N (I - u u^T) D / |t|, d f_N/dy = -eps_N n */
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double s = 0.0;
+      for (int c = 0; c < 3; ++c) s += ((a == c ? 1.0 : 0.0) - u[a] * u[c]) * D[3 * c + b];
+      kc[3 * a + b] -= p->mu * u[a] * (-epsN * n[b]) + p->mu * fN * s / tn;
+    }
+}
+
 int o_assemble(o_model* m, const double* du, double load, double* R, double* Kv, double* fint_all,
                double* reaction) {
   int ndof = m->nd.ndof;
@@ -316,6 +353,7 @@ int o_assemble(o_model* m, const double* du, double load, double* R, double* Kv,
         }
         int K = corner_leaf(m, X, side, xi);
         o_leaf_basis(m, K, xi, &nent, idx, ph, dph);
+        double y0[3] = {y[0], y[1], y[2]};
         for (int i = 0; i < nent; ++i) {
           idx[i] = m->nd.dof[idx[i]];
           for (int d = 0; d < 3; ++d) y[d] += ph[i] * du[3 * idx[i] + d];
@@ -323,8 +361,13 @@ int o_assemble(o_model* m, const double* du, double load, double* R, double* Kv,
         double phi, n[3], H[9];
         o_body_sdf(&m->p, y, &phi, n, H);
         if (!(phi < 0.0)) continue;
-        double f[3];
-        for (int d = 0; d < 3; ++d) f[d] = -epsN * phi * n[d];
+        /* normal force f_N n, f_N = -eps_N phi, and kc = -d f / d y */
+        double fN = -epsN * phi, f[3], kc[9];
+        for (int d = 0; d < 3; ++d) f[d] = fN * n[d];
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) kc[3 * a + b] = epsN * (n[a] * n[b] + phi * H[3 * a + b]);
+        if (m->p.mu > 0.0)
+          friction(&m->p, m->E[p], m->V0[p], y, y0, n, H, fN, epsN, f, kc);
         if (reaction)
           for (int d = 0; d < 3; ++d) reaction[d] -= f[d];
         for (int i = 0; i < nent; ++i)
@@ -333,9 +376,6 @@ int o_assemble(o_model* m, const double* du, double load, double* R, double* Kv,
             fext_c[3 * idx[i] + d] += ph[i] * f[d];
           }
         if (Kv) {
-          double kc[9];
-          for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) kc[3 * a + b] = epsN * (n[a] * n[b] + phi * H[3 * a + b]);
           for (int a = 0; a < nent; ++a)
             for (int b = 0; b < nent; ++b) {
               int sl = o_find_slot(m, idx[a], idx[b]);
@@ -472,7 +512,9 @@ int o_solve(o_model* m, const double* Kv, const double* b, double* x, double tol
   double* q = (double*)malloc(sizeof(double) * (size_t)n3);
   for (int i = 0; i < n3; ++i) r[i] = (m->bcmask[i / 3] & (1 << (i % 3))) ? 0.0 : b[i];
   double bn = sqrt(dot(n3, r, r));
-  int nonsym = m->p.model == 2 && m->p.psi != m->p.phi;
+  /* friction makes the contact stiffness non-symmetric */
+  int nonsym = (m->p.model == 2 && m->p.psi != m->p.phi) ||
+               (m->p.mu > 0.0 && m->p.contact_on && m->p.body_kind != 0);
   st = O_ERR_KRYLOV;
   if (bn == 0.0) {
     st = O_OK;

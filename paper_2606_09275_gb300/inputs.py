@@ -80,7 +80,8 @@ def _block_rollers(x1, y1, fixed_base=True):
             (2, 0.0, FIXED if fixed_base else ROLLER_Z)]
 
 
-_BASE = dict(beta=2.0, nu=0.3, phi=0.0, psi=0.0, g=(0.0, 0.0, 0.0), kappa=10.0, pf=50.0,
+_BASE = dict(beta=2.0, nu=0.3, phi=0.0, psi=0.0, g=(0.0, 0.0, 0.0), kappa=10.0, pf=50.0, pt=25.0,
+             mu=0.0,
              ghost=1, contact=1, body=None, dx_region=0.0, ramp_load=False,
              newton_tol=1e-8, newton_maxit=30, lin_tol=1e-8, lin_maxit=20000)
 
@@ -123,6 +124,20 @@ def workload(name, **over):
                  dx_region=2.0 / 32, nsteps=20,
                  points=dict(lo=(0, 0, 0), hi=(1, 1, 0.5), spacing=1.0 / 16, rho=1000.0,
                              E=1e7, ys=1e5, E_sigma=0.2, seed=0))
+    elif name == "cone_1m":
+        # the cone of "cone" at the ~1M-DOF scale: the same Drucker-Prager layer
+        # and cone on a depth-6 far field (0.025 m cells, 2x2x2 points per cell,
+        # jittered by U(-h/8, h/8)) refined to depth 8 (6.25 mm) within a wider
+        # region around the cone (0.3 m), so that the adapted mesh has about a
+        # million unknowns; the GIMP split grows the points about 4.8 times
+        # (cap_factor: the point capacity to allocate, in initial points)
+        c.update(L=1.6, depth_min=6, depth_max=8, bc=_block_rollers(1.0, 1.0), model=2,
+                 phi=math.radians(30.0), psi=0.0,
+                 body=dict(kind=2, cx=0.5, cy=0.5, z0=1.2, r=0.018, alpha=math.radians(30.0),
+                           dz=-0.3 / 200),
+                 dx_region=0.3, nsteps=200, cap_factor=6,
+                 points=dict(lo=(0, 0, 0), hi=(1, 1, 1.2), spacing=0.0125, rho=1000.0,
+                             E=2e7, ys=5e3, jitter=0.0125 / 4, seed=0))
     elif name == "indent":
         # indentation at the ~1M-DOF scale: the punch physics of "punch" on a depth 6
         # far field (2x2x2 jittered points per cell, U(-h/8, h/8)) refined to depth

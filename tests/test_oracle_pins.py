@@ -937,3 +937,93 @@ def test_global_tangent_matches_finite_difference_with_cone_contact():
             for s_ in range(rp[i], rp[i + 1]):
                 Kv[3 * i:3 * i + 3] += K[s_] @ v[3 * col[s_]:3 * col[s_] + 3]
         assert np.linalg.norm(Kv - fd) <= 1e-6 * np.linalg.norm(fd)
+
+
+# ---------------------------------------------------------------- Coulomb friction (Sec. 2.3)
+#
+# Reading: the slip of a contact node is its displacement relative to the body
+# over the load step, projected on the tangent plane; eps_T = 25 E_p A_p^0
+# (Sec. 2.3), stick while the tangential penalty force stays within mu f_N.
+
+def friction_cfg(mu, d):
+    cfg = tiny_cfg(ghost=0, model=0, mu=mu)
+    cfg["body"]["step_d"] = (d, 0.0, 0.0)
+    return cfg
+
+
+@pytest.mark.parametrize("regime", ["stick", "slip"])
+def test_friction_stick_and_slip_by_hand(regime):
+    # at du = 0 every corner under the punch face has penetration pen = 0.01 m
+    # and slips by -d relative to the body moving by (d, 0, 0): stick gives
+    # f_x = eps_T d, slip gives f_x = mu eps_N pen; stick iff 25 d <= 50 mu pen
+    g = read_golden("paper_constants.txt")
+    mu, pen = 0.3, 0.01
+    d = (0.5 if regime == "stick" else 4.0) * 2 * mu * pen * g["contact_normal_factor"][0] / (
+        2 * g["contact_tangential_factor"][0])
+    cfg = friction_cfg(mu, d)
+    assert cfg["pt"] == g["contact_tangential_factor"][0]
+    m = built(cfg, body_z=0.49)
+    out = m.assemble(np.zeros(3 * m.counts()["ndof"]))
+    P = m.points()
+    ex, ez = 0.0, 0.0
+    for p in range(len(P["x"])):
+        top = P["x"][p, 2] + P["lp"][p, 2]
+        r = np.hypot(P["x"][p, 0] + np.array([-1, 1, -1, 1]) * P["lp"][p, 0] - 0.3,
+                     P["x"][p, 1] + np.array([-1, -1, 1, 1]) * P["lp"][p, 1] - 0.4)
+        if top - 0.49 <= 0:
+            continue
+        assert np.all((r > 0.1) | (0.1 - r > pen))  # every touching corner is under the face
+        A = P["V0"][p] ** (2 / 3)
+        k = np.sum(r < 0.1)
+        fN = 50 * P["E"][p] * A * pen
+        ft = 25 * P["E"][p] * A * d if regime == "stick" else mu * fN
+        ez += k * fN
+        ex += k * ft
+    assert ex > 0
+    # reaction = force on the body = -(force on the material)
+    assert abs(out["reaction"][2] - ez) < 1e-9 * ez
+    assert abs(out["reaction"][0] + ex) < 1e-9 * ex
+    assert abs(out["reaction"][1]) < 1e-9 * ex
+
+
+def test_friction_free_limit_is_frictionless():
+    a = built(tiny_cfg(ghost=0, model=0), body_z=0.49)
+    b = built(friction_cfg(0.0, 0.02), body_z=0.49)
+    du = 1e-3 * np.random.default_rng(4).normal(size=3 * a.counts()["ndof"])
+    oa, ob = a.assemble(du), b.assemble(du)
+    assert np.array_equal(oa["R"], ob["R"]) and np.array_equal(oa["K"], ob["K"])
+
+
+@pytest.mark.parametrize("mu", [0.05, 5.0])
+def test_frictional_tangent_matches_finite_difference(mu):
+    # mu = 0.05: most touching corners slip; mu = 5: all stick.  The body moves
+    # sideways over the step so the tangential forces are not zero.
+    cfg = friction_cfg(mu, 0.004)
+    cfg["points"].update(jitter=0.02, seed=9)
+    m = built(cfg, body_z=0.49)
+    c = m.counts()
+    n3 = 3 * c["ndof"]
+    rng = np.random.default_rng(12)
+    du = 1e-3 * rng.normal(size=n3)
+    out = m.assemble(du)
+    rp, col = m.pattern()
+    K = out["K"]
+    h = 1e-7
+    for _ in range(3):
+        v = rng.normal(size=n3)
+        Rp = m.assemble(du + h * v, tangent=False)["R"]
+        Rm = m.assemble(du - h * v, tangent=False)["R"]
+        fd = (Rp - Rm) / (2 * h)
+        Kv = np.zeros(n3)
+        for i in range(c["ndof"]):
+            for s_ in range(rp[i], rp[i + 1]):
+                Kv[3 * i:3 * i + 3] += K[s_] @ v[3 * col[s_]:3 * col[s_] + 3]
+        assert np.linalg.norm(Kv - fd) <= 1e-6 * np.linalg.norm(fd)
+    if mu < 1:
+        # slipping friction: the contact stiffness is not symmetric
+        n = c["ndof"]
+        G = np.zeros((n3, n3))
+        for i in range(n):
+            for s_ in range(rp[i], rp[i + 1]):
+                G[3 * i:3 * i + 3, 3 * col[s_]:3 * col[s_] + 3] = K[s_]
+        assert np.abs(G - G.T).max() > 1e-6 * np.abs(G).max()
