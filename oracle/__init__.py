@@ -60,7 +60,9 @@ class Params(C.Structure):
                 ("model", C.c_int), ("nu", C.c_double), ("phi", C.c_double), ("psi", C.c_double),
                 ("g", C.c_double * 3), ("kappa", C.c_double), ("pf", C.c_double),
                 ("ghost_on", C.c_int), ("contact_on", C.c_int),
-                ("mu", C.c_double), ("pt", C.c_double), ("body_d", C.c_double * 3)]
+                ("mu", C.c_double), ("pt", C.c_double), ("body_d", C.c_double * 3),
+                ("ntri", C.c_int), ("nvert", C.c_int), ("tri_v", C.c_void_p),
+                ("tri_t", C.c_void_p)]
 
 
 class Counts(C.Structure):
@@ -108,6 +110,13 @@ def params_from_cfg(cfg, body_z=None):
         d = b.get("step_d", (0.0, 0.0, b.get("dz", 0.0)))
         for k in range(3):
             p.body_d[k] = d[k]
+        if b["kind"] == 3:
+            # the triangulated surface: host arrays kept alive by the struct
+            v = np.ascontiguousarray(b["mesh"]["v"], dtype=np.float64)
+            t = np.ascontiguousarray(b["mesh"]["t"], dtype=np.int32)
+            p._keep = (v, t)
+            p.nvert, p.ntri = len(v), len(t)
+            p.tri_v, p.tri_t = v.ctypes.data, t.ctypes.data
     return p
 
 

@@ -59,6 +59,14 @@ typedef struct {
    * load step, against which the contact nodes' slip is measured */
   double mu, pt;
   double body_d[3];
+  /* body_kind 3: a closed triangulated surface (Sec. 2.3 represents the rigid
+   * bodies by closed triangular faceted meshes): nvert vertices (x, y, z,
+   * relative to the body's reference point (body_cx, body_cy, body_z)) and
+   * ntri triangles (three vertex indices each, counter-clockwise seen from
+   * outside), host arrays */
+  int ntri, nvert;
+  const double* tri_v;
+  const int* tri_t;
 } o_params;
 
 typedef struct o_model o_model;

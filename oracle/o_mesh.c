@@ -158,14 +158,221 @@ static int tree_balance(o_tree* t, int D) {
 
 /* ---------------- rigid body geometry (Sec. 2.3; analytic surfaces) ---------------- */
 
+/* ---- closed triangulated body (kind 3) ----
+ * The signed distance is taken from the nearest point q of the surface over
+ * all triangles (the first triangle attaining the smallest distance); the
+ * sign is that of (x - q) . N with N the pseudo-normal of the feature that
+ * holds q: the face normal, the sum of the two face normals at an edge, or
+ * the angle-weighted sum of the face normals at a vertex (Baerentzen and
+ * Aanaes, signed distance by angle-weighted pseudo-normals). */
+
+static void tvert(const o_params* p, int v, double* o) {
+  o[0] = p->tri_v[3 * v] + p->body_cx;
+  o[1] = p->tri_v[3 * v + 1] + p->body_cy;
+  o[2] = p->tri_v[3 * v + 2] + p->body_z;
+}
+
+static void sub3(const double* a, const double* b, double* o) {
+  for (int d = 0; d < 3; ++d) o[d] = a[d] - b[d];
+}
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double* a, const double* b, double* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* unit normal of triangle t */
+static void tri_normal(const o_params* p, int t, double* n) {
+  double a[3], b[3], c[3], u[3], v[3];
+  tvert(p, p->tri_t[3 * t], a);
+  tvert(p, p->tri_t[3 * t + 1], b);
+  tvert(p, p->tri_t[3 * t + 2], c);
+  sub3(b, a, u);
+  sub3(c, a, v);
+  cross3(u, v, n);
+  double l = sqrt(dot3(n, n));
+  for (int d = 0; d < 3; ++d) n[d] /= l;
+}
+
+/* nearest point q of triangle (a, b, c) to x by the Voronoi regions of its
+ * vertices, edges and face; feat: 0 face, 1 edge ab, 2 edge bc, 3 edge ca,
+ * 4 vertex a, 5 vertex b, 6 vertex c */
+static void tri_nearest(const double* x, const double* a, const double* b, const double* c,
+                        double* q, int* feat) {
+  double ab[3], ac[3], ax[3], bx[3], cx[3];
+  sub3(b, a, ab);
+  sub3(c, a, ac);
+  sub3(x, a, ax);
+  double d1 = dot3(ab, ax), d2 = dot3(ac, ax);
+  if (d1 <= 0.0 && d2 <= 0.0) {
+    for (int d = 0; d < 3; ++d) q[d] = a[d];
+    *feat = 4;
+    return;
+  }
+  sub3(x, b, bx);
+  double d3 = dot3(ab, bx), d4 = dot3(ac, bx);
+  if (d3 >= 0.0 && d4 <= d3) {
+    for (int d = 0; d < 3; ++d) q[d] = b[d];
+    *feat = 5;
+    return;
+  }
+  double vc = d1 * d4 - d3 * d2;
+  if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
+    double v = d1 / (d1 - d3);
+    for (int d = 0; d < 3; ++d) q[d] = a[d] + v * ab[d];
+    *feat = 1;
+    return;
+  }
+  sub3(x, c, cx);
+  double d5 = dot3(ab, cx), d6 = dot3(ac, cx);
+  if (d6 >= 0.0 && d5 <= d6) {
+    for (int d = 0; d < 3; ++d) q[d] = c[d];
+    *feat = 6;
+    return;
+  }
+  double vb = d5 * d2 - d1 * d6;
+  if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
+    double w = d2 / (d2 - d6);
+    for (int d = 0; d < 3; ++d) q[d] = a[d] + w * ac[d];
+    *feat = 3;
+    return;
+  }
+  double va = d3 * d6 - d5 * d4;
+  if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) {
+    double w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    for (int d = 0; d < 3; ++d) q[d] = b[d] + w * (c[d] - b[d]);
+    *feat = 2;
+    return;
+  }
+  double den = 1.0 / (va + vb + vc), v = vb * den, w = vc * den;
+  for (int d = 0; d < 3; ++d) q[d] = a[d] + v * ab[d] + w * ac[d];
+  *feat = 0;
+}
+
+/* pseudo-normal of feature `feat` of triangle t (any length; its sign matters) */
+static void tri_pseudo_normal(const o_params* p, int t, int feat, double* N) {
+  const int* T = p->tri_t;
+  tri_normal(p, t, N);
+  if (feat == 0) return;
+  if (feat <= 3) {
+    int i = T[3 * t + feat - 1], j = T[3 * t + feat % 3];
+    for (int u = 0; u < p->ntri; ++u) {
+      if (u == t) continue;
+      int has_i = 0, has_j = 0;
+      for (int k = 0; k < 3; ++k) {
+        has_i |= T[3 * u + k] == i;
+        has_j |= T[3 * u + k] == j;
+      }
+      if (has_i && has_j) {
+        double n2[3];
+        tri_normal(p, u, n2);
+        for (int d = 0; d < 3; ++d) N[d] += n2[d];
+        return;
+      }
+    }
+    return;
+  }
+  int v = T[3 * t + feat - 4];
+  for (int d = 0; d < 3; ++d) N[d] = 0.0;
+  for (int u = 0; u < p->ntri; ++u)
+    for (int k = 0; k < 3; ++k) {
+      if (T[3 * u + k] != v) continue;
+      double a[3], b[3], c[3], e1[3], e2[3], n2[3];
+      tvert(p, v, a);
+      tvert(p, T[3 * u + (k + 1) % 3], b);
+      tvert(p, T[3 * u + (k + 2) % 3], c);
+      sub3(b, a, e1);
+      sub3(c, a, e2);
+      double cs = dot3(e1, e2) / sqrt(dot3(e1, e1) * dot3(e2, e2));
+      double ang = acos(cs < -1.0 ? -1.0 : (cs > 1.0 ? 1.0 : cs));
+      tri_normal(p, u, n2);
+      for (int d = 0; d < 3; ++d) N[d] += ang * n2[d];
+    }
+}
+
+/* signed distance of the triangulated body at x, with its gradient n and
+ * Hessian H (zero on a face; (I - e e^T - u u^T)/phi at an edge of direction
+ * e and (I - u u^T)/phi at a vertex, u = (x - q)/|x - q|) */
+static double tri_sdf(const o_params* p, const double* x, double* n, double* H) {
+  double best = INFINITY, qb[3] = {0, 0, 0};
+  int tb = -1, fb = 0;
+  for (int t = 0; t < p->ntri; ++t) {
+    double a[3], b[3], c[3], q[3];
+    int f;
+    tvert(p, p->tri_t[3 * t], a);
+    tvert(p, p->tri_t[3 * t + 1], b);
+    tvert(p, p->tri_t[3 * t + 2], c);
+    tri_nearest(x, a, b, c, q, &f);
+    double r[3];
+    sub3(x, q, r);
+    double d2 = dot3(r, r);
+    if (d2 < best) {
+      best = d2;
+      tb = t;
+      fb = f;
+      for (int d = 0; d < 3; ++d) qb[d] = q[d];
+    }
+  }
+  if (n) n[0] = n[1] = n[2] = 0.0;
+  if (H)
+    for (int i = 0; i < 9; ++i) H[i] = 0.0;
+  if (tb < 0) return INFINITY;
+  double dist = sqrt(best), N[3], r[3], nt[3], cr[3];
+  sub3(x, qb, r);
+  /* x - q along the nearest triangle's normal: q lies on that face's plane
+   * (its edge or vertex only bounds it), so the surface is flat there: face */
+  tri_normal(p, tb, nt);
+  cross3(r, nt, cr);
+  if (fb != 0 && dot3(cr, cr) <= 1e-24 * best) fb = 0;
+  tri_pseudo_normal(p, tb, fb, N);
+  double sg = dot3(r, N) < 0.0 ? -1.0 : 1.0;
+  double phi = sg * dist;
+  if (!(dist > 0.0)) return 0.0;
+  double u[3] = {r[0] / dist, r[1] / dist, r[2] / dist};
+  if (n) {
+    if (fb == 0) {
+      tri_normal(p, tb, n);
+    } else {
+      for (int d = 0; d < 3; ++d) n[d] = sg * u[d];
+    }
+  }
+  if (H && fb != 0) {
+    double e[3] = {0, 0, 0};
+    if (fb <= 3) {
+      double a[3], b[3];
+      tvert(p, p->tri_t[3 * tb + fb - 1], a);
+      tvert(p, p->tri_t[3 * tb + fb % 3], b);
+      sub3(b, a, e);
+      double l = sqrt(dot3(e, e));
+      for (int d = 0; d < 3; ++d) e[d] /= l;
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        H[3 * i + j] = ((i == j ? 1.0 : 0.0) - e[i] * e[j] - u[i] * u[j]) / phi;
+  }
+  return phi;
+}
+
 static double dist_xy_rect(const o_params* p, const double* lo, const double* hi) {
   double dx = fmax(fmax(lo[0] - p->body_cx, 0.0), p->body_cx - hi[0]);
   double dy = fmax(fmax(lo[1] - p->body_cy, 0.0), p->body_cy - hi[1]);
   return sqrt(dx * dx + dy * dy);
 }
 
-/* Step 1 of Sec. 5: does the closed box meet the solid body? */
+/* Step 1 of Sec. 5: does the closed box meet the solid body?  For the
+ * triangulated body (reading): when the ball around the box (centre, half
+ * diagonal) meets it, i.e. the signed distance at the centre is at most the
+ * half diagonal. */
 static int body_box_intersect(const o_params* p, const double* lo, const double* hi) {
+  if (p->body_kind == 3) {
+    double c[3], h2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      c[d] = 0.5 * (lo[d] + hi[d]);
+      h2 += 0.25 * (hi[d] - lo[d]) * (hi[d] - lo[d]);
+    }
+    return tri_sdf(p, c, NULL, NULL) <= sqrt(h2);
+  }
   if (p->body_kind == 1) {
     return hi[2] >= p->body_z && dist_xy_rect(p, lo, hi) <= p->body_r;
   }
@@ -188,6 +395,7 @@ static double seg_dist(double px, double pz, double ax, double az, double bx, do
 
 /* Step 2 of Sec. 5: Euclidean distance from a node to the solid (0 inside) */
 static double body_dist(const o_params* p, const double* x) {
+  if (p->body_kind == 3) return fmax(tri_sdf(p, x, NULL, NULL), 0.0);
   double rx = x[0] - p->body_cx, ry = x[1] - p->body_cy;
   double rho = sqrt(rx * rx + ry * ry), z = x[2];
   if (p->body_kind == 1) {
@@ -212,6 +420,13 @@ static double body_dist(const o_params* p, const double* x) {
 /* Signed distance used by the penalty contact (negative inside the body),
  * its gradient n (unit outward normal) and Hessian H. */
 int o_body_sdf(const o_params* p, const double* x, double* phi, double* n, double* H) {
+  if (p->body_kind == 3) {
+    *phi = tri_sdf(p, x, n, H);
+    if (*phi < 0.0) return 1;
+    for (int i = 0; i < 3; ++i) n[i] = 0.0;
+    for (int i = 0; i < 9; ++i) H[i] = 0.0;
+    return 0;
+  }
   double rx = x[0] - p->body_cx, ry = x[1] - p->body_cy;
   double rho = sqrt(rx * rx + ry * ry), z = x[2];
   for (int i = 0; i < 9; ++i) H[i] = 0.0;

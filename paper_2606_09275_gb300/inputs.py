@@ -65,6 +65,54 @@ def make_points(cfg):
                           E_sigma=pc.get("E_sigma", 0.0))
 
 
+def sphere_mesh(radius, nlat=40, nlon=40):
+    """Closed triangulated sphere on a latitude-longitude grid (the smallest
+    triangles at the poles): nlat bands, nlon sectors, 2 nlon (nlat - 1)
+    triangles (3120 for 40 x 40), counter-clockwise seen from outside, centred
+    on the origin."""
+    th = np.pi * np.arange(1, nlat) / nlat
+    ph = 2 * np.pi * np.arange(nlon) / nlon
+    v = [[0.0, 0.0, radius]]
+    for t in th:
+        for p in ph:
+            v.append([radius * math.sin(t) * math.cos(p), radius * math.sin(t) * math.sin(p),
+                      radius * math.cos(t)])
+    v.append([0.0, 0.0, -radius])
+    south = len(v) - 1
+    ring = lambda i, j: 1 + i * nlon + (j % nlon)
+    tri = []
+    for j in range(nlon):
+        tri.append([0, ring(0, j), ring(0, j + 1)])
+    for i in range(nlat - 2):
+        for j in range(nlon):
+            a, b, c, d = ring(i, j), ring(i, j + 1), ring(i + 1, j), ring(i + 1, j + 1)
+            tri.append([a, c, d])
+            tri.append([a, d, b])
+    for j in range(nlon):
+        tri.append([south, ring(nlat - 2, j + 1), ring(nlat - 2, j)])
+    return dict(v=np.array(v), t=np.array(tri, dtype=np.int32))
+
+
+def cylinder_mesh(radius, height, nside=64):
+    """Closed triangulated flat-ended cylinder (a prism of nside sides) with
+    its bottom face at z = 0 centred on the axis, counter-clockwise seen from
+    outside."""
+    ph = 2 * np.pi * np.arange(nside) / nside
+    v = [[0.0, 0.0, 0.0], [0.0, 0.0, height]]
+    for z in (0.0, height):
+        for p in ph:
+            v.append([radius * math.cos(p), radius * math.sin(p), z])
+    lo = lambda j: 2 + (j % nside)
+    hi = lambda j: 2 + nside + (j % nside)
+    tri = []
+    for j in range(nside):
+        tri.append([0, lo(j + 1), lo(j)])        # bottom, normal -z
+        tri.append([1, hi(j), hi(j + 1)])        # top, normal +z
+        tri.append([lo(j), lo(j + 1), hi(j + 1)])
+        tri.append([lo(j), hi(j + 1), hi(j)])
+    return dict(v=np.array(v), t=np.array(tri, dtype=np.int32))
+
+
 def body_z(cfg, step):
     """Vertical position of the rigid body at the end of load step `step` (1-based)."""
     b = cfg["body"]

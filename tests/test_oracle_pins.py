@@ -1027,3 +1027,119 @@ def test_frictional_tangent_matches_finite_difference(mu):
             for s_ in range(rp[i], rp[i + 1]):
                 G[3 * i:3 * i + 3, 3 * col[s_]:3 * col[s_] + 3] = K[s_]
         assert np.abs(G - G.T).max() > 1e-6 * np.abs(G).max()
+
+
+# ---------------------------------------------------------------- triangulated bodies (Sec. 2.3)
+#
+# Sec. 2.3 represents the rigid bodies by closed triangular faceted meshes.
+# The signed distance of such a body is checked against the distance to a
+# dense sampling of its triangles and, for the sign, against the analytic
+# solid it approximates (away from the band where the two differ).
+
+def mesh_samples(v, t, h):
+    """Points on every triangle, no surface point farther than about h."""
+    out = []
+    for a, b, c in t:
+        A, B, C = v[a], v[b], v[c]
+        L = max(np.linalg.norm(B - A), np.linalg.norm(C - A), np.linalg.norm(C - B))
+        k = max(1, int(math.ceil(L / h)))
+        i, j = np.meshgrid(np.arange(k + 1), np.arange(k + 1), indexing="ij")
+        sel = (i + j) <= k
+        u, w = i[sel] / k, j[sel] / k
+        out.append(A[None] + u[:, None] * (B - A)[None] + w[:, None] * (C - A)[None])
+    return np.concatenate(out)
+
+
+def sphere_body_cfg(radius=0.3, nlat=12, nlon=16, center=(0.5, 0.5, 0.7)):
+    cfg = tiny_cfg()
+    cfg["body"] = dict(kind=3, cx=center[0], cy=center[1], z0=center[2], r=radius, alpha=0.0,
+                       dz=-0.002, mesh=inputs.sphere_mesh(radius, nlat, nlon))
+    return cfg
+
+
+def test_triangulated_body_signed_distance_brute_force():
+    cfg = sphere_body_cfg()
+    b = cfg["body"]
+    c = np.array([b["cx"], b["cy"], b["z0"]])
+    v = b["mesh"]["v"] + c[None]
+    h = 4e-3
+    S = mesh_samples(v, b["mesh"]["t"], h)
+    rng = np.random.default_rng(21)
+    x = c[None] + rng.uniform(-0.45, 0.45, size=(300, 3))
+    phi, n, H, ins = oracle.body_sdf(cfg, x)
+    d = brute_dist(x, S)
+    assert np.all(np.abs(phi) <= d + 1e-12) and np.all(np.abs(phi) >= d - h)
+    # sign against the sphere, outside the band between the sphere and its
+    # inscribed polyhedron (chord sagitta of the coarsest triangles)
+    r = np.linalg.norm(x - c[None], axis=1)
+    band = b["r"] * (1 - math.cos(math.pi / 12))
+    far = np.abs(r - b["r"]) > band
+    assert far.sum() > 200
+    assert np.array_equal(ins[far], (r < b["r"])[far])
+    assert np.all(phi[ins] < 0) and np.all(phi[~ins] >= 0)
+    # inside, the normal is the nearest face's outward normal: the gradient of phi
+    e = 1e-6
+    xi = x[ins & far]
+    for dd in range(3):
+        dx = np.zeros(3)
+        dx[dd] = e
+        pp = oracle.body_sdf(cfg, xi + dx)[0]
+        pm = oracle.body_sdf(cfg, xi - dx)[0]
+        ok = np.abs((pp - pm) / (2 * e) - n[ins & far][:, dd]) < 1e-6
+        assert ok.mean() > 0.95  # the few misses sit on bisectors between faces
+
+
+def test_triangulated_punch_matches_analytic_punch_under_the_face():
+    # a 64-sided prism for the flat punch: corners under its bottom face see
+    # the same gap and normal as under the analytic cylinder's face, so the
+    # contact force (with friction) on the body is the same at du = 0 (the
+    # octrees differ, Step 1 being conservative for meshes: no GIMP split, and
+    # only the reaction, which does not depend on the background basis at
+    # du = 0, is compared)
+    mu = 0.3
+    a_cfg = friction_cfg(mu, 0.004)
+    t_cfg = friction_cfg(mu, 0.004)
+    for c in (a_cfg, t_cfg):
+        c["points"]["spacing"] = 0.125
+    t_cfg["body"] = dict(a_cfg["body"], kind=3, mesh=inputs.cylinder_mesh(0.1, 0.6, 64))
+    ma = built(a_cfg, body_z=0.49, nosplit=True)
+    mt = built(t_cfg, body_z=0.49, nosplit=True)
+    P = ma.points()
+    inner = 0.1 * math.cos(math.pi / 64)
+    for p in range(len(P["x"])):
+        if P["x"][p, 2] + P["lp"][p, 2] <= 0.49:
+            continue
+        r = np.hypot(P["x"][p, 0] + np.array([-1, 1, -1, 1]) * P["lp"][p, 0] - 0.3,
+                     P["x"][p, 1] + np.array([-1, -1, 1, 1]) * P["lp"][p, 1] - 0.4)
+        assert not np.any((r > inner - 0.011) & (r <= 0.1))
+    oa = ma.assemble(np.zeros(3 * ma.counts()["ndof"]))
+    ot = mt.assemble(np.zeros(3 * mt.counts()["ndof"]))
+    assert np.abs(oa["reaction"]).max() > 0 and abs(oa["reaction"][0]) > 0
+    assert np.allclose(oa["reaction"], ot["reaction"], rtol=1e-12, atol=0)
+
+
+def test_global_tangent_matches_finite_difference_with_triangulated_body():
+    # a faceted sphere pressed into the block with friction: facets, edges and
+    # the sphere's curvature through the facet changes
+    cfg = sphere_body_cfg(radius=0.25, nlat=10, nlon=12, center=(0.31, 0.42, 0.73))
+    cfg.update(mu=0.2, ghost=0, model=0)
+    cfg["body"]["step_d"] = (0.003, 0.0, -0.002)
+    m = built(cfg)
+    c = m.counts()
+    n3 = 3 * c["ndof"]
+    rng = np.random.default_rng(13)
+    du = 1e-3 * rng.normal(size=n3)
+    out = m.assemble(du)
+    assert np.linalg.norm(out["reaction"]) > 0
+    rp, col = m.pattern()
+    K = out["K"]
+    h = 1e-7
+    for _ in range(3):
+        v = rng.normal(size=n3)
+        fd = (m.assemble(du + h * v, tangent=False)["R"] -
+              m.assemble(du - h * v, tangent=False)["R"]) / (2 * h)
+        Kv = np.zeros(n3)
+        for i in range(c["ndof"]):
+            for s_ in range(rp[i], rp[i + 1]):
+                Kv[3 * i:3 * i + 3] += K[s_] @ v[3 * col[s_]:3 * col[s_] + 3]
+        assert np.linalg.norm(Kv - fd) <= 1e-6 * np.linalg.norm(fd)
