@@ -65,12 +65,27 @@ typedef struct {
   int bc_mask[8];
 } mpm_domain;
 
-/* Rigid body of Sec. 2.3 as an analytic surface: kind 0 none, 1 flat-ended
- * cylinder {z >= z, rho <= r}, 2 cone of half angle alpha with tip at z and a
- * cylindrical shaft of radius r; axis through (cx, cy). */
+/* Rigid body of Sec. 2.3: kind 0 none, 1 flat-ended cylinder {z >= z, rho <=
+ * r}, 2 cone of half angle alpha with tip at z and a cylindrical shaft of
+ * radius r (axis through (cx, cy) for both), 3 a closed triangular faceted
+ * mesh (Sec. 2.3's representation of the rigid bodies): nvert vertices tri_v
+ * (device, 3 doubles each, relative to the reference point (cx, cy, z)) and
+ * ntri triangles tri_t (device, 3 vertex indices each, counter-clockwise seen
+ * from outside, every edge shared by two triangles); the arrays are the
+ * caller's and must stay the same (up to the reference point) between
+ * mpm_octree_build and the assemblies on its mesh.  Its signed distance is
+ * that of the nearest surface point over all triangles, signed by the
+ * angle-weighted pseudo-normal; Step 1 of Sec. 5 marks a leaf when the ball
+ * around it meets the body.  step_d is the body's translation over the
+ * current load step: the Coulomb friction of Sec. 2.3 measures the slip of
+ * each contact node against it (unused when mu = 0). */
 typedef struct {
   int kind;
   double cx, cy, z, r, alpha;
+  double step_d[3];
+  int ntri, nvert;
+  const double* tri_v;
+  const int* tri_t;
 } mpm_rigid;
 
 /* Adaptivity of Sec. 5: refine leaves meeting the body or with a node within
@@ -81,13 +96,18 @@ typedef struct {
 
 /* Material of Sec. 2.2 (model 0 Hencky elastic, 1 von Mises, 2 Drucker-Prager
  * with friction phi and dilation psi in radians), gravity g (Eq. MPMweak body
- * force), ghost constant kappa (Sec. 4), contact penalty factor pf (Sec. 2.3). */
+ * force), ghost constant kappa (Sec. 4), contact penalty factors pf (normal,
+ * eps_N = pf E_p (V0_p)^(2/3)) and pt (tangential, eps_T = pt E_p (V0_p)^(2/3))
+ * and the Coulomb friction coefficient mu between body and material (Sec.
+ * 2.3; mu > 0 makes the tangent non-symmetric, so the Krylov solve is
+ * BiCGStab). */
 typedef struct {
   int model;
   double nu, phi, psi;
   double g[3];
   double kappa, pf;
   int ghost_on, contact_on;
+  double mu, pt;
 } mpm_material;
 
 /* Caller-owned device point arrays (layout above).  mpm_octree_build may grow
@@ -139,6 +159,12 @@ typedef struct {
   double eta_hist[64];
   double reaction[3];
   double ms_build, ms_assemble, ms_solve, ms_update;
+  /* sizes of the step's mesh, for the benchmark's byte counts: point-support
+   * pairs plus ghost-face entries of the row source lists, padded block slots
+   * of the sliced stiffness, and the rows and stencil size of the first
+   * multigrid level (0 when no multigrid solve ran) */
+  long long nsrc, nslot;
+  int mg_rows1, mg_stencil1;
 } mpm_step_stats;
 
 typedef struct mpm_ctx mpm_ctx;
@@ -284,13 +310,15 @@ int mpm_adjoint(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body, cons
  * so that a cudaMalloc would fail or fragment it, or a latency-bound loop that
  * cannot afford an allocation on its first call.  It runs the FP64 3x3
  * block-Jacobi PCG of mpm_solve (precision MPM_FP64, method PCG) with every
- * work vector, the preconditioner and the scalars placed in one static
- * device array of 32 MiB that the library reserves on each device that loads
- * it and keeps until the process exits; the call itself allocates nothing.
- * Limit: 256 + 224 * 32 * ceil(ndof / 32) bytes must fit (vectors padded
- * to 4 components and to whole slices of 32 rows), i.e. at most 149,792 dofs
- * (449,376 unknowns); larger meshes are rejected with MPM_ERR_ARG and a
- * message.  The first call on a device looks up the array's device address,
+ * work vector, the preconditioner, the scalars and the partial sums of its
+ * fixed-order reductions placed in one static device array of 32 MiB that the
+ * library reserves on each device that loads it and keeps until the process
+ * exits; the call itself allocates nothing.
+ * Limit: 16,896 + 224 * 32 * ceil(ndof / 32) bytes must fit (vectors padded
+ * to 4 components and to whole slices of 32 rows), i.e. at most 149,696 dofs
+ * (449,088 unknowns); larger meshes are rejected with MPM_ERR_ARG and a
+ * message.  The context's device must be the current device (MPM_ERR_ARG
+ * otherwise).  The first call on a device looks up the array's device address,
  * so make that first call before any stream capture.  All calls share the one
  * array and it keeps the last call's contents (each call clears what must
  * start at zero): calls that overlap on the GPU, from any stream or context,
@@ -312,20 +340,31 @@ enum {
   MPM_PROF_TANGENT = 2,      /* row-gather tangent assembly                     */
   MPM_PROF_CONSTITUTIVE = 3, /* per-point return map (+ spatial tangent)        */
   MPM_PROF_KINEMATICS = 4,   /* per-point dF                                     */
-  MPM_PROF_FORCE = 5,        /* internal force scatter                           */
+  MPM_PROF_FORCE = 5,        /* spatial basis gradients for the tangent          */
   MPM_PROF_BASIS = 6,        /* discrete GIMP basis                              */
-  MPM_PROF_RESIDUAL = 7,     /* residual rows (ghost term, gravity)              */
+  MPM_PROF_RESIDUAL = 7,     /* residual rows: internal force gather, ghost term */
   MPM_PROF_CONTACT = 8,      /* penalty contact                                  */
   MPM_PROF_BICG_SPMV = 9,    /* BiCGStab SpMV                                    */
   MPM_PROF_REFINE = 10,      /* FP64 refinement residual                         */
   MPM_PROF_PATTERN = 11,     /* block pattern rows                               */
-  MPM_PROF_MG = 12,          /* one multigrid V-cycle (all of its launches)      */
-  MPM_PROF_MG_SETUP = 13,    /* multigrid Galerkin operators and inverses        */
-  MPM_PROF_NCLASS = 14
+  MPM_PROF_MG = 12,          /* V-cycle kernels below level 1 and the transfers  */
+  MPM_PROF_MG_SETUP = 13,    /* multigrid smoother inverses and FP16 copy        */
+  MPM_PROF_MG_FINE = 14,     /* V-cycle fine-level residual and smoothing        */
+  MPM_PROF_MG_LEVEL1 = 15,   /* V-cycle level-1 residual and smoothing           */
+  MPM_PROF_MG_RAP = 16,      /* multigrid Galerkin products                      */
+  MPM_PROF_NCLASS = 17
 };
 int mpm_profile(mpm_ctx* ctx, int enable);
 int mpm_profile_read(mpm_ctx* ctx, long long* launches, double* ms);
 int mpm_launch_count(const mpm_ctx* ctx, long long* launches);
+
+/* Measured FP64 fused multiply-add throughput of the context's GPU (no
+ * counterpart in the paper; the roofline of the kernels that the precision
+ * pattern keeps in FP64): independent FMA chains on every SM, timed with CUDA
+ * events on the context stream for about `seconds` (0.05 to 10).
+ * flops_per_s (host) receives 2 x FMAs / s, ms (host, may be NULL) the timed
+ * duration.  Synchronises the stream. */
+int mpm_fp64_peak(mpm_ctx* ctx, double seconds, double* flops_per_s, double* ms);
 
 #ifdef __cplusplus
 }

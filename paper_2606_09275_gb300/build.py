@@ -15,7 +15,7 @@ INC = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmpm_gb300.so")
 OBJ = os.path.join(HERE, "_build")
 UNITS = ["mpm_ctx", "mpm_cub", "mpm_build", "mpm_assemble", "mpm_solve", "mpm_step", "mpm_adjoint",
-         "mpm_mg"]
+         "mpm_mg", "mpm_peak"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # the mesh build decides discrete events (overlaps, splits, marks) from box
 # arithmetic: keep it to separately rounded multiplies and adds

@@ -374,7 +374,7 @@ struct MeshView {
 // (nodal seed into ub and x, l, E adjoints).
 __global__ void k_adj_contact(int nc8, int mode, const int* __restrict__ cand, MeshView mv,
                               const int* __restrict__ perm, const double* __restrict__ pE,
-                              const double* __restrict__ pV0, mpm_rigid body, double pf,
+                              const double* __restrict__ pV0, Body body, double pf,
                               const double* __restrict__ u, const double* __restrict__ mu, double w0,
                               double w1, double w2, double* ub, Adj mid, Adj a) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -866,6 +866,14 @@ extern "C" int mpm_adjoint(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* b
     set_error(c, "adjoint: supports the Hencky elastic and von Mises models (symmetric tangent)");
     return MPM_ERR_ARG;
   }
+  if (mat->mu > 0.0 && mat->contact_on) {
+    set_error(c, "adjoint: frictional contact (mu > 0) has a non-symmetric tangent; not supported");
+    return MPM_ERR_ARG;
+  }
+  if (body && body->kind == 3) {
+    set_error(c, "adjoint: the analytic bodies (kinds 1, 2) only");
+    return MPM_ERR_ARG;
+  }
   if (!(prm->tol > 0) || prm->maxit < 0 || prm->maxit > 63) {
     set_error(c, "adjoint: need tol > 0 and 0 <= maxit <= 63");
     return MPM_ERR_ARG;
@@ -973,7 +981,7 @@ extern "C" int mpm_adjoint(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* b
       if (n == nsteps - 1 && contact)
         MPM_LAUNCH(k_adj_contact<<<grid_for(8LL * m->ncand, 128), 128, 0, st>>>(
             8 * m->ncand, 1, ptr<int>(m->cand), mv, ptr<int>(m->perm), ptr<double>(m->pE),
-            ptr<double>(m->pV0), bd, mat->pf, u, nullptr, dJ_dreaction[0], dJ_dreaction[1],
+            ptr<double>(m->pV0), body_view(m, bd), mat->pf, u, nullptr, dJ_dreaction[0], dJ_dreaction[1],
             dJ_dreaction[2], ub, Mid, A));
       MPM_LAUNCH(k_mask_vec<<<grid_for(nd, 256), 256, 0, st>>>(nd, ptr<int>(m->dof_mask), ub));
       // 3. K mu = seed (K symmetric)
@@ -995,7 +1003,7 @@ extern "C" int mpm_adjoint(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* b
       if (contact)
         MPM_LAUNCH(k_adj_contact<<<grid_for(8LL * m->ncand, 128), 128, 0, st>>>(
             8 * m->ncand, 0, ptr<int>(m->cand), mv, ptr<int>(m->perm), ptr<double>(m->pE),
-            ptr<double>(m->pV0), bd, mat->pf, u, mu, 0.0, 0.0, 0.0, nullptr, Mid, A));
+            ptr<double>(m->pV0), body_view(m, bd), mat->pf, u, mu, 0.0, 0.0, 0.0, nullptr, Mid, A));
       int* argK = grow<int>(c, X.argk, m->nleaf);
       MPM_LAUNCH(k_fill_int<<<grid_for(m->nleaf, 256), 256, 0, st>>>(m->nleaf, argK, 0x7fffffff));
       MPM_LAUNCH(k_adj_basis<<<grid_for(P, AW), 32 * AW, 0, st>>>(

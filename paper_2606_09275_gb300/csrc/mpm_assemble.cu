@@ -535,7 +535,8 @@ __device__ inline int find_slot(const int* __restrict__ rp, const int* __restric
 __global__ void k_contact_corner(int nc8, const int* __restrict__ cand, const int* __restrict__ cb_n,
                                  const int* __restrict__ cb_idx, const double* __restrict__ cb_phi,
                                  const double* __restrict__ cb_y0, const double* __restrict__ pE,
-                                 const double* __restrict__ pV0, mpm_rigid body, double L, double pf,
+                                 const double* __restrict__ pV0, Body body, double L, double pf,
+                                 double pt, double mu,
                                  const double* __restrict__ du, double* cf, double* ck, int* con,
                                  double* reac, GridRed gr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -552,10 +553,40 @@ __global__ void k_contact_corner(int nc8, const int* __restrict__ cand, const in
     double kc[9];
     for (int e = 0; e < 9; ++e) kc[e] = 0.0;
     if (on) {
-      double epsN = pf * pE[w] * pow(pV0[w], 2.0 / 3.0);
-      for (int d = 0; d < 3; ++d) f[d] = -epsN * phi * nv[d];
+      double A0 = pow(pV0[w], 2.0 / 3.0);
+      double epsN = pf * pE[w] * A0, fN = -epsN * phi;
+      for (int d = 0; d < 3; ++d) f[d] = fN * nv[d];
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) kc[3 * a + b] = epsN * (nv[a] * nv[b] + phi * H[3 * a + b]);
+      if (mu > 0.0) {
+        // Coulomb friction: the node's slip against the body over the load
+        // step, g = (y - y0) - d_body, on the tangent plane; trial force
+        // t = -eps_T (I - n n^T) g, stick while |t| <= mu f_N, else slip with
+        // mu f_N t/|t|; kc gets -d(force)/dy (not symmetric when slipping)
+        double epsT = pt * pE[w] * A0;
+        double g[3], t[3], Hg[3], D[9];
+        for (int d = 0; d < 3; ++d) g[d] = (y[d] - cb_y0[3 * (size_t)i + d]) - body.b.step_d[d];
+        double ng = nv[0] * g[0] + nv[1] * g[1] + nv[2] * g[2];
+        for (int a = 0; a < 3; ++a) Hg[a] = H[3 * a] * g[0] + H[3 * a + 1] * g[1] + H[3 * a + 2] * g[2];
+        for (int d = 0; d < 3; ++d) t[d] = -epsT * (g[d] - nv[d] * ng);
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            D[3 * a + b] = -epsT * ((a == b ? 1.0 : 0.0) - nv[a] * nv[b] - ng * H[3 * a + b] - nv[a] * Hg[b]);
+        double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+        if (tn <= mu * fN) {
+          for (int d = 0; d < 3; ++d) f[d] += t[d];
+          for (int q = 0; q < 9; ++q) kc[q] -= D[q];
+        } else {
+          double u[3] = {t[0] / tn, t[1] / tn, t[2] / tn};
+          for (int d = 0; d < 3; ++d) f[d] += mu * fN * u[d];
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+              double sm = 0.0;
+              for (int c = 0; c < 3; ++c) sm += ((a == c ? 1.0 : 0.0) - u[a] * u[c]) * D[3 * c + b];
+              kc[3 * a + b] -= mu * u[a] * (-epsN * nv[b]) + mu * fN * sm / tn;
+            }
+        }
+      }
     }
     for (int d = 0; d < 3; ++d) cf[3 * (size_t)i + d] = f[d];
     for (int e = 0; e < 9; ++e) ck[9 * (size_t)i + e] = kc[e];
@@ -681,7 +712,9 @@ void contact_terms(mpm_ctx* c, mpm_mesh* m, const mpm_material& mat, const mpm_r
   int* con = grow<int>(c, m->cc_on, n8);
   MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact_corner<<<grid_for(n8, 128), 128, 0, st>>>(
       n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
-      ptr<double>(m->cb_y0), ptr<double>(m->pE), ptr<double>(m->pV0), body, m->g.L, mat.pf, du, cf, ck,
+      ptr<double>(m->cb_y0), ptr<double>(m->pE), ptr<double>(m->pV0), body_view(m, body), m->g.L,
+      mat.pf, mat.pt,
+      mat.mu, du, cf, ck,
       con, reac, grid_red(c, 3, grid_for(n8, 128))));
   if (!m->nct) return;
   Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};

@@ -24,7 +24,7 @@ __global__ void k_tree_uniform(int n, int shift, int lev, uint64_t* key, int* le
 
 // Sec. 5, Steps 1-2: mark leaves meeting the body or with a corner within dx_region
 __global__ void k_mark_refine(int n, const uint64_t* __restrict__ key, const int* __restrict__ lev,
-                              Geo g, mpm_rigid b, double dxr, int dmax, int* flag, int* any) {
+                              Geo g, Body b, double dxr, int dmax, int* flag, int* any) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int f = 0;
@@ -42,7 +42,7 @@ __global__ void k_mark_refine(int n, const uint64_t* __restrict__ key, const int
     } else {
       for (int c = 0; c < 8 && !f; ++c) {
         double xc[3] = {(c & 1) ? hi[0] : lo[0], (c & 2) ? hi[1] : lo[1], (c & 4) ? hi[2] : lo[2]};
-        if (body_distance(b, xc) <= dxr) f = 1;
+        if (body_distance(b, xc, dxr) <= dxr) f = 1;
       }
     }
   }
@@ -1120,7 +1120,7 @@ __global__ void k_fext_rows(int nd, int P, const long long* __restrict__ sptr,
 }
 
 __global__ void k_cand_flag(int P, const double* __restrict__ px, const double* __restrict__ plp,
-                            mpm_rigid b, double margin, int* flag) {
+                            Body b, double margin, int* flag) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= P) return;
   int f = 0;
@@ -1128,7 +1128,7 @@ __global__ void k_cand_flag(int P, const double* __restrict__ px, const double* 
     double y[3];
     for (int d = 0; d < 3; ++d)
       y[d] = px[3 * (size_t)w + d] + (((c >> d) & 1) ? 1.0 : -1.0) * plp[3 * (size_t)w + d];
-    if (body_distance(b, y) <= margin) f = 1;
+    if (body_distance(b, y, margin) <= margin) f = 1;
   }
   flag[w] = f;
 }
@@ -1227,6 +1227,68 @@ __global__ void k_ct_write(long long n, const uint64_t* __restrict__ keys, const
   if (q == n - 1 || keys[q + 1] == ~0ULL) cptr[nrow] = (int)(q + 1);
 }
 
+// ------------------------------------------------------------------ triangulated body
+
+// unit normal of every triangle (body frame)
+__global__ void k_tri_fn(int nt, const double* __restrict__ v, const int* __restrict__ t, double* fn) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  const double *a = v + 3 * (size_t)t[3 * i], *b = v + 3 * (size_t)t[3 * i + 1],
+               *c = v + 3 * (size_t)t[3 * i + 2];
+  double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double w[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+  double l = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  for (int d = 0; d < 3; ++d) fn[3 * (size_t)i + d] = n[d] / l;
+}
+
+// edge pseudo-normals: the face normal plus that of the first other triangle
+// (in index order) holding both ends of the edge
+__global__ void k_tri_en(int nt, const int* __restrict__ t, const double* __restrict__ fn, double* en) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 3 * nt) return;
+  int i = e / 3, k = e % 3;
+  int a = t[3 * i + k], b = t[3 * i + (k + 1) % 3];
+  double N[3] = {fn[3 * (size_t)i], fn[3 * (size_t)i + 1], fn[3 * (size_t)i + 2]};
+  for (int u = 0; u < nt; ++u) {
+    if (u == i) continue;
+    int ha = 0, hb = 0;
+    for (int q = 0; q < 3; ++q) {
+      ha |= t[3 * u + q] == a;
+      hb |= t[3 * u + q] == b;
+    }
+    if (ha && hb) {
+      for (int d = 0; d < 3; ++d) N[d] += fn[3 * (size_t)u + d];
+      break;
+    }
+  }
+  for (int d = 0; d < 3; ++d) en[3 * (size_t)e + d] = N[d];
+}
+
+// vertex pseudo-normals: angle-weighted sum of the face normals around the
+// vertex (triangles in index order)
+__global__ void k_tri_vn(int nv, int nt, const double* __restrict__ v, const int* __restrict__ t,
+                         const double* __restrict__ fn, double* vn) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nv) return;
+  double N[3] = {0.0, 0.0, 0.0};
+  const double* a = v + 3 * (size_t)p;
+  for (int u = 0; u < nt; ++u)
+    for (int k = 0; k < 3; ++k) {
+      if (t[3 * u + k] != p) continue;
+      const double* b = v + 3 * (size_t)t[3 * u + (k + 1) % 3];
+      const double* c = v + 3 * (size_t)t[3 * u + (k + 2) % 3];
+      double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+      double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+      double cs = (e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2]) /
+                  sqrt((e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]) *
+                       (e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]));
+      double ang = acos(fmin(fmax(cs, -1.0), 1.0));
+      for (int d = 0; d < 3; ++d) N[d] += ang * fn[3 * (size_t)u + d];
+    }
+  for (int d = 0; d < 3; ++d) vn[3 * (size_t)p + d] = N[d];
+}
+
 // ------------------------------------------------------------------ sliced storage
 
 // width of each slice of 32 rows: longest row, rounded up to 4 blocks
@@ -1319,6 +1381,35 @@ int bits_for(long long v) {
 
 // ------------------------------------------------------------------ the build
 
+// a triangulated body: check its arrays, then its pseudo-normals and bounding box
+void tri_setup(mpm_ctx* c, mpm_mesh* m, const mpm_rigid& b) {
+  cudaStream_t st = c->stream;
+  if (b.ntri <= 0 || b.nvert <= 0 || !b.tri_v || !b.tri_t)
+    throw CudaError(MPM_ERR_ARG, "triangulated body: need ntri > 0, nvert > 0 and both arrays");
+  std::vector<double> v(3 * (size_t)b.nvert);
+  std::vector<int> t(3 * (size_t)b.ntri);
+  MPM_CUDA(cudaMemcpyAsync(v.data(), b.tri_v, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, st));
+  MPM_CUDA(cudaMemcpyAsync(t.data(), b.tri_t, sizeof(int) * t.size(), cudaMemcpyDeviceToHost, st));
+  MPM_CUDA(cudaStreamSynchronize(st));
+  for (int i : t)
+    if (i < 0 || i >= b.nvert) throw CudaError(MPM_ERR_ARG, "triangulated body: vertex index out of range");
+  for (int d = 0; d < 3; ++d) {
+    m->tri_lo[d] = 1e300;
+    m->tri_hi[d] = -1e300;
+  }
+  for (int i = 0; i < b.nvert; ++i)
+    for (int d = 0; d < 3; ++d) {
+      m->tri_lo[d] = std::min(m->tri_lo[d], v[3 * (size_t)i + d]);
+      m->tri_hi[d] = std::max(m->tri_hi[d], v[3 * (size_t)i + d]);
+    }
+  double* fn = grow<double>(c, m->tri_fn, 3 * (size_t)b.ntri);
+  double* en = grow<double>(c, m->tri_en, 9 * (size_t)b.ntri);
+  double* vn = grow<double>(c, m->tri_vn, 3 * (size_t)b.nvert);
+  MPM_LAUNCH(k_tri_fn<<<grid_for(b.ntri, 128), 128, 0, st>>>(b.ntri, b.tri_v, b.tri_t, fn));
+  MPM_LAUNCH(k_tri_en<<<grid_for(3LL * b.ntri, 128), 128, 0, st>>>(b.ntri, b.tri_t, fn, en));
+  MPM_LAUNCH(k_tri_vn<<<grid_for(b.nvert, 128), 128, 0, st>>>(b.nvert, b.ntri, b.tri_v, b.tri_t, fn, vn));
+}
+
 void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid& body,
                 const mpm_adapt& ad, const mpm_material& mat, mpm_points* pts, int flags) {
   cudaStream_t st = c->stream;
@@ -1335,6 +1426,8 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
   g.unit = dom.L / ldexp(1.0, g.D);
   g.scale = ldexp(1.0, g.D) / dom.L;
   int* d_err = c->d_err;
+  if (body.kind == 3) tri_setup(c, m, body);
+  const Body bv = body_view(m, body);
 
   // ---- a1: uniform tree at depth_min, then Sec. 5 refinement + balance
   {
@@ -1352,7 +1445,7 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
         int* flag = grow<int>(c, m->flag, nl);
         MPM_CUDA(cudaMemsetAsync(any, 0, sizeof(int), st));
         MPM_LAUNCH(k_mark_refine<<<grid_for(nl, 256), 256, 0, st>>>(nl, ptr<uint64_t>(m->leaf_key),
-                                                         ptr<int>(m->leaf_lev), g, body, ad.dx_region,
+                                                         ptr<int>(m->leaf_lev), g, bv, ad.dx_region,
                                                          dom.depth_max, flag, any));
         if (!read_flag(c, any)) {
           settled = true;
@@ -1614,7 +1707,7 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
   if (mat.contact_on && body.kind != 0) {
     int* flag = grow<int>(c, c->tmp[0], P);
     int* pos = grow<int>(c, c->tmp[1], P);
-    MPM_LAUNCH(k_cand_flag<<<grid_for(P, 256), 256, 0, st>>>(P, ptr<double>(m->px), ptr<double>(m->plp), body,
+    MPM_LAUNCH(k_cand_flag<<<grid_for(P, 256), 256, 0, st>>>(P, ptr<double>(m->px), ptr<double>(m->plp), bv,
                                                   4.0 * g.unit, flag));
     cub_exclusive_sum_int(c, flag, pos, P);
     int nc = read_total(c, pos, flag, P);
@@ -1666,6 +1759,21 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
   }
   m->nhang = nh;
   m->built = 1;
+}
+
+Body body_view(const mpm_mesh* m, const mpm_rigid& b) {
+  Body v{};
+  v.b = b;
+  if (b.kind == 3) {
+    v.fn = ptr<double>(m->tri_fn);
+    v.en = ptr<double>(m->tri_en);
+    v.vn = ptr<double>(m->tri_vn);
+    for (int d = 0; d < 3; ++d) {
+      v.lo[d] = m->tri_lo[d];
+      v.hi[d] = m->tri_hi[d];
+    }
+  }
+  return v;
 }
 
 }  // namespace mpm

@@ -39,6 +39,17 @@ struct Geo {
   double scale; // 2^D / L
 };
 
+// the rigid body as the kernels see it: the caller's description and, for a
+// triangulated body (kind 3), its pseudo-normals (computed with the mesh)
+// and the bounding box of its vertices (body frame)
+struct Body {
+  mpm_rigid b;
+  const double* fn;     // [ntri][3] unit face normals
+  const double* en;     // [ntri][3][3] edge pseudo-normals (edges v0v1, v1v2, v2v0)
+  const double* vn;     // [nvert][3] angle-weighted vertex pseudo-normals
+  double lo[3], hi[3];  // vertex bounding box
+};
+
 struct CudaError : std::runtime_error {
   int code;
   CudaError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
@@ -200,6 +211,9 @@ struct mpm_mesh {
   mpm::Buf ct_row, ct_ptr, ct_ent, cc_f, cc_k, cc_on;
   // ghost faces: jumps J at the 4 Gauss points (4 x MAXG) and the coefficient
   mpm::Buf gJ, gcoef;
+  // triangulated body of the build: pseudo-normals and vertex bounding box
+  mpm::Buf tri_fn, tri_en, tri_vn;
+  double tri_lo[3] = {0, 0, 0}, tri_hi[3] = {0, 0, 0};
   // per-iteration point data (Mf: V0 tau dF^-T, 12 per point)
   mpm::Buf dF, dFinv, tau, Aalg, gx, Mf;
   mpm::Buf lawst;  // spectral state of the last residual-only evaluation (22 per point)
@@ -332,8 +346,159 @@ __device__ inline double body_rxy(const mpm_rigid& b, const double* lo, const do
   return sqrt(dx * dx + dy * dy);
 }
 
-// does the closed box meet the solid body?
-__device__ inline bool body_meets_box(const mpm_rigid& b, const double* lo, const double* hi) {
+// ---- triangulated body (kind 3): signed distance of the nearest surface
+// point over all triangles (the first triangle attaining the smallest
+// distance), signed by the pseudo-normal of the feature holding it (face,
+// edge: sum of the two face normals, vertex: angle-weighted sum)
+
+__device__ inline void tri_vertex(const Body& B, int v, double* o) {
+  o[0] = B.b.tri_v[3 * (size_t)v] + B.b.cx;
+  o[1] = B.b.tri_v[3 * (size_t)v + 1] + B.b.cy;
+  o[2] = B.b.tri_v[3 * (size_t)v + 2] + B.b.z;
+}
+
+// nearest point q of triangle (a, b, c) to x by the Voronoi regions of its
+// vertices, edges and face; feature 0 face, 1..3 edges ab, bc, ca, 4..6
+// vertices a, b, c
+__device__ inline int tri_nearest(const double* x, const double* a, const double* b,
+                                  const double* c, double* q) {
+  double ab[3], ac[3], ax[3], bx[3], cx[3];
+  for (int d = 0; d < 3; ++d) {
+    ab[d] = b[d] - a[d];
+    ac[d] = c[d] - a[d];
+    ax[d] = x[d] - a[d];
+  }
+  double d1 = ab[0] * ax[0] + ab[1] * ax[1] + ab[2] * ax[2];
+  double d2 = ac[0] * ax[0] + ac[1] * ax[1] + ac[2] * ax[2];
+  if (d1 <= 0.0 && d2 <= 0.0) {
+    for (int d = 0; d < 3; ++d) q[d] = a[d];
+    return 4;
+  }
+  for (int d = 0; d < 3; ++d) bx[d] = x[d] - b[d];
+  double d3 = ab[0] * bx[0] + ab[1] * bx[1] + ab[2] * bx[2];
+  double d4 = ac[0] * bx[0] + ac[1] * bx[1] + ac[2] * bx[2];
+  if (d3 >= 0.0 && d4 <= d3) {
+    for (int d = 0; d < 3; ++d) q[d] = b[d];
+    return 5;
+  }
+  double vc = d1 * d4 - d3 * d2;
+  if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
+    double v = d1 / (d1 - d3);
+    for (int d = 0; d < 3; ++d) q[d] = a[d] + v * ab[d];
+    return 1;
+  }
+  for (int d = 0; d < 3; ++d) cx[d] = x[d] - c[d];
+  double d5 = ab[0] * cx[0] + ab[1] * cx[1] + ab[2] * cx[2];
+  double d6 = ac[0] * cx[0] + ac[1] * cx[1] + ac[2] * cx[2];
+  if (d6 >= 0.0 && d5 <= d6) {
+    for (int d = 0; d < 3; ++d) q[d] = c[d];
+    return 6;
+  }
+  double vb = d5 * d2 - d1 * d6;
+  if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
+    double w = d2 / (d2 - d6);
+    for (int d = 0; d < 3; ++d) q[d] = a[d] + w * ac[d];
+    return 3;
+  }
+  double va = d3 * d6 - d5 * d4;
+  if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) {
+    double w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    for (int d = 0; d < 3; ++d) q[d] = b[d] + w * (c[d] - b[d]);
+    return 2;
+  }
+  double den = 1.0 / (va + vb + vc), v = vb * den, w = vc * den;
+  for (int d = 0; d < 3; ++d) q[d] = a[d] + v * ab[d] + w * ac[d];
+  return 0;
+}
+
+// distance from x to the vertex bounding box (a lower bound of the distance
+// to the body)
+__device__ inline double tri_box_distance(const Body& B, const double* x) {
+  const double o[3] = {B.b.cx, B.b.cy, B.b.z};
+  double s = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    double e = fmax(fmax(B.lo[d] + o[d] - x[d], 0.0), x[d] - (B.hi[d] + o[d]));
+    s += e * e;
+  }
+  return sqrt(s);
+}
+
+// signed distance at x with gradient n and Hessian H (n, H may be null):
+// H is zero on a face, (I - e e^T - u u^T)/phi at an edge of direction e,
+// (I - u u^T)/phi at a vertex, u = (x - q)/|x - q|
+__device__ inline double tri_sdf(const Body& B, const double* x, double* n, double* H) {
+  const int* T = B.b.tri_t;
+  double best = 1e300, qb[3] = {0.0, 0.0, 0.0};
+  int tb = -1, fb = 0;
+  for (int t = 0; t < B.b.ntri; ++t) {
+    double a[3], b[3], c[3], q[3];
+    tri_vertex(B, T[3 * (size_t)t], a);
+    tri_vertex(B, T[3 * (size_t)t + 1], b);
+    tri_vertex(B, T[3 * (size_t)t + 2], c);
+    int f = tri_nearest(x, a, b, c, q);
+    double r0 = x[0] - q[0], r1 = x[1] - q[1], r2 = x[2] - q[2];
+    double d2 = r0 * r0 + r1 * r1 + r2 * r2;
+    if (d2 < best) {
+      best = d2;
+      tb = t;
+      fb = f;
+      qb[0] = q[0];
+      qb[1] = q[1];
+      qb[2] = q[2];
+    }
+  }
+  if (n) n[0] = n[1] = n[2] = 0.0;
+  if (H)
+    for (int i = 0; i < 9; ++i) H[i] = 0.0;
+  if (tb < 0) return 1e300;
+  double dist = sqrt(best);
+  double r[3] = {x[0] - qb[0], x[1] - qb[1], x[2] - qb[2]};
+  const double* nt = B.fn + 3 * (size_t)tb;
+  // x - q along the nearest triangle's normal: the surface is flat there
+  double cr0 = r[1] * nt[2] - r[2] * nt[1], cr1 = r[2] * nt[0] - r[0] * nt[2],
+         cr2 = r[0] * nt[1] - r[1] * nt[0];
+  if (fb != 0 && cr0 * cr0 + cr1 * cr1 + cr2 * cr2 <= 1e-24 * best) fb = 0;
+  const double* N = fb == 0 ? nt
+                            : (fb <= 3 ? B.en + 9 * (size_t)tb + 3 * (fb - 1)
+                                       : B.vn + 3 * (size_t)T[3 * (size_t)tb + fb - 4]);
+  double sg = (r[0] * N[0] + r[1] * N[1] + r[2] * N[2]) < 0.0 ? -1.0 : 1.0;
+  if (!(dist > 0.0)) return 0.0;
+  double phi = sg * dist;
+  double u[3] = {r[0] / dist, r[1] / dist, r[2] / dist};
+  if (n) {
+    for (int d = 0; d < 3; ++d) n[d] = fb == 0 ? nt[d] : sg * u[d];
+  }
+  if (H && fb != 0) {
+    double e[3] = {0.0, 0.0, 0.0};
+    if (fb <= 3) {
+      double a[3], b[3];
+      tri_vertex(B, T[3 * (size_t)tb + fb - 1], a);
+      tri_vertex(B, T[3 * (size_t)tb + fb % 3], b);
+      double l = sqrt((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]) +
+                      (b[2] - a[2]) * (b[2] - a[2]));
+      for (int d = 0; d < 3; ++d) e[d] = (b[d] - a[d]) / l;
+    }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        H[3 * i + j] = ((i == j ? 1.0 : 0.0) - e[i] * e[j] - u[i] * u[j]) / phi;
+  }
+  return phi;
+}
+
+// does the closed box meet the solid body?  (triangulated body: when the
+// ball around the box meets it)
+__device__ inline bool body_meets_box(const Body& B, const double* lo, const double* hi) {
+  const mpm_rigid& b = B.b;
+  if (b.kind == 3) {
+    double c[3], h2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      c[d] = 0.5 * (lo[d] + hi[d]);
+      h2 += 0.25 * (hi[d] - lo[d]) * (hi[d] - lo[d]);
+    }
+    double hd = sqrt(h2);
+    if (tri_box_distance(B, c) > hd) return false;  // (then the distance is > hd too)
+    return tri_sdf(B, c, nullptr, nullptr) <= hd;
+  }
   if (b.kind == 1) return hi[2] >= b.z && body_rxy(b, lo, hi) <= b.r;
   if (b.kind == 2) {
     if (hi[2] < b.z) return false;
@@ -352,8 +517,16 @@ __device__ inline double dist_to_segment(double px, double pz, double ax, double
   return sqrt(qx * qx + qz * qz);
 }
 
-// Euclidean distance from a point to the solid (0 inside)
-__device__ inline double body_distance(const mpm_rigid& b, const double* x) {
+// Euclidean distance from a point to the solid (0 inside); callers compare it
+// with thr, and where it is surely above thr (triangulated body farther than
+// thr from its bounding box) a lower bound above thr is returned instead
+__device__ inline double body_distance(const Body& B, const double* x, double thr) {
+  const mpm_rigid& b = B.b;
+  if (b.kind == 3) {
+    double lb = tri_box_distance(B, x);
+    if (lb > thr) return lb;
+    return fmax(tri_sdf(B, x, nullptr, nullptr), 0.0);
+  }
   double rx = x[0] - b.cx, ry = x[1] - b.cy;
   double rho = sqrt(rx * rx + ry * ry), z = x[2];
   if (b.kind == 1) {
@@ -373,8 +546,16 @@ __device__ inline double body_distance(const mpm_rigid& b, const double* x) {
 
 // Signed distance (negative inside), outward normal n and Hessian H (row-major)
 // of the body surface, for the penalty contact.  Returns true inside.
-__device__ inline bool body_sdf(const mpm_rigid& b, double L, const double* x, double* phi,
+__device__ inline bool body_sdf(const Body& B, double L, const double* x, double* phi,
                                 double* n, double* H) {
+  const mpm_rigid& b = B.b;
+  if (b.kind == 3) {
+    *phi = tri_sdf(B, x, n, H);
+    if (*phi < 0.0) return true;
+    n[0] = n[1] = n[2] = 0.0;
+    for (int i = 0; i < 9; ++i) H[i] = 0.0;
+    return false;
+  }
   double rx = x[0] - b.cx, ry = x[1] - b.cy;
   double rho = sqrt(rx * rx + ry * ry), z = x[2];
 #pragma unroll
@@ -385,7 +566,7 @@ __device__ inline bool body_sdf(const mpm_rigid& b, double L, const double* x, d
   double curv = 0.0;  // curvature factor of the lateral surface
   if (b.kind == 1) {
     if (!(z > b.z && rho < b.r)) {
-      *phi = body_distance(b, x);
+      *phi = body_distance(B, x, 1e300);
       return false;
     }
     double fb = b.z - z, fs = rho - b.r;
@@ -402,7 +583,7 @@ __device__ inline bool body_sdf(const mpm_rigid& b, double L, const double* x, d
   } else if (b.kind == 2) {
     double ta = tan(b.alpha), hc = b.r / ta;
     if (!(z > b.z && rho < fmin((z - b.z) * ta, b.r))) {
-      *phi = body_distance(b, x);
+      *phi = body_distance(B, x, 1e300);
       return false;
     }
     // nearest boundary point inside: the flank below the rim, the shaft wall
@@ -559,6 +740,9 @@ inline void prof_end(mpm_ctx* c) {
 void set_error(mpm_ctx* c, const std::string& m);
 int check_device_error(mpm_ctx* c, const char* where);
 void sync(mpm_ctx* c);
+
+// the kernels' view of the body for this mesh (mpm_build.cu)
+Body body_view(const mpm_mesh* m, const mpm_rigid& b);
 
 // build phase (mpm_build.cu)
 void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid& body,

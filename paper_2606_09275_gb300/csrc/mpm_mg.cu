@@ -955,7 +955,7 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
   unsigned long long* bnd = grow<unsigned long long>(c, G.bound, 16);
   MPM_CUDA(cudaMemsetAsync(bnd, 0, 16 * sizeof(unsigned long long), st));
   T* fD = grow<T>(c, G.fDinv, 12 * (size_t)npad);
-  MPM_LAUNCH(k_mg_dinv_fine<T><<<grid_for(npad, 256), 256, 0, st>>>(nd, npad, SK, K, fD, c->d_err, kSmoothW, bnd));
+  MPM_LAUNCH_P(MPM_PROF_MG_SETUP, k_mg_dinv_fine<T><<<grid_for(npad, 256), 256, 0, st>>>(nd, npad, SK, K, fD, c->d_err, kSmoothW, bnd));
   grow<T>(c, G.fr, 4 * (size_t)npad);
   grow<T>(c, G.fx, 4 * (size_t)npad);
   if constexpr (sizeof(T) == 4) {
@@ -964,8 +964,8 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
     unsigned* amax = (unsigned*)(c->d_red + 10);
     float* ksc = (float*)(c->d_red + 11);
     MPM_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned), st));
-    MPM_LAUNCH(k_absmax<<<4 * 152, 256, 0, st>>>(n9, K, amax));
-    MPM_LAUNCH(k_to_half<<<8 * 152, 256, 0, st>>>(n9, K, amax, grow<__half>(c, G.fKh, n9), ksc));
+    MPM_LAUNCH_P(MPM_PROF_MG_SETUP, k_absmax<<<4 * 152, 256, 0, st>>>(n9, K, amax));
+    MPM_LAUNCH_P(MPM_PROF_MG_SETUP, k_to_half<<<8 * 152, 256, 0, st>>>(n9, K, amax, grow<__half>(c, G.fKh, n9), ksc));
   }
   if (!coarse) return;
   for (int l = 0; l < G.nlev; ++l) {
@@ -977,19 +977,19 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
     double cnt;
     if (l == 0) {
       cnt = (double)std::max(G.t_max, 1);
-      MPM_LAUNCH(k_mg_rap1<T><<<grid_for(nd, 8), 256, 0, st>>>(
+      MPM_LAUNCH_P(MPM_PROF_MG_RAP, k_mg_rap1<T><<<grid_for(nd, 8), 256, 0, st>>>(
           nd, L.R, L.S, ptr<float>(G.p_w), ptr<int>(G.p_idx), ptr<int>(m->dof_mask), ptr<int>(m->row_ptr),
           ptr<int>(m->col), SK, K, ptr<int>(L.xyz), acc, bnd, cnt, c->d_err));
     } else {
       MGLevel& F = G.lev[l - 1];
       cnt = 27.0;
-      MPM_LAUNCH(k_mg_rapu<T><<<grid_for(F.nrow, 8), 256, 0, st>>>(
+      MPM_LAUNCH_P(MPM_PROF_MG_RAP, k_mg_rapu<T><<<grid_for(F.nrow, 8), 256, 0, st>>>(
           F.nrow, L.R, L.S, L.n1, ptr<int>(L.gid), F.R, F.S, F.n1, ptr<int>(F.gid), ptr<int>(F.xyz),
           ptr<int>(F.mask), ptr<T>(F.A), acc, bnd + l, c->d_err));
     }
-    MPM_LAUNCH(k_mg_from_fixed<T><<<4 * 152, 256, 0, st>>>((long long)nA, acc, bnd + l, cnt, A));
-    MPM_LAUNCH(k_mg_fix_masked<T><<<grid_for(L.nrow, 128), 128, 0, st>>>(L.nrow, L.S, L.R, ptr<int>(L.mask), A));
-    MPM_LAUNCH(k_mg_dinv<T><<<grid_for(L.npad, 128), 128, 0, st>>>(L.nrow, L.npad, L.S, L.R, A,
+    MPM_LAUNCH_P(MPM_PROF_MG_RAP, k_mg_from_fixed<T><<<4 * 152, 256, 0, st>>>((long long)nA, acc, bnd + l, cnt, A));
+    MPM_LAUNCH_P(MPM_PROF_MG_SETUP, k_mg_fix_masked<T><<<grid_for(L.nrow, 128), 128, 0, st>>>(L.nrow, L.S, L.R, ptr<int>(L.mask), A));
+    MPM_LAUNCH_P(MPM_PROF_MG_SETUP, k_mg_dinv<T><<<grid_for(L.npad, 128), 128, 0, st>>>(L.nrow, L.npad, L.S, L.R, A,
                                                                    grow<T>(c, L.Dinv, 12 * (size_t)L.npad), c->d_err, kSmoothW,
                                                                    bnd + l + 1));
     // level vectors: padding rows stay zero
@@ -1002,7 +1002,7 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
   T* Ci = grow<T>(c, G.cinv, (size_t)std::max(n3 * n3, 1));
   size_t dsm = sizeof(double) * (size_t)n3 * 2 * n3;
   MPM_CUDA(cudaFuncSetAttribute(k_mg_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
-  MPM_LAUNCH(k_mg_dense<T><<<1, 256, dsm, st>>>(C.nrow, C.S, C.R, ptr<int>(C.xyz), C.n1, ptr<int>(C.gid),
+  MPM_LAUNCH_P(MPM_PROF_MG_SETUP, k_mg_dense<T><<<1, 256, dsm, st>>>(C.nrow, C.S, C.R, ptr<int>(C.xyz), C.n1, ptr<int>(C.gid),
                                                 ptr<T>(C.A), Ci));
   G.prec = sizeof(T) == 4 ? MPM_MIXED : MPM_FP64;
   G.num_gen = m->gen;
@@ -1012,13 +1012,11 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
 
 template <class T>
 void mg_setup(mpm_ctx* c, mpm_mesh* m, const T* K, bool reuse) {
-  prof_begin(c, MPM_PROF_MG_SETUP);
   if (!m->mg || m->mg->gen != m->gen) mg_structure(c, m);
   MGData& G = *m->mg;
   int prec = sizeof(T) == 4 ? MPM_MIXED : MPM_FP64;
   bool keep = reuse && G.num_gen == m->gen && G.prec == prec;
   mg_numeric<T>(c, m, K, !keep);
-  prof_end(c);
 }
 
 template <class T>
@@ -1037,15 +1035,15 @@ void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, cons
   // fine pre-smoothing from zero, residual, restriction (gathered)
   MGLevel& L0 = G.lev[0];
   T* fr = ptr<T>(G.fr);
-  MPM_LAUNCH(k_mg_jac0<T><<<grid_for(npad, 256), 256, 0, st>>>(npad, fD, r, fx, sk, k));
+  MPM_LAUNCH_P(MPM_PROF_MG, k_mg_jac0<T><<<grid_for(npad, 256), 256, 0, st>>>(npad, fD, r, fx, sk, k));
   const float* ksc = (const float*)(c->d_red + 11);
   if constexpr (sizeof(T) == 4)
-    MPM_LAUNCH(k_mg_fine<T, 0, __half><<<grid_for(npad, FB), FB, 0, st>>>(
+    MPM_LAUNCH_P(MPM_PROF_MG_FINE, k_mg_fine<T, 0, __half><<<grid_for(npad, FB), FB, 0, st>>>(
         nd, npad, SK, ptr<__half>(G.fKh), ksc, r, fx, fD, fr, fmask, nullptr, sk, k, gr));
   else
-    MPM_LAUNCH(k_mg_fine<T, 0, T><<<grid_for(npad, FB), FB, 0, st>>>(
+    MPM_LAUNCH_P(MPM_PROF_MG_FINE, k_mg_fine<T, 0, T><<<grid_for(npad, FB), FB, 0, st>>>(
         nd, npad, SK, K, ksc, r, fx, fD, fr, fmask, nullptr, sk, k, gr));
-  MPM_LAUNCH(k_mg_restrict1<T><<<grid_for(L0.npad, MGW), 32 * MGW, 0, st>>>(
+  MPM_LAUNCH_P(MPM_PROF_MG, k_mg_restrict1<T><<<grid_for(L0.npad, MGW), 32 * MGW, 0, st>>>(
       L0.nrow, L0.npad, ptr<int>(G.t_ptr), ptr<int>(G.t_idx), ptr<float>(G.t_w), fr, ptr<T>(L0.Dinv),
       ptr<T>(L0.b), ptr<T>(L0.x), sk, k));
   // down the uniform levels: residual, then the next level's gathered
@@ -1054,34 +1052,34 @@ void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, cons
   for (int l = 0; l + 1 < G.nlev; ++l) {
     MGLevel& L = G.lev[l];
     MGLevel& N = G.lev[l + 1];
-    MPM_LAUNCH(k_mg_lvl<T, 0><<<grid_for(L.nrow, MGW), 32 * MGW, 0, st>>>(
+    MPM_LAUNCH_P(l == 0 ? MPM_PROF_MG_LEVEL1 : MPM_PROF_MG, k_mg_lvl<T, 0><<<grid_for(L.nrow, MGW), 32 * MGW, 0, st>>>(
         L.nrow, L.S, L.R, L.n1, ptr<int>(L.xyz), ptr<int>(L.gid), ptr<T>(L.A), ptr<T>(L.b), ptr<T>(L.x),
         ptr<T>(L.Dinv), ptr<T>(L.r), ptr<int>(L.mask), sk, k));
-    MPM_LAUNCH(k_mg_restrictu<T><<<grid_for(N.npad, 128), 128, 0, st>>>(
+    MPM_LAUNCH_P(MPM_PROF_MG, k_mg_restrictu<T><<<grid_for(N.npad, 128), 128, 0, st>>>(
         N.nrow, N.npad, ptr<int>(N.xyz), L.n1, ptr<int>(L.gid), ptr<T>(L.r), ptr<T>(N.Dinv), ptr<T>(N.b),
         ptr<T>(N.x), sk, k));
   }
   MGLevel& C = G.lev[G.nlev - 1];
-  MPM_LAUNCH(k_mg_coarse<T><<<1, 256, 0, st>>>(C.nrow, ptr<T>(G.cinv), ptr<T>(C.b), ptr<T>(C.x), sk, k));
+  MPM_LAUNCH_P(MPM_PROF_MG, k_mg_coarse<T><<<1, 256, 0, st>>>(C.nrow, ptr<T>(G.cinv), ptr<T>(C.b), ptr<T>(C.x), sk, k));
   xcur[G.nlev - 1] = ptr<T>(C.x);
   // up: prolongate, post-smooth (into the r buffer, which becomes the iterate)
   for (int l = G.nlev - 2; l >= 0; --l) {
     MGLevel& L = G.lev[l];
     MGLevel& N = G.lev[l + 1];
-    MPM_LAUNCH(k_mg_prolong_u<T><<<grid_for(L.nrow, 128), 128, 0, st>>>(
+    MPM_LAUNCH_P(MPM_PROF_MG, k_mg_prolong_u<T><<<grid_for(L.nrow, 128), 128, 0, st>>>(
         L.nrow, ptr<int>(L.xyz), ptr<int>(L.mask), N.n1, ptr<int>(N.gid), xcur[l + 1], ptr<T>(L.x), sk, k));
-    MPM_LAUNCH(k_mg_lvl<T, 1><<<grid_for(L.nrow, MGW), 32 * MGW, 0, st>>>(
+    MPM_LAUNCH_P(l == 0 ? MPM_PROF_MG_LEVEL1 : MPM_PROF_MG, k_mg_lvl<T, 1><<<grid_for(L.nrow, MGW), 32 * MGW, 0, st>>>(
         L.nrow, L.S, L.R, L.n1, ptr<int>(L.xyz), ptr<int>(L.gid), ptr<T>(L.A), ptr<T>(L.b), ptr<T>(L.x),
         ptr<T>(L.Dinv), ptr<T>(L.r), nullptr, sk, k));
     xcur[l] = ptr<T>(L.r);
   }
-  MPM_LAUNCH(k_mg_prolong1<T><<<grid_for(nd, 128), 128, 0, st>>>(nd, ptr<int>(G.p_idx), ptr<float>(G.p_w), fmask,
+  MPM_LAUNCH_P(MPM_PROF_MG, k_mg_prolong1<T><<<grid_for(nd, 128), 128, 0, st>>>(nd, ptr<int>(G.p_idx), ptr<float>(G.p_w), fmask,
                                                                   xcur[0], fx, sk, k));
   if constexpr (sizeof(T) == 4)
-    MPM_LAUNCH(k_mg_fine<T, 1, __half><<<grid_for(npad, FB), FB, 0, st>>>(
+    MPM_LAUNCH_P(MPM_PROF_MG_FINE, k_mg_fine<T, 1, __half><<<grid_for(npad, FB), FB, 0, st>>>(
         nd, npad, SK, ptr<__half>(G.fKh), ksc, r, fx, fD, z, nullptr, rz, sk, k, gr));
   else
-    MPM_LAUNCH(k_mg_fine<T, 1, T><<<grid_for(npad, FB), FB, 0, st>>>(
+    MPM_LAUNCH_P(MPM_PROF_MG_FINE, k_mg_fine<T, 1, T><<<grid_for(npad, FB), FB, 0, st>>>(
         nd, npad, SK, K, ksc, r, fx, fD, z, nullptr, rz, sk, k, gr));
 }
 

@@ -517,9 +517,7 @@ int run_pcg_mg(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* b, T* x,
     int kend = std::min(maxit, k + batch);
     for (; k < kend; ++k) {
       MPM_LAUNCH_P(MPM_PROF_PCG_UPDATE, k_pcg_a<T, false><<<vb, 256, 0, st>>>(nd, k, nullptr, x, r, z, p, q, sc_d, gr));
-      prof_begin(c, MPM_PROF_MG);
       mg_apply<T>(c, m, K, r, z, sc_d, k, &sc_d->rz[(k + 1) % 3]);
-      prof_end(c);
       MPM_LAUNCH_P(MPM_PROF_PCG_SPMV, k_pcg_b<T, T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, k, S, K, z, p, q, sc_d, gr));
     }
     MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
@@ -562,9 +560,9 @@ void mg_precondition(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* y,
     long long n4 = 4LL * 32 * m->nslice;
     float* y32 = grow<float>(c, c->v[23], 2 * (size_t)n4);
     float* z32 = y32 + n4;
-    MPM_LAUNCH(k_d2f<<<4 * 152, 256, 0, st>>>(n4, y, y32, sc));
+    MPM_LAUNCH_P(MPM_PROF_MG, k_d2f<<<4 * 152, 256, 0, st>>>(n4, y, y32, sc));
     mg_apply<float>(c, m, K, y32, z32, sc, -1, nullptr);
-    MPM_LAUNCH(k_f2d<<<4 * 152, 256, 0, st>>>(n4, z32, z, sc));
+    MPM_LAUNCH_P(MPM_PROF_MG, k_f2d<<<4 * 152, 256, 0, st>>>(n4, z32, z, sc));
   }
 }
 
@@ -619,17 +617,13 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
       MPM_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
       MPM_LAUNCH(k_bicg_p<<<vb, 256, 0, st>>>(npad, p, r, v, ph, Dinv, sc_d));
       if (!Dinv) {
-        prof_begin(c, MPM_PROF_MG);
         mg_precondition<T>(c, m, K, p, ph, sc_d);
-        prof_end(c);
       }
       MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, ph, v, r0, &sc_d->a[4], nullptr, sc_d, 0, gr));
       MPM_LAUNCH(k_bicg_s<<<vb, 256, 0, st>>>(npad, r, v, s, shv, Dinv, sc_d, gr));
       MPM_LAUNCH(k_bicg_check_s<<<vb, 256, 0, st>>>(nd, x, ph, sc_d));
       if (!Dinv) {
-        prof_begin(c, MPM_PROF_MG);
         mg_precondition<T>(c, m, K, s, shv, sc_d);
-        prof_end(c);
       }
       MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, shv, t, s, &sc_d->a[6], &sc_d->a[7], sc_d, 1, gr));
       MPM_LAUNCH(k_bicg_x<<<vb, 256, 0, st>>>(nd, npad, x, r, ph, shv, s, t, r0, sc_d, red, red + 1, gr));
@@ -657,7 +651,8 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   const int* col = ptr<int>(m->col);
   Sliced S = sliced_of(m);
   int method = prm.method;
-  bool sym = !(mat.model == 2 && mat.psi != mat.phi);
+  // non-associated Drucker-Prager and Coulomb friction make K non-symmetric
+  bool sym = !(mat.model == 2 && mat.psi != mat.phi) && !(mat.mu > 0.0 && mat.contact_on);
   if (method == 0) method = sym ? 1 : 2;
   bool mgb = method == 3 && !sym;  // multigrid-preconditioned BiCGStab
   Scal* sc_d = grow<Scal>(c, c->v[20], 1);

@@ -171,9 +171,15 @@ extern "C" int mpm_step(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* body
     st.npts = m->np;
     st.ndof = m->ndof;
     st.nnzb = m->nnzb;
+    st.nsrc = m->nsrc;
+    st.nslot = m->nslot;
     if (status) throw CudaError(status, c->err);
     double* du = nullptr;
     newton(c, m, mat, bd, prm, st, &du);
+    if (m->mg && m->mg->gen == m->gen && m->mg->nlev > 0) {
+      st.mg_rows1 = m->mg->lev[0].nrow;
+      st.mg_stencil1 = m->mg->lev[0].S;
+    }
     if (prm->du_out) {
       long long n3 = 3LL * m->ndof;
       if (n3 > prm->du_capacity)

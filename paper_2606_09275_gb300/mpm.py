@@ -28,7 +28,7 @@ EXPORT = dict(leaf_level=0, leaf_anchor=1, node_coord=2, node_hang=3, node_dof=4
 SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_octree_build", "mpm_mesh_free",
            "mpm_mesh_counts", "mpm_mesh_export", "mpm_assemble", "mpm_solve", "mpm_step",
            "mpm_profile", "mpm_profile_read", "mpm_launch_count", "mpm_solve_static",
-           "mpm_blocks_export", "mpm_adjoint"]
+           "mpm_blocks_export", "mpm_adjoint", "mpm_fp64_peak"]
 
 
 class Domain(C.Structure):
@@ -39,7 +39,8 @@ class Domain(C.Structure):
 
 class Rigid(C.Structure):
     _fields_ = [("kind", C.c_int), ("cx", C.c_double), ("cy", C.c_double), ("z", C.c_double),
-                ("r", C.c_double), ("alpha", C.c_double)]
+                ("r", C.c_double), ("alpha", C.c_double), ("step_d", C.c_double * 3),
+                ("ntri", C.c_int), ("nvert", C.c_int), ("tri_v", C.c_void_p), ("tri_t", C.c_void_p)]
 
 
 class Adapt(C.Structure):
@@ -49,7 +50,8 @@ class Adapt(C.Structure):
 class Material(C.Structure):
     _fields_ = [("model", C.c_int), ("nu", C.c_double), ("phi", C.c_double), ("psi", C.c_double),
                 ("g", C.c_double * 3), ("kappa", C.c_double), ("pf", C.c_double),
-                ("ghost_on", C.c_int), ("contact_on", C.c_int)]
+                ("ghost_on", C.c_int), ("contact_on", C.c_int), ("mu", C.c_double),
+                ("pt", C.c_double)]
 
 
 class PointsT(C.Structure):
@@ -81,7 +83,8 @@ class StepStats(C.Structure):
     _fields_ = [(n, C.c_int) for n in ("newton_its", "lin_its", "status", "npts", "ndof", "nnzb")] + [
         ("res_hist", C.c_double * 64), ("eta_hist", C.c_double * 64), ("reaction", C.c_double * 3),
         ("ms_build", C.c_double), ("ms_assemble", C.c_double), ("ms_solve", C.c_double),
-        ("ms_update", C.c_double)]
+        ("ms_update", C.c_double), ("nsrc", C.c_longlong), ("nslot", C.c_longlong),
+        ("mg_rows1", C.c_int), ("mg_stencil1", C.c_int)]
 
 
 class Checkpoint(C.Structure):
@@ -129,6 +132,7 @@ def lib():
         L.mpm_profile.argtypes = [vp, i]
         L.mpm_profile_read.argtypes = [vp, vp, vp]
         L.mpm_launch_count.argtypes = [vp, vp]
+        L.mpm_fp64_peak.argtypes = [vp, d, vp, vp]
         L.mpm_adjoint.argtypes = [vp, C.POINTER(Domain), C.POINTER(Rigid), C.POINTER(Adapt),
                                   C.POINTER(Material), C.POINTER(Checkpoint), i,
                                   C.POINTER(StepParams), vp, vp, vp, C.POINTER(AdjointStats)]
@@ -154,6 +158,20 @@ def domain(cfg):
     return d
 
 
+_TRI = {}  # device copies of triangulated bodies, by the id of their vertex array
+
+
+def _tri_device(mesh):
+    v = mesh["v"]
+    hit = _TRI.get(id(v))
+    if hit is None or hit[0] is not v:
+        tv = torch.as_tensor(np.ascontiguousarray(v, dtype=np.float64), device="cuda").contiguous()
+        tt = torch.as_tensor(np.ascontiguousarray(mesh["t"], dtype=np.int32), device="cuda").contiguous()
+        hit = (v, tv, tt)
+        _TRI[id(v)] = hit
+    return hit[1], hit[2]
+
+
 def rigid(cfg, z=None):
     r = Rigid()
     b = cfg.get("body")
@@ -161,6 +179,13 @@ def rigid(cfg, z=None):
         r.kind, r.cx, r.cy = b["kind"], b["cx"], b["cy"]
         r.z = b["z0"] if z is None else z
         r.r, r.alpha = b["r"], b.get("alpha", 0.0)
+        d = b.get("step_d", (0.0, 0.0, b.get("dz", 0.0)))
+        for k in range(3):
+            r.step_d[k] = d[k]
+        if b["kind"] == 3:
+            tv, tt = _tri_device(b["mesh"])
+            r.nvert, r.ntri = tv.shape[0], tt.shape[0]
+            r.tri_v, r.tri_t = tv.data_ptr(), tt.data_ptr()
     return r
 
 
@@ -175,6 +200,7 @@ def material(cfg):
         m.g[k] = cfg["g"][k]
     m.kappa, m.pf = cfg.get("kappa", 10.0), cfg.get("pf", 50.0)
     m.ghost_on, m.contact_on = int(cfg.get("ghost", 1)), int(cfg.get("contact", 1))
+    m.mu, m.pt = cfg.get("mu", 0.0), cfg.get("pt", 25.0)
     return m
 
 
@@ -399,10 +425,18 @@ def step(ctx, cfg, points, body_z=None, load=1.0, tol=1e-8, maxit=30, lin_tol=1e
                nnzb=ss.nnzb, res_hist=np.array(ss.res_hist[: ss.newton_its + 1]),
                eta_hist=np.array(ss.eta_hist[: ss.newton_its]), reaction=np.array(ss.reaction[:]),
                ms_build=ss.ms_build, ms_assemble=ss.ms_assemble, ms_solve=ss.ms_solve,
-               ms_update=ss.ms_update)
+               ms_update=ss.ms_update, nsrc=ss.nsrc, nslot=ss.nslot, mg_rows1=ss.mg_rows1,
+               mg_stencil1=ss.mg_stencil1)
     if check:
         ctx.check(st)
     return out
+
+
+def fp64_peak(ctx, seconds=1.0):
+    """mpm_fp64_peak: measured FP64 FMA throughput (flop/s) and the timed ms."""
+    f, ms = C.c_double(), C.c_double()
+    ctx.check(lib().mpm_fp64_peak(ctx.h, seconds, C.byref(f), C.byref(ms)))
+    return f.value, ms.value
 
 
 def blocks(ctx, mesh, K, precision=FP64):

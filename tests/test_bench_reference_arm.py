@@ -16,7 +16,7 @@ def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
                                                   points=dict(spacing=1.0 / 8, jitter=1.0 / 32)))
     monkeypatch.delenv("RANK", raising=False)
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "2",
-                                      "--warmup", "3"])
+                                      "--warmup", "3", "--cpu-procs", "1"])
     assert bench.main() == 0
     out = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
     assert len(out) == 1
@@ -31,6 +31,7 @@ def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
     assert line["value"] > 0 and line["ms_per_step"] > 0
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert cb["nproc"] >= 1 and cb["cpu_model"] and cb["dof"] > 0
     assert "depth 2->3" in cb["sample"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]

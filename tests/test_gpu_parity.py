@@ -33,6 +33,13 @@ def tiny_cfg(**over):
     return c
 
 
+def sphere_cfg():
+    c = tiny_cfg(mu=0.2)
+    c["body"] = dict(kind=3, cx=0.31, cy=0.42, z0=0.73, r=0.25, alpha=0.0, dz=-0.002,
+                     step_d=(0.003, 0.0, -0.002), mesh=inputs.sphere_mesh(0.25, 10, 12))
+    return c
+
+
 CASES = {
     "tiny_punch": lambda: (tiny_cfg(), 0.49),
     "column_d3": lambda: (inputs.workload("column"), None),
@@ -40,6 +47,17 @@ CASES = {
     "cone_d4_8": lambda: (inputs.workload("cone"), inputs.body_z(inputs.workload("cone"), 1)),
     "jitter_hang": lambda: (tiny_cfg(depth_min=2, depth_max=4, dx_region=0.1,
                                      points=dict(spacing=0.125, jitter=0.03, seed=5)), 0.47),
+    # Coulomb friction (Sec. 2.3, mu = 0.3 as in the paper's CPT and anchor
+    # runs) with the body also moving sideways over the step: stick and slip
+    "friction_punch": lambda: (dict(tiny_cfg(mu=0.3), body=dict(
+        tiny_cfg()["body"], step_d=(0.003, -0.001, -0.01))), 0.49),
+    # a closed triangulated body (Sec. 2.3's faceted rigid bodies): a coarse
+    # sphere pressed into the block, with friction and a sideways motion
+    "sphere_mesh": lambda: (sphere_cfg(), None),
+    # the benchmark's recipe one level coarser: 239 k points, 101 k unknowns,
+    # 3.6 M blocks, rows up to 171 blocks (the tangent's long-row pass)
+    "indent_small": lambda: (inputs.workload("indent_small"),
+                             inputs.body_z(inputs.workload("indent_small"), 1)),
 }
 
 
@@ -100,7 +118,8 @@ def free_mask(bcmask):
     return np.array([[not (m >> c) & 1 for c in range(3)] for m in bcmask]).ravel()
 
 
-@pytest.mark.parametrize("case", ["tiny_punch", "punch_d3_6", "cone_d4_8", "jitter_hang"])
+@pytest.mark.parametrize("case", ["tiny_punch", "punch_d3_6", "cone_d4_8", "jitter_hang",
+                                  "friction_punch", "sphere_mesh", "indent_small"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_assembly_matches_oracle(gpu, case, precision):
     mpm, ctx, torch = gpu
@@ -220,6 +239,36 @@ def test_punch_steps_match_oracle_fp64(gpu):
     assert pg["x"].shape == x0.shape
     d = np.max(np.abs(pg["x"] - po["x"]))
     assert d <= 1e-9 * 0.1 * 3 / 50
+    for k in ("F", "be", "lp"):
+        assert np.max(np.abs(pg[k] - po[k])) <= 1e-9 * max(1.0, np.abs(po[k]).max()), k
+
+
+def test_punch_steps_with_friction_match_oracle_fp64(gpu):
+    # Coulomb friction mu = 0.3 (non-symmetric tangent: BiCGStab on both sides)
+    cfg = inputs.workload("punch", mu=0.3)
+    om, P, ho, hg = run_steps(gpu, cfg, 3)
+    for a, b in zip(ho, hg):
+        assert np.max(np.abs(b["reaction"] - a["reaction"])) <= 1e-9 * abs(a["reaction"][2])
+    po, pg = om.points(), P.numpy()
+    assert np.max(np.abs(pg["x"] - po["x"])) <= 1e-9 * 0.1 * 3 / 50
+    for k in ("F", "be", "lp"):
+        assert np.max(np.abs(pg[k] - po[k])) <= 1e-9 * max(1.0, np.abs(po[k]).max()), k
+    # friction changes the load step against the frictionless run
+    om0, P0, ho0, hg0 = run_steps(gpu, inputs.workload("punch"), 1)
+    assert abs(hg[0]["reaction"][2] - hg0[0]["reaction"][2]) > 1e-6 * abs(hg0[0]["reaction"][2])
+
+
+def test_triangulated_punch_steps_with_friction_match_oracle_fp64(gpu):
+    # the flat punch as a closed 64-sided prism of triangles, mu = 0.3
+    cfg = inputs.workload("punch", mu=0.3)
+    cfg["body"] = dict(cfg["body"], kind=3, mesh=inputs.cylinder_mesh(0.1, 0.6, 64))
+    om, P, ho, hg = run_steps(gpu, cfg, 2)
+    for a, b in zip(ho, hg):
+        assert np.max(np.abs(b["reaction"] - a["reaction"])) <= 1e-9 * abs(a["reaction"][2])
+    po, pg = om.points(), P.numpy()
+    assert np.max(np.abs(pg["x"] - po["x"])) <= 1e-9 * 0.1 * 2 / 50
+    for k in ("F", "be", "lp"):
+        assert np.max(np.abs(pg[k] - po[k])) <= 1e-9 * max(1.0, np.abs(po[k]).max()), k
 
 
 def test_punch_steps_mixed_precision_within_1e6(gpu):
@@ -230,11 +279,20 @@ def test_punch_steps_mixed_precision_within_1e6(gpu):
 
 
 def test_cone_drucker_prager_step_matches_oracle(gpu):
+    # non-associated Drucker-Prager (BiCGStab) with the cone in contact: the
+    # reactions and every point array at 1e-9 after two load steps
     cfg = inputs.workload("cone")
-    om, P, ho, hg = run_steps(gpu, cfg, 2, tol=1e-10, lin_tol=1e-11)
+    om, P, ho, hg = run_steps(gpu, cfg, 2, tol=1e-12, lin_tol=1e-12)
     for a, b in zip(ho, hg):
         ra, rb = a["reaction"][2], b["reaction"][2]
-        assert abs(rb - ra) <= 1e-8 * abs(ra)
+        assert abs(rb - ra) <= 1e-9 * abs(ra)
+    po, pg = om.points(), P.numpy()
+    assert pg["x"].shape == po["x"].shape
+    x0 = inputs.make_points(cfg)["x"]
+    du_o = po["x"][:len(x0)] - x0
+    assert np.max(np.abs(pg["x"] - po["x"])) <= 1e-9 * max(np.abs(du_o).max(), 1e-12)
+    for k in ("F", "be", "lp"):
+        assert np.max(np.abs(pg[k] - po[k])) <= 1e-9 * max(1.0, np.abs(po[k]).max()), k
 
 
 # ---------------------------------------------------------------- edge cases
