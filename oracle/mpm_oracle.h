@@ -47,7 +47,8 @@ typedef struct {
   double body_r, body_alpha;         /* radius, cone half angle (rad)     */
   /* adaptivity (Sec. 5) */
   double dx_region, beta;
-  /* material (Sec. 2.2): 0 Hencky elastic, 1 von Mises, 2 Drucker-Prager */
+  /* material (Sec. 2.2): 0 Hencky elastic, 1 von Mises, 2 Drucker-Prager,
+   * 3 Drucker-Prager cone with the Willam-Warnke deviatoric section (Sec. 6.4) */
   int model;
   double nu, phi, psi;
   double g[3];

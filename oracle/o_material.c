@@ -11,6 +11,8 @@
  *    outer-cone match eta = 6 sin(phi)/(sqrt3 (3 - sin phi)),
  *    xi = 6 cos(phi)/(sqrt3 (3 - sin phi)); potential uses psi; cone return,
  *    apex return when the cone return overshoots the apex;
+ *  - model 3: the same cone with the Willam-Warnke deviatoric section
+ *    (Sec. 6.4) and the circular Drucker-Prager potential;
  *  - tangent: A_ijkm = 2 (d tau_ij / d b_kl) b_lm, built in the eigenbasis of
  *    b^tr from the principal algorithmic tangent d_ab = d tau_a / d eps_b and
  *    the shear ratio g = (tau_a - tau_b)/(eps_a - eps_b); the divided difference
@@ -101,6 +103,33 @@ static double dlog(double a, double b) {
   return log1p(x) / (a - b);
 }
 
+/* Willam-Warnke deviatoric section (Sec. 6.4, frictional cone of the CPT
+ * material): with c = cos(theta), theta the Lode angle (0 on the tensile
+ * meridian, pi/3 on the compressive one) and eccentricity e, the elliptic
+ * interpolation
+ *   r(c) = (4 a c^2 + b^2) / (2 a c + b sqrt(4 a c^2 + 5 e^2 - 4 e)),
+ * a = 1 - e^2, b = 2 e - 1, gives r = 1 on the compressive meridian and 1/e on
+ * the tensile one.  Returns r and dr/dzeta, zeta = cos(3 theta) (c solves
+ * 4 c^3 - 3 c = zeta; near the compressive meridian, where dc/dzeta is
+ * unbounded and dr/dc vanishes, the limit of their product is taken). */
+static double ww_r(double zeta, double e, double* dr_dzeta) {
+  if (zeta > 1.0) zeta = 1.0;
+  if (zeta < -1.0) zeta = -1.0;
+  double c = cos(acos(zeta) / 3.0);
+  double a = 1.0 - e * e, b = 2.0 * e - 1.0;
+  double w = sqrt(4.0 * a * c * c + 5.0 * e * e - 4.0 * e);
+  double N = 4.0 * a * c * c + b * b, D = 2.0 * a * c + b * w;
+  double r = N / D;
+  double dN = 8.0 * a * c, dD = 2.0 * a + 4.0 * a * b * c / w;
+  double rc = (dN * D - N * dD) / (D * D);
+  double q = 4.0 * c * c - 1.0;
+  if (fabs(q) > 1e-5)
+    *dr_dzeta = rc / (3.0 * q);
+  else
+    *dr_dzeta = 4.0 * a / (6.0 * b * b * (2.0 * c + 1.0));
+  return r;
+}
+
 /* principal return map: trial strains eps -> tau, d (3x3, d tau_a/d eps_b), g */
 static int return_map(const o_params* p, double E, double ys, const double* eps, double* tau,
                       double* d, double* g, int* plastic) {
@@ -156,6 +185,64 @@ static int return_map(const o_params* p, double E, double ys, const double* eps,
       for (int a = 0; a < 3; ++a) tau[a] = 2.0 * G * e[a] * ratio + pn;
       double ddg[3];
       for (int b = 0; b < 3; ++b) ddg[b] = (sqrt(2.0) * G * eh[b] + eta * Kb) / den;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double dev = (a == b ? 1.0 : 0.0) - 1.0 / 3.0;
+          d[3 * a + b] = 2.0 * G * dev -
+                         sqrt(2.0) * G * (eh[a] * ddg[b] + dg * (dev - eh[a] * eh[b]) / en) + Kb -
+                         Kb * etab * ddg[b];
+        }
+      *g = 2.0 * G * ratio;
+    } else {
+      *plastic = 2;
+      double pa = xi * c / eta;
+      for (int a = 0; a < 3; ++a) tau[a] = pa;
+      for (int i = 0; i < 9; ++i) d[i] = 0.0;
+      *g = 0.0;
+    }
+    return 0;
+  }
+  if (p->model == 3) {
+    /* frictional cone with the Willam-Warnke section and the non-associated
+     * Drucker-Prager potential (Sec. 6.4): f = sqrt(J2) r(theta) + eta p - xi c
+     * with the outer-cone eta, xi (r = 1 on the compressive meridian) and
+     * e = (3 - sin phi)/(3 + sin phi), the Mohr-Coulomb ratio of the tensile
+     * to the compressive meridian radius.  The potential sqrt(J2) + etab p has
+     * a circular section, so the return shrinks the deviator radially and
+     * keeps theta: f(dg) = (sqrt(J2) - G dg) r + eta (p - K etab dg) - xi c. */
+    double sphi = sin(p->phi), spsi = sin(p->psi);
+    double eta = 6.0 * sphi / (sqrt(3.0) * (3.0 - sphi));
+    double xi = 6.0 * cos(p->phi) / (sqrt(3.0) * (3.0 - sphi));
+    double etab = 6.0 * spsi / (sqrt(3.0) * (3.0 - spsi));
+    double ecc = (3.0 - sphi) / (3.0 + sphi);
+    double G = mu, c = ys;
+    double pm = Kb * tr;
+    double sj2 = sqrt(2.0) * G * en;
+    double r = 1.0, drz = 0.0, dz[3] = {0.0, 0.0, 0.0};
+    if (en > 0.0) {
+      /* zeta = cos(3 theta) = (3 sqrt3 / 2) J3 / J2^(3/2) = 3 sqrt6 e1 e2 e3 / |e|^3 */
+      double pr = e[0] * e[1] * e[2];
+      double zeta = 3.0 * sqrt(6.0) * pr / (en * en * en);
+      r = ww_r(zeta, ecc, &drz);
+      double mm[3] = {e[1] * e[2], e[0] * e[2], e[0] * e[1]};
+      double M = mm[0] + mm[1] + mm[2];
+      for (int b = 0; b < 3; ++b)
+        dz[b] = 3.0 * sqrt(6.0) * ((mm[b] - M / 3.0) / (en * en * en) - 3.0 * pr * e[b] / pow(en, 5.0));
+      if (zeta >= 1.0 || zeta <= -1.0) dz[0] = dz[1] = dz[2] = 0.0;
+    }
+    double f = sj2 * r + eta * pm - xi * c;
+    if (f <= 0.0) return 0;
+    *plastic = 1;
+    double den = G * r + Kb * eta * etab;
+    double dg = f / den;
+    if (sj2 - G * dg >= 0.0 && en > 0.0) {
+      double ratio = 1.0 - G * dg / sj2;
+      double pn = pm - Kb * etab * dg;
+      double eh[3] = {e[0] / en, e[1] / en, e[2] / en};
+      for (int a = 0; a < 3; ++a) tau[a] = 2.0 * G * e[a] * ratio + pn;
+      double ddg[3];
+      for (int b = 0; b < 3; ++b)
+        ddg[b] = (sqrt(2.0) * G * eh[b] * r + (sj2 - G * dg) * drz * dz[b] + eta * Kb) / den;
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
           double dev = (a == b ? 1.0 : 0.0) - 1.0 / 3.0;

@@ -513,7 +513,7 @@ int o_solve(o_model* m, const double* Kv, const double* b, double* x, double tol
   for (int i = 0; i < n3; ++i) r[i] = (m->bcmask[i / 3] & (1 << (i % 3))) ? 0.0 : b[i];
   double bn = sqrt(dot(n3, r, r));
   /* friction makes the contact stiffness non-symmetric */
-  int nonsym = (m->p.model == 2 && m->p.psi != m->p.phi) ||
+  int nonsym = (m->p.model == 2 && m->p.psi != m->p.phi) || m->p.model == 3 ||
                (m->p.mu > 0.0 && m->p.contact_on && m->p.body_kind != 0);
   st = O_ERR_KRYLOV;
   if (bn == 0.0) {

@@ -58,11 +58,26 @@ def lattice_points(lo, hi, spacing, rho, E, ys, jitter=0.0, seed=0, E_sigma=0.0)
     return pts
 
 
+def cpt_stiffness(depth, E_ref=19.2e6, gamma=16.3e3, phi=math.radians(32.0), m_E=0.6,
+                  p_ref=100e3):
+    """E50 of the CPT sand (Sec. 6.4): E_ref (sigma_v K0 / p_ref)^m_E with
+    sigma_v = gamma d (d the initial depth of the point centre, gamma the unit
+    weight) and K0 = 1 - sin(phi); p_ref, which the paper does not state, is
+    taken as the usual 100 kPa."""
+    K0 = 1.0 - math.sin(phi)
+    return E_ref * (gamma * np.asarray(depth) * K0 / p_ref) ** m_E
+
+
 def make_points(cfg):
     pc = cfg["points"]
-    return lattice_points(pc["lo"], pc["hi"], pc["spacing"], pc["rho"], pc["E"], pc["ys"],
-                          jitter=pc.get("jitter", 0.0), seed=pc.get("seed", 0),
-                          E_sigma=pc.get("E_sigma", 0.0))
+    pts = lattice_points(pc["lo"], pc["hi"], pc["spacing"], pc["rho"], pc["E"], pc["ys"],
+                         jitter=pc.get("jitter", 0.0), seed=pc.get("seed", 0),
+                         E_sigma=pc.get("E_sigma", 0.0))
+    if cfg.get("cpt"):
+        # fixed by each point's initial depth below the block top
+        pts["E"] = cpt_stiffness(pc["hi"][2] - pts["x"][:, 2], E_ref=pc["E"],
+                                 gamma=pc["rho"] * 9.81, phi=cfg["phi"])
+    return pts
 
 
 def sphere_mesh(radius, nlat=40, nlon=40):
@@ -120,6 +135,8 @@ def body_z(cfg, step):
 
 
 def load_factor(cfg, step):
+    if cfg.get("ramp_steps"):
+        return min(1.0, step / cfg["ramp_steps"])
     return step / cfg["nsteps"] if cfg.get("ramp_load", False) else 1.0
 
 
@@ -165,6 +182,23 @@ def workload(name, **over):
                  dx_region=2.0 * 1.6 / 256, nsteps=200,
                  points=dict(lo=(0, 0, 0), hi=(1, 1, 1.2), spacing=0.05, rho=1000.0,
                              E=2e7, ys=5e3, jitter=0.0125, seed=0))
+    elif name == "cpt":
+        # the cone penetration test of Sec. 6.4 on a quarter domain (symmetry
+        # planes x = 0 and y = 0 through the cone axis): the CPT sand of the
+        # material table (E50_ref 19.2 MPa, unit weight 16.3 kN/m3, nu 0.25,
+        # phi 32, psi 2, c 0.3 kPa, K0 0.47, m_E 0.6) as the Willam-Warnke cone
+        # (model 3), E fixed per point by its initial depth (cpt_stiffness),
+        # self-weight (ramped over the first 5 load steps, while the cone
+        # approaches), a 60-degree cone of radius 0.4 m with friction 0.3; the
+        # block 6.4 x 6.4 x 24.6 m in a 25.6 m cube, 1.6 m cells refined to
+        # 0.1 m within 0.2 m of the cone
+        c.update(L=25.6, depth_min=4, depth_max=8, bc=_block_rollers(6.4, 6.4), model=3,
+                 nu=0.25, phi=math.radians(32.0), psi=math.radians(2.0), mu=0.3,
+                 g=(0.0, 0.0, -9.81), dx_region=0.2, nsteps=300, cpt=True, ramp_steps=5,
+                 body=dict(kind=2, cx=0.0, cy=0.0, z0=24.6 + 0.135, r=0.4,
+                           alpha=math.radians(30.0), dz=-0.025),
+                 points=dict(lo=(0, 0, 0), hi=(6.4, 6.4, 24.6), spacing=0.8,
+                             rho=16.3e3 / 9.81, E=19.2e6, ys=300.0, jitter=0.1, seed=0))
     elif name == "adjoint":
         # the punch at depth 3 to 5, 20 load steps, lognormal E (sigma 0.2)
         c.update(L=1.0, depth_min=3, depth_max=5, bc=_block_rollers(1.0, 1.0), model=1,

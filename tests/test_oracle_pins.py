@@ -1143,3 +1143,184 @@ def test_global_tangent_matches_finite_difference_with_triangulated_body():
             for s_ in range(rp[i], rp[i + 1]):
                 Kv[3 * i:3 * i + 3] += K[s_] @ v[3 * col[s_]:3 * col[s_] + 3]
         assert np.linalg.norm(Kv - fd) <= 1e-6 * np.linalg.norm(fd)
+
+
+# ---------------------------------------------------------------- Willam-Warnke cone (Sec. 6.4)
+#
+# The CPT material's frictional cone with a Willam-Warnke deviatoric section
+# and a non-associated Drucker-Prager potential: f = sqrt(J2) r(theta) + eta p
+# - xi c, r = 1 on the compressive meridian (the outer Drucker-Prager cone)
+# and 1/e on the tensile one, e = (3 - sin phi)/(3 + sin phi) (the
+# Mohr-Coulomb ratio of the two meridian radii).
+
+def ww_cfg(phi=32.0, psi=2.0):
+    return inputs.workload("cone", model=3, phi=math.radians(phi), psi=math.radians(psi))
+
+
+def stress_invariants(tau):
+    p = np.trace(tau) / 3
+    s = tau - p * np.eye(3)
+    J2 = 0.5 * np.sum(s * s)
+    J3 = np.linalg.det(s)
+    zeta = np.clip(1.5 * math.sqrt(3) * J3 / J2 ** 1.5, -1, 1)
+    return p, math.sqrt(J2), math.acos(zeta) / 3
+
+
+def mohr_coulomb_radius_ratio(phi):
+    # deviatoric radius of the Mohr-Coulomb hexagon on the tensile over the
+    # compressive meridian, from the Mohr-Coulomb criterion written out in
+    # principal stresses (tension positive): (s1 - s3) = -(s1 + s3) sin phi
+    # + 2 c cos phi at p = 0, c = 1
+    out = []
+    for lode in ("t", "c"):
+        # s = k (2, -1, -1)/sqrt6 (tensile) or k (1, 1, -2)/sqrt6 (compressive)
+        d = np.array([2, -1, -1]) / math.sqrt(6) if lode == "t" else np.array([1, 1, -2]) / math.sqrt(6)
+        s1, s3 = d.max(), d.min()
+        k = 2 * math.cos(math.radians(phi)) / ((s1 - s3) + (s1 + s3) * math.sin(math.radians(phi)))
+        out.append(k)
+    return out[0] / out[1]
+
+
+def test_willam_warnke_meridians_match_mohr_coulomb_and_drucker_prager():
+    G, K, E = None, None, 2e7
+    c = 5e3
+    for phi in (20.0, 32.0, 40.0):
+        cfg = ww_cfg(phi, 2.0)
+        sphi = math.sin(math.radians(phi))
+        eta = 6 * sphi / (math.sqrt(3) * (3 - sphi))
+        xi = 6 * math.cos(math.radians(phi)) / (math.sqrt(3) * (3 - sphi))
+        e = (3 - sphi) / (3 + sphi)
+        assert abs(e - mohr_coulomb_radius_ratio(phi)) < 1e-12
+        # compressive meridian (axial shortening with equal lateral strains):
+        # identical to the outer-cone Drucker-Prager return
+        dF = np.diag([1.0 + 0.008, 1.0 + 0.008, 1.0 - 0.015])
+        t3, _, _, pl3 = oracle.constitutive(cfg, E, c, np.array([1, 1, 1, 0, 0, 0.0]), dF)
+        t2, _, _, pl2 = oracle.constitutive(dict(cfg, model=2), E, c, np.array([1, 1, 1, 0, 0, 0.0]), dF)
+        assert pl3 == 1 and pl2 == 1
+        assert np.allclose(t3, t2, rtol=0, atol=1e-9 * c)
+        p, sj, th = stress_invariants(t3)
+        assert abs(th - math.pi / 3) < 1e-6
+        # tensile meridian (axial extension): yields at e times that radius
+        dF = np.diag([1.0 - 0.006, 1.0 - 0.006, 1.0 + 0.01])
+        t3, _, _, pl3 = oracle.constitutive(cfg, E, c, np.array([1, 1, 1, 0, 0, 0.0]), dF)
+        assert pl3 == 1
+        p, sj, th = stress_invariants(t3)
+        assert abs(th) < 1e-6
+        assert abs(sj - e * (xi * c - eta * p)) < 1e-9 * c
+
+
+def test_willam_warnke_return_is_consistent_keeps_lode_angle_and_section_is_convex():
+    cfg = ww_cfg()
+    E, c = 2e7, 5e3
+    rng = np.random.default_rng(31)
+    sphi = math.sin(math.radians(32.0))
+    eta = 6 * sphi / (math.sqrt(3) * (3 - sphi))
+    xi = 6 * math.cos(math.radians(32.0)) / (math.sqrt(3) * (3 - sphi))
+    n_pl = 0
+    for _ in range(40):
+        dF = np.eye(3) + 0.02 * rng.normal(size=(3, 3)) - 0.01 * np.eye(3)
+        el, _, _, _ = oracle.constitutive(dict(cfg, model=0), E, c, np.array([1, 1, 1, 0, 0, 0.0]), dF)
+        t, _, _, pl = oracle.constitutive(cfg, E, c, np.array([1, 1, 1, 0, 0, 0.0]), dF)
+        if pl != 1:
+            continue
+        n_pl += 1
+        p, sj, th = stress_invariants(t)
+        pe, sje, the = stress_invariants(el)
+        assert abs(th - the) < 1e-7  # radial return: the Lode angle is kept
+        # consistency: the section radius at this Lode angle
+        r = ww_radius(th, (3 - sphi) / (3 + sphi))
+        assert abs(sj * r + eta * p - xi * c) < 1e-8 * c
+    assert n_pl >= 10
+    # the deviatoric section rho(theta) = 1 / r(theta) is convex
+    e = (3 - sphi) / (3 + sphi)
+    th = np.linspace(0, math.pi / 3, 400)
+    rho = 1.0 / np.array([ww_radius(t, e) for t in th])
+    x, y = rho * np.cos(th), rho * np.sin(th)
+    cross = (x[1:-1] - x[:-2]) * (y[2:] - y[1:-1]) - (y[1:-1] - y[:-2]) * (x[2:] - x[1:-1])
+    assert np.all(cross > 0)
+
+
+def ww_radius(theta, e):
+    # the Willam-Warnke elliptic interpolation written in terms of theta
+    a, b = 1 - e * e, 2 * e - 1
+    c = math.cos(theta)
+    return (4 * a * c * c + b * b) / (2 * a * c + b * math.sqrt(4 * a * c * c + 5 * e * e - 4 * e))
+
+
+@pytest.mark.parametrize("psi", [2.0, 32.0])
+def test_willam_warnke_spatial_tangent_matches_finite_difference(psi):
+    cfg = ww_cfg(32.0, psi)
+    E, ys = 2e7, 5e3
+    rng = np.random.default_rng(8)
+    be = np.array([1.02, 0.99, 1.01, 0.01, -0.005, 0.002])
+    checked = 0
+    for _ in range(6):
+        dF = np.eye(3) + 0.01 * rng.normal(size=(3, 3)) - 0.003 * np.eye(3)
+        tau, _, A, pl = oracle.constitutive(cfg, E, ys, be, dF)
+        if pl != 1:
+            continue
+        checked += 1
+        h = 1e-7
+        for k in range(3):
+            for mm in range(3):
+                Lp = np.zeros((3, 3))
+                Lp[k, mm] = h
+                tp, _, _, _ = oracle.constitutive(cfg, E, ys, be, (np.eye(3) + Lp) @ dF, tangent=False)
+                tm, _, _, _ = oracle.constitutive(cfg, E, ys, be, (np.eye(3) - Lp) @ dF, tangent=False)
+                fd = (tp - tm) / (2 * h)
+                assert np.allclose(A[:, :, k, mm], fd, atol=2e-6 * E, rtol=0), (k, mm)
+    assert checked >= 2
+
+
+def test_global_tangent_matches_finite_difference_willam_warnke_with_cone():
+    # (the directions avoid cone/apex and contact switches within the FD step)
+    cfg = cone_cfg(model=3, phi=math.radians(32.0), psi=math.radians(2.0))
+    z0 = cfg["body"]["z0"]
+    m = built(cfg, body_z=z0 - 0.06)
+    c = m.counts()
+    n3 = 3 * c["ndof"]
+    du = 1e-3 * np.random.default_rng(17).normal(size=n3)
+    out = m.assemble(du)
+    rp, col = m.pattern()
+    K = out["K"]
+    h = 1e-7
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        v = rng.normal(size=n3)
+        fd = (m.assemble(du + h * v, tangent=False)["R"] -
+              m.assemble(du - h * v, tangent=False)["R"]) / (2 * h)
+        Kv = np.zeros(n3)
+        for i in range(c["ndof"]):
+            for s_ in range(rp[i], rp[i + 1]):
+                Kv[3 * i:3 * i + 3] += K[s_] @ v[3 * col[s_]:3 * col[s_] + 3]
+        assert np.linalg.norm(Kv - fd) <= 1e-6 * np.linalg.norm(fd)
+
+
+def test_cpt_workload_follows_the_paper_table_and_stiffness_law():
+    # Sec. 6.4: the CPT sand's constants, K0 = 1 - sin(phi) (Jaky), and E50
+    # fixed per point by its initial depth d: E50_ref (gamma d K0 / p_ref)^m_E
+    g = read_golden("paper_constants.txt")
+    cfg = inputs.workload("cpt")
+    pc = cfg["points"]
+    assert pc["E"] == g["cpt_E50_ref"][0] and cfg["nu"] == g["cpt_nu"][0]
+    assert abs(pc["rho"] * 9.81 - g["cpt_unit_weight"][0]) < 1e-9
+    assert abs(math.degrees(cfg["phi"]) - g["cpt_phi"][0]) < 1e-12
+    assert abs(math.degrees(cfg["psi"]) - g["cpt_psi"][0]) < 1e-12
+    assert pc["ys"] == g["cpt_cohesion"][0] and cfg["mu"] == g["cpt_mu"][0]
+    assert cfg["model"] == 3
+    assert abs((1 - math.sin(cfg["phi"])) - g["cpt_K0"][0]) < 5e-3
+    b = cfg["body"]
+    assert b["r"] == g["cpt_cone_radius"][0]
+    assert abs(2 * math.degrees(b["alpha"]) - g["cpt_cone_apex_angle"][0]) < 1e-12
+    # quarter domain: half the width, rollers on the symmetry planes through the axis
+    assert pc["hi"][0] == g["cpt_Lx"][0] / 2 and pc["hi"][2] == g["cpt_Lz"][0]
+    assert b["cx"] == 0.0 and b["cy"] == 0.0
+    assert (0, 0.0, inputs.ROLLER_X) in cfg["bc"] and (1, 0.0, inputs.ROLLER_Y) in cfg["bc"]
+    pts = inputs.make_points(cfg)
+    d = pc["hi"][2] - pts["x"][:, 2]
+    K0 = 1 - math.sin(math.radians(g["cpt_phi"][0]))
+    for k in (0, len(d) // 2, len(d) - 1):
+        e = g["cpt_E50_ref"][0] * (g["cpt_unit_weight"][0] * d[k] * K0 / 100e3) ** g["cpt_mE"][0]
+        assert abs(pts["E"][k] - e) < 1e-9 * e
+    # at 10 m depth: 19.2 MPa (16.3 * 10 * 0.47 / 100)^0.6 = about 15.7 MPa
+    assert abs(inputs.cpt_stiffness(10.0) - 19.2e6 * (16.3 * 10 * K0 / 100) ** 0.6) < 1e-6
