@@ -384,7 +384,9 @@ def compare_arms(mixed, fp64):
         same = ev(a) == ev(b)
         if not same and first is None:
             first = n
-        steps.append({"step": n, "events_match": same, "reaction_rel": float(rel)})
+        steps.append({"step": n, "events_match": same, "reaction_rel": float(rel),
+                      "newton_its": [a["newton_its"], b["newton_its"]],
+                      "line_search_eta": [list(map(float, a["eta_hist"])), list(map(float, b["eta_hist"]))]})
     before = [s["reaction_rel"] for s in steps if first is None or s["step"] < first]
     return {"events_match_fp64": first is None, "first_event_divergence_step": first,
             "reaction_mixed_vs_fp64_rel_max_before_divergence": max(before) if before else None,

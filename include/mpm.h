@@ -95,7 +95,10 @@ typedef struct {
 } mpm_adapt;
 
 /* Material of Sec. 2.2 (model 0 Hencky elastic, 1 von Mises, 2 Drucker-Prager
- * with friction phi and dilation psi in radians), gravity g (Eq. MPMweak body
+ * with friction phi and dilation psi in radians, 3 the CPT material of Sec.
+ * 6.4: the frictional cone with a Willam-Warnke deviatoric section, radius 1
+ * on the compressive and (3 - sin phi)/(3 + sin phi) on the tensile meridian
+ * relative to model 2's outer cone, with model 2's potential), gravity g (Eq. MPMweak body
  * force), ghost constant kappa (Sec. 4), contact penalty factors pf (normal,
  * eps_N = pf E_p (V0_p)^(2/3)) and pt (tangential, eps_T = pt E_p (V0_p)^(2/3))
  * and the Coulomb friction coefficient mu between body and material (Sec.

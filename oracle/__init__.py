@@ -280,8 +280,12 @@ class Model:
         sp = StepParams(load, tol, maxit, lin_tol, lin_maxit)
         ss = StepStats()
         lib().o_step(self.h, C.byref(sp), C.byref(ss))
+        nh = ss.newton_its + 1
+        if ss.status:  # the whole history of a step that did not converge
+            h = np.array(ss.res_hist[: min(maxit + 1, 64)])
+            nh = int(np.max(np.nonzero(h)[0], initial=0)) + 1
         return dict(status=ss.status, newton_its=ss.newton_its, lin_its=ss.lin_its_total,
-                    res_hist=np.array(ss.res_hist[: ss.newton_its + 1]),
+                    res_hist=np.array(ss.res_hist[:nh]),
                     eta_hist=np.array(ss.eta_hist[: ss.newton_its]),
                     reaction=np.array(ss.reaction[:]))
 

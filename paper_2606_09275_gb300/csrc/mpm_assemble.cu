@@ -256,12 +256,15 @@ __global__ void k_tangent_state(int P, const double* __restrict__ lawst, const d
 }
 
 // grad_x S = grad S . dF^{-1} for the tangent gather (in its precision), without
-// the internal force
+// the internal force; also V0 in that precision, so that the gather converts
+// nothing (a conversion from FP64 occupies the slow FP64 pipe)
 template <class TG>
 __global__ void k_gx(int P, const int* __restrict__ nsup, const double* __restrict__ dS,
-                     const double* __restrict__ dFinv, TG* gx) {
+                     const double* __restrict__ dFinv, const double* __restrict__ V0, TG* gx,
+                     TG* V0t) {
   int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (w >= P) return;
+  if (lane == 0) V0t[w] = (TG)V0[w];
   TG fi[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) fi[i] = (TG)dFinv[9 * (size_t)w + i];
@@ -334,7 +337,6 @@ __global__ void k_residual_rows(int nd, int P, double load, const long long* __r
 
 constexpr int TW = 4;  // warps per block of the tangent gather (at most)
 
-
 // open-addressing table of a row's columns (dof -> position in the row), in
 // shared memory: a power of two at least twice the longest row
 __host__ __device__ inline int tangent_hash_size(int mr) {
@@ -343,9 +345,17 @@ __host__ __device__ inline int tangent_hash_size(int mr) {
   return h;
 }
 
+// a block's 9 accumulators, padded to a 16-byte multiple so that one column
+// is read and written with vector accesses: 12 floats or 10 doubles
+template <class T>
+__host__ __device__ constexpr int tangent_acc_stride() {
+  return sizeof(T) == 4 ? 12 : 10;
+}
+
 template <class T>
 __host__ __device__ inline size_t tangent_warp_bytes(int mr) {
-  return (size_t)mr * 9 * sizeof(T) + 32 * sizeof(T) + (size_t)tangent_hash_size(mr) * 2 * sizeof(int);
+  return (size_t)mr * tangent_acc_stride<T>() * sizeof(T) + 32 * sizeof(T) +
+         (size_t)tangent_hash_size(mr) * 2 * sizeof(int);
 }
 
 __device__ inline unsigned tangent_hash(int c, int hmask) {
@@ -375,27 +385,97 @@ __device__ inline void tangent_terms(const double* Tt, double* t) {
   }
 }
 
+// acc[0..8] += the block t (x) g of one (source, column) pair, with vector
+// shared-memory accesses
+__device__ inline void tangent_add(float* a, const float* t, float g0, float g1, float g2) {
+  float4* v = reinterpret_cast<float4*>(a);
+  float4 x = v[0], y = v[1];
+  float z = a[8];
+  x.x += t[0] * g0 + t[1] * g1 + t[2] * g2;
+  x.y += t[3] * g0 + t[4] * g1 + t[5] * g2;
+  x.z += t[6] * g0 + t[7] * g1 + t[8] * g2;
+  x.w += t[9] * g0 + t[10] * g1 + t[11] * g2;
+  y.x += t[12] * g0 + t[13] * g1 + t[14] * g2;
+  y.y += t[15] * g0 + t[16] * g1 + t[17] * g2;
+  y.z += t[18] * g0 + t[19] * g1 + t[20] * g2;
+  y.w += t[21] * g0 + t[22] * g1 + t[23] * g2;
+  z += t[24] * g0 + t[25] * g1 + t[26] * g2;
+  v[0] = x;
+  v[1] = y;
+  a[8] = z;
+}
+__device__ inline void tangent_add(double* a, const double* t, double g0, double g1, double g2) {
+  double2* v = reinterpret_cast<double2*>(a);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    double2 x = v[i];
+    x.x += t[6 * i] * g0 + t[6 * i + 1] * g1 + t[6 * i + 2] * g2;
+    x.y += t[6 * i + 3] * g0 + t[6 * i + 4] * g1 + t[6 * i + 5] * g2;
+    v[i] = x;
+  }
+  a[8] += t[24] * g0 + t[25] * g1 + t[26] * g2;
+}
+
+// the loads of one source (point w, local index k) of a row, issued together:
+// lane l holds the l-th column of the point's support and its grad_x S, lanes
+// < 27 three entries of A'_p for the 27 terms
+template <class T>
+struct TangentSrc {
+  int w, n, c;
+  T v0, gk0, gk1, gk2, a0, a1, a2, g0, g1, g2;
+};
+
+template <class T>
+__device__ inline void tangent_fetch(TangentSrc<T>& s, uint32_t sid, int P, int lane,
+                                     const int* __restrict__ nsup, const int* __restrict__ sidx,
+                                     const T* __restrict__ gx, const T* __restrict__ Aalg,
+                                     const T* __restrict__ V0) {
+  int w = (int)(sid >> 6), k = (int)(sid & 63);
+  s.w = w < P ? w : -1;  // w >= P: a ghost-face source, no point tangent
+  if (s.w < 0) return;
+  size_t ok = ((size_t)w * MAXS + k) * 3;
+  s.gk0 = gx[ok];
+  s.gk1 = gx[ok + 1];
+  s.gk2 = gx[ok + 2];
+  s.v0 = V0[w];
+  s.n = nsup[w];
+  if (lane < 27) {
+    const T* A = Aalg + 81 * (size_t)w + 3 * lane;
+    s.a0 = A[0];
+    s.a1 = A[1];
+    s.a2 = A[2];
+  }
+  // lane < MAXS: inside the point's slot range whatever its support size
+  size_t o = (size_t)w * MAXS + lane;
+  s.c = sidx[o];
+  s.g0 = gx[3 * o];
+  s.g1 = gx[3 * o + 1];
+  s.g2 = gx[3 * o + 2];
+}
+
 // One warp owns block row r: for every point p with r in its support (local
 // index k), K_{r,w} += V0_p (grad_x S_k)^T A'_p (grad_x S_w) for all w in the
 // support of p.  The row accumulates in shared memory (mr = longest row, a
 // multiple of 4), in source order, free of atomics and deterministic; the
-// position of a column in the row comes from a per-row hash table, and the 27
-// entries of (grad_x S_k)^T A'_p sit in registers while the point's support
-// is swept.  Ghost coefficients and the Dirichlet identity rows/columns are
+// position of a column in the row comes from a per-row hash table.  Ghost coefficients and the Dirichlet identity rows/columns are
 // applied when the row is written out, coalesced, in the sliced layout.
-template <class T>
+// UPPER (a symmetric tangent: Hencky, von Mises, frictionless contact): only
+// the blocks of columns c >= r are formed and written, about half the work;
+// k_tangent_mirror then copies each into its transposed place.
+template <class T, bool UPPER>
 __global__ void __launch_bounds__(32 * TW)
     k_tangent_rows(int nd, int P, int minlen, int mr, int last, const int* __restrict__ rp,
                    const int* __restrict__ col,
                    Sliced S, const long long* __restrict__ sptr, const uint64_t* __restrict__ skeys,
                    const int* __restrict__ nsup, const int* __restrict__ sidx,
                    const T* __restrict__ gx, const T* __restrict__ Aalg,
-                   const double* __restrict__ V0, const double* __restrict__ kg,
+                   const T* __restrict__ V0, const double* __restrict__ kg,
                    const int* __restrict__ mask, T* K, int* err) {
+  constexpr int AS = tangent_acc_stride<T>();
   extern __shared__ __align__(16) unsigned char smraw[];
   int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* acc = (T*)(smraw + wi * tangent_warp_bytes<T>(mr));
-  T* Tt = acc + 9 * (size_t)mr;
+  T* Tt = acc + AS * (size_t)mr;
   int* hkey = (int*)(Tt + 32);
   int hs = tangent_hash_size(mr), hmask = hs - 1;
   int* hval = hkey + hs;
@@ -409,7 +489,7 @@ __global__ void __launch_bounds__(32 * TW)
     return;
   }
   for (int i = lane; i < hs; i += 32) hkey[i] = -1;
-  for (int i = lane; i < 9 * nb; i += 32) acc[i] = (T)0;
+  for (int i = lane; i < AS * nb; i += 32) acc[i] = (T)0;
   __syncwarp();
   for (int i = lane; i < nb; i += 32) {
     int c = col[s0 + i];
@@ -425,31 +505,34 @@ __global__ void __launch_bounds__(32 * TW)
     int cnt = (int)min(32LL, q1 - qb);
     uint32_t kb = lane < cnt ? (uint32_t)skeys[qb + lane] : 0u;
     for (int u = 0; u < cnt; ++u) {
-      uint32_t sid = __shfl_sync(FULL, kb, u);
-      int w = (int)(sid >> 6), k = (int)(sid & 63);
-      if (w >= P) continue;  // ghost-face source: no point tangent
-      size_t ok = ((size_t)w * MAXS + k) * 3;
-      T gk0 = gx[ok], gk1 = gx[ok + 1], gk2 = gx[ok + 2];
-      T v0 = (T)V0[w];
-      if (lane < 27) {
-        const T* A = Aalg + 81 * (size_t)w + 3 * lane;
-        Tt[lane] = v0 * (gk0 * A[0] + gk1 * A[1] + gk2 * A[2]);
-      }
+      TangentSrc<T> s;
+      tangent_fetch(s, __shfl_sync(FULL, kb, u), P, lane, nsup, sidx, gx, Aalg, V0);
+      if (s.w < 0) continue;  // the same for every lane
+      if (lane < 27) Tt[lane] = s.v0 * (s.gk0 * s.a0 + s.gk1 * s.a1 + s.gk2 * s.a2);
       __syncwarp();
       T t[27];
       tangent_terms(Tt, t);
-      int n = nsup[w];
-      for (int l = lane; l < n; l += 32) {
-        size_t o = (size_t)w * MAXS + l;
-        int c = sidx[o];
-        T g0 = gx[3 * o], g1 = gx[3 * o + 1], g2 = gx[3 * o + 2];
+      for (int l = lane; l < s.n; l += 32) {
+        int c;
+        T g0, g1, g2;
+        if (l == lane) {
+          c = s.c;
+          g0 = s.g0;
+          g1 = s.g1;
+          g2 = s.g2;
+        } else {  // supports of more than 32 nodes (deep hanging chains)
+          size_t o = (size_t)s.w * MAXS + l;
+          c = sidx[o];
+          g0 = gx[3 * o];
+          g1 = gx[3 * o + 1];
+          g2 = gx[3 * o + 2];
+        }
+        if (UPPER && c < r) continue;
         unsigned h = tangent_hash(c, hmask);
         int key;
         while ((key = hkey[h]) != c && key != -1) h = (h + 1) & hmask;
         if (key != c) continue;
-        int idx = hval[h];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) acc[e * nb + idx] += t[3 * e] * g0 + t[3 * e + 1] * g1 + t[3 * e + 2] * g2;
+        tangent_add(acc + AS * hval[h], t, g0, g1, g2);
       }
       __syncwarp();
     }
@@ -466,19 +549,63 @@ __global__ void __launch_bounds__(32 * TW)
       for (int e = 0; e < 9; ++e) K[sliced_entry(b0, W, slot, e)] = (T)0;
       continue;
     }
-    T kv = (T)kg[s0 + i];
+    // the ghost coefficient is zero away from the cut cells: convert only
+    // where some lane of the warp has one
+    double kd = kg[s0 + i];
+    T kv = __any_sync(__activemask(), kd != 0.0) ? (T)kd : (T)0;
     int c = col[s0 + i];
+    if (UPPER && c < r) continue;  // written by k_tangent_mirror
     int mc = mask[c];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
         int e = 3 * a + b;
-        T v = acc[e * nb + i];
+        T v = acc[AS * i + e];
         if (a == b) v += kv;
         if (((mr_ >> a) & 1) || ((mc >> b) & 1)) v = (c == r && a == b) ? (T)1 : (T)0;
         K[sliced_entry(b0, W, slot, e)] = v;
       }
+  }
+}
+
+// the lower blocks of a symmetric tangent: block (r, c), c < r, is the
+// transpose of block (c, r), found by binary search in row c (one warp per row)
+template <class T>
+__global__ void k_tangent_mirror(int nd, const int* __restrict__ rp, const int* __restrict__ col,
+                                 Sliced S, T* K) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int r = (int)(t >> 5), lane = (int)(t & 31);
+  if (r >= nd) return;
+  int s0 = rp[r], nb = rp[r + 1] - s0;
+  int sl = r >> 5, W = S.w[sl];
+  long long b0 = S.base[sl];
+  for (int i = lane; i < nb; i += 32) {
+    int c = col[s0 + i];
+    if (c >= r) break;  // columns sorted: the rest is the upper part
+    int lo = rp[c], hi = rp[c + 1] - 1, j = -1;
+    while (lo <= hi) {
+      int mid = (lo + hi) >> 1, v = col[mid];
+      if (v == r) {
+        j = mid;
+        break;
+      }
+      if (v < r)
+        lo = mid + 1;
+      else
+        hi = mid - 1;
+    }
+    if (j < 0) continue;  // (the pattern is symmetric: never)
+    int slc = c >> 5, Wc = S.w[slc];
+    long long bc = S.base[slc], sc = sliced_slot(bc, c, j - rp[c]);
+    T v[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) v[e] = K[sliced_entry(bc, Wc, sc, e)];
+    long long slot = sliced_slot(b0, r, i);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) K[sliced_entry(b0, W, slot, 3 * a + b)] = v[3 * b + a];
   }
 }
 
@@ -726,6 +853,25 @@ void contact_terms(mpm_ctx* c, mpm_mesh* m, const mpm_material& mat, const mpm_r
 
 }  // namespace
 
+namespace {
+
+// one pass of the tangent gather (rows of lo < length <= hi blocks)
+template <class T>
+void tangent_launch(mpm_ctx* c, mpm_mesh* m, bool upper, int tw, size_t smem, int lo, int hi, int last,
+                    const void* gx, const void* Aalg, const void* V0t, void* K) {
+  cudaStream_t st = c->stream;
+  int nd = m->ndof, P = m->np;
+  Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+  auto kern = upper ? k_tangent_rows<T, true> : k_tangent_rows<T, false>;
+  MPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  MPM_LAUNCH_P(MPM_PROF_TANGENT, kern<<<grid_for(nd, tw), 32 * tw, smem, st>>>(
+      nd, P, lo, hi, last, ptr<int>(m->row_ptr), ptr<int>(m->col), S, ptr<long long>(m->src_ptr),
+      ptr<uint64_t>(m->src_key), ptr<int>(m->nsup), ptr<int>(m->sidx), (const T*)gx, (const T*)Aalg,
+      (const T*)V0t, ptr<double>(m->kg), ptr<int>(m->dof_mask), (T*)K, c->d_err));
+}
+
+}  // namespace
+
 void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm_rigid& body,
               const double* du, double load, int precision, double* R, void* K, AsmOut* out,
               bool want_norms, bool reuse) {
@@ -749,6 +895,7 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
   size_t asz = mixed ? sizeof(float) : sizeof(double);
   void* Aalg = K ? grow_bytes(c, m->Aalg, 81 * (size_t)P * asz) : nullptr;
   void* gx = K ? grow_bytes(c, m->gx, 3 * (size_t)P * MAXS * asz) : nullptr;
+  void* V0t = K ? grow_bytes(c, m->V0t, (size_t)P * asz) : nullptr;
   double* fint = grow<double>(c, c->v[0], 3 * (size_t)nd);
   double* fc = grow<double>(c, c->v[1], 3 * (size_t)nd);
   bool contact = m->ncand && mat.contact_on && body.kind != 0;
@@ -760,10 +907,10 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
     // dF, dF^-1, tau and spectral state are still in place, R is complete
     if (mixed) {
       MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_tangent_state<float><<<grid_for(P, 128), 128, 0, st>>>(P, lawst, tau, (float*)Aalg));
-      MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<float><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, (float*)gx));
+      MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<float><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, V0, (float*)gx, (float*)V0t));
     } else {
       MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_tangent_state<double><<<grid_for(P, 128), 128, 0, st>>>(P, lawst, tau, (double*)Aalg));
-      MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<double><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, (double*)gx));
+      MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<double><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, V0, (double*)gx, (double*)V0t));
     }
   } else {
     MPM_LAUNCH_P(MPM_PROF_KINEMATICS, k_kinematics<<<grid_for(8LL * P, 256), 256, 0, st>>>(P, nsup, sidx, dS, du, dF));
@@ -785,15 +932,22 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
         ptr<double>(m->kg), du, ptr<double>(m->fext), fint, R));
     if (K) {
       if (mixed)
-        MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<float><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, (float*)gx));
+        MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<float><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, V0, (float*)gx, (float*)V0t));
       else
-        MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<double><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, (double*)gx));
+        MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<double><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, V0, (double*)gx, (double*)V0t));
     }
   }
   if (K) {
     // two passes: rows up to 128 blocks (the 5^3 interior stencil and below)
     // with a small shared-memory footprint per warp, for occupancy, then the
-    // longer rows near hanging nodes
+    // longer rows near hanging nodes; a symmetric tangent forms only its upper
+    // blocks and mirrors them
+    // a symmetric FP64 tangent forms only its upper blocks and mirrors them:
+    // its pairs are bound by the FP64 FMA rate, which the halving pays for
+    // (about 5 ms of 108 per load step at the indentation workload); the FP32
+    // gather is bound by its per-source loads and table lookups instead, and
+    // the mirror pass would cost more than the halved pairs save
+    bool upper = !mixed && (mat.model == 0 || mat.model == 1) && !(mat.mu > 0.0 && contact);
     int mr = (m->maxrow + 3) & ~3;
     const int SHORT = 128;
     int passes[2][2] = {{-1, std::min(mr, SHORT)}, {SHORT, mr}};
@@ -804,19 +958,16 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
       int tw = (int)std::min<size_t>(TW, (size_t)(220 * 1024) / wb);
       if (tw < 1) throw CudaError(MPM_ERR_SUPPORT, "stiffness row too long for the tangent gather");
       size_t smem = wb * tw;
-      if (mixed) {
-        MPM_CUDA(cudaFuncSetAttribute(k_tangent_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<float><<<grid_for(nd, tw), 32 * tw, smem, st>>>(
-            nd, P, lo, hi, last, rp, col, S, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup,
-            sidx, (const float*)gx, (const float*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
-            (float*)K, c->d_err));
-      } else {
-        MPM_CUDA(cudaFuncSetAttribute(k_tangent_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_rows<double><<<grid_for(nd, tw), 32 * tw, smem, st>>>(
-            nd, P, lo, hi, last, rp, col, S, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup,
-            sidx, (const double*)gx, (const double*)Aalg, V0, ptr<double>(m->kg), ptr<int>(m->dof_mask),
-            (double*)K, c->d_err));
-      }
+      if (mixed)
+        tangent_launch<float>(c, m, upper, tw, smem, lo, hi, last, gx, Aalg, V0t, K);
+      else
+        tangent_launch<double>(c, m, upper, tw, smem, lo, hi, last, gx, Aalg, V0t, K);
+    }
+    if (upper) {
+      if (mixed)
+        MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_mirror<float><<<grid_for(32LL * nd, 256), 256, 0, st>>>(nd, rp, col, S, (float*)K));
+      else
+        MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_mirror<double><<<grid_for(32LL * nd, 256), 256, 0, st>>>(nd, rp, col, S, (double*)K));
     }
     int npad = 32 * m->nslice;
     if (npad > nd) {

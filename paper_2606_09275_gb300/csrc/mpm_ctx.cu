@@ -3,6 +3,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cstdlib>
+
 #include "mpm_internal.cuh"
 
 namespace mpm {
@@ -119,6 +121,10 @@ extern "C" int mpm_create(mpm_ctx** out, void* stream) {
     MPM_CUDA(cudaMallocAsync((void**)&c->d_err, sizeof(int), c->stream));
     MPM_CUDA(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     MPM_CUDA(cudaMallocAsync((void**)&c->d_red, 64 * sizeof(double), c->stream));
+    // CUDA graphs for the V-cycle (MPM_GRAPHS=0 in the environment: plain
+    // launches, for comparison)
+    const char* eg = getenv("MPM_GRAPHS");
+    if (!(eg && eg[0] == '0')) MPM_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     MPM_CUDA(cudaMallocAsync((void**)&c->d_ticket, 16, c->stream));
     MPM_CUDA(cudaMemsetAsync(c->d_ticket, 0, 16, c->stream));
     grid_red(c, 4, 4096);
@@ -148,12 +154,12 @@ void mesh_release(mpm_mesh* m) {
                  &m->scan, &m->node_key, &m->corner, &m->hang, &m->owner, &m->cptr, &m->cidx,
                  &m->cw, &m->node_dof, &m->dof_node, &m->dof_mask, &m->perm, &m->pcell, &m->px,
                  &m->plp, &m->pl0, &m->pF, &m->pbe, &m->pV0, &m->pmass, &m->pE, &m->pys,
-                 &m->nsup, &m->sidx, &m->S, &m->dS, &m->S32, &m->dS32, &m->populated, &m->betaK,
+                 &m->nsup, &m->sidx, &m->S, &m->dS, &m->populated, &m->betaK,
                  &m->isB, &m->gface, &m->gdof, &m->gn, &m->row_ptr, &m->col, &m->kg, &m->rowcnt,
                  &m->src_key, &m->src_ptr, &m->fext, &m->cand, &m->cb_n, &m->cb_idx, &m->cb_phi,
                  &m->cb_y0, &m->dF, &m->dFinv, &m->tau, &m->Aalg, &m->gx, &m->slice_w, &m->slice_base, &m->scol,
                  &m->lawst, &m->ct_row, &m->ct_ptr, &m->ct_ent, &m->cc_f, &m->cc_k, &m->cc_on,
-                 &m->gJ, &m->gcoef, &m->Mf, &m->tri_fn, &m->tri_en, &m->tri_vn};
+                 &m->gJ, &m->gcoef, &m->Mf, &m->V0t, &m->tri_fn, &m->tri_en, &m->tri_vn};
   for (Buf* b : bufs) free_buf(c, *b);
 }
 }  // namespace mpm
@@ -183,6 +189,7 @@ extern "C" int mpm_destroy(mpm_ctx* c) {
   if (c->d_ticket) cudaFreeAsync(c->d_ticket, c->stream);
   cudaStreamSynchronize(c->stream);
   if (c->h_red) cudaFreeHost(c->h_red);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->h_int) cudaFreeHost(c->h_int);
   delete c;
   return MPM_OK;

@@ -104,7 +104,20 @@ struct MGLevel {
   Buf A, Dinv, b, x, r;        // operator [S*9][npad], inverses [npad][12], vectors [npad][4]
 };
 
+// a V-cycle captured as a CUDA graph, replayed while its key (the pointers
+// and sizes its launches take) is unchanged
+struct VGraph {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t key = 0;
+  long long used = 0;          // last use (for replacement)
+  int nkern = 0;
+};
+
 struct MGData {
+  static constexpr int NVG = 8;
+  VGraph vg[NVG];              // cached V-cycle graphs
+  long long vg_clock = 0;
+  bool graphs_off = false;     // a capture failed: plain launches
   long long gen = -1;          // mesh build the structure belongs to
   long long num_gen = -1;      // mesh build of the last coarse operators
   int prec = -1;               // value precision of the coarse operators
@@ -114,6 +127,7 @@ struct MGData {
   Buf t_ptr, t_idx, t_w;       // the transpose: level-1 row -> (fine dof, weight), by dof
   int t_max = 0;               // longest row of the transpose
   Buf acc;                     // 64-bit fixed-point accumulator of a Galerkin product
+  Buf kp, kpc;                 // K P of every fine row over the 4^3 level-1 nodes around its cell, the cell
   Buf bound;                   // per level: largest l1 norm of an operator row (double bits)
   Buf fDinv, fx, fr;           // fine smoother inverses, fine V-cycle vectors
   Buf fKh;                     // FP16 copy of the fine matrix (mixed path)
@@ -141,6 +155,7 @@ struct MGData {
 
 struct mpm_ctx {
   cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream on which CUDA graphs are captured
   int device = 0;
   int* d_err = nullptr;        // device error word
   double* d_red = nullptr;     // device reduction slots (64 doubles)
@@ -185,7 +200,7 @@ struct mpm_mesh {
   // points, in cell-sorted order (perm: sorted index -> caller index)
   int np = 0, maxs = 0;
   mpm::Buf perm, pcell, px, plp, pl0, pF, pbe, pV0, pmass, pE, pys;
-  mpm::Buf nsup, sidx, S, dS, S32, dS32;
+  mpm::Buf nsup, sidx, S, dS;
   mpm::Buf populated, betaK, isB;
   // ghost faces
   int nghost = 0;
@@ -215,7 +230,7 @@ struct mpm_mesh {
   mpm::Buf tri_fn, tri_en, tri_vn;
   double tri_lo[3] = {0, 0, 0}, tri_hi[3] = {0, 0, 0};
   // per-iteration point data (Mf: V0 tau dF^-T, 12 per point)
-  mpm::Buf dF, dFinv, tau, Aalg, gx, Mf;
+  mpm::Buf dF, dFinv, tau, Aalg, gx, Mf, V0t;
   mpm::Buf lawst;  // spectral state of the last residual-only evaluation (22 per point)
   int built = 0;
   long long gen = 0;                    // incremented by every build
@@ -357,6 +372,17 @@ __device__ inline void tri_vertex(const Body& B, int v, double* o) {
   o[2] = B.b.tri_v[3 * (size_t)v + 2] + B.b.z;
 }
 
+// Products and sums below are taken one rounding at a time (no fused
+// multiply-add), in the order of the plain expressions: the nearest triangle
+// and its feature are discrete decisions, taken the same way wherever this
+// code is compiled.
+__device__ inline double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ inline double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ inline double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ inline double rdot3(const double* a, const double* b) {
+  return radd(radd(rmul(a[0], b[0]), rmul(a[1], b[1])), rmul(a[2], b[2]));
+}
+
 // nearest point q of triangle (a, b, c) to x by the Voronoi regions of its
 // vertices, edges and face; feature 0 face, 1..3 edges ab, bc, ca, 4..6
 // vertices a, b, c
@@ -364,50 +390,48 @@ __device__ inline int tri_nearest(const double* x, const double* a, const double
                                   const double* c, double* q) {
   double ab[3], ac[3], ax[3], bx[3], cx[3];
   for (int d = 0; d < 3; ++d) {
-    ab[d] = b[d] - a[d];
-    ac[d] = c[d] - a[d];
-    ax[d] = x[d] - a[d];
+    ab[d] = rsub(b[d], a[d]);
+    ac[d] = rsub(c[d], a[d]);
+    ax[d] = rsub(x[d], a[d]);
   }
-  double d1 = ab[0] * ax[0] + ab[1] * ax[1] + ab[2] * ax[2];
-  double d2 = ac[0] * ax[0] + ac[1] * ax[1] + ac[2] * ax[2];
+  double d1 = rdot3(ab, ax), d2 = rdot3(ac, ax);
   if (d1 <= 0.0 && d2 <= 0.0) {
     for (int d = 0; d < 3; ++d) q[d] = a[d];
     return 4;
   }
-  for (int d = 0; d < 3; ++d) bx[d] = x[d] - b[d];
-  double d3 = ab[0] * bx[0] + ab[1] * bx[1] + ab[2] * bx[2];
-  double d4 = ac[0] * bx[0] + ac[1] * bx[1] + ac[2] * bx[2];
+  for (int d = 0; d < 3; ++d) bx[d] = rsub(x[d], b[d]);
+  double d3 = rdot3(ab, bx), d4 = rdot3(ac, bx);
   if (d3 >= 0.0 && d4 <= d3) {
     for (int d = 0; d < 3; ++d) q[d] = b[d];
     return 5;
   }
-  double vc = d1 * d4 - d3 * d2;
+  double vc = rsub(rmul(d1, d4), rmul(d3, d2));
   if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
-    double v = d1 / (d1 - d3);
-    for (int d = 0; d < 3; ++d) q[d] = a[d] + v * ab[d];
+    double v = d1 / rsub(d1, d3);
+    for (int d = 0; d < 3; ++d) q[d] = radd(a[d], rmul(v, ab[d]));
     return 1;
   }
-  for (int d = 0; d < 3; ++d) cx[d] = x[d] - c[d];
-  double d5 = ab[0] * cx[0] + ab[1] * cx[1] + ab[2] * cx[2];
-  double d6 = ac[0] * cx[0] + ac[1] * cx[1] + ac[2] * cx[2];
+  for (int d = 0; d < 3; ++d) cx[d] = rsub(x[d], c[d]);
+  double d5 = rdot3(ab, cx), d6 = rdot3(ac, cx);
   if (d6 >= 0.0 && d5 <= d6) {
     for (int d = 0; d < 3; ++d) q[d] = c[d];
     return 6;
   }
-  double vb = d5 * d2 - d1 * d6;
+  double vb = rsub(rmul(d5, d2), rmul(d1, d6));
   if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
-    double w = d2 / (d2 - d6);
-    for (int d = 0; d < 3; ++d) q[d] = a[d] + w * ac[d];
+    double w = d2 / rsub(d2, d6);
+    for (int d = 0; d < 3; ++d) q[d] = radd(a[d], rmul(w, ac[d]));
     return 3;
   }
-  double va = d3 * d6 - d5 * d4;
-  if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) {
-    double w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
-    for (int d = 0; d < 3; ++d) q[d] = b[d] + w * (c[d] - b[d]);
+  double va = rsub(rmul(d3, d6), rmul(d5, d4));
+  double e43 = rsub(d4, d3), e56 = rsub(d5, d6);
+  if (va <= 0.0 && e43 >= 0.0 && e56 >= 0.0) {
+    double w = e43 / radd(e43, e56);
+    for (int d = 0; d < 3; ++d) q[d] = radd(b[d], rmul(w, rsub(c[d], b[d])));
     return 2;
   }
-  double den = 1.0 / (va + vb + vc), v = vb * den, w = vc * den;
-  for (int d = 0; d < 3; ++d) q[d] = a[d] + v * ab[d] + w * ac[d];
+  double den = 1.0 / radd(radd(va, vb), vc), v = rmul(vb, den), w = rmul(vc, den);
+  for (int d = 0; d < 3; ++d) q[d] = radd(radd(a[d], rmul(v, ab[d])), rmul(w, ac[d]));
   return 0;
 }
 
@@ -436,8 +460,8 @@ __device__ inline double tri_sdf(const Body& B, const double* x, double* n, doub
     tri_vertex(B, T[3 * (size_t)t + 1], b);
     tri_vertex(B, T[3 * (size_t)t + 2], c);
     int f = tri_nearest(x, a, b, c, q);
-    double r0 = x[0] - q[0], r1 = x[1] - q[1], r2 = x[2] - q[2];
-    double d2 = r0 * r0 + r1 * r1 + r2 * r2;
+    double rr[3] = {rsub(x[0], q[0]), rsub(x[1], q[1]), rsub(x[2], q[2])};
+    double d2 = rdot3(rr, rr);
     if (d2 < best) {
       best = d2;
       tb = t;
@@ -452,16 +476,16 @@ __device__ inline double tri_sdf(const Body& B, const double* x, double* n, doub
     for (int i = 0; i < 9; ++i) H[i] = 0.0;
   if (tb < 0) return 1e300;
   double dist = sqrt(best);
-  double r[3] = {x[0] - qb[0], x[1] - qb[1], x[2] - qb[2]};
+  double r[3] = {rsub(x[0], qb[0]), rsub(x[1], qb[1]), rsub(x[2], qb[2])};
   const double* nt = B.fn + 3 * (size_t)tb;
   // x - q along the nearest triangle's normal: the surface is flat there
-  double cr0 = r[1] * nt[2] - r[2] * nt[1], cr1 = r[2] * nt[0] - r[0] * nt[2],
-         cr2 = r[0] * nt[1] - r[1] * nt[0];
-  if (fb != 0 && cr0 * cr0 + cr1 * cr1 + cr2 * cr2 <= 1e-24 * best) fb = 0;
+  double cr[3] = {rsub(rmul(r[1], nt[2]), rmul(r[2], nt[1])), rsub(rmul(r[2], nt[0]), rmul(r[0], nt[2])),
+                  rsub(rmul(r[0], nt[1]), rmul(r[1], nt[0]))};
+  if (fb != 0 && rdot3(cr, cr) <= 1e-24 * best) fb = 0;
   const double* N = fb == 0 ? nt
                             : (fb <= 3 ? B.en + 9 * (size_t)tb + 3 * (fb - 1)
                                        : B.vn + 3 * (size_t)T[3 * (size_t)tb + fb - 4]);
-  double sg = (r[0] * N[0] + r[1] * N[1] + r[2] * N[2]) < 0.0 ? -1.0 : 1.0;
+  double sg = rdot3(r, N) < 0.0 ? -1.0 : 1.0;
   if (!(dist > 0.0)) return 0.0;
   double phi = sg * dist;
   double u[3] = {r[0] / dist, r[1] / dist, r[2] / dist};

@@ -1,5 +1,6 @@
 // Hencky / return-map law shared by the assembly and the adjoint kernels
-// (Sec. 2.2): principal-space return in Kirchhoff stress, 3x3 symmetric
+// (Sec. 2.2; model 3, the CPT material's Willam-Warnke cone, Sec. 6.4):
+// principal-space return in Kirchhoff stress, 3x3 symmetric
 // eigen-decomposition, divided difference of the logarithm.
 #pragma once
 #include "mpm_internal.cuh"
@@ -9,7 +10,27 @@ namespace mpm {
 struct Law {
   int model;
   double nu, eta, xi, etab;
+  double ecc;  // model 3: tensile / compressive meridian radius, (3 - sin phi)/(3 + sin phi)
 };
+
+// Willam-Warnke deviatoric section (Sec. 6.4): r(theta) by the elliptic
+// interpolation r = (4 a c^2 + b^2)/(2 a c + b sqrt(4 a c^2 + 5 e^2 - 4 e)),
+// c = cos(theta), a = 1 - e^2, b = 2 e - 1 (theta the Lode angle, 0 on the
+// tensile meridian where r = 1/e, pi/3 on the compressive one where r = 1),
+// and dr/dzeta for zeta = cos(3 theta); at the compressive meridian the limit
+// 4 a / (6 b^2 (2 c + 1)) of dr/dc over dzeta/dc is taken
+__device__ inline double ww_section(double zeta, double e, double* drdz) {
+  zeta = fmin(fmax(zeta, -1.0), 1.0);
+  double c = cos(acos(zeta) / 3.0);
+  double a = 1.0 - e * e, b = 2.0 * e - 1.0;
+  double w = sqrt(4.0 * a * c * c + 5.0 * e * e - 4.0 * e);
+  double N = 4.0 * a * c * c + b * b, D = 2.0 * a * c + b * w;
+  double dN = 8.0 * a * c, dD = 2.0 * a + 4.0 * a * b * c / w;
+  double rc = (dN * D - N * dD) / (D * D);
+  double q = 4.0 * c * c - 1.0;
+  *drdz = fabs(q) > 1e-5 ? rc / (3.0 * q) : 4.0 * a / (6.0 * b * b * (2.0 * c + 1.0));
+  return N / D;
+}
 
 // symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations; columns of Q
 // are the eigenvectors (Q[3*i + a] = component i of vector a)
@@ -91,13 +112,30 @@ __device__ inline void principal_return(const Law& L, double E, double ys, const
       for (int b = 0; b < 3; ++b) dd[3 * a + b] = kb + g * ((a == b ? 1.0 : 0.0) - 1.0 / 3.0 - nn[a] * nn[b]);
     }
     *gr = g;
-  } else if (L.model == 2) {
-    // Drucker-Prager: f = sqrt(J2) + eta p - xi c, potential with etab
+  } else if (L.model == 2 || L.model == 3) {
+    // Drucker-Prager cone: f = sqrt(J2) r + eta p - xi c with r = 1 (model 2)
+    // or the Willam-Warnke section r(theta) (model 3); potential sqrt(J2) +
+    // etab p, circular, so the return is radial in the deviatoric plane and
+    // keeps theta: f(dg) = (sqrt(J2) - G dg) r + eta (p - K etab dg) - xi c
     double G = mu, pm = kb * tr;
     double sj = 1.4142135623730951 * G * dn;
-    double f = sj + L.eta * pm - L.xi * ys;
+    double r = 1.0, drz = 0.0, dz[3] = {0.0, 0.0, 0.0};
+    if (L.model == 3 && dn > 0.0) {
+      // zeta = cos(3 theta) = 3 sqrt6 e1 e2 e3 / |e|^3 of the trial deviator
+      double pr = dev[0] * dev[1] * dev[2], dn3 = dn * dn * dn;
+      double zeta = 7.348469228349534 * pr / dn3;
+      r = ww_section(zeta, L.ecc, &drz);
+      if (zeta > -1.0 && zeta < 1.0) {
+        double mm[3] = {dev[1] * dev[2], dev[0] * dev[2], dev[0] * dev[1]};
+        double M3 = (mm[0] + mm[1] + mm[2]) / 3.0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          dz[b] = 7.348469228349534 * ((mm[b] - M3) / dn3 - 3.0 * pr * dev[b] / (dn3 * dn * dn));
+      }
+    }
+    double f = sj * r + L.eta * pm - L.xi * ys;
     if (f <= 0.0) return;
-    double den = G + kb * L.eta * L.etab;
+    double den = G * r + kb * L.eta * L.etab;
     double dg = f / den;
     if (sj - G * dg >= 0.0 && dn > 0.0) {
       double ratio = 1.0 - G * dg / sj;
@@ -105,7 +143,8 @@ __device__ inline void principal_return(const Law& L, double E, double ys, const
       double nn[3] = {dev[0] / dn, dev[1] / dn, dev[2] / dn};
       double ddg[3];
 #pragma unroll
-      for (int b = 0; b < 3; ++b) ddg[b] = (1.4142135623730951 * G * nn[b] + L.eta * kb) / den;
+      for (int b = 0; b < 3; ++b)
+        ddg[b] = (1.4142135623730951 * G * nn[b] * r + (sj - G * dg) * drz * dz[b] + L.eta * kb) / den;
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         ta[a] = pn + 2.0 * G * ratio * dev[a];
@@ -139,6 +178,7 @@ inline Law make_law(const mpm_material& mat) {
   L.eta = 6.0 * sp / (sqrt(3.0) * (3.0 - sp));
   L.xi = 6.0 * cos(mat.phi) / (sqrt(3.0) * (3.0 - sp));
   L.etab = 6.0 * ss / (sqrt(3.0) * (3.0 - ss));
+  L.ecc = (3.0 - sp) / (3.0 + sp);
   return L;
 }
 

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <type_traits>
 
 #include "mpm_internal.cuh"
 #include "mpm_sliced.cuh"
@@ -192,23 +193,32 @@ __global__ void k_mg_reach(int nd, int D, int d1, const int* __restrict__ rp,
 // with sum |term| <= B: 2^(60 - floor(log2 B)), so that every partial sum
 // stays below 2^61 in magnitude and the 64-bit integer accumulation cannot
 // overflow; one unit is at most 2^-60 B (below FP64 rounding of the sum).
+// 64-bit accumulators (FP64 operators): partial sums below 2^61; 32-bit
+// (FP32 operators, 24-bit significands): below 2^30, one unit at most
+// 2^-29 B, below FP32 rounding of the larger entries
+template <class ACC>
 __device__ inline double fixed_scale(double B) {
   if (!(B > 0.0) || !isfinite(B)) return 1.0;
-  return ldexp(1.0, 60 - ilogb(B));
+  return ldexp(1.0, (sizeof(ACC) == 8 ? 60 : 29) - ilogb(B));
 }
 
 __device__ inline void fixed_add(unsigned long long* a, double v, double sc) {
-  atomicAdd(a, (unsigned long long)__double2ll_rn(v * sc));
+  if (v != 0.0) atomicAdd(a, (unsigned long long)__double2ll_rn(v * sc));
 }
+__device__ inline void fixed_add(unsigned int* a, double v, double sc) {
+  if (v != 0.0) atomicAdd(a, (unsigned int)__double2int_rn(v * sc));
+}
+__device__ inline double fixed_value(unsigned long long v) { return (double)(long long)v; }
+__device__ inline double fixed_value(unsigned int v) { return (double)(int)v; }
 
 // fixed point -> operator values
-template <class T>
-__global__ void k_mg_from_fixed(long long n, const unsigned long long* __restrict__ acc,
+template <class T, class ACC>
+__global__ void k_mg_from_fixed(long long n, const ACC* __restrict__ acc,
                                 const unsigned long long* __restrict__ bnd, double cnt, T* A) {
-  double inv = 1.0 / fixed_scale(__longlong_as_double((long long)*bnd) * cnt);
+  double inv = 1.0 / fixed_scale<ACC>(__longlong_as_double((long long)*bnd) * cnt);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    A[i] = (T)((double)(long long)acc[i] * inv);
+    A[i] = (T)(fixed_value(acc[i]) * inv);
 }
 
 __device__ inline int stencil_index(const int* cb, const int* ca, int R) {
@@ -234,22 +244,23 @@ __global__ void k_mg_fix_masked(int nrow, int S, int R, const int* __restrict__ 
 
 // level 1: one warp per fine dof i; its block row, weighted by P_ia for every
 // coarse row a it interpolates from, spread to the coarse columns of each
-// column dof j.  The terms go to the zeroed fixed-point operator by 64-bit
-// integer atomics (resolved in L2); a warp per fine row keeps the work
+// column dof j.  The terms go to the zeroed fixed-point operator by integer
+// atomics (resolved in L2; 32-bit for an FP32 operator, 64-bit for FP64); a
+// warp per fine row keeps the work
 // balanced when the coarse grid is much coarser than the finest leaves.  The
 // bound: every entry sums terms P_ia |K_ij| P_jb with sum over j, b at most
 // the l1 norm of row i (bnd, from the fine smoother kernel) and at most cnt
 // fine rows i per coarse row a.
-template <class T>
+template <class T, class ACC>
 __global__ void k_mg_rap1(int nd, int R, int S, const float* __restrict__ pw,
                           const int* __restrict__ pidx, const int* __restrict__ fmask,
                           const int* __restrict__ rp, const int* __restrict__ col, Sliced SK,
                           const T* __restrict__ K, const int* __restrict__ xyz,
-                          unsigned long long* A, const unsigned long long* __restrict__ bnd,
+                          ACC* A, const unsigned long long* __restrict__ bnd,
                           double cnt, int* err) {
   int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (i >= nd) return;
-  double sc = fixed_scale(__longlong_as_double((long long)*bnd) * cnt);
+  double sc = fixed_scale<ACC>(__longlong_as_double((long long)*bnd) * cnt);
   int mi = fmask[i];
   int s0 = rp[i], nb = rp[i + 1] - s0;
   int sl = i >> 5, W = SK.w[sl];
@@ -270,7 +281,7 @@ __global__ void k_mg_rap1(int nd, int R, int S, const float* __restrict__ pw,
       double wa = (double)pw[8 * (size_t)i + qa];
       int ca[3];
       unpack3(xyz[a], ca);
-      unsigned long long* row = A + (size_t)a * S * 9;
+      ACC* row = A + (size_t)a * S * 9;
       for (int q = 0; q < 8; ++q) {
         int b = pidx[8 * (size_t)j + q];
         if (b < 0) break;
@@ -289,19 +300,164 @@ __global__ void k_mg_rap1(int nd, int R, int S, const float* __restrict__ pw,
   }
 }
 
+// Level 1 in two gathers, in plain arithmetic and free of atomics, for the
+// usual stencil radius R = 2 (the fine blocks reach one level-1 cell):
+// (1) k_mg_kp, one warp per fine row i: (K P)_iJ = sum_j K_ij P_jJ for the
+//     4 x 4 x 4 level-1 nodes J = c_i + (-1..2) around the level-1 cell c_i
+//     of dof i (every P_jJ of a column j of the row lands there), the
+//     columns j taken in row order, accumulated in shared memory and written
+//     out as kp[i][9][64];
+// (2) k_mg_ptkp, one warp per level-1 row a: A_ab = sum_i P_ia (K P)_ib over
+//     the fine dofs i of the transpose of P, in dof order, lanes over the
+//     125 stencil offsets b - a.
+// Every sum runs in a fixed order, so the operator is the same bit for bit
+// on every run, like the fixed-point product it replaces where it applies.
+constexpr int KP_NS = 64;  // (2R)^3 level-1 nodes around a fine dof's cell, R = 2
+// warps per block of k_mg_kp: its shared memory (44 KB FP32, 36 KB FP64)
+// stays under the 48 KB of a static allocation
+template <class T>
+__host__ __device__ constexpr int kp_warps() {
+  return sizeof(T) == 4 ? 8 : 4;
+}
+
+template <class T>
+struct KpShared {
+  static constexpr int NW = kp_warps<T>();
+  T tab[NW][KP_NS * 9];     // (K P)_i, [slot][9]
+  T sv[NW][32][9];          // a chunk of 32 blocks K_ij (masked)
+  int ss[NW][32][8];        // their P_j entries: slot (-1: none) ...
+  float sw[NW][32][8];      // ... and weight
+};
+
+template <class T>
+__global__ void __launch_bounds__(32 * kp_warps<T>())
+    k_mg_kp(int nd, int D, int d1, const int* __restrict__ dof_node, const uint64_t* __restrict__ nkey,
+            const float* __restrict__ pw, const int* __restrict__ pidx, const int* __restrict__ fmask,
+            const int* __restrict__ rp, const int* __restrict__ col, Sliced SK, const T* __restrict__ K,
+            const int* __restrict__ xyz, T* kp, int* kpc, int* err) {
+  __shared__ KpShared<T> sh;
+  int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int i = blockIdx.x * kp_warps<T>() + wi;
+  if (i >= nd) return;
+  T* tab = sh.tab[wi];
+  for (int f = lane; f < KP_NS * 9; f += 32) tab[f] = (T)0;
+  int X[3], ci[3];
+  demorton(nkey[dof_node[i]], X);
+  int shf = D - d1, n = 1 << d1;
+  for (int d = 0; d < 3; ++d) ci[d] = min(X[d] >> shf, n - 1);
+  if (lane == 0) kpc[i] = pack3(ci[0], ci[1], ci[2]);
+  int mi = fmask[i];
+  int s0 = rp[i], nb = rp[i + 1] - s0;
+  int sl = i >> 5, W = SK.w[sl];
+  long long b0 = SK.base[sl];
+  bool bad = false;
+  for (int base = 0; base < nb; base += 32) {
+    int idx = base + lane, cnt = min(32, nb - base);
+    __syncwarp();
+    if (idx < nb) {
+      int j = col[s0 + idx];
+      int mj = fmask[j];
+      long long slot = sliced_slot(b0, i, idx);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        int ca = e / 3, ck = e - 3 * (e / 3);
+        sh.sv[wi][lane][e] = (((mi >> ca) & 1) || ((mj >> ck) & 1)) ? (T)0 : K[sliced_entry(b0, W, slot, e)];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int b = pidx[8 * (size_t)j + q];
+        int s = -1;
+        if (b >= 0) {
+          int cb[3];
+          unpack3(xyz[b], cb);
+          int o0 = cb[0] - ci[0] + 1, o1 = cb[1] - ci[1] + 1, o2 = cb[2] - ci[2] + 1;
+          if ((unsigned)o0 < 4u && (unsigned)o1 < 4u && (unsigned)o2 < 4u)
+            s = o0 + 4 * (o1 + 4 * o2);
+          else
+            bad = true;
+          sh.sw[wi][lane][q] = pw[8 * (size_t)j + q];
+        }
+        sh.ss[wi][lane][q] = s;
+      }
+    }
+    __syncwarp();
+    // column by column (a fixed order per accumulator): the 8 x 9 (entry,
+    // component) terms of a column go to distinct accumulators
+    for (int u = 0; u < cnt; ++u) {
+      for (int t = lane; t < 72; t += 32) {
+        int q = t / 9, e = t - 9 * (t / 9);
+        int s = sh.ss[wi][u][q];
+        if (s >= 0) tab[9 * s + e] += (T)sh.sw[wi][u][q] * sh.sv[wi][u][e];
+      }
+      __syncwarp();
+    }
+  }
+  if (bad) atomicOr(err, EB_ROW);
+  __syncwarp();
+  T* out = kp + (size_t)i * 9 * KP_NS;
+  for (int f = lane; f < KP_NS * 9; f += 32) {
+    int e = f / KP_NS, s = f - KP_NS * (f / KP_NS);
+    out[f] = tab[9 * s + e];
+  }
+}
+
+template <class T>
+__global__ void k_mg_ptkp(int nrow, const int* __restrict__ xyz, const int* __restrict__ tptr,
+                          const int* __restrict__ tidx, const float* __restrict__ tw,
+                          const int* __restrict__ kpc, const T* __restrict__ kp, T* A) {
+  constexpr int R = 2, S1 = 2 * R + 1, S = S1 * S1 * S1, NPL = (S + 31) / 32;
+  int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (a >= nrow) return;
+  int ca[3];
+  unpack3(xyz[a], ca);
+  T acc[NPL][9];
+#pragma unroll
+  for (int k = 0; k < NPL; ++k)
+#pragma unroll
+    for (int e = 0; e < 9; ++e) acc[k][e] = (T)0;
+  for (int t = tptr[a]; t < tptr[a + 1]; ++t) {
+    int i = tidx[t];
+    T w = (T)tw[t];
+    int ci[3];
+    unpack3(kpc[i], ci);
+    const T* kv = kp + (size_t)i * 9 * KP_NS;
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+      int o = lane + 32 * k;
+      if (o >= S) continue;
+      // b = a + delta(o); its slot around the cell of i
+      int s0 = ca[0] + o % S1 - R - ci[0] + 1;
+      int s1 = ca[1] + (o / S1) % S1 - R - ci[1] + 1;
+      int s2 = ca[2] + o / (S1 * S1) - R - ci[2] + 1;
+      if ((unsigned)s0 >= 4u || (unsigned)s1 >= 4u || (unsigned)s2 >= 4u) continue;
+      int s = s0 + 4 * (s1 + 4 * s2);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) acc[k][e] += w * kv[e * KP_NS + s];
+    }
+  }
+  T* row = A + (size_t)a * S * 9;
+#pragma unroll
+  for (int k = 0; k < NPL; ++k) {
+    int o = lane + 32 * k;
+    if (o >= S) continue;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) row[9 * o + e] = acc[k][e];
+  }
+}
+
 // uniform level -> next coarser: one warp per row i of the finer level; its
 // operator row, weighted by the trilinear weights prod(1 - |delta|/2) of the
 // coarse rows a around it, spread to the coarse columns of each column j, by
 // fixed-point integer atomics as above (at most 27 finer rows per coarse row)
-template <class T>
+template <class T, class ACC>
 __global__ void k_mg_rapu(int nrow_f, int Rc, int Sc, int n1c, const int* __restrict__ gid_c,
                           int Rf, int Sf, int n1f, const int* __restrict__ gid_f,
                           const int* __restrict__ xyz_f, const int* __restrict__ fmask,
-                          const T* __restrict__ Af, unsigned long long* A,
+                          const T* __restrict__ Af, ACC* A,
                           const unsigned long long* __restrict__ bnd, int* err) {
   int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (i >= nrow_f) return;
-  double sc = fixed_scale(__longlong_as_double((long long)*bnd) * 27.0);
+  double sc = fixed_scale<ACC>(__longlong_as_double((long long)*bnd) * 27.0);
   int fi[3];
   unpack3(xyz_f[i], fi);
   int mi = fmask[i];
@@ -341,7 +497,7 @@ __global__ void k_mg_rapu(int nrow_f, int Rc, int Sc, int n1c, const int* __rest
           if (alo[0] != ahi[0]) wa *= 0.5;
           if (alo[1] != ahi[1]) wa *= 0.5;
           if (alo[2] != ahi[2]) wa *= 0.5;
-          unsigned long long* row = A + (size_t)a * Sc * 9;
+          ACC* row = A + (size_t)a * Sc * 9;
           int ca[3] = {ax, ay, az};
           for (int z = blo[2]; z <= bhi[2]; ++z)
             for (int y = blo[1]; y <= bhi[1]; ++y)
@@ -972,22 +1128,39 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
     MGLevel& L = G.lev[l];
     size_t nA = (size_t)L.nrow * L.S * 9;
     T* A = grow<T>(c, L.A, nA);
-    unsigned long long* acc = grow<unsigned long long>(c, G.acc, nA);
-    MPM_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * nA, st));
+    // 64-bit integer accumulator (a 32-bit one, tried for the FP32 operator,
+    // was no faster and, scaled by the row bound, too coarse for the cone's
+    // level 1: twice the BiCGStab iterations)
+    typedef unsigned long long ACC;
+    if (l == 0 && L.R == 2) {
+      // the two gathers (no accumulator, no atomics)
+      T* kp = grow<T>(c, G.kp, (size_t)nd * 9 * KP_NS);
+      int* kpc = grow<int>(c, G.kpc, nd);
+      constexpr int NW = kp_warps<T>();
+      MPM_LAUNCH_P(MPM_PROF_MG_RAP, k_mg_kp<T><<<(nd + NW - 1) / NW, 32 * NW, 0, st>>>(
+          nd, m->g.D, L.d, ptr<int>(m->dof_node), ptr<uint64_t>(m->node_key), ptr<float>(G.p_w),
+          ptr<int>(G.p_idx), ptr<int>(m->dof_mask), ptr<int>(m->row_ptr), ptr<int>(m->col), SK, K,
+          ptr<int>(L.xyz), kp, kpc, c->d_err));
+      MPM_LAUNCH_P(MPM_PROF_MG_RAP, k_mg_ptkp<T><<<grid_for(L.nrow, 8), 256, 0, st>>>(
+          L.nrow, ptr<int>(L.xyz), ptr<int>(G.t_ptr), ptr<int>(G.t_idx), ptr<float>(G.t_w), kpc, kp, A));
+    } else {
+    ACC* acc = grow<ACC>(c, G.acc, nA);
+    MPM_CUDA(cudaMemsetAsync(acc, 0, sizeof(ACC) * nA, st));
     double cnt;
     if (l == 0) {
       cnt = (double)std::max(G.t_max, 1);
-      MPM_LAUNCH_P(MPM_PROF_MG_RAP, k_mg_rap1<T><<<grid_for(nd, 8), 256, 0, st>>>(
+      MPM_LAUNCH_P(MPM_PROF_MG_RAP, (k_mg_rap1<T, ACC><<<grid_for(nd, 8), 256, 0, st>>>(
           nd, L.R, L.S, ptr<float>(G.p_w), ptr<int>(G.p_idx), ptr<int>(m->dof_mask), ptr<int>(m->row_ptr),
-          ptr<int>(m->col), SK, K, ptr<int>(L.xyz), acc, bnd, cnt, c->d_err));
+          ptr<int>(m->col), SK, K, ptr<int>(L.xyz), acc, bnd, cnt, c->d_err)));
     } else {
       MGLevel& F = G.lev[l - 1];
       cnt = 27.0;
-      MPM_LAUNCH_P(MPM_PROF_MG_RAP, k_mg_rapu<T><<<grid_for(F.nrow, 8), 256, 0, st>>>(
+      MPM_LAUNCH_P(MPM_PROF_MG_RAP, (k_mg_rapu<T, ACC><<<grid_for(F.nrow, 8), 256, 0, st>>>(
           F.nrow, L.R, L.S, L.n1, ptr<int>(L.gid), F.R, F.S, F.n1, ptr<int>(F.gid), ptr<int>(F.xyz),
-          ptr<int>(F.mask), ptr<T>(F.A), acc, bnd + l, c->d_err));
+          ptr<int>(F.mask), ptr<T>(F.A), acc, bnd + l, c->d_err)));
     }
-    MPM_LAUNCH_P(MPM_PROF_MG_RAP, k_mg_from_fixed<T><<<4 * 152, 256, 0, st>>>((long long)nA, acc, bnd + l, cnt, A));
+    MPM_LAUNCH_P(MPM_PROF_MG_RAP, (k_mg_from_fixed<T, ACC><<<4 * 152, 256, 0, st>>>((long long)nA, acc, bnd + l, cnt, A)));
+    }
     MPM_LAUNCH_P(MPM_PROF_MG_SETUP, k_mg_fix_masked<T><<<grid_for(L.nrow, 128), 128, 0, st>>>(L.nrow, L.S, L.R, ptr<int>(L.mask), A));
     MPM_LAUNCH_P(MPM_PROF_MG_SETUP, k_mg_dinv<T><<<grid_for(L.npad, 128), 128, 0, st>>>(L.nrow, L.npad, L.S, L.R, A,
                                                                    grow<T>(c, L.Dinv, 12 * (size_t)L.npad), c->d_err, kSmoothW,
@@ -1019,9 +1192,12 @@ void mg_setup(mpm_ctx* c, mpm_mesh* m, const T* K, bool reuse) {
   mg_numeric<T>(c, m, K, !keep);
 }
 
+namespace {
+
+// the launches of one V-cycle on the context stream
 template <class T>
-void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, const Scal* sk, int k,
-              double* rz) {
+void vcycle_launch(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, const Scal* sk, int k,
+                   double* rz) {
   mpm_mesh* m = const_cast<mpm_mesh*>(mc);
   cudaStream_t st = c->stream;
   MGData& G = *m->mg;
@@ -1083,14 +1259,120 @@ void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, cons
         nd, npad, SK, K, ksc, r, fx, fD, z, nullptr, rz, sk, k, gr));
 }
 
+// everything the launches of a V-cycle take that can change between calls:
+// the graph of a V-cycle is replayed only while these stay the same
+template <class T>
+uint64_t vcycle_key(mpm_ctx* c, const mpm_mesh* m, const T* K, const T* r, const T* z, const Scal* sk,
+                    int kk, double* rz) {
+  const MGData& G = *m->mg;
+  uint64_t h = 1469598103934665603ULL;
+  auto mix = [&](uint64_t v) {
+    h ^= v;
+    h *= 1099511628211ULL;
+  };
+  mix((uint64_t)m->gen);
+  mix((uint64_t)(int64_t)kk);
+  mix(sizeof(T));
+  mix((uint64_t)(uintptr_t)K);
+  mix((uint64_t)(uintptr_t)r);
+  mix((uint64_t)(uintptr_t)z);
+  mix((uint64_t)(uintptr_t)sk);
+  mix((uint64_t)(uintptr_t)rz);
+  mix((uint64_t)(uintptr_t)c->part.p);
+  mix((uint64_t)(uintptr_t)c->d_ticket);
+  mix((uint64_t)(uintptr_t)c->d_red);
+  const Buf* bs[] = {&G.fx, &G.fDinv, &G.fr, &G.fKh, &G.t_ptr, &G.t_idx, &G.t_w, &G.p_idx, &G.p_w, &G.cinv};
+  for (const Buf* b : bs) mix((uint64_t)(uintptr_t)b->p);
+  mix((uint64_t)G.nlev);
+  for (int l = 0; l < G.nlev; ++l) {
+    const MGLevel& L = G.lev[l];
+    const Buf* lb[] = {&L.A, &L.Dinv, &L.b, &L.x, &L.r, &L.gid, &L.xyz, &L.mask};
+    for (const Buf* b : lb) mix((uint64_t)(uintptr_t)b->p);
+    mix(((uint64_t)L.nrow << 32) | (uint64_t)(unsigned)L.S);
+  }
+  return h;
+}
+
+}  // namespace
+
+// z = B r, one V-cycle.  Without per-launch timing, the V-cycle's launches
+// are captured once into a CUDA graph on a private stream and replayed on the
+// context stream: its many small coarse-level kernels then cost one launch.
+// The graphs are cached by their key (every pointer and size the launches
+// take, and k % 3, which is all the kernels read of k); the least recently
+// used one is replaced.  A capture that fails falls back to plain launches.
+template <class T>
+void mg_apply(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z, const Scal* sk, int k,
+              double* rz) {
+  mpm_mesh* m = const_cast<mpm_mesh*>(mc);
+  MGData& G = *m->mg;
+  if (c->prof_on || !c->cap_stream || G.graphs_off) {
+    vcycle_launch<T>(c, m, K, r, z, sk, k, rz);
+    return;
+  }
+  int kk = k < 0 ? -1 : k % 3;
+  uint64_t key = vcycle_key<T>(c, m, K, r, z, sk, kk, rz);
+  ++G.vg_clock;
+  int slot = -1, lru = 0;
+  for (int i = 0; i < MGData::NVG; ++i) {
+    if (G.vg[i].exec && G.vg[i].key == key) slot = i;
+    if (G.vg[i].used < G.vg[lru].used) lru = i;
+  }
+  bool fresh = slot < 0;
+  if (fresh) slot = lru;
+  VGraph& g = G.vg[slot];
+  g.used = G.vg_clock;
+  if (fresh) {
+    cudaStream_t keep = c->stream;
+    long long nl0 = c->nlaunch;
+    cudaGraph_t graph = nullptr;
+    c->stream = c->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      try {
+        vcycle_launch<T>(c, m, K, r, z, sk, kk, rz);
+      } catch (...) {
+        cudaStreamEndCapture(c->stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        c->stream = keep;
+        c->nlaunch = nl0;
+        throw;
+      }
+      e = cudaStreamEndCapture(c->stream, &graph);
+    }
+    c->stream = keep;
+    int nk = (int)(c->nlaunch - nl0);
+    c->nlaunch = nl0;
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || !g.exec) {
+      cudaGetLastError();  // clear a capture or instantiation error
+      g.exec = nullptr;
+      G.graphs_off = true;
+      vcycle_launch<T>(c, m, K, r, z, sk, k, rz);
+      return;
+    }
+    g.key = key;
+    g.nkern = nk;
+  }
+  MPM_CUDA(cudaGraphLaunch(g.exec, c->stream));
+  c->nlaunch += g.nkern;
+}
+
 void mg_release(mpm_ctx* c, mpm_mesh* m) {
   if (!m->mg) return;
   MGData& G = *m->mg;
+  for (VGraph& g : G.vg)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (auto& L : G.lev) {
     Buf* b[] = {&L.gid, &L.xyz, &L.mask, &L.A, &L.Dinv, &L.b, &L.x, &L.r};
     for (Buf* x : b) free_buf(c, *x);
   }
-  Buf* b[] = {&G.p_idx, &G.p_w, &G.t_ptr, &G.t_idx, &G.t_w, &G.acc, &G.bound, &G.fDinv, &G.fx,
+  Buf* b[] = {&G.p_idx, &G.p_w, &G.t_ptr, &G.t_idx, &G.t_w, &G.acc, &G.kp, &G.kpc, &G.bound, &G.fDinv, &G.fx,
               &G.fr, &G.fKh, &G.cinv};
   for (Buf* x : b) free_buf(c, *x);
   delete m->mg;

@@ -230,44 +230,67 @@ __global__ void k_pcg_b(int nd, int npad, int k, Sliced S, const T* __restrict__
 }
 
 // ---------------------------------------------------------------- BiCGStab
-// FP64 vectors padded to 4 components over 32*nslice rows; x keeps the
-// caller's 3-component layout.
+// Vectors padded to 4 components over 32*nslice rows, in FP64 or (the FP32
+// inner solve of the mixed path) FP32; x keeps the caller's 3-component
+// layout; scalars and dot products in FP64.
 
 // y = K x (+ optional dots a.y into slot and y.y into slot2).  Skipped once
 // the solve is done, or (check_s) once the half-step residual s has converged.
-template <class T>
+template <class T, class V>
 __global__ void k_spmv_dot(int nd, int npad, Sliced S, const T* __restrict__ K,
-                           const double* __restrict__ x, double* y, const double* __restrict__ a,
+                           const V* __restrict__ x, V* y, const V* __restrict__ a,
                            double* slot, double* slot2, const Scal* sc, int check_s, GridRed gr) {
   if (sc->done || (check_s && sc->a[5] <= sc->thr)) return;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   double p1 = 0.0, p2 = 0.0;
   if (r < npad) {
-    double v[3];
-    sliced_row<T, double, double, 4>(r, S, K, x, v);
-    if (r >= nd) v[0] = v[1] = v[2] = 0.0;
-    double yv[4] = {v[0], v[1], v[2], 0.0};
+    V v[3];
+    sliced_row<T, V, V, 4>(r, S, K, x, v);
+    if (r >= nd) v[0] = v[1] = v[2] = (V)0;
+    V yv[4] = {v[0], v[1], v[2], (V)0};
     st4(y + 4 * (size_t)r, yv);
     if (a) {
-      double av[4];
+      V av[4];
       ld4(a + 4 * (size_t)r, av);
-      p1 = av[0] * v[0] + av[1] * v[1] + av[2] * v[2];
+      p1 = (double)av[0] * v[0] + (double)av[1] * v[1] + (double)av[2] * v[2];
     }
-    p2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    p2 = (double)v[0] * v[0] + (double)v[1] * v[1] + (double)v[2] * v[2];
   }
   grid_sum2(p1, p2, slot, slot2, gr);
+}
+
+// start: r = r0 = b (free components), x = 0, ||b||^2
+template <class V, class X>
+__global__ void k_bicg_init(int nd, int npad, const double* __restrict__ b, const int* __restrict__ mask,
+                            X* x, V* r, V* r0, Scal* sc, GridRed gr) {
+  double bb = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
+    V rv[4] = {(V)0, (V)0, (V)0, (V)0};
+    if (i < nd) {
+      int mk = mask[i];
+      for (int c = 0; c < 3; ++c) {
+        rv[c] = ((mk >> c) & 1) ? (V)0 : (V)b[3 * (size_t)i + c];
+        x[3 * (size_t)i + c] = (X)0;
+        bb += (double)rv[c] * (double)rv[c];
+      }
+    }
+    st4(r + 4 * (size_t)i, rv);
+    st4(r0 + 4 * (size_t)i, rv);
+  }
+  grid_sum1(bb, &sc->bb, gr);
 }
 
 // BiCGStab scalar slots in Scal::a: 0 rho, 1 alpha, 2 omega, 3 rho1 (r0.r),
 // 4 r0.v, 5 s.s, 6 t.s, 7 t.t; rr[0] = r.r.  Only k_bicg_rotate (one thread)
 // writes `done`, so no block ever sees it change within a launch.
-__global__ void k_bicg_p(int npad, double* p, const double* __restrict__ r, const double* __restrict__ v,
-                         double* ph, const double* __restrict__ Dinv, const Scal* sc) {
+template <class V>
+__global__ void k_bicg_p(int npad, V* p, const V* __restrict__ r, const V* __restrict__ v,
+                         V* ph, const V* __restrict__ Dinv, const Scal* sc) {
   if (sc->done) return;
-  double beta = (sc->a[3] / sc->a[0]) * (sc->a[1] / sc->a[2]);
-  double om = sc->a[2];
+  V beta = (V)((sc->a[3] / sc->a[0]) * (sc->a[1] / sc->a[2]));
+  V om = (V)sc->a[2];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
-    double pv[4], rv[4], vv[4], zv[4];
+    V pv[4], rv[4], vv[4], zv[4];
     ld4(p + 4 * (size_t)i, pv);
     ld4(r + 4 * (size_t)i, rv);
     ld4(v + 4 * (size_t)i, vv);
@@ -280,20 +303,21 @@ __global__ void k_bicg_p(int npad, double* p, const double* __restrict__ r, cons
   }
 }
 
-__global__ void k_bicg_s(int npad, const double* __restrict__ r, const double* __restrict__ v, double* s,
-                         double* sh_, const double* __restrict__ Dinv, Scal* sc, GridRed gr) {
+template <class V>
+__global__ void k_bicg_s(int npad, const V* __restrict__ r, const V* __restrict__ v, V* s,
+                         V* sh_, const V* __restrict__ Dinv, Scal* sc, GridRed gr) {
   if (sc->done) return;
   double rv0 = sc->a[4];
   if (!(fabs(rv0) > 0.0) || !isfinite(rv0)) return;  // breakdown, recorded by k_bicg_rotate
-  double alpha = sc->a[3] / rv0;
+  V alpha = (V)(sc->a[3] / rv0);
   double ss = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
-    double rv[4], vv[4], sv[4], zv[4];
+    V rv[4], vv[4], sv[4], zv[4];
     ld4(r + 4 * (size_t)i, rv);
     ld4(v + 4 * (size_t)i, vv);
     for (int c = 0; c < 4; ++c) {
       sv[c] = rv[c] - alpha * vv[c];
-      ss += sv[c] * sv[c];
+      ss += (double)sv[c] * (double)sv[c];
     }
     st4(s + 4 * (size_t)i, sv);
     if (Dinv) {
@@ -305,18 +329,20 @@ __global__ void k_bicg_s(int npad, const double* __restrict__ r, const double* _
 }
 
 // converged on s: x += alpha ph (the rest of the iteration is skipped)
-__global__ void k_bicg_check_s(int nd, double* x, const double* __restrict__ ph, const Scal* sc) {
+template <class V, class X>
+__global__ void k_bicg_check_s(int nd, X* x, const V* __restrict__ ph, const Scal* sc) {
   if (sc->done || !(sc->a[5] <= sc->thr)) return;
   double rv = sc->a[4];
   if (!(fabs(rv) > 0.0) || !isfinite(rv)) return;
   double alpha = sc->a[3] / rv;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * nd; i += gridDim.x * blockDim.x)
-    x[i] += alpha * ph[4 * (size_t)(i / 3) + i % 3];
+    x[i] += (X)(alpha * (double)ph[4 * (size_t)(i / 3) + i % 3]);
 }
 
-__global__ void k_bicg_x(int nd, int npad, double* x, double* r, const double* __restrict__ ph,
-                         const double* __restrict__ shv, const double* __restrict__ s,
-                         const double* __restrict__ t, const double* __restrict__ r0, const Scal* sc,
+template <class V, class X>
+__global__ void k_bicg_x(int nd, int npad, X* x, V* r, const V* __restrict__ ph,
+                         const V* __restrict__ shv, const V* __restrict__ s,
+                         const V* __restrict__ t, const V* __restrict__ r0, const Scal* sc,
                          double* next_rho1, double* next_rr, GridRed gr) {
   if (sc->done || sc->a[5] <= sc->thr) return;
   double rv0 = sc->a[4];
@@ -326,20 +352,20 @@ __global__ void k_bicg_x(int nd, int npad, double* x, double* r, const double* _
   double alpha = sc->a[3] / rv0;
   double rr = 0.0, rho1 = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += gridDim.x * blockDim.x) {
-    double pv[4], zv[4], sv[4], tv[4], r0v[4], rv[4];
+    V pv[4], zv[4], sv[4], tv[4], r0v[4], rv[4];
     ld4(ph + 4 * (size_t)i, pv);
     ld4(shv + 4 * (size_t)i, zv);
     ld4(s + 4 * (size_t)i, sv);
     ld4(t + 4 * (size_t)i, tv);
     ld4(r0 + 4 * (size_t)i, r0v);
     for (int c = 0; c < 4; ++c) {
-      rv[c] = sv[c] - om * tv[c];
-      rr += rv[c] * rv[c];
-      rho1 += r0v[c] * rv[c];
+      rv[c] = sv[c] - (V)om * tv[c];
+      rr += (double)rv[c] * (double)rv[c];
+      rho1 += (double)r0v[c] * (double)rv[c];
     }
     st4(r + 4 * (size_t)i, rv);
     if (i < nd)
-      for (int c = 0; c < 3; ++c) x[3 * (size_t)i + c] += alpha * pv[c] + om * zv[c];
+      for (int c = 0; c < 3; ++c) x[3 * (size_t)i + c] += (X)(alpha * (double)pv[c] + om * (double)zv[c]);
   }
   grid_sum2(rr, rho1, next_rr, next_rho1, gr);
 }
@@ -534,68 +560,44 @@ int run_pcg_mg(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* b, T* x,
   return sc_h->breakdown ? MPM_ERR_KRYLOV : MPM_OK;
 }
 
-__global__ void k_d2f(long long n, const double* __restrict__ a, float* b, const Scal* sc) {
-  if (sc && sc->done) return;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
-}
-
-__global__ void k_f2d(long long n, const float* __restrict__ a, double* b, const Scal* sc) {
-  if (sc && sc->done) return;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
-}
-
-// z = B y by one V-cycle on FP64 vectors (4 components over 32*nslice rows).
-// The FP32 V-cycle of the mixed path works on FP32 copies of y and z.
+// z = B y by one V-cycle (vectors of 4 components over 32*nslice rows); an
+// FP64 V-cycle on FP64 vectors, or the FP32 V-cycle on FP32 vectors
 template <class T>
-void mg_precondition(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* y, double* z,
-                     const Scal* sc) {
-  if constexpr (sizeof(T) == 8) {
-    mg_apply<double>(c, m, K, y, z, sc, -1, nullptr);
-  } else {
-    cudaStream_t st = c->stream;
-    long long n4 = 4LL * 32 * m->nslice;
-    float* y32 = grow<float>(c, c->v[23], 2 * (size_t)n4);
-    float* z32 = y32 + n4;
-    MPM_LAUNCH_P(MPM_PROF_MG, k_d2f<<<4 * 152, 256, 0, st>>>(n4, y, y32, sc));
-    mg_apply<float>(c, m, K, y32, z32, sc, -1, nullptr);
-    MPM_LAUNCH_P(MPM_PROF_MG, k_f2d<<<4 * 152, 256, 0, st>>>(n4, z32, z, sc));
-  }
+void mg_precondition(mpm_ctx* c, const mpm_mesh* m, const T* K, const T* y, T* z, const Scal* sc) {
+  mg_apply<T>(c, m, K, y, z, sc, -1, nullptr);
 }
 
 // BiCGStab, right preconditioned by block Jacobi (Dinv) or, with Dinv null,
-// by one multigrid V-cycle per half-step (mg_setup already run for K)
-template <class T>
-int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, const double* b,
-                 double* x, double tol, int maxit, Scal* sc_d, Scal* sc_h, double* relres,
+// by one multigrid V-cycle per half-step (mg_setup already run for K).  The
+// vectors are T (the matrix precision): FP64, or FP32 for the inner solve of
+// the mixed path; x (X) is the caller's 3-component solution.
+template <class T, class X>
+int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const T* Dinv, const double* b,
+                 X* x, double tol, int maxit, Scal* sc_d, Scal* sc_h, double* relres,
                  int* iters) {
+  typedef T V;
   cudaStream_t st = c->stream;
   int nd = m->ndof, npad = 32 * m->nslice;
   size_t n4 = 4 * (size_t)npad;
-  double* r = grow<double>(c, c->v[4], n4);
-  double* r0 = grow<double>(c, c->v[5], n4);
-  double* p = grow<double>(c, c->v[6], n4);
-  double* v = grow<double>(c, c->v[7], n4);
-  double* s = grow<double>(c, c->v[8], n4);
-  double* t = grow<double>(c, c->v[9], n4);
-  double* ph = grow<double>(c, c->v[10], n4);
-  double* shv = grow<double>(c, c->v[11], n4);
+  V* r = grow<V>(c, c->v[4], n4);
+  V* r0 = grow<V>(c, c->v[5], n4);
+  V* p = grow<V>(c, c->v[6], n4);
+  V* v = grow<V>(c, c->v[7], n4);
+  V* s = grow<V>(c, c->v[8], n4);
+  V* t = grow<V>(c, c->v[9], n4);
+  V* ph = grow<V>(c, c->v[10], n4);
+  V* shv = grow<V>(c, c->v[11], n4);
   Sliced S = sliced_of(m);
   const int* mask = ptr<int>(m->dof_mask);
   MPM_CUDA(cudaMemsetAsync(sc_d, 0, sizeof(Scal), st));
-  MPM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * 3 * nd, st));
-  MPM_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * n4, st));
-  MPM_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * n4, st));
+  MPM_CUDA(cudaMemsetAsync(p, 0, sizeof(V) * n4, st));
+  MPM_CUDA(cudaMemsetAsync(v, 0, sizeof(V) * n4, st));
   double* red = c->d_red + 40;  // rho1 / rr accumulators of the next iteration
   MPM_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
   int vb = 4 * 152, it = 0;
   GridRed gr = grid_red(c, 2, std::max(vb, grid_for(npad, 32 * SW)));
-  // r = r0 = b (free components), ||b||^2 via r = b - K*0
-  MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<T, 4><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, x, residual_split(c, m, K, x), b, mask, r, &sc_d->bb, gr));
-  MPM_LAUNCH(k_copy_d<<<grid_for((long long)n4, 256), 256, 0, st>>>((int)n4, r0, r));
+  // r = r0 = b (free components), x = 0, ||b||^2
+  MPM_LAUNCH(k_bicg_init<V, X><<<vb, 256, 0, st>>>(nd, npad, b, mask, x, r, r0, sc_d, gr));
   MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
   MPM_CUDA(cudaStreamSynchronize(st));
   double bb = sc_h->bb;
@@ -615,18 +617,14 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const double* Dinv, 
     int iend = std::min(maxit, it + batch);
     for (; it < iend; ++it) {
       MPM_CUDA(cudaMemsetAsync(red, 0, 2 * sizeof(double), st));
-      MPM_LAUNCH(k_bicg_p<<<vb, 256, 0, st>>>(npad, p, r, v, ph, Dinv, sc_d));
-      if (!Dinv) {
-        mg_precondition<T>(c, m, K, p, ph, sc_d);
-      }
-      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, ph, v, r0, &sc_d->a[4], nullptr, sc_d, 0, gr));
-      MPM_LAUNCH(k_bicg_s<<<vb, 256, 0, st>>>(npad, r, v, s, shv, Dinv, sc_d, gr));
-      MPM_LAUNCH(k_bicg_check_s<<<vb, 256, 0, st>>>(nd, x, ph, sc_d));
-      if (!Dinv) {
-        mg_precondition<T>(c, m, K, s, shv, sc_d);
-      }
-      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, shv, t, s, &sc_d->a[6], &sc_d->a[7], sc_d, 1, gr));
-      MPM_LAUNCH(k_bicg_x<<<vb, 256, 0, st>>>(nd, npad, x, r, ph, shv, s, t, r0, sc_d, red, red + 1, gr));
+      MPM_LAUNCH(k_bicg_p<V><<<vb, 256, 0, st>>>(npad, p, r, v, ph, Dinv, sc_d));
+      if (!Dinv) mg_precondition<T>(c, m, K, p, ph, sc_d);
+      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T, V><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, ph, v, r0, &sc_d->a[4], nullptr, sc_d, 0, gr));
+      MPM_LAUNCH(k_bicg_s<V><<<vb, 256, 0, st>>>(npad, r, v, s, shv, Dinv, sc_d, gr));
+      MPM_LAUNCH(k_bicg_check_s<V, X><<<vb, 256, 0, st>>>(nd, x, ph, sc_d));
+      if (!Dinv) mg_precondition<T>(c, m, K, s, shv, sc_d);
+      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_spmv_dot<T, V><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, K, shv, t, s, &sc_d->a[6], &sc_d->a[7], sc_d, 1, gr));
+      MPM_LAUNCH(k_bicg_x<V, X><<<vb, 256, 0, st>>>(nd, npad, x, r, ph, shv, s, t, r0, sc_d, red, red + 1, gr));
       MPM_LAUNCH(k_bicg_rotate<<<1, 1, 0, st>>>(sc_d, red, red + 1, it + 1));
     }
     MPM_CUDA(cudaMemcpyAsync(sc_h, sc_d, sizeof(Scal), cudaMemcpyDeviceToHost, st));
@@ -651,8 +649,10 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   const int* col = ptr<int>(m->col);
   Sliced S = sliced_of(m);
   int method = prm.method;
-  // non-associated Drucker-Prager and Coulomb friction make K non-symmetric
-  bool sym = !(mat.model == 2 && mat.psi != mat.phi) && !(mat.mu > 0.0 && mat.contact_on);
+  // non-associated Drucker-Prager, the Willam-Warnke cone (its potential is
+  // not its yield function) and Coulomb friction make K non-symmetric
+  bool sym = !(mat.model == 2 && mat.psi != mat.phi) && mat.model != 3 &&
+             !(mat.mu > 0.0 && mat.contact_on);
   if (method == 0) method = sym ? 1 : 2;
   bool mgb = method == 3 && !sym;  // multigrid-preconditioned BiCGStab
   Scal* sc_d = grow<Scal>(c, c->v[20], 1);
@@ -674,7 +674,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     int sst;
     if (mgb) {
       mg_setup<double>(c, m, Kd, prm.mg_reuse != 0);
-      sst = run_bicgstab<double>(c, m, Kd, nullptr, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
+      sst = run_bicgstab<double, double>(c, m, Kd, nullptr, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
     } else if (method == 3) {
       mg_setup<double>(c, m, Kd, prm.mg_reuse != 0);
       sst = run_pcg_mg<double>(c, m, Kd, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its,
@@ -685,7 +685,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
                                     grow<double>(c, c->v[4], n4), grow<double>(c, c->v[5], n4),
                                     grow<double>(c, c->v[6], n4), grow<double>(c, c->v[7], n4));
     else
-      sst = run_bicgstab<double>(c, m, Kd, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
+      sst = run_bicgstab<double, double>(c, m, Kd, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
     out->iterations = its;
     out->relres = rel;
     out->status = sst;
@@ -696,81 +696,71 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
                        std::to_string(rel) + (sc_h->breakdown ? ", breakdown)" : ")"));
     return;
   }
-  // mixed: FP32 inner solves inside FP64 iterative refinement
+  // mixed: FP32 inner solves (PCG for symmetric K, BiCGStab otherwise) inside
+  // FP64 iterative refinement, the refinement residual accumulated in
+  // double-float arithmetic from the FP32 matrix
   const float* Kf = (const float*)K;
   double inner = prm.inner_tol > 0 ? prm.inner_tol : 1e-3;
   double* r64 = grow<double>(c, c->v[12], n3);
   float* d32 = grow<float>(c, c->v[13], n3);
   double* slot = c->d_red + 44;
   GridRed gred = grid_red(c, 2, grid_for(npad, 32 * SW));
-  if ((method == 1 || method == 3) && !mgb) {
-    float* Dinv = grow<float>(c, c->v[3], 12 * (size_t)npad);
-    if (method == 3)
-      mg_setup<float>(c, m, Kf, prm.mg_reuse != 0);
+  bool bicg = !sym && method != 1;
+  float* Dinv = grow<float>(c, c->v[3], 12 * (size_t)npad);
+  if (method == 3)
+    mg_setup<float>(c, m, Kf, prm.mg_reuse != 0);
+  else
+    MPM_LAUNCH(k_block_jacobi<float, float><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, Kf, Dinv, c->d_err));
+  float* r = grow<float>(c, c->v[4], n4);
+  float* z = grow<float>(c, c->v[5], n4);
+  float* pp = grow<float>(c, c->v[6], n4);
+  float* q = grow<float>(c, c->v[7], n4);
+  MPM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n3, st));
+  MPM_CUDA(cudaMemsetAsync(slot, 0, sizeof(double), st));
+  MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, residual_split(c, m, Kf, x), b, ptr<int>(m->dof_mask), r64, slot, gred));
+  MPM_CUDA(cudaMemcpyAsync(c->h_red + 60, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
+  MPM_CUDA(cudaStreamSynchronize(st));
+  double bb = c->h_red[60], rr = bb;
+  int total = 0, rounds = 0, status = MPM_OK;
+  bool breakdown = false;
+  while (rr > prm.tol * prm.tol * bb && rr > 0.0) {
+    if (total >= prm.maxit || rounds >= 50) {
+      status = MPM_ERR_KRYLOV;
+      break;
+    }
+    int its = 0;
+    double rel = 0.0;
+    int sst;
+    if (bicg)
+      sst = run_bicgstab<float, float>(c, m, Kf, method == 3 ? nullptr : Dinv, r64, d32, inner,
+                                       prm.maxit - total, sc_d, sc_h, &rel, &its);
+    else if (method == 3)
+      sst = run_pcg_mg<float>(c, m, Kf, r64, d32, inner, prm.maxit - total, sc_d, sc_h, &rel, &its, r,
+                              z, pp, q);
     else
-      MPM_LAUNCH(k_block_jacobi<float, float><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, Kf, Dinv, c->d_err));
-    float* r = grow<float>(c, c->v[4], n4);
-    float* z = grow<float>(c, c->v[5], n4);
-    float* pp = grow<float>(c, c->v[6], n4);
-    float* q = grow<float>(c, c->v[7], n4);
-    MPM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n3, st));
+      sst = run_pcg<float, float>(c, m, Kf, Dinv, r64, d32, inner, prm.maxit - total, sc_d, sc_h,
+                                  &rel, &its, r, z, pp, q);
+    total += its;
+    ++rounds;
+    breakdown = breakdown || sc_h->breakdown;
+    if (sst && its == 0) {
+      status = MPM_ERR_KRYLOV;
+      break;
+    }
+    MPM_LAUNCH(k_axpy_f2d<<<grid_for(n3, 256), 256, 0, st>>>(n3, x, d32));
     MPM_CUDA(cudaMemsetAsync(slot, 0, sizeof(double), st));
     MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, residual_split(c, m, Kf, x), b, ptr<int>(m->dof_mask), r64, slot, gred));
     MPM_CUDA(cudaMemcpyAsync(c->h_red + 60, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
-    double bb = c->h_red[60], rr = bb;
-    int total = 0, rounds = 0, status = MPM_OK;
-    while (rr > prm.tol * prm.tol * bb && rr > 0.0) {
-      if (total >= prm.maxit || rounds >= 50) {
-        status = MPM_ERR_KRYLOV;
-        break;
-      }
-      int its = 0;
-      double rel = 0.0;
-      int sst = method == 3
-                    ? run_pcg_mg<float>(c, m, Kf, r64, d32, inner, prm.maxit - total, sc_d, sc_h, &rel,
-                                        &its, r, z, pp, q)
-                    : run_pcg<float, float>(c, m, Kf, Dinv, r64, d32, inner, prm.maxit - total, sc_d,
-                                            sc_h, &rel, &its, r, z, pp, q);
-      total += its;
-      ++rounds;
-      if (sst && its == 0) {
-        status = MPM_ERR_KRYLOV;
-        break;
-      }
-      MPM_LAUNCH(k_axpy_f2d<<<grid_for(n3, 256), 256, 0, st>>>(n3, x, d32));
-      MPM_CUDA(cudaMemsetAsync(slot, 0, sizeof(double), st));
-      MPM_LAUNCH_P(MPM_PROF_REFINE, k_residual64<float, 3><<<grid_for(npad, 32 * SW), 32 * SW, 0, st>>>(nd, npad, S, Kf, x, residual_split(c, m, Kf, x), b, ptr<int>(m->dof_mask), r64, slot, gred));
-      MPM_CUDA(cudaMemcpyAsync(c->h_red + 60, slot, sizeof(double), cudaMemcpyDeviceToHost, st));
-      MPM_CUDA(cudaStreamSynchronize(st));
-      rr = c->h_red[60];
-    }
-    out->iterations = total;
-    out->refinements = rounds;
-    out->relres = bb > 0 ? sqrt(rr / bb) : 0.0;
-    out->status = status;
-    if (status) set_error(c, "mixed-precision refinement did not reach the tolerance");
-    return;
+    rr = c->h_red[60];
   }
-  // non-symmetric mixed: BiCGStab on the FP32 matrix with FP64 vectors,
-  // preconditioned by block Jacobi or by the FP32 multigrid V-cycle
-  double* Dinv = nullptr;
-  if (mgb) {
-    mg_setup<float>(c, m, Kf, prm.mg_reuse != 0);
-  } else {
-    Dinv = grow<double>(c, c->v[3], 12 * (size_t)npad);
-    MPM_LAUNCH(k_block_jacobi<float, double><<<grid_for(nd, 256), 256, 0, st>>>(nd, rp, col, S, Kf, Dinv, c->d_err));
-  }
-  int its = 0;
-  double rel = 0.0;
-  int sst = run_bicgstab<float>(c, m, Kf, Dinv, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
-  out->iterations = its;
-  out->relres = rel;
-  out->status = sst;
-  if (sst)
-    set_error(c, std::string(mgb ? "multigrid BiCGStab" : "BiCGStab") + " (FP32 matrix) did not reach the tolerance (" + std::to_string(its) +
-                     " iterations, relative residual " + std::to_string(rel) +
-                     (sc_h->breakdown ? ", breakdown)" : ")"));
+  out->iterations = total;
+  out->refinements = rounds;
+  out->relres = bb > 0 ? sqrt(rr / bb) : 0.0;
+  out->status = status;
+  if (status)
+    set_error(c, std::string("mixed-precision refinement (") + (bicg ? "BiCGStab" : "PCG") +
+                     " inner solves) did not reach the tolerance" + (breakdown ? " (breakdown)" : ""));
 }
 
 // ---------------------------------------------------------------- allocation-free PCG

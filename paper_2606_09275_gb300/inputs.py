@@ -108,11 +108,11 @@ def sphere_mesh(radius, nlat=40, nlon=40):
     return dict(v=np.array(v), t=np.array(tri, dtype=np.int32))
 
 
-def cylinder_mesh(radius, height, nside=64):
+def cylinder_mesh(radius, height, nside=64, phase=0.0):
     """Closed triangulated flat-ended cylinder (a prism of nside sides) with
     its bottom face at z = 0 centred on the axis, counter-clockwise seen from
-    outside."""
-    ph = 2 * np.pi * np.arange(nside) / nside
+    outside; the polygon's vertices at angles (k + phase) 2 pi / nside."""
+    ph = 2 * np.pi * (np.arange(nside) + phase) / nside
     v = [[0.0, 0.0, 0.0], [0.0, 0.0, height]]
     for z in (0.0, height):
         for p in ph:

@@ -54,6 +54,10 @@ CASES = {
     # a closed triangulated body (Sec. 2.3's faceted rigid bodies): a coarse
     # sphere pressed into the block, with friction and a sideways motion
     "sphere_mesh": lambda: (sphere_cfg(), None),
+    # the CPT material (Sec. 6.4): the Willam-Warnke cone, plastic, under the cone
+    "cone_ww": lambda: (inputs.workload("cone", model=3, phi=math.radians(32.0),
+                                        psi=math.radians(2.0)),
+                        inputs.body_z(inputs.workload("cone"), 1)),
     # the benchmark's recipe one level coarser: 239 k points, 101 k unknowns,
     # 3.6 M blocks, rows up to 171 blocks (the tangent's long-row pass)
     "indent_small": lambda: (inputs.workload("indent_small"),
@@ -119,7 +123,7 @@ def free_mask(bcmask):
 
 
 @pytest.mark.parametrize("case", ["tiny_punch", "punch_d3_6", "cone_d4_8", "jitter_hang",
-                                  "friction_punch", "sphere_mesh", "indent_small"])
+                                  "friction_punch", "sphere_mesh", "cone_ww", "indent_small"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_assembly_matches_oracle(gpu, case, precision):
     mpm, ctx, torch = gpu
@@ -209,8 +213,9 @@ def run_steps(gpu, cfg, nsteps, precision=0, tol=1e-12, lin_tol=1e-13):
             om.set_body_z(bz)
         so = om.step(load=inputs.load_factor(cfg, n), tol=tol, lin_tol=min(lin_tol, 1e-13))
         sg = mpm.step(ctx, cfg, P, body_z=bz, load=inputs.load_factor(cfg, n), tol=tol,
-                      lin_tol=lin_tol, precision=precision, lin_maxit=100000)
-        assert so["status"] == 0 and sg["status"] == 0
+                      lin_tol=lin_tol, precision=precision, lin_maxit=100000, check=False)
+        assert so["status"] == 0, (n, so["res_hist"])
+        assert sg["status"] == 0, (n, sg["res_hist"], ctx.error())
         hist_o.append(so)
         hist_g.append(sg)
     return om, P, hist_o, hist_g
@@ -259,14 +264,34 @@ def test_punch_steps_with_friction_match_oracle_fp64(gpu):
 
 
 def test_triangulated_punch_steps_with_friction_match_oracle_fp64(gpu):
-    # the flat punch as a closed 64-sided prism of triangles, mu = 0.3
+    # the flat punch as a closed 64-sided prism of triangles, mu = 0.3; the
+    # polygon turned by half a side, so that no lattice corner lies on a
+    # bisector between two wall faces (where the nearest face, and so the
+    # contact normal, jumps, and a tie in the distance decides it)
     cfg = inputs.workload("punch", mu=0.3)
-    cfg["body"] = dict(cfg["body"], kind=3, mesh=inputs.cylinder_mesh(0.1, 0.6, 64))
+    cfg["body"] = dict(cfg["body"], kind=3, mesh=inputs.cylinder_mesh(0.1, 0.6, 64, phase=0.5))
     om, P, ho, hg = run_steps(gpu, cfg, 2)
     for a, b in zip(ho, hg):
         assert np.max(np.abs(b["reaction"] - a["reaction"])) <= 1e-9 * abs(a["reaction"][2])
     po, pg = om.points(), P.numpy()
     assert np.max(np.abs(pg["x"] - po["x"])) <= 1e-9 * 0.1 * 2 / 50
+    for k in ("F", "be", "lp"):
+        assert np.max(np.abs(pg[k] - po[k])) <= 1e-9 * max(1.0, np.abs(po[k]).max()), k
+
+
+def test_cpt_willam_warnke_steps_match_oracle_fp64(gpu):
+    # Sec. 6.4's CPT on a coarse quarter domain: the Willam-Warnke cone,
+    # E50 by depth, self-weight ramped over 5 steps, the cone with friction
+    # 0.3 in contact from step 3 on; five load steps, FP64, against the oracle
+    cfg = inputs.workload("cpt", depth_min=4, depth_max=7, dx_region=2 * 25.6 / 128,
+                          points=dict(spacing=0.8))
+    om, P, ho, hg = run_steps(gpu, cfg, 5)
+    assert abs(ho[-1]["reaction"][2]) > 0
+    for a, b in zip(ho, hg):
+        assert np.max(np.abs(b["reaction"] - a["reaction"])) <= 1e-9 * max(abs(a["reaction"][2]), 1.0)
+    po, pg = om.points(), P.numpy()
+    assert pg["x"].shape == po["x"].shape
+    assert np.max(np.abs(pg["x"] - po["x"])) <= 1e-9 * 0.1
     for k in ("F", "be", "lp"):
         assert np.max(np.abs(pg[k] - po[k])) <= 1e-9 * max(1.0, np.abs(po[k]).max()), k
 
@@ -280,9 +305,13 @@ def test_punch_steps_mixed_precision_within_1e6(gpu):
 
 def test_cone_drucker_prager_step_matches_oracle(gpu):
     # non-associated Drucker-Prager (BiCGStab) with the cone in contact: the
-    # reactions and every point array at 1e-9 after two load steps
+    # reactions and every point array at 1e-9 after two load steps.  Newton
+    # to 2e-10: the oracle's own FP64 residual of this case stops falling at
+    # 5e-11 to 8e-11 of |f| (rounding under the cone tip, where the penalty
+    # stiffness is largest), after the quadratic drop 4e-7 -> 1e-10 of
+    # iteration 6 in both load steps
     cfg = inputs.workload("cone")
-    om, P, ho, hg = run_steps(gpu, cfg, 2, tol=1e-12, lin_tol=1e-12)
+    om, P, ho, hg = run_steps(gpu, cfg, 2, tol=2e-10, lin_tol=1e-13)
     for a, b in zip(ho, hg):
         ra, rb = a["reaction"][2], b["reaction"][2]
         assert abs(rb - ra) <= 1e-9 * abs(ra)
