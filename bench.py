@@ -224,6 +224,15 @@ def reference_main(a):
 
 # ----------------------------------------------------------------- byte and flop models
 
+# ALU and shared-memory ceilings derived from GB300's unit counts and clock
+# (152 SMs at 2070 MHz; 128 FP32 lanes and 128 bytes per clock of shared
+# memory per SM)
+FP32_PEAK = 152 * 128 * 2 * 2.07e9
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s (derived, not measured)"
+SMEM_PEAK = 152 * 128 * 2.07e9
+SMEM_PEAK_NOTE = "152 SMs x 128 B/clock x 2.07 GHz = 40.3 TB/s (derived, not measured)"
+
+
 def spmv_bytes(nnzb, nd, mixed):
     """Algorithmic bytes of one fused PCG SpMV launch: matrix values and column
     indices once, row pointers, and z, p, q (p and q read and written)."""
@@ -253,10 +262,16 @@ def kernel_models(s, mixed=True):
     # tangent rows, per Newton iteration (its two launches together): the
     # 81-entry tangents, grad_x S and support indices, the source keys, V0,
     # ghost coefficients and columns in; the sliced K out
+    # and its arithmetic: 27 FMA per (source, column) pair, npair = sum of the
+    # squared support sizes, plus the 27 terms of each source (81 FMA + 27
+    # multiplications); its accumulators take 9 shared-memory read-modify-writes
+    # per pair (72 bytes in FP32)
+    npair = s.get("npair") or 0
     m["tangent_rows"] = dict(kernel="k_tangent_rows<float> (both passes)",
                              what="row-gather tangent assembly, per Newton iteration",
                              bytes=P * (81 * w + 8) + nsrc * (3 * w + 4 + 8) + nnzb * 12 + nslot * 9 * w,
-                             bound="hbm", per="newton_it")
+                             fp32_flops=54.0 * npair + 189.0 * nsrc, smem_bytes=2.0 * 9 * w * npair,
+                             bound="latency", per="newton_it")
     # internal-force gather + residual rows: FP64, 9 FMA per (point, support)
     m["residual_rows"] = dict(kernel="k_residual_rows", what="internal-force gather + residual (FP64)",
                               bytes=nsrc * (8 + 24) + P * 96 + nnzb * 12 + nd * 96,
@@ -288,31 +303,46 @@ def roofline_entries(prof, s, hbm_peak, fp64_peak, mixed=True):
             f = mdl["flops"] / (per * 1e-3)
             e.update(fp64_flops=int(mdl["flops"]), achieved_fp64_tflops=round(f / 1e12, 4),
                      fp64_frac=round(f / fp64_peak, 4))
+        if mdl.get("fp32_flops"):
+            f = mdl["fp32_flops"] / (per * 1e-3)
+            e.update(fp32_flops=int(mdl["fp32_flops"]), achieved_fp32_tflops=round(f / 1e12, 3),
+                     fp32_frac=round(f / FP32_PEAK, 4), fp32_peak_note=FP32_PEAK_NOTE,
+                     smem_bytes=int(mdl["smem_bytes"]),
+                     smem_frac=round(mdl["smem_bytes"] / (per * 1e-3) / SMEM_PEAK, 4),
+                     smem_peak_note=SMEM_PEAK_NOTE)
         if mdl.get("per"):
             e["per"] = mdl["per"]
         out[name] = e
     return out
 
 
+def source_hash(parts):
+    """Hash of the text of the named functions ([file, function name] pairs):
+    the kernel and the device helpers it calls."""
+    txt = ""
+    for path, name in parts:
+        with open(os.path.join(ROOT, path)) as f:
+            src = f.read()
+        i = src.find(" " + name + "(")
+        if i < 0:
+            return None
+        i = src.rfind("\n", 0, i) + 1
+        txt += src[i:src.index("\n}\n", i) + 3]
+    return hashlib.sha256(txt.encode()).hexdigest()[:16]
+
+
 def traffic_record(kernel):
-    """ncu DRAM bytes per launch of the kernel, if captured for the current source."""
+    """ncu DRAM bytes per launch of the kernel, if captured for the current
+    source (the record's "parts" and their hash)."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             rec = json.load(f)
     except Exception:
         return None
     r = rec.get(kernel)
-    if not r:
+    if not r or "parts" not in r:
         return None
-    with open(os.path.join(ROOT, r["source"])) as f:
-        src = f.read()
-    txt = ""
-    for name in r["kernels"]:
-        i = src.find("__global__ void " + name)
-        if i < 0:
-            return None
-        txt += src[i:src.index("\n}\n", i) + 3]
-    if hashlib.sha256(txt.encode()).hexdigest()[:16] != r["source_sha"]:
+    if source_hash(r["parts"]) != r["source_sha"]:
         return None  # the kernel changed since the counters were taken
     return r
 

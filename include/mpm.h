@@ -165,9 +165,12 @@ typedef struct {
   /* sizes of the step's mesh, for the benchmark's byte counts: point-support
    * pairs plus ghost-face entries of the row source lists, padded block slots
    * of the sliced stiffness, and the rows and stencil size of the first
-   * multigrid level (0 when no multigrid solve ran) */
+   * multigrid level (0 when no multigrid solve ran); npair: the sum over the
+   * points of their squared support sizes (the point-pair blocks of the
+   * tangent) */
   long long nsrc, nslot;
   int mg_rows1, mg_stencil1;
+  long long npair;
 } mpm_step_stats;
 
 typedef struct mpm_ctx mpm_ctx;

@@ -257,17 +257,21 @@ __global__ void k_tangent_state(int P, const double* __restrict__ lawst, const d
 
 // grad_x S = grad S . dF^{-1} for the tangent gather (in its precision), without
 // the internal force; also V0 in that precision, so that the gather converts
-// nothing (a conversion from FP64 occupies the slow FP64 pipe)
-template <class TG>
-__global__ void k_gx(int P, const int* __restrict__ nsup, const double* __restrict__ dS,
+// nothing.  A conversion from FP64 occupies the FP64 pipe (2 lanes per clock
+// per SM on this part) as long as an FMA, for a whole warp instruction: dF^-1
+// is converted one entry per lane and shared by shuffles, and the FP32 path
+// reads grad S from its FP32 copy (TS = float), made once per mesh build.
+template <class TG, class TS>
+__global__ void k_gx(int P, const int* __restrict__ nsup, const TS* __restrict__ dS,
                      const double* __restrict__ dFinv, const double* __restrict__ V0, TG* gx,
                      TG* V0t) {
   int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (w >= P) return;
-  if (lane == 0) V0t[w] = (TG)V0[w];
+  TG mine = lane < 9 ? (TG)dFinv[9 * (size_t)w + lane] : lane == 9 ? (TG)V0[w] : (TG)0;
   TG fi[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) fi[i] = (TG)dFinv[9 * (size_t)w + i];
+  for (int i = 0; i < 9; ++i) fi[i] = __shfl_sync(0xffffffffu, mine, i);
+  if (lane == 9) V0t[w] = mine;
   int n = nsup[w];
   for (int k = lane; k < n; k += 32) {
     size_t o = (size_t)w * MAXS + k;
@@ -276,6 +280,15 @@ __global__ void k_gx(int P, const int* __restrict__ nsup, const double* __restri
     gx[3 * o + 1] = a0 * fi[1] + a1 * fi[4] + a2 * fi[7];
     gx[3 * o + 2] = a0 * fi[2] + a1 * fi[5] + a2 * fi[8];
   }
+}
+
+// the FP32 copy of the basis gradients (the used slots of every point)
+__global__ void k_dS_to_float(int P, const int* __restrict__ nsup, const double* __restrict__ dS,
+                              float* dS32) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int w = (int)(t / (3 * MAXS)), e = (int)(t - (long long)w * 3 * MAXS);
+  if (w >= P || e >= 3 * nsup[w]) return;
+  dS32[t] = (float)dS[t];
 }
 
 // ------------------------------------------------------------------ internal force and residual
@@ -352,6 +365,8 @@ __host__ __device__ constexpr int tangent_acc_stride() {
   return sizeof(T) == 4 ? 12 : 10;
 }
 
+// shared memory of one warp: the row's accumulators, the 32 terms of the
+// current source, then the row's column table
 template <class T>
 __host__ __device__ inline size_t tangent_warp_bytes(int mr) {
   return (size_t)mr * tangent_acc_stride<T>() * sizeof(T) + 32 * sizeof(T) +
@@ -418,7 +433,7 @@ __device__ inline void tangent_add(double* a, const double* t, double g0, double
 
 // the loads of one source (point w, local index k) of a row, issued together:
 // lane l holds the l-th column of the point's support and its grad_x S, lanes
-// < 27 three entries of A'_p for the 27 terms
+// < 27 the three A'_p values of one of the 27 terms
 template <class T>
 struct TangentSrc {
   int w, n, c;
@@ -445,7 +460,7 @@ __device__ inline void tangent_fetch(TangentSrc<T>& s, uint32_t sid, int P, int 
     s.a1 = A[1];
     s.a2 = A[2];
   }
-  // lane < MAXS: inside the point's slot range whatever its support size
+  // lane < 32 <= MAXS: inside the point's slot range whatever its support size
   size_t o = (size_t)w * MAXS + lane;
   s.c = sidx[o];
   s.g0 = gx[3 * o];
@@ -453,12 +468,26 @@ __device__ inline void tangent_fetch(TangentSrc<T>& s, uint32_t sid, int P, int 
   s.g2 = gx[3 * o + 2];
 }
 
+// one (source, column) pair: its column's place in the row, then the block
+template <class T, bool UPPER>
+__device__ inline void tangent_pair(T* acc, const int* hkey, const int* hval, int hmask, int r, int c,
+                                    const T* t, T g0, T g1, T g2) {
+  constexpr int AS = tangent_acc_stride<T>();
+  if (UPPER && c < r) return;
+  unsigned h = tangent_hash(c, hmask);
+  int key;
+  while ((key = hkey[h]) != c && key != -1) h = (h + 1) & hmask;
+  if (key != c) return;
+  tangent_add(acc + AS * hval[h], t, g0, g1, g2);
+}
+
 // One warp owns block row r: for every point p with r in its support (local
 // index k), K_{r,w} += V0_p (grad_x S_k)^T A'_p (grad_x S_w) for all w in the
 // support of p.  The row accumulates in shared memory (mr = longest row, a
 // multiple of 4), in source order, free of atomics and deterministic; the
-// position of a column in the row comes from a per-row hash table.  Ghost coefficients and the Dirichlet identity rows/columns are
-// applied when the row is written out, coalesced, in the sliced layout.
+// position of a column in the row comes from a per-row hash table.  Ghost coefficients and the
+// Dirichlet identity rows/columns are applied when the row is written out,
+// coalesced, in the sliced layout.
 // UPPER (a symmetric tangent: Hencky, von Mises, frictionless contact): only
 // the blocks of columns c >= r are formed and written, about half the work;
 // k_tangent_mirror then copies each into its transposed place.
@@ -512,27 +541,11 @@ __global__ void __launch_bounds__(32 * TW)
       __syncwarp();
       T t[27];
       tangent_terms(Tt, t);
-      for (int l = lane; l < s.n; l += 32) {
-        int c;
-        T g0, g1, g2;
-        if (l == lane) {
-          c = s.c;
-          g0 = s.g0;
-          g1 = s.g1;
-          g2 = s.g2;
-        } else {  // supports of more than 32 nodes (deep hanging chains)
-          size_t o = (size_t)s.w * MAXS + l;
-          c = sidx[o];
-          g0 = gx[3 * o];
-          g1 = gx[3 * o + 1];
-          g2 = gx[3 * o + 2];
-        }
-        if (UPPER && c < r) continue;
-        unsigned h = tangent_hash(c, hmask);
-        int key;
-        while ((key = hkey[h]) != c && key != -1) h = (h + 1) & hmask;
-        if (key != c) continue;
-        tangent_add(acc + AS * hval[h], t, g0, g1, g2);
+      if (lane < s.n) tangent_pair<T, UPPER>(acc, hkey, hval, hmask, r, s.c, t, s.g0, s.g1, s.g2);
+      // supports of more than 32 nodes (deep hanging chains)
+      for (int l = lane + 32; l < s.n; l += 32) {
+        size_t o = (size_t)s.w * MAXS + l;
+        tangent_pair<T, UPPER>(acc, hkey, hval, hmask, r, sidx[o], t, gx[3 * o], gx[3 * o + 1], gx[3 * o + 2]);
       }
       __syncwarp();
     }
@@ -857,10 +870,14 @@ namespace {
 
 // one pass of the tangent gather (rows of lo < length <= hi blocks)
 template <class T>
-void tangent_launch(mpm_ctx* c, mpm_mesh* m, bool upper, int tw, size_t smem, int lo, int hi, int last,
-                    const void* gx, const void* Aalg, const void* V0t, void* K) {
+void tangent_launch(mpm_ctx* c, mpm_mesh* m, bool upper, int lo, int hi, int last, const void* gx,
+                    const void* Aalg, const void* V0t, void* K) {
   cudaStream_t st = c->stream;
   int nd = m->ndof, P = m->np;
+  size_t wb = tangent_warp_bytes<T>(hi);
+  int tw = (int)std::min<size_t>(TW, (size_t)(220 * 1024) / wb);
+  if (tw < 1) throw CudaError(MPM_ERR_SUPPORT, "stiffness row too long for the tangent gather");
+  size_t smem = wb * tw;
   Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
   auto kern = upper ? k_tangent_rows<T, true> : k_tangent_rows<T, false>;
   MPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -896,6 +913,15 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
   void* Aalg = K ? grow_bytes(c, m->Aalg, 81 * (size_t)P * asz) : nullptr;
   void* gx = K ? grow_bytes(c, m->gx, 3 * (size_t)P * MAXS * asz) : nullptr;
   void* V0t = K ? grow_bytes(c, m->V0t, (size_t)P * asz) : nullptr;
+  const float* dS32 = nullptr;
+  if (K && mixed) {
+    float* d32 = grow<float>(c, m->dS32, 3 * (size_t)P * MAXS);
+    if (m->dS32_gen != m->gen) {
+      MPM_LAUNCH_P(MPM_PROF_FORCE, k_dS_to_float<<<grid_for(3LL * MAXS * P, 256), 256, 0, st>>>(P, nsup, dS, d32));
+      m->dS32_gen = m->gen;
+    }
+    dS32 = d32;
+  }
   double* fint = grow<double>(c, c->v[0], 3 * (size_t)nd);
   double* fc = grow<double>(c, c->v[1], 3 * (size_t)nd);
   bool contact = m->ncand && mat.contact_on && body.kind != 0;
@@ -907,10 +933,10 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
     // dF, dF^-1, tau and spectral state are still in place, R is complete
     if (mixed) {
       MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_tangent_state<float><<<grid_for(P, 128), 128, 0, st>>>(P, lawst, tau, (float*)Aalg));
-      MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<float><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, V0, (float*)gx, (float*)V0t));
+      MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<float, float><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS32, dFinv, V0, (float*)gx, (float*)V0t));
     } else {
       MPM_LAUNCH_P(MPM_PROF_CONSTITUTIVE, k_tangent_state<double><<<grid_for(P, 128), 128, 0, st>>>(P, lawst, tau, (double*)Aalg));
-      MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<double><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, V0, (double*)gx, (double*)V0t));
+      MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<double, double><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, V0, (double*)gx, (double*)V0t));
     }
   } else {
     MPM_LAUNCH_P(MPM_PROF_KINEMATICS, k_kinematics<<<grid_for(8LL * P, 256), 256, 0, st>>>(P, nsup, sidx, dS, du, dF));
@@ -932,9 +958,9 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
         ptr<double>(m->kg), du, ptr<double>(m->fext), fint, R));
     if (K) {
       if (mixed)
-        MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<float><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, V0, (float*)gx, (float*)V0t));
+        MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<float, float><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS32, dFinv, V0, (float*)gx, (float*)V0t));
       else
-        MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<double><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, V0, (double*)gx, (double*)V0t));
+        MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<double, double><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS, dFinv, V0, (double*)gx, (double*)V0t));
     }
   }
   if (K) {
@@ -954,14 +980,10 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
     int np_ = mr > SHORT ? 2 : 1;
     for (int ps = 0; ps < np_; ++ps) {
       int lo = passes[ps][0], hi = passes[ps][1], last = ps == np_ - 1;
-      size_t wb = mixed ? tangent_warp_bytes<float>(hi) : tangent_warp_bytes<double>(hi);
-      int tw = (int)std::min<size_t>(TW, (size_t)(220 * 1024) / wb);
-      if (tw < 1) throw CudaError(MPM_ERR_SUPPORT, "stiffness row too long for the tangent gather");
-      size_t smem = wb * tw;
       if (mixed)
-        tangent_launch<float>(c, m, upper, tw, smem, lo, hi, last, gx, Aalg, V0t, K);
+        tangent_launch<float>(c, m, upper, lo, hi, last, gx, Aalg, V0t, K);
       else
-        tangent_launch<double>(c, m, upper, tw, smem, lo, hi, last, gx, Aalg, V0t, K);
+        tangent_launch<double>(c, m, upper, lo, hi, last, gx, Aalg, V0t, K);
     }
     if (upper) {
       if (mixed)

@@ -995,6 +995,15 @@ __global__ void k_ghost_rows(int nd, int P, const long long* __restrict__ sptr,
 
 // ------------------------------------------------------------------ block pattern
 
+// sum over the points of (support size)^2: the (source, column) pairs of the
+// tangent gather, for the benchmark's operation counts (integer, exact)
+__global__ void k_support_pairs(int P, const int* __restrict__ nsup, unsigned long long* out) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long v = w < P ? (unsigned long long)nsup[w] * (unsigned long long)nsup[w] : 0ULL;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, v);
+}
+
 // source keys: row dof << 32 | source << 6 | local index (points, then ghost faces)
 __global__ void k_src_keys_points(int P, const int* __restrict__ nsup, const int* __restrict__ sidx,
                                   const int* __restrict__ off, uint64_t* keys) {
@@ -1631,6 +1640,12 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     MPM_CUDA(cudaMemsetAsync(sptr, 0, sizeof(long long) * (nd + 1), st));
     MPM_LAUNCH(k_src_ptr<<<grid_for(total, 256), 256, 0, st>>>(total, keys, nd, sptr));
     m->nsrc = total;
+    {
+      unsigned long long* np2 = (unsigned long long*)(c->d_red + 50);
+      MPM_CUDA(cudaMemsetAsync(np2, 0, sizeof(unsigned long long), st));
+      MPM_LAUNCH(k_support_pairs<<<grid_for(P, 256), 256, 0, st>>>(P, nsup, np2));
+      MPM_CUDA(cudaMemcpyAsync(&m->npair, np2, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    }
     int* rowcnt = grow<int>(c, m->rowcnt, nd + 1);
     int* rp = grow<int>(c, m->row_ptr, nd + 1);
     MPM_CUDA(cudaMemsetAsync(rowcnt + nd, 0, sizeof(int), st));

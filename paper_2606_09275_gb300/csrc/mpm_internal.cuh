@@ -214,6 +214,7 @@ struct mpm_mesh {
   mpm::Buf slice_w, slice_base, scol;   // width, first slot of each slice, slot columns
   // sources of each row: (sorted point or ghost face) << 6 | local index
   long long nsrc = 0;
+  long long npair = 0;  // sum of squared support sizes (host copy, read after the build)
   mpm::Buf src_key, src_ptr;
   // gravity force at load 1
   mpm::Buf fext;
@@ -231,6 +232,8 @@ struct mpm_mesh {
   double tri_lo[3] = {0, 0, 0}, tri_hi[3] = {0, 0, 0};
   // per-iteration point data (Mf: V0 tau dF^-T, 12 per point)
   mpm::Buf dF, dFinv, tau, Aalg, gx, Mf, V0t;
+  mpm::Buf dS32;                        // FP32 copy of dS for the mixed tangent's grad_x S
+  long long dS32_gen = -1;              // build the copy belongs to
   mpm::Buf lawst;  // spectral state of the last residual-only evaluation (22 per point)
   int built = 0;
   long long gen = 0;                    // incremented by every build

@@ -698,14 +698,39 @@ __global__ void k_absmax(long long n, const float* __restrict__ K, unsigned* out
 // FP16 copy of K scaled by 2^e (the largest |entry| maps below 2^14, clear of
 // the FP16 limit 65504); scaling by a power of two keeps the copy exactly as
 // symmetric as K.  kscale receives 2^-e.
-__global__ void k_to_half(long long n, const float* __restrict__ K, const unsigned* amax, __half* Kh,
-                          float* kscale) {
+__global__ void k_to_half(int nslice, Sliced SK, const float* __restrict__ K, const unsigned* amax,
+                          __half* Kh, float* kscale) {
   float m = __uint_as_float(*amax);
   int e = 14 - (m > 0.f ? (int)ceilf(log2f(m)) : 0);
   float sc = ldexpf(1.f, e);
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) *kscale = ldexpf(1.f, -e);
-  for (; i < n; i += (long long)gridDim.x * blockDim.x) Kh[i] = __float2half_rn(K[i] * sc);
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) *kscale = ldexpf(1.f, -e);
+  // one warp per slice, a lane per row; the plane-pair layout of sliced_row_h
+  int sl = (int)(t >> 5), ln = (int)(t & 31);
+  if (sl >= nslice) return;
+  int W = SK.w[sl];
+  long long b0 = SK.base[sl];
+  const float* Kb = K + 9 * b0;
+  __half* Hb = Kh + 9 * b0;
+  size_t plane = (size_t)32 * W;
+  auto pack = [sc](float a, float b) {
+    __half2 h = __floats2half2_rn(a * sc, b * sc);
+    return *reinterpret_cast<unsigned*>(&h);
+  };
+  for (int k4 = 0; k4 < (W >> 2); ++k4) {
+    size_t off = ((size_t)k4 * 32 + ln) * 4;
+    float4 v[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) v[q] = *reinterpret_cast<const float4*>(Kb + q * plane + off);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint4 o = {pack(v[2 * q].x, v[2 * q].y), pack(v[2 * q].z, v[2 * q].w),
+                 pack(v[2 * q + 1].x, v[2 * q + 1].y), pack(v[2 * q + 1].z, v[2 * q + 1].w)};
+      *reinterpret_cast<uint4*>(Hb + 2 * q * plane + 2 * off) = o;
+    }
+    uint2 o8 = {pack(v[8].x, v[8].y), pack(v[8].z, v[8].w)};
+    *reinterpret_cast<uint2*>(Hb + 8 * plane + off) = o8;
+  }
 }
 
 // ---------------------------------------------------------------- V-cycle kernels
@@ -727,7 +752,7 @@ __global__ void k_mg_jac0(int n, const T* __restrict__ Dinv, const T* __restrict
 // residual that k_mg_restrict1 gathers to level 1); MODE 1, out = x + Dinv
 // (b - K x) with r.z += b.out by a fixed-order grid sum (rz non-null)
 template <class T, int MODE, class TK>
-__global__ void k_mg_fine(int nd, int npad, Sliced SK, const TK* __restrict__ K, const float* kscale,
+__global__ void __launch_bounds__(256, 4) k_mg_fine(int nd, int npad, Sliced SK, const TK* __restrict__ K, const float* kscale,
                           const T* __restrict__ b, const T* __restrict__ x, const T* __restrict__ Dinv,
                           T* out, const int* __restrict__ fmask, double* rz, const Scal* sk, int k,
                           GridRed gr) {
@@ -802,7 +827,8 @@ __global__ void k_mg_restrict1(int nrow, int npad, const int* __restrict__ tptr,
 
 // uniform level -> next coarser right-hand side: coarse node a gathers the
 // residual rf of the 27 finer nodes 2a + delta (delta in {-1, 0, 1}^3) with
-// the weights prod(1 - |delta|/2), then x = Dinv b; one thread per row
+// the weights prod(1 - |delta|/2), then x = Dinv b; one thread per row, its
+// 27 grid lookups issued before its 27 loads (two round trips, not 27)
 template <class T>
 __global__ void k_mg_restrictu(int nrow, int npad, const int* __restrict__ xyz, int n1f,
                                const int* __restrict__ gid_f, const T* __restrict__ rf,
@@ -814,18 +840,23 @@ __global__ void k_mg_restrictu(int nrow, int npad, const int* __restrict__ xyz, 
   if (a < nrow) {
     int ca[3];
     unpack3(xyz[a], ca);
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          int fx = 2 * ca[0] + dx, fy = 2 * ca[1] + dy, fz = 2 * ca[2] + dz;
-          if (fx < 0 || fy < 0 || fz < 0 || fx >= n1f || fy >= n1f || fz >= n1f) continue;
-          int j = gid_f[fx + n1f * (fy + n1f * fz)];
-          if (j < 0) continue;
-          T f = (T)((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
-          T v[4];
-          ld4(rf + 4 * (size_t)j, v);
-          for (int c = 0; c < 3; ++c) s[c] += f * v[c];
-        }
+    int jq[27];
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      int fx = 2 * ca[0] + q % 3 - 1, fy = 2 * ca[1] + (q / 3) % 3 - 1, fz = 2 * ca[2] + q / 9 - 1;
+      bool in = fx >= 0 && fy >= 0 && fz >= 0 && fx < n1f && fy < n1f && fz < n1f;
+      jq[q] = in ? gid_f[fx + n1f * (fy + n1f * fz)] : -1;
+    }
+    // z, then y, then x offsets, in that order
+#pragma unroll
+    for (int q = 0; q < 27; ++q) {
+      if (jq[q] < 0) continue;
+      int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = q / 9 - 1;
+      T f = (T)((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+      T v[4];
+      ld4(rf + 4 * (size_t)jq[q], v);
+      for (int c = 0; c < 3; ++c) s[c] += f * v[c];
+    }
   }
   T bv[4] = {s[0], s[1], s[2], (T)0}, xv[4];
   st4(b + 4 * (size_t)a, bv);
@@ -973,21 +1004,24 @@ __global__ void k_mg_prolong_u(int nrow, const int* __restrict__ xyz_f, const in
   st4(xf + 4 * (size_t)i, xv);
 }
 
-// coarsest: x = Cinv b (one block)
+// coarsest: x = Cinv b (one block, a warp per output entry, the lanes over
+// the columns, combined by a fixed shuffle tree)
 template <class T>
 __global__ void k_mg_coarse(int nrow, const T* __restrict__ Cinv, const T* __restrict__ b, T* x,
                             const Scal* sk, int k) {
   if (skip(sk, k)) return;
   int n3 = 3 * nrow;
-  for (int i = threadIdx.x; i < 4 * nrow; i += blockDim.x) {
+  int wi = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = wi; i < 4 * nrow; i += nw) {
     int a = i >> 2, c = i & 3;
     T s = (T)0;
     if (c < 3) {
       const T* row = Cinv + (size_t)(3 * a + c) * n3;
-      for (int j = 0; j < nrow; ++j)
+      for (int j = lane; j < nrow; j += 32)
         s += row[3 * j] * b[4 * j] + row[3 * j + 1] * b[4 * j + 1] + row[3 * j + 2] * b[4 * j + 2];
     }
-    x[i] = s;
+    s = warp_sum(s);
+    if (lane == 0) x[i] = s;
   }
 }
 
@@ -1121,7 +1155,7 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
     float* ksc = (float*)(c->d_red + 11);
     MPM_CUDA(cudaMemsetAsync(amax, 0, sizeof(unsigned), st));
     MPM_LAUNCH_P(MPM_PROF_MG_SETUP, k_absmax<<<4 * 152, 256, 0, st>>>(n9, K, amax));
-    MPM_LAUNCH_P(MPM_PROF_MG_SETUP, k_to_half<<<8 * 152, 256, 0, st>>>(n9, K, amax, grow<__half>(c, G.fKh, n9), ksc));
+    MPM_LAUNCH_P(MPM_PROF_MG_SETUP, k_to_half<<<grid_for(32LL * m->nslice, 256), 256, 0, st>>>(m->nslice, SK, K, amax, grow<__half>(c, G.fKh, n9), ksc));
   }
   if (!coarse) return;
   for (int l = 0; l < G.nlev; ++l) {
@@ -1236,7 +1270,7 @@ void vcycle_launch(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z,
         ptr<T>(N.x), sk, k));
   }
   MGLevel& C = G.lev[G.nlev - 1];
-  MPM_LAUNCH_P(MPM_PROF_MG, k_mg_coarse<T><<<1, 256, 0, st>>>(C.nrow, ptr<T>(G.cinv), ptr<T>(C.b), ptr<T>(C.x), sk, k));
+  MPM_LAUNCH_P(MPM_PROF_MG, k_mg_coarse<T><<<1, 1024, 0, st>>>(C.nrow, ptr<T>(G.cinv), ptr<T>(C.b), ptr<T>(C.x), sk, k));
   xcur[G.nlev - 1] = ptr<T>(C.x);
   // up: prolongate, post-smooth (into the r buffer, which becomes the iterate)
   for (int l = G.nlev - 2; l >= 0; --l) {

@@ -137,18 +137,41 @@ __global__ inline void k_split_df(int npad, int nd, const double* __restrict__ x
   xs[2 * (size_t)i + 1] = make_float4(hl[4], hl[5], 0.f, 0.f);
 }
 
-// one group of four FP16 blocks (raw 8-byte words of the 9 planes) times x
-__device__ inline void acc_h4(const uint2* u, int4 c, const float* __restrict__ x, float* y) {
+// The FP16 copy of K keeps the sliced block order but stores the entry
+// planes of a slice in pairs: for planes 2q and 2q + 1 (q < 4), the 4 blocks
+// of a lane's group of one plane, then the same 4 blocks of the other, in one
+// 16-byte word per lane at Kh[9 base + 2q (32 W) + 2 off]; plane 8 as in the
+// FP32 layout, 8 bytes per lane at Kh[9 base + 8 (32 W) + off]
+// (off = (group 32 + lane) 4).  A group of four blocks is then five loads
+// instead of nine.
+
+// one group of four FP16 blocks (the four 16-byte plane pairs and plane 8)
+// times x
+__device__ inline void acc_h4(const uint4* u, uint2 u8, int4 c, const float* __restrict__ x, float* y) {
   int cc[4] = {c.x, c.y, c.z, c.w};
   float v[9][4];
 #pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    float2 fa = __half22float2(*reinterpret_cast<const __half2*>(&u[e].x));
-    float2 fb = __half22float2(*reinterpret_cast<const __half2*>(&u[e].y));
-    v[e][0] = fa.x;
-    v[e][1] = fa.y;
-    v[e][2] = fb.x;
-    v[e][3] = fb.y;
+  for (int q = 0; q < 4; ++q) {
+    float2 a0 = __half22float2(*reinterpret_cast<const __half2*>(&u[q].x));
+    float2 a1 = __half22float2(*reinterpret_cast<const __half2*>(&u[q].y));
+    float2 b0 = __half22float2(*reinterpret_cast<const __half2*>(&u[q].z));
+    float2 b1 = __half22float2(*reinterpret_cast<const __half2*>(&u[q].w));
+    v[2 * q][0] = a0.x;
+    v[2 * q][1] = a0.y;
+    v[2 * q][2] = a1.x;
+    v[2 * q][3] = a1.y;
+    v[2 * q + 1][0] = b0.x;
+    v[2 * q + 1][1] = b0.y;
+    v[2 * q + 1][2] = b1.x;
+    v[2 * q + 1][3] = b1.y;
+  }
+  {
+    float2 a0 = __half22float2(*reinterpret_cast<const __half2*>(&u8.x));
+    float2 a1 = __half22float2(*reinterpret_cast<const __half2*>(&u8.y));
+    v[8][0] = a0.x;
+    v[8][1] = a0.y;
+    v[8][2] = a1.x;
+    v[8][3] = a1.y;
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -160,11 +183,17 @@ __device__ inline void acc_h4(const uint2* u, int4 c, const float* __restrict__ 
   }
 }
 
-// y = row r of an FP16 copy of K (same sliced layout, values scaled by a power
-// of two) times x; FP32 arithmetic, the caller undoes the scale.  Two groups
-// of four blocks per trip, all of their loads issued before the arithmetic:
-// FP16 blocks are half the bytes of FP32 ones, so a trip over one group would
-// keep half as many bytes in flight as the FP32 row product.
+__device__ inline void load_h4(const __half* Kb, size_t plane, size_t off, uint4* u, uint2& u8) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) u[q] = *reinterpret_cast<const uint4*>(Kb + 2 * q * plane + 2 * off);
+  u8 = *reinterpret_cast<const uint2*>(Kb + 8 * plane + off);
+}
+
+// y = row r of the FP16 copy of K (values scaled by a power of two) times x;
+// FP32 arithmetic, the caller undoes the scale.  Two groups of four blocks
+// per trip, all of their loads issued before the arithmetic: FP16 blocks are
+// half the bytes of FP32 ones, so a trip over one group would keep half as
+// many bytes in flight as the FP32 row product.
 __device__ inline void sliced_row_h(int r, Sliced S, const __half* __restrict__ K,
                                     const float* __restrict__ x, float* y) {
   int s = r >> 5, ln = r & 31;
@@ -179,22 +208,20 @@ __device__ inline void sliced_row_h(int r, Sliced S, const __half* __restrict__ 
     size_t off0 = ((size_t)k4 * 32 + ln) * 4, off1 = off0 + 128;
     int4 c0 = *reinterpret_cast<const int4*>(cb + off0);
     int4 c1 = *reinterpret_cast<const int4*>(cb + off1);
-    uint2 u0[9], u1[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      u0[e] = *reinterpret_cast<const uint2*>(Kb + e * plane + off0);
-      u1[e] = *reinterpret_cast<const uint2*>(Kb + e * plane + off1);
-    }
-    acc_h4(u0, c0, x, y);
-    acc_h4(u1, c1, x, y);
+    uint4 u0[4], u1[4];
+    uint2 v0, v1;
+    load_h4(Kb, plane, off0, u0, v0);
+    load_h4(Kb, plane, off1, u1, v1);
+    acc_h4(u0, v0, c0, x, y);
+    acc_h4(u1, v1, c1, x, y);
   }
   if (k4 < n4) {
     size_t off = ((size_t)k4 * 32 + ln) * 4;
     int4 c0 = *reinterpret_cast<const int4*>(cb + off);
-    uint2 u0[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) u0[e] = *reinterpret_cast<const uint2*>(Kb + e * plane + off);
-    acc_h4(u0, c0, x, y);
+    uint4 u0[4];
+    uint2 v0;
+    load_h4(Kb, plane, off, u0, v0);
+    acc_h4(u0, v0, c0, x, y);
   }
 }
 

@@ -172,6 +172,7 @@ extern "C" int mpm_step(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* body
     st.ndof = m->ndof;
     st.nnzb = m->nnzb;
     st.nsrc = m->nsrc;
+    st.npair = m->npair;
     st.nslot = m->nslot;
     if (status) throw CudaError(status, c->err);
     double* du = nullptr;

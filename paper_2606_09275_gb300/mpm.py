@@ -84,7 +84,7 @@ class StepStats(C.Structure):
         ("res_hist", C.c_double * 64), ("eta_hist", C.c_double * 64), ("reaction", C.c_double * 3),
         ("ms_build", C.c_double), ("ms_assemble", C.c_double), ("ms_solve", C.c_double),
         ("ms_update", C.c_double), ("nsrc", C.c_longlong), ("nslot", C.c_longlong),
-        ("mg_rows1", C.c_int), ("mg_stencil1", C.c_int)]
+        ("mg_rows1", C.c_int), ("mg_stencil1", C.c_int), ("npair", C.c_longlong)]
 
 
 class Checkpoint(C.Structure):
@@ -426,7 +426,7 @@ def step(ctx, cfg, points, body_z=None, load=1.0, tol=1e-8, maxit=30, lin_tol=1e
                eta_hist=np.array(ss.eta_hist[: ss.newton_its]), reaction=np.array(ss.reaction[:]),
                ms_build=ss.ms_build, ms_assemble=ss.ms_assemble, ms_solve=ss.ms_solve,
                ms_update=ss.ms_update, nsrc=ss.nsrc, nslot=ss.nslot, mg_rows1=ss.mg_rows1,
-               mg_stencil1=ss.mg_stencil1)
+               mg_stencil1=ss.mg_stencil1, npair=ss.npair)
     if check:
         ctx.check(st)
     return out

@@ -74,3 +74,31 @@ def test_l1_block_jacobi_bounds_the_stiffness(plastic):
     # is what makes a weight near 2 pay
     print("generalized eigenvalues of (K, M): [%.3e, %.3f]" % (lam.min(), lam.max()))
     assert lam.max() < 0.9
+
+
+@pytest.mark.parametrize("plastic", [False, True])
+def test_fp16_operator_copy_keeps_the_vcycle_positive_definite(plastic):
+    # the fine level of the V-cycle applies an FP16 copy of K (scaled by a
+    # power of two so that its largest entry sits just below 2^15, rounded to
+    # nearest) with the l1 block Jacobi M of the unrounded K: the cycle stays
+    # SPD while the rounded operator K_h is SPD and 2 M / w - K_h > 0; the
+    # rounding moves each entry by at most 2^-11 of itself, far inside the
+    # 5 % margin of 2 / w = 1.053
+    cfg = tiny_cfg()
+    if plastic:
+        cfg["points"]["ys"] = 2e4
+    m = oracle.Model(cfg, inputs.make_points(cfg), body_z=0.49)
+    m.build()
+    n3 = 3 * m.counts()["ndof"]
+    du = 2e-4 * np.random.default_rng(3).standard_normal(n3) if plastic else np.zeros(n3)
+    out = m.assemble(du)
+    A, free = dense_free(m, out["K"])
+    Kf, Mf = l1_block_jacobi(A, free)
+    Kf = 0.5 * (Kf + Kf.T)
+    e = 14 - int(np.ceil(np.log2(np.abs(Kf).max())))
+    Kh = (Kf * 2.0 ** e).astype(np.float16).astype(np.float64) * 2.0 ** -e
+    assert np.abs(Kh - Kf).max() <= 2.0 ** -11 * np.abs(Kf).max()
+    assert np.linalg.eigvalsh(Kh).min() > 0.0
+    lam = sla.eigh(Kh, Mf, eigvals_only=True)
+    assert lam.max() < 2.0 / W, lam.max()
+    assert np.linalg.eigvalsh(2.0 * Mf / W - Kh).min() > 0.0
