@@ -46,6 +46,10 @@ def lib():
         L.o_eig_sym3.argtypes = [vp, vp, vp]
         L.o_point_stress.argtypes = [vp, vp, vp]
         L.o_body_sdf.argtypes = [C.POINTER(Params), vp, vp, vp, vp]
+        L.o_assemble_body.argtypes = [vp, vp, vp, C.c_double] + [vp] * 8
+        L.o_set_velocity.argtypes = [vp, vp]
+        L.o_get_velocity.argtypes = [vp, vp]
+        L.o_get_body.argtypes = [vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -62,7 +66,9 @@ class Params(C.Structure):
                 ("ghost_on", C.c_int), ("contact_on", C.c_int),
                 ("mu", C.c_double), ("pt", C.c_double), ("body_d", C.c_double * 3),
                 ("ntri", C.c_int), ("nvert", C.c_int), ("tri_v", C.c_void_p),
-                ("tri_t", C.c_void_p)]
+                ("tri_t", C.c_void_p), ("dt", C.c_double), ("body_free", C.c_int),
+                ("body_mass", C.c_double), ("body_inertia", C.c_double),
+                ("body_v", C.c_double * 3), ("body_w", C.c_double * 3)]
 
 
 class Counts(C.Structure):
@@ -78,7 +84,7 @@ class StepParams(C.Structure):
 class StepStats(C.Structure):
     _fields_ = [("newton_its", C.c_int), ("lin_its_total", C.c_int), ("status", C.c_int),
                 ("res_hist", C.c_double * 64), ("reaction", C.c_double * 3),
-                ("eta_hist", C.c_double * 64)]
+                ("eta_hist", C.c_double * 64), ("body_q", C.c_double * 6)]
 
 
 def params_from_cfg(cfg, body_z=None):
@@ -106,10 +112,18 @@ def params_from_cfg(cfg, body_z=None):
     p.kappa, p.pf = cfg.get("kappa", 10.0), cfg.get("pf", 50.0)
     p.ghost_on, p.contact_on = int(cfg.get("ghost", 1)), int(cfg.get("contact", 1))
     p.mu, p.pt = cfg.get("mu", 0.0), cfg.get("pt", 25.0)
+    p.dt = cfg.get("dt", 0.0)
     if b:
         d = b.get("step_d", (0.0, 0.0, b.get("dz", 0.0)))
         for k in range(3):
             p.body_d[k] = d[k]
+        # a free body (time steps only): free components, mass, rotational
+        # inertia and its velocities at the start
+        p.body_free = int(b.get("free", 0))
+        p.body_mass, p.body_inertia = b.get("mass", 0.0), b.get("inertia", 0.0)
+        for k in range(3):
+            p.body_v[k] = b.get("v", (0.0, 0.0, 0.0))[k]
+            p.body_w[k] = b.get("w", (0.0, 0.0, 0.0))[k]
         if b["kind"] == 3:
             # the triangulated surface: host arrays kept alive by the struct
             v = np.ascontiguousarray(b["mesh"]["v"], dtype=np.float64)
@@ -151,6 +165,43 @@ class Model:
 
     def set_body_z(self, z):
         lib().o_set_body_z(self.h, z)
+
+    def set_velocity(self, v):
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+        assert len(v) == self.counts()["npts"] or len(v) == self._keep[0].shape[0]
+        lib().o_set_velocity(self.h, _ptr(v))
+
+    def velocity(self):
+        n = self.counts()["npts"]
+        v = np.zeros((n, 3))
+        lib().o_get_velocity(self.h, _ptr(v))
+        return v
+
+    def body_state(self):
+        out = [np.zeros(3) for _ in range(4)]
+        lib().o_get_body(self.h, *[_ptr(a) for a in out])
+        return dict(pose=out[0], v=out[1], w=out[2], theta=out[3])
+
+    def assemble_body(self, du, q, load=1.0, tangent=True):
+        """Residual and Jacobian of the material and the rigid body's
+        equations at the increments (du, q): R, K (blocks), Rb (6), Kbb (6x6),
+        Kgb (6, 3 ndof) = dR/dq, Kbg (6, 3 ndof) = dRb/du."""
+        c = self.counts()
+        n3 = 3 * c["ndof"]
+        du = np.ascontiguousarray(du, dtype=np.float64).reshape(n3)
+        q = np.ascontiguousarray(q, dtype=np.float64).reshape(6)
+        R = np.zeros(n3)
+        fi = np.zeros(n3 + 2)
+        K = np.zeros((max(c["nnzb"], 1), 3, 3)) if tangent else None
+        reac, Rb, Kbb = np.zeros(3), np.zeros(6), np.zeros((6, 6))
+        Kgb, Kbg = np.zeros((6, n3)), np.zeros((6, n3))
+        st = lib().o_assemble_body(self.h, _ptr(du), _ptr(q), load, _ptr(R),
+                                   _ptr(K) if tangent else None, _ptr(fi), _ptr(reac), _ptr(Rb),
+                                   _ptr(Kbb), _ptr(Kgb), _ptr(Kbg))
+        if st:
+            raise RuntimeError("oracle assemble status %d" % st)
+        return dict(R=R, K=K[: c["nnzb"]] if tangent else None, fint=fi[:n3], fextc_norm=fi[n3],
+                    reaction=reac, Rb=Rb, Kbb=Kbb, Kgb=Kgb, Kbg=Kbg)
 
     def counts(self):
         c = Counts()
@@ -245,7 +296,7 @@ class Model:
         n3 = 3 * c["ndof"]
         du = np.ascontiguousarray(du, dtype=np.float64).reshape(n3)
         R = np.zeros(n3)
-        fi = np.zeros(n3 + 1)
+        fi = np.zeros(n3 + 2)
         K = np.zeros((max(c["nnzb"], 1), 3, 3)) if tangent else None
         reac = np.zeros(3)
         st = lib().o_assemble(self.h, _ptr(du), load, _ptr(R), _ptr(K) if tangent else None,
@@ -287,7 +338,7 @@ class Model:
         return dict(status=ss.status, newton_its=ss.newton_its, lin_its=ss.lin_its_total,
                     res_hist=np.array(ss.res_hist[:nh]),
                     eta_hist=np.array(ss.eta_hist[: ss.newton_its]),
-                    reaction=np.array(ss.reaction[:]))
+                    reaction=np.array(ss.reaction[:]), body_q=np.array(ss.body_q[:]))
 
 
 def constitutive(cfg, E, ys, be_n, dF, tangent=True):

@@ -41,7 +41,8 @@ typedef struct {
   int bc_axis[8];
   double bc_pos[8];
   int bc_mask[8];
-  /* rigid body (Sec. 2.3): 0 none, 1 flat-ended cylinder, 2 cone + shaft */
+  /* rigid body (Sec. 2.3): 0 none, 1 flat-ended cylinder, 2 cone + shaft,
+   * 3 triangulated surface, 4 sphere */
   int body_kind;
   double body_cx, body_cy, body_z;   /* axis and bottom face / tip height */
   double body_r, body_alpha;         /* radius, cone half angle (rad)     */
@@ -68,6 +69,22 @@ typedef struct {
   int ntri, nvert;
   const double* tri_v;
   const int* tri_t;
+  /* body_kind 4: a sphere of radius body_r centred at (body_cx, body_cy,
+   * body_z).
+   * Dynamics (Sec. 2.4): dt > 0 makes the step a Newmark time step with
+   * gamma = 1, beta = 1/2 (dt = 0: a quasi-static load step).  body_free
+   * (bits 0-2 translation x, y, z, bits 3-5 rotation about x, y, z) lists
+   * the rigid-body degrees of freedom that are unknowns of the Newton
+   * iteration, coupled to the material by the contact forces; the others are
+   * prescribed (translation body_d over the step, no rotation).  With free
+   * components the body pose above is the one at the START of the step, and
+   * body_mass, body_inertia (isotropic) and the body's velocity body_v and
+   * angular velocity body_w at the step start enter its Newmark equations;
+   * rotation may be free for the sphere only. */
+  double dt;
+  int body_free;
+  double body_mass, body_inertia;
+  double body_v[3], body_w[3];
 } o_params;
 
 typedef struct o_model o_model;
@@ -89,6 +106,7 @@ typedef struct {
   double res_hist[64];
   double reaction[3];
   double eta_hist[64];
+  double body_q[6];    /* the rigid body's converged increment over the step */
 } o_step_stats;
 
 o_model* o_create(const o_params* prm);
@@ -122,9 +140,28 @@ void o_export_ghost_faces(const o_model* m, int* faces /*4*nghost: K,N,axis,sign
 int o_eval_background(const o_model* m, const double* x, int* nent, int* idx /*O_MAXS*/,
                       double* phi, double* dphi);
 
-/* Eq. (MPMweak): residual and consistent tangent for a nodal increment du */
+/* Eq. (MPMweak): residual and consistent tangent for a nodal increment du;
+ * fint_all (optional) receives f_int over all dofs, then ||f_ext + f_c||, and
+ * for time steps ||f_inert|| (3 ndof + 2 doubles) */
 int o_assemble(o_model* m, const double* du, double load, double* R, double* Kvals,
                double* fint_all, double* reaction);
+/* The same with the rigid body's increment q over the step (translation
+ * q[0..2], rotation q[3..5]; prescribed components must hold their
+ * prescribed values) and the body's equations: Rb[6] (host) its residual
+ * (Newmark inertia, gravity and the contact forces and moments), Kbb[36] its
+ * Jacobian in q (row-major), Kgb[6][3 ndof] the derivative of R in each
+ * component of q, Kbg[6][3 ndof] the derivative of each component of Rb in
+ * du.  Any of the body outputs may be NULL. */
+int o_assemble_body(o_model* m, const double* du, const double* q, double load, double* R,
+                    double* Kvals, double* fint_all, double* reaction, double* Rb, double* Kbb,
+                    double* Kgb, double* Kbg);
+/* material point velocities (3 per point, zero until set; children of a
+ * GIMP split inherit their parent's) and the rigid body's state:
+ * pose[3] (body_cx, body_cy, body_z), v[3], w[3], accumulated rotation
+ * theta[3] */
+int o_set_velocity(o_model* m, const double* v);
+int o_get_velocity(const o_model* m, double* v);
+void o_get_body(const o_model* m, double* pose, double* v, double* w, double* theta);
 /* linear solve K x = b on the free components (dense LU when small, else PCG/BiCGStab) */
 int o_solve(o_model* m, const double* Kvals, const double* b, double* x, double tol, int maxit,
             int* its);

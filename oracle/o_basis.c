@@ -188,6 +188,7 @@ int o_split_points(o_model* m) {
       m->mass = (double*)realloc(m->mass, sizeof(double) * (size_t)cap);
       m->E = (double*)realloc(m->E, sizeof(double) * (size_t)cap);
       m->ys = (double*)realloc(m->ys, sizeof(double) * (size_t)cap);
+      m->v = (double*)realloc(m->v, sizeof(double) * 3 * (size_t)cap);
       m->cap = cap;
     }
     int next = np;
@@ -214,6 +215,7 @@ int o_split_points(o_model* m) {
           m->mass[q] = m->mass[p] / 8.0;
           m->E[q] = m->E[p];
           m->ys[q] = m->ys[p];
+          for (int d = 0; d < 3; ++d) m->v[3 * q + d] = m->v[3 * p + d];
         }
       }
       /* child 0 keeps the parent slot */

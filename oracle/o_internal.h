@@ -32,6 +32,8 @@ struct o_model {
   /* points */
   int np, cap;
   double *x, *lp, *l0, *F, *be, *V0, *mass, *E, *ys;
+  double *v;         /* velocities (dynamic steps), 3 per point        */
+  double body_theta[3];
   /* mesh */
   o_tree t;
   o_nodes nd;

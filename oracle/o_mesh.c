@@ -376,6 +376,16 @@ static int body_box_intersect(const o_params* p, const double* lo, const double*
   if (p->body_kind == 1) {
     return hi[2] >= p->body_z && dist_xy_rect(p, lo, hi) <= p->body_r;
   }
+  if (p->body_kind == 4) {
+    /* the closed box meets the ball when its nearest point to the centre does */
+    const double c[3] = {p->body_cx, p->body_cy, p->body_z};
+    double s = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double e = fmax(fmax(lo[d] - c[d], 0.0), c[d] - hi[d]);
+      s += e * e;
+    }
+    return sqrt(s) <= p->body_r;
+  }
   if (p->body_kind == 2) {
     if (hi[2] < p->body_z) return 0;
     double rmax = fmin((hi[2] - p->body_z) * tan(p->body_alpha), p->body_r);
@@ -396,6 +406,10 @@ static double seg_dist(double px, double pz, double ax, double az, double bx, do
 /* Step 2 of Sec. 5: Euclidean distance from a node to the solid (0 inside) */
 static double body_dist(const o_params* p, const double* x) {
   if (p->body_kind == 3) return fmax(tri_sdf(p, x, NULL, NULL), 0.0);
+  if (p->body_kind == 4) {
+    double dx = x[0] - p->body_cx, dy = x[1] - p->body_cy, dz = x[2] - p->body_z;
+    return fmax(sqrt(dx * dx + dy * dy + dz * dz) - p->body_r, 0.0);
+  }
   double rx = x[0] - p->body_cx, ry = x[1] - p->body_cy;
   double rho = sqrt(rx * rx + ry * ry), z = x[2];
   if (p->body_kind == 1) {
@@ -426,6 +440,20 @@ int o_body_sdf(const o_params* p, const double* x, double* phi, double* n, doubl
     for (int i = 0; i < 3; ++i) n[i] = 0.0;
     for (int i = 0; i < 9; ++i) H[i] = 0.0;
     return 0;
+  }
+  if (p->body_kind == 4) {
+    /* sphere: phi = |x - c| - r, n = (x - c) / |x - c|, H = (I - n n^T) / |x - c| */
+    double d[3] = {x[0] - p->body_cx, x[1] - p->body_cy, x[2] - p->body_z};
+    double rho = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int i = 0; i < 9; ++i) H[i] = 0.0;
+    n[0] = n[1] = n[2] = 0.0;
+    *phi = rho - p->body_r;
+    if (!(*phi < 0.0)) return 0;
+    if (rho < 1e-12 * p->L) return 1; /* at the centre every direction is nearest (reading: n = 0) */
+    for (int i = 0; i < 3; ++i) n[i] = d[i] / rho;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) H[3 * i + j] = ((i == j ? 1.0 : 0.0) - n[i] * n[j]) / rho;
+    return 1;
   }
   double rx = x[0] - p->body_cx, ry = x[1] - p->body_cy;
   double rho = sqrt(rx * rx + ry * ry), z = x[2];

@@ -229,6 +229,24 @@ def workload(name, **over):
                  dx_region=2.0 / 128, nsteps=50,
                  points=dict(lo=(0, 0, 0), hi=(1, 1, 0.875), spacing=1.0 / 128, rho=1000.0,
                              E=1e7, ys=1e5, jitter=1.0 / 512, seed=0))
+    elif name == "rolling_sphere":
+        # the rigid sphere rolling down a 45-degree slope of Sec. 6.3, shortened:
+        # sphere of diameter 2 m, mass 1e4 kg, rotational inertia 4000 kg m2
+        # (the analytic sphere), on a stiff elastic slab (E 1e9 Pa, nu 0;
+        # density 2000 kg/m3, which the paper does not state) 4 x 1 x 1 m in
+        # a 4 m cube, 0.5 m cells refined to 0.125 m within 0.25 m of the
+        # sphere; the slope is the slab's top face under the tilted gravity
+        # 9.81 (1/sqrt 2, 0, -1/sqrt 2); the sphere starts at rest touching the
+        # slab; Newmark time steps of 0.01 s; the sphere is free to translate
+        # in x and z and to rotate about y (the motion stays in that plane by
+        # symmetry); rollers on the slab's sides, its base fixed
+        gs = 9.81 / math.sqrt(2.0)
+        c.update(L=4.0, depth_min=3, depth_max=5, bc=_block_rollers(4.0, 1.0), model=0, nu=0.0,
+                 g=(gs, 0.0, -gs), dt=0.01, nsteps=40, mu=1.0, dx_region=0.25,
+                 body=dict(kind=4, cx=1.0, cy=0.5, z0=2.0, r=1.0, dz=0.0, step_d=(0.0, 0.0, 0.0),
+                           free=1 | 4 | 16, mass=1e4, inertia=4000.0),
+                 points=dict(lo=(0, 0, 0), hi=(4, 1, 1), spacing=0.25, rho=2000.0,
+                             E=1e9, ys=0.0))
     elif name == "indent_small":
         # the indentation recipe one level coarser (depth 5 -> 6): stiffness larger
         # than L2 but a few GB on the device, for detailed profiles
