@@ -59,6 +59,7 @@ def args():
     ap.add_argument("--cone-warmup", type=int, default=3)
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-dynamics", action="store_true")
     ap.add_argument("--method", type=int, default=SOLVER,
                     help="Krylov method of mpm_solve_params (1 block-Jacobi PCG, 3 multigrid PCG)")
     ap.add_argument("--inner-tol", type=float, default=1e-4,
@@ -403,6 +404,54 @@ def adjoint_leg(dev, method):
             "forward_krylov_its": int(sum(s["lin_its"] for s in st_plain))}
 
 
+def dynamics_leg(dev, nwarm=3, nsteps=12):
+    """Newmark time steps with a free rigid body (Sec. 2.4, 2.3): the rolling
+    sphere of Sec. 6.3 (mu = 1, the sticking regime), FP64 and mixed, timed
+    over `nsteps` time steps after `nwarm`, and the distance travelled against
+    the paper's closed form 5 g t^2 sin(theta) / 14."""
+    import torch
+
+    from paper_2606_09275_gb300 import inputs, mpm
+    cfg = inputs.workload("rolling_sphere", mu=1.0)
+    out = {"workload": "rolling_sphere: rigid sphere (d 2 m, 1e4 kg, J 4000 kg m2) rolling on a "
+                       "stiff slab under gravity tilted 45 degrees, mu = 1 (sticking), Newmark "
+                       "gamma 1 beta 1/2, dt %.3g s, the sphere free in x, z and about y "
+                       "(Schur elimination: 1 + 3 solves per Newton iteration)" % cfg["dt"],
+           "timed_steps": "time steps %d-%d after %d warm-up steps" % (nwarm + 1, nwarm + nsteps, nwarm)}
+    for prec, name in ((mpm.FP64, "fp64"), (mpm.MIXED, "mixed")):
+        pts = inputs.make_points(cfg)
+        ctx = mpm.Context()
+        P = mpm.Points(pts, capacity=64 * len(pts["x"]), velocity=True)
+        state = mpm.body_start(cfg)
+        lin_tol = cfg["lin_tol"]
+        run = lambda: mpm.step(ctx, cfg, P, load=1.0, tol=cfg["newton_tol"], maxit=40,
+                               lin_tol=lin_tol, lin_maxit=cfg["lin_maxit"], precision=prec,
+                               inner_tol=1e-4, dt=cfg["dt"], body_state=state)
+        for _ in range(nwarm):
+            run()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sts = [run() for _ in range(nsteps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        its = sum(st["newton_its"] for st in sts)
+        t = (nwarm + nsteps) * cfg["dt"]
+        d = float(state["pose"][0] - cfg["body"]["cx"])
+        ana = 5.0 * 9.81 * t * t * math.sin(math.pi / 4) / 14.0
+        out[name] = {"time_steps_per_s": round(nsteps / (ms * 1e-3), 3),
+                     "newton_its_per_s": round(its / (ms * 1e-3), 3), "ms_per_step": round(ms / nsteps, 3),
+                     "newton_its": its, "krylov_its": int(sum(st["lin_its"] for st in sts)),
+                     "points": sts[-1]["npts"], "dof": 3 * sts[-1]["ndof"],
+                     "distance_m": round(d, 6), "closed_form_m": round(ana, 6),
+                     "distance_rel_err": round(abs(d - ana) / ana, 5),
+                     "rolling_theta_r_over_distance": round(float(state["theta"][1]) * cfg["body"]["r"] / d, 5)}
+        ctx.close()
+    return out
+
+
 def compare_arms(mixed, fp64):
     """Step-by-step comparison of the mixed and FP64 runs from the same
     initial state (warm-up steps included): discrete events (points after
@@ -636,6 +685,8 @@ def gpu_main(a):
     if not a.no_adjoint:
         # the adjoint workload is small (about a thousand dofs): block-Jacobi PCG
         line["adjoint"] = adjoint_leg(dev, 1)
+    if not a.no_dynamics:
+        line["rolling_sphere"] = dynamics_leg(dev)
     if not a.no_cpu:
         cb = cpu_baseline(a.workload, 1, a.cpu_procs)
         line["cpu_baseline"] = cb

@@ -78,7 +78,20 @@ typedef struct {
  * angle-weighted pseudo-normal; Step 1 of Sec. 5 marks a leaf when the ball
  * around it meets the body.  step_d is the body's translation over the
  * current load step: the Coulomb friction of Sec. 2.3 measures the slip of
- * each contact node against it (unused when mu = 0). */
+ * each contact node against it (unused when mu = 0).  Kind 4 is a sphere of
+ * radius r centred at (cx, cy, z).
+ *
+ * A free body (Sec. 2.3 and 2.4: the contact forces "influence any
+ * unconstrained degrees of freedom of the rigid body"), for time steps
+ * (mpm_step_params.dt > 0) only: `free` lists the body's unknowns, bits 0-2
+ * translation along x, y, z and bits 3-5 rotation about x, y, z (rotation
+ * for the sphere only); the other components are prescribed (translation
+ * step_d over the step, no rotation).  With free components (cx, cy, z) is
+ * the pose at the START of the step, `mass` and the isotropic rotational
+ * inertia `inertia` enter the body's Newmark equations, and v, w are its
+ * velocity and angular velocity at the step start; mpm_step returns the
+ * step's increment and the new velocities in mpm_step_stats, and the caller
+ * moves the pose by the increment. */
 typedef struct {
   int kind;
   double cx, cy, z, r, alpha;
@@ -86,6 +99,9 @@ typedef struct {
   int ntri, nvert;
   const double* tri_v;
   const int* tri_t;
+  int free;
+  double mass, inertia;
+  double v[3], w[3];
 } mpm_rigid;
 
 /* Adaptivity of Sec. 5: refine leaves meeting the body or with a node within
@@ -114,10 +130,14 @@ typedef struct {
 } mpm_material;
 
 /* Caller-owned device point arrays (layout above).  mpm_octree_build may grow
- * `count` up to `capacity` when it splits GIMPs (Sec. 5). */
+ * `count` up to `capacity` when it splits GIMPs (Sec. 5).  v[3P]: point
+ * velocities, needed by time steps (Sec. 2.4) and updated by them; may be
+ * NULL for quasi-static load steps.  Split children inherit their parent's
+ * velocity. */
 typedef struct {
   int count, capacity;
   double *x, *lp, *l0, *F, *be, *V0, *mass, *E, *ys;
+  double* v;
 } mpm_points;
 
 typedef struct {
@@ -154,6 +174,12 @@ typedef struct {
                       increment, 3*ndof doubles in the step's dof numbering, so
                       that mpm_adjoint need not solve the step again           */
   long long du_capacity; /* doubles du_out holds (MPM_ERR_CAPACITY if short) */
+  double dt;       /* > 0: a Newmark time step of this length (Sec. 2.4, gamma = 1,
+                      beta = 1/2: each point's acceleration at the step end is
+                      2 (du_p - dt v_p) / dt^2, du_p = sum_v S_vp du_v, and its
+                      velocity becomes v_p + dt a_p; the inertia term of Eq.
+                      (MPMweak) joins the residual and the consistent mass
+                      times 2 / dt^2 the tangent); 0: a quasi-static load step */
 } mpm_step_params;
 
 typedef struct {
@@ -171,6 +197,11 @@ typedef struct {
   long long nsrc, nslot;
   int mg_rows1, mg_stencil1;
   long long npair;
+  /* a free body's converged increment over the step (translation, rotation;
+   * prescribed components at their values) and its velocity and angular
+   * velocity at the step end */
+  double body_q[6];
+  double body_v[3], body_w[3];
 } mpm_step_stats;
 
 typedef struct mpm_ctx mpm_ctx;
@@ -239,6 +270,24 @@ int mpm_assemble(mpm_ctx* ctx, const mpm_mesh* mesh, const mpm_material* mat,
                  const mpm_rigid* body, const double* du, double load, int precision, double* R,
                  void* K_values, double* reaction, double* fint_norms);
 
+/* Eq. (MPMweak) with its inertia term (Sec. 2.4) and the rigid body's
+ * equations of a time step: mpm_assemble's R and K_values at the nodal
+ * increment du for a Newmark step of length dt > 0 (the mesh must have been
+ * built from points with velocities), with the body's increment q (host [6]:
+ * translation, rotation over the step; prescribed components at their
+ * values) and, for a free body, Rb (host [6]) its residual m a - m g +
+ * sum f, J alpha + sum d x f (f the contact force on the material at a node,
+ * d the node's offset from the body centre), Kbb (host [36], row-major) its
+ * derivative in q, Kgb (device [6][3*ndof]) the derivative of R in each
+ * component of q and Kbg (device [6][3*ndof]) the derivative of each
+ * component of Rb in du.  Any of Rb, Kbb, Kgb, Kbg, K_values may be NULL.
+ * fint_norms (host [3], may be NULL): ||f_int||, ||f_ext + f_c||,
+ * ||f_inert||.  Synchronises the stream. */
+int mpm_assemble_body(mpm_ctx* ctx, const mpm_mesh* mesh, const mpm_material* mat,
+                      const mpm_rigid* body, const double* du, const double* q, double dt,
+                      double load, int precision, double* R, void* K_values, double* reaction,
+                      double* fint_norms, double* Rb, double* Kbb, double* Kgb, double* Kbg);
+
 /* Copies stiffness values (as written by mpm_assemble with `precision`) to host
  * memory as [nnzb][3][3] row-major blocks in the CSR order of the pattern;
  * blocks_host must hold 9*nnzb doubles.  Synchronises the stream. */
@@ -253,9 +302,17 @@ int mpm_blocks_export(mpm_ctx* ctx, const mpm_mesh* mesh, const void* K_values, 
 int mpm_solve(mpm_ctx* ctx, const mpm_mesh* mesh, const mpm_material* mat, const void* K_values,
               const double* rhs, double* x, const mpm_solve_params* prm, mpm_solve_stats* stats);
 
-/* One quasi-static load step (Sec. 2.4 Newton-Raphson with line search, Sec. 5
+/* One load step (Sec. 2.4 Newton-Raphson with line search, Sec. 5
  * re-adaptation): rebuild the mesh for the body pose, iterate assemble/solve
- * until converged, then update the points (positions, F, b_e, domain sizes).
+ * until converged, then update the points (positions, F, b_e, domain sizes,
+ * and for a time step their velocities).  A quasi-static load step when
+ * prm->dt = 0, a Newmark time step when dt > 0 (then pts->v is required).
+ * With a free body (mpm_rigid.free) each Newton iteration solves the linear
+ * system of the material and body increments, the body's part by block
+ * elimination: w = K^-1 (-R), Z = K^-1 dR/dq (one solve per free component),
+ * (dRb/dq - dRb/du Z) dq = -Rb - dRb/du w, du = w - Z dq; the convergence test
+ * takes the free components of the body's residual Rb into ||R_free|| and
+ * the body's weight and the material's inertia force into the reference.
  * stats (host) receives the history.  The mesh is kept in the context. */
 int mpm_step(mpm_ctx* ctx, const mpm_domain* dom, const mpm_rigid* body, const mpm_adapt* ad,
              const mpm_material* mat, mpm_points* pts, const mpm_step_params* prm,

@@ -201,7 +201,7 @@ class Model:
         if st:
             raise RuntimeError("oracle assemble status %d" % st)
         return dict(R=R, K=K[: c["nnzb"]] if tangent else None, fint=fi[:n3], fextc_norm=fi[n3],
-                    reaction=reac, Rb=Rb, Kbb=Kbb, Kgb=Kgb, Kbg=Kbg)
+                    finert_norm=fi[n3 + 1], reaction=reac, Rb=Rb, Kbb=Kbb, Kgb=Kgb, Kbg=Kbg)
 
     def counts(self):
         c = Counts()

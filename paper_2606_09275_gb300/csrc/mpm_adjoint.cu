@@ -870,8 +870,12 @@ extern "C" int mpm_adjoint(mpm_ctx* c, const mpm_domain* dom, const mpm_rigid* b
     set_error(c, "adjoint: frictional contact (mu > 0) has a non-symmetric tangent; not supported");
     return MPM_ERR_ARG;
   }
-  if (body && body->kind == 3) {
-    set_error(c, "adjoint: the analytic bodies (kinds 1, 2) only");
+  if (body && (body->kind == 3 || body->kind == 4 || body->free)) {
+    set_error(c, "adjoint: the prescribed analytic bodies (kinds 1, 2) only");
+    return MPM_ERR_ARG;
+  }
+  if (prm->dt != 0.0) {
+    set_error(c, "adjoint: quasi-static load steps only (dt = 0)");
     return MPM_ERR_ARG;
   }
   if (!(prm->tol > 0) || prm->maxit < 0 || prm->maxit > 63) {

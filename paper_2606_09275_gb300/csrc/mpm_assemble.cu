@@ -667,18 +667,41 @@ __device__ inline int find_slot(const int* __restrict__ rp, const int* __restric
   return -1;
 }
 
+// [a]x, the matrix of b -> a x b (row-major)
+__device__ inline void cross_mat(const double* a, double* C) {
+  C[0] = 0.0;
+  C[1] = -a[2];
+  C[2] = a[1];
+  C[3] = a[2];
+  C[4] = 0.0;
+  C[5] = -a[0];
+  C[6] = -a[1];
+  C[7] = a[0];
+  C[8] = 0.0;
+}
+
+__device__ inline void mul33(const double* A, const double* B, double* C) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+
 // one thread per candidate domain corner: the gap against the body at the moved
-// corner; in contact the force on the material f = -eps_N phi n and the
-// stiffness k_c = eps_N (n n^T + phi H) are stored for the row gather below
-// (zeros and on = 0 otherwise), and with `reac` the force on the body, -sum f,
-// is summed in a fixed order (every thread of the grid takes part)
+// corner; in contact the force on the material f (normal f_N n with
+// f_N = -eps_N phi, plus Coulomb friction) and k_c = -d f / d y are stored for
+// the row gather below (zeros and on = 0 otherwise), and with `reac` the
+// force on the body, -sum f, is summed in a fixed order (every thread of the
+// grid takes part).  The body sits at its given pose moved by bi.shift; the
+// friction measures the node's slip against the body's own displacement at
+// the node, qt + qr x d (d = y - X, X the body's reference point); with
+// `ct` the derivative of f in the body's rotation ([d]x through the slip) and
+// d are stored per corner for the body's equations.
 __global__ void k_contact_corner(int nc8, const int* __restrict__ cand, const int* __restrict__ cb_n,
                                  const int* __restrict__ cb_idx, const double* __restrict__ cb_phi,
                                  const double* __restrict__ cb_y0, const double* __restrict__ pE,
                                  const double* __restrict__ pV0, Body body, double L, double pf,
-                                 double pt, double mu,
+                                 double pt, double mu, BodyInc bi,
                                  const double* __restrict__ du, double* cf, double* ck, int* con,
-                                 double* reac, GridRed gr) {
+                                 double* ct, double* cdv, double* reac, GridRed gr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   double f[3] = {0.0, 0.0, 0.0};
   if (i < nc8) {
@@ -688,54 +711,256 @@ __global__ void k_contact_corner(int nc8, const int* __restrict__ cand, const in
     double y[3] = {cb_y0[3 * (size_t)i], cb_y0[3 * (size_t)i + 1], cb_y0[3 * (size_t)i + 2]};
     for (int e = 0; e < n; ++e)
       for (int d = 0; d < 3; ++d) y[d] += ph[e] * du[3 * (size_t)ids[e] + d];
-    double phi, nv[3], H[9];
-    bool on = body_sdf(body, L, y, &phi, nv, H) && phi < 0.0;
-    double kc[9];
-    for (int e = 0; e < 9; ++e) kc[e] = 0.0;
+    double phi, nv[3], H[9], yb[3], dv[3];
+    for (int d = 0; d < 3; ++d) yb[d] = y[d] - bi.shift[d];
+    bool on = body_sdf(body, L, yb, &phi, nv, H) && phi < 0.0;
+    dv[0] = y[0] - (body.b.cx + bi.shift[0]);
+    dv[1] = y[1] - (body.b.cy + bi.shift[1]);
+    dv[2] = y[2] - (body.b.z + bi.shift[2]);
+    double Fy[9], Ft[9];
+    for (int e = 0; e < 9; ++e) Fy[e] = Ft[e] = 0.0;
     if (on) {
       double A0 = pow(pV0[w], 2.0 / 3.0);
       double epsN = pf * pE[w] * A0, fN = -epsN * phi;
       for (int d = 0; d < 3; ++d) f[d] = fN * nv[d];
       for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) kc[3 * a + b] = epsN * (nv[a] * nv[b] + phi * H[3 * a + b]);
+        for (int b = 0; b < 3; ++b) Fy[3 * a + b] = -epsN * (nv[a] * nv[b] + phi * H[3 * a + b]);
       if (mu > 0.0) {
-        // Coulomb friction: the node's slip against the body over the load
-        // step, g = (y - y0) - d_body, on the tangent plane; trial force
-        // t = -eps_T (I - n n^T) g, stick while |t| <= mu f_N, else slip with
-        // mu f_N t/|t|; kc gets -d(force)/dy (not symmetric when slipping)
+        // Coulomb friction: the slip g = (y - y0) - (qt + qr x d) on the
+        // tangent plane; trial force t = -eps_T (I - n n^T) g, stick while
+        // |t| <= mu f_N, else slip with mu f_N t / |t|; Jd, Jg its
+        // derivatives in d (through n, H, f_N) and in g
         double epsT = pt * pE[w] * A0;
-        double g[3], t[3], Hg[3], D[9];
-        for (int d = 0; d < 3; ++d) g[d] = (y[d] - cb_y0[3 * (size_t)i + d]) - body.b.step_d[d];
+        double g[3], t[3], Hg[3], Td[9], Tg[9], Jd[9], Jg[9];
+        for (int d = 0; d < 3; ++d) {
+          double rot = bi.qr[(d + 1) % 3] * dv[(d + 2) % 3] - bi.qr[(d + 2) % 3] * dv[(d + 1) % 3];
+          g[d] = (y[d] - cb_y0[3 * (size_t)i + d]) - (bi.qt[d] + rot);
+        }
         double ng = nv[0] * g[0] + nv[1] * g[1] + nv[2] * g[2];
         for (int a = 0; a < 3; ++a) Hg[a] = H[3 * a] * g[0] + H[3 * a + 1] * g[1] + H[3 * a + 2] * g[2];
         for (int d = 0; d < 3; ++d) t[d] = -epsT * (g[d] - nv[d] * ng);
         for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b)
-            D[3 * a + b] = -epsT * ((a == b ? 1.0 : 0.0) - nv[a] * nv[b] - ng * H[3 * a + b] - nv[a] * Hg[b]);
+          for (int b = 0; b < 3; ++b) {
+            Td[3 * a + b] = epsT * (ng * H[3 * a + b] + nv[a] * Hg[b]);
+            Tg[3 * a + b] = -epsT * ((a == b ? 1.0 : 0.0) - nv[a] * nv[b]);
+          }
         double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
         if (tn <= mu * fN) {
           for (int d = 0; d < 3; ++d) f[d] += t[d];
-          for (int q = 0; q < 9; ++q) kc[q] -= D[q];
+          for (int e = 0; e < 9; ++e) {
+            Jd[e] = Td[e];
+            Jg[e] = Tg[e];
+          }
         } else {
           double u[3] = {t[0] / tn, t[1] / tn, t[2] / tn};
           for (int d = 0; d < 3; ++d) f[d] += mu * fN * u[d];
           for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) {
-              double sm = 0.0;
-              for (int c = 0; c < 3; ++c) sm += ((a == c ? 1.0 : 0.0) - u[a] * u[c]) * D[3 * c + b];
-              kc[3 * a + b] -= mu * u[a] * (-epsN * nv[b]) + mu * fN * sm / tn;
+              double sd = 0.0, sg = 0.0;
+              for (int c = 0; c < 3; ++c) {
+                double P = (a == c ? 1.0 : 0.0) - u[a] * u[c];
+                sd += P * Td[3 * c + b];
+                sg += P * Tg[3 * c + b];
+              }
+              Jd[3 * a + b] = mu * u[a] * (-epsN * nv[b]) + mu * fN * sd / tn;
+              Jg[3 * a + b] = mu * fN * sg / tn;
             }
         }
+        // d f / d y = N + Jd + Jg (I - [qr]x); d f / d qr = Jg [d]x
+        double Qr[9], IQ[9], T[9], Dx[9];
+        cross_mat(bi.qr, Qr);
+        for (int e = 0; e < 9; ++e) IQ[e] = (e % 4 == 0 ? 1.0 : 0.0) - Qr[e];
+        mul33(Jg, IQ, T);
+        for (int e = 0; e < 9; ++e) Fy[e] += Jd[e] + T[e];
+        cross_mat(dv, Dx);
+        mul33(Jg, Dx, Ft);
       }
     }
     for (int d = 0; d < 3; ++d) cf[3 * (size_t)i + d] = f[d];
-    for (int e = 0; e < 9; ++e) ck[9 * (size_t)i + e] = kc[e];
+    for (int e = 0; e < 9; ++e) ck[9 * (size_t)i + e] = -Fy[e];
     con[i] = on ? 1 : 0;
+    if (ct) {
+      for (int e = 0; e < 9; ++e) ct[9 * (size_t)i + e] = Ft[e];
+      for (int d = 0; d < 3; ++d) cdv[3 * (size_t)i + d] = dv[d];
+    }
   }
   if (reac) {
     double v[3] = {-f[0], -f[1], -f[2]};
     double* o[3] = {reac, reac + 1, reac + 2};
     grid_sum<3>(v, o, gr);
+  }
+}
+
+// The rigid body's sums over the contact corners, in a fixed order (one
+// block; each thread takes the corners i = t, t + blockDim, ..., then the
+// block's fixed tree): out[0..5] the residual terms f and d x f, out[6..41]
+// their derivative in the body's increment q (row-major 6 x 6):
+// [d f / d qt, d f / d qr; [f]x + [d]x d f / d qt, [d]x d f / d qr] with
+// d f / d qt = -d f / d y
+__global__ void k_body_sums(int nc8, const double* __restrict__ cf, const double* __restrict__ ck,
+                            const double* __restrict__ ct, const double* __restrict__ cdv,
+                            const int* __restrict__ con, double* out) {
+  __shared__ double sh[32];
+  double acc[42];
+  for (int e = 0; e < 42; ++e) acc[e] = 0.0;
+  for (int i = threadIdx.x; i < nc8; i += blockDim.x) {
+    if (!con[i]) continue;
+    const double* f = cf + 3 * (size_t)i;
+    const double* d = cdv + 3 * (size_t)i;
+    const double* Ft = ct + 9 * (size_t)i;
+    double FX[9], Dx[9], Fx[9], DF[9], DT[9];
+    for (int e = 0; e < 9; ++e) FX[e] = ck[9 * (size_t)i + e];  // -d f / d y
+    cross_mat(d, Dx);
+    cross_mat(f, Fx);
+    mul33(Dx, FX, DF);
+    mul33(Dx, Ft, DT);
+    for (int a = 0; a < 3; ++a) {
+      acc[a] += f[a];
+      acc[3 + a] += d[(a + 1) % 3] * f[(a + 2) % 3] - d[(a + 2) % 3] * f[(a + 1) % 3];
+      for (int b = 0; b < 3; ++b) {
+        acc[6 + 6 * a + b] += FX[3 * a + b];
+        acc[6 + 6 * a + 3 + b] += Ft[3 * a + b];
+        acc[6 + 6 * (3 + a) + b] += Fx[3 * a + b] + DF[3 * a + b];
+        acc[6 + 6 * (3 + a) + 3 + b] += DT[3 * a + b];
+      }
+    }
+  }
+  for (int e = 0; e < 42; ++e) {
+    double v = block_sum(acc[e], sh);
+    if (threadIdx.x == 0) out[e] = v;
+  }
+}
+
+// the body's coupling columns and rows at the rows of the contact list (one
+// warp per row, a lane per output value, the row's corner entries in list
+// order): Kgb[j][3r + a] = d R_{r,a} / d q_j = sum phi (d f / d y)[a][j] for
+// the translation (j < 3) and -sum phi (d f / d qr)[a][j - 3] for the
+// rotation; Kbg[j][3r + b] = d Rb_j / d du_{r,b} = sum phi (d f / d y)[j][b]
+// (j < 3) and sum phi ([d]x d f / d y - [f]x)[j - 3][b]
+__global__ void k_body_rows(int nrow, const int* __restrict__ crow, const int* __restrict__ cptr,
+                            const int* __restrict__ cent, const double* __restrict__ cb_phi,
+                            const double* __restrict__ cf, const double* __restrict__ ck,
+                            const double* __restrict__ ct, const double* __restrict__ cdv,
+                            const int* __restrict__ con, long long n3, double* Kgb, double* Kbg) {
+  int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (t >= nrow) return;
+  int r = crow[t], e0 = cptr[t], e1 = cptr[t + 1];
+  for (int o = lane; o < 36; o += 32) {
+    // o < 18: Kgb, component a = o / 6 of row r, body column j = o % 6;
+    // o >= 18: Kbg, body row j = (o - 18) / 3, component b = (o - 18) % 3
+    bool gb = o < 18;
+    int a = gb ? o / 6 : (o - 18) % 3, j = gb ? o % 6 : (o - 18) / 3;
+    double s = 0.0;
+    for (int e = e0; e < e1; ++e) {
+      int pk = cent[e], i = pk >> 5;
+      if (!con[i]) continue;
+      double ph = cb_phi[(size_t)i * MAXCB + (pk & 31)];
+      const double* Fm = ck + 9 * (size_t)i;  // -d f / d y
+      double v;
+      if (gb) {
+        v = j < 3 ? -Fm[3 * a + j] : -ct[9 * (size_t)i + 3 * a + (j - 3)];
+      } else if (j < 3) {
+        v = -Fm[3 * j + a];
+      } else {
+        const double* d = cdv + 3 * (size_t)i;
+        const double* f = cf + 3 * (size_t)i;
+        int jr = j - 3, j1 = (jr + 1) % 3, j2 = (jr + 2) % 3;
+        // ([d]x (d f / d y))[jr][a] - ([f]x)[jr][a]
+        double dF = -(d[j1] * Fm[3 * j2 + a] - d[j2] * Fm[3 * j1 + a]);
+        double fx = (a == j2 ? f[j1] : 0.0) - (a == j1 ? f[j2] : 0.0);
+        v = dF - fx;
+      }
+      s += ph * v;
+    }
+    if (gb)
+      Kgb[(size_t)j * n3 + 3 * (size_t)r + a] = s;
+    else
+      Kbg[(size_t)j * n3 + 3 * (size_t)r + a] = s;
+  }
+}
+
+// Newmark inertia of each point (time steps): m_p a_p with
+// a_p = (2 / dt^2) (sum_v S_vp du_v - dt v_p)
+__global__ void k_point_inertia(int P, const int* __restrict__ nsup, const int* __restrict__ sidx,
+                                const double* __restrict__ S, const double* __restrict__ du,
+                                const double* __restrict__ v, const double* __restrict__ mass,
+                                double dt, double* ma) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= P) return;
+  double u[3] = {0.0, 0.0, 0.0};
+  int n = nsup[w];
+  for (int k = 0; k < n; ++k) {
+    size_t o = (size_t)w * MAXS + k;
+    int j = sidx[o];
+    for (int d = 0; d < 3; ++d) u[d] += S[o] * du[3 * (size_t)j + d];
+  }
+  double c2 = 2.0 / (dt * dt);
+  for (int d = 0; d < 3; ++d) ma[3 * (size_t)w + d] = mass[w] * (c2 * (u[d] - dt * v[3 * (size_t)w + d]));
+}
+
+// the inertia term of Eq. (MPMweak), sum_p S_vp m_p a_p, gathered per row over
+// the row's point sources (warp per row): added to R and stored in finert
+__global__ void k_inertia_rows(int nd, int P, const long long* __restrict__ sptr,
+                               const uint64_t* __restrict__ skeys, const double* __restrict__ S,
+                               const double* __restrict__ ma, double* R, double* finert) {
+  int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= nd) return;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (long long q = sptr[r] + lane; q < sptr[r + 1]; q += 32) {
+    uint32_t sid = (uint32_t)skeys[q];
+    int w = (int)(sid >> 6), k = (int)(sid & 63);
+    if (w >= P) continue;  // ghost-face source
+    double sv = S[(size_t)w * MAXS + k];
+    a0 += sv * ma[3 * (size_t)w];
+    a1 += sv * ma[3 * (size_t)w + 1];
+    a2 += sv * ma[3 * (size_t)w + 2];
+  }
+  a0 = warp_sum(a0);
+  a1 = warp_sum(a1);
+  a2 = warp_sum(a2);
+  if (lane < 3) {
+    double a = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+    R[3 * (size_t)r + lane] += a;
+    finert[3 * (size_t)r + lane] = a;
+  }
+}
+
+// the consistent mass of a time step, (2 / dt^2) m_p S_vp S_wp I, added to the
+// tangent's diagonal entries: one warp per row r, the row's point sources in
+// key order, the lanes over the source point's support (distinct columns),
+// the Dirichlet components skipped
+template <class T>
+__global__ void k_mass_rows(int nd, int P, const long long* __restrict__ sptr,
+                            const uint64_t* __restrict__ skeys, const int* __restrict__ nsup,
+                            const int* __restrict__ sidx, const double* __restrict__ S,
+                            const double* __restrict__ mass, double c2, const int* __restrict__ rp,
+                            const int* __restrict__ col, Sliced SL, const int* __restrict__ mask, T* K) {
+  int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= nd) return;
+  int s0r = rp[r], ma = mask[r];
+  int slc = r >> 5, W = SL.w[slc];
+  long long b0 = SL.base[slc];
+  for (long long q = sptr[r]; q < sptr[r + 1]; ++q) {
+    uint32_t sid = (uint32_t)skeys[q];
+    int w = (int)(sid >> 6), k = (int)(sid & 63);
+    if (w >= P) continue;
+    double sk = c2 * mass[w] * S[(size_t)w * MAXS + k];
+    int n = nsup[w];
+    for (int l = lane; l < n; l += 32) {
+      size_t o = (size_t)w * MAXS + l;
+      int cb = sidx[o];
+      int sl = find_slot(rp, col, r, cb);
+      if (sl < 0) continue;
+      long long slot = sliced_slot(b0, r, sl - s0r);
+      int mb = mask[cb];
+      double v = sk * S[o];
+      for (int a = 0; a < 3; ++a) {
+        if (((ma >> a) & 1) || ((mb >> a) & 1)) continue;
+        T* kv = K + sliced_entry(b0, W, slot, 4 * a);
+        *kv += (T)v;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -805,13 +1030,14 @@ __global__ void k_contact_rows(int nrow, const int* __restrict__ crow, const int
 
 // ------------------------------------------------------------------ norms
 
-// slots: 0 ||R_free||^2, 1 ||f_int||^2, 2 ||load f_ext + f_c||^2
-// (fixed-order grid sums: the norms, and so Newton's convergence test and
-// line search, are the same on every run)
+// slots: 0 ||R_free||^2, 1 ||f_int||^2, 2 ||load f_ext + f_c||^2, 3
+// ||f_inert||^2 (time steps) (fixed-order grid sums: the norms, and so
+// Newton's convergence test and line search, are the same on every run)
 __global__ void k_norms(int n3, const double* __restrict__ R, const double* __restrict__ fint,
                         const double* __restrict__ fext, const double* __restrict__ fc, double load,
-                        const int* __restrict__ mask, double* out, GridRed gr) {
-  double a = 0.0, b = 0.0, c = 0.0;
+                        const double* __restrict__ finert, const int* __restrict__ mask, double* out,
+                        GridRed gr) {
+  double a = 0.0, b = 0.0, c = 0.0, e2 = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
     if (!((mask[i / 3] >> (i % 3)) & 1)) a += R[i] * R[i];
     if (fint) b += fint[i] * fint[i];
@@ -819,10 +1045,11 @@ __global__ void k_norms(int n3, const double* __restrict__ R, const double* __re
       double e = load * fext[i] + (fc ? fc[i] : 0.0);
       c += e * e;
     }
+    if (finert) e2 += finert[i] * finert[i];
   }
-  double v[3] = {a, b, c};
-  double* o[3] = {out, out + 1, out + 2};
-  grid_sum<3>(v, o, gr);
+  double v[4] = {a, b, c, e2};
+  double* o[4] = {out, out + 1, out + 2, out + 3};
+  grid_sum<4>(v, o, gr);
 }
 
 }  // namespace
@@ -830,9 +1057,9 @@ __global__ void k_norms(int n3, const double* __restrict__ R, const double* __re
 
 double norm_free(mpm_ctx* c, const mpm_mesh* m, const double* R) {
   double* slot = c->d_red + 16;
-  MPM_CUDA(cudaMemsetAsync(slot, 0, 3 * sizeof(double), c->stream));
+  MPM_CUDA(cudaMemsetAsync(slot, 0, 4 * sizeof(double), c->stream));
   MPM_LAUNCH(k_norms<<<4 * 152, 256, 0, c->stream>>>(3 * m->ndof, R, nullptr, nullptr, nullptr, 0.0,
-                                          ptr<int>(m->dof_mask), slot, grid_red(c, 3, 4 * 152)));
+                                          nullptr, ptr<int>(m->dof_mask), slot, grid_red(c, 4, 4 * 152)));
   MPM_CUDA(cudaMemcpyAsync(c->h_red + 16, slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   MPM_CUDA(cudaStreamSynchronize(c->stream));
   return sqrt(c->h_red[16]);
@@ -841,27 +1068,44 @@ double norm_free(mpm_ctx* c, const mpm_mesh* m, const double* R) {
 namespace {
 
 // the penalty contact of one assembly: per-corner forces and stiffness (and
-// the reaction when `reac` is given), then the row gather
+// the reaction when `reac` is given), then the row gather; with a free body
+// (dyn->body) also the body's sums (bsum, device [42]: k_body_sums) and, with
+// the tangent, the coupling blocks
 template <class T, bool RES, bool TANGENT>
 void contact_terms(mpm_ctx* c, mpm_mesh* m, const mpm_material& mat, const mpm_rigid& body,
-                   const double* du, double* R, double* fc, double* reac, T* K) {
+                   const double* du, double* R, double* fc, double* reac, T* K, const Dyn* dyn,
+                   double* bsum) {
   cudaStream_t st = c->stream;
   int n8 = 8 * m->ncand;
   double* cf = grow<double>(c, m->cc_f, 3 * (size_t)n8);
   double* ck = grow<double>(c, m->cc_k, 9 * (size_t)n8);
   int* con = grow<int>(c, m->cc_on, n8);
+  bool couple = dyn && dyn->body;
+  double* ct = couple ? grow<double>(c, m->cc_t, 9 * (size_t)n8) : nullptr;
+  double* cdv = couple ? grow<double>(c, m->cc_d, 3 * (size_t)n8) : nullptr;
+  BodyInc bi{};
+  for (int d = 0; d < 3; ++d) {
+    bi.qt[d] = dyn ? dyn->q[d] : body.step_d[d];
+    bi.qr[d] = dyn ? dyn->q[3 + d] : 0.0;
+    bi.shift[d] = body.free ? bi.qt[d] : 0.0;
+  }
   MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact_corner<<<grid_for(n8, 128), 128, 0, st>>>(
       n8, ptr<int>(m->cand), ptr<int>(m->cb_n), ptr<int>(m->cb_idx), ptr<double>(m->cb_phi),
       ptr<double>(m->cb_y0), ptr<double>(m->pE), ptr<double>(m->pV0), body_view(m, body), m->g.L,
-      mat.pf, mat.pt,
-      mat.mu, du, cf, ck,
-      con, reac, grid_red(c, 3, grid_for(n8, 128))));
+      mat.pf, mat.pt, mat.mu, bi, du, cf, ck, con, ct, cdv, reac,
+      grid_red(c, 3, grid_for(n8, 128))));
+  if (couple && bsum)
+    MPM_LAUNCH_P(MPM_PROF_CONTACT, k_body_sums<<<1, 256, 0, st>>>(n8, cf, ck, ct, cdv, con, bsum));
   if (!m->nct) return;
   Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
   MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact_rows<T, RES, TANGENT><<<grid_for(m->nct, 4), 128, 0, st>>>(
       m->nct, ptr<int>(m->ct_row), ptr<int>(m->ct_ptr), ptr<int>(m->ct_ent), ptr<int>(m->cb_n),
       ptr<int>(m->cb_idx), ptr<double>(m->cb_phi), cf, ck, con, R, fc, ptr<int>(m->row_ptr),
       ptr<int>(m->col), S, ptr<int>(m->dof_mask), K));
+  if (TANGENT && couple && dyn->Kgb && dyn->Kbg)
+    MPM_LAUNCH_P(MPM_PROF_CONTACT, k_body_rows<<<grid_for(m->nct, 4), 128, 0, st>>>(
+        m->nct, ptr<int>(m->ct_row), ptr<int>(m->ct_ptr), ptr<int>(m->ct_ent),
+        ptr<double>(m->cb_phi), cf, ck, ct, cdv, con, 3LL * m->ndof, dyn->Kgb, dyn->Kbg));
 }
 
 }  // namespace
@@ -889,9 +1133,40 @@ void tangent_launch(mpm_ctx* c, mpm_mesh* m, bool upper, int lo, int hi, int las
 
 }  // namespace
 
+namespace {
+
+// the free body's equations on the host from the contact sums (bsum, device
+// [42]): Rb = m (2 / dt^2) (qt - dt v) - m load g + sum f,
+// J (2 / dt^2) (qr - dt w) + sum d x f, and (with the tangent) Kbb = the
+// sums' derivative plus the inertia's m (2 / dt^2) I, J (2 / dt^2) I
+void body_out(mpm_ctx* c, const mpm_material& mat, const mpm_rigid& body, double load, const Dyn* dyn,
+              const double* bsum, AsmOut* out, bool tangent) {
+  double h[42];
+  MPM_CUDA(cudaMemcpyAsync(h, bsum, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  MPM_CUDA(cudaStreamSynchronize(c->stream));
+  double dt = dyn->dt, c2 = dt > 0.0 ? 2.0 / (dt * dt) : 0.0;
+  for (int d = 0; d < 3; ++d) {
+    out->Rb[d] = h[d];
+    out->Rb[3 + d] = h[3 + d];
+    if (dt > 0.0) {
+      out->Rb[d] += body.mass * (c2 * (dyn->q[d] - dt * body.v[d]) - load * mat.g[d]);
+      out->Rb[3 + d] += body.inertia * c2 * (dyn->q[3 + d] - dt * body.w[d]);
+    }
+  }
+  if (!tangent) return;
+  for (int e = 0; e < 36; ++e) out->Kbb[e] = h[6 + e];
+  if (dt > 0.0)
+    for (int d = 0; d < 3; ++d) {
+      out->Kbb[7 * d] += body.mass * c2;
+      out->Kbb[7 * (3 + d)] += body.inertia * c2;
+    }
+}
+
+}  // namespace
+
 void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm_rigid& body,
               const double* du, double load, int precision, double* R, void* K, AsmOut* out,
-              bool want_norms, bool reuse) {
+              bool want_norms, bool reuse, const Dyn* dyn) {
   mpm_mesh* m = const_cast<mpm_mesh*>(mc);
   cudaStream_t st = c->stream;
   int P = m->np, nd = m->ndof;
@@ -925,6 +1200,16 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
   double* fint = grow<double>(c, c->v[0], 3 * (size_t)nd);
   double* fc = grow<double>(c, c->v[1], 3 * (size_t)nd);
   bool contact = m->ncand && mat.contact_on && body.kind != 0;
+  bool inertia = dyn && dyn->dt > 0.0;
+  if (inertia && !m->has_v) throw CudaError(MPM_ERR_ARG, "a time step needs point velocities");
+  double* finert = inertia ? grow<double>(c, c->v[2], 3 * (size_t)nd) : nullptr;
+  bool couple = dyn && dyn->body;
+  double* bsum = couple ? grow<double>(c, m->cc_b, 42) : nullptr;
+  if (couple) MPM_CUDA(cudaMemsetAsync(bsum, 0, 42 * sizeof(double), st));
+  if (couple && K && dyn->Kgb && dyn->Kbg) {
+    MPM_CUDA(cudaMemsetAsync(dyn->Kgb, 0, sizeof(double) * 18 * (size_t)nd, st));
+    MPM_CUDA(cudaMemsetAsync(dyn->Kbg, 0, sizeof(double) * 18 * (size_t)nd, st));
+  }
   // grid-sum partials for every reduction below, sized once; a clean ticket
   grid_red(c, 4, std::max(4096, grid_for(8LL * m->ncand, 128)));
   MPM_CUDA(cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), st));
@@ -956,6 +1241,13 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
     MPM_LAUNCH_P(MPM_PROF_RESIDUAL, k_residual_rows<<<grid_for(nd, 8), 256, 0, st>>>(
         nd, P, load, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), Mf, dS, rp, col,
         ptr<double>(m->kg), du, ptr<double>(m->fext), fint, R));
+    if (inertia) {
+      double* ma = grow<double>(c, m->pma, 3 * (size_t)P);
+      MPM_LAUNCH_P(MPM_PROF_RESIDUAL, k_point_inertia<<<grid_for(P, 128), 128, 0, st>>>(
+          P, nsup, sidx, ptr<double>(m->S), du, ptr<double>(m->pv), ptr<double>(m->pmass), dyn->dt, ma));
+      MPM_LAUNCH_P(MPM_PROF_RESIDUAL, k_inertia_rows<<<grid_for(nd, 8), 256, 0, st>>>(
+          nd, P, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), ptr<double>(m->S), ma, R, finert));
+    }
     if (K) {
       if (mixed)
         MPM_LAUNCH_P(MPM_PROF_FORCE, k_gx<float, float><<<grid_for(P, 8), 256, 0, st>>>(P, nsup, dS32, dFinv, V0, (float*)gx, (float*)V0t));
@@ -991,6 +1283,17 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
       else
         MPM_LAUNCH_P(MPM_PROF_TANGENT, k_tangent_mirror<double><<<grid_for(32LL * nd, 256), 256, 0, st>>>(nd, rp, col, S, (double*)K));
     }
+    if (inertia) {
+      double c2 = 2.0 / (dyn->dt * dyn->dt);
+      if (mixed)
+        MPM_LAUNCH_P(MPM_PROF_TANGENT, k_mass_rows<float><<<grid_for(nd, 4), 128, 0, st>>>(
+            nd, P, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx, ptr<double>(m->S),
+            ptr<double>(m->pmass), c2, rp, col, S, ptr<int>(m->dof_mask), (float*)K));
+      else
+        MPM_LAUNCH_P(MPM_PROF_TANGENT, k_mass_rows<double><<<grid_for(nd, 4), 128, 0, st>>>(
+            nd, P, ptr<long long>(m->src_ptr), ptr<uint64_t>(m->src_key), nsup, sidx, ptr<double>(m->S),
+            ptr<double>(m->pmass), c2, rp, col, S, ptr<int>(m->dof_mask), (double*)K));
+    }
     int npad = 32 * m->nslice;
     if (npad > nd) {
       if (mixed)
@@ -1004,32 +1307,35 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
     // contact stiffness only: its forces are already in R
     if (contact) {
       if (mixed)
-        contact_terms<float, false, true>(c, m, mat, body, du, R, fc, nullptr, (float*)K);
+        contact_terms<float, false, true>(c, m, mat, body, du, R, fc, nullptr, (float*)K, dyn, bsum);
       else
-        contact_terms<double, false, true>(c, m, mat, body, du, R, fc, nullptr, (double*)K);
+        contact_terms<double, false, true>(c, m, mat, body, du, R, fc, nullptr, (double*)K, dyn, bsum);
     }
+    if (couple) body_out(c, mat, body, load, dyn, bsum, out, true);
     return;
   }
   MPM_CUDA(cudaMemsetAsync(reac, 0, 3 * sizeof(double), st));
   if (contact) {
     if (!K)
-      contact_terms<double, true, false>(c, m, mat, body, du, R, fc, reac, (double*)nullptr);
+      contact_terms<double, true, false>(c, m, mat, body, du, R, fc, reac, (double*)nullptr, dyn, bsum);
     else if (mixed)
-      contact_terms<float, true, true>(c, m, mat, body, du, R, fc, reac, (float*)K);
+      contact_terms<float, true, true>(c, m, mat, body, du, R, fc, reac, (float*)K, dyn, bsum);
     else
-      contact_terms<double, true, true>(c, m, mat, body, du, R, fc, reac, (double*)K);
+      contact_terms<double, true, true>(c, m, mat, body, du, R, fc, reac, (double*)K, dyn, bsum);
   }
   if (want_norms) {
     double* slot = c->d_red + 16;
-    MPM_CUDA(cudaMemsetAsync(slot, 0, 3 * sizeof(double), st));
-    MPM_LAUNCH(k_norms<<<4 * 152, 256, 0, st>>>(3 * nd, R, fint, ptr<double>(m->fext), fc, load,
-                                     ptr<int>(m->dof_mask), slot, grid_red(c, 3, 4 * 152)));
+    MPM_CUDA(cudaMemsetAsync(slot, 0, 4 * sizeof(double), st));
+    MPM_LAUNCH(k_norms<<<4 * 152, 256, 0, st>>>(3 * nd, R, fint, ptr<double>(m->fext), fc, load, finert,
+                                     ptr<int>(m->dof_mask), slot, grid_red(c, 4, 4 * 152)));
     MPM_CUDA(cudaMemcpyAsync(c->h_red + 16, slot, 7 * sizeof(double), cudaMemcpyDeviceToHost, st));
     MPM_CUDA(cudaStreamSynchronize(st));
     out->fint_norm = sqrt(c->h_red[17]);
     out->fextc_norm = sqrt(c->h_red[18]);
+    out->finert_norm = sqrt(c->h_red[19]);
     for (int d = 0; d < 3; ++d) out->reaction[d] = c->h_red[20 + d];
   }
+  if (couple) body_out(c, mat, body, load, dyn, bsum, out, K != nullptr);
 }
 
 void blocks_export(mpm_ctx* c, const mpm_mesh* m, const void* K, int precision, double* out) {
@@ -1053,7 +1359,8 @@ __global__ void k_point_update(int P, Law L, const int* __restrict__ perm,
                                const double* __restrict__ du, const double* __restrict__ pE,
                                const double* __restrict__ pys, const double* __restrict__ pbe,
                                const double* __restrict__ pF, const double* __restrict__ px,
-                               const double* __restrict__ pl0, mpm_points pts, int* err) {
+                               const double* __restrict__ pl0, const double* __restrict__ pv,
+                               double dt, mpm_points pts, int* err) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= P) return;
   double dF[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, dx[3] = {0, 0, 0};
@@ -1089,6 +1396,11 @@ __global__ void k_point_update(int P, Law L, const int* __restrict__ perm,
     for (int a = 0; a < 3; ++a) u += sqrt(lam[a]) * Q[3 * d + a] * Q[3 * d + a];
     pts.x[3 * p + d] = px[3 * (size_t)w + d] + dx[d];
     pts.lp[3 * p + d] = pl0[3 * (size_t)w + d] * u;
+    // a time step's velocity: v + dt a, a = (2 / dt^2) (du_p - dt v)
+    if (dt > 0.0) {
+      double v = pv[3 * (size_t)w + d];
+      pts.v[3 * p + d] = v + dt * ((2.0 / (dt * dt)) * (dx[d] - dt * v));
+    }
   }
   for (int i = 0; i < 9; ++i) pts.F[9 * p + i] = Fn[i];
   for (int s = 0; s < 6; ++s) pts.be[6 * p + s] = bn[s];
@@ -1097,13 +1409,15 @@ __global__ void k_point_update(int P, Law L, const int* __restrict__ perm,
 }  // namespace
 
 void point_update(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const double* du,
-                  mpm_points* pts) {
+                  mpm_points* pts, double dt) {
   mpm_mesh* m = const_cast<mpm_mesh*>(mc);
   int P = m->np;
+  if (dt > 0.0 && !(m->has_v && pts->v)) throw CudaError(MPM_ERR_ARG, "a time step needs point velocities");
   MPM_LAUNCH(k_point_update<<<grid_for(P, 128), 128, 0, c->stream>>>(
       P, make_law(mat), ptr<int>(m->perm), ptr<int>(m->nsup), ptr<int>(m->sidx), ptr<double>(m->S),
       ptr<double>(m->dS), du, ptr<double>(m->pE), ptr<double>(m->pys), ptr<double>(m->pbe),
-      ptr<double>(m->pF), ptr<double>(m->px), ptr<double>(m->pl0), *pts, c->d_err));
+      ptr<double>(m->pF), ptr<double>(m->px), ptr<double>(m->pl0), dt > 0.0 ? ptr<double>(m->pv) : nullptr,
+      dt, *pts, c->d_err));
 }
 
 }  // namespace mpm

@@ -393,6 +393,8 @@ __global__ void k_split_write(int P, const int* __restrict__ flag, const int* __
       pts.mass[q] = pts.mass[p] / 8.0;
       pts.E[q] = pts.E[p];
       pts.ys[q] = pts.ys[p];
+      if (pts.v)
+        for (int d = 0; d < 3; ++d) pts.v[3 * q + d] = pts.v[3 * (size_t)p + d];
     }
   }
   pts.V0[p] /= 8.0;
@@ -416,7 +418,7 @@ __global__ void k_point_cell(int P, const double* __restrict__ x, Geo g,
 
 __global__ void k_gather_points(int P, const int* __restrict__ perm, mpm_points pts, double* x,
                                 double* lp, double* l0, double* F, double* be, double* V0,
-                                double* mass, double* E, double* ys) {
+                                double* mass, double* E, double* ys, double* v) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= P) return;
   size_t p = perm[w];
@@ -424,6 +426,7 @@ __global__ void k_gather_points(int P, const int* __restrict__ perm, mpm_points 
     x[3 * (size_t)w + d] = pts.x[3 * p + d];
     lp[3 * (size_t)w + d] = pts.lp[3 * p + d];
     l0[3 * (size_t)w + d] = pts.l0[3 * p + d];
+    if (v) v[3 * (size_t)w + d] = pts.v[3 * p + d];
   }
   for (int i = 0; i < 9; ++i) F[9 * (size_t)w + i] = pts.F[9 * p + i];
   for (int i = 0; i < 6; ++i) be[6 * (size_t)w + i] = pts.be[6 * p + i];
@@ -1420,7 +1423,8 @@ void tri_setup(mpm_ctx* c, mpm_mesh* m, const mpm_rigid& b) {
 }
 
 void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid& body,
-                const mpm_adapt& ad, const mpm_material& mat, mpm_points* pts, int flags) {
+                const mpm_adapt& ad, const mpm_material& mat, mpm_points* pts, int flags,
+                double cand_extra) {
   cudaStream_t st = c->stream;
   m->built = 0;
   ++m->gen;
@@ -1552,7 +1556,9 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
         P, perm, *pts, grow<double>(c, m->px, 3 * (size_t)P), grow<double>(c, m->plp, 3 * (size_t)P),
         grow<double>(c, m->pl0, 3 * (size_t)P), grow<double>(c, m->pF, 9 * (size_t)P),
         grow<double>(c, m->pbe, 6 * (size_t)P), grow<double>(c, m->pV0, P),
-        grow<double>(c, m->pmass, P), grow<double>(c, m->pE, P), grow<double>(c, m->pys, P)));
+        grow<double>(c, m->pmass, P), grow<double>(c, m->pE, P), grow<double>(c, m->pys, P),
+        pts->v ? grow<double>(c, m->pv, 3 * (size_t)P) : nullptr));
+    m->has_v = pts->v != nullptr;
   }
 
   // ---- a4: discrete GIMP basis
@@ -1716,14 +1722,15 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
                                                              mat.g[2], fext));
   }
 
-  // ---- contact candidates: domains with a corner within 4 finest cells of the body
+  // ---- contact candidates: domains with a corner within 4 finest cells of the
+  // body (plus cand_extra: a free body's motion over the step)
   m->ncand = 0;
   m->nct = 0;
   if (mat.contact_on && body.kind != 0) {
     int* flag = grow<int>(c, c->tmp[0], P);
     int* pos = grow<int>(c, c->tmp[1], P);
     MPM_LAUNCH(k_cand_flag<<<grid_for(P, 256), 256, 0, st>>>(P, ptr<double>(m->px), ptr<double>(m->plp), bv,
-                                                  4.0 * g.unit, flag));
+                                                  4.0 * g.unit + cand_extra, flag));
     cub_exclusive_sum_int(c, flag, pos, P);
     int nc = read_total(c, pos, flag, P);
     m->ncand = nc;

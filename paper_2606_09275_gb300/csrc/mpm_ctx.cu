@@ -159,7 +159,7 @@ void mesh_release(mpm_mesh* m) {
                  &m->src_key, &m->src_ptr, &m->fext, &m->cand, &m->cb_n, &m->cb_idx, &m->cb_phi,
                  &m->cb_y0, &m->dF, &m->dFinv, &m->tau, &m->Aalg, &m->gx, &m->slice_w, &m->slice_base, &m->scol,
                  &m->lawst, &m->ct_row, &m->ct_ptr, &m->ct_ent, &m->cc_f, &m->cc_k, &m->cc_on,
-                 &m->gJ, &m->gcoef, &m->Mf, &m->V0t, &m->dS32, &m->tri_fn, &m->tri_en, &m->tri_vn};
+                 &m->gJ, &m->gcoef, &m->Mf, &m->V0t, &m->dS32, &m->pv, &m->cc_t, &m->cc_d, &m->cc_b, &m->pma, &m->tri_fn, &m->tri_en, &m->tri_vn};
   for (Buf* b : bufs) free_buf(c, *b);
 }
 }  // namespace mpm
@@ -473,6 +473,38 @@ extern "C" int mpm_assemble(mpm_ctx* c, const mpm_mesh* m, const mpm_material* m
       fint_norms[0] = o.fint_norm;
       fint_norms[1] = o.fextc_norm;
     }
+    return (int)MPM_OK;
+  })
+}
+
+extern "C" int mpm_assemble_body(mpm_ctx* c, const mpm_mesh* m, const mpm_material* mat,
+                                 const mpm_rigid* body, const double* du, const double* q, double dt,
+                                 double load, int precision, double* R, void* K, double* reaction,
+                                 double* fint_norms, double* Rb, double* Kbb, double* Kgb, double* Kbg) {
+  if (!c || !m || !mat || !body || !du || !q || !R || !m->built || !(dt > 0.0)) return MPM_ERR_ARG;
+  if (precision != MPM_FP64 && precision != MPM_MIXED) return MPM_ERR_ARG;
+  MPM_GUARD(c, {
+    Dyn dyn;
+    dyn.dt = dt;
+    dyn.body = body->free != 0 && body->kind != 0;
+    for (int j = 0; j < 6; ++j) dyn.q[j] = q[j];
+    dyn.Kgb = Kgb;
+    dyn.Kbg = Kbg;
+    AsmOut o{};
+    assemble(c, m, *mat, *body, du, load, precision, R, K, &o, true, false, &dyn);
+    int st = check_device_error(c, "mpm_assemble_body");
+    if (st) return st;
+    if (reaction)
+      for (int d = 0; d < 3; ++d) reaction[d] = o.reaction[d];
+    if (fint_norms) {
+      fint_norms[0] = o.fint_norm;
+      fint_norms[1] = o.fextc_norm;
+      fint_norms[2] = o.finert_norm;
+    }
+    if (Rb)
+      for (int j = 0; j < 6; ++j) Rb[j] = o.Rb[j];
+    if (Kbb)
+      for (int j = 0; j < 36; ++j) Kbb[j] = o.Kbb[j];
     return (int)MPM_OK;
   })
 }

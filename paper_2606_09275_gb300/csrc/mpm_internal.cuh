@@ -171,7 +171,7 @@ struct mpm_ctx {
   mpm_mesh* step_mesh = nullptr;
   std::vector<mpm_mesh*> meshes;  // meshes made by mpm_octree_build, freed with the context
   // Newton / Krylov work vectors (grown on demand)
-  mpm::Buf v[24];
+  mpm::Buf v[32];
   // measurement: launch count and optional per-class CUDA-event timing
   long long nlaunch = 0;
   bool prof_on = false;
@@ -233,6 +233,11 @@ struct mpm_mesh {
   // per-iteration point data (Mf: V0 tau dF^-T, 12 per point)
   mpm::Buf dF, dFinv, tau, Aalg, gx, Mf, V0t;
   mpm::Buf dS32;                        // FP32 copy of dS for the mixed tangent's grad_x S
+  mpm::Buf pv;                          // sorted point velocities (time steps)
+  bool has_v = false;                   // the points of this build carried velocities
+  mpm::Buf cc_t, cc_d;                  // per contact corner: d f / d(rotation), offset from the body centre
+  mpm::Buf cc_b;                        // the body's contact sums (42 doubles)
+  mpm::Buf pma;                         // per point m_p a_p of a time step
   long long dS32_gen = -1;              // build the copy belongs to
   mpm::Buf lawst;  // spectral state of the last residual-only evaluation (22 per point)
   int built = 0;
@@ -527,6 +532,16 @@ __device__ inline bool body_meets_box(const Body& B, const double* lo, const dou
     return tri_sdf(B, c, nullptr, nullptr) <= hd;
   }
   if (b.kind == 1) return hi[2] >= b.z && body_rxy(b, lo, hi) <= b.r;
+  if (b.kind == 4) {
+    // sphere: the box's nearest point to the centre is inside the ball
+    const double c[3] = {b.cx, b.cy, b.z};
+    double s2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double e = fmax(fmax(lo[d] - c[d], 0.0), c[d] - hi[d]);
+      s2 += e * e;
+    }
+    return sqrt(s2) <= b.r;
+  }
   if (b.kind == 2) {
     if (hi[2] < b.z) return false;
     double rmax = fmin((hi[2] - b.z) * tan(b.alpha), b.r);
@@ -553,6 +568,10 @@ __device__ inline double body_distance(const Body& B, const double* x, double th
     double lb = tri_box_distance(B, x);
     if (lb > thr) return lb;
     return fmax(tri_sdf(B, x, nullptr, nullptr), 0.0);
+  }
+  if (b.kind == 4) {
+    double dx = x[0] - b.cx, dy = x[1] - b.cy, dz = x[2] - b.z;
+    return fmax(sqrt(dx * dx + dy * dy + dz * dz) - b.r, 0.0);
   }
   double rx = x[0] - b.cx, ry = x[1] - b.cy;
   double rho = sqrt(rx * rx + ry * ry), z = x[2];
@@ -582,6 +601,21 @@ __device__ inline bool body_sdf(const Body& B, double L, const double* x, double
     n[0] = n[1] = n[2] = 0.0;
     for (int i = 0; i < 9; ++i) H[i] = 0.0;
     return false;
+  }
+  if (b.kind == 4) {
+    // sphere: phi = |x - c| - r, n = (x - c) / |x - c|, H = (I - n n^T) / |x - c|
+    double d[3] = {x[0] - b.cx, x[1] - b.cy, x[2] - b.z};
+    double rho = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) H[i] = 0.0;
+    n[0] = n[1] = n[2] = 0.0;
+    *phi = rho - b.r;
+    if (!(*phi < 0.0)) return false;
+    if (rho < 1e-12 * L) return true;  // at the centre: no direction is nearest
+    for (int i = 0; i < 3; ++i) n[i] = d[i] / rho;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) H[3 * i + j] = ((i == j ? 1.0 : 0.0) - n[i] * n[j]) / rho;
+    return true;
   }
   double rx = x[0] - b.cx, ry = x[1] - b.cy;
   double rho = sqrt(rx * rx + ry * ry), z = x[2];
@@ -771,20 +805,43 @@ void sync(mpm_ctx* c);
 // the kernels' view of the body for this mesh (mpm_build.cu)
 Body body_view(const mpm_mesh* m, const mpm_rigid& b);
 
-// build phase (mpm_build.cu)
+// build phase (mpm_build.cu); cand_extra widens the contact candidates' band
+// beyond 4 finest cells (a free body's possible motion over a time step)
 void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid& body,
-                const mpm_adapt& ad, const mpm_material& mat, mpm_points* pts, int flags);
+                const mpm_adapt& ad, const mpm_material& mat, mpm_points* pts, int flags,
+                double cand_extra = 0.0);
+
+// the rigid body's increment as the contact kernels see it: translation qt
+// and rotation qr over the step (the friction's reference displacement at a
+// node is qt + qr x d) and the shift of the body from its given pose (qt for
+// a free body, whose given pose is the step-start one; zero otherwise)
+struct BodyInc {
+  double qt[3], qr[3], shift[3];
+};
 
 // assembly (mpm_assemble.cu)
 struct AsmOut {
   double reaction[3];
-  double fint_norm, fextc_norm;
+  double fint_norm, fextc_norm, finert_norm;
+  double Rb[6], Kbb[36];  // a free body's residual and its derivative in q
+};
+// a time step's inertia and a free body's equations: dt > 0 adds the Newmark
+// inertia (needs the build's point velocities); q is the body's increment;
+// with `body` the assembly forms the body's residual (AsmOut.Rb, with its
+// residual) and, with the tangent, AsmOut.Kbb and the coupling blocks Kgb,
+// Kbg (device [6][3 nd] each, when non-null)
+struct Dyn {
+  double dt = 0.0;
+  double q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  bool body = false;
+  double* Kgb = nullptr;
+  double* Kbg = nullptr;
 };
 // reuse: with K, only the tangent, from the state the last residual-only call
 // left at the same increment (dF, tau and the spectral state); R untouched
 void assemble(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const mpm_rigid& body,
               const double* du, double load, int precision, double* R, void* K, AsmOut* out,
-              bool want_norms, bool reuse = false);
+              bool want_norms, bool reuse = false, const Dyn* dyn = nullptr);
 double norm_free(mpm_ctx* c, const mpm_mesh* m, const double* R);
 void blocks_export(mpm_ctx* c, const mpm_mesh* m, const void* K, int precision, double* out);
 
@@ -814,7 +871,7 @@ void newton(mpm_ctx* c, mpm_mesh* m, const mpm_material* mat, const mpm_rigid& b
 
 // point update (mpm_step.cu)
 void point_update(mpm_ctx* c, const mpm_mesh* m, const mpm_material& mat, const double* du,
-                  mpm_points* pts);
+                  mpm_points* pts, double dt = 0.0);
 
 // CUB wrappers (mpm_cub.cu)
 void cub_exclusive_sum_int(mpm_ctx* c, const int* in, int* out, int n);

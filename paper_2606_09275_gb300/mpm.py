@@ -28,7 +28,7 @@ EXPORT = dict(leaf_level=0, leaf_anchor=1, node_coord=2, node_hang=3, node_dof=4
 SYMBOLS = ["mpm_create", "mpm_destroy", "mpm_last_error", "mpm_octree_build", "mpm_mesh_free",
            "mpm_mesh_counts", "mpm_mesh_export", "mpm_assemble", "mpm_solve", "mpm_step",
            "mpm_profile", "mpm_profile_read", "mpm_launch_count", "mpm_solve_static",
-           "mpm_blocks_export", "mpm_adjoint", "mpm_fp64_peak"]
+           "mpm_blocks_export", "mpm_adjoint", "mpm_fp64_peak", "mpm_assemble_body"]
 
 
 class Domain(C.Structure):
@@ -40,7 +40,9 @@ class Domain(C.Structure):
 class Rigid(C.Structure):
     _fields_ = [("kind", C.c_int), ("cx", C.c_double), ("cy", C.c_double), ("z", C.c_double),
                 ("r", C.c_double), ("alpha", C.c_double), ("step_d", C.c_double * 3),
-                ("ntri", C.c_int), ("nvert", C.c_int), ("tri_v", C.c_void_p), ("tri_t", C.c_void_p)]
+                ("ntri", C.c_int), ("nvert", C.c_int), ("tri_v", C.c_void_p), ("tri_t", C.c_void_p),
+                ("free", C.c_int), ("mass", C.c_double), ("inertia", C.c_double),
+                ("v", C.c_double * 3), ("w", C.c_double * 3)]
 
 
 class Adapt(C.Structure):
@@ -56,7 +58,7 @@ class Material(C.Structure):
 
 class PointsT(C.Structure):
     _fields_ = [("count", C.c_int), ("capacity", C.c_int)] + [
-        (n, C.c_void_p) for n in ("x", "lp", "l0", "F", "be", "V0", "mass", "E", "ys")]
+        (n, C.c_void_p) for n in ("x", "lp", "l0", "F", "be", "V0", "mass", "E", "ys", "v")]
 
 
 class MeshInfo(C.Structure):
@@ -76,7 +78,8 @@ class SolveStats(C.Structure):
 
 class StepParams(C.Structure):
     _fields_ = [("load", C.c_double), ("tol", C.c_double), ("maxit", C.c_int),
-                ("lin", SolveParams), ("du_out", C.c_void_p), ("du_capacity", C.c_longlong)]
+                ("lin", SolveParams), ("du_out", C.c_void_p), ("du_capacity", C.c_longlong),
+                ("dt", C.c_double)]
 
 
 class StepStats(C.Structure):
@@ -84,7 +87,8 @@ class StepStats(C.Structure):
         ("res_hist", C.c_double * 64), ("eta_hist", C.c_double * 64), ("reaction", C.c_double * 3),
         ("ms_build", C.c_double), ("ms_assemble", C.c_double), ("ms_solve", C.c_double),
         ("ms_update", C.c_double), ("nsrc", C.c_longlong), ("nslot", C.c_longlong),
-        ("mg_rows1", C.c_int), ("mg_stencil1", C.c_int), ("npair", C.c_longlong)]
+        ("mg_rows1", C.c_int), ("mg_stencil1", C.c_int), ("npair", C.c_longlong),
+        ("body_q", C.c_double * 6), ("body_v", C.c_double * 3), ("body_w", C.c_double * 3)]
 
 
 class Checkpoint(C.Structure):
@@ -133,6 +137,8 @@ def lib():
         L.mpm_profile_read.argtypes = [vp, vp, vp]
         L.mpm_launch_count.argtypes = [vp, vp]
         L.mpm_fp64_peak.argtypes = [vp, d, vp, vp]
+        L.mpm_assemble_body.argtypes = [vp, vp, C.POINTER(Material), C.POINTER(Rigid), vp, vp, d, d,
+                                        i, vp, vp, vp, vp, vp, vp, vp, vp]
         L.mpm_adjoint.argtypes = [vp, C.POINTER(Domain), C.POINTER(Rigid), C.POINTER(Adapt),
                                   C.POINTER(Material), C.POINTER(Checkpoint), i,
                                   C.POINTER(StepParams), vp, vp, vp, C.POINTER(AdjointStats)]
@@ -172,7 +178,10 @@ def _tri_device(mesh):
     return hit[1], hit[2]
 
 
-def rigid(cfg, z=None):
+def rigid(cfg, z=None, state=None):
+    """The body of cfg at height z (default its start height); `state`
+    (optional dict: pose (3), v (3), w (3)) overrides a free body's pose and
+    velocities, which a run of time steps carries from step to step."""
     r = Rigid()
     b = cfg.get("body")
     if b:
@@ -182,6 +191,14 @@ def rigid(cfg, z=None):
         d = b.get("step_d", (0.0, 0.0, b.get("dz", 0.0)))
         for k in range(3):
             r.step_d[k] = d[k]
+        r.free, r.mass, r.inertia = int(b.get("free", 0)), b.get("mass", 0.0), b.get("inertia", 0.0)
+        for k in range(3):
+            r.v[k] = b.get("v", (0.0, 0.0, 0.0))[k]
+            r.w[k] = b.get("w", (0.0, 0.0, 0.0))[k]
+        if state is not None:
+            r.cx, r.cy, r.z = [float(x) for x in state["pose"]]
+            for k in range(3):
+                r.v[k], r.w[k] = float(state["v"][k]), float(state["w"][k])
         if b["kind"] == 3:
             tv, tt = _tri_device(b["mesh"])
             r.nvert, r.ntri = tv.shape[0], tt.shape[0]
@@ -263,16 +280,20 @@ _PT = (("x", 3), ("lp", 3), ("l0", 3), ("F", 9), ("be", 6), ("V0", 1), ("mass", 
 
 
 class Points:
-    """Caller-owned device point arrays (torch float64 tensors of `capacity` rows)."""
+    """Caller-owned device point arrays (torch float64 tensors of `capacity`
+    rows); with velocity=True (or a "v" entry in pts) also the velocities that
+    time steps need."""
 
-    def __init__(self, pts, capacity=None, device="cuda"):
+    def __init__(self, pts, capacity=None, device="cuda", velocity=False):
         n = len(pts["x"])
         cap = max(n, capacity or n)
         self.count, self.capacity = n, cap
         self.t = {}
-        for k, w in _PT:
+        keys = _PT + ((("v", 3),) if velocity or "v" in pts else ())
+        for k, w in keys:
             t = torch.zeros((cap, w) if w > 1 else (cap,), dtype=torch.float64, device=device)
-            t[:n] = torch.as_tensor(np.asarray(pts[k], dtype=np.float64)).reshape(t[:n].shape)
+            if k in pts:
+                t[:n] = torch.as_tensor(np.asarray(pts[k], dtype=np.float64)).reshape(t[:n].shape)
             self.t[k] = t
 
     def clone(self):
@@ -287,11 +308,12 @@ class Points:
         s.count, s.capacity = self.count, self.capacity
         for k, _ in _PT:
             setattr(s, k, self.t[k].data_ptr())
+        s.v = self.t["v"].data_ptr() if "v" in self.t else None
         return s
 
     def numpy(self):
         n = self.count
-        return {k: self.t[k][:n].cpu().numpy().copy() for k, _ in _PT}
+        return {k: self.t[k][:n].cpu().numpy().copy() for k in self.t}
 
 
 class Mesh:
@@ -369,6 +391,32 @@ def assemble(ctx, mesh, cfg, du, load=1.0, precision=FP64, tangent=True, body_z=
     return dict(R=R, K=K, reaction=np.array(reac[:]), fint_norm=norms[0], fextc_norm=norms[1])
 
 
+def assemble_body(ctx, mesh, cfg, du, q, dt, load=1.0, precision=FP64, tangent=True, state=None):
+    """mpm_assemble_body: the residual, tangent and a free body's equations of a
+    time step at the increments (du, q): R, K, Rb (6), Kbb (6x6), Kgb and Kbg
+    (device [6, 3 ndof])."""
+    info = mesh.info()
+    nd, ns = info["ndof"], info["nslot"]
+    R = torch.empty(3 * nd, dtype=torch.float64, device=du.device)
+    K = Kgb = Kbg = None
+    if tangent:
+        K = torch.empty(9 * max(ns, 1), dtype=torch.float32 if precision == MIXED else torch.float64,
+                        device=du.device)
+        Kgb = torch.empty((6, 3 * nd), dtype=torch.float64, device=du.device)
+        Kbg = torch.empty((6, 3 * nd), dtype=torch.float64, device=du.device)
+    qv = (C.c_double * 6)(*[float(v) for v in q])
+    reac, norms = (C.c_double * 3)(), (C.c_double * 3)()
+    Rb, Kbb = (C.c_double * 6)(), (C.c_double * 36)()
+    st = lib().mpm_assemble_body(ctx.h, mesh.h, C.byref(material(cfg)),
+                                 C.byref(rigid(cfg, state=state)), _p(du), C.cast(qv, C.c_void_p), dt,
+                                 load, precision, _p(R), _p(K), reac, norms, Rb, Kbb, _p(Kgb),
+                                 _p(Kbg))
+    ctx.check(st)
+    return dict(R=R, K=K, reaction=np.array(reac[:]), fint_norm=norms[0], fextc_norm=norms[1],
+                finert_norm=norms[2], Rb=np.array(Rb[:]), Kbb=np.array(Kbb[:]).reshape(6, 6),
+                Kgb=Kgb, Kbg=Kbg)
+
+
 def solve(ctx, mesh, cfg, K, rhs, precision=FP64, tol=1e-10, maxit=20000, method=0,
           inner_tol=1e-3, mg_reuse=0):
     """mpm_solve: block-Jacobi PCG, BiCGStab or multigrid PCG / BiCGStab (method 3); FP32
@@ -407,26 +455,45 @@ def solve_static(ctx, mesh, K, rhs, tol=1e-10, maxit=20000):
     return x, stats
 
 
+def body_start(cfg):
+    """A free body's state at the start of a run: pose, velocity, angular velocity."""
+    b = cfg["body"]
+    return dict(pose=np.array([b["cx"], b["cy"], b["z0"]], dtype=np.float64),
+                v=np.array(b.get("v", (0.0, 0.0, 0.0)), dtype=np.float64),
+                w=np.array(b.get("w", (0.0, 0.0, 0.0)), dtype=np.float64),
+                theta=np.zeros(3))
+
+
 def step(ctx, cfg, points, body_z=None, load=1.0, tol=1e-8, maxit=30, lin_tol=1e-8,
          lin_maxit=20000, precision=FP64, method=0, inner_tol=1e-3, check=True, mg_reuse=0,
-         du_out=None):
-    """mpm_step: one quasi-static load step; returns the statistics.  du_out
-    (optional float64 device tensor) receives the converged increment."""
+         du_out=None, dt=0.0, body_state=None):
+    """mpm_step: one load step (dt = 0) or Newmark time step (dt > 0); returns
+    the statistics.  du_out (optional float64 device tensor) receives the
+    converged increment.  body_state (a free body's pose and velocities at
+    the step start, see body_start) is advanced in place."""
     s = points.struct()
     sp = StepParams(load, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol,
                                                   mg_reuse),
                     _p(du_out) if du_out is not None else None,
-                    du_out.numel() if du_out is not None else 0)
+                    du_out.numel() if du_out is not None else 0, dt)
     ss = StepStats()
-    st = lib().mpm_step(ctx.h, C.byref(domain(cfg)), C.byref(rigid(cfg, body_z)), C.byref(adapt(cfg)),
-                        C.byref(material(cfg)), C.byref(s), C.byref(sp), C.byref(ss))
+    st = lib().mpm_step(ctx.h, C.byref(domain(cfg)), C.byref(rigid(cfg, body_z, body_state)),
+                        C.byref(adapt(cfg)), C.byref(material(cfg)), C.byref(s), C.byref(sp),
+                        C.byref(ss))
+    if st == 0 and body_state is not None:
+        q = np.array(ss.body_q[:])
+        body_state["pose"] = body_state["pose"] + q[:3]
+        body_state["theta"] = body_state["theta"] + q[3:]
+        body_state["v"] = np.array(ss.body_v[:])
+        body_state["w"] = np.array(ss.body_w[:])
     points.count = s.count
     out = dict(status=st, newton_its=ss.newton_its, lin_its=ss.lin_its, npts=ss.npts, ndof=ss.ndof,
                nnzb=ss.nnzb, res_hist=np.array(ss.res_hist[: ss.newton_its + 1]),
                eta_hist=np.array(ss.eta_hist[: ss.newton_its]), reaction=np.array(ss.reaction[:]),
                ms_build=ss.ms_build, ms_assemble=ss.ms_assemble, ms_solve=ss.ms_solve,
                ms_update=ss.ms_update, nsrc=ss.nsrc, nslot=ss.nslot, mg_rows1=ss.mg_rows1,
-               mg_stencil1=ss.mg_stencil1, npair=ss.npair)
+               mg_stencil1=ss.mg_stencil1, npair=ss.npair, body_q=np.array(ss.body_q[:]),
+               body_v=np.array(ss.body_v[:]), body_w=np.array(ss.body_w[:]))
     if check:
         ctx.check(st)
     return out
@@ -473,7 +540,7 @@ def adjoint(ctx, cfg, checkpoints, w, tol=1e-8, maxit=30, lin_tol=1e-10, lin_max
     dys = torch.zeros_like(dE)
     wv = (C.c_double * 3)(*[float(v) for v in w])
     sp = StepParams(1.0, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol,
-                                                 mg_reuse), None, 0)
+                                                 mg_reuse), None, 0, 0.0)
     st_ = AdjointStats()
     st = lib().mpm_adjoint(ctx.h, C.byref(domain(cfg)), C.byref(rigid(cfg)), C.byref(adapt(cfg)),
                            C.byref(material(cfg)), arr, n, C.byref(sp),
