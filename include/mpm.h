@@ -148,7 +148,10 @@ typedef struct {
   int method;      /* 0 auto (PCG if symmetric else BiCGStab), 1 PCG, 2 BiCGStab,
                       3 preconditioned by a geometric multigrid V-cycle:
                       PCG for symmetric tangents, BiCGStab (one V-cycle per
-                      half-step) for the non-associated Drucker-Prager one */
+                      half-step) for the non-associated Drucker-Prager one,
+                      4 restarted GMRES(30) with the block-Jacobi
+                      preconditioner (Sec. 6.4 names GMRES with a Jacobi
+                      preconditioner as the iterative route), any tangent */
   int precision;   /* mpm_precision of the stored matrix and the inner solve     */
   double tol;      /* relative residual target ||b - K x|| <= tol ||b||           */
   int maxit;       /* cap on Krylov iterations (all refinement rounds together)  */

@@ -9,6 +9,7 @@
 //    refinement, the refinement residual accumulated in FP64.
 #include <algorithm>
 #include <atomic>
+#include <vector>
 #include <cmath>
 #include <string>
 
@@ -637,6 +638,231 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const T* Dinv, const
   return MPM_OK;
 }
 
+// ---------------------------------------------------------------- GMRES
+// Restarted GMRES(m) right preconditioned by 3x3 block Jacobi (Sec. 6.4 names
+// GMRES with a Jacobi preconditioner as the iterative route for the CPT's
+// linear solves).  The Arnoldi basis is orthogonalised by classical
+// Gram-Schmidt applied twice (CGS2: two passes of j + 1 dot products and one
+// combined update each, instead of the j + 1 dependent steps of modified
+// Gram-Schmidt); the dot products are fixed-order two-stage reductions, the
+// small Hessenberg least-squares problem is solved on the host by Givens
+// rotations.  Vectors are T (FP64, or FP32 for the inner solve of the mixed
+// path) padded to 4 components over 32 nslice rows; sums in FP64.
+
+// r = b - K x on the free components (x over 4-component rows), rows beyond
+// nd and fixed components zero
+template <class T, class V>
+__global__ void k_gm_residual(int nd, int npad, Sliced S, const T* __restrict__ K, const V* __restrict__ x,
+                              const double* __restrict__ b, const int* __restrict__ mask, V* r) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  V y[3];
+  sliced_row<T, V, V, 4>(i, S, K, x, y);
+  V rv[4] = {(V)0, (V)0, (V)0, (V)0};
+  if (i < nd) {
+    int mi = mask[i];
+    for (int c = 0; c < 3; ++c)
+      rv[c] = ((mi >> c) & 1) ? (V)0 : (V)(b[3 * (size_t)i + c] - (double)y[c]);
+  }
+  st4(r + 4 * (size_t)i, rv);
+}
+
+// w = K (Dinv v): the preconditioned direction z = Dinv v first (kept in z),
+// then the row product
+template <class V>
+__global__ void k_gm_dinv(int nd, int npad, const V* __restrict__ Dinv, const V* __restrict__ v, V* z) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  V rv[4], zv[4] = {(V)0, (V)0, (V)0, (V)0};
+  if (i < nd) {  // rows beyond nd: no preconditioner block
+    ld4(v + 4 * (size_t)i, rv);
+    apply_dinv(Dinv, i, rv, zv);
+  }
+  st4(z + 4 * (size_t)i, zv);
+}
+
+template <class T, class V>
+__global__ void k_gm_spmv(int nd, int npad, Sliced S, const T* __restrict__ K, const V* __restrict__ z, V* w) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  V y[3];
+  sliced_row<T, V, V, 4>(i, S, K, z, y);
+  V wv[4] = {y[0], y[1], y[2], (V)0};
+  if (i >= nd) wv[0] = wv[1] = wv[2] = (V)0;
+  st4(w + 4 * (size_t)i, wv);
+}
+
+// stage 1 of the dots V_i . w (i = blockIdx.y < nv; V_i at Vb + i n4): each
+// block's partial sum of its strided entries, by the block's fixed tree
+template <class V>
+__global__ void k_gm_dots(long long n4, const V* __restrict__ Vb, const V* __restrict__ w, double* part) {
+  __shared__ double sh[32];
+  const V* vi = Vb + (size_t)blockIdx.y * n4;
+  double s = 0.0;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n4; k += (long long)gridDim.x * blockDim.x)
+    s += (double)vi[k] * (double)w[k];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// stage 2: h[i] = the block partials of dot i added in block order
+__global__ void k_gm_dots_fin(int nb, const double* __restrict__ part, double* h) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(size_t)blockIdx.x * nb + b];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) h[blockIdx.x] = s;
+}
+
+// w -= sum_i h[i] V_i (i < nv)
+template <class V>
+__global__ void k_gm_orth(long long n4, int nv, const V* __restrict__ Vb, const double* __restrict__ h, V* w) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n4) return;
+  double s = (double)w[k];
+  for (int i = 0; i < nv; ++i) s -= h[i] * (double)Vb[(size_t)i * n4 + k];
+  w[k] = (V)s;
+}
+
+// y = a x
+template <class V>
+__global__ void k_gm_scale(long long n4, double a, const V* __restrict__ x, V* y) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n4) y[k] = (V)(a * (double)x[k]);
+}
+
+// u = sum_i y[i] V_i, then x += Dinv u over the rows (one thread per row)
+template <class V>
+__global__ void k_gm_update_x(int nd, long long n4, int nv, const V* __restrict__ Vb, const double* __restrict__ y,
+                              const V* __restrict__ Dinv, V* x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  V u[4];
+  for (int c = 0; c < 4; ++c) {
+    double s = 0.0;
+    for (int j = 0; j < nv; ++j) s += y[j] * (double)Vb[(size_t)j * n4 + 4 * (size_t)i + c];
+    u[c] = (V)s;
+  }
+  V zv[4], xv[4];
+  apply_dinv(Dinv, i, u, zv);
+  ld4(x + 4 * (size_t)i, xv);
+  for (int c = 0; c < 3; ++c) xv[c] += zv[c];
+  st4(x + 4 * (size_t)i, xv);
+}
+
+// x (4-component rows) -> the caller's 3-component solution
+template <class V, class X>
+__global__ void k_gm_out(int nd, const V* __restrict__ x4, X* x) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * nd) return;
+  x[i] = (X)x4[4 * (size_t)(i / 3) + i % 3];
+}
+
+template <class T>
+int run_gmres(mpm_ctx* c, const mpm_mesh* m, const T* K, const T* Dinv, const double* b, T* xout,
+              double tol, int maxit, int restart, double* relres, int* iters) {
+  typedef T V;
+  cudaStream_t st = c->stream;
+  int nd = m->ndof, npad = 32 * m->nslice, mr = restart;
+  long long n4 = 4LL * npad;
+  V* Vb = grow<V>(c, c->v[28], (size_t)(mr + 1) * n4);
+  V* w = grow<V>(c, c->v[29], n4);
+  V* z = grow<V>(c, c->v[30], n4);
+  V* x = grow<V>(c, c->v[31], n4);
+  Sliced S = sliced_of(m);
+  const int* mask = ptr<int>(m->dof_mask);
+  int nbk = std::min(4 * 152, std::max(1, (int)((n4 + 255) / 256)));
+  double* part = grow<double>(c, c->v[23], (size_t)(mr + 1) * nbk + 2 * (mr + 1));
+  double* hd = part + (size_t)(mr + 1) * nbk;  // device h (mr + 1) and y (mr + 1)
+  double* yd = hd + (mr + 1);
+  double* hh = c->h_red;  // pinned host: up to 32 values
+  if (mr + 1 > 32) throw CudaError(MPM_ERR_ARG, "GMRES restart too long");
+  int gr = grid_for(npad, 256);
+  int gv = (int)((n4 + 255) / 256);
+  auto dots = [&](int nv, const V* base, const V* vec) {
+    MPM_LAUNCH(k_gm_dots<V><<<dim3(nbk, nv), 256, 0, st>>>(n4, base, vec, part));
+    MPM_LAUNCH(k_gm_dots_fin<<<nv, 256, 0, st>>>(nbk, part, hd));
+    MPM_CUDA(cudaMemcpyAsync(hh, hd, sizeof(double) * nv, cudaMemcpyDeviceToHost, st));
+    MPM_CUDA(cudaStreamSynchronize(st));
+  };
+  MPM_CUDA(cudaMemsetAsync(x, 0, sizeof(V) * n4, st));
+  // ||b|| over the free components
+  MPM_LAUNCH(k_gm_residual<T, V><<<gr, 256, 0, st>>>(nd, npad, S, K, x, b, mask, w));
+  dots(1, w, w);
+  double bn = sqrt(hh[0]);
+  *iters = 0;
+  *relres = 0.0;
+  if (bn == 0.0) {
+    MPM_LAUNCH(k_gm_out<V, T><<<grid_for(3 * nd, 256), 256, 0, st>>>(nd, x, xout));
+    return MPM_OK;
+  }
+  std::vector<double> H((size_t)(mr + 1) * mr), cs(mr), sn(mr), g(mr + 1), y(mr + 1);
+  int total = 0;
+  double beta = bn;
+  bool conv = false;
+  while (total < maxit && !conv) {
+    // restart: V_0 = r / ||r||
+    MPM_LAUNCH(k_gm_scale<V><<<gv, 256, 0, st>>>(n4, 1.0 / beta, w, Vb));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    for (; j < mr && total < maxit; ++j) {
+      V* vj1 = Vb + (size_t)(j + 1) * n4;
+      MPM_LAUNCH(k_gm_dinv<V><<<gr, 256, 0, st>>>(nd, npad, Dinv, Vb + (size_t)j * n4, z));
+      MPM_LAUNCH_P(MPM_PROF_BICG_SPMV, k_gm_spmv<T, V><<<gr, 256, 0, st>>>(nd, npad, S, K, z, w));
+      double hcol[33];
+      for (int i = 0; i <= j; ++i) hcol[i] = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {
+        dots(j + 1, Vb, w);
+        for (int i = 0; i <= j; ++i) hcol[i] += hh[i];
+        MPM_LAUNCH(k_gm_orth<V><<<gv, 256, 0, st>>>(n4, j + 1, Vb, hd, w));
+      }
+      dots(1, w, w);
+      double hn = sqrt(hh[0]);
+      hcol[j + 1] = hn;
+      ++total;
+      // apply the earlier rotations to the new column, then its own
+      for (int i = 0; i < j; ++i) {
+        double t0 = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+        hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+        hcol[i] = t0;
+      }
+      double den = hypot(hcol[j], hcol[j + 1]);
+      cs[j] = den > 0.0 ? hcol[j] / den : 1.0;
+      sn[j] = den > 0.0 ? hcol[j + 1] / den : 0.0;
+      hcol[j] = den;
+      hcol[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      for (int i = 0; i <= j; ++i) H[(size_t)i * mr + j] = hcol[i];
+      if (fabs(g[j + 1]) <= tol * bn || hn == 0.0) {
+        conv = true;
+        ++j;
+        break;
+      }
+      MPM_LAUNCH(k_gm_scale<V><<<gv, 256, 0, st>>>(n4, 1.0 / hn, w, vj1));
+    }
+    // y = R^-1 g (upper triangular), x += Dinv (V y)
+    int k = j;
+    for (int i = k - 1; i >= 0; --i) {
+      double sm = g[i];
+      for (int l = i + 1; l < k; ++l) sm -= H[(size_t)i * mr + l] * y[l];
+      y[i] = H[(size_t)i * mr + i] != 0.0 ? sm / H[(size_t)i * mr + i] : 0.0;
+    }
+    MPM_CUDA(cudaMemcpyAsync(yd, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+    MPM_LAUNCH(k_gm_update_x<V><<<grid_for(nd, 256), 256, 0, st>>>(nd, n4, k, Vb, yd, Dinv, x));
+    // the true residual of the restart (and of the end)
+    MPM_LAUNCH(k_gm_residual<T, V><<<gr, 256, 0, st>>>(nd, npad, S, K, x, b, mask, w));
+    dots(1, w, w);
+    beta = sqrt(hh[0]);
+    conv = beta <= tol * bn;
+  }
+  MPM_LAUNCH(k_gm_out<V, T><<<grid_for(3 * nd, 256), 256, 0, st>>>(nd, x, xout));
+  *iters = total;
+  *relres = beta / bn;
+  return conv ? MPM_OK : MPM_ERR_KRYLOV;
+}
+
 }  // namespace
 
 void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* K,
@@ -655,6 +881,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
              !(mat.mu > 0.0 && mat.contact_on);
   if (method == 0) method = sym ? 1 : 2;
   bool mgb = method == 3 && !sym;  // multigrid-preconditioned BiCGStab
+  const int GMRES_M = 30;          // restart length of method 4
   Scal* sc_d = grow<Scal>(c, c->v[20], 1);
   Scal* sc_h = (Scal*)(c->h_red + 32);  // pinned, 32 doubles fit Scal
   // partial sums of every grid sum of this solve in one buffer, sized once so
@@ -672,7 +899,9 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     int its = 0;
     double rel = 0.0;
     int sst;
-    if (mgb) {
+    if (method == 4) {
+      sst = run_gmres<double>(c, m, Kd, Dinv, b, x, prm.tol, prm.maxit, GMRES_M, &rel, &its);
+    } else if (mgb) {
       mg_setup<double>(c, m, Kd, prm.mg_reuse != 0);
       sst = run_bicgstab<double, double>(c, m, Kd, nullptr, b, x, prm.tol, prm.maxit, sc_d, sc_h, &rel, &its);
     } else if (method == 3) {
@@ -690,7 +919,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     out->relres = rel;
     out->status = sst;
     if (sst)
-      set_error(c, std::string(method == 1 ? "PCG" : (mgb ? "multigrid BiCGStab" : (method == 3 ? "multigrid PCG" : "BiCGStab"))) +
+      set_error(c, std::string(method == 4 ? "GMRES" : method == 1 ? "PCG" : (mgb ? "multigrid BiCGStab" : (method == 3 ? "multigrid PCG" : "BiCGStab"))) +
                        " did not reach the tolerance (" +
                        std::to_string(its) + " iterations, relative residual " +
                        std::to_string(rel) + (sc_h->breakdown ? ", breakdown)" : ")"));
@@ -705,7 +934,8 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   float* d32 = grow<float>(c, c->v[13], n3);
   double* slot = c->d_red + 44;
   GridRed gred = grid_red(c, 2, grid_for(npad, 32 * SW));
-  bool bicg = !sym && method != 1;
+  bool gmres = method == 4;
+  bool bicg = !sym && method != 1 && !gmres;
   float* Dinv = grow<float>(c, c->v[3], 12 * (size_t)npad);
   if (method == 3)
     mg_setup<float>(c, m, Kf, prm.mg_reuse != 0);
@@ -731,7 +961,9 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
     int its = 0;
     double rel = 0.0;
     int sst;
-    if (bicg)
+    if (gmres)
+      sst = run_gmres<float>(c, m, Kf, Dinv, r64, d32, inner, prm.maxit - total, GMRES_M, &rel, &its);
+    else if (bicg)
       sst = run_bicgstab<float, float>(c, m, Kf, method == 3 ? nullptr : Dinv, r64, d32, inner,
                                        prm.maxit - total, sc_d, sc_h, &rel, &its);
     else if (method == 3)
@@ -759,7 +991,7 @@ void solve(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const void* 
   out->relres = bb > 0 ? sqrt(rr / bb) : 0.0;
   out->status = status;
   if (status)
-    set_error(c, std::string("mixed-precision refinement (") + (bicg ? "BiCGStab" : "PCG") +
+    set_error(c, std::string("mixed-precision refinement (") + (gmres ? "GMRES" : bicg ? "BiCGStab" : "PCG") +
                      " inner solves) did not reach the tolerance" + (breakdown ? " (breakdown)" : ""));
 }
 
