@@ -196,3 +196,25 @@ def test_rolling_sphere_gpu_matches_the_closed_form(gpu, mu, regime):
     else:
         ana = 0.5 * g * t * t * (math.sin(th) - mu * math.cos(th))
     assert abs(d - ana) <= 0.02 * ana, (regime, d, ana)
+
+
+def test_time_step_argument_errors(gpu):
+    # rejected before any work, with a status and a message
+    mpm, ctx, torch = gpu
+    cfg = inputs.workload("rolling_sphere", mu=1.0)
+    pts = inputs.make_points(cfg)
+    P = mpm.Points(pts, capacity=64 * len(pts["x"]))  # no velocities
+    st = mpm.step(ctx, cfg, P, dt=cfg["dt"], body_state=mpm.body_start(cfg), check=False)
+    assert st["status"] == 1 and "velocities" in ctx.error()
+    Pv = mpm.Points(pts, capacity=64 * len(pts["x"]), velocity=True)
+    st = mpm.step(ctx, cfg, Pv, dt=0.0, body_state=mpm.body_start(cfg), check=False)
+    assert st["status"] == 1 and "free body" in ctx.error()
+    punch = inputs.workload("punch")
+    punch["body"].update(free=1 | 8, mass=1.0, inertia=1.0)  # free rotation of a cylinder
+    Pp = mpm.Points(inputs.make_points(punch), capacity=64 * 2048, velocity=True)
+    st = mpm.step(ctx, punch, Pp, body_z=inputs.body_z(punch, 1), dt=0.01, check=False)
+    assert st["status"] == 1 and "sphere" in ctx.error()
+    # the next call works: the context is still usable
+    st = mpm.step(ctx, cfg, Pv, load=1.0, tol=1e-10, maxit=40, lin_tol=1e-12, dt=cfg["dt"],
+                  body_state=mpm.body_start(cfg), check=False)
+    assert st["status"] == 0
