@@ -553,10 +553,10 @@ __global__ void __launch_bounds__(32 * TW)
   // ghost, then the Dirichlet identity, then the row (and its padding slots,
   // zero) into the sliced storage
   int mr_ = mask[r];
-  int sl = r >> 5, W = S.w[sl];
+  int sr = S.pos[r], sl = sr >> 5, W = S.w[sl];
   long long b0 = S.base[sl];
   for (int i = lane; i < W; i += 32) {
-    long long slot = sliced_slot(b0, r, i);
+    long long slot = sliced_slot(b0, sr, i);
     if (i >= nb) {
 #pragma unroll
       for (int e = 0; e < 9; ++e) K[sliced_entry(b0, W, slot, e)] = (T)0;
@@ -591,7 +591,7 @@ __global__ void k_tangent_mirror(int nd, const int* __restrict__ rp, const int* 
   int r = (int)(t >> 5), lane = (int)(t & 31);
   if (r >= nd) return;
   int s0 = rp[r], nb = rp[r + 1] - s0;
-  int sl = r >> 5, W = S.w[sl];
+  int sr = S.pos[r], sl = sr >> 5, W = S.w[sl];
   long long b0 = S.base[sl];
   for (int i = lane; i < nb; i += 32) {
     int c = col[s0 + i];
@@ -609,12 +609,12 @@ __global__ void k_tangent_mirror(int nd, const int* __restrict__ rp, const int* 
         hi = mid - 1;
     }
     if (j < 0) continue;  // (the pattern is symmetric: never)
-    int slc = c >> 5, Wc = S.w[slc];
-    long long bc = S.base[slc], sc = sliced_slot(bc, c, j - rp[c]);
+    int src = S.pos[c], slc = src >> 5, Wc = S.w[slc];
+    long long bc = S.base[slc], sc = sliced_slot(bc, src, j - rp[c]);
     T v[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) v[e] = K[sliced_entry(bc, Wc, sc, e)];
-    long long slot = sliced_slot(b0, r, i);
+    long long slot = sliced_slot(b0, sr, i);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -622,7 +622,7 @@ __global__ void k_tangent_mirror(int nd, const int* __restrict__ rp, const int* 
   }
 }
 
-// rows beyond ndof in the last slice: zero padding slots
+// rows beyond ndof in the last slice (stored in place): zero padding slots
 template <class T>
 __global__ void k_zero_pad_rows(int nd, int npad, Sliced S, T* K) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -643,10 +643,10 @@ __global__ void k_blocks_export(int nd, const int* __restrict__ rp, Sliced S, co
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int r = (int)(t >> 5), lane = (int)(t & 31);
   if (r >= nd) return;
-  int sl = r >> 5, W = S.w[sl];
+  int sr = S.pos[r], sl = sr >> 5, W = S.w[sl];
   long long b0 = S.base[sl];
   for (int i = lane; i < rp[r + 1] - rp[r]; i += 32) {
-    long long slot = sliced_slot(b0, r, i);
+    long long slot = sliced_slot(b0, sr, i);
     for (int e = 0; e < 9; ++e) out[9 * (size_t)(rp[r] + i) + e] = (double)K[sliced_entry(b0, W, slot, e)];
   }
 }
@@ -938,7 +938,7 @@ __global__ void k_mass_rows(int nd, int P, const long long* __restrict__ sptr,
   int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (r >= nd) return;
   int s0r = rp[r], ma = mask[r];
-  int slc = r >> 5, W = SL.w[slc];
+  int srr = SL.pos[r], slc = srr >> 5, W = SL.w[slc];
   long long b0 = SL.base[slc];
   for (long long q = sptr[r]; q < sptr[r + 1]; ++q) {
     uint32_t sid = (uint32_t)skeys[q];
@@ -951,7 +951,7 @@ __global__ void k_mass_rows(int nd, int P, const long long* __restrict__ sptr,
       int cb = sidx[o];
       int sl = find_slot(rp, col, r, cb);
       if (sl < 0) continue;
-      long long slot = sliced_slot(b0, r, sl - s0r);
+      long long slot = sliced_slot(b0, srr, sl - s0r);
       int mb = mask[cb];
       double v = sk * S[o];
       for (int a = 0; a < 3; ++a) {
@@ -1002,7 +1002,7 @@ __global__ void k_contact_rows(int nrow, const int* __restrict__ crow, const int
   }
   if (!TANGENT) return;
   int s0r = rp[r], ma = mask[r];
-  int slc = r >> 5, W = S.w[slc];
+  int srr = S.pos[r], slc = srr >> 5, W = S.w[slc];
   long long b0 = S.base[slc];
   for (int e = e0; e < e1; ++e) {
     int pk = cent[e], i = pk >> 5;
@@ -1014,7 +1014,7 @@ __global__ void k_contact_rows(int nrow, const int* __restrict__ crow, const int
       int cb = cb_idx[(size_t)i * MAXCB + eb];
       int sl = find_slot(rp, col, r, cb);
       if (sl < 0) continue;
-      long long slot = sliced_slot(b0, r, sl - s0r);
+      long long slot = sliced_slot(b0, srr, sl - s0r);
       int mb = mask[cb];
       double pp = pa * cb_phi[(size_t)i * MAXCB + eb];
       for (int a = 0; a < 3; ++a)
@@ -1097,7 +1097,7 @@ void contact_terms(mpm_ctx* c, mpm_mesh* m, const mpm_material& mat, const mpm_r
   if (couple && bsum)
     MPM_LAUNCH_P(MPM_PROF_CONTACT, k_body_sums<<<1, 256, 0, st>>>(n8, cf, ck, ct, cdv, con, bsum));
   if (!m->nct) return;
-  Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+  Sliced S = sliced_view(m);
   MPM_LAUNCH_P(MPM_PROF_CONTACT, k_contact_rows<T, RES, TANGENT><<<grid_for(m->nct, 4), 128, 0, st>>>(
       m->nct, ptr<int>(m->ct_row), ptr<int>(m->ct_ptr), ptr<int>(m->ct_ent), ptr<int>(m->cb_n),
       ptr<int>(m->cb_idx), ptr<double>(m->cb_phi), cf, ck, con, R, fc, ptr<int>(m->row_ptr),
@@ -1122,7 +1122,7 @@ void tangent_launch(mpm_ctx* c, mpm_mesh* m, bool upper, int lo, int hi, int las
   int tw = (int)std::min<size_t>(TW, (size_t)(220 * 1024) / wb);
   if (tw < 1) throw CudaError(MPM_ERR_SUPPORT, "stiffness row too long for the tangent gather");
   size_t smem = wb * tw;
-  Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+  Sliced S = sliced_view(m);
   auto kern = upper ? k_tangent_rows<T, true> : k_tangent_rows<T, false>;
   MPM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   MPM_LAUNCH_P(MPM_PROF_TANGENT, kern<<<grid_for(nd, tw), 32 * tw, smem, st>>>(
@@ -1182,7 +1182,7 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
   const double* V0 = ptr<double>(m->pV0);
   const int* rp = ptr<int>(m->row_ptr);
   const int* col = ptr<int>(m->col);
-  Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+  Sliced S = sliced_view(m);
   bool mixed = precision == MPM_MIXED;
   size_t asz = mixed ? sizeof(float) : sizeof(double);
   void* Aalg = K ? grow_bytes(c, m->Aalg, 81 * (size_t)P * asz) : nullptr;
@@ -1339,7 +1339,7 @@ void assemble(mpm_ctx* c, const mpm_mesh* mc, const mpm_material& mat, const mpm
 }
 
 void blocks_export(mpm_ctx* c, const mpm_mesh* m, const void* K, int precision, double* out) {
-  Sliced S{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+  Sliced S = sliced_view(m);
   int nd = m->ndof;
   if (precision == MPM_MIXED)
     MPM_LAUNCH(k_blocks_export<float><<<grid_for(32LL * nd, 256), 256, 0, c->stream>>>(nd, ptr<int>(m->row_ptr), S, (const float*)K, out));

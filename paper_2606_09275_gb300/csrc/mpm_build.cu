@@ -1303,12 +1303,37 @@ __global__ void k_tri_vn(int nv, int nt, const double* __restrict__ v, const int
 
 // ------------------------------------------------------------------ sliced storage
 
-// width of each slice of 32 rows: longest row, rounded up to 4 blocks
-__global__ void k_slice_width(int nd, int ns, const int* __restrict__ rp, int* w) {
+// storage order: one block per window of SLICE_WINDOW storage rows, a thread
+// per dof row of the window; the window's dof rows by decreasing length, ties
+// by dof (a rank by counting, so the order is the same on every run); rows at
+// or beyond nd stay in place
+__global__ void k_slice_order(int nd, int npad, const int* __restrict__ rp, int* row, int* pos) {
+  __shared__ int len[SLICE_WINDOW];
+  int w0 = blockIdx.x * SLICE_WINDOW, t = threadIdx.x, r = w0 + t;
+  int n = min(SLICE_WINDOW, max(0, nd - w0));
+  len[t] = t < n ? rp[r + 1] - rp[r] : -1;
+  __syncthreads();
+  if (r >= npad) return;
+  if (t >= n) {
+    row[r] = r;
+    pos[r] = r;
+    return;
+  }
+  int L = len[t], rank = 0;
+  for (int j = 0; j < n; ++j) rank += (len[j] > L) || (len[j] == L && j < t);
+  pos[r] = w0 + rank;
+  row[w0 + rank] = r;
+}
+
+// width of each slice of 32 storage rows: longest row, rounded up to 4 blocks
+__global__ void k_slice_width(int nd, int ns, const int* __restrict__ rp, const int* __restrict__ row, int* w) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= ns) return;
   int m = 0;
-  for (int r = 32 * s; r < min(nd, 32 * s + 32); ++r) m = max(m, rp[r + 1] - rp[r]);
+  for (int sr = 32 * s; sr < 32 * s + 32; ++sr) {
+    int r = row[sr];
+    if (r < nd) m = max(m, rp[r + 1] - rp[r]);
+  }
   w[s] = (m + 3) & ~3;
 }
 
@@ -1322,17 +1347,18 @@ __global__ void k_slice_base64(int ns, const int* __restrict__ pos, long long* b
   if (s < ns) base[s] = pos[s];
 }
 
-// slot columns: the row's sorted columns, then padding slots pointing at the row
+// slot columns of each storage row: its dof row's sorted columns, then padding
+// slots pointing at that row
 __global__ void k_slice_cols(int nd, int ns, const int* __restrict__ rp, const int* __restrict__ col,
                              const int* __restrict__ w, const long long* __restrict__ base,
-                             int* scol) {
+                             const int* __restrict__ row, int* scol) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  int r = (int)(t >> 5), lane = (int)(t & 31);
-  if (r >= 32 * ns) return;
-  int s = r >> 5;
+  int sr = (int)(t >> 5), lane = (int)(t & 31);
+  if (sr >= 32 * ns) return;
+  int s = sr >> 5, r = row[sr];
   int nb = r < nd ? rp[r + 1] - rp[r] : 0;
   for (int idx = lane; idx < w[s]; idx += 32)
-    scol[sliced_slot(base[s], r, idx)] = idx < nb ? col[rp[r] + idx] : (r < nd ? r : 0);
+    scol[sliced_slot(base[s], sr, idx)] = idx < nb ? col[rp[r] + idx] : (r < nd ? r : 0);
 }
 
 // ------------------------------------------------------------------ host helpers
@@ -1682,7 +1708,10 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     int* sw = grow<int>(c, m->slice_w, ns + 1);
     int* slots = grow<int>(c, c->tmp[1], ns + 1);
     int* spos = grow<int>(c, c->tmp[2], ns + 1);
-    MPM_LAUNCH(k_slice_width<<<grid_for(ns, 256), 256, 0, st>>>(nd, ns, rp, sw));
+    int* srow = grow<int>(c, m->srow, 32 * (size_t)ns);
+    int* rpos = grow<int>(c, m->spos, 32 * (size_t)ns);
+    MPM_LAUNCH(k_slice_order<<<(32 * ns + SLICE_WINDOW - 1) / SLICE_WINDOW, SLICE_WINDOW, 0, st>>>(nd, 32 * ns, rp, srow, rpos));
+    MPM_LAUNCH(k_slice_width<<<grid_for(ns, 256), 256, 0, st>>>(nd, ns, rp, srow, sw));
     MPM_LAUNCH(k_slice_slots<<<grid_for(ns, 256), 256, 0, st>>>(ns, sw, slots));
     MPM_CUDA(cudaMemsetAsync(slots + ns, 0, sizeof(int), st));
     cub_exclusive_sum_int(c, slots, spos, ns + 1);
@@ -1690,7 +1719,7 @@ void build_mesh(mpm_ctx* c, mpm_mesh* m, const mpm_domain& dom, const mpm_rigid&
     long long* sb = grow<long long>(c, m->slice_base, ns + 1);
     MPM_LAUNCH(k_slice_base64<<<grid_for(ns + 1, 256), 256, 0, st>>>(ns + 1, spos, sb));
     int* scol = grow<int>(c, m->scol, m->nslot);
-    MPM_LAUNCH(k_slice_cols<<<grid_for(32LL * 32 * ns, 256), 256, 0, st>>>(nd, ns, rp, col, sw, sb, scol));
+    MPM_LAUNCH(k_slice_cols<<<grid_for(32LL * 32 * ns, 256), 256, 0, st>>>(nd, ns, rp, col, sw, sb, srow, scol));
   }
   const int* rp = ptr<int>(m->row_ptr);
   const int* col = ptr<int>(m->col);

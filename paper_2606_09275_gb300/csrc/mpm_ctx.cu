@@ -157,7 +157,7 @@ void mesh_release(mpm_mesh* m) {
                  &m->nsup, &m->sidx, &m->S, &m->dS, &m->populated, &m->betaK,
                  &m->isB, &m->gface, &m->gdof, &m->gn, &m->row_ptr, &m->col, &m->kg, &m->rowcnt,
                  &m->src_key, &m->src_ptr, &m->fext, &m->cand, &m->cb_n, &m->cb_idx, &m->cb_phi,
-                 &m->cb_y0, &m->dF, &m->dFinv, &m->tau, &m->Aalg, &m->gx, &m->slice_w, &m->slice_base, &m->scol,
+                 &m->cb_y0, &m->dF, &m->dFinv, &m->tau, &m->Aalg, &m->gx, &m->slice_w, &m->slice_base, &m->scol, &m->srow, &m->spos,
                  &m->lawst, &m->ct_row, &m->ct_ptr, &m->ct_ent, &m->cc_f, &m->cc_k, &m->cc_on,
                  &m->gJ, &m->gcoef, &m->Mf, &m->V0t, &m->dS32, &m->pv, &m->cc_t, &m->cc_d, &m->cc_b, &m->pma, &m->tri_fn, &m->tri_en, &m->tri_vn};
   for (Buf* b : bufs) free_buf(c, *b);

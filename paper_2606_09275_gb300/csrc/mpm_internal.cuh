@@ -212,6 +212,7 @@ struct mpm_mesh {
   int nslice = 0;
   long long nslot = 0;                  // padded block slots of the sliced storage
   mpm::Buf slice_w, slice_base, scol;   // width, first slot of each slice, slot columns
+  mpm::Buf srow, spos;                  // storage row -> dof row, and back (npad each)
   // sources of each row: (sorted point or ghost face) << 6 | local index
   long long nsrc = 0;
   long long npair = 0;  // sum of squared support sizes (host copy, read after the build)
@@ -248,16 +249,26 @@ struct mpm_mesh {
 };
 
 namespace mpm {
-// position of block idx of row r in the sliced storage (block slot index);
+// The sliced storage of the stiffness: slices of 32 storage rows, each as
+// wide as its longest row rounded up to 4 blocks.  Storage row sr holds the
+// dof row row[sr]: within each window of 256 storage rows (8 slices) the dof
+// rows are ordered by decreasing length (ties by dof), so that the rows of a
+// slice have nearly the same length and the slices carry little padding;
+// pos[] is the inverse map.  Rows beyond ndof (the last slice's padding)
+// are stored in place.  Vectors stay in dof order.
+// sliced_slot: position of block idx of storage row sr (block slot index);
 // entry e of that block lives at values[9*base + e*32*w + slot - base] where
 // base/w are the slice's first slot and width
 struct Sliced {
   const int* w;          // width (blocks) of each slice
   const long long* base; // first slot of each slice
   const int* scol;       // column of each slot (padding slots: the row itself)
+  const int* row;        // dof row of each storage row
+  const int* pos;        // storage row of each dof row
 };
-__host__ __device__ inline long long sliced_slot(long long base, int r, int idx) {
-  return base + ((long long)(idx >> 2) * 32 + (r & 31)) * 4 + (idx & 3);
+constexpr int SLICE_WINDOW = 256;  // storage rows over which the dof rows are sorted
+__host__ __device__ inline long long sliced_slot(long long base, int sr, int idx) {
+  return base + ((long long)(idx >> 2) * 32 + (sr & 31)) * 4 + (idx & 3);
 }
 __host__ __device__ inline long long sliced_entry(long long base, int w, long long slot, int e) {
   return 9 * base + (long long)e * 32 * w + (slot - base);
@@ -288,6 +299,12 @@ inline T* grow(mpm_ctx* c, Buf& b, size_t n) {
 template <class T>
 inline T* ptr(const Buf& b) {
   return (T*)b.p;
+}
+
+// the kernels' view of a mesh's sliced storage
+inline Sliced sliced_view(const mpm_mesh* m) {
+  return Sliced{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol), ptr<int>(m->srow),
+                ptr<int>(m->spos)};
 }
 
 inline void free_buf(mpm_ctx* c, Buf& b) {

@@ -263,12 +263,12 @@ __global__ void k_mg_rap1(int nd, int R, int S, const float* __restrict__ pw,
   double sc = fixed_scale<ACC>(__longlong_as_double((long long)*bnd) * cnt);
   int mi = fmask[i];
   int s0 = rp[i], nb = rp[i + 1] - s0;
-  int sl = i >> 5, W = SK.w[sl];
+  int si = SK.pos[i], sl = si >> 5, W = SK.w[sl];
   long long b0 = SK.base[sl];
   for (int idx = lane; idx < nb; idx += 32) {
     int j = col[s0 + idx];
     int mj = fmask[j];
-    long long slot = sliced_slot(b0, i, idx);
+    long long slot = sliced_slot(b0, si, idx);
     T v[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(32 * kp_warps<T>())
   if (lane == 0) kpc[i] = pack3(ci[0], ci[1], ci[2]);
   int mi = fmask[i];
   int s0 = rp[i], nb = rp[i + 1] - s0;
-  int sl = i >> 5, W = SK.w[sl];
+  int si = SK.pos[i], sl = si >> 5, W = SK.w[sl];
   long long b0 = SK.base[sl];
   bool bad = false;
   for (int base = 0; base < nb; base += 32) {
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(32 * kp_warps<T>())
     if (idx < nb) {
       int j = col[s0 + idx];
       int mj = fmask[j];
-      long long slot = sliced_slot(b0, i, idx);
+      long long slot = sliced_slot(b0, si, idx);
 #pragma unroll
       for (int e = 0; e < 9; ++e) {
         int ca = e / 3, ck = e - 3 * (e / 3);
@@ -551,15 +551,16 @@ __device__ inline void store_inv(const double* a, T* o, int* err, double w) {
 template <class T>
 __global__ void k_mg_dinv_fine(int nd, int npad, Sliced SK, const T* __restrict__ K, T* Dinv, int* err,
                                double w, unsigned long long* bnd) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= npad) return;
+  int sr = blockIdx.x * blockDim.x + threadIdx.x;  // storage row
+  if (sr >= npad) return;
+  int r = SK.row[sr];
   T* o = Dinv + 12 * (size_t)r;
   if (r >= nd) {
     for (int e = 0; e < 12; ++e) o[e] = (T)0;
     return;
   }
   // the row in the access pattern of the SpMV: four slots per 16-byte load
-  int sl = r >> 5, ln = r & 31, W = SK.w[sl];
+  int sl = sr >> 5, ln = sr & 31, W = SK.w[sl];
   long long b0 = SK.base[sl];
   const T* Kb = K + 9 * b0;
   const int* cb = SK.scol + b0;
@@ -757,17 +758,18 @@ __global__ void __launch_bounds__(256, 4) k_mg_fine(int nd, int npad, Sliced SK,
                           T* out, const int* __restrict__ fmask, double* rz, const Scal* sk, int k,
                           GridRed gr) {
   if (skip(sk, k)) return;
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int sr = blockIdx.x * blockDim.x + threadIdx.x;  // storage row
   double part = 0.0;
-  if (r < npad) {
+  if (sr < npad) {
+    int r = SK.row[sr];
     T y[3];
     if constexpr (sizeof(TK) == 2) {
       float yf[3];
-      sliced_row_h(r, SK, (const __half*)K, (const float*)x, yf);
+      sliced_row_h(sr, SK, (const __half*)K, (const float*)x, yf);
       float ks = *kscale;
       for (int c = 0; c < 3; ++c) y[c] = (T)(yf[c] * ks);
     } else {
-      sliced_row<T, T, T, 4>(r, SK, (const T*)K, x, y);
+      sliced_row<T, T, T, 4>(sr, SK, (const T*)K, x, y);
     }
     T bv[4], res[4];
     ld4(b + 4 * (size_t)r, bv);
@@ -1139,7 +1141,7 @@ void mg_numeric(mpm_ctx* c, mpm_mesh* m, const T* K, bool coarse) {
   cudaStream_t st = c->stream;
   MGData& G = *m->mg;
   int nd = m->ndof, npad = 32 * m->nslice;
-  Sliced SK{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+  Sliced SK = sliced_view(m);
   // fine smoother and V-cycle vectors; bnd[l]: largest row l1 norm of the
   // level-l operator (l = 0 the fine matrix), the Galerkin products' bounds
   unsigned long long* bnd = grow<unsigned long long>(c, G.bound, 16);
@@ -1236,7 +1238,7 @@ void vcycle_launch(mpm_ctx* c, const mpm_mesh* mc, const T* K, const T* r, T* z,
   cudaStream_t st = c->stream;
   MGData& G = *m->mg;
   int nd = m->ndof, npad = 32 * m->nslice;
-  Sliced SK{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
+  Sliced SK = sliced_view(m);
   const int* fmask = ptr<int>(m->dof_mask);
   T* fx = ptr<T>(G.fx);
   const T* fD = ptr<T>(G.fDinv);

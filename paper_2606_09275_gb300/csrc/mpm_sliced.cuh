@@ -25,8 +25,9 @@ __device__ inline void st4(double* p, const double* v) {
   *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
 }
 
-// y = row r of K times x, sliced storage (one thread per row; a warp is one
-// slice).  XS = 4: x padded to 4 components per dof; XS = 3: plain 3-vectors.
+// y = storage row r of K (dof row S.row[r]) times x, sliced storage (one
+// thread per storage row; a warp is one slice).  XS = 4: x padded to 4
+// components per dof; XS = 3: plain 3-vectors.
 template <class T, class V, class A, int XS>
 __device__ inline void sliced_row(int r, Sliced S, const T* __restrict__ K,
                                   const V* __restrict__ x, A* y) {
@@ -73,7 +74,7 @@ __device__ inline void apply_dinv(const V* __restrict__ Dinv, size_t i, const V*
   zv[3] = (V)0;
 }
 
-// y = row r of K times x with FP32 values and FP64 x, accumulated in
+// y = storage row r of K times x with FP32 values and FP64 x, accumulated in
 // double-float arithmetic: each product k * x is split exactly as
 // k * x_hi = p + e (Dekker's two-product through one fused multiply-add),
 // k * x_lo is added to the error term, and p enters a (hi, lo) pair of floats
@@ -189,7 +190,7 @@ __device__ inline void load_h4(const __half* Kb, size_t plane, size_t off, uint4
   u8 = *reinterpret_cast<const uint2*>(Kb + 8 * plane + off);
 }
 
-// y = row r of the FP16 copy of K (values scaled by a power of two) times x;
+// y = storage row r of the FP16 copy of K (values scaled by a power of two) times x;
 // FP32 arithmetic, the caller undoes the scale.  Two groups of four blocks
 // per trip, all of their loads issued before the arithmetic: FP16 blocks are
 // half the bytes of FP32 ones, so a trip over one group would keep half as

@@ -42,8 +42,8 @@ __global__ void k_block_jacobi(int nd, const int* __restrict__ rp, const int* __
     else
       hi = mid - 1;
   }
-  int sl = r >> 5;
-  long long b0 = S.base[sl], slot = k >= 0 ? sliced_slot(b0, r, k) : 0;
+  int sr = S.pos[r], sl = sr >> 5;
+  long long b0 = S.base[sl], slot = k >= 0 ? sliced_slot(b0, sr, k) : 0;
   double a[9];
   for (int e = 0; e < 9; ++e)
     a[e] = k >= 0 ? (double)K[sliced_entry(b0, S.w[sl], slot, e)] : (double)(e % 4 == 0);
@@ -103,11 +103,12 @@ __global__ void k_pcg_init(int nd, int npad, const double* __restrict__ b, const
 template <class T, class V>
 __global__ void k_pcg_q0(int nd, int npad, Sliced S, const T* __restrict__ K, const V* __restrict__ p,
                          V* q, Scal* sc, GridRed gr) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int sr = blockIdx.x * blockDim.x + threadIdx.x;  // storage row
   double part = 0.0;
-  if (r < npad) {
+  if (sr < npad) {
+    int r = S.row[sr];
     V y[3];
-    sliced_row<T, V, V, 4>(r, S, K, p, y);
+    sliced_row<T, V, V, 4>(sr, S, K, p, y);
     V yv[4] = {y[0], y[1], y[2], (V)0};
     if (r >= nd) yv[0] = yv[1] = yv[2] = (V)0;
     st4(q + 4 * (size_t)r, yv);
@@ -208,11 +209,12 @@ __global__ void k_pcg_b(int nd, int npad, int k, Sliced S, const T* __restrict__
     sc->rz[i2] = 0.0;
     sc->rr[i2] = 0.0;
   }
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int sr = blockIdx.x * blockDim.x + threadIdx.x;  // storage row
   double part = 0.0;
-  if (r < npad) {
+  if (sr < npad) {
+    int r = S.row[sr];
     V y[3];
-    sliced_row<T, V, V, 4>(r, S, K, z, y);
+    sliced_row<T, V, V, 4>(sr, S, K, z, y);
     if (r < nd) {
       V zv[4], pv[4], qv[4];
       ld4(z + 4 * (size_t)r, zv);
@@ -242,11 +244,12 @@ __global__ void k_spmv_dot(int nd, int npad, Sliced S, const T* __restrict__ K,
                            const V* __restrict__ x, V* y, const V* __restrict__ a,
                            double* slot, double* slot2, const Scal* sc, int check_s, GridRed gr) {
   if (sc->done || (check_s && sc->a[5] <= sc->thr)) return;
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  int sr = blockIdx.x * blockDim.x + threadIdx.x;  // storage row
   double p1 = 0.0, p2 = 0.0;
-  if (r < npad) {
+  if (sr < npad) {
+    int r = S.row[sr];
     V v[3];
-    sliced_row<T, V, V, 4>(r, S, K, x, v);
+    sliced_row<T, V, V, 4>(sr, S, K, x, v);
     if (r >= nd) v[0] = v[1] = v[2] = (V)0;
     V yv[4] = {v[0], v[1], v[2], (V)0};
     st4(y + 4 * (size_t)r, yv);
@@ -414,14 +417,15 @@ __global__ void k_residual64(int nd, int npad, Sliced S, const T* __restrict__ K
                              const double* __restrict__ x, const float4* __restrict__ xs,
                              const double* __restrict__ b, const int* __restrict__ mask, double* r,
                              double* slot, GridRed gr) {
-  int rr = blockIdx.x * blockDim.x + threadIdx.x;
+  int sr = blockIdx.x * blockDim.x + threadIdx.x;  // storage row
   double part = 0.0;
-  if (rr < npad) {
+  if (sr < npad) {
+    int rr = S.row[sr];
     double y[3];
     if constexpr (sizeof(T) == 4)
-      sliced_row_df(rr, S, (const float*)K, xs, y);
+      sliced_row_df(sr, S, (const float*)K, xs, y);
     else
-      sliced_row<T, double, double, 3>(rr, S, K, x, y);
+      sliced_row<T, double, double, 3>(sr, S, K, x, y);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     if (rr < nd) {
       int mk = mask[rr];
@@ -463,9 +467,7 @@ const float4* residual_split(mpm_ctx* c, const mpm_mesh* m, const T* K, const do
   }
 }
 
-Sliced sliced_of(const mpm_mesh* m) {
-  return Sliced{ptr<int>(m->slice_w), ptr<long long>(m->slice_base), ptr<int>(m->scol)};
-}
+Sliced sliced_of(const mpm_mesh* m) { return sliced_view(m); }
 
 template <class T, class V>
 int run_pcg(mpm_ctx* c, const mpm_mesh* m, const T* K, const V* Dinv, const double* b, V* x,
@@ -654,10 +656,11 @@ int run_bicgstab(mpm_ctx* c, const mpm_mesh* m, const T* K, const T* Dinv, const
 template <class T, class V>
 __global__ void k_gm_residual(int nd, int npad, Sliced S, const T* __restrict__ K, const V* __restrict__ x,
                               const double* __restrict__ b, const int* __restrict__ mask, V* r) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= npad) return;
+  int sr = blockIdx.x * blockDim.x + threadIdx.x;  // storage row
+  if (sr >= npad) return;
+  int i = S.row[sr];
   V y[3];
-  sliced_row<T, V, V, 4>(i, S, K, x, y);
+  sliced_row<T, V, V, 4>(sr, S, K, x, y);
   V rv[4] = {(V)0, (V)0, (V)0, (V)0};
   if (i < nd) {
     int mi = mask[i];
@@ -683,10 +686,11 @@ __global__ void k_gm_dinv(int nd, int npad, const V* __restrict__ Dinv, const V*
 
 template <class T, class V>
 __global__ void k_gm_spmv(int nd, int npad, Sliced S, const T* __restrict__ K, const V* __restrict__ z, V* w) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= npad) return;
+  int sr = blockIdx.x * blockDim.x + threadIdx.x;  // storage row
+  if (sr >= npad) return;
+  int i = S.row[sr];
   V y[3];
-  sliced_row<T, V, V, 4>(i, S, K, z, y);
+  sliced_row<T, V, V, 4>(sr, S, K, z, y);
   V wv[4] = {y[0], y[1], y[2], (V)0};
   if (i >= nd) wv[0] = wv[1] = wv[2] = (V)0;
   st4(w + 4 * (size_t)i, wv);

@@ -200,12 +200,16 @@ def workload(name, **over):
                  points=dict(lo=(0, 0, 0), hi=(6.4, 6.4, 24.6), spacing=0.8,
                              rho=16.3e3 / 9.81, E=19.2e6, ys=300.0, jitter=0.1, seed=0))
     elif name == "adjoint":
-        # the punch at depth 3 to 5, 20 load steps, lognormal E (sigma 0.2)
+        # the punch at depth 3 to 5, 20 load steps, lognormal E (sigma 0.2);
+        # centres jittered by U(-h/8, h/8) as in the indentation recipes, so
+        # that no domain face starts on a cell plane (there the far field's
+        # tiny displacements decide whether a cell is populated, and the
+        # discrete events of a run flip under any perturbation of the input)
         c.update(L=1.0, depth_min=3, depth_max=5, bc=_block_rollers(1.0, 1.0), model=1,
                  body=dict(kind=1, cx=0.5, cy=0.5, z0=0.5, r=0.1, alpha=0.0, dz=-0.1 / 50),
                  dx_region=2.0 / 32, nsteps=20,
                  points=dict(lo=(0, 0, 0), hi=(1, 1, 0.5), spacing=1.0 / 16, rho=1000.0,
-                             E=1e7, ys=1e5, E_sigma=0.2, seed=0))
+                             E=1e7, ys=1e5, E_sigma=0.2, seed=0, jitter=1.0 / 128))
     elif name == "cone_1m":
         # the cone of "cone" at the ~1M-DOF scale: the same Drucker-Prager layer
         # and cone on a depth-6 far field (0.025 m cells, 2x2x2 points per cell,

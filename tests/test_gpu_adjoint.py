@@ -24,7 +24,7 @@ W = (0.0, 0.0, 1.0)
 
 def adj_cfg(**over):
     c = inputs.workload("adjoint", depth_min=2, depth_max=4, dx_region=2.0 / 16,
-                        points=dict(spacing=1.0 / 8, E_sigma=0.2, seed=3))
+                        points=dict(spacing=1.0 / 8, E_sigma=0.2, seed=3, jitter=0.0))
     c.update(over)
     return c
 
