@@ -751,9 +751,13 @@ __global__ void k_mg_jac0(int n, const T* __restrict__ Dinv, const T* __restrict
 
 // fine level: MODE 0, out = b - K x with the Dirichlet components zeroed (the
 // residual that k_mg_restrict1 gathers to level 1); MODE 1, out = x + Dinv
-// (b - K x) with r.z += b.out by a fixed-order grid sum (rz non-null)
+// (b - K x) with r.z += b.out by a fixed-order grid sum (rz non-null).
+// Bounded to 2 resident blocks of 256 per SM: with the FP16 row product's two
+// groups of loads in flight the kernel needs about 96 registers; at 4 blocks
+// (64 registers) it spilled and ran 10 % slower (0.120 against 0.108 ms at
+// 248 k rows)
 template <class T, int MODE, class TK>
-__global__ void __launch_bounds__(256, 4) k_mg_fine(int nd, int npad, Sliced SK, const TK* __restrict__ K, const float* kscale,
+__global__ void __launch_bounds__(256, 2) k_mg_fine(int nd, int npad, Sliced SK, const TK* __restrict__ K, const float* kscale,
                           const T* __restrict__ b, const T* __restrict__ x, const T* __restrict__ Dinv,
                           T* out, const int* __restrict__ fmask, double* rz, const Scal* sk, int k,
                           GridRed gr) {
