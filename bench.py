@@ -676,6 +676,23 @@ def gpu_main(a):
                "kernels": {n: {"launches": cp["launches"][i], "ms": round(cp["ms"][i], 3)}
                            for i, n in enumerate(PROF_NAMES) if cp["launches"][i]},
                "kernels_note": "per-launch CUDA events on in this run (adds about 1 us per launch)"}
+        try:
+            # the BiCGStab SpMV (FP32 K, FP32 vectors padded to 4 components):
+            # values and columns once, x, y and the dot's second vector per row
+            ib = PROF_NAMES.index("bicgstab_spmv")
+            nlb, msb = cp["launches"][ib], cp["ms"][ib]
+            if nlb:
+                perb = msb / nlb
+                byb = cl["nnzb"] * (9 * 4 + 4) + 48 * cn
+                gbs = byb / (perb * 1e-3) / 1e9
+                ent["roofline_bicgstab_spmv"] = {
+                    "kernel": "k_spmv_dot<float,float>", "bound": "hbm", "avg_ms": round(perb, 5),
+                    "launches": nlb, "algorithmic_bytes": int(byb), "achieved_gbs": round(gbs, 1),
+                    "hbm_frac": round(gbs / hbm_peak, 4),
+                    "note": "average over every launch of the class, including the few that "
+                            "return at once after convergence"}
+        except Exception as ex:  # a report field only: never lose the line for it
+            ent["roofline_bicgstab_spmv"] = {"error": str(ex)[:120]}
         if cone64:
             c64 = cone64["its_all"] / (cone64["ms"] * 1e-3)
             ent["fp64"] = {"value": round(c64, 4), "unit": "Newton it/s",

@@ -239,8 +239,11 @@ __global__ void k_pcg_b(int nd, int npad, int k, Sliced S, const T* __restrict__
 
 // y = K x (+ optional dots a.y into slot and y.y into slot2).  Skipped once
 // the solve is done, or (check_s) once the half-step residual s has converged.
+// Bounded to 4 resident blocks of 256 per SM (64 registers): left to itself
+// the compiler took 72, which allows 3, and the launch ran at 0.337 against
+// 0.281 ms (FP32, 41.7 M blocks)
 template <class T, class V>
-__global__ void k_spmv_dot(int nd, int npad, Sliced S, const T* __restrict__ K,
+__global__ void __launch_bounds__(256, 4) k_spmv_dot(int nd, int npad, Sliced S, const T* __restrict__ K,
                            const V* __restrict__ x, V* y, const V* __restrict__ a,
                            double* slot, double* slot2, const Scal* sc, int check_s, GridRed gr) {
   if (sc->done || (check_s && sc->a[5] <= sc->thr)) return;
