@@ -364,14 +364,16 @@ def replica_totals(its, ms, world, dev):
     return int(round(t_its.item())), float(t_ms.item())
 
 
-def adjoint_leg(dev, method):
+def adjoint_leg(dev, method, name="adjoint"):
     """Cost of the discrete adjoint against the forward run it differentiates:
     the punch at depth 3 -> 5 with lognormal E, 20 load steps, FP64, gradient
-    of the final vertical punch reaction in every point's E and yield stress."""
+    of the final vertical punch reaction in every point's E and yield stress;
+    `name` picks the point lattice ("adjoint": spacing 1/16, "adjoint_60k":
+    spacing 1/48)."""
     import torch
 
     from paper_2606_09275_gb300 import autodiff, inputs, mpm
-    cfg = inputs.workload("adjoint")
+    cfg = inputs.workload(name)
     pts = inputs.make_points(cfg)
     ctx = mpm.Context()
     path = autodiff.LoadPath(ctx, cfg, pts, cfg["nsteps"], tol=cfg["newton_tol"],
@@ -393,8 +395,10 @@ def adjoint_leg(dev, method):
     n = cfg["nsteps"]
     fwd, fwd_ck, adj = (e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3]))
     ctx.close()
-    return {"workload": "adjoint: flat punch into a von Mises block 1x1x0.5 m, depth 3 -> 5, "
-                        "lognormal E (sigma 0.2), %d load steps, FP64, d(reaction_z)/d(E, ys)" % n,
+    return {"workload": "%s: flat punch into a von Mises block 1x1x0.5 m, depth 3 -> 5, "
+                        "lognormal E (sigma 0.2), %d load steps, FP64, d(reaction_z)/d(E, ys)"
+                        % (name, n),
+            "points_first_step": st_plain[0]["npts"], "initial_points": len(pts["x"]),
             "points_last_step": st_plain[-1]["npts"], "dof_last_step": 3 * st_plain[-1]["ndof"],
             "forward_ms_per_step": round(fwd / n, 3),
             "forward_with_checkpoints_ms_per_step": round(fwd_ck / n, 3),
@@ -723,8 +727,14 @@ def gpu_main(a):
             "fp64_at_1e-8_vs_1e-10_first_event_divergence_step": e64["first_event_divergence_step"],
             "per_step_reaction_rel": [s_["reaction_rel"] for s_ in cmp["per_step"]]}
     if not a.no_adjoint:
-        # the adjoint workload is small (about a thousand dofs): block-Jacobi PCG
-        line["adjoint"] = adjoint_leg(dev, 1)
+        # the adjoint workloads are small (about a thousand nodes): block-Jacobi
+        # PCG; "adjoint" at about 67 k points, "adjoint_small" on the 2,048-point
+        # lattice of the 32-point finite-difference test
+        for key, name in (("adjoint", "adjoint_60k"), ("adjoint_small", "adjoint")):
+            try:
+                line[key] = adjoint_leg(dev, 1, name)
+            except Exception as ex:  # recorded in the line; the other legs still run
+                line[key] = {"workload": name, "error": "%s: %s" % (type(ex).__name__, ex)}
     if not a.no_dynamics:
         line["rolling_sphere"] = dynamics_leg(dev)
     if not a.no_cpu:

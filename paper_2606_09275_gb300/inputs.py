@@ -210,6 +210,12 @@ def workload(name, **over):
                  dx_region=2.0 / 32, nsteps=20,
                  points=dict(lo=(0, 0, 0), hi=(1, 1, 0.5), spacing=1.0 / 16, rho=1000.0,
                              E=1e7, ys=1e5, E_sigma=0.2, seed=0, jitter=1.0 / 128))
+    elif name == "adjoint_60k":
+        # the same punch and mesh with the points three times finer per axis
+        # (spacing 1/48, 6x6x6 per depth-3 cell, jitter U(-h/8, h/8)): 55,296
+        # points at the start, about 67 k after the first step's splits
+        c = workload("adjoint")
+        c["points"].update(spacing=1.0 / 48, jitter=1.0 / 384)
     elif name == "cone_1m":
         # the cone of "cone" at the ~1M-DOF scale: the same Drucker-Prager layer
         # and cone on a depth-6 far field (0.025 m cells, 2x2x2 points per cell,
