@@ -225,6 +225,24 @@ def _p(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _check_vec(fn, name, t, dtype, n):
+    """The library cannot see the size or type of a device buffer, so every
+    tensor handed to it is checked here: contiguous, `dtype`, exactly `n`
+    entries, on the current CUDA device."""
+    ok = (isinstance(t, torch.Tensor) and t.dtype == dtype and t.is_cuda and
+          t.device.index == torch.cuda.current_device() and t.is_contiguous() and t.numel() == n)
+    if not ok:
+        got = ("%s %s[%d] on %s%s" % (type(t).__name__, t.dtype, t.numel(), t.device,
+                                      "" if t.is_contiguous() else ", not contiguous")
+               if isinstance(t, torch.Tensor) else type(t).__name__)
+        raise MPMError(1, "%s: %s must be a contiguous %s tensor of %d entries on the current "
+                          "CUDA device (got %s)" % (fn, name, dtype, n, got))
+
+
+def _k_dtype(precision):
+    return torch.float32 if precision == MIXED else torch.float64
+
+
 def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -378,11 +396,11 @@ def assemble(ctx, mesh, cfg, du, load=1.0, precision=FP64, tangent=True, body_z=
     """mpm_assemble: residual R (and the tangent values) at the increment du."""
     info = mesh.info()
     nd, ns = info["ndof"], info["nslot"]
+    _check_vec("assemble", "du", du, torch.float64, 3 * nd)
     R = torch.empty(3 * nd, dtype=torch.float64, device=du.device)
     K = None
     if tangent:
-        K = torch.empty(9 * max(ns, 1), dtype=torch.float32 if precision == MIXED else torch.float64,
-                        device=du.device)
+        K = torch.empty(9 * max(ns, 1), dtype=_k_dtype(precision), device=du.device)
     reac = (C.c_double * 3)()
     norms = (C.c_double * 2)()
     st = lib().mpm_assemble(ctx.h, mesh.h, C.byref(material(cfg)), C.byref(rigid(cfg, body_z)),
@@ -397,11 +415,13 @@ def assemble_body(ctx, mesh, cfg, du, q, dt, load=1.0, precision=FP64, tangent=T
     (device [6, 3 ndof])."""
     info = mesh.info()
     nd, ns = info["ndof"], info["nslot"]
+    _check_vec("assemble_body", "du", du, torch.float64, 3 * nd)
+    if len(q) != 6:
+        raise MPMError(1, "assemble_body: q must hold 6 values (translation, rotation)")
     R = torch.empty(3 * nd, dtype=torch.float64, device=du.device)
     K = Kgb = Kbg = None
     if tangent:
-        K = torch.empty(9 * max(ns, 1), dtype=torch.float32 if precision == MIXED else torch.float64,
-                        device=du.device)
+        K = torch.empty(9 * max(ns, 1), dtype=_k_dtype(precision), device=du.device)
         Kgb = torch.empty((6, 3 * nd), dtype=torch.float64, device=du.device)
         Kbg = torch.empty((6, 3 * nd), dtype=torch.float64, device=du.device)
     qv = (C.c_double * 6)(*[float(v) for v in q])
@@ -420,7 +440,11 @@ def assemble_body(ctx, mesh, cfg, du, q, dt, load=1.0, precision=FP64, tangent=T
 def solve(ctx, mesh, cfg, K, rhs, precision=FP64, tol=1e-10, maxit=20000, method=0,
           inner_tol=1e-3, mg_reuse=0):
     """mpm_solve: block-Jacobi PCG, BiCGStab or multigrid PCG / BiCGStab (method 3); FP32
-    inner solves inside FP64 refinement when mixed."""
+    inner solves inside FP64 refinement when mixed.  K holds mpm_assemble's values for the
+    same precision (FP32 when mixed), rhs 3 * ndof doubles."""
+    info = mesh.info()
+    _check_vec("solve", "K", K, _k_dtype(precision), 9 * max(info["nslot"], 1))
+    _check_vec("solve", "rhs", rhs, torch.float64, 3 * info["ndof"])
     x = torch.empty_like(rhs)
     sp = SolveParams(method, precision, tol, maxit, inner_tol, mg_reuse)
     ss = SolveStats()
@@ -439,13 +463,8 @@ def solve_static(ctx, mesh, K, rhs, tol=1e-10, maxit=20000):
     both contiguous on the current CUDA device: the library cannot check the
     size of a device buffer, so they are checked here."""
     info = mesh.info()
-    dev = torch.cuda.current_device()
-    for name, t, n in (("K", K, 9 * max(info["nslot"], 1)), ("rhs", rhs, 3 * info["ndof"])):
-        ok = (isinstance(t, torch.Tensor) and t.dtype == torch.float64 and t.is_cuda and
-              t.device.index == dev and t.is_contiguous() and t.numel() == n)
-        if not ok:
-            raise MPMError(1, "solve_static: %s must be a contiguous float64 tensor of %d entries "
-                              "on cuda:%d" % (name, n, dev))
+    _check_vec("solve_static", "K", K, torch.float64, 9 * max(info["nslot"], 1))
+    _check_vec("solve_static", "rhs", rhs, torch.float64, 3 * info["ndof"])
     x = torch.empty_like(rhs)
     ss = SolveStats()
     st = lib().mpm_solve_static(ctx.h, mesh.h, _p(K), _p(rhs), _p(x), tol, maxit, C.byref(ss))
@@ -508,7 +527,9 @@ def fp64_peak(ctx, seconds=1.0):
 
 def blocks(ctx, mesh, K, precision=FP64):
     """mpm_blocks_export: stiffness values -> host array [nnzb, 3, 3] in CSR order."""
-    nz = mesh.info()["nnzb"]
+    info = mesh.info()
+    _check_vec("blocks", "K", K, _k_dtype(precision), 9 * max(info["nslot"], 1))
+    nz = info["nnzb"]
     out = np.zeros((max(nz, 1), 3, 3))
     ctx.check(lib().mpm_blocks_export(ctx.h, mesh.h, _p(K), precision,
                                       out.ctypes.data_as(C.c_void_p)))

@@ -30,3 +30,18 @@ def test_library_exports_every_declared_symbol():
 def test_binding_names_match_header():
     from paper_2606_09275_gb300 import mpm
     assert set(mpm.SYMBOLS) <= set(declared_symbols())
+
+
+def test_binding_refuses_host_or_missized_buffers_before_the_call():
+    # the library cannot see a device buffer's size or type: the binding checks
+    # every tensor it hands over (no GPU needed, nothing reaches the library)
+    import numpy as np
+    import pytest
+    import torch
+    from paper_2606_09275_gb300 import mpm
+    for bad in (torch.zeros(6, dtype=torch.float64), np.zeros(6),
+                torch.zeros(6, dtype=torch.float32), torch.zeros(12, dtype=torch.float64)[::2]):
+        with pytest.raises(mpm.MPMError) as e:
+            mpm._check_vec("solve", "rhs", bad, torch.float64, 6)
+        assert e.value.code == 1 and "rhs" in str(e.value)
+    assert mpm._k_dtype(mpm.MIXED) == torch.float32 and mpm._k_dtype(mpm.FP64) == torch.float64
