@@ -225,18 +225,21 @@ def _p(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
-def _check_vec(fn, name, t, dtype, n):
+def _check_vec(fn, name, t, dtype, n=None):
     """The library cannot see the size or type of a device buffer, so every
     tensor handed to it is checked here: contiguous, `dtype`, exactly `n`
-    entries, on the current CUDA device."""
+    entries (any number when n is None: the caller passes the count), on the
+    current CUDA device."""
     ok = (isinstance(t, torch.Tensor) and t.dtype == dtype and t.is_cuda and
-          t.device.index == torch.cuda.current_device() and t.is_contiguous() and t.numel() == n)
+          t.device.index == torch.cuda.current_device() and t.is_contiguous() and
+          (n is None or t.numel() == n))
     if not ok:
         got = ("%s %s[%d] on %s%s" % (type(t).__name__, t.dtype, t.numel(), t.device,
                                       "" if t.is_contiguous() else ", not contiguous")
                if isinstance(t, torch.Tensor) else type(t).__name__)
-        raise MPMError(1, "%s: %s must be a contiguous %s tensor of %d entries on the current "
-                          "CUDA device (got %s)" % (fn, name, dtype, n, got))
+        raise MPMError(1, "%s: %s must be a contiguous %s tensor%s on the current CUDA device "
+                          "(got %s)" % (fn, name, dtype, "" if n is None else " of %d entries" % n,
+                                        got))
 
 
 def _k_dtype(precision):
@@ -490,6 +493,8 @@ def step(ctx, cfg, points, body_z=None, load=1.0, tol=1e-8, maxit=30, lin_tol=1e
     the statistics.  du_out (optional float64 device tensor) receives the
     converged increment.  body_state (a free body's pose and velocities at
     the step start, see body_start) is advanced in place."""
+    if du_out is not None:
+        _check_vec("step", "du_out", du_out, torch.float64)
     s = points.struct()
     sp = StepParams(load, tol, maxit, SolveParams(method, precision, lin_tol, lin_maxit, inner_tol,
                                                   mg_reuse),
@@ -551,6 +556,8 @@ def adjoint(ctx, cfg, checkpoints, w, tol=1e-8, maxit=30, lin_tol=1e-10, lin_max
     for k, ck in enumerate(checkpoints):
         pts, bz, ld = ck[:3]
         du = ck[3] if len(ck) > 3 else None
+        if du is not None:
+            _check_vec("adjoint", "checkpoint %d's du" % k, du, torch.float64)
         arr[k].pts = pts.struct()
         arr[k].body_z = bz
         arr[k].load = ld

@@ -45,3 +45,5 @@ def test_binding_refuses_host_or_missized_buffers_before_the_call():
             mpm._check_vec("solve", "rhs", bad, torch.float64, 6)
         assert e.value.code == 1 and "rhs" in str(e.value)
     assert mpm._k_dtype(mpm.MIXED) == torch.float32 and mpm._k_dtype(mpm.FP64) == torch.float64
+    with pytest.raises(mpm.MPMError):
+        mpm._check_vec("step", "du_out", torch.zeros(6, dtype=torch.float32), torch.float64)
