@@ -10,7 +10,10 @@ the mixed-precision path on the headline workload (`indent`, the punch at
 ~0.75 M unknowns); the FP64 path is timed on the same steps and the two are
 compared step by step (events and reactions).  The ~1 M-DOF Drucker-Prager
 cone (`cone_1m`, non-symmetric tangent, multigrid BiCGStab) is timed beside it.
-Multi-GPU runs are independent replicas (the path has no data-parallel
+Further keys: the discrete adjoint's cost against the forward run it
+differentiates, 20 load steps of the punch at depth 3 -> 5 with about 70 k
+points (`adjoint`) and with 9.5 k (`adjoint_small`); Newmark time steps of the
+rolling sphere with a free rigid body (`rolling_sphere`).  Multi-GPU runs are independent replicas (the path has no data-parallel
 exchange at this level), so scaling is weak.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
