@@ -1,7 +1,7 @@
 """Python wrapper of the FP64 CPU oracle (ctypes over oracle/liboracle.so).
 
 TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the CPU-baseline
-leg of the benchmark use it; the product path never imports it.  It shares no
+and reference legs of the benchmark use it; the product path never imports it.  It shares no
 code with the CUDA library; inputs come from the seeded generators in
 paper_2606_09275_gb300.inputs, passed in as plain arrays and dicts.
 """

@@ -5,7 +5,8 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This library is the plain, slow reference that the
  * GPU path is checked against.  Only the test-suite, the smoke check and the
- * CPU-baseline leg of the benchmark may load it; the product path never does.
+ * CPU-baseline and reference legs of the benchmark may load it; the product
+ * path never does.
  * It shares no code, header or table with the CUDA library.
  *
  * Everything is double precision, single threaded, written as plain loops in
