@@ -129,9 +129,10 @@ def test_adjoint_twenty_load_steps_matches_finite_differences(gpu):
 def test_adjoint_sixty_thousand_points_matches_finite_differences(gpu):
     # the same punch with 55,296 points at the start (spacing 1/48), over its
     # first 8 load steps, FD on 12 seeded points; over all 20 steps every one
-    # of 8 sampled points moved an event (the oracle shows the same for its
-    # first point, with both signs of the perturbation moving the same events
-    # the same way: ties that any change of the input's bits decides)
+    # of 8 sampled points moved an event: at about load step 12 this finer
+    # block reaches its plastic limit load, where the step's solution is not
+    # unique and the last bits of the start decide which one Newton reaches
+    # (the oracle: both perturbed runs 0.63 mm from the base run there)
     checked, worst, stats = adjoint_against_fd(gpu, "adjoint_60k", 8, 12, 12)
     print("adjoint_60k, 8 steps: %d points at step 1, %d at step 8; %d of 12 points keep their "
           "events; largest |FD - adjoint| %.2e of max |dJ/dE|"
