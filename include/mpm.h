@@ -257,7 +257,7 @@ enum {
   MPM_EXPORT_GHOST_FACES = 17, /* int[4*nghost]: K, N, axis, sign              */
   MPM_EXPORT_MG_LEVELS = 18    /* int[32]: per multigrid coarse level (up to 8):
                                   depth, rows, stencil radius, stencil size;
-                                  zeros until a method-3 solve on this build */
+                                  zeros until a method-3 solve on this mesh */
 };
 int mpm_mesh_export(const mpm_mesh* mesh, int what, void* dst, size_t bytes);
 

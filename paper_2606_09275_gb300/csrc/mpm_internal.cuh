@@ -235,7 +235,7 @@ struct mpm_mesh {
   mpm::Buf dF, dFinv, tau, Aalg, gx, Mf, V0t;
   mpm::Buf dS32;                        // FP32 copy of dS for the mixed tangent's grad_x S
   mpm::Buf pv;                          // sorted point velocities (time steps)
-  bool has_v = false;                   // the points of this build carried velocities
+  bool has_v = false;                   // the points of this mesh build carried velocities
   mpm::Buf cc_t, cc_d;                  // per contact corner: d f / d(rotation), offset from the body centre
   mpm::Buf cc_b;                        // the body's contact sums (42 doubles)
   mpm::Buf pma;                         // per point m_p a_p of a time step
